@@ -1,0 +1,302 @@
+"""Benchmark: coupled-field MLUPS of the multirate MRT-LBM on B300.
+
+Workload: the thermosolutal free dendrite with forced convection on a
+512 x 512 lattice (phi, U, T on D2Q9 plus D2Q9 flow; update factors
+phi 1, U 1, T 2, flow 2; k = 0.15, Le = 10, inlet velocity 0.01 from the left,
+outflow right, periodic top/bottom, seed radius 8), FP32 storage and
+arithmetic, synthetic seeded inputs.
+
+One step = one schedule period = 2 base steps, in which every field updates
+at least once (phase x2, transfer x2, U x2, T x1, flow x1).  Coupled-field
+MLUPS = lattice nodes x base steps / s / 1e6.  L2 is flushed (a 512 MiB
+buffer written) between timed steps, and each step is timed on the device
+with CUDA events on the library's stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only other implementation of
+the method here) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+N_LATTICE = 512
+STEP_BASE = 2          # base steps per bench step (one schedule period)
+METRIC = "coupled-field MLUPS"
+UNIT = "MLUPS"
+
+# algorithmic bytes per node of one launch, FP32 storage (8 stored
+# populations read + written, each macro read / written once)
+ALGO_BYTES = {
+    "phase": 8 * 4 * 2 + 4 + 4 + 4 + 4,        # pops R+W, phi^q R, U R, T R, phi^{q+1} W = 80
+    "transfer": 6 * 4,                          # phi^q, phi^{q+1}, U, T R; U, T W = 24
+    "scalar_U": 8 * 4 * 2 + 4 + 4 + 4 + 8,      # pops, U R+W, phi R, u R = 84
+    "scalar_T": 8 * 4 * 2 + 4 + 4 + 4 + 8,      # = 84
+    "flow": 8 * 4 * 2 + 4 + 12 + 12,            # pops, phi R, (rho, ux, uy) R + W = 92
+}
+
+
+def workload():
+    return W.thermosolutal_convection(n=N_LATTICE, R=8.0)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(target_s: float = 12.0, max_steps: int = 400):
+    """The FP64 oracle on the host cores, on a bounded sample of the workload:
+    the full 512^2 lattice advanced for as many base steps as fit in ~target_s."""
+    import oracle
+    wl = workload()
+    o = oracle.Oracle(wl.params, wl.fields)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps and (time.perf_counter() - t0) < target_s:
+        o.advance(STEP_BASE)
+        steps += STEP_BASE
+    dt = time.perf_counter() - t0
+    o.close()
+    nodes = wl.params.nx * wl.params.ny
+    return {"value": nodes * steps / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d^2 thermosolutal+flow lattice, first %d base steps, FP64 oracle (%.1f s)" % (
+                N_LATTICE, steps, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    wl = workload()
+    o = oracle.Oracle(wl.params, wl.fields)
+    for _ in range(args.warmup):
+        o.advance(STEP_BASE)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.advance(STEP_BASE)
+    dt = time.perf_counter() - t0
+    nodes = wl.params.nx * wl.params.ny
+    v = nodes * STEP_BASE * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": "thermosolutal free dendrite + forced convection, 512x512, N=(1,1,2,2)",
+                       "base_steps_per_step": STEP_BASE},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "%d steps of %d base steps on the full %d^2 lattice" % (
+                                 args.steps, STEP_BASE, N_LATTICE)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_2609_25670_b300 as lbm
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = workload()
+    p = wl.params
+    nodes = p.nx * p.ny
+    sim = lbm.Simulation(p, precision="f32")
+    sim.init_fields(wl.fields)
+    stream = sim.stream
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    # warm-up (captures the period graph)
+    for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
+        sim.advance(STEP_BASE)
+    kinds = ["phase", "transfer", "scalar_U", "scalar_T", "flow"]
+    sim.timing_enable(kinds)
+    sim.advance(STEP_BASE)           # recapture with timing nodes, untimed
+    sim.timing_read(reset=True)
+    launches0 = sim.launch_counts()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+        sim.advance(STEP_BASE)
+        with torch.cuda.stream(stream):
+            ev[k][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    ktimes = sim.timing_read(reset=True)
+    launches1 = sim.launch_counts()
+    gpu_launches = int(sum(launches1[k] - launches0[k] for k in launches1))
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    value = nodes * STEP_BASE * args.steps * world / (ms_max * 1e-3) / 1e6
+
+    # roofline of the dominant kernel (largest share of the timed kernel time)
+    dom = max(kinds, key=lambda k: ktimes[k][0])
+    dom_ms, dom_n = ktimes[dom]
+    avg_s = dom_ms * 1e-3 / max(dom_n, 1)
+    peak, peak_kind = measured_peaks()
+    achieved = ALGO_BYTES[dom] * nodes / avg_s / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get(dom)
+
+    # end to end through the public API with pinned host buffers
+    host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in wl.fields.items()}
+    host_np = {k: v.numpy() for k, v in host.items()}
+    out_phi = torch.empty((p.ny, p.nx), dtype=torch.float64).pin_memory().numpy()
+    e2e_steps = max(3, min(args.steps, 50))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.init_fields(host_np)
+        sim.advance(STEP_BASE)
+        sim.field("phi", out=out_phi)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = nodes * STEP_BASE * e2e_steps * world / e2e_s / 1e6
+    h2d = 6 * 8 * nodes
+    d2h = 8 * nodes
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": "thermosolutal free dendrite + forced convection, 512x512, phi/U/T/flow on D2Q9, "
+                                   "N=(1,1,2,2), FP32", "base_steps_per_step": STEP_BASE,
+                       "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "algo_bytes_per_node": ALGO_BYTES[dom], "avg_launch_us": avg_s * 1e6,
+                         "launches_timed": dom_n},
+            "kernel_ms": {k: ktimes[k][0] for k in kinds},
+            "gpu_launches": gpu_launches,
+            "wall_s_timed_region": wall,
+            "clocks": clk,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps, "calls": "init_fields(host f64 x6) + advance(2) + field(phi -> host)"},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,228 @@
+/*
+ * lbm.h -- C ABI of the B300 multirate MRT lattice Boltzmann library for
+ * thermosolutal dendritic solidification (Liu, Wu, Zhan: "A unified multirate
+ * lattice Boltzmann framework for thermosolutal dendritic solidification").
+ *
+ * The library advances, on one CUDA device, the four coupled D2Q9 distribution
+ * sets of the paper -- phase phi, supersaturation U, temperature T and flow F
+ * (Sec. 3.1, Eq. 15) -- each at its own update factor N_chi (Eq. 34), with the
+ * phase-step transfer of solute rejection and latent heat (Eqs. 36-39).
+ *
+ * Conventions for every entry point:
+ *   - All functions return an lbm_status; none aborts, traps or exits.  After
+ *     an error, lbm_last_error(h) returns a one-line description.
+ *   - Fields are row-major ny x nx (x fastest), node (x, y) at y*nx + x, in
+ *     lattice units (dx = 1).
+ *   - The caller owns every pointer it passes (params, seeds, field buffers);
+ *     the library copies what it keeps.  The library owns the device state it
+ *     allocates (through the lbm_allocator if given, else cudaMalloc).
+ *   - Work is queued on the CUDA stream given to lbm_create; calls that return
+ *     data to the host (lbm_fields with host dst, lbm_diagnostics) synchronise
+ *     that stream.  One handle must not be used from two threads at once.
+ *   - Status codes are sticky for LBM_E_NONFINITE: once a diagnostics call has
+ *     seen a non-finite value (the failure mode of the paper's accumulated
+ *     coupling, Sec. 4.4), lbm_advance refuses with LBM_E_STATE until the
+ *     simulation is initialised again.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_PARAMS_VERSION 1u
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_E_INVALID_ARG = 1,     /* null pointer, bad size, bad enum value          */
+    LBM_E_UNSTABLE_PARAMS = 2, /* a relaxation time <= 1/2 (Eqs. 24, 32) etc.     */
+    LBM_E_OOM = 3,             /* device allocation failed                         */
+    LBM_E_CUDA = 4,            /* a CUDA runtime call failed                       */
+    LBM_E_NONFINITE = 5,       /* a macroscopic field holds NaN or Inf             */
+    LBM_E_TIMEOUT = 6,         /* a bounded device wait ran out                    */
+    LBM_E_STATE = 7            /* call out of order (not initialised, sticky error)*/
+} lbm_status;
+
+/* boundary kinds (Sec. 4: zero-flux walls for phi, U, T; periodic or
+ * inlet/outflow for the flow) */
+enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_INLET_OUTFLOW = 2 };
+
+/* lbm_params.fields: phi is always present */
+enum {
+    LBM_FIELD_U = 1u,        /* solute, Eq. 6                                      */
+    LBM_FIELD_T = 2u,        /* temperature, Eq. 10                                */
+    LBM_FIELD_FROZEN_T = 4u, /* prescribed theta(y,t) = theta_c + G (y - y0 - V t) */
+    LBM_FIELD_FLOW = 8u      /* D2Q9 flow, Eqs. 13, 27-33                          */
+};
+
+/* lbm_params.precision: storage of the distributions / arithmetic */
+enum {
+    LBM_PREC_F64 = 0,      /* FP64 storage and arithmetic                          */
+    LBM_PREC_F32 = 1,      /* FP32 storage and arithmetic                          */
+    LBM_PREC_F16_DEV = 2,  /* FP16 storage of f_i - w_i * (node's zeroth moment), FP32 arithmetic */
+    LBM_PREC_BF16_DEV = 3  /* BF16 storage of the same deviations, FP32 arithmetic */
+};
+
+/* lbm_params.coupling (Sec. 4.4 source-coupling ablation) */
+enum { LBM_COUPLING_INSTANTANEOUS = 0, LBM_COUPLING_ACCUMULATED = 1 };
+
+/* Inputs of one simulation.  Symbols follow the paper:
+ *   Eq. 34:   dt_chi = N_chi dt_base
+ *   Eqs. 1-4: W0, tau0, eps (eps_s), lam (lambda)
+ *   Eqs. 5-9: Mc, k (k_c), DL, DS
+ *   Eqs. 10-12: kappaS, kappaL, rhoCpS, rhoCpL (volumetric heat capacities),
+ *             rhoL_Lh (rho_L L_h); theta = (T - T_shift)/T_scale (Eq. 5)
+ *   Eqs. 27-33: nu, u_in (inlet velocity), Fbx, Fby (body force), s_e, s_eps, s_q
+ *   frozen temperature: theta = theta_c + frozen_G (y - frozen_y0 - frozen_V t);
+ *             with neither T nor FROZEN_T, theta = theta_c.
+ *   tip_cx, tip_cy: node through which lbm_diagnostics measures the tips. */
+typedef struct {
+    uint32_t struct_version; /* = LBM_PARAMS_VERSION */
+    int32_t nx, ny;          /* lattice size, >= 4 each */
+    uint32_t fields;         /* LBM_FIELD_* bits */
+    int32_t bc_scalar_x, bc_scalar_y; /* PERIODIC or WALL, for phi, U, T */
+    int32_t bc_flow_x, bc_flow_y;     /* PERIODIC, WALL or (x only) INLET_OUTFLOW */
+    uint32_t precision;      /* LBM_PREC_* */
+    uint32_t coupling;       /* LBM_COUPLING_* */
+    int32_t N_phi, N_U, N_T, N_F; /* update factors, >= 1 */
+    int32_t tip_cx, tip_cy;
+    double dt_base;
+    double W0, tau0, eps, lam;
+    double Mc, k, DL, DS;
+    double kappaS, kappaL, rhoCpS, rhoCpL, rhoL_Lh, T_shift, T_scale;
+    double nu, u_in, Fbx, Fby, s_e, s_eps, s_q;
+    double theta_c, frozen_G, frozen_y0, frozen_V;
+} lbm_params;
+
+/* Initial-condition primitives for lbm_init_seed. phi is the maximum over all
+ * seeds of their profiles:
+ *   CIRCLE:   tanh[(r - |x - (x, y)|)/(sqrt 2 W0)]                 (Sec. 4.1)
+ *   PLANAR:   tanh[(y - y_node)/(sqrt 2 W0)] plus noise amp*(2u - 1) on nodes
+ *             with |phi| < 0.99, clipped to [-1, 1]; u is the draw of node
+ *             n = y*nx + x from SplitMix64 seeded with rng_seed
+ *   SINUSOID: tanh[(y + amp sin(2 pi waves x / nx) - y_node)/(sqrt 2 W0)] (Eq. 41) */
+enum { LBM_SEED_CIRCLE = 0, LBM_SEED_PLANAR = 1, LBM_SEED_SINUSOID = 2 };
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    double x, y, r, amp, waves;
+} lbm_seed;
+
+/* Diagnostics of one simulation (Sec. 4.1 tip histories, Sec. 4.4 ablation).
+ *   M_C     = sum over nodes of C/C_inf = (1 + (1-k) U)((1+k) - (1-k) phi)/2 (Eq. 5), FP64 sum
+ *   H_total = sum of (rho Cp)_eff(phi) T - rho_L L_h phi / 2, FP64 sum
+ *   S_phi   = max |Delta U_pc| over nodes and phase steps since the previous call
+ *   J_U     = max |U_post - U_pre| over the phase-change applications since the
+ *             previous call (equals S_phi under instantaneous coupling)
+ *   tip[d]  = distance from (tip_cx, tip_cy) of the outermost phi = 0 crossing
+ *             along +x, +y, -x, -y (linear interpolation)
+ *   nonfinite = 1 if any phi, U, T, ux, uy is NaN or Inf */
+typedef struct {
+    int64_t base_step;
+    double M_C, H_total, S_phi, J_U;
+    double tip[4];
+    int32_t nonfinite;
+    int32_t reserved;
+} lbm_diag;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc
+ * returns device memory of at least `bytes` usable on `stream`, or NULL;
+ * free releases it.  Both may be called from lbm_create / lbm_destroy only. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+    void* ctx;
+} lbm_allocator;
+
+typedef struct lbm_sim* lbm_handle;
+
+/* Create n_sims independent simulations on the current CUDA device.
+ * p: parameters of every simulation when per_sim is NULL; otherwise per_sim
+ * holds n_sims parameter sets and p only selects precision (all members must
+ * share it).  a: NULL for cudaMalloc.  cuda_stream: a cudaStream_t (NULL =
+ * legacy default stream).  Validates every field (versions, sizes >= 4,
+ * N_chi >= 1, tau_chi > 1/2 in both phases, nonzero denominators).
+ * Errors: INVALID_ARG, UNSTABLE_PARAMS, OOM, CUDA.  On error *out = NULL. */
+lbm_status lbm_create(const lbm_params* p, int32_t n_sims, const lbm_params* per_sim,
+                      const lbm_allocator* a, void* cuda_stream, lbm_handle* out);
+
+/* Initialise simulation `sim` from seed primitives (host FP64 generation):
+ * phi from the seeds, U = U0, T = T0, rho = 1, u = u_in (1 - phi)/2 along x
+ * when the flow is on; then every distribution is set to the equilibrium of
+ * these fields (for phi with v_n from the initial gradient, Eqs. 19, 21, 28).
+ * Resets the base-step clock and the sticky error.  Synchronises the stream. */
+lbm_status lbm_init_seed(lbm_handle h, int32_t sim, const lbm_seed* seeds, int32_t n_seeds,
+                         double U0, double T0, uint64_t rng_seed);
+
+/* Initialise simulation `sim` from caller fields, each ny x nx FP64: phi, U,
+ * T, ux, uy, rho (U / T / ux, uy, rho are ignored when that field is off, and
+ * may then be NULL).  src_is_device: 1 if the pointers are device memory.
+ * Then as lbm_init_seed.  Synchronises the stream. */
+lbm_status lbm_init_fields(lbm_handle h, int32_t sim, const double* phi, const double* U,
+                           const double* T, const double* ux, const double* uy,
+                           const double* rho, int32_t src_is_device);
+
+/* Advance every simulation by n_base_steps ticks of the global clock (Eq. 34;
+ * field chi updates at base step n iff (n+1) mod N_chi == 0, in the order
+ * phase -> transfer -> U -> T -> flow of Fig. 1).  Asynchronous: returns once
+ * the work is queued (as captured CUDA graphs of one schedule period when
+ * graphs are enabled).  Errors: STATE (not initialised / sticky), CUDA. */
+lbm_status lbm_advance(lbm_handle h, int64_t n_base_steps);
+
+/* Copy a macroscopic field of simulation `sim` into dst (ny x nx).
+ * which: 0 phi, 1 U, 2 T, 3 ux, 4 uy, 5 rho, 6 C/C_inf, 7 theta.
+ * as_f64 = 1: dst holds doubles; 0: dst holds the arithmetic type (double for
+ * F64, float otherwise).  dst_is_device: 1 for a device pointer (copy queued
+ * on the stream), 0 for host memory (synchronises).  Fields that are off read
+ * as zeros (U, T), theta_c-based theta, or rest (ux, uy = 0, rho = 1). */
+lbm_status lbm_fields(lbm_handle h, int32_t sim, uint32_t which, void* dst, int32_t dst_is_device,
+                      int32_t as_f64);
+
+/* Reduce the diagnostics of simulation `sim` on the device (FP64 sums,
+ * deterministic order) and return them; resets the S_phi / J_U maxima.
+ * Synchronises the stream.  Returns NONFINITE (and sets the sticky state)
+ * when a non-finite value is present; *out is filled in either case. */
+lbm_status lbm_diagnostics(lbm_handle h, int32_t sim, lbm_diag* out);
+
+/* One-line description of the last error on h (or of the last failed
+ * lbm_create when h is NULL).  Owned by the library; valid until the next call. */
+const char* lbm_last_error(lbm_handle h);
+
+/* Free every device buffer and graph of h.  NULL is a no-op. */
+void lbm_destroy(lbm_handle h);
+
+/* ---- runtime controls and measurement hooks (no counterpart in the paper) ---- */
+
+/* enable = 1 (default): lbm_advance replays CUDA graphs captured per schedule
+ * period; 0: plain stream launches.  Results are identical. */
+lbm_status lbm_set_graphs(lbm_handle h, int32_t enable);
+
+/* Kernel kinds for timing and launch counts. */
+enum { LBM_K_PHASE = 0, LBM_K_TRANSFER = 1, LBM_K_SCALAR_U = 2, LBM_K_SCALAR_T = 3,
+       LBM_K_FLOW = 4, LBM_K_DIAG = 5, LBM_K_INIT = 6, LBM_K_COUNT = 7 };
+
+/* Time every launch of the kernel kinds in kind_mask (bit k = kind k) with
+ * CUDA events on the library's stream, inside graphs as event-record nodes;
+ * lbm_advance then synchronises after each replay to collect the times.
+ * kind_mask = 0 turns timing off.  Recaptures graphs. */
+lbm_status lbm_timing_enable(lbm_handle h, uint32_t kind_mask);
+
+/* Per kind: accumulated milliseconds and number of timed launches since the
+ * last reset; reset = 1 clears them. ms and count hold LBM_K_COUNT entries. */
+lbm_status lbm_timing_read(lbm_handle h, double* ms, int64_t* count, int32_t reset);
+
+/* Number of kernel launches the library has issued (graph replays count
+ * their kernel nodes), per kind; counts hold LBM_K_COUNT entries. */
+lbm_status lbm_launch_counts(lbm_handle h, int64_t* counts);
+
+/* Bytes of device memory held by h. */
+lbm_status lbm_device_bytes(lbm_handle h, size_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

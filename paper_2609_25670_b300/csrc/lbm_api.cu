@@ -1,0 +1,804 @@
+// Host runtime of the B300 multirate MRT-LBM: the C ABI of include/lbm.h,
+// device-state ownership, the multirate schedule (Eq. 34, workflow of
+// Fig. 1), CUDA-graph capture of one schedule period, kernel timing hooks.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_kernels.cuh"
+
+using namespace lbmk;
+
+namespace {
+
+constexpr int TX = 32;
+constexpr int TY = 8;   // tile height of the update kernels (256 threads)
+constexpr int kMaxGraphPeriod = 4096;
+
+thread_local std::string g_create_error;
+
+enum { FP = 0, FU = 1, FT = 2, FF = 3 };
+
+struct SimState {
+    lbm_params p{};
+    int nx = 0, ny = 0, pitch = 0;
+    size_t nn = 0;        // pitch * ny
+    void* pops[4][2] = {};
+    int cur_pop[4] = {0, 0, 0, 0};
+    void* phi[2] = {};
+    int cur_phi = 0;
+    void* U[2] = {};
+    int cur_U = 0;
+    void* T[2] = {};
+    int cur_T = 0;
+    void* ux[2] = {};
+    void* uy[2] = {};
+    void* rho[2] = {};
+    void* accU = nullptr;
+    void* accT = nullptr;
+    bool acc_reset_U = true, acc_reset_T = true;
+    unsigned long long* smax = nullptr;  // [S_phi, J_U] as double bits
+    long long* clock = nullptr;          // base step at the start of a graph replay
+    double* part = nullptr;              // diagnostics partial sums
+    double* dout = nullptr;              // diagnostics results (9 doubles)
+    int diag_blocks = 0;
+    int64_t step = 0;
+    bool initialized = false;
+    bool sticky = false;
+    bool has_U = false, has_T = false, frozen_T = false, has_flow = false, accumulated = false;
+    int period = 1;                      // 2 * lcm of the update factors
+    cudaGraphExec_t graph = nullptr;
+    int graph_kernels[LBM_K_COUNT] = {};
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> graph_events;
+};
+
+struct TimedEvent {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct lbm_sim {
+    std::vector<SimState> sims;
+    uint32_t precision = LBM_PREC_F32;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    lbm_allocator alloc{};
+    bool has_alloc = false;
+    std::vector<std::pair<void*, size_t>> blocks;
+    size_t bytes = 0;
+    bool graphs = true;
+    uint32_t timing_mask = 0;
+    double timing_ms[LBM_K_COUNT] = {};
+    int64_t timing_n[LBM_K_COUNT] = {};
+    int64_t launches[LBM_K_COUNT] = {};
+    std::vector<TimedEvent> pending;     // eager-mode timed launches
+    std::vector<cudaEvent_t> event_pool;
+    bool capturing = false;
+    SimState* cap_sim = nullptr;         // sim whose graph is being captured
+    double* staging = nullptr;           // FP64 upload / download staging (lazy)
+    size_t staging_bytes = 0;
+    std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm_sim* h, lbm_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_create_error = buf;
+    return s;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) return fail(h, LBM_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+lbm_status dev_alloc(lbm_sim* h, size_t bytes, void** out) {
+    *out = nullptr;
+    if (bytes == 0) return LBM_OK;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (h->has_alloc) {
+        p = h->alloc.alloc(bytes, (void*)h->stream, h->alloc.ctx);
+        if (!p) return fail(h, LBM_E_OOM, "allocator callback returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, LBM_E_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    h->blocks.push_back({p, bytes});
+    h->bytes += bytes;
+    *out = p;
+    return LBM_OK;
+}
+
+void free_all(lbm_sim* h) {
+    for (auto& b : h->blocks) {
+        if (h->has_alloc) h->alloc.free(b.first, b.second, (void*)h->stream, h->alloc.ctx);
+        else cudaFree(b.first);
+    }
+    h->blocks.clear();
+    h->bytes = 0;
+}
+
+size_t real_size(uint32_t prec) { return prec == LBM_PREC_F64 ? 8 : 4; }
+size_t store_size(uint32_t prec) { return prec == LBM_PREC_F64 ? 8 : prec == LBM_PREC_F32 ? 4 : 2; }
+
+int64_t gcd64(int64_t a, int64_t b) { return b == 0 ? a : gcd64(b, a % b); }
+int64_t lcm64(int64_t a, int64_t b) { return a / gcd64(a, b) * b; }
+
+lbm_status validate(const lbm_params* p, std::string& why) {
+    char buf[256];
+    auto bad = [&](const char* m) { why = m; return LBM_E_INVALID_ARG; };
+    if (p->struct_version != LBM_PARAMS_VERSION) return bad("struct_version != LBM_PARAMS_VERSION");
+    if (p->nx < 4 || p->ny < 4) return bad("nx and ny must be >= 4");
+    if ((int64_t)p->nx * p->ny > (int64_t)1 << 31) return bad("nx * ny must be < 2^31");
+    if (p->fields & ~(uint32_t)(LBM_FIELD_U | LBM_FIELD_T | LBM_FIELD_FROZEN_T | LBM_FIELD_FLOW)) return bad("unknown fields bit");
+    if ((p->fields & LBM_FIELD_T) && (p->fields & LBM_FIELD_FROZEN_T)) return bad("T and FROZEN_T are exclusive");
+    if (p->bc_scalar_x < 0 || p->bc_scalar_x > 1 || p->bc_scalar_y < 0 || p->bc_scalar_y > 1)
+        return bad("scalar boundaries must be PERIODIC or WALL");
+    if (p->bc_flow_x < 0 || p->bc_flow_x > 2 || p->bc_flow_y < 0 || p->bc_flow_y > 1)
+        return bad("flow boundary x must be PERIODIC, WALL or INLET_OUTFLOW; y PERIODIC or WALL");
+    if (p->bc_flow_x == LBM_BC_INLET_OUTFLOW && (p->nx % TX) == 1)
+        return bad("INLET_OUTFLOW needs nx % 32 != 1");
+    if (p->precision > LBM_PREC_BF16_DEV) return bad("unknown precision");
+    if (p->coupling > LBM_COUPLING_ACCUMULATED) return bad("unknown coupling");
+    if (p->N_phi < 1 || p->N_U < 1 || p->N_T < 1 || p->N_F < 1) return bad("update factors must be >= 1");
+    if (!(p->dt_base > 0.0)) return bad("dt_base must be > 0");
+    if (!(p->W0 > 0.0) || !(p->tau0 > 0.0)) return bad("W0 and tau0 must be > 0");
+    if (p->tip_cx < 0 || p->tip_cx >= p->nx || p->tip_cy < 0 || p->tip_cy >= p->ny) return bad("tip centre outside the lattice");
+    const double dtp = p->N_phi * p->dt_base;
+    const double amin = 1.0 - 3.0 * std::fabs(p->eps);
+    if (!(amin > 0.0)) return bad("1 - 3 eps must be > 0 (a_s > 0)");
+    if (3.0 * dtp * amin * amin * p->W0 * p->W0 / p->tau0 <= 0.0) return bad("tau_phi <= 1/2");
+    if (p->fields & LBM_FIELD_U) {
+        if (!(p->k > 0.0 && p->k <= 1.0)) return bad("k must be in (0, 1]");
+        double dS = p->DS / p->k, dL = p->DL;          // D_eff at phi = +1, -1 (Eq. 7)
+        if (!(3.0 * p->N_U * p->dt_base * std::min(dS, dL) > 0.0)) {
+            snprintf(buf, sizeof buf, "tau_U <= 1/2 (D_S/k = %g, D_L = %g)", dS, dL);
+            why = buf;
+            return LBM_E_UNSTABLE_PARAMS;
+        }
+    }
+    if (p->fields & LBM_FIELD_T) {
+        if (!(p->rhoCpS > 0.0 && p->rhoCpL > 0.0)) return bad("heat capacities must be > 0");
+        if (!(p->T_scale != 0.0)) return bad("T_scale must be nonzero");
+        double aS = p->kappaS / p->rhoCpS, aL = p->kappaL / p->rhoCpL;
+        if (!(std::min(aS, aL) > 0.0)) { why = "tau_T <= 1/2 (alpha <= 0)"; return LBM_E_UNSTABLE_PARAMS; }
+    }
+    if (p->fields & LBM_FIELD_FLOW) {
+        if (!(p->nu > 0.0)) { why = "tau_F <= 1/2 (nu <= 0)"; return LBM_E_UNSTABLE_PARAMS; }
+    }
+    return LBM_OK;
+}
+
+template <typename R> KP<R> make_kp(const SimState& s) {
+    const lbm_params& p = s.p;
+    KP<R> k{};
+    k.nx = s.nx; k.ny = s.ny; k.pitch = s.pitch; k.plane = (long long)s.nn;
+    k.bsx = p.bc_scalar_x; k.bsy = p.bc_scalar_y; k.bfx = p.bc_flow_x; k.bfy = p.bc_flow_y;
+    k.has_U = s.has_U; k.has_T = s.has_T; k.frozen_T = s.frozen_T; k.has_flow = s.has_flow;
+    k.accumulated = s.accumulated;
+    const double dtp = p.N_phi * p.dt_base, dtU = p.N_U * p.dt_base, dtT = p.N_T * p.dt_base, dtF = p.N_F * p.dt_base;
+    k.dtp = (R)dtp; k.W0sq_tau0 = (R)(p.W0 * p.W0 / p.tau0); k.inv_tau0 = (R)(1.0 / p.tau0);
+    k.eps = (R)p.eps; k.lam = (R)p.lam; k.Mc = (R)p.Mc;
+    k.k = (R)p.k; k.at_pre = (R)(p.W0 / (2.0 * std::sqrt(2.0))); k.rhoL_Lh = (R)p.rhoL_Lh;
+    k.dtU = (R)dtU; k.DS = (R)p.DS; k.DL = (R)p.DL;
+    k.dtT = (R)dtT; k.kS = (R)p.kappaS; k.kL = (R)p.kappaL; k.cS = (R)p.rhoCpS; k.cL = (R)p.rhoCpL;
+    k.T_shift = (R)p.T_shift; k.inv_T_scale = (R)(1.0 / p.T_scale);
+    k.dtF = (R)dtF; k.cF = (R)(1.0 / dtF); k.Fbx = (R)p.Fbx; k.Fby = (R)p.Fby;
+    k.se = (R)p.s_e; k.seps = (R)p.s_eps; k.sq = (R)p.s_q; k.snu = (R)(1.0 / (3.0 * dtF * p.nu + 0.5));
+    k.u_in = (R)p.u_in;
+    k.theta_c = (R)p.theta_c; k.fG = (R)p.frozen_G; k.fy0 = (R)p.frozen_y0; k.fV = (R)p.frozen_V;
+    k.dt_base = (R)p.dt_base;
+    return k;
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers (timing + launch counts)
+// ---------------------------------------------------------------------------
+cudaEvent_t pool_get(lbm_sim* h) {
+    if (!h->event_pool.empty()) {
+        cudaEvent_t e = h->event_pool.back();
+        h->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct LaunchScope {
+    lbm_sim* h;
+    int kind;
+    cudaEvent_t a = nullptr, b = nullptr;
+    LaunchScope(lbm_sim* h_, int kind_) : h(h_), kind(kind_) {
+        if (h->timing_mask & (1u << kind)) {
+            if (h->capturing) {
+                cudaEventCreate(&a);
+                cudaEventCreate(&b);
+                cudaEventRecordWithFlags(a, h->stream, cudaEventRecordExternal);
+            } else {
+                a = pool_get(h);
+                b = pool_get(h);
+                cudaEventRecord(a, h->stream);
+            }
+        }
+    }
+    ~LaunchScope() {
+        if (h->capturing) h->cap_sim->graph_kernels[kind]++;
+        else h->launches[kind]++;
+        if (a) {
+            if (h->capturing) {
+                cudaEventRecordWithFlags(b, h->stream, cudaEventRecordExternal);
+                h->cap_sim->graph_events.push_back({kind, {a, b}});
+            } else {
+                cudaEventRecord(b, h->stream);
+                h->pending.push_back({kind, a, b});
+            }
+        }
+    }
+};
+
+lbm_status collect_pending(lbm_sim* h) {
+    if (h->pending.empty()) return LBM_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    for (auto& t : h->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            h->timing_ms[t.kind] += ms;
+            h->timing_n[t.kind]++;
+        }
+        h->event_pool.push_back(t.a);
+        h->event_pool.push_back(t.b);
+    }
+    h->pending.clear();
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the update sequence of one base step (Fig. 1), precision-templated
+// ---------------------------------------------------------------------------
+template <typename R, typename ST, bool DEV>
+void enqueue_step(lbm_sim* h, SimState& s, int64_t n, const long long* clock, long long off) {
+    const lbm_params& p = s.p;
+    const KP<R> P = make_kp<R>(s);
+    const dim3 blk(TX, TY), grd((s.nx + TX - 1) / TX, (s.ny + TY - 1) / TY);
+    cudaStream_t st = h->stream;
+    R* phi_c = (R*)s.phi[s.cur_phi];
+    R* phi_n = (R*)s.phi[1 - s.cur_phi];
+    if ((n + 1) % p.N_phi == 0) {
+        {
+            LaunchScope ls(h, LBM_K_PHASE);
+            k_phase<R, ST, DEV, TY><<<grd, blk, 0, st>>>(
+                P, (const ST*)s.pops[FP][s.cur_pop[FP]], (ST*)s.pops[FP][1 - s.cur_pop[FP]], phi_c, phi_n,
+                s.has_U ? (const R*)s.U[s.cur_U] : nullptr, s.has_T ? (const R*)s.T[s.cur_T] : nullptr, clock, off);
+        }
+        s.cur_pop[FP] ^= 1;
+        {
+            LaunchScope ls(h, LBM_K_TRANSFER);
+            k_transfer<R, TY><<<grd, blk, 0, st>>>(
+                P, phi_c, phi_n, s.has_U ? (const R*)s.U[s.cur_U] : nullptr, s.has_U ? (R*)s.U[1 - s.cur_U] : nullptr,
+                s.has_T ? (const R*)s.T[s.cur_T] : nullptr, s.has_T ? (R*)s.T[1 - s.cur_T] : nullptr, (R*)s.accU,
+                (R*)s.accT, s.acc_reset_U ? 1 : 0, s.acc_reset_T ? 1 : 0, s.smax);
+        }
+        s.cur_phi ^= 1;
+        if (!s.accumulated) {
+            if (s.has_U) s.cur_U ^= 1;
+            if (s.has_T) s.cur_T ^= 1;
+        } else {
+            s.acc_reset_U = false;
+            s.acc_reset_T = false;
+        }
+    }
+    const R* phi_now = (const R*)s.phi[s.cur_phi];
+    const R* uxc = s.has_flow ? (const R*)s.ux[s.cur_pop[FF]] : nullptr;
+    const R* uyc = s.has_flow ? (const R*)s.uy[s.cur_pop[FF]] : nullptr;
+    if (s.has_U && (n + 1) % p.N_U == 0) {
+        {
+            LaunchScope ls(h, LBM_K_SCALAR_U);
+            k_scalar<R, ST, DEV, TY, 0><<<grd, blk, 0, st>>>(
+                P, (const ST*)s.pops[FU][s.cur_pop[FU]], (ST*)s.pops[FU][1 - s.cur_pop[FU]], (const R*)s.U[s.cur_U],
+                (R*)s.U[1 - s.cur_U], (const R*)s.accU, phi_now, uxc, uyc, s.smax);
+        }
+        s.cur_pop[FU] ^= 1;
+        s.cur_U ^= 1;
+        s.acc_reset_U = true;
+    }
+    if (s.has_T && (n + 1) % p.N_T == 0) {
+        {
+            LaunchScope ls(h, LBM_K_SCALAR_T);
+            k_scalar<R, ST, DEV, TY, 1><<<grd, blk, 0, st>>>(
+                P, (const ST*)s.pops[FT][s.cur_pop[FT]], (ST*)s.pops[FT][1 - s.cur_pop[FT]], (const R*)s.T[s.cur_T],
+                (R*)s.T[1 - s.cur_T], (const R*)s.accT, phi_now, uxc, uyc, s.smax);
+        }
+        s.cur_pop[FT] ^= 1;
+        s.cur_T ^= 1;
+        s.acc_reset_T = true;
+    }
+    if (s.has_flow && (n + 1) % p.N_F == 0) {
+        const int c = s.cur_pop[FF];
+        {
+            LaunchScope ls(h, LBM_K_FLOW);
+            k_flow<R, ST, DEV, TY><<<grd, blk, 0, st>>>(P, (const ST*)s.pops[FF][c], (ST*)s.pops[FF][1 - c], phi_now,
+                                                     (const R*)s.ux[c], (const R*)s.uy[c], (const R*)s.rho[c],
+                                                     (R*)s.ux[1 - c], (R*)s.uy[1 - c], (R*)s.rho[1 - c]);
+        }
+        s.cur_pop[FF] ^= 1;
+    }
+}
+
+void enqueue_base_step(lbm_sim* h, SimState& s, int64_t n, const long long* clock, long long off) {
+    switch (h->precision) {
+        case LBM_PREC_F64: enqueue_step<double, double, false>(h, s, n, clock, off); break;
+        case LBM_PREC_F32: enqueue_step<float, float, false>(h, s, n, clock, off); break;
+        case LBM_PREC_F16_DEV: enqueue_step<float, __half, true>(h, s, n, clock, off); break;
+        default: enqueue_step<float, __nv_bfloat16, true>(h, s, n, clock, off); break;
+    }
+}
+
+void drop_graph(SimState& s) {
+    if (s.graph) cudaGraphExecDestroy(s.graph);
+    s.graph = nullptr;
+    for (auto& e : s.graph_events) {
+        cudaEventDestroy(e.second.first);
+        cudaEventDestroy(e.second.second);
+    }
+    s.graph_events.clear();
+    std::fill(std::begin(s.graph_kernels), std::end(s.graph_kernels), 0);
+}
+
+// Capture one schedule period (s.step must be a multiple of s.period, where
+// every ping-pong parity equals its value after initialisation).
+lbm_status capture_graph(lbm_sim* h, SimState& s) {
+    drop_graph(s);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    h->cap_sim = &s;
+    for (int k = 0; k < s.period; ++k) enqueue_base_step(h, s, s.step + k, s.frozen_T ? s.clock : nullptr, k);
+    if (s.frozen_T) k_tick<<<1, 1, 0, h->stream>>>(s.clock, s.period);
+    h->capturing = false;
+    h->cap_sim = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess) return fail(h, LBM_E_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&s.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { s.graph = nullptr; return fail(h, LBM_E_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e)); }
+    return LBM_OK;
+}
+
+lbm_status graph_replay(lbm_sim* h, SimState& s) {
+    CK(cudaGraphLaunch(s.graph, h->stream));
+    for (int k = 0; k < LBM_K_COUNT; ++k) h->launches[k] += s.graph_kernels[k];
+    s.step += s.period;
+    if (!s.graph_events.empty()) {
+        CK(cudaStreamSynchronize(h->stream));
+        for (auto& ev : s.graph_events) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev.second.first, ev.second.second) == cudaSuccess) {
+                h->timing_ms[ev.first] += ms;
+                h->timing_n[ev.first]++;
+            }
+        }
+    }
+    return LBM_OK;
+}
+
+template <typename R>
+lbm_status upload_and_init(lbm_sim* h, SimState& s, const double* src[6], int src_dev) {
+    const size_t n = (size_t)s.nx * s.ny;
+    const size_t need = n * sizeof(double);
+    if (h->staging_bytes < need) {
+        void* p = nullptr;
+        lbm_status st = dev_alloc(h, need, &p);
+        if (st) return st;
+        h->staging = (double*)p;
+        h->staging_bytes = need;
+    }
+    const dim3 blk(32, 8), grd((s.nx + 31) / 32, (s.ny + 7) / 8);
+    void* dst[6] = {s.phi[0], s.U[0], s.T[0], s.ux[0], s.uy[0], s.rho[0]};
+    for (int f = 0; f < 6; ++f) {
+        if (!dst[f] || !src[f]) continue;
+        CK(cudaMemcpyAsync(h->staging, src[f], need, src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+        k_from_f64<R><<<grd, blk, 0, h->stream>>>(h->staging, (R*)dst[f], s.nx, s.ny, s.pitch);
+    }
+    s.cur_phi = s.cur_U = s.cur_T = 0;
+    for (int f = 0; f < 4; ++f) s.cur_pop[f] = 0;
+    const KP<R> P = make_kp<R>(s);
+    {
+        LaunchScope ls(h, LBM_K_INIT);
+        switch (h->precision) {
+            case LBM_PREC_F64:
+            case LBM_PREC_F32:
+                k_init<R, R, false><<<grd, blk, 0, h->stream>>>(P, (const R*)s.phi[0], (const R*)s.U[0], (const R*)s.T[0],
+                                                               (const R*)s.ux[0], (const R*)s.uy[0], (const R*)s.rho[0],
+                                                               (R*)s.pops[FP][0], (R*)s.pops[FU][0], (R*)s.pops[FT][0],
+                                                               (R*)s.pops[FF][0]);
+                break;
+            case LBM_PREC_F16_DEV:
+                k_init<float, __half, true><<<grd, blk, 0, h->stream>>>(
+                    make_kp<float>(s), (const float*)s.phi[0], (const float*)s.U[0], (const float*)s.T[0],
+                    (const float*)s.ux[0], (const float*)s.uy[0], (const float*)s.rho[0], (__half*)s.pops[FP][0],
+                    (__half*)s.pops[FU][0], (__half*)s.pops[FT][0], (__half*)s.pops[FF][0]);
+                break;
+            default:
+                k_init<float, __nv_bfloat16, true><<<grd, blk, 0, h->stream>>>(
+                    make_kp<float>(s), (const float*)s.phi[0], (const float*)s.U[0], (const float*)s.T[0],
+                    (const float*)s.ux[0], (const float*)s.uy[0], (const float*)s.rho[0], (__nv_bfloat16*)s.pops[FP][0],
+                    (__nv_bfloat16*)s.pops[FU][0], (__nv_bfloat16*)s.pops[FT][0], (__nv_bfloat16*)s.pops[FF][0]);
+        }
+    }
+    (void)P;
+    CK(cudaGetLastError());
+    const size_t rs = sizeof(R);
+    if (s.accU) CK(cudaMemsetAsync(s.accU, 0, s.nn * rs, h->stream));
+    if (s.accT) CK(cudaMemsetAsync(s.accT, 0, s.nn * rs, h->stream));
+    CK(cudaMemsetAsync(s.smax, 0, 2 * sizeof(unsigned long long), h->stream));
+    if (s.clock) CK(cudaMemsetAsync(s.clock, 0, sizeof(long long), h->stream));
+    s.acc_reset_U = s.acc_reset_T = true;
+    s.step = 0;
+    s.initialized = true;
+    s.sticky = false;
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status init_common(lbm_sim* h, int32_t sim, const double* src[6], int src_dev) {
+    SimState& s = h->sims[sim];
+    // a captured period graph stays valid: it was captured at a step where every
+    // ping-pong parity has its initial value, which initialisation restores
+    return h->precision == LBM_PREC_F64 ? upload_and_init<double>(h, s, src, src_dev)
+                                        : upload_and_init<float>(h, s, src, src_dev);
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014), counter form: draw k of stream s
+inline uint64_t splitmix64(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <typename R>
+lbm_status read_field(lbm_sim* h, SimState& s, uint32_t which, void* dst, int dst_dev, int as_f64) {
+    const KP<R> P = make_kp<R>(s);
+    const dim3 blk(32, 8), grd((s.nx + 31) / 32, (s.ny + 7) / 8);
+    const size_t n = (size_t)s.nx * s.ny;
+    const size_t esz = as_f64 ? sizeof(double) : sizeof(R);
+    void* out = dst;
+    if (!dst_dev) {
+        if (h->staging_bytes < n * sizeof(double)) {
+            void* p = nullptr;
+            lbm_status st = dev_alloc(h, n * sizeof(double), &p);
+            if (st) return st;
+            h->staging = (double*)p;
+            h->staging_bytes = n * sizeof(double);
+        }
+        out = h->staging;
+    }
+    // clock holds the base step of the last graph replay start; keep it exact here
+    if (s.clock) k_set_clock<<<1, 1, 0, h->stream>>>(s.clock, (long long)s.step);
+    const int fc = s.cur_pop[FF];
+    if (as_f64)
+        k_out<R, double><<<grd, blk, 0, h->stream>>>(P, (int)which, (const R*)s.phi[s.cur_phi],
+                                                     s.has_U ? (const R*)s.U[s.cur_U] : nullptr,
+                                                     s.has_T ? (const R*)s.T[s.cur_T] : nullptr, (const R*)s.ux[fc],
+                                                     (const R*)s.uy[fc], (const R*)s.rho[fc], (const R*)s.accU,
+                                                     (const R*)s.accT, (double*)out, s.clock);
+    else
+        k_out<R, R><<<grd, blk, 0, h->stream>>>(P, (int)which, (const R*)s.phi[s.cur_phi],
+                                                s.has_U ? (const R*)s.U[s.cur_U] : nullptr,
+                                                s.has_T ? (const R*)s.T[s.cur_T] : nullptr, (const R*)s.ux[fc],
+                                                (const R*)s.uy[fc], (const R*)s.rho[fc], (const R*)s.accU,
+                                                (const R*)s.accT, (R*)out, s.clock);
+    CK(cudaGetLastError());
+    if (!dst_dev) {
+        CK(cudaMemcpyAsync(dst, out, n * esz, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return LBM_OK;
+}
+
+template <typename R>
+lbm_status run_diag(lbm_sim* h, SimState& s, lbm_diag* out) {
+    const KP<R> P = make_kp<R>(s);
+    {
+        LaunchScope ls(h, LBM_K_DIAG);
+        const int fc = s.cur_pop[FF];
+        k_diag_partial<R><<<s.diag_blocks, 256, 0, h->stream>>>(
+            P, (const R*)s.phi[s.cur_phi], s.has_U ? (const R*)s.U[s.cur_U] : nullptr,
+            s.has_T ? (const R*)s.T[s.cur_T] : nullptr, (const R*)s.ux[fc], (const R*)s.uy[fc], s.part);
+        k_diag_final<R><<<1, 128, 0, h->stream>>>(P, s.part, s.diag_blocks, (const R*)s.phi[s.cur_phi], s.p.tip_cx,
+                                                 s.p.tip_cy, s.smax, s.dout);
+    }
+    CK(cudaGetLastError());
+    double r[9];
+    CK(cudaMemcpyAsync(r, s.dout, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    out->base_step = s.step;
+    out->M_C = r[0];
+    out->H_total = r[1];
+    out->nonfinite = r[2] > 0.0 ? 1 : 0;
+    for (int d = 0; d < 4; ++d) out->tip[d] = r[3 + d];
+    out->S_phi = r[7];
+    out->J_U = r[8];
+    out->reserved = 0;
+    if (out->nonfinite) {
+        s.sticky = true;
+        return fail(h, LBM_E_NONFINITE, "non-finite value in the macroscopic fields at base step %lld", (long long)s.step);
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+lbm_status lbm_create(const lbm_params* p, int32_t n_sims, const lbm_params* per_sim, const lbm_allocator* a,
+                      void* cuda_stream, lbm_handle* out) {
+    lbm_sim* h = nullptr;
+    if (!out) return fail(nullptr, LBM_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(nullptr, LBM_E_INVALID_ARG, "params is NULL");
+    if (n_sims < 1) return fail(nullptr, LBM_E_INVALID_ARG, "n_sims must be >= 1");
+    if (a && (!a->alloc || !a->free)) return fail(nullptr, LBM_E_INVALID_ARG, "allocator needs alloc and free");
+    std::vector<lbm_params> ps(n_sims);
+    for (int i = 0; i < n_sims; ++i) {
+        ps[i] = per_sim ? per_sim[i] : *p;
+        std::string why;
+        lbm_status st = validate(&ps[i], why);
+        if (st) return fail(nullptr, st, "sim %d: %s", i, why.c_str());
+        if (ps[i].precision != p->precision) return fail(nullptr, LBM_E_INVALID_ARG, "sim %d: precision differs", i);
+    }
+    h = new lbm_sim();
+    h->precision = p->precision;
+    if (a) { h->alloc = *a; h->has_alloc = true; }
+    if (cuda_stream) h->stream = (cudaStream_t)cuda_stream;
+    else {
+        cudaError_t e = cudaStreamCreate(&h->stream);
+        if (e != cudaSuccess) {
+            delete h;
+            return fail(nullptr, LBM_E_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        h->own_stream = true;
+    }
+    h->sims.resize(n_sims);
+    const size_t rs = real_size(h->precision), ss = store_size(h->precision);
+    for (int i = 0; i < n_sims; ++i) {
+        SimState& s = h->sims[i];
+        s.p = ps[i];
+        s.nx = s.p.nx;
+        s.ny = s.p.ny;
+        s.pitch = s.nx;
+        s.nn = (size_t)s.pitch * s.ny;
+        s.has_U = (s.p.fields & LBM_FIELD_U) != 0;
+        s.has_T = (s.p.fields & LBM_FIELD_T) != 0;
+        s.frozen_T = (s.p.fields & LBM_FIELD_FROZEN_T) != 0;
+        s.has_flow = (s.p.fields & LBM_FIELD_FLOW) != 0;
+        s.accumulated = s.p.coupling == LBM_COUPLING_ACCUMULATED;
+        int64_t L = lcm64(lcm64(s.p.N_phi, s.has_U ? s.p.N_U : 1), lcm64(s.has_T ? s.p.N_T : 1, s.has_flow ? s.p.N_F : 1));
+        s.period = (int)std::min<int64_t>(2 * L, (int64_t)1 << 30);
+        const bool present[4] = {true, s.has_U, s.has_T, s.has_flow};
+        lbm_status st = LBM_OK;
+        for (int f = 0; f < 4 && !st; ++f)
+            for (int b = 0; b < 2 && !st; ++b)
+                if (present[f]) st = dev_alloc(h, 8 * s.nn * ss, &s.pops[f][b]);
+        for (int b = 0; b < 2 && !st; ++b) st = dev_alloc(h, s.nn * rs, &s.phi[b]);
+        for (int b = 0; b < 2 && !st; ++b) if (s.has_U) st = dev_alloc(h, s.nn * rs, &s.U[b]);
+        for (int b = 0; b < 2 && !st; ++b) if (s.has_T) st = dev_alloc(h, s.nn * rs, &s.T[b]);
+        for (int b = 0; b < 2 && !st; ++b)
+            if (s.has_flow) {
+                st = dev_alloc(h, s.nn * rs, &s.ux[b]);
+                if (!st) st = dev_alloc(h, s.nn * rs, &s.uy[b]);
+                if (!st) st = dev_alloc(h, s.nn * rs, &s.rho[b]);
+            }
+        if (!st && s.accumulated && s.has_U) st = dev_alloc(h, s.nn * rs, &s.accU);
+        if (!st && s.accumulated && s.has_T) st = dev_alloc(h, s.nn * rs, &s.accT);
+        if (!st) st = dev_alloc(h, 2 * sizeof(unsigned long long), (void**)&s.smax);
+        if (!st && s.frozen_T) st = dev_alloc(h, sizeof(long long), (void**)&s.clock);
+        s.diag_blocks = (int)std::min<size_t>(1184, (s.nn + 255) / 256);
+        if (!st) st = dev_alloc(h, 3 * sizeof(double) * s.diag_blocks, (void**)&s.part);
+        if (!st) st = dev_alloc(h, 16 * sizeof(double), (void**)&s.dout);
+        if (st) {
+            std::string m = h->err;
+            free_all(h);
+            if (h->own_stream) cudaStreamDestroy(h->stream);
+            delete h;
+            return fail(nullptr, st, "%s", m.c_str());
+        }
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_init_fields(lbm_handle h, int32_t sim, const double* phi, const double* U, const double* T,
+                           const double* ux, const double* uy, const double* rho, int32_t src_is_device) {
+    if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
+    if (sim < 0 || sim >= (int)h->sims.size()) return fail(h, LBM_E_INVALID_ARG, "sim index %d out of range", sim);
+    SimState& s = h->sims[sim];
+    if (!phi) return fail(h, LBM_E_INVALID_ARG, "phi is NULL");
+    if (s.has_U && !U) return fail(h, LBM_E_INVALID_ARG, "U is NULL but the solute field is on");
+    if (s.has_T && !T) return fail(h, LBM_E_INVALID_ARG, "T is NULL but the temperature field is on");
+    if (s.has_flow && (!ux || !uy || !rho)) return fail(h, LBM_E_INVALID_ARG, "ux, uy, rho needed with the flow field on");
+    const double* src[6] = {phi, s.has_U ? U : nullptr, s.has_T ? T : nullptr, s.has_flow ? ux : nullptr,
+                            s.has_flow ? uy : nullptr, s.has_flow ? rho : nullptr};
+    return init_common(h, sim, src, src_is_device);
+}
+
+lbm_status lbm_init_seed(lbm_handle h, int32_t sim, const lbm_seed* seeds, int32_t n_seeds, double U0, double T0,
+                         uint64_t rng_seed) {
+    if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
+    if (sim < 0 || sim >= (int)h->sims.size()) return fail(h, LBM_E_INVALID_ARG, "sim index %d out of range", sim);
+    if (n_seeds < 1 || !seeds) return fail(h, LBM_E_INVALID_ARG, "need at least one seed");
+    SimState& s = h->sims[sim];
+    const int nx = s.nx, ny = s.ny;
+    const size_t n = (size_t)nx * ny;
+    const double sw = std::sqrt(2.0) * s.p.W0;
+    std::vector<double> phi(n, -1.0), U(n, U0), T(n, T0), ux(n, 0.0), uy(n, 0.0), rho(n, 1.0);
+    for (int k = 0; k < n_seeds; ++k) {
+        const lbm_seed& sd = seeds[k];
+        if (sd.kind < LBM_SEED_CIRCLE || sd.kind > LBM_SEED_SINUSOID)
+            return fail(h, LBM_E_INVALID_ARG, "seed %d: unknown kind %d", k, sd.kind);
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const size_t i = (size_t)y * nx + x;
+                double v;
+                if (sd.kind == LBM_SEED_CIRCLE) {
+                    const double r = std::sqrt((x - sd.x) * (x - sd.x) + (y - sd.y) * (y - sd.y));
+                    v = std::tanh((sd.r - r) / sw);
+                } else if (sd.kind == LBM_SEED_PLANAR) {
+                    v = std::tanh((sd.y - y) / sw);
+                    if (sd.amp > 0.0 && std::fabs(v) < 0.99) {
+                        const double u = (double)(splitmix64(rng_seed, i) >> 11) * 0x1.0p-53;
+                        v = std::min(1.0, std::max(-1.0, v + sd.amp * (2.0 * u - 1.0)));
+                    }
+                } else {
+                    const double pi = 3.14159265358979323846;
+                    v = std::tanh((sd.y + sd.amp * std::sin(2.0 * pi * sd.waves * x / nx) - y) / sw);
+                }
+                phi[i] = (k == 0) ? v : std::max(phi[i], v);
+            }
+    }
+    if (s.has_flow)
+        for (size_t i = 0; i < n; ++i) ux[i] = s.p.u_in * 0.5 * (1.0 - phi[i]);
+    const double* src[6] = {phi.data(), s.has_U ? U.data() : nullptr, s.has_T ? T.data() : nullptr,
+                            s.has_flow ? ux.data() : nullptr, s.has_flow ? uy.data() : nullptr,
+                            s.has_flow ? rho.data() : nullptr};
+    return init_common(h, sim, src, 0);
+}
+
+lbm_status lbm_advance(lbm_handle h, int64_t n_base_steps) {
+    if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
+    if (n_base_steps < 0) return fail(h, LBM_E_INVALID_ARG, "n_base_steps < 0");
+    for (auto& s : h->sims) {
+        if (!s.initialized) return fail(h, LBM_E_STATE, "simulation not initialised");
+        if (s.sticky) return fail(h, LBM_E_STATE, "a non-finite value was seen; initialise again");
+    }
+    for (auto& s : h->sims) {
+        int64_t left = n_base_steps;
+        bool clock_set = false;
+        while (left > 0) {
+            const bool use_graph = h->graphs && s.period <= kMaxGraphPeriod && (s.step % s.period) == 0 && left >= s.period;
+            if (use_graph) {
+                if (!s.graph) {
+                    lbm_status st = capture_graph(h, s);
+                    if (st) return st;
+                }
+                if (s.frozen_T && !clock_set) {
+                    k_set_clock<<<1, 1, 0, h->stream>>>(s.clock, (long long)s.step);
+                    clock_set = true;
+                }
+                lbm_status st = graph_replay(h, s);
+                if (st) return st;
+                left -= s.period;
+            } else {
+                enqueue_base_step(h, s, s.step, nullptr, (long long)s.step);
+                s.step += 1;
+                left -= 1;
+                clock_set = false;
+            }
+        }
+    }
+    CK(cudaGetLastError());
+    return collect_pending(h);
+}
+
+lbm_status lbm_fields(lbm_handle h, int32_t sim, uint32_t which, void* dst, int32_t dst_is_device, int32_t as_f64) {
+    if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
+    if (sim < 0 || sim >= (int)h->sims.size()) return fail(h, LBM_E_INVALID_ARG, "sim index %d out of range", sim);
+    if (which > 7) return fail(h, LBM_E_INVALID_ARG, "unknown field %u", which);
+    if (!dst) return fail(h, LBM_E_INVALID_ARG, "dst is NULL");
+    SimState& s = h->sims[sim];
+    if (!s.initialized) return fail(h, LBM_E_STATE, "simulation not initialised");
+    return h->precision == LBM_PREC_F64 ? read_field<double>(h, s, which, dst, dst_is_device, as_f64)
+                                        : read_field<float>(h, s, which, dst, dst_is_device, as_f64);
+}
+
+lbm_status lbm_diagnostics(lbm_handle h, int32_t sim, lbm_diag* out) {
+    if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
+    if (sim < 0 || sim >= (int)h->sims.size()) return fail(h, LBM_E_INVALID_ARG, "sim index %d out of range", sim);
+    if (!out) return fail(h, LBM_E_INVALID_ARG, "out is NULL");
+    SimState& s = h->sims[sim];
+    if (!s.initialized) return fail(h, LBM_E_STATE, "simulation not initialised");
+    lbm_status st = h->precision == LBM_PREC_F64 ? run_diag<double>(h, s, out) : run_diag<float>(h, s, out);
+    if (st == LBM_OK || st == LBM_E_NONFINITE) {
+        lbm_status c = collect_pending(h);
+        if (c) return c;
+    }
+    return st;
+}
+
+const char* lbm_last_error(lbm_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void lbm_destroy(lbm_handle h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (auto& s : h->sims) drop_graph(s);
+    for (auto& t : h->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+    for (auto e : h->event_pool) cudaEventDestroy(e);
+    free_all(h);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+lbm_status lbm_set_graphs(lbm_handle h, int32_t enable) {
+    if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
+    h->graphs = enable != 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_timing_enable(lbm_handle h, uint32_t kind_mask) {
+    if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
+    if (kind_mask >> LBM_K_COUNT) return fail(h, LBM_E_INVALID_ARG, "unknown kernel kind bit");
+    h->timing_mask = kind_mask;
+    for (auto& s : h->sims) drop_graph(s);
+    return LBM_OK;
+}
+
+lbm_status lbm_timing_read(lbm_handle h, double* ms, int64_t* count, int32_t reset) {
+    if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
+    lbm_status st = collect_pending(h);
+    if (st) return st;
+    for (int k = 0; k < LBM_K_COUNT; ++k) {
+        if (ms) ms[k] = h->timing_ms[k];
+        if (count) count[k] = h->timing_n[k];
+        if (reset) { h->timing_ms[k] = 0.0; h->timing_n[k] = 0; }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_launch_counts(lbm_handle h, int64_t* counts) {
+    if (!h || !counts) return fail(h, LBM_E_INVALID_ARG, "NULL argument");
+    for (int k = 0; k < LBM_K_COUNT; ++k) counts[k] = h->launches[k];
+    return LBM_OK;
+}
+
+lbm_status lbm_device_bytes(lbm_handle h, size_t* bytes) {
+    if (!h || !bytes) return fail(h, LBM_E_INVALID_ARG, "NULL argument");
+    *bytes = h->bytes;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 runs must match the oracle within 1e-10 max-abs after up to 1000 base
+steps; FP32 and 16-bit-storage runs within the bounds derived in the design doc
+(per-step rounding of the arithmetic type accumulated linearly over the
+steps)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_helpers import active, max_err, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def _check(p, fields, steps, tol, precision="f64", **kw):
+    g = run_gpu(p, fields, steps, precision=precision, **kw)
+    o = run_oracle(p, fields, steps)
+    err = max_err(g, o, active(p))
+    assert max(err.values()) <= tol, err
+    return g, o, err
+
+
+# ---------------------------------------------------------------------------
+# single field updates, isolated through the schedule (a huge update factor
+# keeps a field from firing within the run)
+# ---------------------------------------------------------------------------
+BIG = 100000
+
+
+def _random_state(n=70, m=45, seed=0, flow=True, bc=W.BC_WALL):
+    wl = W.thermosolutal_convection(n=n, R=8.0)
+    p = wl.params
+    p.nx, p.ny = n, m
+    p.tip_cx, p.tip_cy = n // 2, m // 2
+    p.bc_scalar_x = p.bc_scalar_y = bc
+    p.has_flow = flow
+    p.eps = 0.05
+    rng = np.random.default_rng(seed)
+    phi = W.circle_seed(n, m, n / 2 + 0.3, m / 2 - 0.2, 12.0, p.W0)
+    f = W.base_fields(p, phi, U0=0.0, T0=-0.55)
+    f["U"] = 0.1 * rng.standard_normal((m, n)) * (1 - phi ** 2) + 0.05
+    f["T"] = -0.55 + 0.05 * rng.standard_normal((m, n))
+    if flow:
+        f["ux"] = 0.01 + 0.002 * rng.standard_normal((m, n))
+        f["uy"] = 0.002 * rng.standard_normal((m, n))
+        f["rho"] = 1 + 0.001 * rng.standard_normal((m, n))
+    return p, f
+
+
+@pytest.mark.parametrize("bc", [W.BC_WALL, W.BC_PERIODIC])
+@pytest.mark.parametrize("which", ["phase", "U", "T", "flow"])
+def test_single_update_fp64(which, bc):
+    p, f = _random_state(bc=bc, flow=(which in ("flow", "U")))
+    if bc == W.BC_PERIODIC:
+        p.bc_flow_x = W.BC_PERIODIC
+    p.N_phi = 1 if which == "phase" else BIG
+    p.N_U = 1 if which == "U" else BIG
+    p.N_T = 1 if which == "T" else BIG
+    p.N_F = 1 if which == "flow" else BIG
+    _check(p, f, 3, 1e-13)
+
+
+# ---------------------------------------------------------------------------
+# whole runs
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N_T", [1, 2])
+def test_thermal_dendrite_fp64_1000_steps(N_T):
+    """128^2 periodic thermal dendrite (phi + T), FP64, 1000 base steps:
+    max-abs phi, T within 1e-10 of the oracle; exact enthalpy invariant."""
+    wl = W.thermal_free_dendrite(n=128, N_T=N_T)
+    g, o, err = _check(wl.params, wl.fields, 1000, 1e-10)
+    assert abs(g["diag"]["H"] - o["diag"]["H"]) < 1e-9
+    assert np.abs(g["diag"]["tip"] - o["diag"]["tip"]).max() < 1e-8
+
+
+def test_thermosolutal_convection_fp64_ragged():
+    """All four fields with inlet/outflow, multirate (1, 1, 2, 2), on a
+    ragged 80 x 70 lattice (tiles of 32 x 8 do not divide it)."""
+    wl = W.thermosolutal_convection(n=80, R=8.0)
+    p = wl.params
+    p.ny = 70
+    p.tip_cy = 35
+    f = W.base_fields(p, W.circle_seed(80, 70, 40, 35, 8.0, p.W0), U0=0.0, T0=-0.55)
+    g, o, err = _check(p, f, 300, 1e-10)
+    assert abs(g["diag"]["M_C"] - o["diag"]["M_C"]) / o["diag"]["M_C"] < 1e-12
+
+
+def test_accumulated_coupling_fp64():
+    wl = W.thermosolutal_convection(n=64, R=6.0, N=(1, 3, 2, 2))
+    wl.params.accumulated = True
+    g, o, err = _check(wl.params, wl.fields, 120, 1e-10)
+    assert abs(g["diag"]["J_U"] - o["diag"]["J_U"]) <= 1e-10 * max(1.0, o["diag"]["J_U"])
+
+
+def test_directional_frozen_temperature_fp64():
+    wl = W.directional_saline(Le=10, nx=96, ny=160, y0=40.0, seed=3)
+    g, o, err = _check(wl.params, wl.fields, 200, 1e-10)
+
+
+def test_graphs_and_chunking_bitwise_identical():
+    wl = W.thermosolutal_convection(n=64, R=6.0)
+    a = run_gpu(wl.params, wl.fields, 40, precision="f32", graphs=True)
+    b = run_gpu(wl.params, wl.fields, 40, precision="f32", graphs=False, chunks=[3, 5, 1, 31])
+    for k in active(wl.params):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_fp32_thermosolutal_1000_steps():
+    """FP32 storage and arithmetic against the FP64 oracle after 1000 steps."""
+    wl = W.thermosolutal_convection(n=128, R=8.0)
+    g, o, err = _check(wl.params, wl.fields, 1000, 2e-3, precision="f32")
+    assert abs(g["diag"]["M_C"] - o["diag"]["M_C"]) / o["diag"]["M_C"] < 1e-5
+
+
+def test_init_seed_matches_generator():
+    import paper_2609_25670_b300 as lbm
+    wl = W.thermosolutal_convection(n=96, R=8.0)
+    sim = lbm.Simulation(wl.params, precision="f64")
+    sim.init_seed([{"kind": "circle", "x": 48, "y": 48, "r": 8.0}], U0=0.0, T0=-0.55)
+    for k in ("phi", "U", "T", "ux", "rho"):
+        assert np.abs(sim.field(k) - wl.fields[k]).max() < 1e-14, k
+    sim.close()
+    wd = W.directional_saline(Le=10, nx=64, ny=96, y0=40.0, seed=3)
+    sim = lbm.Simulation(wd.params, precision="f64")
+    sim.init_seed([{"kind": "planar", "y": 40.0, "amp": 0.01}], U0=0.0, rng_seed=3)
+    assert np.abs(sim.field("phi") - wd.fields["phi"]).max() < 1e-14
+    sim.close()
