@@ -51,8 +51,8 @@ ALGO_BYTES = {
 }
 
 
-def workload():
-    return W.thermosolutal_convection(n=N_LATTICE, R=8.0)
+def workload(n=None):
+    return W.thermosolutal_convection(n=n or N_LATTICE, R=8.0)
 
 
 def dist_env():
@@ -180,7 +180,7 @@ def run_ours(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
-    wl = workload()
+    wl = workload(args.lattice)
     p = wl.params
     nodes = p.nx * p.ny
     sim = lbm.Simulation(p, precision="f32")
@@ -194,9 +194,11 @@ def run_ours(args):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
-    # warm-up (captures the period graph)
+    # warm-up, tile autotuning on the live state (leaves it unchanged), graph capture
     for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
         sim.advance(STEP_BASE)
+    tiles = sim.autotune(reps=10)
+    sim.advance(STEP_BASE)
     kinds = ["phase", "transfer", "scalar_U", "scalar_T", "flow"]
     sim.timing_enable(kinds)
     sim.advance(STEP_BASE)           # recapture with timing nodes, untimed
@@ -244,7 +246,7 @@ def run_ours(args):
     host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in wl.fields.items()}
     host_np = {k: v.numpy() for k, v in host.items()}
     out_phi = torch.empty((p.ny, p.nx), dtype=torch.float64).pin_memory().numpy()
-    e2e_steps = max(3, min(args.steps, 50))
+    e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 50))
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -253,7 +255,7 @@ def run_ours(args):
         sim.field("phi", out=out_phi)
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e_val = nodes * STEP_BASE * e2e_steps * world / e2e_s / 1e6
+    e2e_val = nodes * STEP_BASE * e2e_steps * world / e2e_s / 1e6 if e2e_steps else None
     h2d = 6 * 8 * nodes
     d2h = 8 * nodes
 
@@ -270,6 +272,7 @@ def run_ours(args):
                          "algo_bytes_per_node": ALGO_BYTES[dom], "avg_launch_us": avg_s * 1e6,
                          "launches_timed": dom_n},
             "kernel_ms": {k: ktimes[k][0] for k in kinds},
+            "tiles": {k: tiles[k] for k in kinds},
             "gpu_launches": gpu_launches,
             "wall_s_timed_region": wall,
             "clocks": clk,
@@ -292,6 +295,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
+    ap.add_argument("--lattice", type=int, default=None,
+                    help="lattice size override for profiling runs (the reported workload is 512)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -215,6 +215,15 @@ lbm_status lbm_timing_enable(lbm_handle h, uint32_t kind_mask);
  * last reset; reset = 1 clears them. ms and count hold LBM_K_COUNT entries. */
 lbm_status lbm_timing_read(lbm_handle h, double* ms, int64_t* count, int32_t reset);
 
+/* Autotuner: for every update kernel kind of every simulation, time each
+ * compiled tile shape (32 x 4, 32 x 8, 32 x 16 threads) over `reps` launches on
+ * the current state and keep the fastest.  The update kernels read one
+ * ping-pong buffer and write the other, so the repeated launches leave the
+ * simulation unchanged (the S_phi / J_U maxima are cleared).  chosen (nullable)
+ * receives LBM_K_COUNT tile heights of simulation 0.  Recaptures graphs.
+ * Errors: STATE (not initialised), CUDA. */
+lbm_status lbm_autotune(lbm_handle h, int32_t reps, int32_t* chosen);
+
 /* Number of kernel launches the library has issued (graph replays count
  * their kernel nodes), per kind; counts hold LBM_K_COUNT entries. */
 lbm_status lbm_launch_counts(lbm_handle h, int64_t* counts);

@@ -30,7 +30,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSTABLE_PARAMS", 3: "OOM", 4: "CUDA", 
 
 EXPORTED = ["lbm_create", "lbm_init_seed", "lbm_init_fields", "lbm_advance", "lbm_fields",
             "lbm_diagnostics", "lbm_last_error", "lbm_destroy", "lbm_set_graphs", "lbm_timing_enable",
-            "lbm_timing_read", "lbm_launch_counts", "lbm_device_bytes"]
+            "lbm_timing_read", "lbm_launch_counts", "lbm_device_bytes", "lbm_autotune"]
 
 
 class LbmError(RuntimeError):
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.lbm_timing_read.argtypes = [vp, dp, C.POINTER(C.c_int64), i32]
     lib.lbm_launch_counts.argtypes = [vp, C.POINTER(C.c_int64)]
     lib.lbm_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+    lib.lbm_autotune.argtypes = [vp, i32, C.POINTER(C.c_int32)]
     for nm in EXPORTED:
         f = getattr(lib, nm)
         if nm not in ("lbm_last_error", "lbm_destroy"):
@@ -273,6 +274,12 @@ class Simulation:
         cnt = (C.c_int64 * len(KERNEL_KINDS))()
         self._ck(self.lib.lbm_timing_read(self.h, ms, cnt, 1 if reset else 0))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def autotune(self, reps: int = 20) -> Dict[str, int]:
+        """Pick the fastest compiled tile height per kernel kind on the current state."""
+        ch = (C.c_int32 * len(KERNEL_KINDS))()
+        self._ck(self.lib.lbm_autotune(self.h, int(reps), ch))
+        return {k: ch[i] for i, k in enumerate(KERNEL_KINDS)}
 
     def launch_counts(self) -> Dict[str, int]:
         cnt = (C.c_int64 * len(KERNEL_KINDS))()

@@ -20,7 +20,6 @@ using namespace lbmk;
 namespace {
 
 constexpr int TX = 32;
-constexpr int TY = 8;   // tile height of the update kernels (256 threads)
 constexpr int kMaxGraphPeriod = 4096;
 
 thread_local std::string g_create_error;
@@ -57,6 +56,7 @@ struct SimState {
     int period = 1;                      // 2 * lcm of the update factors
     cudaGraphExec_t graph = nullptr;
     int graph_kernels[LBM_K_COUNT] = {};
+    int tile[LBM_K_COUNT] = {8, 8, 8, 8, 8, 8, 8};   // tile height per kernel kind (autotuned)
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> graph_events;
 };
 
@@ -274,33 +274,79 @@ lbm_status collect_pending(lbm_sim* h) {
     return LBM_OK;
 }
 
-// ---------------------------------------------------------------------------
-// the update sequence of one base step (Fig. 1), precision-templated
-// ---------------------------------------------------------------------------
+// Launch one update kernel of `kind` for the current ping-pong parities
+// (the caller flips them).  Reads buffer `cur`, writes buffer `1 - cur`: a
+// repeated launch recomputes the same output, which the autotuner relies on.
+template <int TYV>
+inline dim3 grid_of(const SimState& s) { return dim3((s.nx + TX - 1) / TX, (s.ny + TYV - 1) / TYV); }
+
+#define LBM_TY_SWITCH(sel, BODY)                       \
+    switch (sel) {                                     \
+        case 4: { constexpr int TYV = 4; BODY; } break;   \
+        case 16: { constexpr int TYV = 16; BODY; } break; \
+        default: { constexpr int TYV = 8; BODY; } break;  \
+    }
+
 template <typename R, typename ST, bool DEV>
-void enqueue_step(lbm_sim* h, SimState& s, int64_t n, const long long* clock, long long off) {
-    const lbm_params& p = s.p;
+void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* clock, long long off) {
     const KP<R> P = make_kp<R>(s);
-    const dim3 blk(TX, TY), grd((s.nx + TX - 1) / TX, (s.ny + TY - 1) / TY);
     cudaStream_t st = h->stream;
-    R* phi_c = (R*)s.phi[s.cur_phi];
-    R* phi_n = (R*)s.phi[1 - s.cur_phi];
+    LaunchScope ls(h, kind);
+    const R* phi_now = (const R*)s.phi[s.cur_phi];
+    const R* uxc = s.has_flow ? (const R*)s.ux[s.cur_pop[FF]] : nullptr;
+    const R* uyc = s.has_flow ? (const R*)s.uy[s.cur_pop[FF]] : nullptr;
+    switch (kind) {
+        case LBM_K_PHASE:
+            LBM_TY_SWITCH(tysel, (k_phase<R, ST, DEV, TYV><<<grid_of<TYV>(s), dim3(TX, TYV), 0, st>>>(
+                P, (const ST*)s.pops[FP][s.cur_pop[FP]], (ST*)s.pops[FP][1 - s.cur_pop[FP]], phi_now,
+                (R*)s.phi[1 - s.cur_phi], s.has_U ? (const R*)s.U[s.cur_U] : nullptr,
+                s.has_T ? (const R*)s.T[s.cur_T] : nullptr, clock, off)));
+            break;
+        case LBM_K_TRANSFER:   // phi^q = phi[1 - cur], phi^{q+1} = phi[cur] (after the phase flip)
+            LBM_TY_SWITCH(tysel, (k_transfer<R, TYV><<<grid_of<TYV>(s), dim3(TX, TYV), 0, st>>>(
+                P, (const R*)s.phi[1 - s.cur_phi], phi_now, s.has_U ? (const R*)s.U[s.cur_U] : nullptr,
+                s.has_U ? (R*)s.U[1 - s.cur_U] : nullptr, s.has_T ? (const R*)s.T[s.cur_T] : nullptr,
+                s.has_T ? (R*)s.T[1 - s.cur_T] : nullptr, (R*)s.accU, (R*)s.accT, s.acc_reset_U ? 1 : 0,
+                s.acc_reset_T ? 1 : 0, s.smax)));
+            break;
+        case LBM_K_SCALAR_U:
+            LBM_TY_SWITCH(tysel, (k_scalar<R, ST, DEV, TYV, 0><<<grid_of<TYV>(s), dim3(TX, TYV), 0, st>>>(
+                P, (const ST*)s.pops[FU][s.cur_pop[FU]], (ST*)s.pops[FU][1 - s.cur_pop[FU]], (const R*)s.U[s.cur_U],
+                (R*)s.U[1 - s.cur_U], (const R*)s.accU, phi_now, uxc, uyc, s.smax)));
+            break;
+        case LBM_K_SCALAR_T:
+            LBM_TY_SWITCH(tysel, (k_scalar<R, ST, DEV, TYV, 1><<<grid_of<TYV>(s), dim3(TX, TYV), 0, st>>>(
+                P, (const ST*)s.pops[FT][s.cur_pop[FT]], (ST*)s.pops[FT][1 - s.cur_pop[FT]], (const R*)s.T[s.cur_T],
+                (R*)s.T[1 - s.cur_T], (const R*)s.accT, phi_now, uxc, uyc, s.smax)));
+            break;
+        case LBM_K_FLOW: {
+            const int c = s.cur_pop[FF];
+            LBM_TY_SWITCH(tysel, (k_flow<R, ST, DEV, TYV><<<grid_of<TYV>(s), dim3(TX, TYV), 0, st>>>(
+                P, (const ST*)s.pops[FF][c], (ST*)s.pops[FF][1 - c], phi_now, (const R*)s.ux[c], (const R*)s.uy[c],
+                (const R*)s.rho[c], (R*)s.ux[1 - c], (R*)s.uy[1 - c], (R*)s.rho[1 - c])));
+            break;
+        }
+        default: break;
+    }
+}
+
+void launch_any(lbm_sim* h, SimState& s, int kind, int tysel, const long long* clock, long long off) {
+    switch (h->precision) {
+        case LBM_PREC_F64: launch_kind<double, double, false>(h, s, kind, tysel, clock, off); break;
+        case LBM_PREC_F32: launch_kind<float, float, false>(h, s, kind, tysel, clock, off); break;
+        case LBM_PREC_F16_DEV: launch_kind<float, __half, true>(h, s, kind, tysel, clock, off); break;
+        default: launch_kind<float, __nv_bfloat16, true>(h, s, kind, tysel, clock, off); break;
+    }
+}
+
+// The update sequence of one base step (Eq. 34 schedule, workflow of Fig. 1).
+void enqueue_base_step(lbm_sim* h, SimState& s, int64_t n, const long long* clock, long long off) {
+    const lbm_params& p = s.p;
     if ((n + 1) % p.N_phi == 0) {
-        {
-            LaunchScope ls(h, LBM_K_PHASE);
-            k_phase<R, ST, DEV, TY><<<grd, blk, 0, st>>>(
-                P, (const ST*)s.pops[FP][s.cur_pop[FP]], (ST*)s.pops[FP][1 - s.cur_pop[FP]], phi_c, phi_n,
-                s.has_U ? (const R*)s.U[s.cur_U] : nullptr, s.has_T ? (const R*)s.T[s.cur_T] : nullptr, clock, off);
-        }
+        launch_any(h, s, LBM_K_PHASE, s.tile[LBM_K_PHASE], clock, off);
         s.cur_pop[FP] ^= 1;
-        {
-            LaunchScope ls(h, LBM_K_TRANSFER);
-            k_transfer<R, TY><<<grd, blk, 0, st>>>(
-                P, phi_c, phi_n, s.has_U ? (const R*)s.U[s.cur_U] : nullptr, s.has_U ? (R*)s.U[1 - s.cur_U] : nullptr,
-                s.has_T ? (const R*)s.T[s.cur_T] : nullptr, s.has_T ? (R*)s.T[1 - s.cur_T] : nullptr, (R*)s.accU,
-                (R*)s.accT, s.acc_reset_U ? 1 : 0, s.acc_reset_T ? 1 : 0, s.smax);
-        }
-        s.cur_phi ^= 1;
+        s.cur_phi ^= 1;                      // phi[cur] = phi^{q+1}
+        launch_any(h, s, LBM_K_TRANSFER, s.tile[LBM_K_TRANSFER], clock, off);
         if (!s.accumulated) {
             if (s.has_U) s.cur_U ^= 1;
             if (s.has_T) s.cur_T ^= 1;
@@ -309,49 +355,21 @@ void enqueue_step(lbm_sim* h, SimState& s, int64_t n, const long long* clock, lo
             s.acc_reset_T = false;
         }
     }
-    const R* phi_now = (const R*)s.phi[s.cur_phi];
-    const R* uxc = s.has_flow ? (const R*)s.ux[s.cur_pop[FF]] : nullptr;
-    const R* uyc = s.has_flow ? (const R*)s.uy[s.cur_pop[FF]] : nullptr;
     if (s.has_U && (n + 1) % p.N_U == 0) {
-        {
-            LaunchScope ls(h, LBM_K_SCALAR_U);
-            k_scalar<R, ST, DEV, TY, 0><<<grd, blk, 0, st>>>(
-                P, (const ST*)s.pops[FU][s.cur_pop[FU]], (ST*)s.pops[FU][1 - s.cur_pop[FU]], (const R*)s.U[s.cur_U],
-                (R*)s.U[1 - s.cur_U], (const R*)s.accU, phi_now, uxc, uyc, s.smax);
-        }
+        launch_any(h, s, LBM_K_SCALAR_U, s.tile[LBM_K_SCALAR_U], clock, off);
         s.cur_pop[FU] ^= 1;
         s.cur_U ^= 1;
         s.acc_reset_U = true;
     }
     if (s.has_T && (n + 1) % p.N_T == 0) {
-        {
-            LaunchScope ls(h, LBM_K_SCALAR_T);
-            k_scalar<R, ST, DEV, TY, 1><<<grd, blk, 0, st>>>(
-                P, (const ST*)s.pops[FT][s.cur_pop[FT]], (ST*)s.pops[FT][1 - s.cur_pop[FT]], (const R*)s.T[s.cur_T],
-                (R*)s.T[1 - s.cur_T], (const R*)s.accT, phi_now, uxc, uyc, s.smax);
-        }
+        launch_any(h, s, LBM_K_SCALAR_T, s.tile[LBM_K_SCALAR_T], clock, off);
         s.cur_pop[FT] ^= 1;
         s.cur_T ^= 1;
         s.acc_reset_T = true;
     }
     if (s.has_flow && (n + 1) % p.N_F == 0) {
-        const int c = s.cur_pop[FF];
-        {
-            LaunchScope ls(h, LBM_K_FLOW);
-            k_flow<R, ST, DEV, TY><<<grd, blk, 0, st>>>(P, (const ST*)s.pops[FF][c], (ST*)s.pops[FF][1 - c], phi_now,
-                                                     (const R*)s.ux[c], (const R*)s.uy[c], (const R*)s.rho[c],
-                                                     (R*)s.ux[1 - c], (R*)s.uy[1 - c], (R*)s.rho[1 - c]);
-        }
+        launch_any(h, s, LBM_K_FLOW, s.tile[LBM_K_FLOW], clock, off);
         s.cur_pop[FF] ^= 1;
-    }
-}
-
-void enqueue_base_step(lbm_sim* h, SimState& s, int64_t n, const long long* clock, long long off) {
-    switch (h->precision) {
-        case LBM_PREC_F64: enqueue_step<double, double, false>(h, s, n, clock, off); break;
-        case LBM_PREC_F32: enqueue_step<float, float, false>(h, s, n, clock, off); break;
-        case LBM_PREC_F16_DEV: enqueue_step<float, __half, true>(h, s, n, clock, off); break;
-        default: enqueue_step<float, __nv_bfloat16, true>(h, s, n, clock, off); break;
     }
 }
 
@@ -786,6 +804,48 @@ lbm_status lbm_timing_read(lbm_handle h, double* ms, int64_t* count, int32_t res
         if (count) count[k] = h->timing_n[k];
         if (reset) { h->timing_ms[k] = 0.0; h->timing_n[k] = 0; }
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_handle h, int32_t reps, int32_t* chosen) {
+    if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
+    if (reps < 1) return fail(h, LBM_E_INVALID_ARG, "reps must be >= 1");
+    static const int variants[3] = {4, 8, 16};
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    const uint32_t mask = h->timing_mask;
+    h->timing_mask = 0;
+    for (auto& s : h->sims) {
+        if (!s.initialized) { cudaEventDestroy(a); cudaEventDestroy(b); h->timing_mask = mask;
+                              return fail(h, LBM_E_STATE, "simulation not initialised"); }
+        const bool present[LBM_K_COUNT] = {true, !s.accumulated, s.has_U, s.has_T, s.has_flow, false, false};
+        for (int kind = 0; kind < LBM_K_FLOW + 1; ++kind) {
+            if (!present[kind]) continue;
+            float best = 1e30f;
+            int bestv = s.tile[kind];
+            for (int v : variants) {
+                launch_any(h, s, kind, v, s.clock, 0);          // warm the variant
+                CK(cudaEventRecord(a, h->stream));
+                for (int r = 0; r < reps; ++r) launch_any(h, s, kind, v, s.clock, 0);
+                CK(cudaEventRecord(b, h->stream));
+                CK(cudaEventSynchronize(b));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, a, b));
+                if (ms < best) { best = ms; bestv = v; }
+            }
+            s.tile[kind] = bestv;
+        }
+        CK(cudaMemsetAsync(s.smax, 0, 2 * sizeof(unsigned long long), h->stream));
+        drop_graph(s);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    h->timing_mask = mask;
+    if (chosen)
+        for (int k = 0; k < LBM_K_COUNT; ++k) chosen[k] = h->sims[0].tile[k];
     return LBM_OK;
 }
 

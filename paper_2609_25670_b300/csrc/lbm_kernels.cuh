@@ -149,101 +149,152 @@ __device__ __forceinline__ void put_scalar_post(R (*sp)[HY][HX], int ly, int lx,
     sp[8][ly][lx] = a2 + (b2x - b2y) + (cx - cy);
 }
 
-// first moment of stored populations 1..8 (deviation references cancel for U, T)
-template <typename R, typename ST>
-__device__ __forceinline__ void first_moment(const ST* __restrict__ f, size_t node, long long plane, R& jx, R& jy) {
-    R v[9];
-#pragma unroll
-    for (int i = 1; i < 9; ++i) v[i] = (R)Cvt<ST>::ld(f[(size_t)(i - 1) * plane + node]);
-    jx = v[1] - v[3] + v[5] - v[6] - v[7] + v[8];
-    jy = v[2] - v[4] + v[5] + v[6] - v[7] - v[8];
-}
-
-// phase populations 1..8 (+ f_0 from phi); DEV: h_i = f_i - w_i phi
-template <typename R, typename ST, bool DEV>
-__device__ __forceinline__ void load_phase(const ST* __restrict__ f, size_t node, long long plane, R phi, R* v) {
-    R s = R(0);
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        R h = (R)Cvt<ST>::ld(f[(size_t)(i - 1) * plane + node]);
-        v[i] = DEV ? (wq<R>(i) * phi + h) : h;
-        s += v[i];
-    }
-    v[0] = phi - s;
-}
-
 template <typename R> __device__ __forceinline__ R theta_frozen(const KP<R>& P, int y, R t) {
     return P.theta_c + P.fG * ((R)y - P.fy0 - P.fV * t);
 }
 
 // ---------------------------------------------------------------------------
+// Work items of a tile.  Every update kernel collides the tile plus a 1-node
+// ring: item A of thread (tx, ty) is its own node (halo position tx+1, ty+1);
+// item B of threads tid < NR is one of the NR = 2(TX+2) + 2 TY ring positions.
+// All global loads of both items are issued before the first barrier, so a
+// block pays one memory round trip before it computes.
+// ---------------------------------------------------------------------------
+template <int TY>
+__device__ __forceinline__ void ring_pos(int t, int& lx, int& ly) {
+    constexpr int HX = 34;
+    if (t < HX) { lx = t; ly = 0; }
+    else if (t < 2 * HX) { lx = t - HX; ly = TY + 1; }
+    else if (t < 2 * HX + TY) { lx = 0; ly = t - 2 * HX + 1; }
+    else { lx = HX - 1; ly = t - 2 * HX - TY + 1; }
+}
+
+// resolve both coordinates (each is always evaluated)
+__device__ __forceinline__ bool resolve_xy(int& x, int& y, int nx, int ny, int bcx, int bcy) {
+    const bool a = resolve(x, nx, bcx);
+    const bool b = resolve(y, ny, bcy);
+    return a && b;
+}
+
+// phi on the tile plus a 2-node ghost ring (scalar boundary rule)
+template <typename R, int TY>
+__device__ __forceinline__ void load_phi_ring2(const KP<R>& P, const R* __restrict__ phi, R (*s)[36], int x0, int y0,
+                                               int tid) {
+    constexpr int GX = 36, GY = TY + 4, NT = 32 * TY;
+    R v[(GX * GY + NT - 1) / NT];
+#pragma unroll
+    for (int k = 0; k < (GX * GY + NT - 1) / NT; ++k) {
+        const int p = tid + k * NT;
+        if (p < GX * GY) {
+            const int lx = p % GX, ly = p / GX;
+            const int gx = scalar_map(x0 - 2 + lx, P.nx, P.bsx), gy = scalar_map(y0 - 2 + ly, P.ny, P.bsy);
+            v[k] = phi[(size_t)gy * P.pitch + gx];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < (GX * GY + NT - 1) / NT; ++k) {
+        const int p = tid + k * NT;
+        if (p < GX * GY) s[p / GX][p % GX] = v[k];
+    }
+}
+
+template <typename R, typename ST>
+__device__ __forceinline__ void load8(const ST* __restrict__ f, size_t node, long long plane, R* v) {
+#pragma unroll
+    for (int i = 1; i < 9; ++i) v[i] = (R)Cvt<ST>::ld(f[(size_t)(i - 1) * plane + node]);
+}
+template <typename R> __device__ __forceinline__ R mom_x(const R* v) { return v[1] - v[3] + v[5] - v[6] - v[7] + v[8]; }
+template <typename R> __device__ __forceinline__ R mom_y(const R* v) { return v[2] - v[4] + v[5] + v[6] - v[7] - v[8]; }
+
+// ---------------------------------------------------------------------------
 // Phase-field update (Eqs. 2-4, 14, 21-24, 26, 18)
 // ---------------------------------------------------------------------------
+// collision of the phase populations at halo position (lx, ly); returns a_s^2
+template <typename R, int TY>
+__device__ __forceinline__ R phase_collide(const KP<R>& P, const R (*sphi)[36], R (*sp)[TY + 2][34], int lx, int ly,
+                                           int gy, R jx, R jy, R Us, R Tv, R tnow) {
+    const R c = sphi[ly + 1][lx + 1];
+    R gxv, gyv, as, Nx, Ny;
+    iso_grad<R, 36>(sphi, lx + 1, ly + 1, gxv, gyv);
+    aniso(gxv, gyv, P.eps, as, Nx, Ny);
+    const R a2 = as * as;
+    const R s = R(1) / (R(3) * P.dtp * a2 * P.W0sq_tau0 + R(0.5));              // Eq. 24
+    R th;
+    if (P.has_T) th = (Tv - P.T_shift) * P.inv_T_scale;                          // Eq. 5
+    else if (P.frozen_T) th = theta_frozen(P, gy, tnow);
+    else th = P.theta_c;
+    const R one = R(1) - c * c;
+    const R Q = c * one - P.lam * (P.Mc * Us + th) * one * one;                   // Eq. 4
+    const R bx = -P.dtp * P.W0sq_tau0 * Nx, by = -P.dtp * P.W0sq_tau0 * Ny;      // dt v_n (Eqs. 21-22)
+    const R k6 = (R(1) - s) * (R(1) / R(6));
+    put_scalar_post<R, TY + 2, 34>(sp, ly, lx, c + P.dtp * Q * P.inv_tau0, bx, by, k6 * (jx - bx), k6 * (jy - by));
+    return a2;
+}
+
 template <typename R, typename ST, bool DEV, int TY>
 __global__ void __launch_bounds__(32 * TY)
 k_phase(const KP<R> P, const ST* __restrict__ fin, ST* __restrict__ fout, const R* __restrict__ phi,
         R* __restrict__ phin, const R* __restrict__ Um, const R* __restrict__ Tm,
         const long long* __restrict__ clock, long long step_off) {
-    constexpr int TX = 32, HX = TX + 2, HY = TY + 2, GX = TX + 4, GY = TY + 4, NT = 32 * TY;
-    __shared__ R sphi[GY][GX];
+    constexpr int TX = 32, HX = TX + 2, HY = TY + 2, GY = TY + 4, NR = 2 * HX + 2 * TY;
+    static_assert(NR <= 32 * TY, "ring larger than the block");
+    __shared__ R sphi[GY][36];
     __shared__ R spost[9][HY][HX];
-    __shared__ R sas2[TY][TX];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int tid = threadIdx.y * TX + threadIdx.x;
-
-    for (int p = tid; p < GX * GY; p += NT) {
-        const int lx = p % GX, ly = p / GX;
-        const int gx = scalar_map(x0 - 2 + lx, P.nx, P.bsx), gy = scalar_map(y0 - 2 + ly, P.ny, P.bsy);
-        sphi[ly][lx] = phi[(size_t)gy * P.pitch + gx];
+    int ax = x0 + tx, ay = y0 + ty;
+    const bool own = ax < P.nx && ay < P.ny;
+    const bool va = resolve_xy(ax, ay, P.nx, P.ny, P.bsx, P.bsy);
+    int blx = 0, bly = 0, bx = 0, by = 0;
+    bool vb = false;
+    if (tid < NR) {
+        ring_pos<TY>(tid, blx, bly);
+        bx = x0 - 1 + blx;
+        by = y0 - 1 + bly;
+        vb = resolve_xy(bx, by, P.nx, P.ny, P.bsx, P.bsy);
     }
+    const size_t na = (size_t)ay * P.pitch + ax, nb = (size_t)by * P.pitch + bx;
+    R fa[9], fb[9];
+    R Ua = R(0), Ta = R(0), Ub = R(0), Tb = R(0);
+    if (va) {
+        load8<R, ST>(fin, na, P.plane, fa);
+        if (P.has_U) Ua = Um[na];
+        if (P.has_T) Ta = Tm[na];
+    }
+    if (vb) {
+        load8<R, ST>(fin, nb, P.plane, fb);
+        if (P.has_U) Ub = Um[nb];
+        if (P.has_T) Tb = Tm[nb];
+    }
+    load_phi_ring2<R, TY>(P, phi, sphi, x0, y0, tid);
     R tnow = R(0);
     if (P.frozen_T) tnow = (R)((clock ? *clock : 0ll) + step_off) * P.dt_base;
     __syncthreads();
-
-    for (int p = tid; p < HX * HY; p += NT) {
-        const int lx = p % HX, ly = p / HX;
-        int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-        if (!resolve(gx, P.nx, P.bsx) || !resolve(gy, P.ny, P.bsy)) continue;
-        const size_t node = (size_t)gy * P.pitch + gx;
-        const R c = sphi[ly + 1][lx + 1];
-        R gxv, gyv, as, Nx, Ny;
-        iso_grad<R, GX>(sphi, lx + 1, ly + 1, gxv, gyv);
-        aniso(gxv, gyv, P.eps, as, Nx, Ny);
-        const R a2 = as * as;
-        const R s = R(1) / (R(3) * P.dtp * a2 * P.W0sq_tau0 + R(0.5));          // Eq. 24
-        const R Us = P.has_U ? Um[node] : R(0);
-        R th;
-        if (P.has_T) th = (Tm[node] - P.T_shift) * P.inv_T_scale;                // Eq. 5
-        else if (P.frozen_T) th = theta_frozen(P, gy, tnow);
-        else th = P.theta_c;
-        const R one = R(1) - c * c;
-        const R Q = c * one - P.lam * (P.Mc * Us + th) * one * one;               // Eq. 4
-        R jx, jy;
-        first_moment<R, ST>(fin, node, P.plane, jx, jy);                        // DEV refs cancel
-        const R bx = -P.dtp * P.W0sq_tau0 * Nx, by = -P.dtp * P.W0sq_tau0 * Ny;  // dt v_n (Eqs. 21-22)
-        const R k6 = (R(1) - s) * (R(1) / R(6));
-        put_scalar_post<R, HY, HX>(spost, ly, lx, c + P.dtp * Q * P.inv_tau0, bx, by, k6 * (jx - bx), k6 * (jy - by));
-        if (lx >= 1 && lx <= TX && ly >= 1 && ly <= TY) sas2[ly - 1][lx - 1] = a2;
-    }
+    R a2own = R(1);
+    if (va) a2own = phase_collide<R, TY>(P, sphi, spost, tx + 1, ty + 1, ay, mom_x(fa), mom_y(fa), Ua, Ta, tnow);
+    if (vb) phase_collide<R, TY>(P, sphi, spost, blx, bly, by, mom_x(fb), mom_y(fb), Ub, Tb, tnow);
     __syncthreads();
-
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int gx = x0 + tx, gy = y0 + ty;
-    if (gx >= P.nx || gy >= P.ny) return;
-    const size_t node = (size_t)gy * P.pitch + gx;
+    if (!own) return;
     const R c = sphi[ty + 2][tx + 2];
-    const R inva2 = R(1) / sas2[ty][tx];
-    R fo[9], fn[9];
-    load_phase<R, ST, DEV>(fin, node, P.plane, c, fo);
-    R sum = R(0);
+    const R inva2 = R(1) / a2own;
+    R s8 = R(0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        if (DEV) fa[i] += wq<R>(i) * c;          // decode h_i = f_i - w_i phi
+        s8 += fa[i];
+    }
+    fa[0] = c - s8;                              // population 0 from the zeroth moment
+    const int gx = x0 + tx, gy = y0 + ty;
+    R fn[9], sum = R(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int sx = gx - c_ex[i], sy = gy - c_ey[i];
         const bool wall = (P.bsx != BC_PERIODIC && outside(sx, P.nx)) || (P.bsy != BC_PERIODIC && outside(sy, P.ny));
         const R inc = wall ? spost[c_opp[i]][ty + 1][tx + 1] : spost[i][ty + 1 - c_ey[i]][tx + 1 - c_ex[i]];
-        fn[i] = fo[i] + (inc - fo[i]) * inva2;                                  // Eq. 26
+        fn[i] = fa[i] + (inc - fa[i]) * inva2;                                   // Eq. 26
         sum += fn[i];
     }
+    const size_t node = (size_t)gy * P.pitch + gx;
     phin[node] = sum;                                                            // Eq. 18
 #pragma unroll
     for (int i = 1; i < 9; ++i)
@@ -257,87 +308,102 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* slot, double 
     if (v > 0.0) atomicMax(slot, (unsigned long long)__double_as_longlong(v));
 }
 
+// map a halo position to the node whose J fills it: periodic wrap, or the
+// mirrored node with the wall-normal flips; (cx, cy) = its shared-tile position
+__device__ __forceinline__ bool j_source(int& g, int n, int bc, int base, int& c, bool& flip) {
+    flip = false;
+    if (g >= 0 && g < n) return true;
+    if (bc == BC_PERIODIC) { g = wrap_idx(g, n); return true; }
+    g = (g < 0) ? (-1 - g) : (2 * n - 1 - g);
+    flip = true;
+    c = g - base;
+    return g >= 0 && g < n;
+}
+
 template <typename R, int TY>
 __global__ void __launch_bounds__(32 * TY)
 k_transfer(const KP<R> P, const R* __restrict__ phio, const R* __restrict__ phin, const R* __restrict__ Uin,
            R* __restrict__ Uout, const R* __restrict__ Tin, R* __restrict__ Tout, R* __restrict__ accU,
            R* __restrict__ accT, int acc_reset_U, int acc_reset_T, unsigned long long* __restrict__ smax) {
-    constexpr int TX = 32, HX = TX + 2, HY = TY + 2, GX = TX + 4, GY = TY + 4, NT = 32 * TY;
+    constexpr int TX = 32, HX = TX + 2, HY = TY + 2, GX = 36, GY = TY + 4, NT = 32 * TY, NR = 2 * HX + 2 * TY;
     __shared__ R spn[GY][GX];
     __shared__ R sJx[HY][HX], sJy[HY][HX];
     __shared__ double sred[NT / 32];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    for (int p = tid; p < GX * GY; p += NT) {
-        const int lx = p % GX, ly = p / GX;
-        const int gx = scalar_map(x0 - 2 + lx, P.nx, P.bsx), gy = scalar_map(y0 - 2 + ly, P.ny, P.bsy);
-        spn[ly][lx] = phin[(size_t)gy * P.pitch + gx];
+    // item A: own halo position; item B: a ring position
+    int alx = tx + 1, aly = ty + 1, blx = 0, bly = 0;
+    if (tid < NR) ring_pos<TY>(tid, blx, bly);
+    int ax = x0 - 1 + alx, ay = y0 - 1 + aly, bx = x0 - 1 + blx, by = y0 - 1 + bly;
+    int acx = alx + 1, acy = aly + 1, bcx = blx + 1, bcy = bly + 1;
+    bool afx, afy, bfx = false, bfy = false;
+    const bool va = j_source(ax, P.nx, P.bsx, x0 - 2, acx, afx) & j_source(ay, P.ny, P.bsy, y0 - 2, acy, afy) &&
+                    acx >= 1 && acx <= GX - 2 && acy >= 1 && acy <= GY - 2;
+    bool vb = false;
+    if (tid < NR)
+        vb = j_source(bx, P.nx, P.bsx, x0 - 2, bcx, bfx) & j_source(by, P.ny, P.bsy, y0 - 2, bcy, bfy) &&
+             bcx >= 1 && bcx <= GX - 2 && bcy >= 1 && bcy <= GY - 2;
+    const size_t na = (size_t)ay * P.pitch + ax, nb = (size_t)by * P.pitch + bx;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool own = gx < P.nx && gy < P.ny;
+    const size_t node = (size_t)gy * P.pitch + gx;
+    R poa = R(0), Usa = R(0), pob = R(0), Usb = R(0), Town = R(0), accUo = R(0), accTo = R(0);
+    if (va) { poa = phio[na]; if (P.has_U) Usa = Uin[na]; }
+    if (vb) { pob = phio[nb]; if (P.has_U) Usb = Uin[nb]; }
+    if (own) {
+        if (P.has_T) Town = Tin[node];
+        if (P.accumulated) {
+            if (P.has_U && !acc_reset_U) accUo = accU[node];
+            if (P.has_T && !acc_reset_T) accTo = accT[node];
+        }
     }
+    load_phi_ring2<R, TY>(P, phin, spn, x0, y0, tid);
     __syncthreads();
     const R pre = P.at_pre;
-    for (int p = tid; p < HX * HY; p += NT) {
-        const int lx = p % HX, ly = p / HX;
-        int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-        // the node whose J fills this slot, its shared-tile position, and the
-        // wall-normal sign flips of a mirrored ghost
-        int cx = lx + 1, cy = ly + 1;
-        bool fx = false, fy = false;
-        if (outside(gx, P.nx)) {
-            if (P.bsx == BC_PERIODIC) gx = wrap_idx(gx, P.nx);
-            else { gx = (gx < 0) ? (-1 - gx) : (2 * P.nx - 1 - gx); fx = true; cx = gx - (x0 - 2); }
+    auto jfill = [&](bool v, int lx, int ly, int cx, int cy, bool fx, bool fy, R po, R Us) {
+        R jx = R(0), jy = R(0);
+        if (v) {
+            R gxv, gyv;
+            iso_grad<R, GX>(spn, cx, cy, gxv, gyv);
+            const R g2 = gxv * gxv + gyv * gyv;
+            R nxv = R(0), nyv = R(0);
+            if (g2 > R(1e-12)) {
+                const R ig = R(1) / sqrt(g2);
+                nxv = -gxv * ig;
+                nyv = -gyv * ig;
+            }
+            const R a = pre * (R(1) + (R(1) - P.k) * Us) * (spn[cy][cx] - po);     // Eqs. 36-37
+            jx = fx ? -a * nxv : a * nxv;
+            jy = fy ? -a * nyv : a * nyv;
         }
-        if (outside(gy, P.ny)) {
-            if (P.bsy == BC_PERIODIC) gy = wrap_idx(gy, P.ny);
-            else { gy = (gy < 0) ? (-1 - gy) : (2 * P.ny - 1 - gy); fy = true; cy = gy - (y0 - 2); }
-        }
-        if (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny || cx < 1 || cx > GX - 2 || cy < 1 || cy > GY - 2) {
-            sJx[ly][lx] = R(0);   // only reached by slots no valid node reads
-            sJy[ly][lx] = R(0);
-            continue;
-        }
-        const size_t node = (size_t)gy * P.pitch + gx;
-        R gxv, gyv;
-        iso_grad<R, GX>(spn, cx, cy, gxv, gyv);
-        const R g2 = gxv * gxv + gyv * gyv;
-        R nxv = R(0), nyv = R(0);
-        if (g2 > R(1e-12)) {
-            const R ig = R(1) / sqrt(g2);
-            nxv = -gxv * ig;
-            nyv = -gyv * ig;
-        }
-        const R dphi = spn[cy][cx] - phio[node];                                // Eq. 36
-        const R Us = P.has_U ? Uin[node] : R(0);
-        const R a = pre * (R(1) + (R(1) - P.k) * Us) * dphi;                    // Eq. 37
-        sJx[ly][lx] = fx ? -a * nxv : a * nxv;
-        sJy[ly][lx] = fy ? -a * nyv : a * nyv;
-    }
+        sJx[ly][lx] = jx;
+        sJy[ly][lx] = jy;
+    };
+    jfill(va, alx, aly, acx, acy, afx, afy, poa, Usa);
+    if (tid < NR) jfill(vb, blx, bly, bcx, bcy, bfx, bfy, pob, Usb);
     __syncthreads();
-
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int gx = x0 + tx, gy = y0 + ty;
     double mydu = 0.0;
-    if (gx < P.nx && gy < P.ny) {
-        const size_t node = (size_t)gy * P.pitch + gx;
+    if (own) {
         const int hx = tx + 1, hy = ty + 1;
         const R div = (sJx[hy][hx + 1] - sJx[hy][hx - 1] + sJy[hy + 1][hx] - sJy[hy - 1][hx]) * (R(1) / R(3)) +
                       ((sJx[hy + 1][hx + 1] + sJy[hy + 1][hx + 1]) + (sJy[hy + 1][hx - 1] - sJx[hy + 1][hx - 1]) -
                        (sJx[hy - 1][hx - 1] + sJy[hy - 1][hx - 1]) + (sJx[hy - 1][hx + 1] - sJy[hy - 1][hx + 1])) *
                           (R(1) / R(12));
         const R pn = spn[ty + 2][tx + 2];
-        const R dphi = pn - phio[node];
+        const R dphi = pn - poa;                      // item A of an own node is the node itself
         if (P.has_U) {
-            const R Us = Uin[node];
+            const R Us = Usa;
             const R dU = ((R(1) + (R(1) - P.k) * Us) * dphi - R(2) * div) /
                          ((R(1) + P.k) - (R(1) - P.k) * pn);                       // Eq. 38
             mydu = fabs((double)dU);
             if (!P.accumulated) Uout[node] = Us + dU;                               // Eq. 39
-            else accU[node] = (acc_reset_U ? R(0) : accU[node]) + dU;
+            else accU[node] = accUo + dU;
         }
         if (P.has_T) {
             const R rc = R(0.5) * (R(1) + pn) * P.cS + R(0.5) * (R(1) - pn) * P.cL;
             const R dT = P.rhoL_Lh * dphi / (R(2) * rc);                            // Eq. 38
-            if (!P.accumulated) Tout[node] = Tin[node] + dT;
-            else accT[node] = (acc_reset_T ? R(0) : accT[node]) + dT;
+            if (!P.accumulated) Tout[node] = Town + dT;
+            else accT[node] = accTo + dT;
         }
     }
     // block maximum of |Delta U_pc| -> S_phi (and J_U when instantaneous)
@@ -357,57 +423,72 @@ k_transfer(const KP<R> P, const R* __restrict__ phio, const R* __restrict__ phin
 // Concentration / temperature update (Eqs. 7-8, 10-12 tr parts; 14, 19-20,
 // 23-25, 40, 18).  FIELD 0 = U, 1 = T.
 // ---------------------------------------------------------------------------
+template <typename R, int TY, int FIELD>
+__device__ __forceinline__ void scalar_collide(const KP<R>& P, const R (*sphi)[36], R (*sp)[TY + 2][34], int lx,
+                                               int ly, R chi, R jx, R jy, R vx, R vy) {
+    const R dt = FIELD == 0 ? P.dtU : P.dtT;
+    const R ph = sphi[ly + 1][lx + 1];
+    R D, coef;
+    if (FIELD == 0) {
+        const R den = (R(1) + P.k) - (R(1) - P.k) * ph;
+        D = ((R(1) + ph) * P.DS + (R(1) - ph) * P.DL) / den;                      // Eq. 7
+        coef = -(R(1) - P.k) * D / den;                                           // Eq. 8, tr
+    } else {
+        const R rc = R(0.5) * (R(1) + ph) * P.cS + R(0.5) * (R(1) - ph) * P.cL;
+        D = (R(0.5) * (R(1) + ph) * P.kS + R(0.5) * (R(1) - ph) * P.kL) / rc;     // Eq. 11
+        coef = (P.cS - P.cL) / (R(2) * rc) * D;                                   // Eq. 12, tr
+    }
+    const R s = R(1) / (R(3) * dt * D + R(0.5));                                  // Eq. 24
+    const R bx = dt * chi * vx, by = dt * chi * vy;                                // Eqs. 19-20
+    const R jnx = jx - bx, jny = jy - by;
+    R gpx, gpy;
+    iso_grad<R, 36>(sphi, lx + 1, ly + 1, gpx, gpy);
+    const R Q = coef * (R(-3) * s) * (jnx * gpx + jny * gpy);                       // Eq. 40 in Eq. 8 / 12
+    const R k6 = (R(1) - s) * (R(1) / R(6));
+    put_scalar_post<R, TY + 2, 34>(sp, ly, lx, chi + dt * Q, bx, by, k6 * jnx, k6 * jny);
+}
+
 template <typename R, typename ST, bool DEV, int TY, int FIELD>
 __global__ void __launch_bounds__(32 * TY)
 k_scalar(const KP<R> P, const ST* __restrict__ fin, ST* __restrict__ fout, const R* __restrict__ mac_in,
          R* __restrict__ mac_out, const R* __restrict__ acc, const R* __restrict__ phi, const R* __restrict__ ux,
          const R* __restrict__ uy, unsigned long long* __restrict__ smax) {
-    constexpr int TX = 32, HX = TX + 2, HY = TY + 2, GX = TX + 4, GY = TY + 4, NT = 32 * TY;
-    __shared__ R sphi[GY][GX];
+    constexpr int TX = 32, HX = TX + 2, HY = TY + 2, GY = TY + 4, NT = 32 * TY, NR = 2 * HX + 2 * TY;
+    __shared__ R sphi[GY][36];
     __shared__ R spost[9][HY][HX];
     __shared__ double sred[NT / 32];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    const R dt = FIELD == 0 ? P.dtU : P.dtT;
-    for (int p = tid; p < GX * GY; p += NT) {
-        const int lx = p % GX, ly = p / GX;
-        const int gx = scalar_map(x0 - 2 + lx, P.nx, P.bsx), gy = scalar_map(y0 - 2 + ly, P.ny, P.bsy);
-        sphi[ly][lx] = phi[(size_t)gy * P.pitch + gx];
+    int ax = x0 + tx, ay = y0 + ty;
+    const bool va = resolve_xy(ax, ay, P.nx, P.ny, P.bsx, P.bsy);
+    int blx = 0, bly = 0, bx = 0, by = 0;
+    bool vb = false;
+    if (tid < NR) {
+        ring_pos<TY>(tid, blx, bly);
+        bx = x0 - 1 + blx;
+        by = y0 - 1 + bly;
+        vb = resolve_xy(bx, by, P.nx, P.ny, P.bsx, P.bsy);
     }
-    __syncthreads();
-    for (int p = tid; p < HX * HY; p += NT) {
-        const int lx = p % HX, ly = p / HX;
-        int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-        if (!resolve(gx, P.nx, P.bsx) || !resolve(gy, P.ny, P.bsy)) continue;
-        const size_t node = (size_t)gy * P.pitch + gx;
-        R chi = mac_in[node];
-        if (P.accumulated) chi += acc[node];                     // coarse-step injection (Sec. 4.4 ablation)
-        const R ph = sphi[ly + 1][lx + 1];
-        R D, coef;
-        if (FIELD == 0) {
-            const R den = (R(1) + P.k) - (R(1) - P.k) * ph;
-            D = ((R(1) + ph) * P.DS + (R(1) - ph) * P.DL) / den;                  // Eq. 7
-            coef = -(R(1) - P.k) * D / den;                                       // Eq. 8, tr
-        } else {
-            const R rc = R(0.5) * (R(1) + ph) * P.cS + R(0.5) * (R(1) - ph) * P.cL;
-            D = (R(0.5) * (R(1) + ph) * P.kS + R(0.5) * (R(1) - ph) * P.kL) / rc; // Eq. 11
-            coef = (P.cS - P.cL) / (R(2) * rc) * D;                               // Eq. 12, tr
-        }
-        const R s = R(1) / (R(3) * dt * D + R(0.5));                              // Eq. 24
-        R vx = R(0), vy = R(0);
-        if (P.has_flow) { vx = ux[node]; vy = uy[node]; }
-        R jx, jy;
-        first_moment<R, ST>(fin, node, P.plane, jx, jy);
-        const R bx = dt * chi * vx, by = dt * chi * vy;                            // Eqs. 19-20
-        const R jnx = jx - bx, jny = jy - by;
-        R gpx, gpy;
-        iso_grad<R, GX>(sphi, lx + 1, ly + 1, gpx, gpy);
-        const R Q = coef * (R(-3) * s) * (jnx * gpx + jny * gpy);                   // Eq. 40 in Eq. 8 / 12
-        const R k6 = (R(1) - s) * (R(1) / R(6));
-        put_scalar_post<R, HY, HX>(spost, ly, lx, chi + dt * Q, bx, by, k6 * jnx, k6 * jny);
+    const size_t na = (size_t)ay * P.pitch + ax, nb = (size_t)by * P.pitch + bx;
+    R fa[9], fb[9];
+    R ca = R(0), cb = R(0), uxa = R(0), uya = R(0), uxb = R(0), uyb = R(0), acca = R(0);
+    if (va) {
+        load8<R, ST>(fin, na, P.plane, fa);
+        ca = mac_in[na];
+        if (P.accumulated) { acca = acc[na]; ca += acca; }   // coarse-step injection (Sec. 4.4 ablation)
+        if (P.has_flow) { uxa = ux[na]; uya = uy[na]; }
     }
+    if (vb) {
+        load8<R, ST>(fin, nb, P.plane, fb);
+        cb = mac_in[nb];
+        if (P.accumulated) cb += acc[nb];
+        if (P.has_flow) { uxb = ux[nb]; uyb = uy[nb]; }
+    }
+    load_phi_ring2<R, TY>(P, phi, sphi, x0, y0, tid);
     __syncthreads();
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (va) scalar_collide<R, TY, FIELD>(P, sphi, spost, tx + 1, ty + 1, ca, mom_x(fa), mom_y(fa), uxa, uya);
+    if (vb) scalar_collide<R, TY, FIELD>(P, sphi, spost, blx, bly, cb, mom_x(fb), mom_y(fb), uxb, uyb);
+    __syncthreads();
     const int gx = x0 + tx, gy = y0 + ty;
     double myj = 0.0;
     if (gx < P.nx && gy < P.ny) {
@@ -424,7 +505,7 @@ k_scalar(const KP<R> P, const ST* __restrict__ fin, ST* __restrict__ fout, const
 #pragma unroll
         for (int i = 1; i < 9; ++i)
             fout[(size_t)(i - 1) * P.plane + node] = Cvt<ST>::st(DEV ? fn[i] - wq<R>(i) * sum : fn[i]);
-        if (FIELD == 0 && P.accumulated) myj = fabs((double)acc[node]);
+        if (FIELD == 0 && P.accumulated) myj = fabs((double)acca);
     }
     if (FIELD == 0 && P.accumulated) {
 #pragma unroll
@@ -452,96 +533,106 @@ __device__ __forceinline__ void feq_flow(R rho, R ux, R uy, R c, R* f) {        
     }
 }
 
+// MRT collision of Eq. 14 with S of Eq. 31 and Guo forcing (Eq. 30); f holds
+// populations 1..8 (decoded) on entry, rho and u the macros written with them
+template <typename R, int TY>
+__device__ __forceinline__ void flow_collide(const KP<R>& P, R (*sp)[TY + 2][34], int lx, int ly, R* f, R rho) {
+    const R c = P.cF, dt = P.dtF;
+    R s8 = R(0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) s8 += f[i];
+    f[0] = rho - s8;
+    const R jx = mom_x(f), jy = mom_y(f);
+    const R ux = (c * jx + R(0.5) * dt * P.Fbx) / rho, uy = (c * jy + R(0.5) * dt * P.Fby) / rho; // Eq. 27
+    const R ic = R(1) / c, ic2 = ic * ic, u2 = (ux * ux + uy * uy) * ic2;
+    // non-conserved moments of f (rows 1, 2, 4, 6, 7, 8 of M, Eq. 16)
+    const R sa = f[1] + f[2] + f[3] + f[4], sd = f[5] + f[6] + f[7] + f[8];
+    const R m1 = R(-4) * f[0] - sa + R(2) * sd;
+    const R m2 = R(4) * f[0] - R(2) * sa + sd;
+    const R m4 = R(-2) * f[1] + R(2) * f[3] + f[5] - f[6] - f[7] + f[8];
+    const R m6 = R(-2) * f[2] + R(2) * f[4] + f[5] + f[6] - f[7] - f[8];
+    const R m7 = f[1] - f[2] + f[3] - f[4];
+    const R m8 = f[5] - f[6] + f[7] - f[8];
+    // Eq. 29 equilibria, Eq. 30 Guo moments, Eq. 31 rates; dm_k scaled by the
+    // diagonal of M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+    const R fu = (P.Fbx * ux + P.Fby * uy) * ic2;
+    const R G1 = R(6) * fu, G3 = P.Fbx * ic, G5 = P.Fby * ic;
+    const R G7 = R(2) * (P.Fbx * ux - P.Fby * uy) * ic2, G8 = (P.Fby * ux + P.Fbx * uy) * ic2;
+    const R d1 = (-P.se * (m1 - rho * (R(-2) + R(3) * u2)) + (R(1) - R(0.5) * P.se) * G1) * (R(1) / R(36));
+    const R d2 = (-P.seps * (m2 - rho * (R(1) - R(3) * u2)) - (R(1) - R(0.5) * P.seps) * G1) * (R(1) / R(36));
+    const R d3 = G3 * (R(1) / R(6));
+    const R d4 = (-P.sq * (m4 + rho * ux * ic) - (R(1) - R(0.5) * P.sq) * G3) * (R(1) / R(12));
+    const R d5 = G5 * (R(1) / R(6));
+    const R d6 = (-P.sq * (m6 + rho * uy * ic) - (R(1) - R(0.5) * P.sq) * G5) * (R(1) / R(12));
+    const R d7 = (-P.snu * (m7 - rho * (ux * ux - uy * uy) * ic2) + (R(1) - R(0.5) * P.snu) * G7) * (R(1) / R(4));
+    const R d8 = (-P.snu * (m8 - rho * ux * uy * ic2) + (R(1) - R(0.5) * P.snu) * G8) * (R(1) / R(4));
+    const R axis = -d1 - R(2) * d2, diag = R(2) * d1 + d2;
+    sp[0][ly][lx] = f[0] - R(4) * d1 + R(4) * d2;
+    sp[1][ly][lx] = f[1] + axis + d3 - R(2) * d4 + d7;
+    sp[2][ly][lx] = f[2] + axis + d5 - R(2) * d6 - d7;
+    sp[3][ly][lx] = f[3] + axis - d3 + R(2) * d4 + d7;
+    sp[4][ly][lx] = f[4] + axis - d5 + R(2) * d6 - d7;
+    sp[5][ly][lx] = f[5] + diag + d3 + d4 + d5 + d6 + d8;
+    sp[6][ly][lx] = f[6] + diag - d3 - d4 + d5 + d6 - d8;
+    sp[7][ly][lx] = f[7] + diag - d3 - d4 - d5 - d6 + d8;
+    sp[8][ly][lx] = f[8] + diag + d3 + d4 - d5 - d6 - d8;
+}
+
 template <typename R, typename ST, bool DEV, int TY>
 __global__ void __launch_bounds__(32 * TY)
 k_flow(const KP<R> P, const ST* __restrict__ fin, ST* __restrict__ fout, const R* __restrict__ phi,
        const R* __restrict__ ux_in, const R* __restrict__ uy_in, const R* __restrict__ rho_in,
        R* __restrict__ ux_out, R* __restrict__ uy_out, R* __restrict__ rho_out) {
-    constexpr int TX = 32, HX = TX + 2, HY = TY + 2, NT = 32 * TY;
+    constexpr int TX = 32, HX = TX + 2, HY = TY + 2, NR = 2 * HX + 2 * TY;
     __shared__ R sfl[HY][HX];
     __shared__ R spost[9][HY][HX];
-    __shared__ R srho[HY][HX], sux[HY][HX], suy[HY][HX];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int tid = threadIdx.y * TX + threadIdx.x;
     const R c = P.cF, dt = P.dtF;
-    // pass 1: the halo's liquid fractions and the macros written together with
-    // the input populations (they decode population 0 and the deviations)
-    for (int p = tid; p < HX * HY; p += NT) {
-        const int lx = p % HX, ly = p / HX;
-        int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-        if (!resolve(gx, P.nx, P.bfx) || !resolve(gy, P.ny, P.bfy)) continue;
-        const size_t node = (size_t)gy * P.pitch + gx;
-        sfl[ly][lx] = R(0.5) * (R(1) - phi[node]);                                // f_L = (1 - phi)/2
-        srho[ly][lx] = rho_in[node];
-        sux[ly][lx] = ux_in[node];
-        suy[ly][lx] = uy_in[node];
+    int ax = x0 + tx, ay = y0 + ty;
+    const bool va = resolve_xy(ax, ay, P.nx, P.ny, P.bfx, P.bfy);
+    int blx = 0, bly = 0, bx = 0, by = 0;
+    bool vb = false;
+    if (tid < NR) {
+        ring_pos<TY>(tid, blx, bly);
+        bx = x0 - 1 + blx;
+        by = y0 - 1 + bly;
+        vb = resolve_xy(bx, by, P.nx, P.ny, P.bfx, P.bfy);
+    }
+    const size_t na = (size_t)ay * P.pitch + ax, nb = (size_t)by * P.pitch + bx;
+    R fa[9], fb[9];
+    R ra = R(1), rb = R(1), uxa = R(0), uya = R(0), uxb = R(0), uyb = R(0), pa = R(0), pb = R(0);
+    if (va) {
+        load8<R, ST>(fin, na, P.plane, fa);
+        ra = rho_in[na]; uxa = ux_in[na]; uya = uy_in[na]; pa = phi[na];
+    }
+    if (vb) {
+        load8<R, ST>(fin, nb, P.plane, fb);
+        rb = rho_in[nb]; uxb = ux_in[nb]; uyb = uy_in[nb]; pb = phi[nb];
+    }
+    if (DEV) {     // h_i = f_i - f_eq_i(rho, u) of the writer's macros
+        R ref[9];
+        if (va) { feq_flow<R>(ra, uxa, uya, c, ref);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) fa[i] += ref[i]; }
+        if (vb) { feq_flow<R>(rb, uxb, uyb, c, ref);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) fb[i] += ref[i]; }
+    }
+    if (va) {
+        sfl[ty + 1][tx + 1] = R(0.5) * (R(1) - pa);                                  // f_L = (1 - phi)/2
+        flow_collide<R, TY>(P, spost, tx + 1, ty + 1, fa, ra);
+    }
+    if (vb) {
+        sfl[bly][blx] = R(0.5) * (R(1) - pb);
+        flow_collide<R, TY>(P, spost, blx, bly, fb, rb);
     }
     __syncthreads();
-    const R Mi0 = R(1) / R(9), Mi1 = R(1) / R(36), Mi3 = R(1) / R(6), Mi4 = R(1) / R(12), Mi7 = R(1) / R(4);
-    for (int p = tid; p < HX * HY; p += NT) {
-        const int lx = p % HX, ly = p / HX;
-        int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-        if (!resolve(gx, P.nx, P.bfx) || !resolve(gy, P.ny, P.bfy)) continue;
-        const size_t node = (size_t)gy * P.pitch + gx;
-        const R rho = srho[ly][lx];
-        R f[9];
-        if (DEV) {
-            R ref[9];
-            feq_flow<R>(rho, sux[ly][lx], suy[ly][lx], c, ref);
-            R s = R(0);
-#pragma unroll
-            for (int i = 1; i < 9; ++i) { f[i] = ref[i] + (R)Cvt<ST>::ld(fin[(size_t)(i - 1) * P.plane + node]); s += f[i]; }
-            f[0] = rho - s;
-        } else {
-            R s = R(0);
-#pragma unroll
-            for (int i = 1; i < 9; ++i) { f[i] = (R)Cvt<ST>::ld(fin[(size_t)(i - 1) * P.plane + node]); s += f[i]; }
-            f[0] = rho - s;
-        }
-        const R jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
-        const R jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
-        const R ux = (c * jx + R(0.5) * dt * P.Fbx) / rho, uy = (c * jy + R(0.5) * dt * P.Fby) / rho; // Eq. 27
-        const R ic = R(1) / c, ic2 = ic * ic, u2 = (ux * ux + uy * uy) * ic2;
-        // non-conserved moments of f (rows 1, 2, 4, 6, 7, 8 of M, Eq. 16)
-        const R sa = f[1] + f[2] + f[3] + f[4], sd = f[5] + f[6] + f[7] + f[8];
-        const R m1 = R(-4) * f[0] - sa + R(2) * sd;
-        const R m2 = R(4) * f[0] - R(2) * sa + sd;
-        const R m4 = R(-2) * f[1] + R(2) * f[3] + f[5] - f[6] - f[7] + f[8];
-        const R m6 = R(-2) * f[2] + R(2) * f[4] + f[5] + f[6] - f[7] - f[8];
-        const R m7 = f[1] - f[2] + f[3] - f[4];
-        const R m8 = f[5] - f[6] + f[7] - f[8];
-        // Eq. 29 equilibria, Eq. 30 Guo moments, Eq. 31 rates
-        const R fu = (P.Fbx * ux + P.Fby * uy) * ic2;
-        const R G1 = R(6) * fu, G3 = P.Fbx * ic, G5 = P.Fby * ic;
-        const R G7 = R(2) * (P.Fbx * ux - P.Fby * uy) * ic2, G8 = (P.Fby * ux + P.Fbx * uy) * ic2;
-        const R d1 = (-P.se * (m1 - rho * (R(-2) + R(3) * u2)) + (R(1) - R(0.5) * P.se) * G1) * Mi1;
-        const R d2 = (-P.seps * (m2 - rho * (R(1) - R(3) * u2)) - (R(1) - R(0.5) * P.seps) * G1) * Mi1;
-        const R d3 = G3 * Mi3;
-        const R d4 = (-P.sq * (m4 + rho * ux * ic) - (R(1) - R(0.5) * P.sq) * G3) * Mi4;
-        const R d5 = G5 * Mi3;
-        const R d6 = (-P.sq * (m6 + rho * uy * ic) - (R(1) - R(0.5) * P.sq) * G5) * Mi4;
-        const R d7 = (-P.snu * (m7 - rho * (ux * ux - uy * uy) * ic2) + (R(1) - R(0.5) * P.snu) * G7) * Mi7;
-        const R d8 = (-P.snu * (m8 - rho * ux * uy * ic2) + (R(1) - R(0.5) * P.snu) * G8) * Mi7;
-        (void)Mi0;
-        // f* = f + M^-1 dm, with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
-        const R axis = -d1 - R(2) * d2, diag = R(2) * d1 + d2;
-        spost[0][ly][lx] = f[0] - R(4) * d1 + R(4) * d2;
-        spost[1][ly][lx] = f[1] + axis + d3 - R(2) * d4 + d7;
-        spost[2][ly][lx] = f[2] + axis + d5 - R(2) * d6 - d7;
-        spost[3][ly][lx] = f[3] + axis - d3 + R(2) * d4 + d7;
-        spost[4][ly][lx] = f[4] + axis - d5 + R(2) * d6 - d7;
-        spost[5][ly][lx] = f[5] + diag + d3 + d4 + d5 + d6 + d8;
-        spost[6][ly][lx] = f[6] + diag - d3 - d4 + d5 + d6 - d8;
-        spost[7][ly][lx] = f[7] + diag - d3 - d4 - d5 - d6 + d8;
-        spost[8][ly][lx] = f[8] + diag + d3 + d4 - d5 - d6 - d8;
-    }
-    __syncthreads();
-    const int tx = threadIdx.x, ty = threadIdx.y;
     const int gx = x0 + tx, gy = y0 + ty;
     if (gx >= P.nx || gy >= P.ny) return;
     const size_t node = (size_t)gy * P.pitch + gx;
     // streamed value of direction i into the node at shared position (hx, hy),
-    // global (nx_, ny_), with the weighted partial bounce-back of Eq. 33
+    // global (gxn, gyn), with the weighted partial bounce-back of Eq. 33
     auto pulled = [&](int i, int hx, int hy, int gxn, int gyn) -> R {
         const int sx = gxn - c_ex[i], sy = gyn - c_ey[i];
         const int o = c_opp[i];
@@ -564,11 +655,10 @@ k_flow(const KP<R> P, const ST* __restrict__ fin, ST* __restrict__ fout, const R
 #pragma unroll
         for (int i = 0; i < 9; ++i) fn[i] = pulled(i, hx, hy, gx, gy);
     }
-    R rho = R(0), jx, jy;
+    R rho = R(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) rho += fn[i];
-    jx = fn[1] - fn[3] + fn[5] - fn[6] - fn[7] + fn[8];
-    jy = fn[2] - fn[4] + fn[5] + fn[6] - fn[7] - fn[8];
+    const R jx = mom_x(fn), jy = mom_y(fn);
     const R ux = (c * jx + R(0.5) * dt * P.Fbx) / rho, uy = (c * jy + R(0.5) * dt * P.Fby) / rho;
     rho_out[node] = rho;
     ux_out[node] = ux;
@@ -583,7 +673,6 @@ k_flow(const KP<R> P, const ST* __restrict__ fin, ST* __restrict__ fout, const R
         for (int i = 1; i < 9; ++i) fout[(size_t)(i - 1) * P.plane + node] = Cvt<ST>::st(fn[i]);
     }
 }
-
 // ---------------------------------------------------------------------------
 // Initial distributions f = f_eq of the macroscopic fields (Eqs. 19, 21, 28)
 // ---------------------------------------------------------------------------

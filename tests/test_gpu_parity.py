@@ -132,3 +132,32 @@ def test_init_seed_matches_generator():
     sim.init_seed([{"kind": "planar", "y": 40.0, "amp": 0.01}], U0=0.0, rng_seed=3)
     assert np.abs(sim.field("phi") - wd.fields["phi"]).max() < 1e-14
     sim.close()
+
+
+def test_tile_variants_bitwise_identical():
+    """Every node's update is the same arithmetic whichever tile shape holds
+    it, so autotuned tile shapes cannot change the result."""
+    import paper_2609_25670_b300 as lbm
+    wl = W.thermosolutal_convection(n=96, R=8.0)
+    outs = []
+    for tune in (False, True):
+        sim = lbm.Simulation(wl.params, precision="f32")
+        sim.init_fields(wl.fields)
+        sim.advance(10)
+        if tune:
+            ch = sim.autotune(reps=2)
+            assert set(ch[k] for k in ("phase", "transfer", "scalar_U", "scalar_T", "flow")) <= {4, 8, 16}
+        sim.advance(30)
+        outs.append({k: sim.field(k) for k in active(wl.params)})
+        sim.close()
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+@pytest.mark.parametrize("prec,tol", [("f16dev", 5e-3), ("bf16dev", 4e-2)])
+def test_deviation_storage_thermosolutal(prec, tol):
+    """16-bit storage of the deviations f_i - ref_i with FP32 arithmetic
+    against the FP64 oracle after 1000 base steps (bounds in the design doc)."""
+    wl = W.thermosolutal_convection(n=128, R=8.0)
+    g, o, err = _check(wl.params, wl.fields, 1000, tol, precision=prec)
+    assert abs(g["diag"]["M_C"] - o["diag"]["M_C"]) / o["diag"]["M_C"] < 1e-5
