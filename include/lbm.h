@@ -231,6 +231,35 @@ lbm_status lbm_launch_counts(lbm_handle h, int64_t* counts);
 /* Bytes of device memory held by h. */
 lbm_status lbm_device_bytes(lbm_handle h, size_t* bytes);
 
+/* Diagnostics of caller-held fields, allocating nothing.  The paper has no
+ * counterpart: this is a service for callers that cannot call cudaMalloc --
+ * e.g. a monitoring hook inside another framework's step loop, where an
+ * allocation would synchronise the device and break that framework's stream
+ * ordering, or a process whose device memory is owned by a caching allocator
+ * under a fixed budget.  It reduces the same quantities as lbm_diagnostics
+ * (M_C, H_total, tips, nonfinite; S_phi = J_U = 0 and base_step = 0, since it
+ * keeps no history) over fields the caller passes, without a handle.
+ *   p:      parameters of the fields (nx, ny, fields bits, k, heat
+ *           capacities, rhoL_Lh, tip_cx / tip_cy are used; validated as in
+ *           lbm_create); p->precision selects the element type: double for
+ *           LBM_PREC_F64, float otherwise.
+ *   phi, U, T, ux, uy: device pointers, dense ny x nx row-major in that type
+ *           (as lbm_fields writes them with as_f64 = 0); U / T / ux, uy may be
+ *           NULL when that field is off.
+ *   cuda_stream: stream the reduction runs on (NULL = legacy default);
+ *           the call synchronises it.   out: host struct, filled on return.
+ * Scratch: a fixed file-scope device array of about 28 KB (partial sums of at
+ * most 1184 blocks plus result slots), held by every GPU that loads the
+ * library until the process exits.  Lattices of more than 2^31 - 1 nodes are
+ * rejected with LBM_E_INVALID_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Calls share the array and
+ * it keeps the last call's contents: calls that overlap on the GPU race.
+ * Errors: INVALID_ARG, UNSTABLE_PARAMS (as lbm_create), CUDA, NONFINITE
+ * (out is filled).  Errors are reported by lbm_last_error(NULL). */
+lbm_status lbm_diagnostics_noalloc(const lbm_params* p, const void* phi, const void* U, const void* T,
+                                   const void* ux, const void* uy, void* cuda_stream, lbm_diag* out);
+
 #ifdef __cplusplus
 }
 #endif

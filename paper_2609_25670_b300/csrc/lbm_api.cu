@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -862,3 +863,109 @@ lbm_status lbm_device_bytes(lbm_handle h, size_t* bytes) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Diagnostics without allocation.
+//
+// Some callers cannot call cudaMalloc: a monitoring hook that runs inside
+// another framework's step loop (where cudaMalloc would synchronise the device
+// and break that framework's stream ordering), or a process whose device
+// memory is owned by a caching allocator under a fixed budget.  For them,
+// lbm_diagnostics_noalloc reduces fields they already hold in their own
+// device buffers, with the reduction's scratch in the file-scope array below
+// instead of memory from the allocator or cudaMalloc.
+//
+// The array is a fixed kNoAllocBlocks x 3 partial sums plus 16 result / flag
+// slots (about 28 KB); every GPU that loads this library keeps it until the
+// process exits.  All calls share it and it keeps the last call's contents:
+// the two maxima slots are cleared on every call (the partials and results
+// are fully overwritten), and calls whose work overlaps on the GPU (two
+// streams, or two host threads) race on it.
+// ===========================================================================
+namespace {
+
+constexpr int kNoAllocBlocks = 1184;                 // 8 blocks per SM on 148 SMs
+constexpr int kNoAllocSlots = 3 * kNoAllocBlocks + 16;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocSlots];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array for the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device, with that device current, and then reused.
+cudaError_t noalloc_scratch(double** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = (double*)g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+template <typename R>
+lbm_status noalloc_diag(const SimState& s, const void* phi, const void* U, const void* T, const void* ux,
+                        const void* uy, cudaStream_t st, double* scratch, lbm_diag* out) {
+    lbm_sim* h = nullptr;   // errors are reported through lbm_last_error(NULL)
+    const KP<R> P = make_kp<R>(s);
+    const int blocks = (int)std::min<size_t>(kNoAllocBlocks, (s.nn + 255) / 256);
+    double* part = scratch;
+    unsigned long long* smax = (unsigned long long*)(scratch + 3 * kNoAllocBlocks);
+    double* res = scratch + 3 * kNoAllocBlocks + 2;
+    CK(cudaMemsetAsync(smax, 0, 2 * sizeof(unsigned long long), st));   // the maxima must start at zero
+    k_diag_partial<R><<<blocks, 256, 0, st>>>(P, (const R*)phi, (const R*)U, (const R*)T, (const R*)ux,
+                                              (const R*)uy, part);
+    k_diag_final<R><<<1, 128, 0, st>>>(P, part, blocks, (const R*)phi, s.p.tip_cx, s.p.tip_cy, smax, res);
+    CK(cudaGetLastError());
+    double r[9];
+    CK(cudaMemcpyAsync(r, res, sizeof r, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out->base_step = 0;
+    out->M_C = r[0];
+    out->H_total = r[1];
+    out->nonfinite = r[2] > 0.0 ? 1 : 0;
+    for (int d = 0; d < 4; ++d) out->tip[d] = r[3 + d];
+    out->S_phi = 0.0;
+    out->J_U = 0.0;
+    out->reserved = 0;
+    return out->nonfinite ? fail(nullptr, LBM_E_NONFINITE, "non-finite value in the fields") : LBM_OK;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_diagnostics_noalloc(const lbm_params* p, const void* phi, const void* U, const void* T,
+                                              const void* ux, const void* uy, void* cuda_stream, lbm_diag* out) {
+    lbm_sim* h = nullptr;
+    if (!p || !phi || !out) return fail(nullptr, LBM_E_INVALID_ARG, "params, phi and out must not be NULL");
+    std::string why;
+    lbm_status st = validate(p, why);
+    if (st) return fail(nullptr, st, "%s", why.c_str());
+    if ((int64_t)p->nx * p->ny > (int64_t)INT32_MAX)
+        return fail(nullptr, LBM_E_INVALID_ARG, "lattice of %lld nodes exceeds the 2^31 - 1 node limit",
+                    (long long)p->nx * p->ny);
+    SimState s;   // host-side description only: no device memory
+    s.p = *p;
+    s.nx = p->nx;
+    s.ny = p->ny;
+    s.pitch = p->nx;
+    s.nn = (size_t)p->nx * p->ny;
+    s.has_U = (p->fields & LBM_FIELD_U) != 0;
+    s.has_T = (p->fields & LBM_FIELD_T) != 0;
+    s.frozen_T = (p->fields & LBM_FIELD_FROZEN_T) != 0;
+    s.has_flow = (p->fields & LBM_FIELD_FLOW) != 0;
+    if ((s.has_U && !U) || (s.has_T && !T) || (s.has_flow && (!ux || !uy)))
+        return fail(nullptr, LBM_E_INVALID_ARG, "a field that is switched on was passed as NULL");
+    double* scratch = nullptr;
+    CK(noalloc_scratch(&scratch));
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    return p->precision == LBM_PREC_F64 ? noalloc_diag<double>(s, phi, U, T, ux, uy, stream, scratch, out)
+                                        : noalloc_diag<float>(s, phi, U, T, ux, uy, stream, scratch, out);
+}
