@@ -51,6 +51,64 @@ ALGO_BYTES = {
 }
 
 
+def transport_bytes(tr, u, t, f, has_T=True, has_flow=True):
+    """Algorithmic bytes per node of one fused transport launch (FP32): the
+    transfer reads phi^q, phi^{q+1}, U, T once; each scheduled field reads and
+    writes its 8 populations and writes its macro; a macro whose field does
+    not update in this step is written back with the injection."""
+    b = 4                                       # phi (current) R
+    if tr:
+        b += 4 + 4 + (4 if has_T else 0)        # phi^q, U, T R
+        b += (0 if u else 4) + (0 if (t or not has_T) else 4)   # injected macros carried over
+    else:
+        b += (4 if u else 0) + (4 if t else 0)
+    if (u or t) and has_flow:
+        b += 8                                  # u for the scalar equilibria
+    if u:
+        b += 64 + 4
+    if t:
+        b += 64 + 4
+    if f:
+        b += 64 + 12 + 12 - (8 if (u or t) else 0)   # rho, u R (u shared with the scalars) + W
+    return b
+
+
+def period_bytes(p):
+    """(total transport bytes per node over one schedule period, launches)."""
+    from math import gcd
+    L = 1
+    for N in (p.N_phi, p.N_U, p.N_T, p.N_F):
+        L = L * N // gcd(L, N)
+    tot, n = 0, 0
+    for k in range(2 * L):
+        tr = (k + 1) % p.N_phi == 0
+        u = p.has_U and (k + 1) % p.N_U == 0
+        t = p.has_T and (k + 1) % p.N_T == 0
+        f = p.has_flow and (k + 1) % p.N_F == 0
+        if tr or u or t or f:
+            tot += transport_bytes(tr, u, t, f, p.has_T, p.has_flow)
+            n += 1
+    return tot, n
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu
+# capture, cold cache) of each update kernel on the 512^2 workload, from the
+# capture summarised in profiles/update_kernels_convection512_f32_ncu_full.md.
+# Reported only while the kernel sources hash to TRAFFIC_SOURCE_SHA; after any
+# change to them the roofline's traffic is null until re-measured.
+TRAFFIC_SOURCE_SHA = None
+TRAFFIC_PER_LAUNCH = {}
+
+
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for nm in ("lbm_common.cuh", "lbm_kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2609_25670_b300", "csrc", nm), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def workload(n=None):
     return W.thermosolutal_convection(n=n or N_LATTICE, R=8.0)
 
@@ -184,6 +242,7 @@ def run_ours(args):
     p = wl.params
     nodes = p.nx * p.ny
     sim = lbm.Simulation(p, precision="f32")
+    sim.set_fusion(args.fusion == "on")
     sim.init_fields(wl.fields)
     stream = sim.stream
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -199,9 +258,21 @@ def run_ours(args):
         sim.advance(STEP_BASE)
     tiles = sim.autotune(reps=10)
     sim.advance(STEP_BASE)
-    kinds = ["phase", "transfer", "scalar_U", "scalar_T", "flow"]
+    kinds = ["phase", "transfer", "scalar_U", "scalar_T", "flow", "transport"]
+    tb, tn = period_bytes(p)
+    algo = dict(ALGO_BYTES)
+    algo["transport"] = tb / max(tn, 1)       # mean over the period's transport launches
+    # untimed pre-pass with every kind timed, to find the dominant kernel; the
+    # timed region then times only that kind (fewest event nodes in the graph)
     sim.timing_enable(kinds)
-    sim.advance(STEP_BASE)           # recapture with timing nodes, untimed
+    for _ in range(10):
+        with torch.cuda.stream(stream):
+            flush.fill_(0.0)
+        sim.advance(STEP_BASE)
+    pre = sim.timing_read(reset=True)
+    dom = max(kinds, key=lambda k: pre[k][0])
+    sim.timing_enable([dom])
+    sim.advance(STEP_BASE)           # recapture with the dominant kind's timing nodes, untimed
     sim.timing_read(reset=True)
     launches0 = sim.launch_counts()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -231,16 +302,13 @@ def run_ours(args):
     value = nodes * STEP_BASE * args.steps * world / (ms_max * 1e-3) / 1e6
 
     # roofline of the dominant kernel (largest share of the timed kernel time)
-    dom = max(kinds, key=lambda k: ktimes[k][0])
     dom_ms, dom_n = ktimes[dom]
     avg_s = dom_ms * 1e-3 / max(dom_n, 1)
     peak, peak_kind = measured_peaks()
-    achieved = ALGO_BYTES[dom] * nodes / avg_s / 1e9
+    achieved = algo[dom] * nodes / avg_s / 1e9
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "dram_traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            traffic = json.load(f).get(dom)
+    if args.lattice in (None, N_LATTICE) and TRAFFIC_SOURCE_SHA == kernel_source_sha():
+        traffic = TRAFFIC_PER_LAUNCH.get(dom)
 
     # end to end through the public API with pinned host buffers
     host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in wl.fields.items()}
@@ -264,14 +332,15 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-            "config": {"workload": "thermosolutal free dendrite + forced convection, 512x512, phi/U/T/flow on D2Q9, "
-                                   "N=(1,1,2,2), FP32", "base_steps_per_step": STEP_BASE,
+            "config": {"workload": f"thermosolutal free dendrite + forced convection, {p.nx}x{p.ny}, "
+                                   "phi/U/T/flow on D2Q9, N=(1,1,2,2), FP32", "base_steps_per_step": STEP_BASE,
+                       "fused_transport": args.fusion == "on",
                        "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "algo_bytes_per_node": ALGO_BYTES[dom], "avg_launch_us": avg_s * 1e6,
+                         "algo_bytes_per_node": algo[dom], "avg_launch_us": avg_s * 1e6,
                          "launches_timed": dom_n},
-            "kernel_ms": {k: ktimes[k][0] for k in kinds},
+            "kernel_avg_us_prepass": {k: pre[k][0] / max(pre[k][1], 1) * 1e3 for k in kinds},
             "tiles": {k: tiles[k] for k in kinds},
             "gpu_launches": gpu_launches,
             "wall_s_timed_region": wall,
@@ -288,19 +357,77 @@ def run_ours(args):
     return 0
 
 
+def run_ensemble(args):
+    """Batched ensemble: 64 thermosolutal members of sizes 128..1024 (seeded
+    draws of undercooling, Le, update factors, seed radius), 16-bit deviation
+    storage with FP32 arithmetic; aggregate MLUPS of the batched launches vs
+    the same members advanced one after another.  One step = one common
+    schedule period (8 base steps)."""
+    import torch
+    import paper_2609_25670_b300 as lbm
+    ms = W.ensemble_members(count=args.members, seed=4)
+    prec = args.precision or "f16dev"
+    sim = lbm.Simulation([m.params for m in ms], precision=prec)
+    for i, m in enumerate(ms):
+        sim.init_fields(m.fields, sim=i)
+    period = 8
+    nodes = sum(m.params.nx * m.params.ny for m in ms)
+    res = {}
+    for mode in ("batched", "sequential"):
+        sim.set_batching(mode == "batched")
+        for _ in range(max(args.warmup, 3)):
+            sim.advance(period)
+        if mode == "batched":
+            sim.autotune(reps=3)
+            sim.advance(period)
+        torch.cuda.synchronize()
+        l0 = sim.launch_counts()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(sim.stream):
+            e0.record(sim.stream)
+        for _ in range(args.steps):
+            sim.advance(period)
+        with torch.cuda.stream(sim.stream):
+            e1.record(sim.stream)
+        torch.cuda.synchronize()
+        ms_t = e0.elapsed_time(e1)
+        l1 = sim.launch_counts()
+        res[mode] = {"value": nodes * period * args.steps / (ms_t * 1e-3) / 1e6, "ms_per_step": ms_t / args.steps,
+                     "gpu_launches": int(sum(l1[k] - l0[k] for k in l1))}
+    line = {"metric": METRIC + " (ensemble aggregate)", "value": res["batched"]["value"], "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["batched"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
+            "data": "synthetic (seeded)",
+            "config": {"workload": "batched ensemble of %d thermosolutal members, sizes 128..1024, seed 4" % len(ms),
+                       "nodes": nodes, "base_steps_per_step": period, "l2": "inputs larger than L2"},
+            "gpu_launches": res["batched"]["gpu_launches"], "sequential": res["sequential"],
+            "speedup_vs_sequential": res["batched"]["value"] / res["sequential"]["value"]}
+    print(json.dumps(line), flush=True)
+    sim.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="convection512", choices=["convection512", "ensemble"],
+                    help="convection512: the reported workload; ensemble: batched-ensemble measurement")
+    ap.add_argument("--members", type=int, default=64)
+    ap.add_argument("--precision", default=None)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
+    ap.add_argument("--fusion", default="on", choices=["on", "off"],
+                    help="one fused transport launch per base step (on) or one launch per stage (off)")
     ap.add_argument("--lattice", type=int, default=None,
                     help="lattice size override for profiling runs (the reported workload is 512)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ensemble":
+        return run_ensemble(args)
     return run_ours(args)
 
 

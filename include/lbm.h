@@ -201,14 +201,36 @@ void lbm_destroy(lbm_handle h);
  * period; 0: plain stream launches.  Results are identical. */
 lbm_status lbm_set_graphs(lbm_handle h, int32_t enable);
 
+/* Batched ensemble (default on when n_sims >= 2): while the members are in
+ * lockstep, each base step runs one launch per kernel kind whose blocks cover
+ * the tiles of every member that updates that field in that step (members keep
+ * their own parameters, sizes and update factors); the launches of one common
+ * schedule period are one CUDA graph.  enable = 0 advances the members one
+ * after another with their own graphs (the results are identical).
+ * Errors: INVALID_ARG (fewer than two members, or a common period over 4096
+ * base steps). */
+lbm_status lbm_set_batching(lbm_handle h, int32_t enable);
+
+/* enable = 1 (default): under instantaneous coupling, everything a base step
+ * does after the phase update -- the phase-change transfer (Eqs. 36-39) and
+ * the scheduled U, T and flow updates -- runs as one fused launch per base
+ * step (LBM_K_TRANSPORT) that recomputes the transfer on the halo it needs
+ * instead of storing the injected U, T.  0: one launch per stage.  The two
+ * agree to floating-point contraction rounding.  Recaptures graphs. */
+lbm_status lbm_set_fusion(lbm_handle h, int32_t enable);
+
 /* Kernel kinds for timing and launch counts. */
 enum { LBM_K_PHASE = 0, LBM_K_TRANSFER = 1, LBM_K_SCALAR_U = 2, LBM_K_SCALAR_T = 3,
-       LBM_K_FLOW = 4, LBM_K_DIAG = 5, LBM_K_INIT = 6, LBM_K_COUNT = 7 };
+       LBM_K_FLOW = 4, LBM_K_DIAG = 5, LBM_K_INIT = 6,
+       LBM_K_TRANSPORT = 7,   /* fused transfer + U + T + flow of one base step */
+       LBM_K_COUNT = 8 };
 
 /* Time every launch of the kernel kinds in kind_mask (bit k = kind k) with
- * CUDA events on the library's stream, inside graphs as event-record nodes;
- * lbm_advance then synchronises after each replay to collect the times.
- * kind_mask = 0 turns timing off.  Recaptures graphs. */
+ * CUDA events on the library's stream, inside graphs as event-record nodes
+ * that each replay points at fresh events.  No host wait is added to
+ * lbm_advance: the times are read by lbm_timing_read and lbm_diagnostics
+ * (which synchronise the stream), or when more than 4096 timed launches are
+ * queued.  kind_mask = 0 turns timing off.  Recaptures graphs. */
 lbm_status lbm_timing_enable(lbm_handle h, uint32_t kind_mask);
 
 /* Per kind: accumulated milliseconds and number of timed launches since the
@@ -223,6 +245,14 @@ lbm_status lbm_timing_read(lbm_handle h, double* ms, int64_t* count, int32_t res
  * receives LBM_K_COUNT tile heights of simulation 0.  Recaptures graphs.
  * Errors: STATE (not initialised), CUDA. */
 lbm_status lbm_autotune(lbm_handle h, int32_t reps, int32_t* chosen);
+
+/* Fix the tile height (4, 8 or 16 rows of 32 nodes) of one update kernel kind
+ * (LBM_K_PHASE .. LBM_K_FLOW) for every simulation and for the batched
+ * launches.  Different tile shapes are different compilations of the same
+ * arithmetic and agree to floating-point contraction rounding; a fixed
+ * choice makes runs bitwise reproducible.  Recaptures graphs.
+ * Errors: INVALID_ARG. */
+lbm_status lbm_set_tile(lbm_handle h, int32_t kind, int32_t ty);
 
 /* Number of kernel launches the library has issued (graph replays count
  * their kernel nodes), per kind; counts hold LBM_K_COUNT entries. */

@@ -24,13 +24,14 @@ PRECISIONS = {"f64": 0, "f32": 1, "f16dev": 2, "bf16dev": 3}
 COUPLING_INSTANTANEOUS, COUPLING_ACCUMULATED = 0, 1
 SEED_CIRCLE, SEED_PLANAR, SEED_SINUSOID = 0, 1, 2
 OUT_FIELDS = {"phi": 0, "U": 1, "T": 2, "ux": 3, "uy": 4, "rho": 5, "C": 6, "theta": 7}
-KERNEL_KINDS = ["phase", "transfer", "scalar_U", "scalar_T", "flow", "diag", "init"]
+KERNEL_KINDS = ["phase", "transfer", "scalar_U", "scalar_T", "flow", "diag", "init", "transport"]
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSTABLE_PARAMS", 3: "OOM", 4: "CUDA", 5: "NONFINITE",
           6: "TIMEOUT", 7: "STATE"}
 
 EXPORTED = ["lbm_create", "lbm_init_seed", "lbm_init_fields", "lbm_advance", "lbm_fields",
             "lbm_diagnostics", "lbm_last_error", "lbm_destroy", "lbm_set_graphs", "lbm_timing_enable",
-            "lbm_timing_read", "lbm_launch_counts", "lbm_device_bytes", "lbm_autotune"]
+            "lbm_timing_read", "lbm_launch_counts", "lbm_device_bytes", "lbm_autotune",
+            "lbm_diagnostics_noalloc", "lbm_set_batching", "lbm_set_tile", "lbm_set_fusion"]
 
 
 class LbmError(RuntimeError):
@@ -105,6 +106,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.lbm_launch_counts.argtypes = [vp, C.POINTER(C.c_int64)]
     lib.lbm_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
     lib.lbm_autotune.argtypes = [vp, i32, C.POINTER(C.c_int32)]
+    lib.lbm_set_batching.argtypes = [vp, i32]
+    lib.lbm_set_tile.argtypes = [vp, i32, i32]
+    lib.lbm_set_fusion.argtypes = [vp, i32]
+    lib.lbm_diagnostics_noalloc.argtypes = [C.POINTER(lbm_params)] + [vp] * 6 + [C.POINTER(lbm_diag)]
     for nm in EXPORTED:
         f = getattr(lib, nm)
         if nm not in ("lbm_last_error", "lbm_destroy"):
@@ -238,6 +243,19 @@ class Simulation:
     # ---- stepping
     def advance(self, n_base_steps: int):
         self._ck(self.lib.lbm_advance(self.h, int(n_base_steps)))
+
+    def set_batching(self, enable: bool):
+        """Ensembles: one launch per kernel kind over all members (default) or
+        members one after another."""
+        self._ck(self.lib.lbm_set_batching(self.h, 1 if enable else 0))
+
+    def set_tile(self, kind: str, ty: int):
+        """Fix the tile height of one update kernel kind (4, 8 or 16)."""
+        self._ck(self.lib.lbm_set_tile(self.h, KERNEL_KINDS.index(kind), int(ty)))
+
+    def set_fusion(self, enable: bool):
+        """One fused launch per base step after the phase update (default) or one per stage."""
+        self._ck(self.lib.lbm_set_fusion(self.h, 1 if enable else 0))
 
     def set_graphs(self, enable: bool):
         self._ck(self.lib.lbm_set_graphs(self.h, 1 if enable else 0))

@@ -8,7 +8,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", "lbm_api.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", "lbm_kernels.cuh"), os.path.join(ROOT, "include", "lbm.h")]
+DEPS = SRC + [os.path.join(HERE, "csrc", n) for n in ("lbm_kernels.cuh", "lbm_common.cuh", "lbm_aux.cuh", "lbm_transport.cuh")] + \
+    [os.path.join(ROOT, "include", "lbm.h")]
 LIB = os.path.join(HERE, "liblbm.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",

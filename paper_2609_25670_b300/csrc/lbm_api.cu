@@ -8,13 +8,16 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
 
 #include "../../include/lbm.h"
+#include "lbm_aux.cuh"
 #include "lbm_kernels.cuh"
+#include "lbm_transport.cuh"
 
 using namespace lbmk;
 
@@ -26,6 +29,25 @@ constexpr int kMaxGraphPeriod = 4096;
 thread_local std::string g_create_error;
 
 enum { FP = 0, FU = 1, FT = 2, FF = 3 };
+
+// an instantiated graph with the kernels it launches per replay and the
+// event pairs of its timed launches
+// Host-side buffer selectors of one simulation: which half of every
+// ping-pong pair is current, and the accumulation-reset flags.
+struct Parity {
+    int cur_pop[4] = {0, 0, 0, 0};
+    int cur_phi = 0, cur_U = 0, cur_T = 0;
+    bool acc_reset_U = true, acc_reset_T = true;
+};
+
+struct GraphRec {
+    cudaGraphExec_t exec = nullptr;
+    int kernels[LBM_K_COUNT] = {};
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
+    cudaGraph_t graph = nullptr;         // kept while timing nodes exist
+    std::vector<std::pair<cudaGraphNode_t, cudaGraphNode_t>> nodes;   // event record nodes of `events`
+    std::vector<Parity> post;            // each simulation's selectors after a replay
+};
 
 struct SimState {
     lbm_params p{};
@@ -47,6 +69,7 @@ struct SimState {
     bool acc_reset_U = true, acc_reset_T = true;
     unsigned long long* smax = nullptr;  // [S_phi, J_U] as double bits
     long long* clock = nullptr;          // base step at the start of a graph replay
+    void* dkp = nullptr;                 // device copy of the coefficient block KP<R>
     double* part = nullptr;              // diagnostics partial sums
     double* dout = nullptr;              // diagnostics results (9 doubles)
     int diag_blocks = 0;
@@ -54,12 +77,34 @@ struct SimState {
     bool initialized = false;
     bool sticky = false;
     bool has_U = false, has_T = false, frozen_T = false, has_flow = false, accumulated = false;
-    int period = 1;                      // 2 * lcm of the update factors
-    cudaGraphExec_t graph = nullptr;
-    int graph_kernels[LBM_K_COUNT] = {};
-    int tile[LBM_K_COUNT] = {8, 8, 8, 8, 8, 8, 8};   // tile height per kernel kind (autotuned)
-    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> graph_events;
+    int period = 2;                      // 2 * lcm of the update factors: every parity returns
+    int half = 1;                        // lcm of the update factors: one captured graph
+    GraphRec g[2];                       // the two halves of the period
+    int tile[LBM_K_COUNT] = {8, 8, 8, 8, 8, 8, 8, 8};   // tile height per kernel kind (autotuned)
+    void* tjobs = nullptr;               // transport jobs: one per base step of the period + an eager slot
+    size_t tjob_bytes = 0;               // bytes of one transport job in this precision
+    int teager = 0;                      // index of the eager slot
 };
+
+Parity get_parity(const SimState& s) {
+    Parity q;
+    for (int k = 0; k < 4; ++k) q.cur_pop[k] = s.cur_pop[k];
+    q.cur_phi = s.cur_phi;
+    q.cur_U = s.cur_U;
+    q.cur_T = s.cur_T;
+    q.acc_reset_U = s.acc_reset_U;
+    q.acc_reset_T = s.acc_reset_T;
+    return q;
+}
+
+void set_parity(SimState& s, const Parity& q) {
+    for (int k = 0; k < 4; ++k) s.cur_pop[k] = q.cur_pop[k];
+    s.cur_phi = q.cur_phi;
+    s.cur_U = q.cur_U;
+    s.cur_T = q.cur_T;
+    s.acc_reset_U = q.acc_reset_U;
+    s.acc_reset_T = q.acc_reset_T;
+}
 
 struct TimedEvent {
     int kind;
@@ -78,6 +123,9 @@ struct lbm_sim {
     std::vector<std::pair<void*, size_t>> blocks;
     size_t bytes = 0;
     bool graphs = true;
+    bool fuse = true;                    // fused transport launch (instantaneous coupling)
+    bool cap_single = false;             // recording the transport jobs of a single simulation's period
+    int cap_tcount = 0;                  // transport launches captured so far in that period
     uint32_t timing_mask = 0;
     double timing_ms[LBM_K_COUNT] = {};
     int64_t timing_n[LBM_K_COUNT] = {};
@@ -85,7 +133,19 @@ struct lbm_sim {
     std::vector<TimedEvent> pending;     // eager-mode timed launches
     std::vector<cudaEvent_t> event_pool;
     bool capturing = false;
-    SimState* cap_sim = nullptr;         // sim whose graph is being captured
+    int* cap_kernels = nullptr;          // kernel counts of the graph being captured
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>* cap_events = nullptr;
+    // batched ensemble: one launch per kernel kind covers every member's tiles
+    bool batching = false;
+    bool recording = false;              // launch_kind appends a job instead of launching
+    int batch_tile[LBM_K_COUNT] = {8, 8, 8, 8, 8, 8, 8, 8};
+    std::vector<unsigned char> rec[LBM_K_COUNT];
+    int rec_jobs[LBM_K_COUNT] = {};
+    int rec_tiles[LBM_K_COUNT] = {};
+    int64_t half_all = 1;                // lcm of the members' halves: one captured graph
+    void* job_buf = nullptr;             // device job tables: one region per half
+    size_t job_buf_bytes = 0;
+    GraphRec bg[2];                      // the two halves of the common period
     double* staging = nullptr;           // FP64 upload / download staging (lazy)
     size_t staging_bytes = 0;
     std::string err;
@@ -151,7 +211,8 @@ lbm_status validate(const lbm_params* p, std::string& why) {
     auto bad = [&](const char* m) { why = m; return LBM_E_INVALID_ARG; };
     if (p->struct_version != LBM_PARAMS_VERSION) return bad("struct_version != LBM_PARAMS_VERSION");
     if (p->nx < 4 || p->ny < 4) return bad("nx and ny must be >= 4");
-    if ((int64_t)p->nx * p->ny > (int64_t)1 << 31) return bad("nx * ny must be < 2^31");
+    // the update kernels address population planes with 32-bit offsets
+    if ((int64_t)p->nx * p->ny * 8 >= (int64_t)1 << 31) return bad("nx * ny must be below 2^28 nodes");
     if (p->fields & ~(uint32_t)(LBM_FIELD_U | LBM_FIELD_T | LBM_FIELD_FROZEN_T | LBM_FIELD_FLOW)) return bad("unknown fields bit");
     if ((p->fields & LBM_FIELD_T) && (p->fields & LBM_FIELD_FROZEN_T)) return bad("T and FROZEN_T are exclusive");
     if (p->bc_scalar_x < 0 || p->bc_scalar_x > 1 || p->bc_scalar_y < 0 || p->bc_scalar_y > 1)
@@ -245,12 +306,12 @@ struct LaunchScope {
         }
     }
     ~LaunchScope() {
-        if (h->capturing) h->cap_sim->graph_kernels[kind]++;
+        if (h->capturing) h->cap_kernels[kind]++;
         else h->launches[kind]++;
         if (a) {
             if (h->capturing) {
                 cudaEventRecordWithFlags(b, h->stream, cudaEventRecordExternal);
-                h->cap_sim->graph_events.push_back({kind, {a, b}});
+                h->cap_events->push_back({kind, {a, b}});
             } else {
                 cudaEventRecord(b, h->stream);
                 h->pending.push_back({kind, a, b});
@@ -281,6 +342,26 @@ lbm_status collect_pending(lbm_sim* h) {
 template <int TYV>
 inline dim3 grid_of(const SimState& s) { return dim3((s.nx + TX - 1) / TX, (s.ny + TYV - 1) / TYV); }
 
+// Update-kernel launch on the handle's stream, with dynamic shared memory
+// (opted in above the 48 KB default when a kernel needs more).
+template <typename... KArgs, typename... Args>
+inline void launch_ex_smem(lbm_sim* h, void (*kern)(KArgs...), dim3 g, dim3 b, size_t smem, Args... args) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = h->stream;
+    cfg.attrs = nullptr;
+    cfg.numAttrs = 0;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_ex(lbm_sim* h, void (*kern)(KArgs...), dim3 g, dim3 b, Args... args) {
+    launch_ex_smem(h, kern, g, b, 0, args...);
+}
+
 #define LBM_TY_SWITCH(sel, BODY)                       \
     switch (sel) {                                     \
         case 4: { constexpr int TYV = 4; BODY; } break;   \
@@ -288,41 +369,148 @@ inline dim3 grid_of(const SimState& s) { return dim3((s.nx + TX - 1) / TX, (s.ny
         default: { constexpr int TYV = 8; BODY; } break;  \
     }
 
+// Batched ensemble: instead of launching, append this member's job (the same
+// arguments a single launch would get) to the table of `kind`.
+template <typename J>
+void push_job(lbm_sim* h, int kind, J& j, const SimState& s) {
+    const int tyv = h->batch_tile[kind];
+    j.tiles_x = (s.nx + TX - 1) / TX;
+    j.tile0 = h->rec_tiles[kind];
+    h->rec_tiles[kind] += j.tiles_x * ((s.ny + tyv - 1) / tyv);
+    const unsigned char* b = (const unsigned char*)&j;
+    h->rec[kind].insert(h->rec[kind].end(), b, b + sizeof(J));
+    h->rec_jobs[kind]++;
+}
+
 template <typename R, typename ST, bool DEV>
-void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* clock, long long off) {
-    const KP<R> P = make_kp<R>(s);
-    cudaStream_t st = h->stream;
-    LaunchScope ls(h, kind);
+void record_job(lbm_sim* h, SimState& s, int kind, const long long* clock, long long off) {
     const R* phi_now = (const R*)s.phi[s.cur_phi];
     const R* uxc = s.has_flow ? (const R*)s.ux[s.cur_pop[FF]] : nullptr;
     const R* uyc = s.has_flow ? (const R*)s.uy[s.cur_pop[FF]] : nullptr;
     switch (kind) {
+        case LBM_K_PHASE: {
+            PhaseJob<R, ST> j{(const KP<R>*)s.dkp,(const ST*)s.pops[FP][s.cur_pop[FP]], (ST*)s.pops[FP][1 - s.cur_pop[FP]],
+                              phi_now, (R*)s.phi[1 - s.cur_phi], s.has_U ? (const R*)s.U[s.cur_U] : nullptr,
+                              s.has_T ? (const R*)s.T[s.cur_T] : nullptr, clock, off, 0, 0};
+            push_job(h, kind, j, s);
+            break;
+        }
+        case LBM_K_TRANSFER: {
+            TransferJob<R> j{(const KP<R>*)s.dkp,(const R*)s.phi[1 - s.cur_phi], phi_now,
+                             s.has_U ? (const R*)s.U[s.cur_U] : nullptr, s.has_U ? (R*)s.U[1 - s.cur_U] : nullptr,
+                             s.has_T ? (const R*)s.T[s.cur_T] : nullptr, s.has_T ? (R*)s.T[1 - s.cur_T] : nullptr,
+                             (R*)s.accU, (R*)s.accT, s.acc_reset_U ? 1 : 0, s.acc_reset_T ? 1 : 0, s.smax, 0, 0};
+            push_job(h, kind, j, s);
+            break;
+        }
+        case LBM_K_SCALAR_U:
+        case LBM_K_SCALAR_T: {
+            const int f = kind == LBM_K_SCALAR_U ? FU : FT;
+            void* const* mac = kind == LBM_K_SCALAR_U ? s.U : s.T;
+            const int cm = kind == LBM_K_SCALAR_U ? s.cur_U : s.cur_T;
+            ScalarJob<R, ST> j{(const KP<R>*)s.dkp,(const ST*)s.pops[f][s.cur_pop[f]], (ST*)s.pops[f][1 - s.cur_pop[f]],
+                               (const R*)mac[cm], (R*)mac[1 - cm],
+                               (const R*)(kind == LBM_K_SCALAR_U ? s.accU : s.accT), phi_now, uxc, uyc, s.smax, 0, 0};
+            push_job(h, kind, j, s);
+            break;
+        }
+        case LBM_K_FLOW: {
+            const int c = s.cur_pop[FF];
+            FlowJob<R, ST> j{(const KP<R>*)s.dkp,(const ST*)s.pops[FF][c], (ST*)s.pops[FF][1 - c], phi_now,
+                             (const R*)s.ux[c], (const R*)s.uy[c], (const R*)s.rho[c], (R*)s.ux[1 - c],
+                             (R*)s.uy[1 - c], (R*)s.rho[1 - c], 0, 0};
+            push_job(h, kind, j, s);
+            break;
+        }
+        default: break;
+    }
+}
+
+template <typename R, typename ST, bool DEV>
+void launch_batch(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, int tiles) {
+    LaunchScope ls(h, kind);
+    const dim3 g(tiles);
+    switch (kind) {
         case LBM_K_PHASE:
-            LBM_TY_SWITCH(tysel, (k_phase<R, ST, DEV, TYV><<<grid_of<TYV>(s), dim3(TX, TYV), 0, st>>>(
+            LBM_TY_SWITCH(tysel, (launch_ex(h, k_phase_batch<R, ST, DEV, TYV>, g, dim3(TX, TYV),
+                                            (const PhaseJob<R, ST>*)jobs, njobs)));
+            break;
+        case LBM_K_TRANSFER:
+            LBM_TY_SWITCH(tysel, (launch_ex(h, k_transfer_batch<R, TYV>, g, dim3(TX, TYV),
+                                            (const TransferJob<R>*)jobs, njobs)));
+            break;
+        case LBM_K_SCALAR_U:
+            LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar_batch<R, ST, DEV, TYV, 0>, g, dim3(TX, TYV),
+                                            (const ScalarJob<R, ST>*)jobs, njobs)));
+            break;
+        case LBM_K_SCALAR_T:
+            LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar_batch<R, ST, DEV, TYV, 1>, g, dim3(TX, TYV),
+                                            (const ScalarJob<R, ST>*)jobs, njobs)));
+            break;
+        case LBM_K_FLOW:
+            LBM_TY_SWITCH(tysel, (launch_ex(h, k_flow_batch<R, ST, DEV, TYV>, g, dim3(TX, TYV),
+                                            (const FlowJob<R, ST>*)jobs, njobs)));
+            break;
+        case LBM_K_TRANSPORT:
+            LBM_TY_SWITCH(tysel, (launch_ex_smem(h, k_transport_batch<R, ST, DEV, TYV>, g, dim3(TX, TYV),
+                                                 sizeof(TransportSmem<R, TYV>), (const TransportJob<R, ST>*)jobs,
+                                                 njobs)));
+            break;
+        default: break;
+    }
+}
+
+void launch_batch_any(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, int tiles) {
+    switch (h->precision) {
+        case LBM_PREC_F64: launch_batch<double, double, false>(h, kind, tysel, jobs, njobs, tiles); break;
+        case LBM_PREC_F32: launch_batch<float, float, false>(h, kind, tysel, jobs, njobs, tiles); break;
+        case LBM_PREC_F16_DEV: launch_batch<float, __half, true>(h, kind, tysel, jobs, njobs, tiles); break;
+        default: launch_batch<float, __nv_bfloat16, true>(h, kind, tysel, jobs, njobs, tiles); break;
+    }
+}
+
+template <typename R, typename ST, bool DEV>
+void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* clock, long long off) {
+    if (h->recording) {
+        record_job<R, ST, DEV>(h, s, kind, clock, off);
+        return;
+    }
+    // the coefficients are read from the simulation's device copy, as the
+    // batched launches do: one code path, identical arithmetic
+    const KP<R>* P = (const KP<R>*)s.dkp;
+    LaunchScope ls(h, kind);
+    const R* phi_now = (const R*)s.phi[s.cur_phi];
+    const R* uxc = s.has_flow ? (const R*)s.ux[s.cur_pop[FF]] : nullptr;
+    const R* uyc = s.has_flow ? (const R*)s.uy[s.cur_pop[FF]] : nullptr;
+    const R* null_r = nullptr;
+    R* null_w = nullptr;
+    switch (kind) {
+        case LBM_K_PHASE:
+            LBM_TY_SWITCH(tysel, (launch_ex(h, k_phase<R, ST, DEV, TYV>, grid_of<TYV>(s), dim3(TX, TYV),
                 P, (const ST*)s.pops[FP][s.cur_pop[FP]], (ST*)s.pops[FP][1 - s.cur_pop[FP]], phi_now,
-                (R*)s.phi[1 - s.cur_phi], s.has_U ? (const R*)s.U[s.cur_U] : nullptr,
-                s.has_T ? (const R*)s.T[s.cur_T] : nullptr, clock, off)));
+                (R*)s.phi[1 - s.cur_phi], s.has_U ? (const R*)s.U[s.cur_U] : null_r,
+                s.has_T ? (const R*)s.T[s.cur_T] : null_r, clock, off)));
             break;
         case LBM_K_TRANSFER:   // phi^q = phi[1 - cur], phi^{q+1} = phi[cur] (after the phase flip)
-            LBM_TY_SWITCH(tysel, (k_transfer<R, TYV><<<grid_of<TYV>(s), dim3(TX, TYV), 0, st>>>(
-                P, (const R*)s.phi[1 - s.cur_phi], phi_now, s.has_U ? (const R*)s.U[s.cur_U] : nullptr,
-                s.has_U ? (R*)s.U[1 - s.cur_U] : nullptr, s.has_T ? (const R*)s.T[s.cur_T] : nullptr,
-                s.has_T ? (R*)s.T[1 - s.cur_T] : nullptr, (R*)s.accU, (R*)s.accT, s.acc_reset_U ? 1 : 0,
+            LBM_TY_SWITCH(tysel, (launch_ex(h, k_transfer<R, TYV>, grid_of<TYV>(s), dim3(TX, TYV),
+                P, (const R*)s.phi[1 - s.cur_phi], phi_now, s.has_U ? (const R*)s.U[s.cur_U] : null_r,
+                s.has_U ? (R*)s.U[1 - s.cur_U] : null_w, s.has_T ? (const R*)s.T[s.cur_T] : null_r,
+                s.has_T ? (R*)s.T[1 - s.cur_T] : null_w, (R*)s.accU, (R*)s.accT, s.acc_reset_U ? 1 : 0,
                 s.acc_reset_T ? 1 : 0, s.smax)));
             break;
         case LBM_K_SCALAR_U:
-            LBM_TY_SWITCH(tysel, (k_scalar<R, ST, DEV, TYV, 0><<<grid_of<TYV>(s), dim3(TX, TYV), 0, st>>>(
+            LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar<R, ST, DEV, TYV, 0>, grid_of<TYV>(s), dim3(TX, TYV),
                 P, (const ST*)s.pops[FU][s.cur_pop[FU]], (ST*)s.pops[FU][1 - s.cur_pop[FU]], (const R*)s.U[s.cur_U],
                 (R*)s.U[1 - s.cur_U], (const R*)s.accU, phi_now, uxc, uyc, s.smax)));
             break;
         case LBM_K_SCALAR_T:
-            LBM_TY_SWITCH(tysel, (k_scalar<R, ST, DEV, TYV, 1><<<grid_of<TYV>(s), dim3(TX, TYV), 0, st>>>(
+            LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar<R, ST, DEV, TYV, 1>, grid_of<TYV>(s), dim3(TX, TYV),
                 P, (const ST*)s.pops[FT][s.cur_pop[FT]], (ST*)s.pops[FT][1 - s.cur_pop[FT]], (const R*)s.T[s.cur_T],
                 (R*)s.T[1 - s.cur_T], (const R*)s.accT, phi_now, uxc, uyc, s.smax)));
             break;
         case LBM_K_FLOW: {
             const int c = s.cur_pop[FF];
-            LBM_TY_SWITCH(tysel, (k_flow<R, ST, DEV, TYV><<<grid_of<TYV>(s), dim3(TX, TYV), 0, st>>>(
+            LBM_TY_SWITCH(tysel, (launch_ex(h, k_flow<R, ST, DEV, TYV>, grid_of<TYV>(s), dim3(TX, TYV),
                 P, (const ST*)s.pops[FF][c], (ST*)s.pops[FF][1 - c], phi_now, (const R*)s.ux[c], (const R*)s.uy[c],
                 (const R*)s.rho[c], (R*)s.ux[1 - c], (R*)s.uy[1 - c], (R*)s.rho[1 - c])));
             break;
@@ -341,8 +529,110 @@ void launch_any(lbm_sim* h, SimState& s, int kind, int tysel, const long long* c
 }
 
 // The update sequence of one base step (Eq. 34 schedule, workflow of Fig. 1).
+// ---------------------------------------------------------------------------
+// fused transport (transfer + U + T + flow of one base step)
+// ---------------------------------------------------------------------------
+template <typename R, typename ST>
+TransportJob<R, ST> make_transport_job(const SimState& s, bool tr, bool u, bool t, bool f) {
+    TransportJob<R, ST> j{};
+    j.P = (const KP<R>*)s.dkp;
+    j.do_tr = tr; j.do_U = u; j.do_T = t; j.do_F = f;
+    j.phio = (const R*)s.phi[1 - s.cur_phi];
+    j.phi = (const R*)s.phi[s.cur_phi];
+    if (s.has_U) {
+        j.Uin = (const R*)s.U[s.cur_U];
+        j.Uout = (R*)s.U[1 - s.cur_U];
+        j.fUin = (const ST*)s.pops[FU][s.cur_pop[FU]];
+        j.fUout = (ST*)s.pops[FU][1 - s.cur_pop[FU]];
+    }
+    if (s.has_T) {
+        j.Tin = (const R*)s.T[s.cur_T];
+        j.Tout = (R*)s.T[1 - s.cur_T];
+        j.fTin = (const ST*)s.pops[FT][s.cur_pop[FT]];
+        j.fTout = (ST*)s.pops[FT][1 - s.cur_pop[FT]];
+    }
+    if (s.has_flow) {
+        const int c = s.cur_pop[FF];
+        j.fFin = (const ST*)s.pops[FF][c];
+        j.fFout = (ST*)s.pops[FF][1 - c];
+        j.ux_in = (const R*)s.ux[c]; j.uy_in = (const R*)s.uy[c]; j.rho_in = (const R*)s.rho[c];
+        j.ux_out = (R*)s.ux[1 - c]; j.uy_out = (R*)s.uy[1 - c]; j.rho_out = (R*)s.rho[1 - c];
+    }
+    j.smax = s.smax;
+    return j;
+}
+
+template <typename R, typename ST, bool DEV, int TYV>
+size_t transport_smem() { return sizeof(TransportSmem<R, TYV>); }
+
+template <typename R, typename ST, bool DEV>
+void launch_transport_jobs(lbm_sim* h, int tysel, const void* jobs, int njobs, int tiles) {
+    LaunchScope ls(h, LBM_K_TRANSPORT);
+    LBM_TY_SWITCH(tysel, (launch_ex_smem(h, k_transport_batch<R, ST, DEV, TYV>, dim3(tiles), dim3(TX, TYV),
+                                          transport_smem<R, ST, DEV, TYV>(),
+                                          (const TransportJob<R, ST>*)jobs, njobs)));
+}
+
+// One simulation's transport launch: recorded (batched ensembles, or the
+// job-table pass of a single-simulation capture), replayed from the table
+// uploaded before a capture, or staged through the eager slot.
+template <typename R, typename ST, bool DEV>
+void transport_one(lbm_sim* h, SimState& s, bool tr, bool u, bool t, bool f) {
+    TransportJob<R, ST> j = make_transport_job<R, ST>(s, tr, u, t, f);
+    if (h->recording && !h->cap_single) {
+        push_job(h, LBM_K_TRANSPORT, j, s);
+        return;
+    }
+    const int tyv = s.tile[LBM_K_TRANSPORT];
+    j.tiles_x = (s.nx + TX - 1) / TX;
+    j.tile0 = 0;
+    const int tiles = j.tiles_x * ((s.ny + tyv - 1) / tyv);
+    if (h->recording) {       // single-simulation job-table pass
+        const unsigned char* b = (const unsigned char*)&j;
+        h->rec[LBM_K_TRANSPORT].insert(h->rec[LBM_K_TRANSPORT].end(), b, b + sizeof j);
+        h->rec_jobs[LBM_K_TRANSPORT]++;
+        return;
+    }
+    TransportJob<R, ST>* slot;
+    if (h->capturing) slot = (TransportJob<R, ST>*)s.tjobs + h->cap_tcount++;
+    else {
+        slot = (TransportJob<R, ST>*)s.tjobs + s.teager;
+        cudaMemcpyAsync(slot, &j, sizeof j, cudaMemcpyHostToDevice, h->stream);
+    }
+    launch_transport_jobs<R, ST, DEV>(h, tyv, slot, 1, tiles);
+}
+
+void transport_any(lbm_sim* h, SimState& s, bool tr, bool u, bool t, bool f) {
+    switch (h->precision) {
+        case LBM_PREC_F64: transport_one<double, double, false>(h, s, tr, u, t, f); break;
+        case LBM_PREC_F32: transport_one<float, float, false>(h, s, tr, u, t, f); break;
+        case LBM_PREC_F16_DEV: transport_one<float, __half, true>(h, s, tr, u, t, f); break;
+        default: transport_one<float, __nv_bfloat16, true>(h, s, tr, u, t, f); break;
+    }
+}
+
 void enqueue_base_step(lbm_sim* h, SimState& s, int64_t n, const long long* clock, long long off) {
     const lbm_params& p = s.p;
+    if (h->fuse && !s.accumulated) {
+        const bool ph = (n + 1) % p.N_phi == 0;
+        const bool u = s.has_U && (n + 1) % p.N_U == 0;
+        const bool t = s.has_T && (n + 1) % p.N_T == 0;
+        const bool f = s.has_flow && (n + 1) % p.N_F == 0;
+        if (ph) {
+            launch_any(h, s, LBM_K_PHASE, s.tile[LBM_K_PHASE], clock, off);
+            s.cur_pop[FP] ^= 1;
+            s.cur_phi ^= 1;                  // phi[cur] = phi^{q+1}
+        }
+        if (ph || u || t || f) {
+            transport_any(h, s, ph, u, t, f);
+            if (s.has_U && (ph || u)) s.cur_U ^= 1;
+            if (s.has_T && (ph || t)) s.cur_T ^= 1;
+            if (u) s.cur_pop[FU] ^= 1;
+            if (t) s.cur_pop[FT] ^= 1;
+            if (f) s.cur_pop[FF] ^= 1;
+        }
+        return;
+    }
     if ((n + 1) % p.N_phi == 0) {
         launch_any(h, s, LBM_K_PHASE, s.tile[LBM_K_PHASE], clock, off);
         s.cur_pop[FP] ^= 1;
@@ -374,51 +664,198 @@ void enqueue_base_step(lbm_sim* h, SimState& s, int64_t n, const long long* cloc
     }
 }
 
-void drop_graph(SimState& s) {
-    if (s.graph) cudaGraphExecDestroy(s.graph);
-    s.graph = nullptr;
-    for (auto& e : s.graph_events) {
+void drop_rec(GraphRec& r) {
+    if (r.exec) cudaGraphExecDestroy(r.exec);
+    r.exec = nullptr;
+    for (auto& e : r.events) {
         cudaEventDestroy(e.second.first);
         cudaEventDestroy(e.second.second);
     }
-    s.graph_events.clear();
-    std::fill(std::begin(s.graph_kernels), std::end(s.graph_kernels), 0);
+    r.events.clear();
+    if (r.graph) cudaGraphDestroy(r.graph);
+    r.graph = nullptr;
+    r.nodes.clear();
+    std::fill(std::begin(r.kernels), std::end(r.kernels), 0);
+    r.post.clear();
 }
 
-// Capture one schedule period (s.step must be a multiple of s.period, where
-// every ping-pong parity equals its value after initialisation).
-lbm_status capture_graph(lbm_sim* h, SimState& s) {
-    drop_graph(s);
-    cudaGraph_t g = nullptr;
-    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    h->capturing = true;
-    h->cap_sim = &s;
-    for (int k = 0; k < s.period; ++k) enqueue_base_step(h, s, s.step + k, s.frozen_T ? s.clock : nullptr, k);
-    if (s.frozen_T) k_tick<<<1, 1, 0, h->stream>>>(s.clock, s.period);
+void drop_graph(SimState& s) {
+    drop_rec(s.g[0]);
+    drop_rec(s.g[1]);
+}
+
+lbm_status end_capture(lbm_sim* h, GraphRec& r) {
     h->capturing = false;
-    h->cap_sim = nullptr;
+    cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess) return fail(h, LBM_E_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&s.graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) { s.graph = nullptr; return fail(h, LBM_E_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e)); }
+    e = cudaGraphInstantiate(&r.exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        r.exec = nullptr;
+        return fail(h, LBM_E_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+    if (r.events.empty()) {
+        cudaGraphDestroy(g);
+        return LBM_OK;
+    }
+    // timing nodes: find the event record node of each captured event, so
+    // that every replay can record into fresh events without a host wait
+    r.graph = g;
+    size_t n = 0;
+    CK(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> all(n);
+    CK(cudaGraphGetNodes(g, all.data(), &n));
+    std::map<cudaEvent_t, cudaGraphNode_t> of;
+    for (cudaGraphNode_t nd : all) {
+        cudaGraphNodeType t;
+        CK(cudaGraphNodeGetType(nd, &t));
+        if (t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev = nullptr;
+        CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+        of[ev] = nd;
+    }
+    for (auto& ev : r.events) {
+        auto a = of.find(ev.second.first), b = of.find(ev.second.second);
+        if (a == of.end() || b == of.end()) return fail(h, LBM_E_CUDA, "timing node missing from the captured graph");
+        r.nodes.push_back({a->second, b->second});
+    }
     return LBM_OK;
 }
 
-lbm_status graph_replay(lbm_sim* h, SimState& s) {
-    CK(cudaGraphLaunch(s.graph, h->stream));
-    for (int k = 0; k < LBM_K_COUNT; ++k) h->launches[k] += s.graph_kernels[k];
-    s.step += s.period;
-    if (!s.graph_events.empty()) {
-        CK(cudaStreamSynchronize(h->stream));
-        for (auto& ev : s.graph_events) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, ev.second.first, ev.second.second) == cudaSuccess) {
-                h->timing_ms[ev.first] += ms;
-                h->timing_n[ev.first]++;
-            }
+// Point the timing nodes of `r` at fresh pool events for the next replay and
+// queue them; the elapsed times are read when the pending list is collected.
+lbm_status arm_graph_events(lbm_sim* h, GraphRec& r) {
+    for (size_t i = 0; i < r.events.size(); ++i) {
+        cudaEvent_t a = pool_get(h), b = pool_get(h);
+        CK(cudaGraphExecEventRecordNodeSetEvent(r.exec, r.nodes[i].first, a));
+        CK(cudaGraphExecEventRecordNodeSetEvent(r.exec, r.nodes[i].second, b));
+        h->pending.push_back({r.events[i].first, a, b});
+    }
+    return LBM_OK;
+}
+
+// Capture half `which` of the schedule period: s.half = lcm(N_chi) base steps
+// starting at a step n with n mod 2*half == which*half.  Every ping-pong
+// parity depends only on n mod 2*half, so the two halves replay forever.
+void clear_records(lbm_sim* h);
+
+lbm_status capture_graph(lbm_sim* h, SimState& s, int which) {
+    drop_rec(s.g[which]);
+    // pass 1: this half's transport jobs (their buffer pointers depend on the
+    // parities of each base step), uploaded to the simulation's job table
+    clear_records(h);
+    const Parity pre = get_parity(s);
+    h->recording = true;
+    h->cap_single = true;
+    for (int k = 0; k < s.half; ++k) enqueue_base_step(h, s, s.step + k, s.frozen_T ? s.clock : nullptr, k);
+    h->recording = false;
+    h->cap_single = false;
+    set_parity(s, pre);
+    if (!h->rec[LBM_K_TRANSPORT].empty())
+        CK(cudaMemcpy((unsigned char*)s.tjobs + (size_t)which * s.half * s.tjob_bytes, h->rec[LBM_K_TRANSPORT].data(),
+                      h->rec[LBM_K_TRANSPORT].size(), cudaMemcpyHostToDevice));
+    clear_records(h);
+    // pass 2: capture
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    h->cap_tcount = which * s.half;
+    h->cap_kernels = s.g[which].kernels;
+    h->cap_events = &s.g[which].events;
+    for (int k = 0; k < s.half; ++k) enqueue_base_step(h, s, s.step + k, s.frozen_T ? s.clock : nullptr, k);
+    if (s.frozen_T) k_tick<<<1, 1, 0, h->stream>>>(s.clock, s.half);
+    s.g[which].post.assign(1, get_parity(s));
+    set_parity(s, pre);                  // the replay applies the post state
+    return end_capture(h, s.g[which]);
+}
+
+void drop_batch_graph(lbm_sim* h) {
+    drop_rec(h->bg[0]);
+    drop_rec(h->bg[1]);
+}
+
+void clear_records(lbm_sim* h) {
+    for (int k = 0; k < LBM_K_COUNT; ++k) {
+        h->rec[k].clear();
+        h->rec_jobs[k] = 0;
+        h->rec_tiles[k] = 0;
+    }
+}
+
+// Capture half `which` of the common period of a batched ensemble (half_all =
+// lcm of the members' halves; every member's parities depend only on the step
+// mod 2 * half_all): per base step, one launch per kernel kind over the tiles
+// of every member that fires (members are independent, so the per-member
+// order phase -> transfer -> U -> T -> flow is kept by the order of the
+// launches).  The job tables of each half live in their own half of job_buf.
+lbm_status capture_batch(lbm_sim* h, int which) {
+    drop_rec(h->bg[which]);
+    struct Seg { int kind; size_t off; int njobs, tiles; };
+    std::vector<std::vector<Seg>> steps((size_t)h->half_all);
+    std::vector<unsigned char> all;
+    std::vector<Parity> pre;
+    for (auto& s : h->sims) pre.push_back(get_parity(s));
+    static const int order[6] = {LBM_K_PHASE, LBM_K_TRANSFER, LBM_K_TRANSPORT, LBM_K_SCALAR_U, LBM_K_SCALAR_T,
+                                 LBM_K_FLOW};
+    for (int64_t k = 0; k < h->half_all; ++k) {
+        clear_records(h);
+        h->recording = true;
+        for (auto& s : h->sims) enqueue_base_step(h, s, s.step + k, s.frozen_T ? s.clock : nullptr, k);
+        h->recording = false;
+        for (int kind : order) {
+            if (!h->rec_jobs[kind]) continue;
+            size_t off = (all.size() + 255) & ~size_t(255);
+            all.resize(off);
+            all.insert(all.end(), h->rec[kind].begin(), h->rec[kind].end());
+            steps[k].push_back({kind, off, h->rec_jobs[kind], h->rec_tiles[kind]});
         }
     }
+    clear_records(h);
+    h->bg[which].post.clear();
+    for (size_t i = 0; i < h->sims.size(); ++i) {
+        h->bg[which].post.push_back(get_parity(h->sims[i]));
+        set_parity(h->sims[i], pre[i]);  // the replay applies the post state
+    }
+    const size_t region = h->job_buf_bytes / 2;
+    if (all.size() > region)
+        return fail(h, LBM_E_STATE, "job tables of %zu bytes exceed the %zu reserved", all.size(), region);
+    unsigned char* base = (unsigned char*)h->job_buf + (size_t)which * region;
+    CK(cudaMemcpy(base, all.data(), all.size(), cudaMemcpyHostToDevice));
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    h->cap_kernels = h->bg[which].kernels;
+    h->cap_events = &h->bg[which].events;
+    for (int64_t k = 0; k < h->half_all; ++k)
+        for (const Seg& sg : steps[k])
+            launch_batch_any(h, sg.kind, h->batch_tile[sg.kind], base + sg.off, sg.njobs, sg.tiles);
+    for (auto& s : h->sims)
+        if (s.frozen_T) k_tick<<<1, 1, 0, h->stream>>>(s.clock, h->half_all);
+    return end_capture(h, h->bg[which]);
+}
+
+lbm_status batch_replay(lbm_sim* h, int which) {
+    if (!h->bg[which].events.empty()) {
+        lbm_status st = arm_graph_events(h, h->bg[which]);
+        if (st) return st;
+    }
+    CK(cudaGraphLaunch(h->bg[which].exec, h->stream));
+    for (int k = 0; k < LBM_K_COUNT; ++k) h->launches[k] += h->bg[which].kernels[k];
+    for (size_t i = 0; i < h->sims.size(); ++i) {
+        h->sims[i].step += h->half_all;
+        set_parity(h->sims[i], h->bg[which].post[i]);
+    }
+    return LBM_OK;
+}
+
+lbm_status graph_replay(lbm_sim* h, SimState& s, int which) {
+    if (!s.g[which].events.empty()) {
+        lbm_status st = arm_graph_events(h, s.g[which]);
+        if (st) return st;
+    }
+    CK(cudaGraphLaunch(s.g[which].exec, h->stream));
+    for (int k = 0; k < LBM_K_COUNT; ++k) h->launches[k] += s.g[which].kernels[k];
+    s.step += s.half;
+    set_parity(s, s.g[which].post[0]);
     return LBM_OK;
 }
 
@@ -618,7 +1055,8 @@ lbm_status lbm_create(const lbm_params* p, int32_t n_sims, const lbm_params* per
         s.has_flow = (s.p.fields & LBM_FIELD_FLOW) != 0;
         s.accumulated = s.p.coupling == LBM_COUPLING_ACCUMULATED;
         int64_t L = lcm64(lcm64(s.p.N_phi, s.has_U ? s.p.N_U : 1), lcm64(s.has_T ? s.p.N_T : 1, s.has_flow ? s.p.N_F : 1));
-        s.period = (int)std::min<int64_t>(2 * L, (int64_t)1 << 30);
+        s.half = (int)std::min<int64_t>(L, (int64_t)1 << 29);
+        s.period = 2 * s.half;
         const bool present[4] = {true, s.has_U, s.has_T, s.has_flow};
         lbm_status st = LBM_OK;
         for (int f = 0; f < 4 && !st; ++f)
@@ -640,12 +1078,46 @@ lbm_status lbm_create(const lbm_params* p, int32_t n_sims, const lbm_params* per
         s.diag_blocks = (int)std::min<size_t>(1184, (s.nn + 255) / 256);
         if (!st) st = dev_alloc(h, 3 * sizeof(double) * s.diag_blocks, (void**)&s.part);
         if (!st) st = dev_alloc(h, 16 * sizeof(double), (void**)&s.dout);
+        if (!st) st = dev_alloc(h, sizeof(KP<double>), &s.dkp);
+        s.teager = s.half <= kMaxGraphPeriod ? s.period : 0;
+        s.tjob_bytes = h->precision == LBM_PREC_F64 ? sizeof(TransportJob<double, double>)
+                       : h->precision == LBM_PREC_F32 ? sizeof(TransportJob<float, float>)
+                                                      : sizeof(TransportJob<float, __half>);
+        if (!st) st = dev_alloc(h, (size_t)(s.teager + 1) * s.tjob_bytes, &s.tjobs);
+        if (!st) {
+            cudaError_t e = h->precision == LBM_PREC_F64
+                                ? [&] { const KP<double> k = make_kp<double>(s); return cudaMemcpy(s.dkp, &k, sizeof k, cudaMemcpyHostToDevice); }()
+                                : [&] { const KP<float> k = make_kp<float>(s); return cudaMemcpy(s.dkp, &k, sizeof k, cudaMemcpyHostToDevice); }();
+            if (e != cudaSuccess) st = fail(h, LBM_E_CUDA, "cudaMemcpy(coefficients): %s", cudaGetErrorString(e));
+        }
         if (st) {
             std::string m = h->err;
             free_all(h);
             if (h->own_stream) cudaStreamDestroy(h->stream);
             delete h;
             return fail(nullptr, st, "%s", m.c_str());
+        }
+    }
+    if (n_sims > 1) {
+        // batched ensemble: common period and room for one period of job tables
+        int64_t P = 1;
+        for (auto& s : h->sims) P = std::min<int64_t>(lcm64(P, s.half), (int64_t)1 << 40);
+        h->half_all = P;
+        h->batching = P <= kMaxGraphPeriod;
+        if (h->batching) {
+            const size_t per = std::max(std::max(std::max(sizeof(PhaseJob<double, double>), sizeof(TransferJob<double>)),
+                                                 std::max(sizeof(ScalarJob<double, double>), sizeof(FlowJob<double, double>))),
+                                        sizeof(TransportJob<double, double>));
+            // two halves x P base steps x 6 kinds x (members' jobs + alignment)
+            h->job_buf_bytes = 2 * (size_t)P * 6 * ((size_t)n_sims * per + 256);
+            lbm_status st = dev_alloc(h, h->job_buf_bytes, &h->job_buf);
+            if (st) {
+                std::string m = h->err;
+                free_all(h);
+                if (h->own_stream) cudaStreamDestroy(h->stream);
+                delete h;
+                return fail(nullptr, st, "%s", m.c_str());
+            }
         }
     }
     *out = h;
@@ -715,23 +1187,58 @@ lbm_status lbm_advance(lbm_handle h, int64_t n_base_steps) {
         if (!s.initialized) return fail(h, LBM_E_STATE, "simulation not initialised");
         if (s.sticky) return fail(h, LBM_E_STATE, "a non-finite value was seen; initialise again");
     }
+    if (h->batching && h->graphs && h->half_all <= kMaxGraphPeriod) {
+        // batched ensemble: members in lockstep replay one graph per half of
+        // the common ping-pong period
+        int64_t left = n_base_steps;
+        bool clock_set = false;
+        const int64_t H = h->half_all;
+        while (left > 0) {
+            bool aligned = true;
+            for (auto& s : h->sims) aligned = aligned && s.step == h->sims[0].step;
+            if (!aligned) break;
+            if (h->sims[0].step % H == 0 && left >= H) {
+                const int which = (int)((h->sims[0].step / H) % 2);
+                if (!h->bg[which].exec) {
+                    lbm_status st = capture_batch(h, which);
+                    if (st) return st;
+                }
+                if (!clock_set)
+                    for (auto& s : h->sims)
+                        if (s.frozen_T) k_set_clock<<<1, 1, 0, h->stream>>>(s.clock, (long long)s.step);
+                clock_set = true;
+                lbm_status st = batch_replay(h, which);
+                if (st) return st;
+                left -= H;
+            } else {
+                for (auto& s : h->sims) {
+                    enqueue_base_step(h, s, s.step, nullptr, (long long)s.step);
+                    s.step += 1;
+                }
+                left -= 1;
+                clock_set = false;
+            }
+        }
+        n_base_steps = left;   // members out of lockstep continue one by one below
+    }
     for (auto& s : h->sims) {
         int64_t left = n_base_steps;
         bool clock_set = false;
         while (left > 0) {
-            const bool use_graph = h->graphs && s.period <= kMaxGraphPeriod && (s.step % s.period) == 0 && left >= s.period;
+            const bool use_graph = h->graphs && s.half <= kMaxGraphPeriod && (s.step % s.half) == 0 && left >= s.half;
             if (use_graph) {
-                if (!s.graph) {
-                    lbm_status st = capture_graph(h, s);
+                const int which = (int)((s.step / s.half) % 2);
+                if (!s.g[which].exec) {
+                    lbm_status st = capture_graph(h, s, which);
                     if (st) return st;
                 }
                 if (s.frozen_T && !clock_set) {
                     k_set_clock<<<1, 1, 0, h->stream>>>(s.clock, (long long)s.step);
                     clock_set = true;
                 }
-                lbm_status st = graph_replay(h, s);
+                lbm_status st = graph_replay(h, s, which);
                 if (st) return st;
-                left -= s.period;
+                left -= s.half;
             } else {
                 enqueue_base_step(h, s, s.step, nullptr, (long long)s.step);
                 s.step += 1;
@@ -741,7 +1248,8 @@ lbm_status lbm_advance(lbm_handle h, int64_t n_base_steps) {
         }
     }
     CK(cudaGetLastError());
-    return collect_pending(h);
+    // timed launches are read without a host wait until many are queued
+    return h->pending.size() > 4096 ? collect_pending(h) : LBM_OK;
 }
 
 lbm_status lbm_fields(lbm_handle h, int32_t sim, uint32_t which, void* dst, int32_t dst_is_device, int32_t as_f64) {
@@ -775,6 +1283,7 @@ void lbm_destroy(lbm_handle h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     for (auto& s : h->sims) drop_graph(s);
+    drop_batch_graph(h);
     for (auto& t : h->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     for (auto e : h->event_pool) cudaEventDestroy(e);
     free_all(h);
@@ -793,6 +1302,38 @@ lbm_status lbm_timing_enable(lbm_handle h, uint32_t kind_mask) {
     if (kind_mask >> LBM_K_COUNT) return fail(h, LBM_E_INVALID_ARG, "unknown kernel kind bit");
     h->timing_mask = kind_mask;
     for (auto& s : h->sims) drop_graph(s);
+    drop_batch_graph(h);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_tile(lbm_handle h, int32_t kind, int32_t ty) {
+    if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
+    if (kind < 0 || (kind > LBM_K_FLOW && kind != LBM_K_TRANSPORT))
+        return fail(h, LBM_E_INVALID_ARG, "kind %d is not an update kernel", kind);
+    if (ty != 4 && ty != 8 && ty != 16) return fail(h, LBM_E_INVALID_ARG, "tile height %d not in {4, 8, 16}", ty);
+    for (auto& s : h->sims) {
+        s.tile[kind] = ty;
+        drop_graph(s);
+    }
+    h->batch_tile[kind] = ty;
+    drop_batch_graph(h);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_fusion(lbm_handle h, int32_t enable) {
+    if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
+    h->fuse = enable != 0;
+    for (auto& s : h->sims) drop_graph(s);
+    drop_batch_graph(h);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_batching(lbm_handle h, int32_t enable) {
+    if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
+    if (enable && (h->sims.size() < 2 || !h->job_buf))
+        return fail(h, LBM_E_INVALID_ARG, "batching needs >= 2 simulations with a common period <= %d", kMaxGraphPeriod);
+    h->batching = enable != 0;
+    drop_batch_graph(h);
     return LBM_OK;
 }
 
@@ -820,15 +1361,29 @@ lbm_status lbm_autotune(lbm_handle h, int32_t reps, int32_t* chosen) {
     for (auto& s : h->sims) {
         if (!s.initialized) { cudaEventDestroy(a); cudaEventDestroy(b); h->timing_mask = mask;
                               return fail(h, LBM_E_STATE, "simulation not initialised"); }
-        const bool present[LBM_K_COUNT] = {true, !s.accumulated, s.has_U, s.has_T, s.has_flow, false, false};
-        for (int kind = 0; kind < LBM_K_FLOW + 1; ++kind) {
+        const bool fused = h->fuse && !s.accumulated;
+        const bool present[LBM_K_COUNT] = {true, !s.accumulated && !fused, s.has_U && !fused, s.has_T && !fused,
+                                           s.has_flow && !fused, false, false, fused};
+        // one launch of `kind` with tile height v on the current state; the
+        // transport launch runs every stage the simulation has
+        auto tune_launch = [&](int kind, int v) {
+            if (kind == LBM_K_TRANSPORT) {
+                const int keep = s.tile[kind];
+                s.tile[kind] = v;
+                transport_any(h, s, true, s.has_U, s.has_T, s.has_flow);
+                s.tile[kind] = keep;
+            } else {
+                launch_any(h, s, kind, v, s.clock, 0);
+            }
+        };
+        for (int kind = 0; kind < LBM_K_COUNT; ++kind) {
             if (!present[kind]) continue;
             float best = 1e30f;
             int bestv = s.tile[kind];
             for (int v : variants) {
-                launch_any(h, s, kind, v, s.clock, 0);          // warm the variant
+                tune_launch(kind, v);          // warm the variant
                 CK(cudaEventRecord(a, h->stream));
-                for (int r = 0; r < reps; ++r) launch_any(h, s, kind, v, s.clock, 0);
+                for (int r = 0; r < reps; ++r) tune_launch(kind, v);
                 CK(cudaEventRecord(b, h->stream));
                 CK(cudaEventSynchronize(b));
                 float ms = 0.f;
@@ -837,9 +1392,50 @@ lbm_status lbm_autotune(lbm_handle h, int32_t reps, int32_t* chosen) {
             }
             s.tile[kind] = bestv;
         }
-        CK(cudaMemsetAsync(s.smax, 0, 2 * sizeof(unsigned long long), h->stream));
         drop_graph(s);
     }
+    if (h->batching) {
+        // the batched launches: one job per member that has the field, at the
+        // current parities (idempotent like the single launches)
+        bool any_acc = false;
+        for (auto& s : h->sims) any_acc = any_acc || s.accumulated;
+        drop_batch_graph(h);
+        const bool fused = h->fuse && !any_acc;
+        for (int kind = 0; kind < LBM_K_COUNT; ++kind) {
+            if (kind == LBM_K_DIAG || kind == LBM_K_INIT) continue;
+            if (fused != (kind == LBM_K_TRANSPORT) && kind != LBM_K_PHASE) continue;
+            if (kind == LBM_K_TRANSFER && any_acc) continue;
+            float best = 1e30f;
+            int bestv = h->batch_tile[kind];
+            for (int v : variants) {
+                h->batch_tile[kind] = v;
+                clear_records(h);
+                h->recording = true;
+                for (auto& s : h->sims) {
+                    const bool has = kind == LBM_K_PHASE || kind == LBM_K_TRANSFER ||
+                                     (kind == LBM_K_SCALAR_U && s.has_U) || (kind == LBM_K_SCALAR_T && s.has_T) ||
+                                     (kind == LBM_K_FLOW && s.has_flow);
+                    if (kind == LBM_K_TRANSPORT) transport_any(h, s, true, s.has_U, s.has_T, s.has_flow);
+                    else if (has) launch_any(h, s, kind, v, s.clock, 0);
+                }
+                h->recording = false;
+                if (!h->rec_jobs[kind]) break;
+                CK(cudaMemcpy(h->job_buf, h->rec[kind].data(), h->rec[kind].size(), cudaMemcpyHostToDevice));
+                launch_batch_any(h, kind, v, h->job_buf, h->rec_jobs[kind], h->rec_tiles[kind]);
+                CK(cudaEventRecord(a, h->stream));
+                for (int r = 0; r < reps; ++r)
+                    launch_batch_any(h, kind, v, h->job_buf, h->rec_jobs[kind], h->rec_tiles[kind]);
+                CK(cudaEventRecord(b, h->stream));
+                CK(cudaEventSynchronize(b));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, a, b));
+                if (ms < best) { best = ms; bestv = v; }
+            }
+            h->batch_tile[kind] = bestv;
+        }
+        clear_records(h);
+    }
+    for (auto& s : h->sims) CK(cudaMemsetAsync(s.smax, 0, 2 * sizeof(unsigned long long), h->stream));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
     cudaEventDestroy(a);

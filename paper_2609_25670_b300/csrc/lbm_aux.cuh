@@ -1,0 +1,178 @@
+// Auxiliary kernels: initial distributions, FP64 staging, output fields,
+// diagnostics reductions, the base-step clock.
+#pragma once
+#include "lbm_common.cuh"
+
+namespace lbmk {
+
+// ---------------------------------------------------------------------------
+// Initial distributions f = f_eq of the macroscopic fields (Eqs. 19, 21, 28)
+// ---------------------------------------------------------------------------
+template <typename R, typename ST, bool DEV>
+__global__ void k_init(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ Um, const R* __restrict__ Tm,
+                       const R* __restrict__ uxm, const R* __restrict__ uym, const R* __restrict__ rhom,
+                       ST* __restrict__ fphi, ST* __restrict__ fU, ST* __restrict__ fT, ST* __restrict__ fF) {
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (gx >= P.nx || gy >= P.ny) return;
+    const size_t node = (size_t)gy * P.pitch + gx;
+    // gradient with the same ghost rule as the update kernels
+    R s[3][3];
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx)
+            s[dy + 1][dx + 1] = phi[(size_t)scalar_map(gy + dy, P.ny, P.bsy) * P.pitch + scalar_map(gx + dx, P.nx, P.bsx)];
+    const R gxv = (s[1][2] - s[1][0]) * (R(1) / R(3)) + (s[2][2] - s[2][0] + s[0][2] - s[0][0]) * (R(1) / R(12));
+    const R gyv = (s[2][1] - s[0][1]) * (R(1) / R(3)) + (s[2][2] + s[2][0] - s[0][2] - s[0][0]) * (R(1) / R(12));
+    R as, Nx, Ny;
+    aniso(gxv, gyv, P.eps, as, Nx, Ny);
+    const R bx = -P.dtp * P.W0sq_tau0 * Nx, by = -P.dtp * P.W0sq_tau0 * Ny;
+    const R ph = s[1][1];
+    R vx = R(0), vy = R(0);
+    if (P.has_flow) { vx = uxm[node]; vy = uym[node]; }
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const R w = wq<R>(i), ex = (R)c_ex[i], ey = (R)c_ey[i];
+        const R dp = R(3) * w * (ex * bx + ey * by);                                   // Eq. 21 minus w_i phi
+        fphi[(size_t)(i - 1) * P.plane + node] = Cvt<ST>::st(DEV ? dp : w * ph + dp);
+        if (P.has_U) {
+            const R U = Um[node], d = R(3) * w * U * P.dtU * (ex * vx + ey * vy);       // Eq. 19
+            fU[(size_t)(i - 1) * P.plane + node] = Cvt<ST>::st(DEV ? d : w * U + d);
+        }
+        if (P.has_T) {
+            const R T = Tm[node], d = R(3) * w * T * P.dtT * (ex * vx + ey * vy);
+            fT[(size_t)(i - 1) * P.plane + node] = Cvt<ST>::st(DEV ? d : w * T + d);
+        }
+    }
+    if (P.has_flow) {
+        R fe[9];
+        feq_flow<R>(rhom[node], uxm[node], uym[node], P.cF, fe);                          // Eq. 28
+#pragma unroll
+        for (int i = 1; i < 9; ++i) fF[(size_t)(i - 1) * P.plane + node] = Cvt<ST>::st(DEV ? R(0) : fe[i]);
+    }
+}
+
+// FP64 staging -> arithmetic type, with a pitch
+template <typename R>
+__global__ void k_from_f64(const double* __restrict__ src, R* __restrict__ dst, int nx, int ny, int pitch) {
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (gx < nx && gy < ny) dst[(size_t)gy * pitch + gx] = (R)src[(size_t)gy * nx + gx];
+}
+
+// derived output fields into a dense ny x nx buffer of type O
+// which: 0 phi 1 U 2 T 3 ux 4 uy 5 rho 6 C/C_inf 7 theta
+template <typename R, typename O>
+__global__ void k_out(const KP<R> P, int which, const R* __restrict__ phi, const R* __restrict__ Um,
+                      const R* __restrict__ Tm, const R* __restrict__ uxm, const R* __restrict__ uym,
+                      const R* __restrict__ rhom, const R* __restrict__ accU, const R* __restrict__ accT,
+                      O* __restrict__ dst, const long long* __restrict__ clock) {
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (gx >= P.nx || gy >= P.ny) return;
+    const size_t node = (size_t)gy * P.pitch + gx;
+    R v = R(0);
+    const R U = P.has_U ? Um[node] : R(0);
+    switch (which) {
+        case 0: v = phi[node]; break;
+        case 1: v = U; break;
+        case 2: v = P.has_T ? Tm[node] : R(0); break;
+        case 3: v = P.has_flow ? uxm[node] : R(0); break;
+        case 4: v = P.has_flow ? uym[node] : R(0); break;
+        case 5: v = P.has_flow ? rhom[node] : R(1); break;
+        case 6: v = R(0.5) * (R(1) + (R(1) - P.k) * U) * ((R(1) + P.k) - (R(1) - P.k) * phi[node]); break;
+        case 7:
+            if (P.has_T) v = (Tm[node] - P.T_shift) * P.inv_T_scale;
+            else if (P.frozen_T) v = theta_frozen(P, gy, (R)(*clock) * P.dt_base);
+            else v = P.theta_c;
+            break;
+    }
+    (void)accU; (void)accT;
+    dst[(size_t)gy * P.nx + gx] = (O)v;
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics: deterministic FP64 reductions (warp shuffle -> block -> grid)
+// ---------------------------------------------------------------------------
+// part[b*3 + 0] = sum C/C_inf, [1] = sum H, [2] = non-finite count, for block b
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ Um, const R* __restrict__ Tm,
+               const R* __restrict__ uxm, const R* __restrict__ uym, double* __restrict__ part) {
+    __shared__ double s[3][8];
+    double mc = 0.0, h = 0.0, bad = 0.0;
+    const long long nn = (long long)P.nx * P.ny;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(n / P.nx), x = (int)(n - (long long)y * P.nx);
+        const size_t node = (size_t)y * P.pitch + x;
+        const double ph = (double)phi[node];
+        const double U = P.has_U ? (double)Um[node] : 0.0;
+        const double T = P.has_T ? (double)Tm[node] : 0.0;
+        const double vx = P.has_flow ? (double)uxm[node] : 0.0, vy = P.has_flow ? (double)uym[node] : 0.0;
+        const double k = (double)P.k;
+        if (P.has_U) mc += 0.5 * (1.0 + (1.0 - k) * U) * ((1.0 + k) - (1.0 - k) * ph);
+        if (P.has_T)
+            h += (0.5 * (1.0 + ph) * (double)P.cS + 0.5 * (1.0 - ph) * (double)P.cL) * T - 0.5 * (double)P.rhoL_Lh * ph;
+        if (!isfinite(ph) || !isfinite(U) || !isfinite(T) || !isfinite(vx) || !isfinite(vy)) bad += 1.0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mc += __shfl_xor_sync(0xffffffffu, mc, o);
+        h += __shfl_xor_sync(0xffffffffu, h, o);
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s[0][w] = mc; s[1][w] = h; s[2][w] = bad; }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double a = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += s[threadIdx.x][i];
+        part[blockIdx.x * 3 + threadIdx.x] = a;
+    }
+}
+
+// out[0..2] = totals of the partials (fixed order), out[3..6] tips,
+// out[7] = S_phi, out[8] = J_U; the maxima slots are then cleared.
+template <typename R>
+__global__ void __launch_bounds__(128)
+k_diag_final(const KP<R> P, const double* __restrict__ part, int nblocks, const R* __restrict__ phi, int cx, int cy,
+             unsigned long long* __restrict__ smax, double* __restrict__ out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        double a[3] = {0.0, 0.0, 0.0};
+        for (int b = lane; b < nblocks; b += 32)
+            for (int j = 0; j < 3; ++j) a[j] += part[b * 3 + j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            for (int j = 0; j < 3; ++j) a[j] += __shfl_xor_sync(0xffffffffu, a[j], o);
+        if (lane == 0) {
+            out[0] = a[0];
+            out[1] = a[1];
+            out[2] = a[2];
+            out[7] = __longlong_as_double((long long)smax[0]);
+            out[8] = __longlong_as_double((long long)smax[1]);
+        }
+    }
+    // tips: warp d scans direction d (+x, +y, -x, -y) for the outermost crossing
+    const int d = warp;
+    const int len = (d == 0) ? P.nx - cx : (d == 1) ? P.ny - cy : (d == 2) ? cx + 1 : cy + 1;
+    auto at = [&](int k) -> double {
+        const int x = (d == 0) ? cx + k : (d == 2) ? cx - k : cx;
+        const int y = (d == 1) ? cy + k : (d == 3) ? cy - k : cy;
+        return (double)phi[(size_t)y * P.pitch + x];
+    };
+    int best = -1;
+    for (int k = lane; k < len - 1; k += 32)
+        if (at(k) >= 0.0 && at(k + 1) < 0.0) best = max(best, k);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane == 0) {
+        double r = 0.0;
+        if (len > 0 && at(len - 1) >= 0.0) r = (double)(len - 1);
+        else if (best >= 0) { const double a = at(best), b = at(best + 1); r = (double)best + a / (a - b); }
+        out[3 + d] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { smax[0] = 0ull; smax[1] = 0ull; }
+}
+
+__global__ void k_set_clock(long long* clock, long long v) { *clock = v; }
+__global__ void k_tick(long long* clock, long long d) { *clock += d; }
+
+}  // namespace lbmk

@@ -1,0 +1,165 @@
+// Shared device definitions of the multirate MRT-LBM kernels (Liu, Wu, Zhan,
+// Secs. 2-3): lattice constants, the coefficient block, storage conversions,
+// boundary index maps and the per-node pieces of the collision operators.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbmk {
+
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET_OUTFLOW = 2 };
+
+// D2Q9 velocity set and weights (Eq. 15); the constexpr copies let fully
+// unrolled loops resolve directions at compile time
+__device__ __constant__ int c_ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__device__ __constant__ int c_ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+__device__ __constant__ int c_opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+__host__ __device__ constexpr int ex_of(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0; }
+__host__ __device__ constexpr int ey_of(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0; }
+__host__ __device__ constexpr int opp_of(int i) { return i == 0 ? 0 : (i < 5 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5); }
+
+template <typename R> struct Wt {
+    static constexpr R w0 = R(4) / R(9), w1 = R(1) / R(9), w2 = R(1) / R(36);
+};
+template <typename R> __host__ __device__ constexpr R wq(int i) {
+    return i == 0 ? Wt<R>::w0 : (i < 5 ? Wt<R>::w1 : Wt<R>::w2);
+}
+
+// Coefficients derived on the host in FP64, then rounded to R.
+template <typename R> struct KP {
+    int nx, ny, pitch;
+    long long plane;       // elements per population plane
+    int bsx, bsy, bfx, bfy; // scalar / flow boundary kinds
+    int has_U, has_T, frozen_T, has_flow, accumulated;
+    // phase (Eqs. 2-4, 21-24)
+    R dtp, W0sq_tau0, inv_tau0, eps, lam, Mc;
+    // transfer (Eqs. 37-38)
+    R k, at_pre, rhoL_Lh;
+    // solute (Eqs. 7-8)
+    R dtU, DS, DL;
+    // thermal (Eqs. 11-12)
+    R dtT, kS, kL, cS, cL, T_shift, inv_T_scale;
+    // flow (Eqs. 27-32)
+    R dtF, cF, Fbx, Fby, se, seps, sq, snu, u_in;
+    // prescribed undercooling
+    R theta_c, fG, fy0, fV, dt_base;
+};
+
+// Correctly rounded reciprocal (the same value as 1/x under IEEE division)
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+// 1/sqrt(x): the CUDA single-precision rsqrtf (within 2 ulp) for FP32, exact
+// division of a correctly rounded sqrt for FP64
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
+
+// ---------------------------------------------------------------------------
+// storage conversion
+// ---------------------------------------------------------------------------
+template <typename ST> struct Cvt;
+template <> struct Cvt<double> {
+    static __device__ __forceinline__ double ld(double v) { return v; }
+    template <typename R> static __device__ __forceinline__ double st(R v) { return (double)v; }
+};
+template <> struct Cvt<float> {
+    static __device__ __forceinline__ float ld(float v) { return v; }
+    template <typename R> static __device__ __forceinline__ float st(R v) { return (float)v; }
+};
+template <> struct Cvt<__half> {
+    static __device__ __forceinline__ float ld(__half v) { return __half2float(v); }
+    template <typename R> static __device__ __forceinline__ __half st(R v) { return __float2half_rn((float)v); }
+};
+template <> struct Cvt<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+    template <typename R> static __device__ __forceinline__ __nv_bfloat16 st(R v) { return __float2bfloat16_rn((float)v); }
+};
+
+// ---------------------------------------------------------------------------
+// boundary index maps
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrap_idx(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+// scalar ghost (zero-flux wall = mirror about the half-link wall; periodic wrap)
+__device__ __forceinline__ int scalar_map(int v, int n, int bc) {
+    if (v >= 0 && v < n) return v;
+    if (bc == BC_PERIODIC) return wrap_idx(v, n);
+    v = (v < 0) ? (-1 - v) : (2 * n - 1 - v);
+    return min(max(v, 0), n - 1);
+}
+// a node that collides: inside the domain, or a periodic image
+__device__ __forceinline__ bool resolve(int& v, int n, int bc) {
+    if (v >= 0 && v < n) return true;
+    if (bc != BC_PERIODIC) return false;
+    v = wrap_idx(v, n);
+    return true;
+}
+__device__ __forceinline__ bool outside(int v, int n) { return v < 0 || v >= n; }
+// resolve both coordinates (each is always evaluated)
+__device__ __forceinline__ bool resolve_xy(int& x, int& y, int nx, int ny, int bcx, int bcy) {
+    const bool a = resolve(x, nx, bcx);
+    const bool b = resolve(y, ny, bcy);
+    return a && b;
+}
+
+// isotropic gradient g_a = 3 sum_i w_i e_ia s(x + e_i) on a shared tile
+template <typename R, int GX>
+__device__ __forceinline__ void iso_grad(const R (*s)[GX], int cx, int cy, R& gx, R& gy) {
+    const R E = s[cy][cx + 1], Wv = s[cy][cx - 1], N = s[cy + 1][cx], S = s[cy - 1][cx];
+    const R NE = s[cy + 1][cx + 1], NW = s[cy + 1][cx - 1], SE = s[cy - 1][cx + 1], SW = s[cy - 1][cx - 1];
+    gx = (E - Wv) * (R(1) / R(3)) + (NE - NW + SE - SW) * (R(1) / R(12));
+    gy = (N - S) * (R(1) / R(3)) + (NE + NW - SE - SW) * (R(1) / R(12));
+}
+
+// Eq. 2 and Eq. 3 (N = 16 eps a_s g_x g_y^2 (g_x^2 - g_y^2)/|g|^4, y by symmetry)
+template <typename R>
+__device__ __forceinline__ void aniso(R gx, R gy, R eps, R& as, R& Nx, R& Ny) {
+    const R gx2 = gx * gx, gy2 = gy * gy, g2 = gx2 + gy2;
+    if (g2 <= R(1e-12)) { as = R(1); Nx = R(0); Ny = R(0); return; }
+    const R inv = rcp(g2), inv2 = inv * inv;
+    as = R(1) - R(3) * eps + R(4) * eps * (gx2 * gx2 + gy2 * gy2) * inv2;
+    const R t = R(16) * eps * as * inv2;
+    Nx = t * gx * gy2 * (gx2 - gy2);
+    Ny = t * gy * gx2 * (gy2 - gx2);
+}
+
+// f*_i = w_i A + 3 w_i (e_i . b) + (e_i . c): the scalar collision of Eq. 14
+// with S of Eq. 23 in closed form (columns 3 and 5 of M^-1 are e_x/6, e_y/6),
+// A = chi + dt Q, b = j_eq = first moment of f_eq, c = (1 - s) j_neq / 6.
+template <typename R, int HY, int HX>
+__device__ __forceinline__ void put_scalar_post(R (*sp)[HY][HX], int ly, int lx, R A, R bx, R by, R cx, R cy) {
+    const R w1 = Wt<R>::w1, w2 = Wt<R>::w2;
+    const R a1 = w1 * A, a2 = w2 * A, b1x = R(3) * w1 * bx, b1y = R(3) * w1 * by;
+    const R b2x = R(3) * w2 * bx, b2y = R(3) * w2 * by;
+    sp[0][ly][lx] = Wt<R>::w0 * A;
+    sp[1][ly][lx] = a1 + b1x + cx;
+    sp[2][ly][lx] = a1 + b1y + cy;
+    sp[3][ly][lx] = a1 - b1x - cx;
+    sp[4][ly][lx] = a1 - b1y - cy;
+    sp[5][ly][lx] = a2 + (b2x + b2y) + (cx + cy);
+    sp[6][ly][lx] = a2 + (b2y - b2x) + (cy - cx);
+    sp[7][ly][lx] = a2 - (b2x + b2y) - (cx + cy);
+    sp[8][ly][lx] = a2 + (b2x - b2y) + (cx - cy);
+}
+
+template <typename R> __device__ __forceinline__ R theta_frozen(const KP<R>& P, int y, R t) {
+    return P.theta_c + P.fG * ((R)y - P.fy0 - P.fV * t);
+}
+
+template <typename R>
+__device__ __forceinline__ void feq_flow(R rho, R ux, R uy, R c, R* f) {               // Eq. 28
+    const R ic = rcp(c), u2 = (ux * ux + uy * uy) * ic * ic;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const R eu = ((R)ex_of(i) * ux + (R)ey_of(i) * uy) * ic;
+        f[i] = wq<R>(i) * rho * (R(1) + R(3) * eu + R(4.5) * eu * eu - R(1.5) * u2);
+    }
+}
+
+__device__ __forceinline__ void atomic_max_pos(unsigned long long* slot, double v) {
+    if (v > 0.0) atomicMax(slot, (unsigned long long)__double_as_longlong(v));
+}
+
+}  // namespace lbmk

@@ -1,0 +1,366 @@
+// Fused transport update: one launch per base step for everything that
+// follows the phase update -- the phase-change transfer (Eqs. 36-39) and
+// the U, T and flow collide-stream updates that are scheduled in that step
+// (Eq. 34, workflow of Fig. 1).
+//
+// A tile needs the injected U*, T* (= U + Delta U_pc, T + Delta T_pc) on its
+// 1-node ring for the scalar collisions there; Delta U_pc needs div J on
+// that ring, i.e. J on a 2-node ring, i.e. grad phi^{q+1} there, i.e. phi^{q+1}
+// on a 3-node ring.  Each block recomputes that halo work instead of
+// exchanging it, so the injected macros never make a round trip through
+// memory: the transfer and the field updates of a base step read the
+// pre-injection U, T once and write only the final state.  Instantaneous
+// coupling only (the accumulated ablation uses the separate kernels).
+#pragma once
+#include "lbm_kernels.cuh"
+
+namespace lbmk {
+
+template <typename R, typename ST> struct TransportJob {
+    const KP<R>* P;
+    int do_tr, do_U, do_T, do_F;
+    const R* phio;                 // phi^q (transfer only)
+    const R* phi;                  // the current phase field (phi^{q+1} after a phase update)
+    const R* Uin; R* Uout;         // U macro: pre-injection in, final out
+    const R* Tin; R* Tout;
+    const ST* fUin; ST* fUout;
+    const ST* fTin; ST* fTout;
+    const ST* fFin; ST* fFout;
+    const R* ux_in; const R* uy_in; const R* rho_in;   // flow state before this step's flow update
+    R* ux_out; R* uy_out; R* rho_out;
+    unsigned long long* smax;
+    int tiles_x, tile0;
+};
+
+template <typename R, int TY> struct TransportSmem {
+    R phi[TY + 6][38];                 // phase field on the tile + 3-ring
+    R Jx[TY + 4][36], Jy[TY + 4][36];  // J on the 2-ring
+    R dphi[TY + 4][36];                // Delta phi on the 2-ring
+    R Us[TY + 4][36];                  // pre-injection U on the 2-ring
+    R Ui[TY + 2][34], Ti[TY + 2][34];  // injected U*, T* on the 1-ring
+    R fl[TY + 2][34];                  // liquid fraction on the 1-ring (flow)
+    R post[9][TY + 2][34];
+    R red[TY];
+};
+
+template <int TY>
+__device__ __forceinline__ bool interior3(int x0, int y0, int nx, int ny) {
+    return x0 >= 3 && x0 + 35 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
+}
+
+// phase field on the tile plus a 3-node ghost ring (scalar boundary rule)
+template <typename R, int TY, bool IN>
+__device__ __forceinline__ void load_phi_ring3(const KP<R>& P, const R* __restrict__ phi, R (*s)[38], int x0, int y0,
+                                               int tid) {
+    constexpr int GX = 38, GY = TY + 6, NT = 32 * TY, K = (GX * GY + NT - 1) / NT;
+    R v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int p = tid + k * NT;
+        if (p < GX * GY) {
+            int gx = x0 - 3 + p % GX, gy = y0 - 3 + p / GX;
+            if (!IN) {
+                gx = scalar_map(gx, P.nx, P.bsx);
+                gy = scalar_map(gy, P.ny, P.bsy);
+            }
+            v[k] = phi[gy * P.pitch + gx];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int p = tid + k * NT;
+        if (p < GX * GY) s[p / GX][p % GX] = v[k];
+    }
+}
+
+template <typename R, typename ST, bool DEV, int TY, bool IN>
+__device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const KP<R>& P,
+                                               const TransportJob<R, ST>& A, int x0, int y0) {
+    constexpr int TX = 32, HX = 34, NT = 32 * TY, NR = 2 * HX + 2 * TY;
+    constexpr int R2 = 36 * (TY + 4), K2 = (R2 + NT - 1) / NT;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int pl = (int)P.plane;
+    const R omk = R(1) - P.k;
+    // 1-ring items (scalar boundaries): A = own node, B = a ring node
+    int ax = x0 + tx, ay = y0 + ty;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool own = IN || (gx < P.nx && gy < P.ny);
+    const bool va = IN || resolve_xy(ax, ay, P.nx, P.ny, P.bsx, P.bsy);
+    int blx = 0, bly = 0, bx = 0, by = 0;
+    bool vb = false;
+    if (tid < NR) {
+        ring_pos<TY>(tid, blx, bly);
+        bx = x0 - 1 + blx;
+        by = y0 - 1 + bly;
+        vb = IN || resolve_xy(bx, by, P.nx, P.ny, P.bsx, P.bsy);
+    }
+    const int na = ay * P.pitch + ax, nb = by * P.pitch + bx;
+
+    // ---- prologue: every load that does not depend on shared data
+    R po[K2], us[K2];
+    int cxs[K2], cys[K2];
+    bool fxs[K2], fys[K2], v2[K2];
+    if (A.do_tr) {
+#pragma unroll
+        for (int k = 0; k < K2; ++k) {
+            const int p = tid + k * NT;
+            v2[k] = false;
+            po[k] = us[k] = R(0);
+            if (p < R2) {
+                int sx = x0 - 2 + p % 36, sy = y0 - 2 + p / 36;
+                cxs[k] = p % 36 + 1;
+                cys[k] = p / 36 + 1;
+                fxs[k] = fys[k] = false;
+                bool ok = true;
+                if (!IN) {
+                    const bool a = j_source(sx, P.nx, P.bsx, x0 - 3, cxs[k], fxs[k]);
+                    const bool b = j_source(sy, P.ny, P.bsy, y0 - 3, cys[k], fys[k]);
+                    ok = a && b && cxs[k] >= 1 && cxs[k] <= 36 && cys[k] >= 1 && cys[k] <= TY + 4;
+                }
+                v2[k] = ok;
+                if (ok) {
+                    const int node = sy * P.pitch + sx;
+                    po[k] = A.phio[node];
+                    if (P.has_U) us[k] = A.Uin[node];
+                }
+            }
+        }
+    }
+    R Ta = R(0), Tb = R(0), Ua0 = R(0), Ub0 = R(0);
+    if (P.has_T) {
+        if (va) Ta = A.Tin[na];
+        if (vb) Tb = A.Tin[nb];
+    }
+    if (!A.do_tr && P.has_U) {
+        if (va) Ua0 = A.Uin[na];
+        if (vb) Ub0 = A.Uin[nb];
+    }
+    R fa[9], fb[9];
+    if (A.do_U) {
+        if (va) load8<R, ST>(A.fUin, na, pl, fa);
+        if (vb) load8<R, ST>(A.fUin, nb, pl, fb);
+    }
+    R uxa = R(0), uya = R(0), uxb = R(0), uyb = R(0);
+    if (P.has_flow && (A.do_U || A.do_T)) {
+        if (va) { uxa = A.ux_in[na]; uya = A.uy_in[na]; }
+        if (vb) { uxb = A.ux_in[nb]; uyb = A.uy_in[nb]; }
+    }
+    load_phi_ring3<R, TY, IN>(P, A.phi, sm.phi, x0, y0, tid);
+    __syncthreads();
+
+    // ---- J^q on the 2-ring (Eqs. 36-37)
+    if (A.do_tr) {
+        const R pre = P.at_pre;
+#pragma unroll
+        for (int k = 0; k < K2; ++k) {
+            const int p = tid + k * NT;
+            if (p < R2) {
+                R jx = R(0), jy = R(0), dph = R(0);
+                if (v2[k]) {
+                    R gxv, gyv;
+                    iso_grad<R, 38>(sm.phi, cxs[k], cys[k], gxv, gyv);
+                    dph = sm.phi[cys[k]][cxs[k]] - po[k];
+                    const R g2 = gxv * gxv + gyv * gyv;
+                    if (g2 > R(1e-12)) {
+                        const R a = pre * (R(1) + omk * us[k]) * dph * rsq(g2);
+                        jx = fxs[k] ? a * gxv : -a * gxv;    // n = -grad phi / |grad phi|
+                        jy = fys[k] ? a * gyv : -a * gyv;
+                    }
+                }
+                sm.Jx[p / 36][p % 36] = jx;
+                sm.Jy[p / 36][p % 36] = jy;
+                sm.dphi[p / 36][p % 36] = dph;
+                sm.Us[p / 36][p % 36] = us[k];
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- injected U*, T* on the 1-ring (Eqs. 38-39); S_phi over the tile
+    R mydu = R(0);
+    auto inject = [&](bool v, int lx, int ly, R Tn, R U0, R& Uo, R& To) -> R {
+        R Ui = U0, Ti = Tn, adu = R(0);
+        if (v && A.do_tr) {
+            const int hx = lx + 1, hy = ly + 1;      // 2-ring coordinates
+            const R div = (sm.Jx[hy][hx + 1] - sm.Jx[hy][hx - 1] + sm.Jy[hy + 1][hx] - sm.Jy[hy - 1][hx]) * (R(1) / R(3)) +
+                          ((sm.Jx[hy + 1][hx + 1] + sm.Jy[hy + 1][hx + 1]) + (sm.Jy[hy + 1][hx - 1] - sm.Jx[hy + 1][hx - 1]) -
+                           (sm.Jx[hy - 1][hx - 1] + sm.Jy[hy - 1][hx - 1]) + (sm.Jx[hy - 1][hx + 1] - sm.Jy[hy - 1][hx + 1])) *
+                              (R(1) / R(12));
+            const R pn = sm.phi[ly + 2][lx + 2];
+            const R dph = sm.dphi[hy][hx];
+            if (P.has_U) {
+                const R Us = sm.Us[hy][hx];
+                const R dU = ((R(1) + omk * Us) * dph - R(2) * div) * rcp((R(1) + P.k) - omk * pn);   // Eq. 38
+                Ui = Us + dU;                                                                      // Eq. 39
+                adu = fabs(dU);
+            }
+            if (P.has_T) {
+                const R rc = R(0.5) * (R(1) + pn) * P.cS + R(0.5) * (R(1) - pn) * P.cL;
+                Ti = Tn + P.rhoL_Lh * dph * rcp(R(2) * rc);                                        // Eq. 38
+            }
+        }
+        Uo = Ui;
+        To = Ti;
+        return adu;
+    };
+    R Uia, Tia, Uib = R(0), Tib = R(0);
+    mydu = inject(va, tx + 1, ty + 1, Ta, Ua0, Uia, Tia);
+    if (tid < NR) inject(vb, blx, bly, Tb, Ub0, Uib, Tib);
+    sm.Ui[ty + 1][tx + 1] = Uia;
+    sm.Ti[ty + 1][tx + 1] = Tia;
+    if (tid < NR) {
+        sm.Ui[bly][blx] = Uib;
+        sm.Ti[bly][blx] = Tib;
+    }
+    if (own) {
+        const int node = gy * P.pitch + gx;
+        if (P.has_U && !A.do_U) A.Uout[node] = Uia;     // fields not updated this step keep the injection
+        if (P.has_T && !A.do_T) A.Tout[node] = Tia;
+    } else {
+        mydu = R(0);
+    }
+    if (A.do_tr && P.has_U) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mydu = fmax(mydu, __shfl_xor_sync(0xffffffffu, mydu, o));
+        if ((tid & 31) == 0) sm.red[tid >> 5] = mydu;
+    }
+    __syncthreads();
+    if (A.do_tr && P.has_U && tid == 0) {
+        R m = R(0);
+        for (int w = 0; w < NT / 32; ++w) m = fmax(m, sm.red[w]);
+        atomic_max_pos(&A.smax[0], (double)m);
+        atomic_max_pos(&A.smax[1], (double)m);
+    }
+    const Walls ws = walls_of<IN>(gx, gy, P.nx, P.ny, P.bsx, P.bsy);
+
+    // ---- scalar updates (Eqs. 7-8, 10-12 tr parts; 14, 19-20, 23-25, 40)
+    auto scalar_stream = [&](ST* __restrict__ fout, R* __restrict__ mac_out) {
+        if (!own) return;
+        const int node = gy * P.pitch + gx;
+        R fn[9], sum = R(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            fn[i] = ws.hit(i) ? sm.post[opp_of(i)][ty + 1][tx + 1] : sm.post[i][ty + 1 - ey_of(i)][tx + 1 - ex_of(i)];
+            sum += fn[i];
+        }
+        mac_out[node] = sum;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) fout[node + (i - 1) * pl] = Cvt<ST>::st(DEV ? fn[i] - wq<R>(i) * sum : fn[i]);
+    };
+    if (A.do_U) {
+        if (va) scalar_collide<R, TY, 0, 38, 2>(P, sm.phi, sm.post, tx + 1, ty + 1, Uia, mom_x(fa), mom_y(fa), uxa, uya);
+        if (vb) scalar_collide<R, TY, 0, 38, 2>(P, sm.phi, sm.post, blx, bly, Uib, mom_x(fb), mom_y(fb), uxb, uyb);
+        __syncthreads();
+        scalar_stream(A.fUout, A.Uout);
+        __syncthreads();
+    }
+    if (A.do_T) {
+        if (va) load8<R, ST>(A.fTin, na, pl, fa);
+        if (vb) load8<R, ST>(A.fTin, nb, pl, fb);
+        if (va) scalar_collide<R, TY, 1, 38, 2>(P, sm.phi, sm.post, tx + 1, ty + 1, Tia, mom_x(fa), mom_y(fa), uxa, uya);
+        if (vb) scalar_collide<R, TY, 1, 38, 2>(P, sm.phi, sm.post, blx, bly, Tib, mom_x(fb), mom_y(fb), uxb, uyb);
+        __syncthreads();
+        scalar_stream(A.fTout, A.Tout);
+        __syncthreads();
+    }
+
+    // ---- flow update (Eqs. 27-33), flow boundaries
+    if (A.do_F) {
+        const R c = P.cF, dt = P.dtF;
+        int fxa = x0 + tx, fya = y0 + ty, fxb = x0 - 1 + blx, fyb = y0 - 1 + bly;
+        const bool fva = IN || resolve_xy(fxa, fya, P.nx, P.ny, P.bfx, P.bfy);
+        bool fvb = false;
+        if (tid < NR) fvb = IN || resolve_xy(fxb, fyb, P.nx, P.ny, P.bfx, P.bfy);
+        const int fna = fya * P.pitch + fxa, fnb = fyb * P.pitch + fxb;
+        R ra = R(1), rb = R(1), vxa = R(0), vya = R(0), vxb = R(0), vyb = R(0);
+        if (fva) {
+            load8<R, ST>(A.fFin, fna, pl, fa);
+            ra = A.rho_in[fna]; vxa = A.ux_in[fna]; vya = A.uy_in[fna];
+        }
+        if (fvb) {
+            load8<R, ST>(A.fFin, fnb, pl, fb);
+            rb = A.rho_in[fnb]; vxb = A.ux_in[fnb]; vyb = A.uy_in[fnb];
+        }
+        if (DEV) {
+            R ref[9];
+            if (fva) { feq_flow<R>(ra, vxa, vya, c, ref);
+#pragma unroll
+                for (int i = 1; i < 9; ++i) fa[i] += ref[i]; }
+            if (fvb) { feq_flow<R>(rb, vxb, vyb, c, ref);
+#pragma unroll
+                for (int i = 1; i < 9; ++i) fb[i] += ref[i]; }
+        }
+        // liquid fraction of the 1-ring positions: from the staged phase field
+        // where the position lies inside the lattice, else (a periodic image
+        // under the flow's own boundary rule) from the node it wraps to
+        if (fva) {
+            const bool inside = IN || (fxa == x0 + tx && fya == y0 + ty);
+            sm.fl[ty + 1][tx + 1] = R(0.5) * (R(1) - (inside ? sm.phi[ty + 3][tx + 3] : A.phi[fna]));
+            flow_collide<R, TY>(P, sm.post, tx + 1, ty + 1, fa, ra);
+        }
+        if (fvb) {
+            const bool inside = IN || (fxb == x0 - 1 + blx && fyb == y0 - 1 + bly);
+            sm.fl[bly][blx] = R(0.5) * (R(1) - (inside ? sm.phi[bly + 2][blx + 2] : A.phi[fnb]));
+            flow_collide<R, TY>(P, sm.post, blx, bly, fb, rb);
+        }
+        __syncthreads();
+        if (own) {
+            const int node = gy * P.pitch + gx;
+            auto pulled = [&](int i, int hx, int hy, int gxn, int gyn) -> R {
+                const int o = opp_of(i);
+                if (!IN) {
+                    const int sx = gxn - ex_of(i), sy = gyn - ey_of(i);
+                    const bool blocked = (P.bfx != BC_PERIODIC && outside(sx, P.nx)) ||
+                                         (P.bfy != BC_PERIODIC && outside(sy, P.ny));
+                    if (blocked) return sm.post[o][hy][hx];
+                }
+                const R fLm = R(0.5) * (sm.fl[hy - ey_of(i)][hx - ex_of(i)] + sm.fl[hy][hx]);
+                return fLm * sm.post[i][hy - ey_of(i)][hx - ex_of(i)] + (R(1) - fLm) * sm.post[o][hy][hx];
+            };
+            R fn[9];
+            const int hx = tx + 1, hy = ty + 1;
+            if (!IN && P.bfx == BC_INLET_OUTFLOW && gx == P.nx - 1) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fn[i] = pulled(i, hx - 1, hy, gx - 1, gy);   // f(L-1) = f(L-2)
+            } else if (!IN && P.bfx == BC_INLET_OUTFLOW && gx == 0) {
+                R rho1 = R(0);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) rho1 += pulled(i, hx + 1, hy, gx + 1, gy);
+                feq_flow<R>(rho1, P.u_in, R(0), c, fn);                                  // f = f_eq(rho(1), u_in)
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fn[i] = pulled(i, hx, hy, gx, gy);
+            }
+            R rho = R(0);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) rho += fn[i];
+            const R irho = rcp(rho);
+            const R ux = (c * mom_x(fn) + R(0.5) * dt * P.Fbx) * irho, uy = (c * mom_y(fn) + R(0.5) * dt * P.Fby) * irho;
+            A.rho_out[node] = rho;
+            A.ux_out[node] = ux;
+            A.uy_out[node] = uy;
+            if (DEV) {
+                R ref[9];
+                feq_flow<R>(rho, ux, uy, c, ref);
+#pragma unroll
+                for (int i = 1; i < 9; ++i) A.fFout[node + (i - 1) * pl] = Cvt<ST>::st(fn[i] - ref[i]);
+            } else {
+#pragma unroll
+                for (int i = 1; i < 9; ++i) A.fFout[node + (i - 1) * pl] = Cvt<ST>::st(fn[i]);
+            }
+        }
+    }
+}
+
+template <typename R, typename ST, bool DEV, int TY>
+__global__ void __launch_bounds__(32 * TY) k_transport_batch(const TransportJob<R, ST>* __restrict__ jobs, int njobs) {
+    extern __shared__ __align__(16) unsigned char transport_smem[];
+    TransportSmem<R, TY>& sm = *reinterpret_cast<TransportSmem<R, TY>*>(transport_smem);
+    int x0, y0;
+    const TransportJob<R, ST>& j = job_of_block(jobs, njobs, blockIdx.x, x0, y0, TY);
+    const KP<R>& P = *j.P;
+    if (interior3<TY>(x0, y0, P.nx, P.ny)) transport_tile<R, ST, DEV, TY, true>(sm, P, j, x0, y0);
+    else transport_tile<R, ST, DEV, TY, false>(sm, P, j, x0, y0);
+}
+
+}  // namespace lbmk

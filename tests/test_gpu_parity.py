@@ -112,6 +112,28 @@ def test_graphs_and_chunking_bitwise_identical():
         assert np.array_equal(a[k], b[k]), k
 
 
+@pytest.mark.parametrize("fuse", [True, False])
+def test_half_period_graphs_bitwise(fuse):
+    """Graph replays of either half of the ping-pong period, entered from any
+    phase of the schedule (advance(2) with update factors (1, 1, 2, 2); a
+    3-step chunk shifts the phase), give exactly the eager result."""
+    import paper_2609_25670_b300 as lbm
+    wl = W.thermosolutal_convection(n=64, R=6.0, N=(1, 1, 2, 2))
+    chunks = [2] * 7 + [3] + [2] * 6 + [1] + [4] * 3 + [2]
+    outs = []
+    for graphs in (True, False):
+        sim = lbm.Simulation(wl.params, precision="f32")
+        sim.set_fusion(fuse)
+        sim.set_graphs(graphs)
+        sim.init_fields(wl.fields)
+        for c in chunks:
+            sim.advance(c)
+        outs.append({k: sim.field(k) for k in active(wl.params)})
+        sim.close()
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
 def test_fp32_thermosolutal_1000_steps():
     """FP32 storage and arithmetic against the FP64 oracle after 1000 steps."""
     wl = W.thermosolutal_convection(n=128, R=8.0)
@@ -134,24 +156,51 @@ def test_init_seed_matches_generator():
     sim.close()
 
 
-def test_tile_variants_bitwise_identical():
-    """Every node's update is the same arithmetic whichever tile shape holds
-    it, so autotuned tile shapes cannot change the result."""
+UPDATE_KINDS = ("phase", "transfer", "scalar_U", "scalar_T", "flow", "transport")
+
+
+@pytest.mark.parametrize("ty", [4, 8, 16])
+def test_every_tile_shape_matches_oracle_fp64(ty):
+    """Each compiled tile height is a correct implementation on its own:
+    FP64, ragged 80 x 70 lattice (edge and interior tiles), all fields."""
+    import paper_2609_25670_b300 as lbm
+    wl = W.thermosolutal_convection(n=80, R=8.0)
+    p = wl.params
+    p.ny, p.tip_cy = 70, 35
+    f = W.base_fields(p, W.circle_seed(80, 70, 40, 35, 8.0, p.W0), U0=0.0, T0=-0.55)
+    sim = lbm.Simulation(p, precision="f64")
+    for k in UPDATE_KINDS:
+        sim.set_tile(k, ty)
+    sim.init_fields(f)
+    sim.advance(60)
+    got = {k: sim.field(k) for k in active(p)}
+    sim.close()
+    o = run_oracle(p, f, 60)
+    for k in got:
+        assert np.abs(got[k] - o[k]).max() < 1e-11, k
+
+
+def test_autotuned_tiles_agree_to_rounding():
+    """Different tile shapes (and the interior / edge paths they select) are
+    different compilations of the same arithmetic: they agree to
+    floating-point contraction rounding; a fixed tile choice is bitwise
+    reproducible."""
     import paper_2609_25670_b300 as lbm
     wl = W.thermosolutal_convection(n=96, R=8.0)
     outs = []
-    for tune in (False, True):
+    for tune in (False, True, False):
         sim = lbm.Simulation(wl.params, precision="f32")
         sim.init_fields(wl.fields)
         sim.advance(10)
         if tune:
             ch = sim.autotune(reps=2)
-            assert set(ch[k] for k in ("phase", "transfer", "scalar_U", "scalar_T", "flow")) <= {4, 8, 16}
+            assert set(ch[k] for k in UPDATE_KINDS) <= {4, 8, 16}
         sim.advance(30)
         outs.append({k: sim.field(k) for k in active(wl.params)})
         sim.close()
     for k in outs[0]:
-        assert np.array_equal(outs[0][k], outs[1][k]), k
+        assert np.array_equal(outs[0][k], outs[2][k]), k           # same tiles: bitwise
+        assert np.abs(outs[0][k] - outs[1][k]).max() < 1e-5, k    # FP32 rounding, 40 steps
 
 
 @pytest.mark.parametrize("prec,tol", [("f16dev", 5e-3), ("bf16dev", 4e-2)])
@@ -161,3 +210,43 @@ def test_deviation_storage_thermosolutal(prec, tol):
     wl = W.thermosolutal_convection(n=128, R=8.0)
     g, o, err = _check(wl.params, wl.fields, 1000, tol, precision=prec)
     assert abs(g["diag"]["M_C"] - o["diag"]["M_C"]) / o["diag"]["M_C"] < 1e-5
+
+
+def test_unfused_path_fp64():
+    """The one-launch-per-stage path (transfer, U, T, flow separately) against
+    the oracle, FP64, ragged lattice, all fields, multirate (1, 1, 2, 2)."""
+    import paper_2609_25670_b300 as lbm
+    wl = W.thermosolutal_convection(n=80, R=8.0)
+    p = wl.params
+    p.ny, p.tip_cy = 70, 35
+    f = W.base_fields(p, W.circle_seed(80, 70, 40, 35, 8.0, p.W0), U0=0.0, T0=-0.55)
+    sim = lbm.Simulation(p, precision="f64")
+    sim.set_fusion(False)
+    sim.init_fields(f)
+    sim.advance(120)
+    got = {k: sim.field(k) for k in active(p)}
+    counts = sim.launch_counts()
+    sim.close()
+    assert counts["transport"] == 0 and counts["transfer"] > 0
+    o = run_oracle(p, f, 120)
+    for k in got:
+        assert np.abs(got[k] - o[k]).max() < 1e-10, k
+
+
+def test_fused_and_unfused_agree_fp32():
+    """One fused launch per base step vs one launch per stage: the same
+    arithmetic in different compilations (contraction rounding only)."""
+    import paper_2609_25670_b300 as lbm
+    wl = W.thermosolutal_convection(n=96, R=8.0)
+    outs = []
+    for fuse in (True, False):
+        sim = lbm.Simulation(wl.params, precision="f32")
+        sim.set_fusion(fuse)
+        sim.init_fields(wl.fields)
+        sim.advance(40)
+        outs.append({k: sim.field(k) for k in active(wl.params)})
+        n = sim.launch_counts()
+        assert (n["transport"] > 0) == fuse
+        sim.close()
+    for k in outs[0]:
+        assert np.abs(outs[0][k] - outs[1][k]).max() < 1e-5, k
