@@ -40,40 +40,53 @@ STEP_BASE = 2          # base steps per bench step (one schedule period)
 METRIC = "coupled-field MLUPS"
 UNIT = "MLUPS"
 
-# algorithmic bytes per node of one launch, FP32 storage (8 stored
-# populations read + written, each macro read / written once)
-ALGO_BYTES = {
-    "phase": 8 * 4 * 2 + 4 + 4 + 4 + 4,        # pops R+W, phi^q R, U R, T R, phi^{q+1} W = 80
-    "transfer": 6 * 4,                          # phi^q, phi^{q+1}, U, T R; U, T W = 24
-    "scalar_U": 8 * 4 * 2 + 4 + 4 + 4 + 8,      # pops, U R+W, phi R, u R = 84
-    "scalar_T": 8 * 4 * 2 + 4 + 4 + 4 + 8,      # = 84
-    "flow": 8 * 4 * 2 + 4 + 12 + 12,            # pops, phi R, (rho, ux, uy) R + W = 92
-}
+# element sizes of the stored populations and of the macroscopic fields per
+# storage precision (16-bit storage keeps FP32 macros)
+POP_BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
+MACRO_BYTES = {"f64": 8, "f32": 4, "f16dev": 4, "bf16dev": 4}
 
 
-def transport_bytes(tr, u, t, f, has_T=True, has_flow=True):
-    """Algorithmic bytes per node of one fused transport launch (FP32): the
-    transfer reads phi^q, phi^{q+1}, U, T once; each scheduled field reads and
-    writes its 8 populations and writes its macro; a macro whose field does
-    not update in this step is written back with the injection."""
-    b = 4                                       # phi (current) R
+def algo_bytes(prec="f32"):
+    """Algorithmic bytes per node of one launch of each update kernel: the 8
+    stored populations read and written once, each macro read / written once."""
+    pb, m = POP_BYTES[prec], MACRO_BYTES[prec]
+    pops = 2 * 8 * pb
+    return {
+        "phase": pops + 4 * m,                  # pops R+W, phi^q R, U R, T R, phi^{q+1} W
+        "transfer": 6 * m,                      # phi^q, phi^{q+1}, U, T R; U, T W
+        "scalar_U": pops + 5 * m,               # pops, U R+W, phi R, u R (2)
+        "scalar_T": pops + 5 * m,
+        "flow": pops + 7 * m,                   # pops, phi R, (rho, ux, uy) R + W
+    }
+
+
+ALGO_BYTES = algo_bytes("f32")
+
+
+def transport_bytes(tr, u, t, f, has_T=True, has_flow=True, prec="f32"):
+    """Algorithmic bytes per node of one fused transport launch: the transfer
+    reads phi^q, phi^{q+1}, U, T once; each scheduled field reads and writes
+    its 8 populations and writes its macro; a macro whose field does not
+    update in this step is written back with the injection."""
+    m, pops = MACRO_BYTES[prec], 2 * 8 * POP_BYTES[prec]
+    b = m                                       # phi (current) R
     if tr:
-        b += 4 + 4 + (4 if has_T else 0)        # phi^q, U, T R
-        b += (0 if u else 4) + (0 if (t or not has_T) else 4)   # injected macros carried over
+        b += m + m + (m if has_T else 0)        # phi^q, U, T R
+        b += (0 if u else m) + (0 if (t or not has_T) else m)   # injected macros carried over
     else:
-        b += (4 if u else 0) + (4 if t else 0)
+        b += (m if u else 0) + (m if t else 0)
     if (u or t) and has_flow:
-        b += 8                                  # u for the scalar equilibria
+        b += 2 * m                              # u for the scalar equilibria
     if u:
-        b += 64 + 4
+        b += pops + m
     if t:
-        b += 64 + 4
+        b += pops + m
     if f:
-        b += 64 + 12 + 12 - (8 if (u or t) else 0)   # rho, u R (u shared with the scalars) + W
+        b += pops + 6 * m - (2 * m if (u or t) else 0)   # rho, u R (u shared with the scalars) + W
     return b
 
 
-def period_bytes(p):
+def period_bytes(p, prec="f32"):
     """(total transport bytes per node over one schedule period, launches)."""
     from math import gcd
     L = 1
@@ -86,7 +99,7 @@ def period_bytes(p):
         t = p.has_T and (k + 1) % p.N_T == 0
         f = p.has_flow and (k + 1) % p.N_F == 0
         if tr or u or t or f:
-            tot += transport_bytes(tr, u, t, f, p.has_T, p.has_flow)
+            tot += transport_bytes(tr, u, t, f, p.has_T, p.has_flow, prec)
             n += 1
     return tot, n
 
@@ -107,6 +120,15 @@ def kernel_source_sha():
         with open(os.path.join(ROOT, "paper_2609_25670_b300", "csrc", nm), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def workload_label(p, prec="f32"):
+    return (f"thermosolutal free dendrite + forced convection, {p.nx}x{p.ny}, phi/U/T/flow on D2Q9, "
+            f"N=({p.N_phi},{p.N_U},{p.N_T},{p.N_F}), {STORAGE_LABEL[prec]}")
+
+
+STORAGE_LABEL = {"f64": "FP64", "f32": "FP32", "f16dev": "FP32 arithmetic, FP16 deviation storage",
+                 "bf16dev": "FP32 arithmetic, BF16 deviation storage"}
 
 
 def workload(n=None):
@@ -218,7 +240,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)",
-            "config": {"workload": "thermosolutal free dendrite + forced convection, 512x512, N=(1,1,2,2)",
+            "config": {"workload": workload_label(wl.params, args.precision or "f32"),
                        "base_steps_per_step": STEP_BASE},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": "%d steps of %d base steps on the full %d^2 lattice" % (
@@ -241,8 +263,10 @@ def run_ours(args):
     wl = workload(args.lattice)
     p = wl.params
     nodes = p.nx * p.ny
-    sim = lbm.Simulation(p, precision="f32")
-    sim.set_fusion(args.fusion == "on")
+    prec = args.precision or "f32"
+    sim = lbm.Simulation(p, precision=prec)
+    if args.fusion != "auto":
+        sim.set_fusion(args.fusion == "on")
     sim.init_fields(wl.fields)
     stream = sim.stream
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -257,10 +281,14 @@ def run_ours(args):
     for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
         sim.advance(STEP_BASE)
     tiles = sim.autotune(reps=10)
+    for spec in args.tile or []:            # fixed kernel variants (profiling runs)
+        kind, v = spec.split("=")
+        sim.set_tile(kind, int(v))
+        tiles[kind] = int(v)
     sim.advance(STEP_BASE)
     kinds = ["phase", "transfer", "scalar_U", "scalar_T", "flow", "transport"]
-    tb, tn = period_bytes(p)
-    algo = dict(ALGO_BYTES)
+    tb, tn = period_bytes(p, prec)
+    algo = algo_bytes(prec)
     algo["transport"] = tb / max(tn, 1)       # mean over the period's transport launches
     # untimed pre-pass with every kind timed, to find the dominant kernel; the
     # timed region then times only that kind (fewest event nodes in the graph)
@@ -307,7 +335,7 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = algo[dom] * nodes / avg_s / 1e9
     traffic = None
-    if args.lattice in (None, N_LATTICE) and TRAFFIC_SOURCE_SHA == kernel_source_sha():
+    if args.lattice in (None, N_LATTICE) and prec == "f32" and TRAFFIC_SOURCE_SHA == kernel_source_sha():
         traffic = TRAFFIC_PER_LAUNCH.get(dom)
 
     # end to end through the public API with pinned host buffers
@@ -331,10 +359,10 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-            "config": {"workload": f"thermosolutal free dendrite + forced convection, {p.nx}x{p.ny}, "
-                                   "phi/U/T/flow on D2Q9, N=(1,1,2,2), FP32", "base_steps_per_step": STEP_BASE,
-                       "fused_transport": args.fusion == "on",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "f64" else "f32",
+            "data": "synthetic (seeded)",
+            "config": {"workload": workload_label(p, prec), "storage": prec, "base_steps_per_step": STEP_BASE,
+                       "fused_transport": sim.fused, "fusion_choice": args.fusion,
                        "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
@@ -396,10 +424,10 @@ def run_ensemble(args):
                      "gpu_launches": int(sum(l1[k] - l0[k] for k in l1))}
     line = {"metric": METRIC + " (ensemble aggregate)", "value": res["batched"]["value"], "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["batched"]["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
-            "data": "synthetic (seeded)",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "f64" else "f32", "data": "synthetic (seeded)",
             "config": {"workload": "batched ensemble of %d thermosolutal members, sizes 128..1024, seed 4" % len(ms),
-                       "nodes": nodes, "base_steps_per_step": period, "l2": "inputs larger than L2"},
+                       "storage": prec, "nodes": nodes, "base_steps_per_step": period, "l2": "inputs larger than L2"},
             "gpu_launches": res["batched"]["gpu_launches"], "sequential": res["sequential"],
             "speedup_vs_sequential": res["batched"]["value"] / res["sequential"]["value"]}
     print(json.dumps(line), flush=True)
@@ -419,8 +447,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
-    ap.add_argument("--fusion", default="on", choices=["on", "off"],
-                    help="one fused transport launch per base step (on) or one launch per stage (off)")
+    ap.add_argument("--fusion", default="auto", choices=["auto", "on", "off"],
+                    help="one fused transport launch per base step (on), one launch per stage (off), "
+                         "or the autotuner's choice (auto)")
+    ap.add_argument("--tile", action="append", metavar="KIND=V",
+                    help="fix a kernel variant after autotuning (profiling runs): V > 0 tile height, V < 0 strip height")
     ap.add_argument("--lattice", type=int, default=None,
                     help="lattice size override for profiling runs (the reported workload is 512)")
     args = ap.parse_args()

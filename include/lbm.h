@@ -211,13 +211,18 @@ lbm_status lbm_set_graphs(lbm_handle h, int32_t enable);
  * base steps). */
 lbm_status lbm_set_batching(lbm_handle h, int32_t enable);
 
-/* enable = 1 (default): under instantaneous coupling, everything a base step
- * does after the phase update -- the phase-change transfer (Eqs. 36-39) and
- * the scheduled U, T and flow updates -- runs as one fused launch per base
- * step (LBM_K_TRANSPORT) that recomputes the transfer on the halo it needs
- * instead of storing the injected U, T.  0: one launch per stage.  The two
- * agree to floating-point contraction rounding.  Recaptures graphs. */
+/* enable = 1: under instantaneous coupling, everything a base step does
+ * after the phase update -- the phase-change transfer (Eqs. 36-39) and the
+ * scheduled U, T and flow updates -- runs as one fused launch per base step
+ * (LBM_K_TRANSPORT) that recomputes the transfer on the halo it needs instead
+ * of storing the injected U, T.  0: one launch per stage (the default until
+ * lbm_autotune has timed both).  The two agree to floating-point contraction
+ * rounding.  An explicit call fixes the choice: lbm_autotune no longer
+ * changes it.  Recaptures graphs. */
 lbm_status lbm_set_fusion(lbm_handle h, int32_t enable);
+
+/* *enabled receives 1 when base steps run the fused transport launch. */
+lbm_status lbm_get_fusion(lbm_handle h, int32_t* enabled);
 
 /* Kernel kinds for timing and launch counts. */
 enum { LBM_K_PHASE = 0, LBM_K_TRANSFER = 1, LBM_K_SCALAR_U = 2, LBM_K_SCALAR_T = 3,
@@ -241,8 +246,12 @@ lbm_status lbm_timing_read(lbm_handle h, double* ms, int64_t* count, int32_t res
  * compiled tile shape (32 x 4, 32 x 8, 32 x 16 threads) over `reps` launches on
  * the current state and keep the fastest.  The update kernels read one
  * ping-pong buffer and write the other, so the repeated launches leave the
- * simulation unchanged (the S_phi / J_U maxima are cleared).  chosen (nullable)
- * receives LBM_K_COUNT tile heights of simulation 0.  Recaptures graphs.
+ * simulation unchanged (the S_phi / J_U maxima are cleared).  Unless
+ * lbm_set_fusion was called, it also times one half schedule period both as
+ * fused transport launches and as one launch per stage (from the per-launch
+ * times, each transport stage combination the schedule uses timed once) and
+ * keeps the faster.  chosen (nullable) receives LBM_K_COUNT tile heights of
+ * simulation 0.  Recaptures graphs.
  * Errors: STATE (not initialised), CUDA. */
 lbm_status lbm_autotune(lbm_handle h, int32_t reps, int32_t* chosen);
 

@@ -31,7 +31,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSTABLE_PARAMS", 3: "OOM", 4: "CUDA", 
 EXPORTED = ["lbm_create", "lbm_init_seed", "lbm_init_fields", "lbm_advance", "lbm_fields",
             "lbm_diagnostics", "lbm_last_error", "lbm_destroy", "lbm_set_graphs", "lbm_timing_enable",
             "lbm_timing_read", "lbm_launch_counts", "lbm_device_bytes", "lbm_autotune",
-            "lbm_diagnostics_noalloc", "lbm_set_batching", "lbm_set_tile", "lbm_set_fusion"]
+            "lbm_diagnostics_noalloc", "lbm_set_batching", "lbm_set_tile", "lbm_set_fusion",
+            "lbm_get_fusion"]
 
 
 class LbmError(RuntimeError):
@@ -109,6 +110,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.lbm_set_batching.argtypes = [vp, i32]
     lib.lbm_set_tile.argtypes = [vp, i32, i32]
     lib.lbm_set_fusion.argtypes = [vp, i32]
+    lib.lbm_get_fusion.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.lbm_diagnostics_noalloc.argtypes = [C.POINTER(lbm_params)] + [vp] * 6 + [C.POINTER(lbm_diag)]
     for nm in EXPORTED:
         f = getattr(lib, nm)
@@ -254,8 +256,15 @@ class Simulation:
         self._ck(self.lib.lbm_set_tile(self.h, KERNEL_KINDS.index(kind), int(ty)))
 
     def set_fusion(self, enable: bool):
-        """One fused launch per base step after the phase update (default) or one per stage."""
+        """One fused launch per base step after the phase update, or one per
+        stage (the default until autotune() has timed both); fixes the choice."""
         self._ck(self.lib.lbm_set_fusion(self.h, 1 if enable else 0))
+
+    @property
+    def fused(self) -> bool:
+        v = C.c_int32(0)
+        self._ck(self.lib.lbm_get_fusion(self.h, C.byref(v)))
+        return bool(v.value)
 
     def set_graphs(self, enable: bool):
         self._ck(self.lib.lbm_set_graphs(self.h, 1 if enable else 0))

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", "lbm_api.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", n) for n in ("lbm_kernels.cuh", "lbm_common.cuh", "lbm_aux.cuh", "lbm_transport.cuh")] + \
+DEPS = SRC + [os.path.join(HERE, "csrc", n) for n in ("lbm_kernels.cuh", "lbm_common.cuh", "lbm_aux.cuh", "lbm_transport.cuh", "lbm_strip.cuh")] + \
     [os.path.join(ROOT, "include", "lbm.h")]
 LIB = os.path.join(HERE, "liblbm.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

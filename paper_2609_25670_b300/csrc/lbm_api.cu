@@ -17,6 +17,7 @@
 #include "../../include/lbm.h"
 #include "lbm_aux.cuh"
 #include "lbm_kernels.cuh"
+#include "lbm_strip.cuh"
 #include "lbm_transport.cuh"
 
 using namespace lbmk;
@@ -123,7 +124,8 @@ struct lbm_sim {
     std::vector<std::pair<void*, size_t>> blocks;
     size_t bytes = 0;
     bool graphs = true;
-    bool fuse = true;                    // fused transport launch (instantaneous coupling)
+    bool fuse = false;                   // fused transport launch (instantaneous coupling)
+    bool fuse_auto = true;               // the autotuner may switch `fuse` (until set explicitly)
     bool cap_single = false;             // recording the transport jobs of a single simulation's period
     int cap_tcount = 0;                  // transport launches captured so far in that period
     uint32_t timing_mask = 0;
@@ -188,6 +190,9 @@ lbm_status dev_alloc(lbm_sim* h, size_t bytes, void** out) {
     h->blocks.push_back({p, bytes});
     h->bytes += bytes;
     *out = p;
+    // zero once: row padding and unused halves never hold stale non-finite bits
+    cudaError_t e = cudaMemsetAsync(p, 0, bytes, h->stream);
+    if (e != cudaSuccess) return fail(h, LBM_E_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     return LBM_OK;
 }
 
@@ -212,7 +217,8 @@ lbm_status validate(const lbm_params* p, std::string& why) {
     if (p->struct_version != LBM_PARAMS_VERSION) return bad("struct_version != LBM_PARAMS_VERSION");
     if (p->nx < 4 || p->ny < 4) return bad("nx and ny must be >= 4");
     // the update kernels address population planes with 32-bit offsets
-    if ((int64_t)p->nx * p->ny * 8 >= (int64_t)1 << 31) return bad("nx * ny must be below 2^28 nodes");
+    if ((((int64_t)p->nx + 31) / 32 * 32) * p->ny * 8 >= (int64_t)1 << 31)
+        return bad("nx * ny must be below 2^28 nodes (rows padded to 32)");
     if (p->fields & ~(uint32_t)(LBM_FIELD_U | LBM_FIELD_T | LBM_FIELD_FROZEN_T | LBM_FIELD_FLOW)) return bad("unknown fields bit");
     if ((p->fields & LBM_FIELD_T) && (p->fields & LBM_FIELD_FROZEN_T)) return bad("T and FROZEN_T are exclusive");
     if (p->bc_scalar_x < 0 || p->bc_scalar_x > 1 || p->bc_scalar_y < 0 || p->bc_scalar_y > 1)
@@ -342,6 +348,37 @@ lbm_status collect_pending(lbm_sim* h) {
 template <int TYV>
 inline dim3 grid_of(const SimState& s) { return dim3((s.nx + TX - 1) / TX, (s.ny + TYV - 1) / TYV); }
 
+// Kernel variants of an update kind: v in {4, 8, 16} is a 32 x v
+// shared-memory tile (blocks of 32 x v threads), v < 0 a warp strip of
+// height -v (blocks of NWS strips, 32 NWS threads), v = VS + h vector strips
+// of height h over the interior with 1-wide strips on the frame (one 1-D
+// launch).  Blocks of one launch over an nx x ny lattice:
+constexpr int VS = 1000;
+inline void blocks_of(int v, int nx, int ny, int& bx, int& by) {
+    if (v > VS) {
+        bx = vs_blocks(nx, ny, v - VS);
+        by = 1;
+    } else if (v > 0) {
+        bx = (nx + TX - 1) / TX;
+        by = (ny + v - 1) / v;
+    } else {
+        const int strips = (nx + SW - 1) / SW;
+        bx = (strips + NWS - 1) / NWS;
+        by = (ny - v - 1) / (-v);
+    }
+}
+inline dim3 grid_v(const SimState& s, int v) {
+    int bx, by;
+    blocks_of(v, s.nx, s.ny, bx, by);
+    return dim3(bx, by);
+}
+inline bool has_strips(int kind) { return kind == LBM_K_SCALAR_U || kind == LBM_K_SCALAR_T; }
+inline bool valid_variant(int kind, int v) {
+    return v == 4 || v == 8 || v == 16 ||
+           (has_strips(kind) && (v == -4 || v == -8 || v == -16 || v == -32 || v == VS + 8 || v == VS + 16 ||
+                                 v == VS + 32));
+}
+
 // Update-kernel launch on the handle's stream, with dynamic shared memory
 // (opted in above the 48 KB default when a kernel needs more).
 template <typename... KArgs, typename... Args>
@@ -368,15 +405,29 @@ inline void launch_ex(lbm_sim* h, void (*kern)(KArgs...), dim3 g, dim3 b, Args..
         case 16: { constexpr int TYV = 16; BODY; } break; \
         default: { constexpr int TYV = 8; BODY; } break;  \
     }
+#define LBM_VS_SWITCH(sel, BODY)                            \
+    switch (sel) {                                          \
+        case VS + 8: { constexpr int HV = 8; BODY; } break;    \
+        case VS + 32: { constexpr int HV = 32; BODY; } break;  \
+        default: { constexpr int HV = 16; BODY; } break;       \
+    }
+#define LBM_STRIP_SWITCH(sel, BODY)                      \
+    switch (sel) {                                       \
+        case -4: { constexpr int HV = 4; BODY; } break;     \
+        case -8: { constexpr int HV = 8; BODY; } break;     \
+        case -32: { constexpr int HV = 32; BODY; } break;   \
+        default: { constexpr int HV = 16; BODY; } break;    \
+    }
 
 // Batched ensemble: instead of launching, append this member's job (the same
 // arguments a single launch would get) to the table of `kind`.
 template <typename J>
 void push_job(lbm_sim* h, int kind, J& j, const SimState& s) {
-    const int tyv = h->batch_tile[kind];
-    j.tiles_x = (s.nx + TX - 1) / TX;
+    int bx, by;
+    blocks_of(h->batch_tile[kind], s.nx, s.ny, bx, by);
+    j.tiles_x = bx;
     j.tile0 = h->rec_tiles[kind];
-    h->rec_tiles[kind] += j.tiles_x * ((s.ny + tyv - 1) / tyv);
+    h->rec_tiles[kind] += bx * by;
     const unsigned char* b = (const unsigned char*)&j;
     h->rec[kind].insert(h->rec[kind].end(), b, b + sizeof(J));
     h->rec_jobs[kind]++;
@@ -440,12 +491,28 @@ void launch_batch(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, 
                                             (const TransferJob<R>*)jobs, njobs)));
             break;
         case LBM_K_SCALAR_U:
-            LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar_batch<R, ST, DEV, TYV, 0>, g, dim3(TX, TYV),
-                                            (const ScalarJob<R, ST>*)jobs, njobs)));
+            if (tysel > VS)
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs_batch<R, ST, DEV, HV, 0>, g, dim3(32 * VNW),
+                                                     (size_t)VNW * VSRing<R>::BYTES, (const ScalarJob<R, ST>*)jobs,
+                                                     njobs)))
+            else if (tysel < 0)
+                LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip_batch<R, ST, DEV, HV, 0>, g, dim3(32 * NWS),
+                                                   (const ScalarJob<R, ST>*)jobs, njobs)))
+            else
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar_batch<R, ST, DEV, TYV, 0>, g, dim3(TX, TYV),
+                                                (const ScalarJob<R, ST>*)jobs, njobs)))
             break;
         case LBM_K_SCALAR_T:
-            LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar_batch<R, ST, DEV, TYV, 1>, g, dim3(TX, TYV),
-                                            (const ScalarJob<R, ST>*)jobs, njobs)));
+            if (tysel > VS)
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs_batch<R, ST, DEV, HV, 1>, g, dim3(32 * VNW),
+                                                     (size_t)VNW * VSRing<R>::BYTES, (const ScalarJob<R, ST>*)jobs,
+                                                     njobs)))
+            else if (tysel < 0)
+                LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip_batch<R, ST, DEV, HV, 1>, g, dim3(32 * NWS),
+                                                   (const ScalarJob<R, ST>*)jobs, njobs)))
+            else
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar_batch<R, ST, DEV, TYV, 1>, g, dim3(TX, TYV),
+                                                (const ScalarJob<R, ST>*)jobs, njobs)))
             break;
         case LBM_K_FLOW:
             LBM_TY_SWITCH(tysel, (launch_ex(h, k_flow_batch<R, ST, DEV, TYV>, g, dim3(TX, TYV),
@@ -499,15 +566,42 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
                 s.acc_reset_T ? 1 : 0, s.smax)));
             break;
         case LBM_K_SCALAR_U:
-            LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar<R, ST, DEV, TYV, 0>, grid_of<TYV>(s), dim3(TX, TYV),
-                P, (const ST*)s.pops[FU][s.cur_pop[FU]], (ST*)s.pops[FU][1 - s.cur_pop[FU]], (const R*)s.U[s.cur_U],
-                (R*)s.U[1 - s.cur_U], (const R*)s.accU, phi_now, uxc, uyc, s.smax)));
+        case LBM_K_SCALAR_T: {
+            const bool isU = kind == LBM_K_SCALAR_U;
+            const int f = isU ? FU : FT;
+            const ST* fin = (const ST*)s.pops[f][s.cur_pop[f]];
+            ST* fout = (ST*)s.pops[f][1 - s.cur_pop[f]];
+            void* const* mac = isU ? s.U : s.T;
+            const int cm = isU ? s.cur_U : s.cur_T;
+            const R* acc = (const R*)(isU ? s.accU : s.accT);
+            if (tysel > VS) {
+                const size_t sm = (size_t)VNW * VSRing<R>::BYTES;
+                if (isU)
+                    LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs<R, ST, DEV, HV, 0>, grid_v(s, tysel),
+                        dim3(32 * VNW), sm, P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc,
+                        s.smax)))
+                else
+                    LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs<R, ST, DEV, HV, 1>, grid_v(s, tysel),
+                        dim3(32 * VNW), sm, P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc,
+                        s.smax)))
+            } else if (tysel < 0) {
+                if (isU)
+                    LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip<R, ST, DEV, HV, 0>, grid_v(s, tysel),
+                        dim3(32 * NWS), P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc,
+                        s.smax)))
+                else
+                    LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip<R, ST, DEV, HV, 1>, grid_v(s, tysel),
+                        dim3(32 * NWS), P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc,
+                        s.smax)))
+            } else if (isU) {
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar<R, ST, DEV, TYV, 0>, grid_of<TYV>(s), dim3(TX, TYV),
+                    P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc, s.smax)));
+            } else {
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar<R, ST, DEV, TYV, 1>, grid_of<TYV>(s), dim3(TX, TYV),
+                    P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc, s.smax)));
+            }
             break;
-        case LBM_K_SCALAR_T:
-            LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar<R, ST, DEV, TYV, 1>, grid_of<TYV>(s), dim3(TX, TYV),
-                P, (const ST*)s.pops[FT][s.cur_pop[FT]], (ST*)s.pops[FT][1 - s.cur_pop[FT]], (const R*)s.T[s.cur_T],
-                (R*)s.T[1 - s.cur_T], (const R*)s.accT, phi_now, uxc, uyc, s.smax)));
-            break;
+        }
         case LBM_K_FLOW: {
             const int c = s.cur_pop[FF];
             LBM_TY_SWITCH(tysel, (launch_ex(h, k_flow<R, ST, DEV, TYV>, grid_of<TYV>(s), dim3(TX, TYV),
@@ -1047,7 +1141,7 @@ lbm_status lbm_create(const lbm_params* p, int32_t n_sims, const lbm_params* per
         s.p = ps[i];
         s.nx = s.p.nx;
         s.ny = s.p.ny;
-        s.pitch = s.nx;
+        s.pitch = (s.nx + 31) / 32 * 32;     // rows start on 128-byte (FP32) boundaries: vector access
         s.nn = (size_t)s.pitch * s.ny;
         s.has_U = (s.p.fields & LBM_FIELD_U) != 0;
         s.has_T = (s.p.fields & LBM_FIELD_T) != 0;
@@ -1310,7 +1404,10 @@ lbm_status lbm_set_tile(lbm_handle h, int32_t kind, int32_t ty) {
     if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
     if (kind < 0 || (kind > LBM_K_FLOW && kind != LBM_K_TRANSPORT))
         return fail(h, LBM_E_INVALID_ARG, "kind %d is not an update kernel", kind);
-    if (ty != 4 && ty != 8 && ty != 16) return fail(h, LBM_E_INVALID_ARG, "tile height %d not in {4, 8, 16}", ty);
+    if (!valid_variant(kind, ty))
+        return fail(h, LBM_E_INVALID_ARG, "variant %d is not a tile height in {4, 8, 16}%s", ty,
+                    has_strips(kind) ? ", a strip height in {-4, -8, -16, -32} or 1000 + a vector strip height in "
+                                       "{8, 16, 32}" : "");
     for (auto& s : h->sims) {
         s.tile[kind] = ty;
         drop_graph(s);
@@ -1323,6 +1420,7 @@ lbm_status lbm_set_tile(lbm_handle h, int32_t kind, int32_t ty) {
 lbm_status lbm_set_fusion(lbm_handle h, int32_t enable) {
     if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
     h->fuse = enable != 0;
+    h->fuse_auto = false;
     for (auto& s : h->sims) drop_graph(s);
     drop_batch_graph(h);
     return LBM_OK;
@@ -1349,51 +1447,100 @@ lbm_status lbm_timing_read(lbm_handle h, double* ms, int64_t* count, int32_t res
     return LBM_OK;
 }
 
+lbm_status lbm_get_fusion(lbm_handle h, int32_t* enabled) {
+    if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
+    if (!enabled) return fail(h, LBM_E_INVALID_ARG, "enabled is NULL");
+    *enabled = h->fuse ? 1 : 0;
+    return LBM_OK;
+}
+
 lbm_status lbm_autotune(lbm_handle h, int32_t reps, int32_t* chosen) {
     if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
     if (reps < 1) return fail(h, LBM_E_INVALID_ARG, "reps must be >= 1");
-    static const int variants[3] = {4, 8, 16};
+    static const int variants[10] = {4, 8, 16, -4, -8, -16, -32, VS + 8, VS + 16, VS + 32};
     cudaEvent_t a = nullptr, b = nullptr;
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
     const uint32_t mask = h->timing_mask;
     h->timing_mask = 0;
+    double cost_fused = 0.0, cost_staged = 0.0;   // per half period, summed over the simulations
+    bool choose = false;
     for (auto& s : h->sims) {
         if (!s.initialized) { cudaEventDestroy(a); cudaEventDestroy(b); h->timing_mask = mask;
                               return fail(h, LBM_E_STATE, "simulation not initialised"); }
-        const bool fused = h->fuse && !s.accumulated;
-        const bool present[LBM_K_COUNT] = {true, !s.accumulated && !fused, s.has_U && !fused, s.has_T && !fused,
-                                           s.has_flow && !fused, false, false, fused};
+        const bool can_fuse = !s.accumulated;
+        const bool pick = h->fuse_auto && can_fuse;   // time both paths and choose
+        const bool fused = h->fuse && can_fuse;
+        const bool staged = pick || !fused;
+        const bool present[LBM_K_COUNT] = {true, !s.accumulated && staged, s.has_U && staged, s.has_T && staged,
+                                           s.has_flow && staged, false, false, can_fuse && (pick || fused)};
         // one launch of `kind` with tile height v on the current state; the
-        // transport launch runs every stage the simulation has
-        auto tune_launch = [&](int kind, int v) {
+        // transport launch runs the stages in `combo` (bit 0 transfer, 1 U,
+        // 2 T, 3 flow), every stage the simulation has by default
+        const int all_stages = 1 | (s.has_U ? 2 : 0) | (s.has_T ? 4 : 0) | (s.has_flow ? 8 : 0);
+        auto tune_launch = [&](int kind, int v, int combo) {
             if (kind == LBM_K_TRANSPORT) {
                 const int keep = s.tile[kind];
                 s.tile[kind] = v;
-                transport_any(h, s, true, s.has_U, s.has_T, s.has_flow);
+                transport_any(h, s, combo & 1, (combo & 2) != 0, (combo & 4) != 0, (combo & 8) != 0);
                 s.tile[kind] = keep;
             } else {
                 launch_any(h, s, kind, v, s.clock, 0);
             }
         };
+        auto time_launch = [&](int kind, int v, int combo, float* ms) -> lbm_status {
+            tune_launch(kind, v, combo);       // warm the variant
+            CK(cudaEventRecord(a, h->stream));
+            for (int r = 0; r < reps; ++r) tune_launch(kind, v, combo);
+            CK(cudaEventRecord(b, h->stream));
+            CK(cudaEventSynchronize(b));
+            CK(cudaEventElapsedTime(ms, a, b));
+            *ms /= (float)reps;
+            return LBM_OK;
+        };
+        double best_ms[LBM_K_COUNT] = {};
         for (int kind = 0; kind < LBM_K_COUNT; ++kind) {
             if (!present[kind]) continue;
             float best = 1e30f;
             int bestv = s.tile[kind];
             for (int v : variants) {
-                tune_launch(kind, v);          // warm the variant
-                CK(cudaEventRecord(a, h->stream));
-                for (int r = 0; r < reps; ++r) tune_launch(kind, v);
-                CK(cudaEventRecord(b, h->stream));
-                CK(cudaEventSynchronize(b));
+                if (!valid_variant(kind, v)) continue;
                 float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, a, b));
+                lbm_status st = time_launch(kind, v, all_stages, &ms);
+                if (st) return st;
                 if (ms < best) { best = ms; bestv = v; }
             }
             s.tile[kind] = bestv;
+            best_ms[kind] = best;
+        }
+        if (pick) {
+            // cost of one half period (lcm of the update factors) both ways
+            choose = true;
+            const lbm_params& q = s.p;
+            double combo_ms[16];
+            for (double& c : combo_ms) c = -1.0;
+            const int steps = std::min(s.half, kMaxGraphPeriod);
+            for (int k = 0; k < steps; ++k) {
+                const bool ph = (k + 1) % q.N_phi == 0;
+                const bool u = s.has_U && (k + 1) % q.N_U == 0;
+                const bool t = s.has_T && (k + 1) % q.N_T == 0;
+                const bool f = s.has_flow && (k + 1) % q.N_F == 0;
+                const double base = ph ? best_ms[LBM_K_PHASE] : 0.0;
+                cost_staged += base + (ph ? best_ms[LBM_K_TRANSFER] : 0.0) + (u ? best_ms[LBM_K_SCALAR_U] : 0.0) +
+                               (t ? best_ms[LBM_K_SCALAR_T] : 0.0) + (f ? best_ms[LBM_K_FLOW] : 0.0);
+                const int combo = (ph ? 1 : 0) | (u ? 2 : 0) | (t ? 4 : 0) | (f ? 8 : 0);
+                if (combo && combo_ms[combo] < 0.0) {
+                    float ms = 0.f;
+                    lbm_status st = time_launch(LBM_K_TRANSPORT, s.tile[LBM_K_TRANSPORT], combo, &ms);
+                    if (st) return st;
+                    combo_ms[combo] = ms;
+                }
+                cost_fused += base + (combo ? combo_ms[combo] : 0.0);
+            }
         }
         drop_graph(s);
     }
+    if (choose) h->fuse = cost_fused < cost_staged;
     if (h->batching) {
         // the batched launches: one job per member that has the field, at the
         // current parities (idempotent like the single launches)
@@ -1408,6 +1555,7 @@ lbm_status lbm_autotune(lbm_handle h, int32_t reps, int32_t* chosen) {
             float best = 1e30f;
             int bestv = h->batch_tile[kind];
             for (int v : variants) {
+                if (!valid_variant(kind, v)) continue;
                 h->batch_tile[kind] = v;
                 clear_records(h);
                 h->recording = true;

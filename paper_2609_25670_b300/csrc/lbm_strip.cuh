@@ -1,0 +1,604 @@
+// Warp-strip update kernels of the multirate MRT-LBM (Liu, Wu, Zhan, Secs.
+// 3.1-3.3): register-blocked alternative to the shared-memory tiles.
+//
+// A warp owns a strip of SW = 30 output columns and H output rows.  Lane l
+// sits on column 30 s - 1 + l: lanes 1..30 are the strip's columns, lanes 0
+// and 31 its left and right neighbours, whose collisions feed the streaming
+// of the edge columns.  The warp walks down the strip one row at a time:
+// it collides row r (every lane), shifts the post-collision populations that
+// move along x one lane with warp shuffles, and completes row r - 1, whose
+// nine incoming populations now sit in registers (row r - 2 for e_y = +1,
+// row r - 1 for e_y = 0, row r for e_y = -1).  The loads of row r + 1 are
+// issued before row r is computed.  There is no shared memory and no block
+// barrier; a strip recomputes H + 2 collision rows for H output rows and
+// 32 collision columns for 30 output columns.
+//
+// Isotropic phi gradients (Eq. 40 context, Q2 reading) are formed from the
+// column sums A(c) = phi(c, r)/3 + (phi(c, r-1) + phi(c, r+1))/12 and
+// B(c) = phi(c, r+1) - phi(c, r-1):  g_x = A(c+1) - A(c-1),
+// g_y = B(c)/3 + (B(c-1) + B(c+1))/12, the same nine-point stencil as the
+// tile kernels.  Lanes 0 and 31 also load the phi column beyond them.
+#pragma once
+#include <cuda_pipeline_primitives.h>
+#include <stdint.h>
+#include <type_traits>
+#include "lbm_common.cuh"
+
+namespace lbmk {
+
+constexpr int SW = 30;     // output columns per strip
+constexpr int NWS = 4;     // warps (strips) per block
+
+template <typename R> __device__ __forceinline__ R from_left(R v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+template <typename R> __device__ __forceinline__ R from_right(R v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
+// strips whose collisions, phi stencils and outputs all lie inside the
+// lattice with a margin: no index maps, no walls
+template <int H>
+__device__ __forceinline__ bool strip_interior(int sx, int y0, int nx, int ny) {
+    return SW * sx - 2 >= 0 && SW * sx + SW + 1 <= nx - 1 && y0 - 2 >= 0 && y0 + H + 1 <= ny - 1;
+}
+
+// isotropic gradient at the lane's column from the phi window (rows r-1, r,
+// r+1) of the lane's own column (c*) and of the extra column (e*)
+template <typename R>
+__device__ __forceinline__ void strip_grad(int lane, R cm, R c0, R cp, R em, R e0, R ep, R& gx, R& gy) {
+    const R A = c0 * (R(1) / R(3)) + (cm + cp) * (R(1) / R(12)), B = cp - cm;
+    const R Ae = e0 * (R(1) / R(3)) + (em + ep) * (R(1) / R(12)), Be = ep - em;
+    R Al = from_left(A), Ar = from_right(A), Bl = from_left(B), Br = from_right(B);
+    if (lane == 0) { Al = Ae; Bl = Be; }
+    if (lane == 31) { Ar = Ae; Br = Be; }
+    gx = Ar - Al;
+    gy = B * (R(1) / R(3)) + (Bl + Br) * (R(1) / R(12));
+}
+
+// post-collision populations of the scalar collision (Eq. 14 with S of
+// Eq. 23 in closed form): p_i = w_i A + 3 w_i (e_i . b) + (e_i . c)
+template <typename R>
+__device__ __forceinline__ void scalar_post9(R A, R bx, R by, R cx, R cy, R* p) {
+    const R w1 = Wt<R>::w1, w2 = Wt<R>::w2;
+    const R a1 = w1 * A, a2 = w2 * A, b1x = R(3) * w1 * bx, b1y = R(3) * w1 * by;
+    const R b2x = R(3) * w2 * bx, b2y = R(3) * w2 * by;
+    p[0] = Wt<R>::w0 * A;
+    p[1] = a1 + b1x + cx;
+    p[2] = a1 + b1y + cy;
+    p[3] = a1 - b1x - cx;
+    p[4] = a1 - b1y - cy;
+    p[5] = a2 + (b2x + b2y) + (cx + cy);
+    p[6] = a2 + (b2y - b2x) + (cy - cx);
+    p[7] = a2 - (b2x + b2y) - (cx + cy);
+    p[8] = a2 + (b2x - b2y) + (cx - cy);
+}
+
+// U (FIELD 0) or T (FIELD 1) collision at one node: chi the zeroth moment
+// (with every injection), (jx, jy) the first moment, (vx, vy) the advecting
+// velocity, ph and (gpx, gpy) phi and its gradient (Eqs. 7-8, 10-12, 19-20,
+// 24, 40)
+template <typename R, int FIELD>
+__device__ __forceinline__ void scalar_collide9(const KP<R>& P, R ph, R gpx, R gpy, R chi, R jx, R jy, R vx, R vy,
+                                                R* p) {
+    const R dt = FIELD == 0 ? P.dtU : P.dtT;
+    R D, coef;
+    if (FIELD == 0) {
+        const R iden = rcp((R(1) + P.k) - (R(1) - P.k) * ph);
+        D = ((R(1) + ph) * P.DS + (R(1) - ph) * P.DL) * iden;                     // Eq. 7
+        coef = -(R(1) - P.k) * D * iden;                                          // Eq. 8, tr
+    } else {
+        const R irc = rcp(R(0.5) * (R(1) + ph) * P.cS + R(0.5) * (R(1) - ph) * P.cL);
+        D = (R(0.5) * (R(1) + ph) * P.kS + R(0.5) * (R(1) - ph) * P.kL) * irc;     // Eq. 11
+        coef = R(0.5) * (P.cS - P.cL) * irc * D;                                  // Eq. 12, tr
+    }
+    const R s = rcp(R(3) * dt * D + R(0.5));                                      // Eq. 24
+    const R bx = dt * chi * vx, by = dt * chi * vy;                                // Eqs. 19-20
+    const R jnx = jx - bx, jny = jy - by;
+    const R Q = coef * (R(-3) * s) * (jnx * gpx + jny * gpy);                       // Eq. 40 in Eq. 8 / 12
+    const R k6 = (R(1) - s) * (R(1) / R(6));
+    scalar_post9<R>(chi + dt * Q, bx, by, k6 * jnx, k6 * jny, p);
+}
+
+// ---------------------------------------------------------------------------
+// Row pipeline.  Each lane copies the words its next rows need from global
+// to a per-warp shared ring of D row slots with asynchronous copies
+// (cp.async through the pipeline primitives), D - 1 rows ahead of the row it
+// computes, so the loads in flight do not depend on the registers free.  A
+// slot holds NA arrays x 32 lanes of 4-byte words (8-byte for FP64).  A lane
+// only reads words it copied itself, so completion of its own copy group is
+// the only ordering needed.  16-bit populations are copied as the aligned
+// 4-byte word that holds them.  Slots of nodes that do not collide are
+// zero-filled.
+// ---------------------------------------------------------------------------
+// output nodes a strip leaves to another kernel path
+struct Rect {
+    int x0, x1, y0, y1;
+    __device__ __forceinline__ bool in(int x, int y) const { return x >= x0 && x < x1 && y >= y0 && y < y1; }
+};
+
+template <typename R> using Word = typename std::conditional<sizeof(R) == 8, unsigned long long, unsigned>::type;
+template <typename R> struct Pipe { static constexpr int D = sizeof(R) == 8 ? 2 : 4; };
+
+template <typename R, typename T>
+__device__ __forceinline__ void fetch_word(Word<R>* dst, const T* a, int idx, bool v) {
+    const void* src = a;
+    if (v) {
+        if constexpr (sizeof(T) >= sizeof(Word<R>)) src = a + idx;
+        else src = (const void*)((uintptr_t)(a + idx) & ~(uintptr_t)(sizeof(Word<R>) - 1));
+    }
+    __pipeline_memcpy_async(dst, src, sizeof(Word<R>), v ? 0 : sizeof(Word<R>));
+}
+// value of type R from a copied word: the element itself, or the 16-bit half
+// selected by the element index parity `odd`
+template <typename R, typename T>
+__device__ __forceinline__ R word_value(Word<R> w, bool odd) {
+    if constexpr (sizeof(T) == sizeof(Word<R>)) {
+        T t;
+        memcpy(&t, &w, sizeof(T));
+        return (R)Cvt<T>::ld(t);
+    } else {
+        const unsigned short b = (unsigned short)(odd ? (w >> 16) : (w & 0xffffu));
+        T t;
+        memcpy(&t, &b, sizeof(T));
+        return (R)Cvt<T>::ld(t);
+    }
+}
+
+// slot arrays of the scalar rows
+enum { SA_F = 0, SA_CHI = 8, SA_ACC = 9, SA_VX = 10, SA_VY = 11, SA_PC = 12, SA_PE = 13, SA_N = 14 };
+
+template <typename R, typename ST, bool IN>
+__device__ __forceinline__ void scalar_row_fetch(const KP<R>& P, const ST* __restrict__ fin,
+                                                 const R* __restrict__ mac_in, const R* __restrict__ acc,
+                                                 const R* __restrict__ phi, const R* __restrict__ ux,
+                                                 const R* __restrict__ uy, int cx, bool colv, int px, int ex, int r,
+                                                 Word<R>* slot, int lane) {
+    const int pl = (int)P.plane;
+    int cy = r;
+    const bool v = IN || (colv && resolve(cy, P.ny, P.bsy));
+    const int node = v ? cy * P.pitch + cx : 0;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) fetch_word<R>(slot + (SA_F + i - 1) * 32 + lane, fin + (size_t)(i - 1) * pl, node, v);
+    fetch_word<R>(slot + SA_CHI * 32 + lane, mac_in, node, v);
+    if (P.accumulated) fetch_word<R>(slot + SA_ACC * 32 + lane, acc, node, v);
+    if (P.has_flow) {
+        fetch_word<R>(slot + SA_VX * 32 + lane, ux, node, v);
+        fetch_word<R>(slot + SA_VY * 32 + lane, uy, node, v);
+    }
+    const int py = IN ? r + 1 : scalar_map(r + 1, P.ny, P.bsy);
+    fetch_word<R>(slot + SA_PC * 32 + lane, phi, py * P.pitch + px, true);
+    fetch_word<R>(slot + SA_PE * 32 + lane, phi, py * P.pitch + ex, true);
+}
+
+template <typename R, typename ST, bool DEV, int H, int FIELD, bool IN>
+__device__ __forceinline__ void scalar_strip(const KP<R>& P, const ST* __restrict__ fin, ST* __restrict__ fout,
+                                             const R* __restrict__ mac_in, R* __restrict__ mac_out,
+                                             const R* __restrict__ acc, const R* __restrict__ phi,
+                                             const R* __restrict__ ux, const R* __restrict__ uy,
+                                             unsigned long long* __restrict__ smax, int sx, int y0, Rect skip,
+                                             Word<R>* __restrict__ ring) {
+    constexpr int D = Pipe<R>::D, NR = H + 2, SLOT = SA_N * 32;
+    const int lane = threadIdx.x & 31, pl = (int)P.plane;
+    const int gx = SW * sx - 1 + lane;
+    int cx = gx;
+    const bool colv = IN || resolve(cx, P.nx, P.bsx);
+    int px = gx, ex = gx + (lane == 0 ? -1 : (lane == 31 ? 1 : 0));
+    if (!IN) {
+        px = scalar_map(px, P.nx, P.bsx);
+        ex = scalar_map(ex, P.nx, P.bsx);
+    }
+    const bool odd = (cx & 1) != 0;               // 16-bit word half of this lane's node (pitch and planes even)
+    const bool outl = lane >= 1 && lane <= SW && (IN || gx < P.nx);
+    // walls beside this column (sources at x - 1 / x + 1 outside)
+    const bool wxm = !IN && P.bsx != BC_PERIODIC && gx == 0;
+    const bool wxp = !IN && P.bsx != BC_PERIODIC && gx == P.nx - 1;
+    // pipeline prologue: collision rows y0-1 .. y0+D-3
+#pragma unroll
+    for (int d = 0; d < D - 1; ++d) {
+        if (d < NR) scalar_row_fetch<R, ST, IN>(P, fin, mac_in, acc, phi, ux, uy, cx, colv, px, ex, y0 - 1 + d,
+                                                ring + d * SLOT, lane);
+        __pipeline_commit();
+    }
+    // phi window of the lane's column and of the extra column
+    R cm, c0, em, e0;
+    {
+        const int ya = IN ? y0 - 2 : scalar_map(y0 - 2, P.ny, P.bsy);
+        const int yb = IN ? y0 - 1 : scalar_map(y0 - 1, P.ny, P.bsy);
+        cm = phi[ya * P.pitch + px]; em = phi[ya * P.pitch + ex];
+        c0 = phi[yb * P.pitch + px]; e0 = phi[yb * P.pitch + ex];
+    }
+    // carried post-collision values: row r-1 (q0, q1s, q3s; q2, q5s, q6s) and
+    // row r-2 (z2, z5s, z6s); own unshifted row r-1 for walls (o[])
+    R q0 = R(0), q1 = R(0), q3 = R(0), q2 = R(0), q5 = R(0), q6 = R(0), z2 = R(0), z5 = R(0), z6 = R(0);
+    R o[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) o[i] = R(0);
+    R myj = R(0);
+#pragma unroll 1
+    for (int k = 0; k < NR; ++k) {
+        const int r = y0 - 1 + k;
+        if (k + D - 1 < NR)
+            scalar_row_fetch<R, ST, IN>(P, fin, mac_in, acc, phi, ux, uy, cx, colv, px, ex, r + D - 1,
+                                        ring + ((k + D - 1) % D) * SLOT, lane);
+        __pipeline_commit();
+        __pipeline_wait_prior(D - 1);             // this lane's copies of row r have landed
+        const Word<R>* sl = ring + (k % D) * SLOT + lane;
+        R f[9];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) f[i] = word_value<R, ST>(sl[(SA_F + i - 1) * 32], odd);
+        R chi = word_value<R, R>(sl[SA_CHI * 32], false), vx = R(0), vy = R(0), accv = R(0);
+        if (P.accumulated) { accv = word_value<R, R>(sl[SA_ACC * 32], false); chi += accv; }  // Sec. 4.4 ablation
+        if (P.has_flow) { vx = word_value<R, R>(sl[SA_VX * 32], false); vy = word_value<R, R>(sl[SA_VY * 32], false); }
+        const R pc = word_value<R, R>(sl[SA_PC * 32], false), pe = word_value<R, R>(sl[SA_PE * 32], false);
+        R gpx, gpy;
+        strip_grad<R>(lane, cm, c0, pc, em, e0, pe, gpx, gpy);
+        R p[9];
+        scalar_collide9<R, FIELD>(P, c0, gpx, gpy, chi, mom_x(f), mom_y(f), vx, vy, p);
+        const R s1 = from_left(p[1]), s3 = from_right(p[3]), s5 = from_left(p[5]);
+        const R s6 = from_right(p[6]), s7 = from_right(p[7]), s8 = from_left(p[8]);
+        const int y = r - 1;                       // row completed in this iteration
+        if (FIELD == 0 && P.accumulated && outl && r >= y0 && r < y0 + H && r < P.ny && !skip.in(gx, r))
+            myj = fmax(myj, fabs(accv));
+        if (k >= 2 && outl && (IN || y < P.ny) && !skip.in(gx, y)) {
+            R fn[9];
+            fn[0] = q0; fn[1] = q1; fn[3] = q3;    // e_y = 0: row y
+            fn[2] = z2; fn[5] = z5; fn[6] = z6;    // e_y = +1: row y - 1
+            fn[4] = p[4]; fn[7] = s7; fn[8] = s8;  // e_y = -1: row y + 1
+            if (!IN) {                              // bounce-back from own node at walls (Eq. 25 with Q8)
+                const bool wym = P.bsy != BC_PERIODIC && y == 0, wyp = P.bsy != BC_PERIODIC && y == P.ny - 1;
+                if (wxm) fn[1] = o[3];
+                if (wxp) fn[3] = o[1];
+                if (wym) fn[2] = o[4];
+                if (wyp) fn[4] = o[2];
+                if (wxm || wym) fn[5] = o[7];
+                if (wxp || wym) fn[6] = o[8];
+                if (wxp || wyp) fn[7] = o[5];
+                if (wxm || wyp) fn[8] = o[6];
+            }
+            R sum = R(0);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) sum += fn[i];
+            const int node = y * P.pitch + gx;
+            mac_out[node] = sum;                                                  // Eq. 18
+#pragma unroll
+            for (int i = 1; i < 9; ++i) fout[node + (i - 1) * pl] = Cvt<ST>::st(DEV ? fn[i] - wq<R>(i) * sum : fn[i]);
+        }
+        z2 = q2; z5 = q5; z6 = q6;
+        q0 = p[0]; q1 = s1; q3 = s3; q2 = p[2]; q5 = s5; q6 = s6;
+        if (!IN) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) o[i] = p[i];
+        }
+        cm = c0; c0 = pc; em = e0; e0 = pe;
+    }
+    if (FIELD == 0 && P.accumulated) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) myj = fmax(myj, __shfl_xor_sync(0xffffffffu, myj, d));
+        if (lane == 0) atomic_max_pos(&smax[1], (double)myj);
+    }
+}
+
+template <typename R, typename ST, bool DEV, int H, int FIELD>
+__device__ __forceinline__ void scalar_strip_block(const KP<R>& P, const ST* fin, ST* fout, const R* mac_in,
+                                                   R* mac_out, const R* acc, const R* phi, const R* ux, const R* uy,
+                                                   unsigned long long* smax, int bx, int by) {
+    constexpr int RING = Pipe<R>::D * SA_N * 32;
+    __shared__ Word<R> ring[NWS * RING];
+    const int w = threadIdx.x >> 5;
+    const int sx = bx * NWS + w, y0 = by * H;
+    if (sx * SW >= P.nx) return;                   // whole warp: past the last strip
+    const Rect none{0, 0, 0, 0};
+    if (strip_interior<H>(sx, y0, P.nx, P.ny))
+        scalar_strip<R, ST, DEV, H, FIELD, true>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, sx, y0,
+                                                  none, ring + w * RING);
+    else
+        scalar_strip<R, ST, DEV, H, FIELD, false>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, sx, y0,
+                                                   none, ring + w * RING);
+}
+
+// ---------------------------------------------------------------------------
+// Vector strips: VW = 4 consecutive nodes per lane, so every population
+// plane and macroscopic array moves as one 16-byte (FP32) word per lane and
+// row -- 512 contiguous bytes per warp -- and the x-shifts of the streaming
+// and of the phi stencil need one shuffle per direction for four nodes.
+// Lane l holds columns 120 s + 4 l .. +3; lanes 1..30 are the strip's 120
+// output columns, lanes 0 and 31 its neighbours.  Vector strips cover only
+// the interior rectangle [VX0, x1) x [VY0, y1) of a lattice (no index maps,
+// no walls, rows padded to 32 elements so every vector is aligned); the 1-wide
+// strips of the same launch complete the frame around it.
+// ---------------------------------------------------------------------------
+constexpr int VW = 4;              // nodes per lane
+constexpr int VSW = 30 * VW;       // output columns per vector strip
+constexpr int VX0 = VW;            // first interior column (strip 0 starts at column 0)
+constexpr int VY0 = 2;             // first interior row
+
+struct VGeo {
+    int nxv, nyv;                  // vector strips across / down
+    Rect in;                       // the interior they cover
+};
+__host__ __device__ inline VGeo vgeo(int nx, int ny, int H) {
+    VGeo g;
+    g.nxv = nx >= 32 * VW ? (nx - 32 * VW) / VSW + 1 : 0;          // columns 120 s .. 120 s + 127 inside
+    g.nyv = ny - 4 - H >= 0 ? (ny - 4 - H) / H + 1 : 0;            // rows y0 - 2 .. y0 + H + 1 inside
+    if (!g.nxv || !g.nyv) g.nxv = g.nyv = 0;
+    g.in = Rect{VX0, VX0 + VSW * g.nxv, VY0, VY0 + H * g.nyv};
+    return g;
+}
+
+template <typename T> struct alignas(sizeof(T) * VW) Vec4 { T v[VW]; };
+
+// asynchronous copy of one lane's vector (VW elements of T) into shared memory
+template <typename T>
+__device__ __forceinline__ void fetch_vec(unsigned char* dst, const T* src) {
+    constexpr int B = (int)sizeof(T) * VW, C = B < 16 ? B : 16;
+#pragma unroll
+    for (int o = 0; o < B; o += C) __pipeline_memcpy_async(dst + o, (const unsigned char*)src + o, C);
+}
+template <typename T> __device__ __forceinline__ Vec4<T> sread(const unsigned char* p) {
+    return *reinterpret_cast<const Vec4<T>*>(p);
+}
+
+enum { VA_CHI = 8, VA_ACC = 9, VA_VX = 10, VA_VY = 11, VA_PHI = 12, VA_N = 13 };
+template <typename R> struct VRing {
+    static constexpr int EB = VW * (int)sizeof(R);     // bytes of one lane's entry
+    static constexpr int SLOT = VA_N * 32 * EB;        // one row
+    static constexpr int D = sizeof(R) == 8 ? 2 : 4;   // rows in the ring (D - 1 in flight)
+    static constexpr int BYTES = D * SLOT;
+};
+constexpr int VNW = 2;     // warps per block of the vector-strip launches
+
+// One vector strip.  UP = false walks rows y0-1 .. y0+H downwards and
+// completes row r-1 after colliding row r; UP = true walks y0+H .. y0-1
+// upwards and completes row r+1.  Neighbouring strip rows walk in opposite
+// directions, so the halo rows two strips share are read close in time (and
+// served by L2 the second time).
+template <typename R, typename ST, bool DEV, int H, int FIELD, bool UP>
+__device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restrict__ fin, ST* __restrict__ fout,
+                                              const R* __restrict__ mac_in, R* __restrict__ mac_out,
+                                              const R* __restrict__ acc, const R* __restrict__ phi,
+                                              const R* __restrict__ ux, const R* __restrict__ uy,
+                                              unsigned long long* __restrict__ smax, int s, int y0,
+                                              unsigned char* __restrict__ ring) {
+    using RG = VRing<R>;
+    constexpr int EB = RG::EB, NR = H + 2, D = RG::D, DIR = UP ? -1 : 1;
+    const int lane = threadIdx.x & 31, pl = (int)P.plane, pitch = P.pitch;
+    const int c0 = VSW * s + VW * lane;
+    const bool outl = lane >= 1 && lane <= 30;
+    const int rfirst = UP ? y0 + H : y0 - 1;    // first collision row
+    unsigned char* const mine = ring + lane * EB;
+    auto fetch_row = [&](int r, unsigned char* slot) {      // collision row r, phi row r + DIR
+        const int base = r * pitch + c0;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) fetch_vec<ST>(slot + (i - 1) * 32 * EB, fin + (size_t)(i - 1) * pl + base);
+        fetch_vec<R>(slot + VA_CHI * 32 * EB, mac_in + base);
+        if (P.accumulated) fetch_vec<R>(slot + VA_ACC * 32 * EB, acc + base);
+        if (P.has_flow) {
+            fetch_vec<R>(slot + VA_VX * 32 * EB, ux + base);
+            fetch_vec<R>(slot + VA_VY * 32 * EB, uy + base);
+        }
+        fetch_vec<R>(slot + VA_PHI * 32 * EB, phi + base + DIR * pitch);
+    };
+#pragma unroll
+    for (int d = 0; d < D - 1; ++d) {
+        fetch_row(rfirst + DIR * d, mine + d * RG::SLOT);
+        __pipeline_commit();
+    }
+    // phi window: the collision row (p0) and the row behind the walk (pb)
+    Vec4<R> pb = *reinterpret_cast<const Vec4<R>*>(phi + (rfirst - DIR) * pitch + c0);
+    Vec4<R> p0 = *reinterpret_cast<const Vec4<R>*>(phi + rfirst * pitch + c0);
+    // carried post-collision values per node: row r - DIR (q0, q1s, q3s and
+    // the three populations that move against the walk, qa*), row r - 2 DIR
+    // (za*).  Walking down the latter are e_y = +1 (2, 5, 6); walking up,
+    // e_y = -1 (4, 7, 8).
+    R q0[VW], q1[VW], q3[VW], qa[VW], qb[VW], qc[VW], za[VW], zb[VW], zc[VW];
+#pragma unroll
+    for (int k = 0; k < VW; ++k) q0[k] = q1[k] = q3[k] = qa[k] = qb[k] = qc[k] = za[k] = zb[k] = zc[k] = R(0);
+    R myj = R(0);
+#pragma unroll 1
+    for (int it = 0; it < NR; ++it) {
+        const int r = rfirst + DIR * it;
+        if (it + D - 1 < NR) fetch_row(r + DIR * (D - 1), mine + ((it + D - 1) % D) * RG::SLOT);
+        __pipeline_commit();
+        __pipeline_wait_prior(D - 1);              // this lane's copies of row r have landed
+        const unsigned char* sl = mine + (it % D) * RG::SLOT;
+        // first moments (the order of mom_x / mom_y)
+        R jx[VW], jy[VW];
+        {
+            R f[9][VW];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const Vec4<ST> v = sread<ST>(sl + (i - 1) * 32 * EB);
+#pragma unroll
+                for (int k = 0; k < VW; ++k) f[i][k] = (R)Cvt<ST>::ld(v.v[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < VW; ++k) {
+                jx[k] = f[1][k] - f[3][k] + f[5][k] - f[6][k] - f[7][k] + f[8][k];
+                jy[k] = f[2][k] - f[4][k] + f[5][k] + f[6][k] - f[7][k] - f[8][k];
+            }
+        }
+        Vec4<R> chi = sread<R>(sl + VA_CHI * 32 * EB), accv{}, vx{}, vy{};
+        if (P.accumulated) {
+            accv = sread<R>(sl + VA_ACC * 32 * EB);
+#pragma unroll
+            for (int k = 0; k < VW; ++k) chi.v[k] += accv.v[k];                // Sec. 4.4 ablation
+        }
+        if (P.has_flow) { vx = sread<R>(sl + VA_VX * 32 * EB); vy = sread<R>(sl + VA_VY * 32 * EB); }
+        const Vec4<R> pf = sread<R>(sl + VA_PHI * 32 * EB);   // phi row r + DIR
+        // phi rows r-1, r, r+1
+        const Vec4<R>& pm = UP ? pf : pb;
+        const Vec4<R>& pp = UP ? pb : pf;
+        // phi gradients of the four nodes (column sums, one shuffle each side)
+        R A[VW + 2], B[VW + 2];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            A[k + 1] = p0.v[k] * (R(1) / R(3)) + (pm.v[k] + pp.v[k]) * (R(1) / R(12));
+            B[k + 1] = pp.v[k] - pm.v[k];
+        }
+        A[0] = from_left(A[VW]); B[0] = from_left(B[VW]);
+        A[VW + 1] = from_right(A[1]); B[VW + 1] = from_right(B[1]);
+        R p[VW][9];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            const R gpx = A[k + 2] - A[k], gpy = B[k + 1] * (R(1) / R(3)) + (B[k] + B[k + 2]) * (R(1) / R(12));
+            scalar_collide9<R, FIELD>(P, p0.v[k], gpx, gpy, chi.v[k], jx[k], jy[k], vx.v[k], vy.v[k], p[k]);
+        }
+        // x-shifts: e_x = +1 (1, 5, 8) from the node on the left, e_x = -1 (3, 6, 7) from the right
+        R s1[VW], s5[VW], s8[VW], s3[VW], s6[VW], s7[VW];
+        s1[0] = from_left(p[VW - 1][1]); s5[0] = from_left(p[VW - 1][5]); s8[0] = from_left(p[VW - 1][8]);
+        s3[VW - 1] = from_right(p[0][3]); s6[VW - 1] = from_right(p[0][6]); s7[VW - 1] = from_right(p[0][7]);
+#pragma unroll
+        for (int k = 1; k < VW; ++k) { s1[k] = p[k - 1][1]; s5[k] = p[k - 1][5]; s8[k] = p[k - 1][8]; }
+#pragma unroll
+        for (int k = 0; k < VW - 1; ++k) { s3[k] = p[k + 1][3]; s6[k] = p[k + 1][6]; s7[k] = p[k + 1][7]; }
+        if (FIELD == 0 && P.accumulated && outl && r >= y0 && r < y0 + H)
+#pragma unroll
+            for (int k = 0; k < VW; ++k) myj = fmax(myj, fabs(accv.v[k]));
+        if (it >= 2 && outl) {                     // complete row r - DIR
+            const int node = (r - DIR) * pitch + c0;
+            Vec4<R> sum;
+            R fn[9][VW];
+#pragma unroll
+            for (int k = 0; k < VW; ++k) {
+                fn[0][k] = q0[k]; fn[1][k] = q1[k]; fn[3][k] = q3[k];
+                if (!UP) {                         // 2, 5, 6 from the row above; 4, 7, 8 from row r
+                    fn[2][k] = za[k]; fn[5][k] = zb[k]; fn[6][k] = zc[k];
+                    fn[4][k] = p[k][4]; fn[7][k] = s7[k]; fn[8][k] = s8[k];
+                } else {                           // 4, 7, 8 from the row below; 2, 5, 6 from row r
+                    fn[4][k] = za[k]; fn[7][k] = zb[k]; fn[8][k] = zc[k];
+                    fn[2][k] = p[k][2]; fn[5][k] = s5[k]; fn[6][k] = s6[k];
+                }
+                R t = R(0);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) t += fn[i][k];
+                sum.v[k] = t;
+            }
+            *reinterpret_cast<Vec4<R>*>(mac_out + node) = sum;                    // Eq. 18
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                Vec4<ST> o;
+#pragma unroll
+                for (int k = 0; k < VW; ++k) o.v[k] = Cvt<ST>::st(DEV ? fn[i][k] - wq<R>(i) * sum.v[k] : fn[i][k]);
+                *reinterpret_cast<Vec4<ST>*>(fout + (size_t)(i - 1) * pl + node) = o;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            za[k] = qa[k]; zb[k] = qb[k]; zc[k] = qc[k];
+            q0[k] = p[k][0]; q1[k] = s1[k]; q3[k] = s3[k];
+            if (!UP) { qa[k] = p[k][2]; qb[k] = s5[k]; qc[k] = s6[k]; }
+            else { qa[k] = p[k][4]; qb[k] = s7[k]; qc[k] = s8[k]; }
+        }
+        pb = p0;
+        p0 = pf;
+    }
+    if (FIELD == 0 && P.accumulated) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) myj = fmax(myj, __shfl_xor_sync(0xffffffffu, myj, d));
+        if (lane == 0) atomic_max_pos(&smax[1], (double)myj);
+    }
+}
+
+// One launch: blocks [0, nvb) run vector strips over the interior, the rest
+// run the 1-wide strips of the whole lattice, skipping those whose outputs
+// all lie in the interior.
+template <typename R> struct VSRing {
+    static constexpr int V1 = Pipe<R>::D * SA_N * 32 * (int)sizeof(Word<R>);
+    static constexpr int BYTES = VRing<R>::BYTES > V1 ? VRing<R>::BYTES : V1;   // per warp
+};
+__host__ __device__ inline int vs_vector_blocks(const VGeo& g) { return (g.nxv * g.nyv + VNW - 1) / VNW; }
+__host__ __device__ inline int vs_frame_blocks_x(int nx) { return ((nx + SW - 1) / SW + VNW - 1) / VNW; }
+__host__ __device__ inline int vs_blocks(int nx, int ny, int H) {
+    return vs_vector_blocks(vgeo(nx, ny, H)) + vs_frame_blocks_x(nx) * ((ny + H - 1) / H);
+}
+
+template <typename R, typename ST, bool DEV, int H, int FIELD>
+__device__ __forceinline__ void scalar_vs_block(const KP<R>& P, const ST* fin, ST* fout, const R* mac_in, R* mac_out,
+                                                const R* acc, const R* phi, const R* ux, const R* uy,
+                                                unsigned long long* smax, int b) {
+    extern __shared__ __align__(128) unsigned char ring[];    // VNW * VSRing<R>::BYTES, dynamic
+    const int w = threadIdx.x >> 5;
+    unsigned char* mine = ring + w * VSRing<R>::BYTES;
+    const VGeo g = vgeo(P.nx, P.ny, H);
+    const int nvb = vs_vector_blocks(g);
+    if (b < nvb) {
+        const int vs = b * VNW + w;
+        if (vs >= g.nxv * g.nyv) return;           // whole warp
+        const int sy = vs / g.nxv;
+        if (sy & 1)
+            scalar_vstrip<R, ST, DEV, H, FIELD, true>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax,
+                                                      vs % g.nxv, VY0 + H * sy, mine);
+        else
+            scalar_vstrip<R, ST, DEV, H, FIELD, false>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax,
+                                                       vs % g.nxv, VY0 + H * sy, mine);
+        return;
+    }
+    b -= nvb;
+    const int fbx = vs_frame_blocks_x(P.nx);
+    const int sx = (b % fbx) * VNW + w, y0 = (b / fbx) * H;
+    if (sx * SW >= P.nx) return;                   // whole warp: past the last strip
+    const Rect& in = g.in;
+    if (SW * sx >= in.x0 && SW * sx + SW <= in.x1 && y0 >= in.y0 && y0 + H <= in.y1) return;   // all interior
+    Word<R>* r1 = reinterpret_cast<Word<R>*>(mine);
+    if (strip_interior<H>(sx, y0, P.nx, P.ny))
+        scalar_strip<R, ST, DEV, H, FIELD, true>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, sx, y0, in, r1);
+    else
+        scalar_strip<R, ST, DEV, H, FIELD, false>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, sx, y0, in, r1);
+}
+
+}  // namespace lbmk
+
+// ---------------------------------------------------------------------------
+// Launch wrappers.  Single simulation: block (bx, by) holds strips
+// bx*NWS .. bx*NWS+NWS-1 of strip row by.  Batched ensemble: block b belongs
+// to the last job whose first block is <= b (job tables of lbm_kernels.cuh).
+// ---------------------------------------------------------------------------
+#include "lbm_kernels.cuh"
+
+namespace lbmk {
+
+template <typename J>
+__device__ __forceinline__ const J& job_block(const J* __restrict__ jobs, int njobs, int b, int& bx, int& by) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].tile0 <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const J& j = jobs[lo];
+    const int t = b - j.tile0;
+    bx = t % j.tiles_x;
+    by = t / j.tiles_x;
+    return j;
+}
+
+template <typename R, typename ST, bool DEV, int H, int FIELD>
+__global__ void __launch_bounds__(32 * NWS)
+k_scalar_strip(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout,
+               const R* __restrict__ mac_in, R* __restrict__ mac_out, const R* __restrict__ acc,
+               const R* __restrict__ phi, const R* __restrict__ ux, const R* __restrict__ uy,
+               unsigned long long* __restrict__ smax) {
+    scalar_strip_block<R, ST, DEV, H, FIELD>(*P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, blockIdx.x,
+                                             blockIdx.y);
+}
+template <typename R, typename ST, bool DEV, int H, int FIELD>
+__global__ void __launch_bounds__(32 * VNW)
+k_scalar_vs(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout,
+            const R* __restrict__ mac_in, R* __restrict__ mac_out, const R* __restrict__ acc,
+            const R* __restrict__ phi, const R* __restrict__ ux, const R* __restrict__ uy,
+            unsigned long long* __restrict__ smax) {
+    scalar_vs_block<R, ST, DEV, H, FIELD>(*P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, blockIdx.x);
+}
+template <typename R, typename ST, bool DEV, int H, int FIELD>
+__global__ void __launch_bounds__(32 * VNW) k_scalar_vs_batch(const ScalarJob<R, ST>* __restrict__ jobs, int njobs) {
+    int bx, by;
+    const ScalarJob<R, ST>& j = job_block(jobs, njobs, blockIdx.x, bx, by);
+    scalar_vs_block<R, ST, DEV, H, FIELD>(*j.P, j.fin, j.fout, j.mac_in, j.mac_out, j.acc, j.phi, j.ux, j.uy, j.smax,
+                                          by * j.tiles_x + bx);
+}
+template <typename R, typename ST, bool DEV, int H, int FIELD>
+__global__ void __launch_bounds__(32 * NWS) k_scalar_strip_batch(const ScalarJob<R, ST>* __restrict__ jobs, int njobs) {
+    int bx, by;
+    const ScalarJob<R, ST>& j = job_block(jobs, njobs, blockIdx.x, bx, by);
+    scalar_strip_block<R, ST, DEV, H, FIELD>(*j.P, j.fin, j.fout, j.mac_in, j.mac_out, j.acc, j.phi, j.ux, j.uy,
+                                             j.smax, bx, by);
+}
+
+}  // namespace lbmk

@@ -71,7 +71,7 @@ def test_batched_fp64_matches_oracle():
 
 
 def test_autotune_batched_keeps_results():
-    ms = members(count=4, seed=14)
+    ms = W.ensemble_members(count=4, seed=14, sizes=(64, 96, 160, 256))
     sim = lbm.Simulation([m.params for m in ms], precision="f32")
     for i, m in enumerate(ms):
         sim.init_fields(m.fields, sim=i)
@@ -84,3 +84,28 @@ def test_autotune_batched_keeps_results():
     for i in range(len(ms)):
         # tile shapes agree to floating-point contraction rounding
         assert np.abs(tuned[i] - ref[i]["phi"]).max() < 1e-5
+
+
+@pytest.mark.parametrize("v", [-8, -32, 1016])
+def test_batched_strips_equal_each_member_alone(v):
+    """Warp-strip U / T kernels in the batched launches: bitwise the results
+    of each member advanced alone with the same variant."""
+    ms = W.ensemble_members(count=4, seed=14, sizes=(64, 96, 160, 256))
+    steps = 16
+    sim = lbm.Simulation([m.params for m in ms], precision="f32")
+    for k in ("scalar_U", "scalar_T"):
+        sim.set_tile(k, v)
+    for i, m in enumerate(ms):
+        sim.init_fields(m.fields, sim=i)
+    sim.advance(steps)
+    batched = [{k: sim.field(k, sim=i) for k in active(m.params)} for i, m in enumerate(ms)]
+    sim.close()
+    for i, m in enumerate(ms):
+        sim = lbm.Simulation(m.params, precision="f32")
+        for k in ("scalar_U", "scalar_T"):
+            sim.set_tile(k, v)
+        sim.init_fields(m.fields)
+        sim.advance(steps)
+        for k in active(m.params):
+            assert np.array_equal(batched[i][k], sim.field(k)), (i, k)
+        sim.close()

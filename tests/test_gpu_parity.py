@@ -157,6 +157,111 @@ def test_init_seed_matches_generator():
 
 
 UPDATE_KINDS = ("phase", "transfer", "scalar_U", "scalar_T", "flow", "transport")
+STRIP_KINDS = ("scalar_U", "scalar_T")
+
+
+@pytest.mark.parametrize("h", [4, 8, 16, 32])
+@pytest.mark.parametrize("bc", [W.BC_WALL, W.BC_PERIODIC])
+def test_strip_kernels_match_oracle_fp64(h, bc):
+    """Warp-strip variants of the U and T updates (strip height h) against
+    the oracle: FP64, ragged lattice (strips of 30 columns and h rows do not
+    divide it), walls or periodic scalar boundaries, all fields coupled."""
+    import paper_2609_25670_b300 as lbm
+    p, f = _random_state(n=95, m=75, seed=5, bc=bc)
+    if bc == W.BC_PERIODIC:
+        p.bc_flow_x = W.BC_PERIODIC
+    sim = lbm.Simulation(p, precision="f64")
+    sim.set_fusion(False)
+    for k in STRIP_KINDS:
+        sim.set_tile(k, -h)
+    sim.init_fields(f)
+    sim.advance(30)
+    got = {k: sim.field(k) for k in active(p)}
+    sim.close()
+    o = run_oracle(p, f, 30)
+    for k in got:
+        assert np.abs(got[k] - o[k]).max() < 1e-11, k
+
+
+@pytest.mark.parametrize("h", [8, 16, 32])
+@pytest.mark.parametrize("bc", [W.BC_WALL, W.BC_PERIODIC])
+def test_vector_strip_kernels_match_oracle_fp64(h, bc):
+    """Vector strips (four nodes per lane) on the interior with 1-wide strips
+    on the frame around it: FP64 against the oracle on a lattice whose
+    interior holds several vector strips and a ragged remainder."""
+    import paper_2609_25670_b300 as lbm
+    p, f = _random_state(n=301, m=90, seed=6, bc=bc)
+    if bc == W.BC_PERIODIC:
+        p.bc_flow_x = W.BC_PERIODIC
+    sim = lbm.Simulation(p, precision="f64")
+    sim.set_fusion(False)
+    for k in STRIP_KINDS:
+        sim.set_tile(k, 1000 + h)
+    sim.init_fields(f)
+    sim.advance(24)
+    got = {k: sim.field(k) for k in active(p)}
+    sim.close()
+    o = run_oracle(p, f, 24)
+    for k in got:
+        assert np.abs(got[k] - o[k]).max() < 1e-11, k
+
+
+def test_vector_strips_accumulated_fp64():
+    """Coarse-step injection read by the vector strips (Sec. 4.4 ablation)."""
+    import paper_2609_25670_b300 as lbm
+    wl = W.thermosolutal_convection(n=260, R=6.0, N=(1, 3, 2, 2))
+    wl.params.accumulated = True
+    sim = lbm.Simulation(wl.params, precision="f64")
+    for k in STRIP_KINDS:
+        sim.set_tile(k, 1016)
+    sim.init_fields(wl.fields)
+    sim.advance(36)
+    got = {k: sim.field(k) for k in active(wl.params)}
+    d = sim.diagnostics()
+    sim.close()
+    o = run_oracle(wl.params, wl.fields, 36)
+    for k in got:
+        assert np.abs(got[k] - o[k]).max() < 1e-10, k
+    assert abs(d["J_U"] - o["diag"]["J_U"]) <= 1e-10 * max(1.0, o["diag"]["J_U"])
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", 1e-5), ("f16dev", 2e-4), ("bf16dev", 2e-3)])
+def test_vector_strips_and_tiles_agree(prec, tol):
+    """Vector strips and tiles in FP32 arithmetic with each storage type:
+    the same arithmetic up to rounding order (16-bit storage rounds the same
+    deviations, so the two stay within FP32 rounding of each other)."""
+    import paper_2609_25670_b300 as lbm
+    wl = W.thermosolutal_convection(n=256, R=8.0)
+    outs = []
+    for v in (8, 1016):
+        sim = lbm.Simulation(wl.params, precision=prec)
+        sim.set_fusion(False)
+        for k in STRIP_KINDS:
+            sim.set_tile(k, v)
+        sim.init_fields(wl.fields)
+        sim.advance(20)
+        outs.append({k: sim.field(k) for k in active(wl.params)})
+        sim.close()
+    for k in outs[0]:
+        assert np.abs(outs[0][k] - outs[1][k]).max() < tol, k
+
+
+def test_strip_and_tile_agree_fp32():
+    """Strip and tile variants: the same arithmetic, different rounding order."""
+    import paper_2609_25670_b300 as lbm
+    wl = W.thermosolutal_convection(n=96, R=8.0)
+    outs = []
+    for v in (8, -16):
+        sim = lbm.Simulation(wl.params, precision="f32")
+        sim.set_fusion(False)
+        for k in STRIP_KINDS:
+            sim.set_tile(k, v)
+        sim.init_fields(wl.fields)
+        sim.advance(40)
+        outs.append({k: sim.field(k) for k in active(wl.params)})
+        sim.close()
+    for k in outs[0]:
+        assert np.abs(outs[0][k] - outs[1][k]).max() < 1e-5, k
 
 
 @pytest.mark.parametrize("ty", [4, 8, 16])
@@ -194,7 +299,7 @@ def test_autotuned_tiles_agree_to_rounding():
         sim.advance(10)
         if tune:
             ch = sim.autotune(reps=2)
-            assert set(ch[k] for k in UPDATE_KINDS) <= {4, 8, 16}
+            assert set(ch[k] for k in UPDATE_KINDS) <= {4, 8, 16, -4, -8, -16, -32}
         sim.advance(30)
         outs.append({k: sim.field(k) for k in active(wl.params)})
         sim.close()
@@ -231,6 +336,27 @@ def test_unfused_path_fp64():
     o = run_oracle(p, f, 120)
     for k in got:
         assert np.abs(got[k] - o[k]).max() < 1e-10, k
+
+
+def test_autotune_fusion_choice():
+    """The autotuner picks the fused or staged path unless it was fixed."""
+    import paper_2609_25670_b300 as lbm
+    wl = W.thermosolutal_convection(n=96, R=8.0)
+    for fixed in (None, True, False):
+        sim = lbm.Simulation(wl.params, precision="f32")
+        if fixed is not None:
+            sim.set_fusion(fixed)
+        sim.init_fields(wl.fields)
+        sim.advance(4)
+        sim.autotune(reps=2)
+        if fixed is not None:
+            assert sim.fused == fixed
+        n0 = sim.launch_counts()
+        sim.advance(4)
+        n = sim.launch_counts()
+        assert (n["transport"] > n0["transport"]) == sim.fused
+        assert (n["transfer"] > n0["transfer"]) != sim.fused
+        sim.close()
 
 
 def test_fused_and_unfused_agree_fp32():
