@@ -354,9 +354,9 @@ inline dim3 grid_of(const SimState& s) { return dim3((s.nx + TX - 1) / TX, (s.ny
 // of height h over the interior with 1-wide strips on the frame (one 1-D
 // launch).  Blocks of one launch over an nx x ny lattice:
 constexpr int VS = 1000;
-inline void blocks_of(int v, int nx, int ny, int& bx, int& by) {
+inline void blocks_of(int kind, int v, int nx, int ny, int& bx, int& by) {
     if (v > VS) {
-        bx = vs_blocks(nx, ny, v - VS);
+        bx = kind == LBM_K_FLOW ? fvs_blocks(nx, ny, v - VS) : vs_blocks(nx, ny, v - VS);
         by = 1;
     } else if (v > 0) {
         bx = (nx + TX - 1) / TX;
@@ -367,16 +367,17 @@ inline void blocks_of(int v, int nx, int ny, int& bx, int& by) {
         by = (ny - v - 1) / (-v);
     }
 }
-inline dim3 grid_v(const SimState& s, int v) {
+inline dim3 grid_v(const SimState& s, int kind, int v) {
     int bx, by;
-    blocks_of(v, s.nx, s.ny, bx, by);
+    blocks_of(kind, v, s.nx, s.ny, bx, by);
     return dim3(bx, by);
 }
 inline bool has_strips(int kind) { return kind == LBM_K_SCALAR_U || kind == LBM_K_SCALAR_T; }
+inline bool has_vstrips(int kind) { return has_strips(kind) || kind == LBM_K_FLOW; }
 inline bool valid_variant(int kind, int v) {
     return v == 4 || v == 8 || v == 16 ||
-           (has_strips(kind) && (v == -4 || v == -8 || v == -16 || v == -32 || v == VS + 8 || v == VS + 16 ||
-                                 v == VS + 32));
+           (has_strips(kind) && (v == -4 || v == -8 || v == -16 || v == -32)) ||
+           (has_vstrips(kind) && (v == VS + 8 || v == VS + 16 || v == VS + 32));
 }
 
 // Update-kernel launch on the handle's stream, with dynamic shared memory
@@ -424,7 +425,7 @@ inline void launch_ex(lbm_sim* h, void (*kern)(KArgs...), dim3 g, dim3 b, Args..
 template <typename J>
 void push_job(lbm_sim* h, int kind, J& j, const SimState& s) {
     int bx, by;
-    blocks_of(h->batch_tile[kind], s.nx, s.ny, bx, by);
+    blocks_of(kind, h->batch_tile[kind], s.nx, s.ny, bx, by);
     j.tiles_x = bx;
     j.tile0 = h->rec_tiles[kind];
     h->rec_tiles[kind] += bx * by;
@@ -515,8 +516,12 @@ void launch_batch(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, 
                                                 (const ScalarJob<R, ST>*)jobs, njobs)))
             break;
         case LBM_K_FLOW:
-            LBM_TY_SWITCH(tysel, (launch_ex(h, k_flow_batch<R, ST, DEV, TYV>, g, dim3(TX, TYV),
-                                            (const FlowJob<R, ST>*)jobs, njobs)));
+            if (tysel > VS)
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_flow_vs_batch<R, ST, DEV, HV>, g, dim3(32, FVW),
+                                                     (size_t)FVSmem<R>::BYTES, (const FlowJob<R, ST>*)jobs, njobs)))
+            else
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_flow_batch<R, ST, DEV, TYV>, g, dim3(TX, TYV),
+                                                (const FlowJob<R, ST>*)jobs, njobs)))
             break;
         case LBM_K_TRANSPORT:
             LBM_TY_SWITCH(tysel, (launch_ex_smem(h, k_transport_batch<R, ST, DEV, TYV>, g, dim3(TX, TYV),
@@ -577,20 +582,20 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
             if (tysel > VS) {
                 const size_t sm = (size_t)VNW * VSRing<R>::BYTES;
                 if (isU)
-                    LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs<R, ST, DEV, HV, 0>, grid_v(s, tysel),
+                    LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs<R, ST, DEV, HV, 0>, grid_v(s, kind, tysel),
                         dim3(32 * VNW), sm, P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc,
                         s.smax)))
                 else
-                    LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs<R, ST, DEV, HV, 1>, grid_v(s, tysel),
+                    LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs<R, ST, DEV, HV, 1>, grid_v(s, kind, tysel),
                         dim3(32 * VNW), sm, P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc,
                         s.smax)))
             } else if (tysel < 0) {
                 if (isU)
-                    LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip<R, ST, DEV, HV, 0>, grid_v(s, tysel),
+                    LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip<R, ST, DEV, HV, 0>, grid_v(s, kind, tysel),
                         dim3(32 * NWS), P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc,
                         s.smax)))
                 else
-                    LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip<R, ST, DEV, HV, 1>, grid_v(s, tysel),
+                    LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip<R, ST, DEV, HV, 1>, grid_v(s, kind, tysel),
                         dim3(32 * NWS), P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc,
                         s.smax)))
             } else if (isU) {
@@ -604,9 +609,15 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
         }
         case LBM_K_FLOW: {
             const int c = s.cur_pop[FF];
-            LBM_TY_SWITCH(tysel, (launch_ex(h, k_flow<R, ST, DEV, TYV>, grid_of<TYV>(s), dim3(TX, TYV),
-                P, (const ST*)s.pops[FF][c], (ST*)s.pops[FF][1 - c], phi_now, (const R*)s.ux[c], (const R*)s.uy[c],
-                (const R*)s.rho[c], (R*)s.ux[1 - c], (R*)s.uy[1 - c], (R*)s.rho[1 - c])));
+            if (tysel > VS)
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_flow_vs<R, ST, DEV, HV>, grid_v(s, kind, tysel),
+                    dim3(32, FVW), (size_t)FVSmem<R>::BYTES, P, (const ST*)s.pops[FF][c], (ST*)s.pops[FF][1 - c],
+                    phi_now, (const R*)s.ux[c], (const R*)s.uy[c], (const R*)s.rho[c], (R*)s.ux[1 - c],
+                    (R*)s.uy[1 - c], (R*)s.rho[1 - c])))
+            else
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_flow<R, ST, DEV, TYV>, grid_of<TYV>(s), dim3(TX, TYV),
+                    P, (const ST*)s.pops[FF][c], (ST*)s.pops[FF][1 - c], phi_now, (const R*)s.ux[c],
+                    (const R*)s.uy[c], (const R*)s.rho[c], (R*)s.ux[1 - c], (R*)s.uy[1 - c], (R*)s.rho[1 - c])))
             break;
         }
         default: break;
@@ -1407,7 +1418,8 @@ lbm_status lbm_set_tile(lbm_handle h, int32_t kind, int32_t ty) {
     if (!valid_variant(kind, ty))
         return fail(h, LBM_E_INVALID_ARG, "variant %d is not a tile height in {4, 8, 16}%s", ty,
                     has_strips(kind) ? ", a strip height in {-4, -8, -16, -32} or 1000 + a vector strip height in "
-                                       "{8, 16, 32}" : "");
+                                       "{8, 16, 32}" : has_vstrips(kind) ? " or 1000 + a vector strip height in {8, 16, 32}"
+                                                                         : "");
     for (auto& s : h->sims) {
         s.tile[kind] = ty;
         drop_graph(s);

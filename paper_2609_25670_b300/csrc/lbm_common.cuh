@@ -112,6 +112,12 @@ __device__ __forceinline__ bool resolve_xy(int& x, int& y, int nx, int ny, int b
     return a && b;
 }
 
+// output nodes a kernel path leaves to another one (empty when x0 == x1)
+struct Rect {
+    int x0, x1, y0, y1;
+    __host__ __device__ __forceinline__ bool in(int x, int y) const { return x >= x0 && x < x1 && y >= y0 && y < y1; }
+};
+
 // isotropic gradient g_a = 3 sum_i w_i e_ia s(x + e_i) on a shared tile
 template <typename R, int GX>
 __device__ __forceinline__ void iso_grad(const R (*s)[GX], int cx, int cy, R& gx, R& gy) {

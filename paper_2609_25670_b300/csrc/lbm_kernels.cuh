@@ -456,9 +456,10 @@ template <typename R, int TY> struct FlowSmem {
 };
 
 // MRT collision of Eq. 14 with S of Eq. 31 and Guo forcing (Eq. 30); f holds
-// populations 1..8 (decoded) on entry, rho the macro written with them
-template <typename R, int TY>
-__device__ __forceinline__ void flow_collide(const KP<R>& P, R (*sp)[TY + 2][34], int lx, int ly, R* f, R rho) {
+// populations 1..8 (decoded) on entry, rho the macro written with them; the
+// nine post-collision populations go to p
+template <typename R>
+__device__ __forceinline__ void flow_post9(const KP<R>& P, R* f, R rho, R* p) {
     const R c = P.cF, dt = P.dtF;
     R s8 = R(0);
 #pragma unroll
@@ -490,15 +491,22 @@ __device__ __forceinline__ void flow_collide(const KP<R>& P, R (*sp)[TY + 2][34]
     const R d7 = (-P.snu * (m7 - rho * (ux * ux - uy * uy) * ic2) + (R(1) - R(0.5) * P.snu) * G7) * (R(1) / R(4));
     const R d8 = (-P.snu * (m8 - rho * ux * uy * ic2) + (R(1) - R(0.5) * P.snu) * G8) * (R(1) / R(4));
     const R axis = -d1 - R(2) * d2, diag = R(2) * d1 + d2;
-    sp[0][ly][lx] = f[0] - R(4) * d1 + R(4) * d2;
-    sp[1][ly][lx] = f[1] + axis + d3 - R(2) * d4 + d7;
-    sp[2][ly][lx] = f[2] + axis + d5 - R(2) * d6 - d7;
-    sp[3][ly][lx] = f[3] + axis - d3 + R(2) * d4 + d7;
-    sp[4][ly][lx] = f[4] + axis - d5 + R(2) * d6 - d7;
-    sp[5][ly][lx] = f[5] + diag + d3 + d4 + d5 + d6 + d8;
-    sp[6][ly][lx] = f[6] + diag - d3 - d4 + d5 + d6 - d8;
-    sp[7][ly][lx] = f[7] + diag - d3 - d4 - d5 - d6 + d8;
-    sp[8][ly][lx] = f[8] + diag + d3 + d4 - d5 - d6 - d8;
+    p[0] = f[0] - R(4) * d1 + R(4) * d2;
+    p[1] = f[1] + axis + d3 - R(2) * d4 + d7;
+    p[2] = f[2] + axis + d5 - R(2) * d6 - d7;
+    p[3] = f[3] + axis - d3 + R(2) * d4 + d7;
+    p[4] = f[4] + axis - d5 + R(2) * d6 - d7;
+    p[5] = f[5] + diag + d3 + d4 + d5 + d6 + d8;
+    p[6] = f[6] + diag - d3 - d4 + d5 + d6 - d8;
+    p[7] = f[7] + diag - d3 - d4 - d5 - d6 + d8;
+    p[8] = f[8] + diag + d3 + d4 - d5 - d6 - d8;
+}
+template <typename R, int TY>
+__device__ __forceinline__ void flow_collide(const KP<R>& P, R (*sp)[TY + 2][34], int lx, int ly, R* f, R rho) {
+    R p[9];
+    flow_post9<R>(P, f, rho, p);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) sp[i][ly][lx] = p[i];
 }
 
 template <typename R, typename ST, bool DEV, int TY, bool IN>
@@ -506,7 +514,8 @@ __device__ __forceinline__ void flow_tile(FlowSmem<R, TY>& sm, const KP<R>& P, c
                                           ST* __restrict__ fout, const R* __restrict__ phi,
                                           const R* __restrict__ ux_in, const R* __restrict__ uy_in,
                                           const R* __restrict__ rho_in, R* __restrict__ ux_out,
-                                          R* __restrict__ uy_out, R* __restrict__ rho_out, int x0, int y0) {
+                                          R* __restrict__ uy_out, R* __restrict__ rho_out, int x0, int y0,
+                                          Rect skip) {
     constexpr int TX = 32, HX = TX + 2, NR = 2 * HX + 2 * TY;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int pl = (int)P.plane;
@@ -552,6 +561,7 @@ __device__ __forceinline__ void flow_tile(FlowSmem<R, TY>& sm, const KP<R>& P, c
     __syncthreads();
     const int gx = x0 + tx, gy = y0 + ty;
     if (!IN && (gx >= P.nx || gy >= P.ny)) return;
+    if (skip.in(gx, gy)) return;                  // written by the vector strips of the same launch
     const int node = gy * P.pitch + gx;
     // streamed value of direction i into the node at shared position (hx, hy),
     // global (gxn, gyn), with the weighted partial bounce-back of Eq. 33
@@ -602,11 +612,14 @@ __device__ __forceinline__ void flow_tile(FlowSmem<R, TY>& sm, const KP<R>& P, c
 template <typename R, typename ST, bool DEV, int TY>
 __device__ __forceinline__ void flow_block(FlowSmem<R, TY>& sm, const KP<R>& P, const ST* fin, ST* fout, const R* phi,
                                            const R* ux_in, const R* uy_in, const R* rho_in, R* ux_out, R* uy_out,
-                                           R* rho_out, int x0, int y0) {
+                                           R* rho_out, int x0, int y0, Rect skip = Rect{0, 0, 0, 0}) {
     // interior: tile + 1-ring inside the lattice, away from the inlet / outflow columns
     if (x0 >= 1 && x0 + 33 <= P.nx && y0 >= 1 && y0 + TY + 1 <= P.ny)
-        flow_tile<R, ST, DEV, TY, true>(sm, P, fin, fout, phi, ux_in, uy_in, rho_in, ux_out, uy_out, rho_out, x0, y0);
-    else flow_tile<R, ST, DEV, TY, false>(sm, P, fin, fout, phi, ux_in, uy_in, rho_in, ux_out, uy_out, rho_out, x0, y0);
+        flow_tile<R, ST, DEV, TY, true>(sm, P, fin, fout, phi, ux_in, uy_in, rho_in, ux_out, uy_out, rho_out, x0, y0,
+                                        skip);
+    else
+        flow_tile<R, ST, DEV, TY, false>(sm, P, fin, fout, phi, ux_in, uy_in, rho_in, ux_out, uy_out, rho_out, x0,
+                                         y0, skip);
 }
 
 // ---------------------------------------------------------------------------

@@ -23,6 +23,7 @@
 #include <stdint.h>
 #include <type_traits>
 #include "lbm_common.cuh"
+#include "lbm_kernels.cuh"
 
 namespace lbmk {
 
@@ -107,12 +108,6 @@ __device__ __forceinline__ void scalar_collide9(const KP<R>& P, R ph, R gpx, R g
 // 4-byte word that holds them.  Slots of nodes that do not collide are
 // zero-filled.
 // ---------------------------------------------------------------------------
-// output nodes a strip leaves to another kernel path
-struct Rect {
-    int x0, x1, y0, y1;
-    __device__ __forceinline__ bool in(int x, int y) const { return x >= x0 && x < x1 && y >= y0 && y < y1; }
-};
-
 template <typename R> using Word = typename std::conditional<sizeof(R) == 8, unsigned long long, unsigned>::type;
 template <typename R> struct Pipe { static constexpr int D = sizeof(R) == 8 ? 2 : 4; };
 
@@ -543,6 +538,205 @@ __device__ __forceinline__ void scalar_vs_block(const KP<R>& P, const ST* fin, S
         scalar_strip<R, ST, DEV, H, FIELD, false>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, sx, y0, in, r1);
 }
 
+// ---------------------------------------------------------------------------
+// Flow vector strips (Eqs. 27-33 in the interior).  Streaming with the
+// partial bounce-back of Eq. 33: the population of direction i entering x
+// from s = x - e_i is  fLm p_i(s) + (1 - fLm) p_opp(i)(x),  fLm = (f_L(s) +
+// f_L(x)) / 2, f_L = (1 - phi)/2.  A completed row needs its own nine
+// post-collision values and f_L, and (p_i, f_L) of its sources in the rows
+// on either side; both are carried in registers as the warp walks.
+// ---------------------------------------------------------------------------
+enum { FA_RHO = 8, FA_UX = 9, FA_UY = 10, FA_PHI = 11 };
+
+template <typename R, typename ST, bool DEV, int H, bool UP>
+__device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict__ fin, ST* __restrict__ fout,
+                                            const R* __restrict__ phi, const R* __restrict__ ux_in,
+                                            const R* __restrict__ uy_in, const R* __restrict__ rho_in,
+                                            R* __restrict__ ux_out, R* __restrict__ uy_out, R* __restrict__ rho_out,
+                                            int s, int y0, unsigned char* __restrict__ ring) {
+    using RG = VRing<R>;
+    constexpr int EB = RG::EB, NR = H + 2, D = RG::D, DIR = UP ? -1 : 1;
+    // directions whose source lies in the row behind the walk (far) and in
+    // the row just collided (near): axis, from the left (e_x = +1), from the right
+    constexpr int FAX = UP ? 4 : 2, FL = UP ? 8 : 5, FR = UP ? 7 : 6;
+    constexpr int NAX = UP ? 2 : 4, NL = UP ? 5 : 8, NRt = UP ? 6 : 7;
+    const int lane = threadIdx.x & 31, pl = (int)P.plane, pitch = P.pitch;
+    const R c = P.cF, dt = P.dtF;
+    const int c0 = VSW * s + VW * lane;
+    const bool outl = lane >= 1 && lane <= 30;
+    const int rfirst = UP ? y0 + H : y0 - 1;
+    unsigned char* const mine = ring + lane * EB;
+    auto fetch_row = [&](int r, unsigned char* slot) {
+        const int base = r * pitch + c0;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) fetch_vec<ST>(slot + (i - 1) * 32 * EB, fin + (size_t)(i - 1) * pl + base);
+        fetch_vec<R>(slot + FA_RHO * 32 * EB, rho_in + base);
+        fetch_vec<R>(slot + FA_UX * 32 * EB, ux_in + base);
+        fetch_vec<R>(slot + FA_UY * 32 * EB, uy_in + base);
+        fetch_vec<R>(slot + FA_PHI * 32 * EB, phi + base);
+    };
+#pragma unroll
+    for (int d = 0; d < D - 1; ++d) {
+        fetch_row(rfirst + DIR * d, mine + d * RG::SLOT);
+        __pipeline_commit();
+    }
+    // row y (the next to complete): own post o, f_L own / left / right, the
+    // shifted post values of directions 1, 3 and of the far pair
+    R o[9][VW], fy[VW], fyl[VW], fyr[VW], q1[VW], q3[VW], qa[VW], qb[VW];
+    // far row: axis post, shifted pair, f_L own / left / right
+    R zx[VW], zl[VW], zr[VW], zf[VW], zfl[VW], zfr[VW];
+#pragma unroll
+    for (int k = 0; k < VW; ++k) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) o[i][k] = R(0);
+        fy[k] = fyl[k] = fyr[k] = q1[k] = q3[k] = qa[k] = qb[k] = R(0);
+        zx[k] = zl[k] = zr[k] = zf[k] = zfl[k] = zfr[k] = R(0);
+    }
+#pragma unroll 1
+    for (int it = 0; it < NR; ++it) {
+        const int r = rfirst + DIR * it;
+        if (it + D - 1 < NR) fetch_row(r + DIR * (D - 1), mine + ((it + D - 1) % D) * RG::SLOT);
+        __pipeline_commit();
+        __pipeline_wait_prior(D - 1);
+        const unsigned char* sl = mine + (it % D) * RG::SLOT;
+        const Vec4<R> rho = sread<R>(sl + FA_RHO * 32 * EB), vx = sread<R>(sl + FA_UX * 32 * EB);
+        const Vec4<R> vy = sread<R>(sl + FA_UY * 32 * EB), ph = sread<R>(sl + FA_PHI * 32 * EB);
+        R p[VW][9], fl[VW];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            R f[9];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const Vec4<ST> v = sread<ST>(sl + (i - 1) * 32 * EB);
+                f[i] = (R)Cvt<ST>::ld(v.v[k]);
+            }
+            if (DEV) {     // h_i = f_i - f_eq_i(rho, u) of the writer's macros
+                R ref[9];
+                feq_flow<R>(rho.v[k], vx.v[k], vy.v[k], c, ref);
+#pragma unroll
+                for (int i = 1; i < 9; ++i) f[i] += ref[i];
+            }
+            flow_post9<R>(P, f, rho.v[k], p[k]);
+            fl[k] = R(0.5) * (R(1) - ph.v[k]);                                       // f_L = (1 - phi)/2
+        }
+        // x-shifts of the post values and of f_L
+        R s1[VW], s5[VW], s8[VW], s3[VW], s6[VW], s7[VW], fll[VW], flr[VW];
+        s1[0] = from_left(p[VW - 1][1]); s5[0] = from_left(p[VW - 1][5]); s8[0] = from_left(p[VW - 1][8]);
+        fll[0] = from_left(fl[VW - 1]);
+        s3[VW - 1] = from_right(p[0][3]); s6[VW - 1] = from_right(p[0][6]); s7[VW - 1] = from_right(p[0][7]);
+        flr[VW - 1] = from_right(fl[0]);
+#pragma unroll
+        for (int k = 1; k < VW; ++k) { s1[k] = p[k - 1][1]; s5[k] = p[k - 1][5]; s8[k] = p[k - 1][8]; fll[k] = fl[k - 1]; }
+#pragma unroll
+        for (int k = 0; k < VW - 1; ++k) { s3[k] = p[k + 1][3]; s6[k] = p[k + 1][6]; s7[k] = p[k + 1][7]; flr[k] = fl[k + 1]; }
+        R(&sNL)[VW] = UP ? s5 : s8;            // near pair, shifted
+        R(&sNR)[VW] = UP ? s6 : s7;
+        if (it >= 2 && outl) {                 // complete row r - DIR
+            const int node = (r - DIR) * pitch + c0;
+            Vec4<R> vrho, vux, vuy;
+            R fn[9][VW];
+#pragma unroll
+            for (int k = 0; k < VW; ++k) {
+                const R f0 = fy[k];
+                auto pull = [&](int i, R src, R fls) -> R {
+                    const R fLm = R(0.5) * (fls + f0);
+                    return fLm * src + (R(1) - fLm) * o[opp_of(i)][k];
+                };
+                fn[0][k] = pull(0, o[0][k], f0);
+                fn[1][k] = pull(1, q1[k], fyl[k]);
+                fn[3][k] = pull(3, q3[k], fyr[k]);
+                fn[FAX][k] = pull(FAX, zx[k], zf[k]);
+                fn[FL][k] = pull(FL, zl[k], zfl[k]);
+                fn[FR][k] = pull(FR, zr[k], zfr[k]);
+                fn[NAX][k] = pull(NAX, p[k][NAX], fl[k]);
+                fn[NL][k] = pull(NL, sNL[k], fll[k]);
+                fn[NRt][k] = pull(NRt, sNR[k], flr[k]);
+                R rr = R(0);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) rr += fn[i][k];
+                R g[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) g[i] = fn[i][k];
+                const R jx = mom_x(g), jy = mom_y(g);
+                const R irho = rcp(rr);
+                vrho.v[k] = rr;
+                vux.v[k] = (c * jx + R(0.5) * dt * P.Fbx) * irho;                   // Eq. 27
+                vuy.v[k] = (c * jy + R(0.5) * dt * P.Fby) * irho;
+            }
+            *reinterpret_cast<Vec4<R>*>(rho_out + node) = vrho;
+            *reinterpret_cast<Vec4<R>*>(ux_out + node) = vux;
+            *reinterpret_cast<Vec4<R>*>(uy_out + node) = vuy;
+            R ref[VW][9];
+            if (DEV)
+#pragma unroll
+                for (int k = 0; k < VW; ++k) feq_flow<R>(vrho.v[k], vux.v[k], vuy.v[k], c, ref[k]);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                Vec4<ST> ov;
+#pragma unroll
+                for (int k = 0; k < VW; ++k) ov.v[k] = Cvt<ST>::st(DEV ? fn[i][k] - ref[k][i] : fn[i][k]);
+                *reinterpret_cast<Vec4<ST>*>(fout + (size_t)(i - 1) * pl + node) = ov;
+            }
+        }
+        // roll: row y becomes the far row, row r becomes row y
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            zx[k] = o[FAX][k]; zl[k] = qa[k]; zr[k] = qb[k]; zf[k] = fy[k]; zfl[k] = fyl[k]; zfr[k] = fyr[k];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) o[i][k] = p[k][i];
+            fy[k] = fl[k]; fyl[k] = fll[k]; fyr[k] = flr[k];
+            q1[k] = s1[k]; q3[k] = s3[k];
+            qa[k] = UP ? s8[k] : s5[k];
+            qb[k] = UP ? s7[k] : s6[k];
+        }
+    }
+}
+
+// One launch of blocks of 32 x 4 threads: blocks [0, nvb) run 4 vector strips
+// each over the interior, the rest run the 32 x 4 shared-memory tiles of the
+// whole lattice (every boundary kind), skipping tiles wholly inside the
+// interior and leaving its nodes to the strips.
+constexpr int FVW = 4;     // warps per block of the flow vector launch (= tile height of its frame)
+template <typename R> struct FVSmem {
+    static constexpr int STRIPS = FVW * VRing<R>::BYTES;
+    static constexpr int TILE = (int)sizeof(FlowSmem<R, FVW>);
+    static constexpr int BYTES = STRIPS > TILE ? STRIPS : TILE;
+};
+__host__ __device__ inline int fvs_vector_blocks(const VGeo& g) { return (g.nxv * g.nyv + FVW - 1) / FVW; }
+__host__ __device__ inline int fvs_blocks(int nx, int ny, int H) {
+    return fvs_vector_blocks(vgeo(nx, ny, H)) + ((nx + 31) / 32) * ((ny + FVW - 1) / FVW);
+}
+
+template <typename R, typename ST, bool DEV, int H>
+__device__ __forceinline__ void flow_vs_block(const KP<R>& P, const ST* fin, ST* fout, const R* phi, const R* ux_in,
+                                              const R* uy_in, const R* rho_in, R* ux_out, R* uy_out, R* rho_out,
+                                              int b) {
+    extern __shared__ __align__(128) unsigned char fsm[];   // FVSmem<R>::BYTES, dynamic
+    const VGeo g = vgeo(P.nx, P.ny, H);
+    const int nvb = fvs_vector_blocks(g);
+    if (b < nvb) {
+        const int w = threadIdx.y;
+        const int vs = b * FVW + w;
+        if (vs >= g.nxv * g.nyv) return;           // whole warp (no block barrier on this path)
+        const int sy = vs / g.nxv;
+        unsigned char* mine = fsm + w * VRing<R>::BYTES;
+        if (sy & 1)
+            flow_vstrip<R, ST, DEV, H, true>(P, fin, fout, phi, ux_in, uy_in, rho_in, ux_out, uy_out, rho_out,
+                                             vs % g.nxv, VY0 + H * sy, mine);
+        else
+            flow_vstrip<R, ST, DEV, H, false>(P, fin, fout, phi, ux_in, uy_in, rho_in, ux_out, uy_out, rho_out,
+                                              vs % g.nxv, VY0 + H * sy, mine);
+        return;
+    }
+    b -= nvb;
+    const int tx = (P.nx + 31) / 32;
+    const int x0 = (b % tx) * 32, y0 = (b / tx) * FVW;
+    const Rect& in = g.in;
+    if (x0 >= in.x0 && x0 + 32 <= in.x1 && y0 >= in.y0 && y0 + FVW <= in.y1) return;   // whole block
+    flow_block<R, ST, DEV, FVW>(*reinterpret_cast<FlowSmem<R, FVW>*>(fsm), P, fin, fout, phi, ux_in, uy_in, rho_in,
+                                ux_out, uy_out, rho_out, x0, y0, in);
+}
+
 }  // namespace lbmk
 
 // ---------------------------------------------------------------------------
@@ -550,7 +744,6 @@ __device__ __forceinline__ void scalar_vs_block(const KP<R>& P, const ST* fin, S
 // bx*NWS .. bx*NWS+NWS-1 of strip row by.  Batched ensemble: block b belongs
 // to the last job whose first block is <= b (job tables of lbm_kernels.cuh).
 // ---------------------------------------------------------------------------
-#include "lbm_kernels.cuh"
 
 namespace lbmk {
 
@@ -592,6 +785,20 @@ __global__ void __launch_bounds__(32 * VNW) k_scalar_vs_batch(const ScalarJob<R,
     const ScalarJob<R, ST>& j = job_block(jobs, njobs, blockIdx.x, bx, by);
     scalar_vs_block<R, ST, DEV, H, FIELD>(*j.P, j.fin, j.fout, j.mac_in, j.mac_out, j.acc, j.phi, j.ux, j.uy, j.smax,
                                           by * j.tiles_x + bx);
+}
+template <typename R, typename ST, bool DEV, int H>
+__global__ void __launch_bounds__(32 * FVW)
+k_flow_vs(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout, const R* __restrict__ phi,
+          const R* __restrict__ ux_in, const R* __restrict__ uy_in, const R* __restrict__ rho_in,
+          R* __restrict__ ux_out, R* __restrict__ uy_out, R* __restrict__ rho_out) {
+    flow_vs_block<R, ST, DEV, H>(*P, fin, fout, phi, ux_in, uy_in, rho_in, ux_out, uy_out, rho_out, blockIdx.x);
+}
+template <typename R, typename ST, bool DEV, int H>
+__global__ void __launch_bounds__(32 * FVW) k_flow_vs_batch(const FlowJob<R, ST>* __restrict__ jobs, int njobs) {
+    int bx, by;
+    const FlowJob<R, ST>& j = job_block(jobs, njobs, blockIdx.x, bx, by);
+    flow_vs_block<R, ST, DEV, H>(*j.P, j.fin, j.fout, j.phi, j.ux_in, j.uy_in, j.rho_in, j.ux_out, j.uy_out,
+                                 j.rho_out, by * j.tiles_x + bx);
 }
 template <typename R, typename ST, bool DEV, int H, int FIELD>
 __global__ void __launch_bounds__(32 * NWS) k_scalar_strip_batch(const ScalarJob<R, ST>* __restrict__ jobs, int njobs) {

@@ -158,6 +158,7 @@ def test_init_seed_matches_generator():
 
 UPDATE_KINDS = ("phase", "transfer", "scalar_U", "scalar_T", "flow", "transport")
 STRIP_KINDS = ("scalar_U", "scalar_T")
+VSTRIP_KINDS = ("scalar_U", "scalar_T", "flow")
 
 
 @pytest.mark.parametrize("h", [4, 8, 16, 32])
@@ -186,16 +187,18 @@ def test_strip_kernels_match_oracle_fp64(h, bc):
 @pytest.mark.parametrize("h", [8, 16, 32])
 @pytest.mark.parametrize("bc", [W.BC_WALL, W.BC_PERIODIC])
 def test_vector_strip_kernels_match_oracle_fp64(h, bc):
-    """Vector strips (four nodes per lane) on the interior with 1-wide strips
-    on the frame around it: FP64 against the oracle on a lattice whose
-    interior holds several vector strips and a ragged remainder."""
+    """Vector strips (four nodes per lane) on the interior of the U, T and
+    flow updates, with 1-wide strips (U, T) or shared-memory tiles (flow) on
+    the frame around it: FP64 against the oracle on a lattice whose interior
+    holds several vector strips and a ragged remainder, inlet / outflow or
+    periodic flow boundaries."""
     import paper_2609_25670_b300 as lbm
     p, f = _random_state(n=301, m=90, seed=6, bc=bc)
     if bc == W.BC_PERIODIC:
         p.bc_flow_x = W.BC_PERIODIC
     sim = lbm.Simulation(p, precision="f64")
     sim.set_fusion(False)
-    for k in STRIP_KINDS:
+    for k in VSTRIP_KINDS:
         sim.set_tile(k, 1000 + h)
     sim.init_fields(f)
     sim.advance(24)
@@ -236,7 +239,7 @@ def test_vector_strips_and_tiles_agree(prec, tol):
     for v in (8, 1016):
         sim = lbm.Simulation(wl.params, precision=prec)
         sim.set_fusion(False)
-        for k in STRIP_KINDS:
+        for k in VSTRIP_KINDS:
             sim.set_tile(k, v)
         sim.init_fields(wl.fields)
         sim.advance(20)
@@ -299,7 +302,7 @@ def test_autotuned_tiles_agree_to_rounding():
         sim.advance(10)
         if tune:
             ch = sim.autotune(reps=2)
-            assert set(ch[k] for k in UPDATE_KINDS) <= {4, 8, 16, -4, -8, -16, -32}
+            assert set(ch[k] for k in UPDATE_KINDS) <= {4, 8, 16, -4, -8, -16, -32, 1008, 1016, 1032}
         sim.advance(30)
         outs.append({k: sim.field(k) for k in active(wl.params)})
         sim.close()
