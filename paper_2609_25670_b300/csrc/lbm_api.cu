@@ -356,7 +356,9 @@ inline dim3 grid_of(const SimState& s) { return dim3((s.nx + TX - 1) / TX, (s.ny
 constexpr int VS = 1000;
 inline void blocks_of(int kind, int v, int nx, int ny, int& bx, int& by) {
     if (v > VS) {
-        bx = kind == LBM_K_FLOW ? fvs_blocks(nx, ny, v - VS) : vs_blocks(nx, ny, v - VS);
+        bx = kind == LBM_K_FLOW       ? fvs_blocks(nx, ny, v - VS)
+             : kind == LBM_K_TRANSFER ? tvs_blocks(nx, ny, v - VS)
+                                      : vs_blocks(nx, ny, v - VS);
         by = 1;
     } else if (v > 0) {
         bx = (nx + TX - 1) / TX;
@@ -373,7 +375,7 @@ inline dim3 grid_v(const SimState& s, int kind, int v) {
     return dim3(bx, by);
 }
 inline bool has_strips(int kind) { return kind == LBM_K_SCALAR_U || kind == LBM_K_SCALAR_T; }
-inline bool has_vstrips(int kind) { return has_strips(kind) || kind == LBM_K_FLOW; }
+inline bool has_vstrips(int kind) { return has_strips(kind) || kind == LBM_K_FLOW || kind == LBM_K_TRANSFER; }
 inline bool valid_variant(int kind, int v) {
     return v == 4 || v == 8 || v == 16 ||
            (has_strips(kind) && (v == -4 || v == -8 || v == -16 || v == -32)) ||
@@ -488,8 +490,12 @@ void launch_batch(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, 
                                             (const PhaseJob<R, ST>*)jobs, njobs)));
             break;
         case LBM_K_TRANSFER:
-            LBM_TY_SWITCH(tysel, (launch_ex(h, k_transfer_batch<R, TYV>, g, dim3(TX, TYV),
-                                            (const TransferJob<R>*)jobs, njobs)));
+            if (tysel > VS)
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_transfer_vs_batch<R, HV>, g, dim3(32, TVW),
+                                                     (size_t)TVSmem<R>::BYTES, (const TransferJob<R>*)jobs, njobs)))
+            else
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_transfer_batch<R, TYV>, g, dim3(TX, TYV),
+                                                (const TransferJob<R>*)jobs, njobs)))
             break;
         case LBM_K_SCALAR_U:
             if (tysel > VS)
@@ -564,11 +570,18 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
                 s.has_T ? (const R*)s.T[s.cur_T] : null_r, clock, off)));
             break;
         case LBM_K_TRANSFER:   // phi^q = phi[1 - cur], phi^{q+1} = phi[cur] (after the phase flip)
-            LBM_TY_SWITCH(tysel, (launch_ex(h, k_transfer<R, TYV>, grid_of<TYV>(s), dim3(TX, TYV),
-                P, (const R*)s.phi[1 - s.cur_phi], phi_now, s.has_U ? (const R*)s.U[s.cur_U] : null_r,
-                s.has_U ? (R*)s.U[1 - s.cur_U] : null_w, s.has_T ? (const R*)s.T[s.cur_T] : null_r,
-                s.has_T ? (R*)s.T[1 - s.cur_T] : null_w, (R*)s.accU, (R*)s.accT, s.acc_reset_U ? 1 : 0,
-                s.acc_reset_T ? 1 : 0, s.smax)));
+            if (tysel > VS)
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_transfer_vs<R, HV>, grid_v(s, kind, tysel), dim3(32, TVW),
+                    (size_t)TVSmem<R>::BYTES, P, (const R*)s.phi[1 - s.cur_phi], phi_now,
+                    s.has_U ? (const R*)s.U[s.cur_U] : null_r, s.has_U ? (R*)s.U[1 - s.cur_U] : null_w,
+                    s.has_T ? (const R*)s.T[s.cur_T] : null_r, s.has_T ? (R*)s.T[1 - s.cur_T] : null_w, (R*)s.accU,
+                    (R*)s.accT, s.acc_reset_U ? 1 : 0, s.acc_reset_T ? 1 : 0, s.smax)))
+            else
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_transfer<R, TYV>, grid_of<TYV>(s), dim3(TX, TYV),
+                    P, (const R*)s.phi[1 - s.cur_phi], phi_now, s.has_U ? (const R*)s.U[s.cur_U] : null_r,
+                    s.has_U ? (R*)s.U[1 - s.cur_U] : null_w, s.has_T ? (const R*)s.T[s.cur_T] : null_r,
+                    s.has_T ? (R*)s.T[1 - s.cur_T] : null_w, (R*)s.accU, (R*)s.accT, s.acc_reset_U ? 1 : 0,
+                    s.acc_reset_T ? 1 : 0, s.smax)))
             break;
         case LBM_K_SCALAR_U:
         case LBM_K_SCALAR_T: {

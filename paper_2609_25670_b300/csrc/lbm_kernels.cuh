@@ -234,7 +234,8 @@ __device__ __forceinline__ void transfer_tile(TransferSmem<R, TY>& sm, const KP<
                                               const R* __restrict__ phin, const R* __restrict__ Uin,
                                               R* __restrict__ Uout, const R* __restrict__ Tin, R* __restrict__ Tout,
                                               R* __restrict__ accU, R* __restrict__ accT, int acc_reset_U,
-                                              int acc_reset_T, unsigned long long* __restrict__ smax, int x0, int y0) {
+                                              int acc_reset_T, unsigned long long* __restrict__ smax, int x0, int y0,
+                                              Rect skip) {
     constexpr int TX = 32, HX = TX + 2, GX = 36, GY = TY + 4, NT = 32 * TY, NR = 2 * HX + 2 * TY;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     // item A: own halo position; item B: a ring position
@@ -253,7 +254,7 @@ __device__ __forceinline__ void transfer_tile(TransferSmem<R, TY>& sm, const KP<
     }
     const int na = ay * P.pitch + ax, nb = by * P.pitch + bx;
     const int gx = x0 + tx, gy = y0 + ty;
-    const bool own = IN || (gx < P.nx && gy < P.ny);
+    const bool own = (IN || (gx < P.nx && gy < P.ny)) && !skip.in(gx, gy);
     const int node = gy * P.pitch + gx;
     R poa = R(0), Usa = R(0), pob = R(0), Usb = R(0), Town = R(0), accUo = R(0), accTo = R(0);
     if (va) { poa = phio[na]; if (P.has_U) Usa = Uin[na]; }
@@ -326,10 +327,11 @@ __device__ __forceinline__ void transfer_tile(TransferSmem<R, TY>& sm, const KP<
 template <typename R, int TY>
 __device__ __forceinline__ void transfer_block(TransferSmem<R, TY>& sm, const KP<R>& P, const R* phio, const R* phin,
                                                const R* Uin, R* Uout, const R* Tin, R* Tout, R* accU, R* accT,
-                                               int ru, int rt, unsigned long long* smax, int x0, int y0) {
+                                               int ru, int rt, unsigned long long* smax, int x0, int y0,
+                                               Rect skip = Rect{0, 0, 0, 0}) {
     if (interior2<TY>(x0, y0, P.nx, P.ny))
-        transfer_tile<R, TY, true>(sm, P, phio, phin, Uin, Uout, Tin, Tout, accU, accT, ru, rt, smax, x0, y0);
-    else transfer_tile<R, TY, false>(sm, P, phio, phin, Uin, Uout, Tin, Tout, accU, accT, ru, rt, smax, x0, y0);
+        transfer_tile<R, TY, true>(sm, P, phio, phin, Uin, Uout, Tin, Tout, accU, accT, ru, rt, smax, x0, y0, skip);
+    else transfer_tile<R, TY, false>(sm, P, phio, phin, Uin, Uout, Tin, Tout, accU, accT, ru, rt, smax, x0, y0, skip);
 }
 
 // ---------------------------------------------------------------------------

@@ -317,6 +317,38 @@ __host__ __device__ inline VGeo vgeo(int nx, int ny, int H) {
     return g;
 }
 
+// The frame: the units (strips or tiles) of a uw x uh grid over the lattice
+// that are not wholly inside the interior rectangle, numbered row by row.
+struct Frame {
+    int nu, nv;            // units across / down
+    int xa, xb, ya, yb;    // the units wholly inside: [xa, xb) x [ya, yb)
+    __host__ __device__ int count() const { return nu * nv - (xb - xa) * (yb - ya); }
+    // unit f -> (u, v)
+    __host__ __device__ void unit(int f, int& u, int& v) const {
+        const int top = ya * nu, w = nu - (xb - xa), mid = (yb - ya) * w;
+        if (f < top) { v = f / nu; u = f % nu; return; }
+        f -= top;
+        if (f < mid) {
+            v = ya + f / w;
+            const int c = f % w;
+            u = c < xa ? c : c + (xb - xa);
+            return;
+        }
+        f -= mid;
+        v = yb + f / nu;
+        u = f % nu;
+    }
+};
+__host__ __device__ inline Frame frame_of(const Rect& in, int nx, int ny, int uw, int uh) {
+    Frame f;
+    f.nu = (nx + uw - 1) / uw;
+    f.nv = (ny + uh - 1) / uh;
+    f.xa = (in.x0 + uw - 1) / uw; f.xb = in.x1 / uw;
+    f.ya = (in.y0 + uh - 1) / uh; f.yb = in.y1 / uh;
+    if (f.xb <= f.xa || f.yb <= f.ya) f.xa = f.xb = f.ya = f.yb = 0;
+    return f;
+}
+
 template <typename T> struct alignas(sizeof(T) * VW) Vec4 { T v[VW]; };
 
 // asynchronous copy of one lane's vector (VW elements of T) into shared memory
@@ -499,9 +531,9 @@ template <typename R> struct VSRing {
     static constexpr int BYTES = VRing<R>::BYTES > V1 ? VRing<R>::BYTES : V1;   // per warp
 };
 __host__ __device__ inline int vs_vector_blocks(const VGeo& g) { return (g.nxv * g.nyv + VNW - 1) / VNW; }
-__host__ __device__ inline int vs_frame_blocks_x(int nx) { return ((nx + SW - 1) / SW + VNW - 1) / VNW; }
 __host__ __device__ inline int vs_blocks(int nx, int ny, int H) {
-    return vs_vector_blocks(vgeo(nx, ny, H)) + vs_frame_blocks_x(nx) * ((ny + H - 1) / H);
+    const VGeo g = vgeo(nx, ny, H);
+    return vs_vector_blocks(g) + (frame_of(g.in, nx, ny, SW, H).count() + VNW - 1) / VNW;
 }
 
 template <typename R, typename ST, bool DEV, int H, int FIELD>
@@ -526,11 +558,13 @@ __device__ __forceinline__ void scalar_vs_block(const KP<R>& P, const ST* fin, S
         return;
     }
     b -= nvb;
-    const int fbx = vs_frame_blocks_x(P.nx);
-    const int sx = (b % fbx) * VNW + w, y0 = (b / fbx) * H;
-    if (sx * SW >= P.nx) return;                   // whole warp: past the last strip
     const Rect& in = g.in;
-    if (SW * sx >= in.x0 && SW * sx + SW <= in.x1 && y0 >= in.y0 && y0 + H <= in.y1) return;   // all interior
+    const Frame fr = frame_of(in, P.nx, P.ny, SW, H);
+    const int f = b * VNW + w;
+    if (f >= fr.count()) return;                   // whole warp
+    int sx, t;
+    fr.unit(f, sx, t);
+    const int y0 = t * H;
     Word<R>* r1 = reinterpret_cast<Word<R>*>(mine);
     if (strip_interior<H>(sx, y0, P.nx, P.ny))
         scalar_strip<R, ST, DEV, H, FIELD, true>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, sx, y0, in, r1);
@@ -704,7 +738,8 @@ template <typename R> struct FVSmem {
 };
 __host__ __device__ inline int fvs_vector_blocks(const VGeo& g) { return (g.nxv * g.nyv + FVW - 1) / FVW; }
 __host__ __device__ inline int fvs_blocks(int nx, int ny, int H) {
-    return fvs_vector_blocks(vgeo(nx, ny, H)) + ((nx + 31) / 32) * ((ny + FVW - 1) / FVW);
+    const VGeo g = vgeo(nx, ny, H);
+    return fvs_vector_blocks(g) + frame_of(g.in, nx, ny, 32, FVW).count();
 }
 
 template <typename R, typename ST, bool DEV, int H>
@@ -729,12 +764,199 @@ __device__ __forceinline__ void flow_vs_block(const KP<R>& P, const ST* fin, ST*
         return;
     }
     b -= nvb;
-    const int tx = (P.nx + 31) / 32;
-    const int x0 = (b % tx) * 32, y0 = (b / tx) * FVW;
     const Rect& in = g.in;
-    if (x0 >= in.x0 && x0 + 32 <= in.x1 && y0 >= in.y0 && y0 + FVW <= in.y1) return;   // whole block
+    int u, v;
+    frame_of(in, P.nx, P.ny, 32, FVW).unit(b, u, v);
+    const int x0 = u * 32, y0 = v * FVW;
     flow_block<R, ST, DEV, FVW>(*reinterpret_cast<FlowSmem<R, FVW>*>(fsm), P, fin, fout, phi, ux_in, uy_in, rho_in,
                                 ux_out, uy_out, rho_out, x0, y0, in);
+}
+
+// ---------------------------------------------------------------------------
+// Phase-change transfer vector strips (Eqs. 36-39 in the interior).  Row r
+// forms J = -a grad(phi^{q+1}) / |grad(phi^{q+1})| with a = W0/(2 sqrt 2)
+// (1 + (1-k) U*) (phi^{q+1} - phi^q) at its nodes; row r - DIR, whose J
+// neighbours are then all known, gets div J (nine-point isotropic stencil
+// as column sums) and the increments Delta U, Delta T.
+// ---------------------------------------------------------------------------
+enum { TA_PN = 0, TA_PO = 1, TA_U = 2, TA_T = 3, TA_AU = 4, TA_AT = 5, TA_N = 6 };
+template <typename R> struct TRing {
+    static constexpr int EB = VW * (int)sizeof(R);
+    static constexpr int SLOT = TA_N * 32 * EB;
+    static constexpr int D = 4;
+    static constexpr int BYTES = D * SLOT;
+};
+
+template <typename R, int H, bool UP>
+__device__ __forceinline__ void transfer_vstrip(const KP<R>& P, const R* __restrict__ phio,
+                                                const R* __restrict__ phin, const R* __restrict__ Uin,
+                                                R* __restrict__ Uout, const R* __restrict__ Tin, R* __restrict__ Tout,
+                                                R* __restrict__ accU, R* __restrict__ accT, int acc_reset_U,
+                                                int acc_reset_T, unsigned long long* __restrict__ smax, int s, int y0,
+                                                unsigned char* __restrict__ ring) {
+    using RG = TRing<R>;
+    constexpr int EB = RG::EB, NR = H + 2, D = RG::D, DIR = UP ? -1 : 1;
+    const int lane = threadIdx.x & 31, pitch = P.pitch;
+    const int c0 = VSW * s + VW * lane;
+    const bool outl = lane >= 1 && lane <= 30;
+    const int rfirst = UP ? y0 + H : y0 - 1;
+    const bool ldU = P.has_U, ldT = P.has_T;
+    const bool ldAU = P.accumulated && P.has_U && !acc_reset_U, ldAT = P.accumulated && P.has_T && !acc_reset_T;
+    unsigned char* const mine = ring + lane * EB;
+    auto fetch_row = [&](int r, unsigned char* slot) {      // phi^{q+1} of row r + DIR; the rest of row r
+        const int base = r * pitch + c0;
+        fetch_vec<R>(slot + TA_PN * 32 * EB, phin + base + DIR * pitch);
+        fetch_vec<R>(slot + TA_PO * 32 * EB, phio + base);
+        if (ldU) fetch_vec<R>(slot + TA_U * 32 * EB, Uin + base);
+        if (ldT) fetch_vec<R>(slot + TA_T * 32 * EB, Tin + base);
+        if (ldAU) fetch_vec<R>(slot + TA_AU * 32 * EB, accU + base);
+        if (ldAT) fetch_vec<R>(slot + TA_AT * 32 * EB, accT + base);
+    };
+#pragma unroll
+    for (int d = 0; d < D - 1; ++d) {
+        fetch_row(rfirst + DIR * d, mine + d * RG::SLOT);
+        __pipeline_commit();
+    }
+    Vec4<R> pb = *reinterpret_cast<const Vec4<R>*>(phin + (rfirst - DIR) * pitch + c0);
+    Vec4<R> p0 = *reinterpret_cast<const Vec4<R>*>(phin + rfirst * pitch + c0);
+    const R pre = P.at_pre, omk = R(1) - P.k;
+    // row y = r - DIR: its J, phi^{q+1}, phi^q, U*, T, accumulators; row y - DIR: J
+    R jxy[VW], jyy[VW], jxz[VW], jyz[VW], pny[VW], poy[VW], Uy[VW], Ty[VW], aUy[VW], aTy[VW];
+#pragma unroll
+    for (int k = 0; k < VW; ++k)
+        jxy[k] = jyy[k] = jxz[k] = jyz[k] = pny[k] = poy[k] = Uy[k] = Ty[k] = aUy[k] = aTy[k] = R(0);
+    R mydu = R(0);
+#pragma unroll 1
+    for (int it = 0; it < NR; ++it) {
+        const int r = rfirst + DIR * it;
+        if (it + D - 1 < NR) fetch_row(r + DIR * (D - 1), mine + ((it + D - 1) % D) * RG::SLOT);
+        __pipeline_commit();
+        __pipeline_wait_prior(D - 1);
+        const unsigned char* sl = mine + (it % D) * RG::SLOT;
+        const Vec4<R> pf = sread<R>(sl + TA_PN * 32 * EB), po = sread<R>(sl + TA_PO * 32 * EB);
+        Vec4<R> Us{}, Tv{}, aU{}, aT{};
+        if (ldU) Us = sread<R>(sl + TA_U * 32 * EB);
+        if (ldT) Tv = sread<R>(sl + TA_T * 32 * EB);
+        if (ldAU) aU = sread<R>(sl + TA_AU * 32 * EB);
+        if (ldAT) aT = sread<R>(sl + TA_AT * 32 * EB);
+        const Vec4<R>& pm = UP ? pf : pb;          // phi^{q+1} rows r-1, r+1
+        const Vec4<R>& pp = UP ? pb : pf;
+        // grad phi^{q+1} at row r (column sums) and J there (Eqs. 36-37)
+        R A[VW + 2], B[VW + 2];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            A[k + 1] = p0.v[k] * (R(1) / R(3)) + (pm.v[k] + pp.v[k]) * (R(1) / R(12));
+            B[k + 1] = pp.v[k] - pm.v[k];
+        }
+        A[0] = from_left(A[VW]); B[0] = from_left(B[VW]);
+        A[VW + 1] = from_right(A[1]); B[VW + 1] = from_right(B[1]);
+        R jx[VW], jy[VW];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            const R gxv = A[k + 2] - A[k], gyv = B[k + 1] * (R(1) / R(3)) + (B[k] + B[k + 2]) * (R(1) / R(12));
+            const R g2 = gxv * gxv + gyv * gyv;
+            jx[k] = R(0);
+            jy[k] = R(0);
+            if (g2 > R(1e-12)) {
+                const R a = pre * (R(1) + omk * Us.v[k]) * (p0.v[k] - po.v[k]) * rsq(g2);
+                jx[k] = -a * gxv;                  // n = -grad phi / |grad phi|
+                jy[k] = -a * gyv;
+            }
+        }
+        if (it >= 2) {
+            // div J at row y: column sums over rows y-1, y, y+1
+            const R(&jxm)[VW] = UP ? jx : jxz;
+            const R(&jxp)[VW] = UP ? jxz : jx;
+            const R(&jym)[VW] = UP ? jy : jyz;
+            const R(&jyp)[VW] = UP ? jyz : jy;
+            R Sx[VW + 2], Dy[VW + 2];
+#pragma unroll
+            for (int k = 0; k < VW; ++k) {
+                Sx[k + 1] = jxy[k] * (R(1) / R(3)) + (jxm[k] + jxp[k]) * (R(1) / R(12));
+                Dy[k + 1] = jyp[k] - jym[k];
+            }
+            Sx[0] = from_left(Sx[VW]); Dy[0] = from_left(Dy[VW]);
+            Sx[VW + 1] = from_right(Sx[1]); Dy[VW + 1] = from_right(Dy[1]);
+            if (outl) {
+                const int node = (r - DIR) * pitch + c0;
+                Vec4<R> oU, oT;
+#pragma unroll
+                for (int k = 0; k < VW; ++k) {
+                    const R div = Sx[k + 2] - Sx[k] + Dy[k + 1] * (R(1) / R(3)) + (Dy[k] + Dy[k + 2]) * (R(1) / R(12));
+                    const R dphi = pny[k] - poy[k];
+                    if (ldU) {
+                        const R dU = ((R(1) + omk * Uy[k]) * dphi - R(2) * div) * rcp((R(1) + P.k) - omk * pny[k]);  // Eq. 38
+                        mydu = fmax(mydu, fabs(dU));
+                        oU.v[k] = P.accumulated ? aUy[k] + dU : Uy[k] + dU;                  // Eq. 39
+                    }
+                    if (ldT) {
+                        const R rc = R(0.5) * (R(1) + pny[k]) * P.cS + R(0.5) * (R(1) - pny[k]) * P.cL;
+                        const R dT = P.rhoL_Lh * dphi * rcp(R(2) * rc);                       // Eq. 38
+                        oT.v[k] = P.accumulated ? aTy[k] + dT : Ty[k] + dT;
+                    }
+                }
+                if (ldU) *reinterpret_cast<Vec4<R>*>((P.accumulated ? accU : Uout) + node) = oU;
+                if (ldT) *reinterpret_cast<Vec4<R>*>((P.accumulated ? accT : Tout) + node) = oT;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            jxz[k] = jxy[k]; jyz[k] = jyy[k]; jxy[k] = jx[k]; jyy[k] = jy[k];
+            pny[k] = p0.v[k]; poy[k] = po.v[k]; Uy[k] = Us.v[k]; Ty[k] = Tv.v[k]; aUy[k] = aU.v[k]; aTy[k] = aT.v[k];
+        }
+        pb = p0;
+        p0 = pf;
+    }
+    if (P.has_U) {           // warp maximum of |Delta U_pc| -> S_phi (and J_U when instantaneous)
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) mydu = fmax(mydu, __shfl_xor_sync(0xffffffffu, mydu, d));
+        if (lane == 0) {
+            atomic_max_pos(&smax[0], (double)mydu);
+            if (!P.accumulated) atomic_max_pos(&smax[1], (double)mydu);
+        }
+    }
+}
+
+constexpr int TVW = 4;     // warps per block of the transfer vector launch (= tile height of its frame)
+template <typename R> struct TVSmem {
+    static constexpr int STRIPS = TVW * TRing<R>::BYTES;
+    static constexpr int TILE = (int)sizeof(TransferSmem<R, TVW>);
+    static constexpr int BYTES = STRIPS > TILE ? STRIPS : TILE;
+};
+__host__ __device__ inline int tvs_vector_blocks(const VGeo& g) { return (g.nxv * g.nyv + TVW - 1) / TVW; }
+__host__ __device__ inline int tvs_blocks(int nx, int ny, int H) {
+    const VGeo g = vgeo(nx, ny, H);
+    return tvs_vector_blocks(g) + frame_of(g.in, nx, ny, 32, TVW).count();
+}
+
+template <typename R, int H>
+__device__ __forceinline__ void transfer_vs_block(const KP<R>& P, const R* phio, const R* phin, const R* Uin, R* Uout,
+                                                  const R* Tin, R* Tout, R* accU, R* accT, int ru, int rt,
+                                                  unsigned long long* smax, int b) {
+    extern __shared__ __align__(128) unsigned char tsm[];   // TVSmem<R>::BYTES, dynamic
+    const VGeo g = vgeo(P.nx, P.ny, H);
+    const int nvb = tvs_vector_blocks(g);
+    if (b < nvb) {
+        const int w = threadIdx.y;
+        const int vs = b * TVW + w;
+        if (vs >= g.nxv * g.nyv) return;           // whole warp (no block barrier on this path)
+        const int sy = vs / g.nxv;
+        unsigned char* mine = tsm + w * TRing<R>::BYTES;
+        if (sy & 1)
+            transfer_vstrip<R, H, true>(P, phio, phin, Uin, Uout, Tin, Tout, accU, accT, ru, rt, smax, vs % g.nxv,
+                                        VY0 + H * sy, mine);
+        else
+            transfer_vstrip<R, H, false>(P, phio, phin, Uin, Uout, Tin, Tout, accU, accT, ru, rt, smax, vs % g.nxv,
+                                         VY0 + H * sy, mine);
+        return;
+    }
+    b -= nvb;
+    const Rect& in = g.in;
+    int u, v;
+    frame_of(in, P.nx, P.ny, 32, TVW).unit(b, u, v);
+    const int x0 = u * 32, y0 = v * TVW;
+    transfer_block<R, TVW>(*reinterpret_cast<TransferSmem<R, TVW>*>(tsm), P, phio, phin, Uin, Uout, Tin, Tout, accU,
+                           accT, ru, rt, smax, x0, y0, in);
 }
 
 }  // namespace lbmk
@@ -785,6 +1007,22 @@ __global__ void __launch_bounds__(32 * VNW) k_scalar_vs_batch(const ScalarJob<R,
     const ScalarJob<R, ST>& j = job_block(jobs, njobs, blockIdx.x, bx, by);
     scalar_vs_block<R, ST, DEV, H, FIELD>(*j.P, j.fin, j.fout, j.mac_in, j.mac_out, j.acc, j.phi, j.ux, j.uy, j.smax,
                                           by * j.tiles_x + bx);
+}
+template <typename R, int H>
+__global__ void __launch_bounds__(32 * TVW)
+k_transfer_vs(const KP<R>* __restrict__ P, const R* __restrict__ phio, const R* __restrict__ phin,
+              const R* __restrict__ Uin, R* __restrict__ Uout, const R* __restrict__ Tin, R* __restrict__ Tout,
+              R* __restrict__ accU, R* __restrict__ accT, int acc_reset_U, int acc_reset_T,
+              unsigned long long* __restrict__ smax) {
+    transfer_vs_block<R, H>(*P, phio, phin, Uin, Uout, Tin, Tout, accU, accT, acc_reset_U, acc_reset_T, smax,
+                            blockIdx.x);
+}
+template <typename R, int H>
+__global__ void __launch_bounds__(32 * TVW) k_transfer_vs_batch(const TransferJob<R>* __restrict__ jobs, int njobs) {
+    int bx, by;
+    const TransferJob<R>& j = job_block(jobs, njobs, blockIdx.x, bx, by);
+    transfer_vs_block<R, H>(*j.P, j.phio, j.phin, j.Uin, j.Uout, j.Tin, j.Tout, j.accU, j.accT, j.acc_reset_U,
+                            j.acc_reset_T, j.smax, by * j.tiles_x + bx);
 }
 template <typename R, typename ST, bool DEV, int H>
 __global__ void __launch_bounds__(32 * FVW)
