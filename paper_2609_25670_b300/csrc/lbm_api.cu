@@ -358,6 +358,7 @@ inline void blocks_of(int kind, int v, int nx, int ny, int& bx, int& by) {
     if (v > VS) {
         bx = kind == LBM_K_FLOW       ? fvs_blocks(nx, ny, v - VS)
              : kind == LBM_K_TRANSFER ? tvs_blocks(nx, ny, v - VS)
+             : kind == LBM_K_PHASE    ? pvs_blocks(nx, ny, v - VS)
                                       : vs_blocks(nx, ny, v - VS);
         by = 1;
     } else if (v > 0) {
@@ -375,7 +376,9 @@ inline dim3 grid_v(const SimState& s, int kind, int v) {
     return dim3(bx, by);
 }
 inline bool has_strips(int kind) { return kind == LBM_K_SCALAR_U || kind == LBM_K_SCALAR_T; }
-inline bool has_vstrips(int kind) { return has_strips(kind) || kind == LBM_K_FLOW || kind == LBM_K_TRANSFER; }
+inline bool has_vstrips(int kind) {
+    return has_strips(kind) || kind == LBM_K_FLOW || kind == LBM_K_TRANSFER || kind == LBM_K_PHASE;
+}
 inline bool valid_variant(int kind, int v) {
     return v == 4 || v == 8 || v == 16 ||
            (has_strips(kind) && (v == -4 || v == -8 || v == -16 || v == -32)) ||
@@ -486,8 +489,12 @@ void launch_batch(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, 
     const dim3 g(tiles);
     switch (kind) {
         case LBM_K_PHASE:
-            LBM_TY_SWITCH(tysel, (launch_ex(h, k_phase_batch<R, ST, DEV, TYV>, g, dim3(TX, TYV),
-                                            (const PhaseJob<R, ST>*)jobs, njobs)));
+            if (tysel > VS)
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_phase_vs_batch<R, ST, DEV, HV>, g, dim3(32, PVW),
+                                                     (size_t)PVSmem<R>::BYTES, (const PhaseJob<R, ST>*)jobs, njobs)))
+            else
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_phase_batch<R, ST, DEV, TYV>, g, dim3(TX, TYV),
+                                                (const PhaseJob<R, ST>*)jobs, njobs)))
             break;
         case LBM_K_TRANSFER:
             if (tysel > VS)
@@ -564,10 +571,16 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
     R* null_w = nullptr;
     switch (kind) {
         case LBM_K_PHASE:
-            LBM_TY_SWITCH(tysel, (launch_ex(h, k_phase<R, ST, DEV, TYV>, grid_of<TYV>(s), dim3(TX, TYV),
-                P, (const ST*)s.pops[FP][s.cur_pop[FP]], (ST*)s.pops[FP][1 - s.cur_pop[FP]], phi_now,
-                (R*)s.phi[1 - s.cur_phi], s.has_U ? (const R*)s.U[s.cur_U] : null_r,
-                s.has_T ? (const R*)s.T[s.cur_T] : null_r, clock, off)));
+            if (tysel > VS)
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_phase_vs<R, ST, DEV, HV>, grid_v(s, kind, tysel),
+                    dim3(32, PVW), (size_t)PVSmem<R>::BYTES, P, (const ST*)s.pops[FP][s.cur_pop[FP]],
+                    (ST*)s.pops[FP][1 - s.cur_pop[FP]], phi_now, (R*)s.phi[1 - s.cur_phi],
+                    s.has_U ? (const R*)s.U[s.cur_U] : null_r, s.has_T ? (const R*)s.T[s.cur_T] : null_r, clock, off)))
+            else
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_phase<R, ST, DEV, TYV>, grid_of<TYV>(s), dim3(TX, TYV),
+                    P, (const ST*)s.pops[FP][s.cur_pop[FP]], (ST*)s.pops[FP][1 - s.cur_pop[FP]], phi_now,
+                    (R*)s.phi[1 - s.cur_phi], s.has_U ? (const R*)s.U[s.cur_U] : null_r,
+                    s.has_T ? (const R*)s.T[s.cur_T] : null_r, clock, off)))
             break;
         case LBM_K_TRANSFER:   // phi^q = phi[1 - cur], phi^{q+1} = phi[cur] (after the phase flip)
             if (tysel > VS)

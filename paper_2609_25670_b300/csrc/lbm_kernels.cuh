@@ -138,7 +138,7 @@ template <typename R, typename ST, bool DEV, int TY, bool IN>
 __device__ __forceinline__ void phase_tile(PhaseSmem<R, TY>& sm, const KP<R>& P, const ST* __restrict__ fin,
                                            ST* __restrict__ fout, const R* __restrict__ phi, R* __restrict__ phin,
                                            const R* __restrict__ Um, const R* __restrict__ Tm, R tnow, int x0,
-                                           int y0) {
+                                           int y0, Rect skip) {
     constexpr int TX = 32, HX = TX + 2, NR = 2 * HX + 2 * TY;
     static_assert(NR <= 32 * TY, "ring larger than the block");
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -175,6 +175,7 @@ __device__ __forceinline__ void phase_tile(PhaseSmem<R, TY>& sm, const KP<R>& P,
     __syncthreads();
     if (!own) return;
     const int gx = x0 + tx, gy = y0 + ty;
+    if (skip.in(gx, gy)) return;                  // written by the vector strips of the same launch
     const R c = sm.phi[ty + 2][tx + 2];
     const R inva2 = rcp(a2own);
     R s8 = R(0);
@@ -201,11 +202,13 @@ __device__ __forceinline__ void phase_tile(PhaseSmem<R, TY>& sm, const KP<R>& P,
 template <typename R, typename ST, bool DEV, int TY>
 __device__ __forceinline__ void phase_block(PhaseSmem<R, TY>& sm, const KP<R>& P, const ST* fin, ST* fout,
                                             const R* phi, R* phin, const R* Um, const R* Tm,
-                                            const long long* clock, long long off, int x0, int y0) {
+                                            const long long* clock, long long off, int x0, int y0,
+                                            Rect skip = Rect{0, 0, 0, 0}) {
     R tnow = R(0);
     if (P.frozen_T) tnow = (R)((clock ? *clock : 0ll) + off) * P.dt_base;
-    if (interior2<TY>(x0, y0, P.nx, P.ny)) phase_tile<R, ST, DEV, TY, true>(sm, P, fin, fout, phi, phin, Um, Tm, tnow, x0, y0);
-    else phase_tile<R, ST, DEV, TY, false>(sm, P, fin, fout, phi, phin, Um, Tm, tnow, x0, y0);
+    if (interior2<TY>(x0, y0, P.nx, P.ny))
+        phase_tile<R, ST, DEV, TY, true>(sm, P, fin, fout, phi, phin, Um, Tm, tnow, x0, y0, skip);
+    else phase_tile<R, ST, DEV, TY, false>(sm, P, fin, fout, phi, phin, Um, Tm, tnow, x0, y0, skip);
 }
 
 // ---------------------------------------------------------------------------

@@ -959,6 +959,210 @@ __device__ __forceinline__ void transfer_vs_block(const KP<R>& P, const R* phio,
                            accT, ru, rt, smax, x0, y0, in);
 }
 
+// ---------------------------------------------------------------------------
+// Phase-field vector strips (Eqs. 2-4, 14, 21-24, 26, 18 in the interior).
+// The anisotropic streaming of Eq. 26 blends the incoming post-collision
+// value with the destination's own pre-collision population,
+// f_i <- f_i + (p_i(x - e_i) - f_i) / a_s^2(x), so a completed row also needs
+// its own loaded populations and a_s^2, carried from its collision.
+// ---------------------------------------------------------------------------
+enum { PA_PHI = 8, PA_U = 9, PA_T = 10, PA_N = 11 };
+template <typename R> struct PRing {
+    static constexpr int EB = VW * (int)sizeof(R);
+    static constexpr int SLOT = PA_N * 32 * EB;
+    static constexpr int D = sizeof(R) == 8 ? 2 : 4;
+    static constexpr int BYTES = D * SLOT;
+};
+
+template <typename R, typename ST, bool DEV, int H, bool UP>
+__device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restrict__ fin, ST* __restrict__ fout,
+                                             const R* __restrict__ phi, R* __restrict__ phin,
+                                             const R* __restrict__ Um, const R* __restrict__ Tm, R tnow, int s,
+                                             int y0, unsigned char* __restrict__ ring) {
+    using RG = PRing<R>;
+    constexpr int EB = RG::EB, NR = H + 2, D = RG::D, DIR = UP ? -1 : 1;
+    constexpr int FAX = UP ? 4 : 2, FL = UP ? 8 : 5, FR = UP ? 7 : 6;     // far row: axis, from left, from right
+    constexpr int NAX = UP ? 2 : 4, NL = UP ? 5 : 8, NRt = UP ? 6 : 7;    // near row (just collided)
+    const int lane = threadIdx.x & 31, pl = (int)P.plane, pitch = P.pitch;
+    const int c0 = VSW * s + VW * lane;
+    const bool outl = lane >= 1 && lane <= 30;
+    const int rfirst = UP ? y0 + H : y0 - 1;
+    unsigned char* const mine = ring + lane * EB;
+    auto fetch_row = [&](int r, unsigned char* slot) {      // populations, U, T of row r; phi of row r + DIR
+        const int base = r * pitch + c0;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) fetch_vec<ST>(slot + (i - 1) * 32 * EB, fin + (size_t)(i - 1) * pl + base);
+        fetch_vec<R>(slot + PA_PHI * 32 * EB, phi + base + DIR * pitch);
+        if (P.has_U) fetch_vec<R>(slot + PA_U * 32 * EB, Um + base);
+        if (P.has_T) fetch_vec<R>(slot + PA_T * 32 * EB, Tm + base);
+    };
+#pragma unroll
+    for (int d = 0; d < D - 1; ++d) {
+        fetch_row(rfirst + DIR * d, mine + d * RG::SLOT);
+        __pipeline_commit();
+    }
+    Vec4<R> pb = *reinterpret_cast<const Vec4<R>*>(phi + (rfirst - DIR) * pitch + c0);
+    Vec4<R> p0 = *reinterpret_cast<const Vec4<R>*>(phi + rfirst * pitch + c0);
+    // row y: own loaded populations (raw), phi, a_s^2, post values q0, q1s,
+    // q3s and its far triple; far row: za, zb, zc
+    R fy[9][VW], cy[VW], ay[VW], q0[VW], q1[VW], q3[VW], qa[VW], qb[VW], qc[VW], za[VW], zb[VW], zc[VW];
+#pragma unroll
+    for (int k = 0; k < VW; ++k) {
+#pragma unroll
+        for (int i = 1; i < 9; ++i) fy[i][k] = R(0);
+        cy[k] = R(0); ay[k] = R(1);
+        q0[k] = q1[k] = q3[k] = qa[k] = qb[k] = qc[k] = za[k] = zb[k] = zc[k] = R(0);
+    }
+#pragma unroll 1
+    for (int it = 0; it < NR; ++it) {
+        const int r = rfirst + DIR * it;
+        if (it + D - 1 < NR) fetch_row(r + DIR * (D - 1), mine + ((it + D - 1) % D) * RG::SLOT);
+        __pipeline_commit();
+        __pipeline_wait_prior(D - 1);
+        const unsigned char* sl = mine + (it % D) * RG::SLOT;
+        R f[9][VW];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const Vec4<ST> v = sread<ST>(sl + (i - 1) * 32 * EB);
+#pragma unroll
+            for (int k = 0; k < VW; ++k) f[i][k] = (R)Cvt<ST>::ld(v.v[k]);
+        }
+        const Vec4<R> pf = sread<R>(sl + PA_PHI * 32 * EB);
+        Vec4<R> Us{}, Tv{};
+        if (P.has_U) Us = sread<R>(sl + PA_U * 32 * EB);
+        if (P.has_T) Tv = sread<R>(sl + PA_T * 32 * EB);
+        const Vec4<R>& pm = UP ? pf : pb;
+        const Vec4<R>& pp = UP ? pb : pf;
+        R A[VW + 2], B[VW + 2];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            A[k + 1] = p0.v[k] * (R(1) / R(3)) + (pm.v[k] + pp.v[k]) * (R(1) / R(12));
+            B[k + 1] = pp.v[k] - pm.v[k];
+        }
+        A[0] = from_left(A[VW]); B[0] = from_left(B[VW]);
+        A[VW + 1] = from_right(A[1]); B[VW + 1] = from_right(B[1]);
+        R p[VW][9], a2[VW];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            const R gxv = A[k + 2] - A[k], gyv = B[k + 1] * (R(1) / R(3)) + (B[k] + B[k + 2]) * (R(1) / R(12));
+            const R c = p0.v[k];
+            R as, Nx, Ny;
+            aniso(gxv, gyv, P.eps, as, Nx, Ny);
+            a2[k] = as * as;
+            const R sv = rcp(R(3) * P.dtp * a2[k] * P.W0sq_tau0 + R(0.5));                // Eq. 24
+            R th;
+            if (P.has_T) th = (Tv.v[k] - P.T_shift) * P.inv_T_scale;                    // Eq. 5
+            else if (P.frozen_T) th = theta_frozen(P, r, tnow);
+            else th = P.theta_c;
+            const R one = R(1) - c * c;
+            const R Q = c * one - P.lam * (P.Mc * Us.v[k] + th) * one * one;              // Eq. 4
+            const R bx = -P.dtp * P.W0sq_tau0 * Nx, by = -P.dtp * P.W0sq_tau0 * Ny;     // dt v_n (Eqs. 21-22)
+            const R k6 = (R(1) - sv) * (R(1) / R(6));
+            const R jx = f[1][k] - f[3][k] + f[5][k] - f[6][k] - f[7][k] + f[8][k];
+            const R jy = f[2][k] - f[4][k] + f[5][k] + f[6][k] - f[7][k] - f[8][k];
+            scalar_post9<R>(c + P.dtp * Q * P.inv_tau0, bx, by, k6 * (jx - bx), k6 * (jy - by), p[k]);
+        }
+        R s1[VW], s5[VW], s8[VW], s3[VW], s6[VW], s7[VW];
+        s1[0] = from_left(p[VW - 1][1]); s5[0] = from_left(p[VW - 1][5]); s8[0] = from_left(p[VW - 1][8]);
+        s3[VW - 1] = from_right(p[0][3]); s6[VW - 1] = from_right(p[0][6]); s7[VW - 1] = from_right(p[0][7]);
+#pragma unroll
+        for (int k = 1; k < VW; ++k) { s1[k] = p[k - 1][1]; s5[k] = p[k - 1][5]; s8[k] = p[k - 1][8]; }
+#pragma unroll
+        for (int k = 0; k < VW - 1; ++k) { s3[k] = p[k + 1][3]; s6[k] = p[k + 1][6]; s7[k] = p[k + 1][7]; }
+        R(&sNL)[VW] = UP ? s5 : s8;
+        R(&sNR)[VW] = UP ? s6 : s7;
+        if (it >= 2 && outl) {                     // complete row y = r - DIR (Eq. 26, Eq. 18)
+            const int node = (r - DIR) * pitch + c0;
+            Vec4<R> sum;
+            R fn[9][VW];
+#pragma unroll
+            for (int k = 0; k < VW; ++k) {
+                const R c = cy[k];
+                R fa[9], s8v = R(0);
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    fa[i] = fy[i][k];
+                    if (DEV) fa[i] += wq<R>(i) * c;                                  // decode h_i = f_i - w_i phi
+                    s8v += fa[i];
+                }
+                fa[0] = c - s8v;                                                     // population 0 from phi
+                R inc[9];
+                inc[0] = q0[k]; inc[1] = q1[k]; inc[3] = q3[k];
+                inc[FAX] = za[k]; inc[FL] = zb[k]; inc[FR] = zc[k];
+                inc[NAX] = p[k][NAX]; inc[NL] = sNL[k]; inc[NRt] = sNR[k];
+                const R inva2 = rcp(ay[k]);
+                R t = R(0);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    fn[i][k] = fa[i] + (inc[i] - fa[i]) * inva2;
+                    t += fn[i][k];
+                }
+                sum.v[k] = t;
+            }
+            *reinterpret_cast<Vec4<R>*>(phin + node) = sum;
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                Vec4<ST> o;
+#pragma unroll
+                for (int k = 0; k < VW; ++k) o.v[k] = Cvt<ST>::st(DEV ? fn[i][k] - wq<R>(i) * sum.v[k] : fn[i][k]);
+                *reinterpret_cast<Vec4<ST>*>(fout + (size_t)(i - 1) * pl + node) = o;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            za[k] = qa[k]; zb[k] = qb[k]; zc[k] = qc[k];
+            q0[k] = p[k][0]; q1[k] = s1[k]; q3[k] = s3[k];
+            qa[k] = p[k][FAX]; qb[k] = UP ? s8[k] : s5[k]; qc[k] = UP ? s7[k] : s6[k];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) fy[i][k] = f[i][k];
+            cy[k] = p0.v[k];
+            ay[k] = a2[k];
+        }
+        pb = p0;
+        p0 = pf;
+    }
+}
+
+constexpr int PVW = 4;     // warps per block of the phase vector launch (= tile height of its frame)
+template <typename R> struct PVSmem {
+    static constexpr int STRIPS = PVW * PRing<R>::BYTES;
+    static constexpr int TILE = (int)sizeof(PhaseSmem<R, PVW>);
+    static constexpr int BYTES = STRIPS > TILE ? STRIPS : TILE;
+};
+__host__ __device__ inline int pvs_blocks(int nx, int ny, int H) {
+    const VGeo g = vgeo(nx, ny, H);
+    return (g.nxv * g.nyv + PVW - 1) / PVW + frame_of(g.in, nx, ny, 32, PVW).count();
+}
+
+template <typename R, typename ST, bool DEV, int H>
+__device__ __forceinline__ void phase_vs_block(const KP<R>& P, const ST* fin, ST* fout, const R* phi, R* phin,
+                                               const R* Um, const R* Tm, const long long* clock, long long off,
+                                               int b) {
+    extern __shared__ __align__(128) unsigned char psm[];   // PVSmem<R>::BYTES, dynamic
+    const VGeo g = vgeo(P.nx, P.ny, H);
+    const int nvb = (g.nxv * g.nyv + PVW - 1) / PVW;
+    if (b < nvb) {
+        const int w = threadIdx.y;
+        const int vs = b * PVW + w;
+        if (vs >= g.nxv * g.nyv) return;           // whole warp (no block barrier on this path)
+        R tnow = R(0);
+        if (P.frozen_T) tnow = (R)((clock ? *clock : 0ll) + off) * P.dt_base;
+        const int sy = vs / g.nxv;
+        unsigned char* mine = psm + w * PRing<R>::BYTES;
+        if (sy & 1)
+            phase_vstrip<R, ST, DEV, H, true>(P, fin, fout, phi, phin, Um, Tm, tnow, vs % g.nxv, VY0 + H * sy, mine);
+        else
+            phase_vstrip<R, ST, DEV, H, false>(P, fin, fout, phi, phin, Um, Tm, tnow, vs % g.nxv, VY0 + H * sy,
+                                               mine);
+        return;
+    }
+    b -= nvb;
+    int u, v;
+    frame_of(g.in, P.nx, P.ny, 32, PVW).unit(b, u, v);
+    phase_block<R, ST, DEV, PVW>(*reinterpret_cast<PhaseSmem<R, PVW>*>(psm), P, fin, fout, phi, phin, Um, Tm, clock,
+                                 off, u * 32, v * PVW, g.in);
+}
+
 }  // namespace lbmk
 
 // ---------------------------------------------------------------------------
@@ -1007,6 +1211,20 @@ __global__ void __launch_bounds__(32 * VNW) k_scalar_vs_batch(const ScalarJob<R,
     const ScalarJob<R, ST>& j = job_block(jobs, njobs, blockIdx.x, bx, by);
     scalar_vs_block<R, ST, DEV, H, FIELD>(*j.P, j.fin, j.fout, j.mac_in, j.mac_out, j.acc, j.phi, j.ux, j.uy, j.smax,
                                           by * j.tiles_x + bx);
+}
+template <typename R, typename ST, bool DEV, int H>
+__global__ void __launch_bounds__(32 * PVW)
+k_phase_vs(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout, const R* __restrict__ phi,
+           R* __restrict__ phin, const R* __restrict__ Um, const R* __restrict__ Tm,
+           const long long* __restrict__ clock, long long step_off) {
+    phase_vs_block<R, ST, DEV, H>(*P, fin, fout, phi, phin, Um, Tm, clock, step_off, blockIdx.x);
+}
+template <typename R, typename ST, bool DEV, int H>
+__global__ void __launch_bounds__(32 * PVW) k_phase_vs_batch(const PhaseJob<R, ST>* __restrict__ jobs, int njobs) {
+    int bx, by;
+    const PhaseJob<R, ST>& j = job_block(jobs, njobs, blockIdx.x, bx, by);
+    phase_vs_block<R, ST, DEV, H>(*j.P, j.fin, j.fout, j.phi, j.phin, j.Um, j.Tm, j.clock, j.off,
+                                  by * j.tiles_x + bx);
 }
 template <typename R, int H>
 __global__ void __launch_bounds__(32 * TVW)

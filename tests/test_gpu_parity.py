@@ -158,7 +158,7 @@ def test_init_seed_matches_generator():
 
 UPDATE_KINDS = ("phase", "transfer", "scalar_U", "scalar_T", "flow", "transport")
 STRIP_KINDS = ("scalar_U", "scalar_T")
-VSTRIP_KINDS = ("transfer", "scalar_U", "scalar_T", "flow")
+VSTRIP_KINDS = ("phase", "transfer", "scalar_U", "scalar_T", "flow")
 
 
 @pytest.mark.parametrize("h", [4, 8, 16, 32])
@@ -207,6 +207,23 @@ def test_vector_strip_kernels_match_oracle_fp64(h, bc):
     o = run_oracle(p, f, 24)
     for k in got:
         assert np.abs(got[k] - o[k]).max() < 1e-11, k
+
+
+def test_vector_strips_directional_fp64():
+    """Vector strips with the frozen, pulled temperature field (directional
+    solidification: theta from the base-step clock) against the oracle."""
+    import paper_2609_25670_b300 as lbm
+    wl = W.directional_saline(Le=10, nx=256, ny=160, y0=40.0, seed=3)
+    sim = lbm.Simulation(wl.params, precision="f64")
+    for k in VSTRIP_KINDS:
+        sim.set_tile(k, 1008)
+    sim.init_fields(wl.fields)
+    sim.advance(50)
+    got = {k: sim.field(k) for k in active(wl.params)}
+    sim.close()
+    o = run_oracle(wl.params, wl.fields, 50)
+    for k in got:
+        assert np.abs(got[k] - o[k]).max() < 1e-10, k
 
 
 def test_vector_strips_accumulated_fp64():
