@@ -104,21 +104,26 @@ def period_bytes(p, prec="f32"):
     return tot, n
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu
-# capture, cold cache) of each update kernel on the 512^2 workload, from the
-# capture summarised in profiles/update_kernels_convection512_f32_ncu_full.md.
-# Reported only while the kernel sources hash to TRAFFIC_SOURCE_SHA; after any
-# change to them the roofline's traffic is null until re-measured.
-TRAFFIC_SOURCE_SHA = None
-TRAFFIC_PER_LAUNCH = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one ncu
+# capture per kernel variant ("kind:variant"), summarised in profiles/: per
+# launch on the 512^2 workload, and per node on 2048^2 (scaled by the nodes a
+# launch processes for the 8192^2 measurement; traffic grows with the node
+# count once the state exceeds L2).  Reported only while the kernel sources
+# hash to TRAFFIC_SOURCE_SHA; after any change the traffic is null until
+# re-measured.
+TRAFFIC_SOURCE_SHA = "a54cd5b8d884bb4c"
+TRAFFIC_PER_LAUNCH_512 = {"transport:8": 33328384.0, "phase:4": 11564032.0}
+TRAFFIC_PER_NODE_2048 = {"phase:1016": 72.46, "transfer:1016": 17.17, "scalar_T:1008": 75.71, "flow:1016": 83.57}
 
 
 def kernel_source_sha():
     import hashlib
     h = hashlib.sha256()
-    for nm in ("lbm_common.cuh", "lbm_kernels.cuh"):
-        with open(os.path.join(ROOT, "paper_2609_25670_b300", "csrc", nm), "rb") as f:
-            h.update(f.read())
+    d = os.path.join(ROOT, "paper_2609_25670_b300", "csrc")
+    for nm in sorted(os.listdir(d)):
+        if nm.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, nm), "rb") as f:
+                h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -336,7 +341,7 @@ def run_ours(args):
     achieved = algo[dom] * nodes / avg_s / 1e9
     traffic = None
     if args.lattice in (None, N_LATTICE) and prec == "f32" and TRAFFIC_SOURCE_SHA == kernel_source_sha():
-        traffic = TRAFFIC_PER_LAUNCH.get(dom)
+        traffic = TRAFFIC_PER_LAUNCH_512.get("%s:%d" % (dom, tiles[dom]))
 
     # end to end through the public API with pinned host buffers
     host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in wl.fields.items()}
@@ -376,13 +381,91 @@ def run_ours(args):
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps, "calls": "init_fields(host f64 x6) + advance(2) + field(phi -> host)"},
         }
+    sim.close()
+    del flush
+    if rank == 0:
+        if not args.no_large and world == 1:
+            line["large_lattice"] = large_lattice(args, torch, lbm, local, measured_peaks)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
-    sim.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def large_lattice(args, torch, lbm, local, peaks_fn):
+    """The HBM-bound regime: the 8192^2 multi-dendrite workload (thermosolutal
+    growth with convection, 32 Poisson-disc seeds, update factors (1, 1, 4,
+    2), FP32; about 20 GB of state, so every step streams from HBM).  Seeded
+    on the device's own data path (lbm_init_seed), autotuned, then timed over
+    whole schedule periods of 4 base steps with CUDA events."""
+    p, pts = W.multi_dendrite_params(8192)
+    sim = lbm.Simulation(p, precision="f32")
+    sim.init_seed([{"kind": "circle", "x": float(x), "y": float(y), "r": 8.0} for x, y in pts], U0=0.0, T0=-0.55)
+    period = 4
+    for _ in range(2):
+        sim.advance(period)
+    tiles = sim.autotune(reps=3)
+    sim.advance(period)
+    kinds = ["phase", "transfer", "scalar_U", "scalar_T", "flow", "transport"]
+    sim.timing_enable(kinds)
+    sim.advance(2 * period)
+    pre = sim.timing_read(reset=True)
+    dom = max(kinds, key=lambda k: pre[k][0])
+    sim.timing_enable([dom])
+    sim.advance(period)
+    sim.timing_read(reset=True)
+    steps = 10
+    stream = sim.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+    for _ in range(steps):
+        sim.advance(period)
+    with torch.cuda.stream(stream):
+        e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    kt = sim.timing_read(reset=True)
+    fused = sim.fused
+    sim.close()
+    nodes = p.nx * p.ny
+    base = steps * period
+    ab = algo_bytes("f32")
+    # algorithmic bytes per node per base step of the staged path (the fused
+    # path moves fewer); U every step, T every 4th, flow every 2nd
+    step_bytes = ab["phase"] + ab["transfer"] + ab["scalar_U"] + ab["scalar_T"] / p.N_T + ab["flow"] / p.N_F
+    if fused:
+        tb, tn = period_bytes(p)
+        step_bytes = ab["phase"] + tb / (2 * period)
+    peak, peak_kind = peaks_fn()
+    gbs = step_bytes * nodes * base / (ms * 1e-3) / 1e9
+    dom_algo = dict(ab)
+    tb, tn = period_bytes(p)
+    dom_algo["transport"] = tb / max(tn, 1)
+    avg_s = kt[dom][0] * 1e-3 / max(kt[dom][1], 1)
+    dom_gbs = dom_algo[dom] * nodes / avg_s / 1e9
+    traffic = None
+    per_node = TRAFFIC_PER_NODE_2048.get("%s:%d" % (dom, tiles[dom]))
+    if per_node is not None and TRAFFIC_SOURCE_SHA == kernel_source_sha():
+        traffic = per_node * nodes
+    return {"workload": "8192x8192 multi-dendrite thermosolutal growth with convection, 32 seeds, N=(1,1,4,2), FP32",
+            "value": nodes * base / (ms * 1e-3) / 1e6, "unit": UNIT, "base_steps": base,
+            "ms_per_period": ms / steps, "fused_transport": fused,
+            "step": {"algo_bytes_per_node_per_base_step": step_bytes, "achieved_GBs": gbs, "peak": peak,
+                     "frac": gbs / peak, "peak_kind": peak_kind},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
+                         "frac": dom_gbs / peak, "traffic": traffic, "traffic_note": "2048^2 capture scaled by nodes",
+                         "algo_bytes_per_node": dom_algo[dom], "avg_launch_us": avg_s * 1e6,
+                         "launches_timed": kt[dom][1]},
+            "kernel_avg_us_prepass": {k: pre[k][0] / max(pre[k][1], 1) * 1e3 for k in kinds},
+            "tiles": {k: tiles[k] for k in kinds}, "clocks": clk, "l2": "inputs larger than L2 (~20 GB state)"}
 
 
 def run_ensemble(args):
@@ -447,6 +530,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
+    ap.add_argument("--no-large", action="store_true", help="skip the 8192^2 HBM-bound measurement")
     ap.add_argument("--fusion", default="auto", choices=["auto", "on", "off"],
                     help="one fused transport launch per base step (on), one launch per stage (off), "
                          "or the autotuner's choice (auto)")

@@ -1283,8 +1283,18 @@ lbm_status lbm_init_seed(lbm_handle h, int32_t sim, const lbm_seed* seeds, int32
         const lbm_seed& sd = seeds[k];
         if (sd.kind < LBM_SEED_CIRCLE || sd.kind > LBM_SEED_SINUSOID)
             return fail(h, LBM_E_INVALID_ARG, "seed %d: unknown kind %d", k, sd.kind);
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x) {
+        // a circle only changes nodes within r + 20 sqrt(2) W0 of its centre:
+        // beyond, tanh rounds to -1 exactly, the value phi already holds
+        int xa = 0, xb = nx, ya = 0, yb = ny;
+        if (sd.kind == LBM_SEED_CIRCLE) {
+            const double reach = std::fabs(sd.r) + 20.0 * sw + 2.0;
+            xa = (int)std::max(0.0, std::floor(sd.x - reach));
+            xb = (int)std::min((double)nx, std::ceil(sd.x + reach) + 1.0);
+            ya = (int)std::max(0.0, std::floor(sd.y - reach));
+            yb = (int)std::min((double)ny, std::ceil(sd.y + reach) + 1.0);
+        }
+        for (int y = ya; y < yb; ++y)
+            for (int x = xa; x < xb; ++x) {
                 const size_t i = (size_t)y * nx + x;
                 double v;
                 if (sd.kind == LBM_SEED_CIRCLE) {

@@ -325,16 +325,9 @@ def poisson_disc(n_seeds: int, lo: float, hi: float, min_dist: float, seed: int,
     return np.array(pts, dtype=np.float64).reshape(-1, 2)
 
 
-def multi_dendrite(n: int = 8192, n_seeds: int = 32, min_dist: float = 800.0, seed: int = 5,
-                   n_base_steps: int = 50000) -> Workload:
-    """Large multi-dendrite thermosolutal growth with convection.
-
-    W0 = 2, eps = 0.02, lambda = 1.5955, M_c = 0.1, k = 0.3, U0 = 0,
-    theta0 = -0.55, D_L = 0.005, D_S = 5e-5, alpha = 0.5 (Le = 100),
-    tau0 = 800, nu = 0.05, u_in = 0.005, update factors (1, 1, 4, 2),
-    seeds of radius 8 placed by dart throwing in [64, n - 64)^2.  Crystal
-    orientations theta_g = (pi/2) u are returned in extra['angles'] (the
-    per-grain frame is an extension beyond the paper's axis-aligned Eq. 2)."""
+def multi_dendrite_params(n: int = 8192, n_seeds: int = 32, min_dist: float = 800.0, seed: int = 5):
+    """Parameters and seed centres of multi_dendrite without the host fields
+    (for device-side seeding of large lattices)."""
     W0 = 2.0
     lam = A1 * W0 / (0.554 * W0)
     DL = 0.005
@@ -346,6 +339,21 @@ def multi_dendrite(n: int = 8192, n_seeds: int = 32, min_dist: float = 800.0, se
                kappaS=0.5, kappaL=0.5, rhoCpS=1.0, rhoCpL=1.0, rhoL_Lh=1.0,
                nu=0.05, u_in=0.005, tip_cx=n // 2, tip_cy=n // 2)
     pts = poisson_disc(n_seeds, 64.0, n - 64.0, min_dist * n / 8192.0, seed)
+    return p, pts
+
+
+def multi_dendrite(n: int = 8192, n_seeds: int = 32, min_dist: float = 800.0, seed: int = 5,
+                   n_base_steps: int = 50000) -> Workload:
+    """Large multi-dendrite thermosolutal growth with convection.
+
+    W0 = 2, eps = 0.02, lambda = 1.5955, M_c = 0.1, k = 0.3, U0 = 0,
+    theta0 = -0.55, D_L = 0.005, D_S = 5e-5, alpha = 0.5 (Le = 100),
+    tau0 = 800, nu = 0.05, u_in = 0.005, update factors (1, 1, 4, 2),
+    seeds of radius 8 placed by dart throwing in [64, n - 64)^2.  Crystal
+    orientations theta_g = (pi/2) u are returned in extra['angles'] (the
+    per-grain frame is an extension beyond the paper's axis-aligned Eq. 2)."""
+    p, pts = multi_dendrite_params(n, n_seeds, min_dist, seed)
+    W0 = p.W0
     phi = np.full((n, n), -1.0)
     for (cx, cy) in pts:
         phi = np.maximum(phi, circle_seed(n, n, cx, cy, 8.0, W0))
