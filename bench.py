@@ -401,7 +401,8 @@ def large_lattice(args, torch, lbm, local, peaks_fn):
     on the device's own data path (lbm_init_seed), autotuned, then timed over
     whole schedule periods of 4 base steps with CUDA events."""
     p, pts = W.multi_dendrite_params(8192)
-    sim = lbm.Simulation(p, precision="f32")
+    prec = args.precision or "f32"
+    sim = lbm.Simulation(p, precision=prec)
     sim.init_seed([{"kind": "circle", "x": float(x), "y": float(y), "r": 8.0} for x, y in pts], U0=0.0, T0=-0.55)
     period = 4
     for _ in range(2):
@@ -437,25 +438,26 @@ def large_lattice(args, torch, lbm, local, peaks_fn):
     sim.close()
     nodes = p.nx * p.ny
     base = steps * period
-    ab = algo_bytes("f32")
+    ab = algo_bytes(prec)
     # algorithmic bytes per node per base step of the staged path (the fused
     # path moves fewer); U every step, T every 4th, flow every 2nd
     step_bytes = ab["phase"] + ab["transfer"] + ab["scalar_U"] + ab["scalar_T"] / p.N_T + ab["flow"] / p.N_F
     if fused:
-        tb, tn = period_bytes(p)
+        tb, tn = period_bytes(p, prec)
         step_bytes = ab["phase"] + tb / (2 * period)
     peak, peak_kind = peaks_fn()
     gbs = step_bytes * nodes * base / (ms * 1e-3) / 1e9
     dom_algo = dict(ab)
-    tb, tn = period_bytes(p)
+    tb, tn = period_bytes(p, prec)
     dom_algo["transport"] = tb / max(tn, 1)
     avg_s = kt[dom][0] * 1e-3 / max(kt[dom][1], 1)
     dom_gbs = dom_algo[dom] * nodes / avg_s / 1e9
     traffic = None
     per_node = TRAFFIC_PER_NODE_2048.get("%s:%d" % (dom, tiles[dom]))
-    if per_node is not None and TRAFFIC_SOURCE_SHA == kernel_source_sha():
+    if per_node is not None and prec == "f32" and TRAFFIC_SOURCE_SHA == kernel_source_sha():
         traffic = per_node * nodes
-    return {"workload": "8192x8192 multi-dendrite thermosolutal growth with convection, 32 seeds, N=(1,1,4,2), FP32",
+    return {"workload": "8192x8192 multi-dendrite thermosolutal growth with convection, 32 seeds, N=(1,1,4,2), "
+                        + STORAGE_LABEL[prec], "storage": prec,
             "value": nodes * base / (ms * 1e-3) / 1e6, "unit": UNIT, "base_steps": base,
             "ms_per_period": ms / steps, "fused_transport": fused,
             "step": {"algo_bytes_per_node_per_base_step": step_bytes, "achieved_GBs": gbs, "peak": peak,

@@ -397,3 +397,26 @@ def test_fused_and_unfused_agree_fp32():
         sim.close()
     for k in outs[0]:
         assert np.abs(outs[0][k] - outs[1][k]).max() < 1e-5, k
+
+
+def test_nonfinite_is_detected_and_sticky():
+    """Failure detection without a GPU fault: a NaN planted on the host in the
+    initial U field spreads through the update; lbm_diagnostics reports it
+    (status NONFINITE), lbm_advance then refuses until the simulation is
+    initialised again, after which it runs normally."""
+    import paper_2609_25670_b300 as lbm
+    wl = W.thermosolutal_convection(n=64, R=6.0)
+    bad = {k: v.copy() for k, v in wl.fields.items()}
+    bad["U"][10, 12] = np.nan
+    sim = lbm.Simulation(wl.params, precision="f32")
+    sim.init_fields(bad)
+    sim.advance(4)
+    d = sim.diagnostics()
+    assert d["nonfinite"] == 1 and d["status"] == 5
+    with pytest.raises(lbm.LbmError):
+        sim.advance(1)
+    sim.init_fields(wl.fields)
+    sim.advance(4)
+    d = sim.diagnostics()
+    assert d["nonfinite"] == 0 and d["status"] == 0
+    sim.close()
