@@ -231,6 +231,8 @@ class Simulation:
                 assert a.dtype == self._torch.float64 and a.is_contiguous()
             arrs.append(a)
         ptrs = [C.c_void_p(_ptr(a)) if a is not None else None for a in arrs]
+        if dev:     # the tensors were written on torch's current stream
+            self.stream.wait_stream(self._torch.cuda.current_stream())
         self._ck(self.lib.lbm_init_fields(self.h, sim, *ptrs, dev))
 
     def init_seed(self, seeds: Sequence[Dict], U0: float = 0.0, T0: float = 0.0, rng_seed: int = 0, sim: int = 0):
@@ -278,7 +280,11 @@ class Simulation:
             out = np.empty((self.ny[sim], self.nx[sim]), dtype=np.float64 if as_f64 else
                            (np.float64 if self.precision == "f64" else np.float32))
         dev = 0 if isinstance(out, np.ndarray) else (1 if out.is_cuda else 0)
+        if dev:     # ordered after the tensor's last use on torch's current stream
+            self.stream.wait_stream(self._torch.cuda.current_stream())
         self._ck(self.lib.lbm_fields(self.h, sim, which, C.c_void_p(_ptr(out)), dev, 1 if as_f64 else 0))
+        if dev:     # and its readers after the library's write
+            self._torch.cuda.current_stream().wait_stream(self.stream)
         return out
 
     def diagnostics(self, sim: int = 0, raise_nonfinite: bool = False) -> Dict:

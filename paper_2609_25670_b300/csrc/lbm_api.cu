@@ -196,6 +196,19 @@ lbm_status dev_alloc(lbm_sim* h, size_t bytes, void** out) {
     return LBM_OK;
 }
 
+// Host -> device upload of a coefficient block or job table, ordered on the
+// handle's stream.  The stream is non-blocking (a caller's stream, e.g. from
+// PyTorch's pool), so a plain cudaMemcpy on the legacy stream would not wait
+// for work queued there: it could land before a pending cudaMemsetAsync of the
+// same allocation (which then wipes it), or overwrite a job table that a
+// queued launch still reads.  Synchronising afterwards lets the caller reuse
+// the host buffer at once.
+lbm_status upload_sync(lbm_sim* h, void* dst, const void* src, size_t bytes) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
 void free_all(lbm_sim* h) {
     for (auto& b : h->blocks) {
         if (h->has_alloc) h->alloc.free(b.first, b.second, (void*)h->stream, h->alloc.ctx);
@@ -884,8 +897,11 @@ lbm_status capture_graph(lbm_sim* h, SimState& s, int which) {
     h->cap_single = false;
     set_parity(s, pre);
     if (!h->rec[LBM_K_TRANSPORT].empty())
-        CK(cudaMemcpy((unsigned char*)s.tjobs + (size_t)which * s.half * s.tjob_bytes, h->rec[LBM_K_TRANSPORT].data(),
-                      h->rec[LBM_K_TRANSPORT].size(), cudaMemcpyHostToDevice));
+    {
+        lbm_status st = upload_sync(h, (unsigned char*)s.tjobs + (size_t)which * s.half * s.tjob_bytes,
+                                    h->rec[LBM_K_TRANSPORT].data(), h->rec[LBM_K_TRANSPORT].size());
+        if (st) return st;
+    }
     clear_records(h);
     // pass 2: capture
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
@@ -951,7 +967,10 @@ lbm_status capture_batch(lbm_sim* h, int which) {
     if (all.size() > region)
         return fail(h, LBM_E_STATE, "job tables of %zu bytes exceed the %zu reserved", all.size(), region);
     unsigned char* base = (unsigned char*)h->job_buf + (size_t)which * region;
-    CK(cudaMemcpy(base, all.data(), all.size(), cudaMemcpyHostToDevice));
+    {
+        lbm_status st = upload_sync(h, base, all.data(), all.size());
+        if (st) return st;
+    }
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     h->capturing = true;
     h->cap_kernels = h->bg[which].kernels;
@@ -1216,10 +1235,14 @@ lbm_status lbm_create(const lbm_params* p, int32_t n_sims, const lbm_params* per
                                                       : sizeof(TransportJob<float, __half>);
         if (!st) st = dev_alloc(h, (size_t)(s.teager + 1) * s.tjob_bytes, &s.tjobs);
         if (!st) {
-            cudaError_t e = h->precision == LBM_PREC_F64
-                                ? [&] { const KP<double> k = make_kp<double>(s); return cudaMemcpy(s.dkp, &k, sizeof k, cudaMemcpyHostToDevice); }()
-                                : [&] { const KP<float> k = make_kp<float>(s); return cudaMemcpy(s.dkp, &k, sizeof k, cudaMemcpyHostToDevice); }();
-            if (e != cudaSuccess) st = fail(h, LBM_E_CUDA, "cudaMemcpy(coefficients): %s", cudaGetErrorString(e));
+            // after the zeroing memsets queued on the stream (see upload_sync)
+            if (h->precision == LBM_PREC_F64) {
+                const KP<double> k = make_kp<double>(s);
+                st = upload_sync(h, s.dkp, &k, sizeof k);
+            } else {
+                const KP<float> k = make_kp<float>(s);
+                st = upload_sync(h, s.dkp, &k, sizeof k);
+            }
         }
         if (st) {
             std::string m = h->err;
@@ -1616,7 +1639,10 @@ lbm_status lbm_autotune(lbm_handle h, int32_t reps, int32_t* chosen) {
                 }
                 h->recording = false;
                 if (!h->rec_jobs[kind]) break;
-                CK(cudaMemcpy(h->job_buf, h->rec[kind].data(), h->rec[kind].size(), cudaMemcpyHostToDevice));
+                {
+                    lbm_status st = upload_sync(h, h->job_buf, h->rec[kind].data(), h->rec[kind].size());
+                    if (st) return st;
+                }
                 launch_batch_any(h, kind, v, h->job_buf, h->rec_jobs[kind], h->rec_tiles[kind]);
                 CK(cudaEventRecord(a, h->stream));
                 for (int r = 0; r < reps; ++r)

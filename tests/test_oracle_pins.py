@@ -459,3 +459,41 @@ def test_tip_diagnostic_on_known_profile():
     o = oracle.Oracle(p, W.base_fields(p, W.circle_seed(n, n, 32, 32, R, 1.0)))
     tip = o.diagnostics()["tip"]
     assert np.abs(tip - R).max() < 0.015
+
+
+@pytest.mark.parametrize("steps", [1, 4])
+def test_update_is_local_within_six_nodes_per_base_step(steps):
+    """The method is an explicit local update (Eqs. 25-26 stream one link;
+    the gradients of Eq. 40, the compact stencil of the anti-trapping
+    divergence and the phase-field gradient reach one node each; Fig. 1's
+    chain phase -> transfer -> U/T/flow adds at most five nodes of reach per
+    base step).  So the state at a node after k base steps depends only on
+    the initial state within 6k nodes: a run on a window of the lattice
+    reproduces the full-lattice run bit for bit at nodes farther than 6k from
+    the window's artificial edges, and also up to an edge that is the
+    lattice's own boundary.  The full-size GPU parity tests rely on this to
+    check sampled outputs of lattices too large for the oracle."""
+    from dataclasses import replace
+    n = 192
+    p, pts = W.multi_dendrite_params(n, n_seeds=3, min_dist=70.0)
+    full = W.circle_seeds_window(p, pts, 8.0, 0, 0, n, n, 0.0, -0.55)
+    o = oracle.Oracle(p, full)
+    o.advance(steps)
+    ref = {f: o.get(f) for f in ("phi", "U", "T", "ux", "uy", "rho")}
+    o.close()
+    m = 6 * steps
+    w = 96
+    # an interior window around the first seed, and windows on the inlet and
+    # outflow columns (their lattice-side edge is exact)
+    cx, cy = int(pts[0][0]), int(pts[0][1])
+    x0 = min(max(cx - w // 2, 1), n - w - 1)
+    y0 = min(max(cy - w // 2, 1), n - w - 1)
+    cases = [(x0, y0, (m, w - m, m, w - m)), (0, 40, (0, w - m, m, w - m)), (n - w, 40, (m, w, m, w - m))]
+    for (wx, wy, (xa, xb, ya, yb)) in cases:
+        pw = replace(p, nx=w, ny=w, tip_cx=w // 2, tip_cy=w // 2)
+        o = oracle.Oracle(pw, W.circle_seeds_window(p, pts, 8.0, wx, wy, w, w, 0.0, -0.55))
+        o.advance(steps)
+        for f, r in ref.items():
+            got = o.get(f)[ya:yb, xa:xb]
+            assert np.array_equal(got, r[wy + ya:wy + yb, wx + xa:wx + xb]), (wx, wy, f)
+        o.close()

@@ -360,3 +360,21 @@ def multi_dendrite(n: int = 8192, n_seeds: int = 32, min_dist: float = 800.0, se
     angles = 0.5 * math.pi * uniform01(seed + 1, len(pts))
     return Workload("multi_dendrite_%d" % n, p, base_fields(p, phi, U0=0.0, T0=-0.55),
                     n_base_steps, extra={"seeds": pts, "angles": angles})
+
+
+def circle_seeds_window(p: Params, pts, R: float, x0: int, y0: int, w: int, h: int,
+                        U0: float = 0.0, T0: float = 0.0) -> Dict[str, np.ndarray]:
+    """Initial fields of the window [x0, x0 + w) x [y0, y0 + h) of a lattice
+    seeded with circles of radius R at the global centres `pts`:
+    phi = max(-1, max_s tanh[(R - r_s)/(sqrt 2 W0)]) (Sec. 4.1), U = U0,
+    T = T0, u = u_in (1 - phi)/2 with the flow on, rho = 1.  It is the same
+    field a full-lattice generation gives, read on the window, without
+    building the full lattice."""
+    y, x = np.mgrid[y0:y0 + h, x0:x0 + w]
+    x = x.astype(np.float64)
+    y = y.astype(np.float64)
+    phi = np.full((h, w), -1.0)
+    for (cx, cy) in pts:
+        r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2)
+        phi = np.maximum(phi, np.tanh((R - r) / (math.sqrt(2.0) * p.W0)))
+    return base_fields(p, phi, U0=U0, T0=T0)
