@@ -47,15 +47,17 @@ MACRO_BYTES = {"f64": 8, "f32": 4, "f16dev": 4, "bf16dev": 4}
 
 
 def algo_bytes(prec="f32"):
-    """Algorithmic bytes per node of one launch of each update kernel: the 8
-    stored populations read and written once, each macro read / written once."""
+    """Algorithmic bytes per node of one launch of each update kernel: the
+    stored state read and written once (phase and flow: 8 populations; U and
+    T: the 2 first-moment planes), each macro read / written once."""
     pb, m = POP_BYTES[prec], MACRO_BYTES[prec]
     pops = 2 * 8 * pb
+    moms = 2 * 2 * pb
     return {
         "phase": pops + 4 * m,                  # pops R+W, phi^q R, U R, T R, phi^{q+1} W
         "transfer": 6 * m,                      # phi^q, phi^{q+1}, U, T R; U, T W
-        "scalar_U": pops + 5 * m,               # pops, U R+W, phi R, u R (2)
-        "scalar_T": pops + 5 * m,
+        "scalar_U": moms + 5 * m,               # j R+W, U R+W, phi R, u R (2)
+        "scalar_T": moms + 5 * m,
         "flow": pops + 7 * m,                   # pops, phi R, (rho, ux, uy) R + W
     }
 
@@ -65,10 +67,11 @@ ALGO_BYTES = algo_bytes("f32")
 
 def transport_bytes(tr, u, t, f, has_T=True, has_flow=True, prec="f32"):
     """Algorithmic bytes per node of one fused transport launch: the transfer
-    reads phi^q, phi^{q+1}, U, T once; each scheduled field reads and writes
-    its 8 populations and writes its macro; a macro whose field does not
-    update in this step is written back with the injection."""
-    m, pops = MACRO_BYTES[prec], 2 * 8 * POP_BYTES[prec]
+    reads phi^q, phi^{q+1}, U, T once; each scheduled scalar reads and writes
+    its first moments and writes its macro, the flow its 8 populations and
+    macros; a macro whose field does not update in this step is written back
+    with the injection."""
+    m, pops, moms = MACRO_BYTES[prec], 2 * 8 * POP_BYTES[prec], 2 * 2 * POP_BYTES[prec]
     b = m                                       # phi (current) R
     if tr:
         b += m + m + (m if has_T else 0)        # phi^q, U, T R
@@ -78,9 +81,9 @@ def transport_bytes(tr, u, t, f, has_T=True, has_flow=True, prec="f32"):
     if (u or t) and has_flow:
         b += 2 * m                              # u for the scalar equilibria
     if u:
-        b += pops + m
+        b += moms + m
     if t:
-        b += pops + m
+        b += moms + m
     if f:
         b += pops + 6 * m - (2 * m if (u or t) else 0)   # rho, u R (u shared with the scalars) + W
     return b

@@ -59,12 +59,18 @@ enum {
     LBM_FIELD_FLOW = 8u      /* D2Q9 flow, Eqs. 13, 27-33                          */
 };
 
-/* lbm_params.precision: storage of the distributions / arithmetic */
+/* lbm_params.precision: storage of the distributions / arithmetic.  The
+ * stored state of a field is: phase and flow, populations 1..8 (population 0
+ * follows from the macro); U and T, the first moment (j_x, j_y) of the
+ * streamed populations -- with the relaxation matrix of Eq. 23 every other
+ * moment of a scalar collision relaxes to equilibrium at rate one, so the
+ * macro and j determine the post-collision populations exactly. */
 enum {
     LBM_PREC_F64 = 0,      /* FP64 storage and arithmetic                          */
     LBM_PREC_F32 = 1,      /* FP32 storage and arithmetic                          */
-    LBM_PREC_F16_DEV = 2,  /* FP16 storage of f_i - w_i * (node's zeroth moment), FP32 arithmetic */
-    LBM_PREC_BF16_DEV = 3  /* BF16 storage of the same deviations, FP32 arithmetic */
+    LBM_PREC_F16_DEV = 2,  /* FP16 storage, FP32 arithmetic: phase f_i - w_i phi,
+                              flow f_i - f_eq_i(rho, u) (Eq. 28), U/T j as is      */
+    LBM_PREC_BF16_DEV = 3  /* BF16 storage of the same quantities, FP32 arithmetic */
 };
 
 /* lbm_params.coupling (Sec. 4.4 source-coupling ablation) */

@@ -54,7 +54,7 @@ struct SimState {
     lbm_params p{};
     int nx = 0, ny = 0, pitch = 0;
     size_t nn = 0;        // pitch * ny
-    void* pops[4][2] = {};
+    void* pops[4][2] = {};   // phase, flow: 8 population planes; U, T: 2 first-moment planes
     int cur_pop[4] = {0, 0, 0, 0};
     void* phi[2] = {};
     int cur_phi = 0;
@@ -1211,7 +1211,7 @@ lbm_status lbm_create(const lbm_params* p, int32_t n_sims, const lbm_params* per
         lbm_status st = LBM_OK;
         for (int f = 0; f < 4 && !st; ++f)
             for (int b = 0; b < 2 && !st; ++b)
-                if (present[f]) st = dev_alloc(h, 8 * s.nn * ss, &s.pops[f][b]);
+                if (present[f]) st = dev_alloc(h, (f == FU || f == FT ? 2 : 8) * s.nn * ss, &s.pops[f][b]);
         for (int b = 0; b < 2 && !st; ++b) st = dev_alloc(h, s.nn * rs, &s.phi[b]);
         for (int b = 0; b < 2 && !st; ++b) if (s.has_U) st = dev_alloc(h, s.nn * rs, &s.U[b]);
         for (int b = 0; b < 2 && !st; ++b) if (s.has_T) st = dev_alloc(h, s.nn * rs, &s.T[b]);

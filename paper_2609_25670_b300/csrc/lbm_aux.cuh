@@ -6,7 +6,8 @@
 namespace lbmk {
 
 // ---------------------------------------------------------------------------
-// Initial distributions f = f_eq of the macroscopic fields (Eqs. 19, 21, 28)
+// Initial distributions f = f_eq of the macroscopic fields (Eqs. 19, 21, 28);
+// for U and T their first moments, the stored state of those fields
 // ---------------------------------------------------------------------------
 template <typename R, typename ST, bool DEV>
 __global__ void k_init(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ Um, const R* __restrict__ Tm,
@@ -33,14 +34,18 @@ __global__ void k_init(const KP<R> P, const R* __restrict__ phi, const R* __rest
         const R w = wq<R>(i), ex = (R)c_ex[i], ey = (R)c_ey[i];
         const R dp = R(3) * w * (ex * bx + ey * by);                                   // Eq. 21 minus w_i phi
         fphi[(size_t)(i - 1) * P.plane + node] = Cvt<ST>::st(DEV ? dp : w * ph + dp);
-        if (P.has_U) {
-            const R U = Um[node], d = R(3) * w * U * P.dtU * (ex * vx + ey * vy);       // Eq. 19
-            fU[(size_t)(i - 1) * P.plane + node] = Cvt<ST>::st(DEV ? d : w * U + d);
-        }
-        if (P.has_T) {
-            const R T = Tm[node], d = R(3) * w * T * P.dtT * (ex * vx + ey * vy);
-            fT[(size_t)(i - 1) * P.plane + node] = Cvt<ST>::st(DEV ? d : w * T + d);
-        }
+    }
+    // U, T: the first moment of f_eq of Eq. 19, sum_i e_i 3 w_i chi dt (e_i . u)
+    // = dt chi u (sum_i w_i e_i e_i = I / 3)
+    if (P.has_U) {
+        const R U = Um[node];
+        fU[node] = Cvt<ST>::st(P.dtU * U * vx);
+        fU[(size_t)P.plane + node] = Cvt<ST>::st(P.dtU * U * vy);
+    }
+    if (P.has_T) {
+        const R T = Tm[node];
+        fT[node] = Cvt<ST>::st(P.dtT * T * vx);
+        fT[(size_t)P.plane + node] = Cvt<ST>::st(P.dtT * T * vy);
     }
     if (P.has_flow) {
         R fe[9];

@@ -9,17 +9,21 @@
 // its first barrier.  Tiles whose ghost ring lies inside the lattice take a
 // compile-time "interior" path without boundary maps or wall tests.
 //
-// Storage (per field, per ping-pong buffer): populations 1..8 as planes of
-// `pitch * ny` elements of type ST; population 0 is never stored.  It follows
-// from the node's zeroth moment, which the macroscopic arrays carry:
-//   phase: f_0 = phi - sum_{i>0} f_i          (Eq. 18)
-//   flow:  f_0 = rho - sum_{i>0} f_i          (Eq. 27)
-//   U, T:  f_0 is not needed at all; the collision uses only the zeroth
-//          moment (the macro) and the first moment (Eq. 23 relaxes every
-//          other moment to equilibrium).
-// With DEV = true the planes hold deviations h_i = f_i - ref_i in 16 bits:
-//   phase ref_i = w_i phi, U/T ref_i = w_i chi (cancels in the first moment),
-//   flow ref_i = f_eq_i(rho, u) of Eq. 28.
+// Storage (per field, per ping-pong buffer), planes of `pitch * ny` elements
+// of type ST:
+//   phase, flow: populations 1..8; population 0 is never stored, it follows
+//          from the node's zeroth moment, which the macroscopic arrays carry:
+//          phase f_0 = phi - sum_{i>0} f_i (Eq. 18), flow f_0 = rho -
+//          sum_{i>0} f_i (Eq. 27).
+//   U, T:  the first moment (j_x, j_y) of the streamed populations, two
+//          planes.  The collision uses only the zeroth moment (the macro) and
+//          the first moment: Eq. 23 relaxes every other moment to equilibrium
+//          at rate one, so nothing else of the populations survives a
+//          collision (load_j / store_j).
+// With DEV = true the phase and flow planes hold deviations h_i = f_i - ref_i
+// in 16 bits: phase ref_i = w_i phi, flow ref_i = f_eq_i(rho, u) of Eq. 28.
+// The U, T first moments are stored in ST as they are (the first moment of
+// w_i chi is zero, so j is already the deviation).
 //
 // The U and T macros include every phase-change increment already injected
 // (Eq. 39).  The injection adds w_i Delta to the populations, which changes
@@ -83,6 +87,25 @@ __device__ __forceinline__ void load8(const ST* __restrict__ f, int node, int pl
 }
 template <typename R> __device__ __forceinline__ R mom_x(const R* v) { return v[1] - v[3] + v[5] - v[6] - v[7] + v[8]; }
 template <typename R> __device__ __forceinline__ R mom_y(const R* v) { return v[2] - v[4] + v[5] + v[6] - v[7] - v[8]; }
+
+// Stored state of a scalar field (U or T) besides its zeroth moment (the
+// macro): the first moment j = sum_i e_i f_i of the streamed populations, two
+// planes.  With S of Eq. 23 every moment of the scalar collision except the
+// fluxes m3, m5 relaxes to its equilibrium at rate one, so the post-collision
+// populations of a node are a function of (chi, j_x, j_y) and of phi, grad phi
+// and u there alone (the closed form of put_scalar_post): the eight
+// populations never need to be stored.  The injection of Eq. 39 changes only
+// the zeroth moment (sum_i w_i e_i = 0) and is carried by the macro.
+template <typename R, typename ST>
+__device__ __forceinline__ void load_j(const ST* __restrict__ f, int node, int plane, R& jx, R& jy) {
+    jx = (R)Cvt<ST>::ld(f[node]);
+    jy = (R)Cvt<ST>::ld(f[node + plane]);
+}
+template <typename R, typename ST>
+__device__ __forceinline__ void store_j(ST* __restrict__ f, int node, int plane, const R* fn) {
+    f[node] = Cvt<ST>::st(mom_x(fn));
+    f[node + plane] = Cvt<ST>::st(mom_y(fn));
+}
 
 // walls around an own node: a population of direction i comes from behind a
 // wall when its source node gx - e_ix (gy - e_iy) lies outside a WALL side
@@ -395,24 +418,24 @@ __device__ __forceinline__ void scalar_tile(ScalarSmem<R, TY>& sm, const KP<R>& 
         vb = IN || resolve_xy(bx, by, P.nx, P.ny, P.bsx, P.bsy);
     }
     const int na = ay * P.pitch + ax, nb = by * P.pitch + bx;
-    R fa[9], fb[9];
+    R jax = R(0), jay = R(0), jbx = R(0), jby = R(0);
     R ca = R(0), cb = R(0), uxa = R(0), uya = R(0), uxb = R(0), uyb = R(0), acca = R(0);
     if (va) {
-        load8<R, ST>(fin, na, pl, fa);
+        load_j<R, ST>(fin, na, pl, jax, jay);
         ca = mac_in[na];
         if (P.accumulated) { acca = acc[na]; ca += acca; }   // coarse-step injection (Sec. 4.4 ablation)
         if (P.has_flow) { uxa = ux[na]; uya = uy[na]; }
     }
     if (vb) {
-        load8<R, ST>(fin, nb, pl, fb);
+        load_j<R, ST>(fin, nb, pl, jbx, jby);
         cb = mac_in[nb];
         if (P.accumulated) cb += acc[nb];
         if (P.has_flow) { uxb = ux[nb]; uyb = uy[nb]; }
     }
     load_phi_ring2<R, TY, IN>(P, phi, sm.phi, x0, y0, tid);
     __syncthreads();
-    if (va) scalar_collide<R, TY, FIELD>(P, sm.phi, sm.post, tx + 1, ty + 1, ca, mom_x(fa), mom_y(fa), uxa, uya);
-    if (vb) scalar_collide<R, TY, FIELD>(P, sm.phi, sm.post, blx, bly, cb, mom_x(fb), mom_y(fb), uxb, uyb);
+    if (va) scalar_collide<R, TY, FIELD>(P, sm.phi, sm.post, tx + 1, ty + 1, ca, jax, jay, uxa, uya);
+    if (vb) scalar_collide<R, TY, FIELD>(P, sm.phi, sm.post, blx, bly, cb, jbx, jby, uxb, uyb);
     __syncthreads();
     const int gx = x0 + tx, gy = y0 + ty;
     R myj = R(0);
@@ -426,8 +449,7 @@ __device__ __forceinline__ void scalar_tile(ScalarSmem<R, TY>& sm, const KP<R>& 
             sum += fn[i];
         }
         mac_out[node] = sum;                                                      // Eq. 18
-#pragma unroll
-        for (int i = 1; i < 9; ++i) fout[node + (i - 1) * pl] = Cvt<ST>::st(DEV ? fn[i] - wq<R>(i) * sum : fn[i]);
+        store_j<R, ST>(fout, node, pl, fn);
         if (FIELD == 0 && P.accumulated) myj = fabs(acca);
     }
     if (FIELD == 0 && P.accumulated) {

@@ -136,8 +136,10 @@ __device__ __forceinline__ R word_value(Word<R> w, bool odd) {
     }
 }
 
-// slot arrays of the scalar rows
-enum { SA_F = 0, SA_CHI = 8, SA_ACC = 9, SA_VX = 10, SA_VY = 11, SA_PC = 12, SA_PE = 13, SA_N = 14 };
+// slot arrays of the scalar rows: the first moments (j_x, j_y), the macro,
+// the accumulator, the velocity, phi of the next row in the lane's and the
+// extra column
+enum { SA_JX = 0, SA_JY = 1, SA_CHI = 2, SA_ACC = 3, SA_VX = 4, SA_VY = 5, SA_PC = 6, SA_PE = 7, SA_N = 8 };
 
 template <typename R, typename ST, bool IN>
 __device__ __forceinline__ void scalar_row_fetch(const KP<R>& P, const ST* __restrict__ fin,
@@ -149,8 +151,8 @@ __device__ __forceinline__ void scalar_row_fetch(const KP<R>& P, const ST* __res
     int cy = r;
     const bool v = IN || (colv && resolve(cy, P.ny, P.bsy));
     const int node = v ? cy * P.pitch + cx : 0;
-#pragma unroll
-    for (int i = 1; i < 9; ++i) fetch_word<R>(slot + (SA_F + i - 1) * 32 + lane, fin + (size_t)(i - 1) * pl, node, v);
+    fetch_word<R>(slot + SA_JX * 32 + lane, fin, node, v);
+    fetch_word<R>(slot + SA_JY * 32 + lane, fin + pl, node, v);
     fetch_word<R>(slot + SA_CHI * 32 + lane, mac_in, node, v);
     if (P.accumulated) fetch_word<R>(slot + SA_ACC * 32 + lane, acc, node, v);
     if (P.has_flow) {
@@ -215,9 +217,7 @@ __device__ __forceinline__ void scalar_strip(const KP<R>& P, const ST* __restric
         __pipeline_commit();
         __pipeline_wait_prior(D - 1);             // this lane's copies of row r have landed
         const Word<R>* sl = ring + (k % D) * SLOT + lane;
-        R f[9];
-#pragma unroll
-        for (int i = 1; i < 9; ++i) f[i] = word_value<R, ST>(sl[(SA_F + i - 1) * 32], odd);
+        const R jx = word_value<R, ST>(sl[SA_JX * 32], odd), jy = word_value<R, ST>(sl[SA_JY * 32], odd);
         R chi = word_value<R, R>(sl[SA_CHI * 32], false), vx = R(0), vy = R(0), accv = R(0);
         if (P.accumulated) { accv = word_value<R, R>(sl[SA_ACC * 32], false); chi += accv; }  // Sec. 4.4 ablation
         if (P.has_flow) { vx = word_value<R, R>(sl[SA_VX * 32], false); vy = word_value<R, R>(sl[SA_VY * 32], false); }
@@ -225,7 +225,7 @@ __device__ __forceinline__ void scalar_strip(const KP<R>& P, const ST* __restric
         R gpx, gpy;
         strip_grad<R>(lane, cm, c0, pc, em, e0, pe, gpx, gpy);
         R p[9];
-        scalar_collide9<R, FIELD>(P, c0, gpx, gpy, chi, mom_x(f), mom_y(f), vx, vy, p);
+        scalar_collide9<R, FIELD>(P, c0, gpx, gpy, chi, jx, jy, vx, vy, p);
         const R s1 = from_left(p[1]), s3 = from_right(p[3]), s5 = from_left(p[5]);
         const R s6 = from_right(p[6]), s7 = from_right(p[7]), s8 = from_left(p[8]);
         const int y = r - 1;                       // row completed in this iteration
@@ -252,8 +252,7 @@ __device__ __forceinline__ void scalar_strip(const KP<R>& P, const ST* __restric
             for (int i = 0; i < 9; ++i) sum += fn[i];
             const int node = y * P.pitch + gx;
             mac_out[node] = sum;                                                  // Eq. 18
-#pragma unroll
-            for (int i = 1; i < 9; ++i) fout[node + (i - 1) * pl] = Cvt<ST>::st(DEV ? fn[i] - wq<R>(i) * sum : fn[i]);
+            store_j<R, ST>(fout, node, pl, fn);
         }
         z2 = q2; z5 = q5; z6 = q6;
         q0 = p[0]; q1 = s1; q3 = s3; q2 = p[2]; q5 = s5; q6 = s6;
@@ -362,13 +361,16 @@ template <typename T> __device__ __forceinline__ Vec4<T> sread(const unsigned ch
     return *reinterpret_cast<const Vec4<T>*>(p);
 }
 
-enum { VA_CHI = 8, VA_ACC = 9, VA_VX = 10, VA_VY = 11, VA_PHI = 12, VA_N = 13 };
-template <typename R> struct VRing {
+enum { VA_JX = 0, VA_JY = 1, VA_CHI = 2, VA_ACC = 3, VA_VX = 4, VA_VY = 5, VA_PHI = 6, VA_N = 7 };
+// per-warp ring of row slots, each holding NA arrays of one 16-byte (FP32)
+// entry per lane
+template <typename R, int NA> struct VRingN {
     static constexpr int EB = VW * (int)sizeof(R);     // bytes of one lane's entry
-    static constexpr int SLOT = VA_N * 32 * EB;        // one row
+    static constexpr int SLOT = NA * 32 * EB;          // one row
     static constexpr int D = sizeof(R) == 8 ? 2 : 4;   // rows in the ring (D - 1 in flight)
     static constexpr int BYTES = D * SLOT;
 };
+template <typename R> using VRing = VRingN<R, VA_N>;     // scalar strips
 constexpr int VNW = 2;     // warps per block of the vector-strip launches
 
 // One vector strip.  UP = false walks rows y0-1 .. y0+H downwards and
@@ -392,8 +394,8 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
     unsigned char* const mine = ring + lane * EB;
     auto fetch_row = [&](int r, unsigned char* slot) {      // collision row r, phi row r + DIR
         const int base = r * pitch + c0;
-#pragma unroll
-        for (int i = 1; i < 9; ++i) fetch_vec<ST>(slot + (i - 1) * 32 * EB, fin + (size_t)(i - 1) * pl + base);
+        fetch_vec<ST>(slot + VA_JX * 32 * EB, fin + base);
+        fetch_vec<ST>(slot + VA_JY * 32 * EB, fin + (size_t)pl + base);
         fetch_vec<R>(slot + VA_CHI * 32 * EB, mac_in + base);
         if (P.accumulated) fetch_vec<R>(slot + VA_ACC * 32 * EB, acc + base);
         if (P.has_flow) {
@@ -425,20 +427,14 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
         __pipeline_commit();
         __pipeline_wait_prior(D - 1);              // this lane's copies of row r have landed
         const unsigned char* sl = mine + (it % D) * RG::SLOT;
-        // first moments (the order of mom_x / mom_y)
+        // first moments of the streamed populations
         R jx[VW], jy[VW];
         {
-            R f[9][VW];
-#pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                const Vec4<ST> v = sread<ST>(sl + (i - 1) * 32 * EB);
-#pragma unroll
-                for (int k = 0; k < VW; ++k) f[i][k] = (R)Cvt<ST>::ld(v.v[k]);
-            }
+            const Vec4<ST> vjx = sread<ST>(sl + VA_JX * 32 * EB), vjy = sread<ST>(sl + VA_JY * 32 * EB);
 #pragma unroll
             for (int k = 0; k < VW; ++k) {
-                jx[k] = f[1][k] - f[3][k] + f[5][k] - f[6][k] - f[7][k] + f[8][k];
-                jy[k] = f[2][k] - f[4][k] + f[5][k] + f[6][k] - f[7][k] - f[8][k];
+                jx[k] = (R)Cvt<ST>::ld(vjx.v[k]);
+                jy[k] = (R)Cvt<ST>::ld(vjy.v[k]);
             }
         }
         Vec4<R> chi = sread<R>(sl + VA_CHI * 32 * EB), accv{}, vx{}, vy{};
@@ -498,13 +494,14 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
                 sum.v[k] = t;
             }
             *reinterpret_cast<Vec4<R>*>(mac_out + node) = sum;                    // Eq. 18
+            Vec4<ST> ox, oy;
 #pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                Vec4<ST> o;
-#pragma unroll
-                for (int k = 0; k < VW; ++k) o.v[k] = Cvt<ST>::st(DEV ? fn[i][k] - wq<R>(i) * sum.v[k] : fn[i][k]);
-                *reinterpret_cast<Vec4<ST>*>(fout + (size_t)(i - 1) * pl + node) = o;
+            for (int k = 0; k < VW; ++k) {
+                ox.v[k] = Cvt<ST>::st(fn[1][k] - fn[3][k] + fn[5][k] - fn[6][k] - fn[7][k] + fn[8][k]);
+                oy.v[k] = Cvt<ST>::st(fn[2][k] - fn[4][k] + fn[5][k] + fn[6][k] - fn[7][k] - fn[8][k]);
             }
+            *reinterpret_cast<Vec4<ST>*>(fout + node) = ox;
+            *reinterpret_cast<Vec4<ST>*>(fout + (size_t)pl + node) = oy;
         }
 #pragma unroll
         for (int k = 0; k < VW; ++k) {
@@ -580,7 +577,8 @@ __device__ __forceinline__ void scalar_vs_block(const KP<R>& P, const ST* fin, S
 // post-collision values and f_L, and (p_i, f_L) of its sources in the rows
 // on either side; both are carried in registers as the warp walks.
 // ---------------------------------------------------------------------------
-enum { FA_RHO = 8, FA_UX = 9, FA_UY = 10, FA_PHI = 11 };
+enum { FA_RHO = 8, FA_UX = 9, FA_UY = 10, FA_PHI = 11, FA_N = 12 };
+template <typename R> using FRing = VRingN<R, FA_N>;    // flow strips: 8 populations, rho, u, phi
 
 template <typename R, typename ST, bool DEV, int H, bool UP>
 __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict__ fin, ST* __restrict__ fout,
@@ -588,7 +586,7 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
                                             const R* __restrict__ uy_in, const R* __restrict__ rho_in,
                                             R* __restrict__ ux_out, R* __restrict__ uy_out, R* __restrict__ rho_out,
                                             int s, int y0, unsigned char* __restrict__ ring) {
-    using RG = VRing<R>;
+    using RG = FRing<R>;
     constexpr int EB = RG::EB, NR = H + 2, D = RG::D, DIR = UP ? -1 : 1;
     // directions whose source lies in the row behind the walk (far) and in
     // the row just collided (near): axis, from the left (e_x = +1), from the right
@@ -732,7 +730,7 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
 // interior and leaving its nodes to the strips.
 constexpr int FVW = 4;     // warps per block of the flow vector launch (= tile height of its frame)
 template <typename R> struct FVSmem {
-    static constexpr int STRIPS = FVW * VRing<R>::BYTES;
+    static constexpr int STRIPS = FVW * FRing<R>::BYTES;
     static constexpr int TILE = (int)sizeof(FlowSmem<R, FVW>);
     static constexpr int BYTES = STRIPS > TILE ? STRIPS : TILE;
 };
@@ -754,7 +752,7 @@ __device__ __forceinline__ void flow_vs_block(const KP<R>& P, const ST* fin, ST*
         const int vs = b * FVW + w;
         if (vs >= g.nxv * g.nyv) return;           // whole warp (no block barrier on this path)
         const int sy = vs / g.nxv;
-        unsigned char* mine = fsm + w * VRing<R>::BYTES;
+        unsigned char* mine = fsm + w * FRing<R>::BYTES;
         if (sy & 1)
             flow_vstrip<R, ST, DEV, H, true>(P, fin, fout, phi, ux_in, uy_in, rho_in, ux_out, uy_out, rho_out,
                                              vs % g.nxv, VY0 + H * sy, mine);

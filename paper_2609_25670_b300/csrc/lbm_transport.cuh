@@ -23,8 +23,8 @@ template <typename R, typename ST> struct TransportJob {
     const R* phi;                  // the current phase field (phi^{q+1} after a phase update)
     const R* Uin; R* Uout;         // U macro: pre-injection in, final out
     const R* Tin; R* Tout;
-    const ST* fUin; ST* fUout;
-    const ST* fTin; ST* fTout;
+    const ST* fUin; ST* fUout;     // first moments (j_x, j_y) of U, two planes
+    const ST* fTin; ST* fTout;     // first moments of T
     const ST* fFin; ST* fFout;
     const R* ux_in; const R* uy_in; const R* rho_in;   // flow state before this step's flow update
     R* ux_out; R* uy_out; R* rho_out;
@@ -135,10 +135,10 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
         if (va) Ua0 = A.Uin[na];
         if (vb) Ub0 = A.Uin[nb];
     }
-    R fa[9], fb[9];
+    R jax = R(0), jay = R(0), jbx = R(0), jby = R(0);     // first moments of U (then T)
     if (A.do_U) {
-        if (va) load8<R, ST>(A.fUin, na, pl, fa);
-        if (vb) load8<R, ST>(A.fUin, nb, pl, fb);
+        if (va) load_j<R, ST>(A.fUin, na, pl, jax, jay);
+        if (vb) load_j<R, ST>(A.fUin, nb, pl, jbx, jby);
     }
     R uxa = R(0), uya = R(0), uxb = R(0), uyb = R(0);
     if (P.has_flow && (A.do_U || A.do_T)) {
@@ -244,21 +244,20 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
             sum += fn[i];
         }
         mac_out[node] = sum;
-#pragma unroll
-        for (int i = 1; i < 9; ++i) fout[node + (i - 1) * pl] = Cvt<ST>::st(DEV ? fn[i] - wq<R>(i) * sum : fn[i]);
+        store_j<R, ST>(fout, node, pl, fn);
     };
     if (A.do_U) {
-        if (va) scalar_collide<R, TY, 0, 38, 2>(P, sm.phi, sm.post, tx + 1, ty + 1, Uia, mom_x(fa), mom_y(fa), uxa, uya);
-        if (vb) scalar_collide<R, TY, 0, 38, 2>(P, sm.phi, sm.post, blx, bly, Uib, mom_x(fb), mom_y(fb), uxb, uyb);
+        if (va) scalar_collide<R, TY, 0, 38, 2>(P, sm.phi, sm.post, tx + 1, ty + 1, Uia, jax, jay, uxa, uya);
+        if (vb) scalar_collide<R, TY, 0, 38, 2>(P, sm.phi, sm.post, blx, bly, Uib, jbx, jby, uxb, uyb);
         __syncthreads();
         scalar_stream(A.fUout, A.Uout);
         __syncthreads();
     }
     if (A.do_T) {
-        if (va) load8<R, ST>(A.fTin, na, pl, fa);
-        if (vb) load8<R, ST>(A.fTin, nb, pl, fb);
-        if (va) scalar_collide<R, TY, 1, 38, 2>(P, sm.phi, sm.post, tx + 1, ty + 1, Tia, mom_x(fa), mom_y(fa), uxa, uya);
-        if (vb) scalar_collide<R, TY, 1, 38, 2>(P, sm.phi, sm.post, blx, bly, Tib, mom_x(fb), mom_y(fb), uxb, uyb);
+        if (va) load_j<R, ST>(A.fTin, na, pl, jax, jay);
+        if (vb) load_j<R, ST>(A.fTin, nb, pl, jbx, jby);
+        if (va) scalar_collide<R, TY, 1, 38, 2>(P, sm.phi, sm.post, tx + 1, ty + 1, Tia, jax, jay, uxa, uya);
+        if (vb) scalar_collide<R, TY, 1, 38, 2>(P, sm.phi, sm.post, blx, bly, Tib, jbx, jby, uxb, uyb);
         __syncthreads();
         scalar_stream(A.fTout, A.Tout);
         __syncthreads();
@@ -272,6 +271,7 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
         bool fvb = false;
         if (tid < NR) fvb = IN || resolve_xy(fxb, fyb, P.nx, P.ny, P.bfx, P.bfy);
         const int fna = fya * P.pitch + fxa, fnb = fyb * P.pitch + fxb;
+        R fa[9], fb[9];
         R ra = R(1), rb = R(1), vxa = R(0), vya = R(0), vxb = R(0), vyb = R(0);
         if (fva) {
             load8<R, ST>(A.fFin, fna, pl, fa);
