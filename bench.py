@@ -114,9 +114,9 @@ def period_bytes(p, prec="f32"):
 # count once the state exceeds L2).  Reported only while the kernel sources
 # hash to TRAFFIC_SOURCE_SHA; after any change the traffic is null until
 # re-measured.
-TRAFFIC_SOURCE_SHA = "a54cd5b8d884bb4c"
-TRAFFIC_PER_LAUNCH_512 = {"transport:8": 33328384.0, "phase:4": 11564032.0}
-TRAFFIC_PER_NODE_2048 = {"phase:1016": 72.46, "transfer:1016": 17.17, "scalar_T:1008": 75.71, "flow:1016": 83.57}
+TRAFFIC_SOURCE_SHA = "cbaed3b1e8860bde"
+TRAFFIC_PER_LAUNCH_512 = {"transport:8": 20006656.0, "phase:4": 11563008.0}
+TRAFFIC_PER_NODE_2048 = {"phase:1016": 72.68, "transfer:1016": 16.99, "scalar_T:1008": 29.08, "flow:1016": 83.53}
 
 
 def kernel_source_sha():

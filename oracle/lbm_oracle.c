@@ -16,7 +16,7 @@
  *     update, phase-change transfer (Eqs. 36-39), concentration update,
  *     temperature update, flow update, each only when scheduled (Eq. 34).
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *   R-sched  field chi fires at base step n iff (n+1) mod N_chi == 0.
  *   R-gradphi  grad(phi) by the isotropic stencil g_a = 3 sum_i w_i e_ia phi(x+e_i)
  *            (the same stencil as the divergence of J, Sec. 3.3); Eq. 40 is

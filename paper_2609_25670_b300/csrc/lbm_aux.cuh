@@ -51,7 +51,8 @@ __global__ void k_init(const KP<R> P, const R* __restrict__ phi, const R* __rest
         R fe[9];
         feq_flow<R>(rhom[node], uxm[node], uym[node], P.cF, fe);                          // Eq. 28
 #pragma unroll
-        for (int i = 1; i < 9; ++i) fF[(size_t)(i - 1) * P.plane + node] = Cvt<ST>::st(DEV ? R(0) : fe[i]);
+        for (int i = 1; i < 9; ++i)
+            fF[(size_t)(i - 1) * P.plane + node] = Cvt<ST>::st(DEV ? fe[i] - wq<R>(i) * rhom[node] : fe[i]);
     }
 }
 

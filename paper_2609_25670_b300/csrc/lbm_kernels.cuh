@@ -21,7 +21,9 @@
 //          at rate one, so nothing else of the populations survives a
 //          collision (load_j / store_j).
 // With DEV = true the phase and flow planes hold deviations h_i = f_i - ref_i
-// in 16 bits: phase ref_i = w_i phi, flow ref_i = f_eq_i(rho, u) of Eq. 28.
+// in 16 bits: phase ref_i = w_i phi, flow ref_i = w_i rho (the zeroth-order
+// part of Eq. 28; the deviation is of order 3 w_i |u| + |f_neq|, one FMA to
+// decode or encode).
 // The U, T first moments are stored in ST as they are (the first moment of
 // w_i chi is zero, so j is already the deviation).
 //
@@ -568,14 +570,12 @@ __device__ __forceinline__ void flow_tile(FlowSmem<R, TY>& sm, const KP<R>& P, c
         load8<R, ST>(fin, nb, pl, fb);
         rb = rho_in[nb]; uxb = ux_in[nb]; uyb = uy_in[nb]; pb = phi[nb];
     }
-    if (DEV) {     // h_i = f_i - f_eq_i(rho, u) of the writer's macros
-        R ref[9];
-        if (va) { feq_flow<R>(ra, uxa, uya, c, ref);
+    if (DEV) {     // h_i = f_i - w_i rho of the writer's density
 #pragma unroll
-            for (int i = 1; i < 9; ++i) fa[i] += ref[i]; }
-        if (vb) { feq_flow<R>(rb, uxb, uyb, c, ref);
-#pragma unroll
-            for (int i = 1; i < 9; ++i) fb[i] += ref[i]; }
+        for (int i = 1; i < 9; ++i) {
+            if (va) fa[i] += wq<R>(i) * ra;
+            if (vb) fb[i] += wq<R>(i) * rb;
+        }
     }
     if (va) {
         sm.fl[ty + 1][tx + 1] = R(0.5) * (R(1) - pa);                               // f_L = (1 - phi)/2
@@ -626,10 +626,8 @@ __device__ __forceinline__ void flow_tile(FlowSmem<R, TY>& sm, const KP<R>& P, c
     ux_out[node] = ux;
     uy_out[node] = uy;
     if (DEV) {
-        R ref[9];
-        feq_flow<R>(rho, ux, uy, c, ref);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) fout[node + (i - 1) * pl] = Cvt<ST>::st(fn[i] - ref[i]);
+        for (int i = 1; i < 9; ++i) fout[node + (i - 1) * pl] = Cvt<ST>::st(fn[i] - wq<R>(i) * rho);
     } else {
 #pragma unroll
         for (int i = 1; i < 9; ++i) fout[node + (i - 1) * pl] = Cvt<ST>::st(fn[i]);

@@ -642,12 +642,9 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
                 const Vec4<ST> v = sread<ST>(sl + (i - 1) * 32 * EB);
                 f[i] = (R)Cvt<ST>::ld(v.v[k]);
             }
-            if (DEV) {     // h_i = f_i - f_eq_i(rho, u) of the writer's macros
-                R ref[9];
-                feq_flow<R>(rho.v[k], vx.v[k], vy.v[k], c, ref);
+            if (DEV)       // h_i = f_i - w_i rho of the writer's density
 #pragma unroll
-                for (int i = 1; i < 9; ++i) f[i] += ref[i];
-            }
+                for (int i = 1; i < 9; ++i) f[i] += wq<R>(i) * rho.v[k];
             flow_post9<R>(P, f, rho.v[k], p[k]);
             fl[k] = R(0.5) * (R(1) - ph.v[k]);                                       // f_L = (1 - phi)/2
         }
@@ -698,15 +695,11 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
             *reinterpret_cast<Vec4<R>*>(rho_out + node) = vrho;
             *reinterpret_cast<Vec4<R>*>(ux_out + node) = vux;
             *reinterpret_cast<Vec4<R>*>(uy_out + node) = vuy;
-            R ref[VW][9];
-            if (DEV)
-#pragma unroll
-                for (int k = 0; k < VW; ++k) feq_flow<R>(vrho.v[k], vux.v[k], vuy.v[k], c, ref[k]);
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 Vec4<ST> ov;
 #pragma unroll
-                for (int k = 0; k < VW; ++k) ov.v[k] = Cvt<ST>::st(DEV ? fn[i][k] - ref[k][i] : fn[i][k]);
+                for (int k = 0; k < VW; ++k) ov.v[k] = Cvt<ST>::st(DEV ? fn[i][k] - wq<R>(i) * vrho.v[k] : fn[i][k]);
                 *reinterpret_cast<Vec4<ST>*>(fout + (size_t)(i - 1) * pl + node) = ov;
             }
         }

@@ -281,14 +281,12 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
             load8<R, ST>(A.fFin, fnb, pl, fb);
             rb = A.rho_in[fnb]; vxb = A.ux_in[fnb]; vyb = A.uy_in[fnb];
         }
-        if (DEV) {
-            R ref[9];
-            if (fva) { feq_flow<R>(ra, vxa, vya, c, ref);
+        if (DEV) {     // h_i = f_i - w_i rho of the writer's density
 #pragma unroll
-                for (int i = 1; i < 9; ++i) fa[i] += ref[i]; }
-            if (fvb) { feq_flow<R>(rb, vxb, vyb, c, ref);
-#pragma unroll
-                for (int i = 1; i < 9; ++i) fb[i] += ref[i]; }
+            for (int i = 1; i < 9; ++i) {
+                if (fva) fa[i] += wq<R>(i) * ra;
+                if (fvb) fb[i] += wq<R>(i) * rb;
+            }
         }
         // liquid fraction of the 1-ring positions: from the staged phase field
         // where the position lies inside the lattice, else (a periodic image
@@ -340,10 +338,8 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
             A.ux_out[node] = ux;
             A.uy_out[node] = uy;
             if (DEV) {
-                R ref[9];
-                feq_flow<R>(rho, ux, uy, c, ref);
 #pragma unroll
-                for (int i = 1; i < 9; ++i) A.fFout[node + (i - 1) * pl] = Cvt<ST>::st(fn[i] - ref[i]);
+                for (int i = 1; i < 9; ++i) A.fFout[node + (i - 1) * pl] = Cvt<ST>::st(fn[i] - wq<R>(i) * rho);
             } else {
 #pragma unroll
                 for (int i = 1; i < 9; ++i) A.fFout[node + (i - 1) * pl] = Cvt<ST>::st(fn[i]);
