@@ -13,6 +13,7 @@
 // coupling only (the accumulated ablation uses the separate kernels).
 #pragma once
 #include "lbm_kernels.cuh"
+#include "lbm_strip.cuh"
 
 namespace lbmk {
 
@@ -32,7 +33,15 @@ template <typename R, typename ST> struct TransportJob {
     int tiles_x, tile0;
 };
 
+// Words the later stages read, copied asynchronously into shared memory by
+// the prologue so that their global latency overlaps the transfer and the U
+// update: the T first moments, the flow populations 1..8 and rho.
+// Each thread copies and later reads only its own entries (own node: item A,
+// a ring node: item B).
+enum { PF_TJX = 0, PF_TJY = 1, PF_F = 2, PF_RHO = 10, PF_N = 11 };
+
 template <typename R, int TY> struct TransportSmem {
+    static constexpr int NRB = 2 * 34 + 2 * TY;   // ring items
     R phi[TY + 6][38];                 // phase field on the tile + 3-ring
     R Jx[TY + 4][36], Jy[TY + 4][36];  // J on the 2-ring
     R dphi[TY + 4][36];                // Delta phi on the 2-ring
@@ -41,6 +50,8 @@ template <typename R, int TY> struct TransportSmem {
     R fl[TY + 2][34];                  // liquid fraction on the 1-ring (flow)
     R post[9][TY + 2][34];
     R red[TY];
+    Word<R> pa[PF_N][32 * TY];         // prefetched words of item A
+    Word<R> pb[PF_N][NRB];             // prefetched words of item B
 };
 
 template <int TY>
@@ -145,6 +156,39 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
         if (va) { uxa = A.ux_in[na]; uya = A.uy_in[na]; }
         if (vb) { uxb = A.ux_in[nb]; uyb = A.uy_in[nb]; }
     }
+    // flow items: the same positions under the flow's own boundary rule
+    // (evaluated here for the prefetch and again in the flow stage, so that
+    // no index stays live across the stages in between)
+    auto flow_item = [&](int lx, int ly, int& fx, int& fy) -> bool {
+        fx = x0 - 1 + lx;
+        fy = y0 - 1 + ly;
+        return IN || resolve_xy(fx, fy, P.nx, P.ny, P.bfx, P.bfy);
+    };
+    // asynchronous prefetch of the T and flow stages' words
+    if (A.do_T) {
+        fetch_word<R>(&sm.pa[PF_TJX][tid], A.fTin, na, va);
+        fetch_word<R>(&sm.pa[PF_TJY][tid], A.fTin + pl, na, va);
+        if (tid < NR) {
+            fetch_word<R>(&sm.pb[PF_TJX][tid], A.fTin, nb, vb);
+            fetch_word<R>(&sm.pb[PF_TJY][tid], A.fTin + pl, nb, vb);
+        }
+    }
+    if (A.do_F) {
+        int fxa, fya, fxb = 0, fyb = 0;
+        const bool fva = flow_item(tx + 1, ty + 1, fxa, fya);
+        const bool fvb = tid < NR && flow_item(blx, bly, fxb, fyb);
+        const int fna = fya * P.pitch + fxa, fnb = fyb * P.pitch + fxb;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) fetch_word<R>(&sm.pa[PF_F + i - 1][tid], A.fFin + (size_t)(i - 1) * pl, fna, fva);
+        fetch_word<R>(&sm.pa[PF_RHO][tid], A.rho_in, fna, fva);
+        if (tid < NR) {
+#pragma unroll
+            for (int i = 1; i < 9; ++i)
+                fetch_word<R>(&sm.pb[PF_F + i - 1][tid], A.fFin + (size_t)(i - 1) * pl, fnb, fvb);
+            fetch_word<R>(&sm.pb[PF_RHO][tid], A.rho_in, fnb, fvb);
+        }
+    }
+    __pipeline_commit();
     load_phi_ring3<R, TY, IN>(P, A.phi, sm.phi, x0, y0, tid);
     __syncthreads();
 
@@ -254,8 +298,15 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
         __syncthreads();
     }
     if (A.do_T) {
-        if (va) load_j<R, ST>(A.fTin, na, pl, jax, jay);
-        if (vb) load_j<R, ST>(A.fTin, nb, pl, jbx, jby);
+        __pipeline_wait_prior(0);                   // this thread's prefetched words have landed
+        if (va) {
+            jax = word_value<R, ST>(sm.pa[PF_TJX][tid], (na & 1) != 0);
+            jay = word_value<R, ST>(sm.pa[PF_TJY][tid], (na & 1) != 0);
+        }
+        if (vb) {
+            jbx = word_value<R, ST>(sm.pb[PF_TJX][tid], (nb & 1) != 0);
+            jby = word_value<R, ST>(sm.pb[PF_TJY][tid], (nb & 1) != 0);
+        }
         if (va) scalar_collide<R, TY, 1, 38, 2>(P, sm.phi, sm.post, tx + 1, ty + 1, Tia, jax, jay, uxa, uya);
         if (vb) scalar_collide<R, TY, 1, 38, 2>(P, sm.phi, sm.post, blx, bly, Tib, jbx, jby, uxb, uyb);
         __syncthreads();
@@ -266,20 +317,22 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
     // ---- flow update (Eqs. 27-33), flow boundaries
     if (A.do_F) {
         const R c = P.cF, dt = P.dtF;
-        int fxa = x0 + tx, fya = y0 + ty, fxb = x0 - 1 + blx, fyb = y0 - 1 + bly;
-        const bool fva = IN || resolve_xy(fxa, fya, P.nx, P.ny, P.bfx, P.bfy);
-        bool fvb = false;
-        if (tid < NR) fvb = IN || resolve_xy(fxb, fyb, P.nx, P.ny, P.bfx, P.bfy);
+        int fxa, fya, fxb = 0, fyb = 0;
+        const bool fva = flow_item(tx + 1, ty + 1, fxa, fya);
+        const bool fvb = tid < NR && flow_item(blx, bly, fxb, fyb);
         const int fna = fya * P.pitch + fxa, fnb = fyb * P.pitch + fxb;
+        __pipeline_wait_prior(0);                   // this thread's prefetched words have landed
         R fa[9], fb[9];
-        R ra = R(1), rb = R(1), vxa = R(0), vya = R(0), vxb = R(0), vyb = R(0);
+        R ra = R(1), rb = R(1);
         if (fva) {
-            load8<R, ST>(A.fFin, fna, pl, fa);
-            ra = A.rho_in[fna]; vxa = A.ux_in[fna]; vya = A.uy_in[fna];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) fa[i] = word_value<R, ST>(sm.pa[PF_F + i - 1][tid], (fna & 1) != 0);
+            ra = word_value<R, R>(sm.pa[PF_RHO][tid], false);
         }
         if (fvb) {
-            load8<R, ST>(A.fFin, fnb, pl, fb);
-            rb = A.rho_in[fnb]; vxb = A.ux_in[fnb]; vyb = A.uy_in[fnb];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) fb[i] = word_value<R, ST>(sm.pb[PF_F + i - 1][tid], (fnb & 1) != 0);
+            rb = word_value<R, R>(sm.pb[PF_RHO][tid], false);
         }
         if (DEV) {     // h_i = f_i - w_i rho of the writer's density
 #pragma unroll
@@ -348,8 +401,13 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
     }
 }
 
+// FP32: at least 1024 resident threads per SM (64 registers a thread), the
+// occupancy the tile's latency hiding needs; FP64 (parity runs) unconstrained
+template <typename R, int TY> struct TransportOcc { static constexpr int MIN_BLOCKS = sizeof(R) == 4 ? 32 / TY : 1; };
+
 template <typename R, typename ST, bool DEV, int TY>
-__global__ void __launch_bounds__(32 * TY) k_transport_batch(const TransportJob<R, ST>* __restrict__ jobs, int njobs) {
+__global__ void __launch_bounds__(32 * TY, (TransportOcc<R, TY>::MIN_BLOCKS))
+k_transport_batch(const TransportJob<R, ST>* __restrict__ jobs, int njobs) {
     extern __shared__ __align__(16) unsigned char transport_smem[];
     TransportSmem<R, TY>& sm = *reinterpret_cast<TransportSmem<R, TY>*>(transport_smem);
     int x0, y0;
