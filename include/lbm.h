@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define LBM_PARAMS_VERSION 1u
+#define LBM_PARAMS_VERSION 2u
 
 typedef enum {
     LBM_OK = 0,
@@ -69,7 +69,7 @@ enum {
     LBM_PREC_F64 = 0,      /* FP64 storage and arithmetic                          */
     LBM_PREC_F32 = 1,      /* FP32 storage and arithmetic                          */
     LBM_PREC_F16_DEV = 2,  /* FP16 storage, FP32 arithmetic: phase f_i - w_i phi,
-                              flow f_i - f_eq_i(rho, u) (Eq. 28), U/T j as is      */
+                              flow f_i - w_i rho, U/T j as is                      */
     LBM_PREC_BF16_DEV = 3  /* BF16 storage of the same quantities, FP32 arithmetic */
 };
 
@@ -85,7 +85,11 @@ enum { LBM_COUPLING_INSTANTANEOUS = 0, LBM_COUPLING_ACCUMULATED = 1 };
  *   Eqs. 27-33: nu, u_in (inlet velocity), Fbx, Fby (body force), s_e, s_eps, s_q
  *   frozen temperature: theta = theta_c + frozen_G (y - frozen_y0 - frozen_V t);
  *             with neither T nor FROZEN_T, theta = theta_c.
- *   tip_cx, tip_cy: node through which lbm_diagnostics measures the tips. */
+ *   tip_cx, tip_cy: node through which lbm_diagnostics measures the tips.
+ *   T_ymin_dirichlet, T_ymin: with T on and bc_scalar_y = WALL, the bottom
+ *             wall holds T = T_ymin (Sec. 4.4, the cold bottom boundary kept at
+ *             T_b) instead of zero flux, by anti-bounce-back at the half-way
+ *             wall; phi and U keep zero flux there. */
 typedef struct {
     uint32_t struct_version; /* = LBM_PARAMS_VERSION */
     int32_t nx, ny;          /* lattice size, >= 4 each */
@@ -96,12 +100,15 @@ typedef struct {
     uint32_t coupling;       /* LBM_COUPLING_* */
     int32_t N_phi, N_U, N_T, N_F; /* update factors, >= 1 */
     int32_t tip_cx, tip_cy;
+    int32_t T_ymin_dirichlet;    /* 1: T = T_ymin on the bottom wall (version 2) */
+    int32_t reserved;
     double dt_base;
     double W0, tau0, eps, lam;
     double Mc, k, DL, DS;
     double kappaS, kappaL, rhoCpS, rhoCpL, rhoL_Lh, T_shift, T_scale;
     double nu, u_in, Fbx, Fby, s_e, s_eps, s_q;
     double theta_c, frozen_G, frozen_y0, frozen_V;
+    double T_ymin;               /* bottom-wall temperature (version 2) */
 } lbm_params;
 
 /* Initial-condition primitives for lbm_init_seed. phi is the maximum over all

@@ -40,7 +40,7 @@ class _OrcParams(C.Structure):
         ("bc_flow_x", C.c_int32), ("bc_flow_y", C.c_int32),
         ("accumulated", C.c_int32),
         ("N_phi", C.c_int32), ("N_U", C.c_int32), ("N_T", C.c_int32), ("N_F", C.c_int32),
-        ("tip_cx", C.c_int32), ("tip_cy", C.c_int32),
+        ("tip_cx", C.c_int32), ("tip_cy", C.c_int32), ("T_ymin_dirichlet", C.c_int32),
         ("dt_base", C.c_double),
         ("W0", C.c_double), ("tau0", C.c_double), ("eps", C.c_double), ("lam", C.c_double),
         ("Mc", C.c_double), ("k", C.c_double), ("DL", C.c_double), ("DS", C.c_double),
@@ -49,7 +49,7 @@ class _OrcParams(C.Structure):
         ("nu", C.c_double), ("u_in", C.c_double), ("Fbx", C.c_double), ("Fby", C.c_double),
         ("s_e", C.c_double), ("s_eps", C.c_double), ("s_q", C.c_double),
         ("theta_c", C.c_double), ("frozen_G", C.c_double), ("frozen_y0", C.c_double),
-        ("frozen_V", C.c_double),
+        ("frozen_V", C.c_double), ("T_ymin", C.c_double),
     ]
 
 
@@ -97,10 +97,12 @@ def to_orc_params(p) -> _OrcParams:
     o.accumulated = int(bool(d["accumulated"]))
     o.N_phi, o.N_U, o.N_T, o.N_F = int(d["N_phi"]), int(d["N_U"]), int(d["N_T"]), int(d["N_F"])
     o.tip_cx, o.tip_cy = int(d["tip_cx"]), int(d["tip_cy"])
+    o.T_ymin_dirichlet = int(bool(d.get("T_ymin_dirichlet", False)))
     for nm in ("dt_base", "W0", "tau0", "eps", "lam", "Mc", "k", "DL", "DS", "kappaS", "kappaL",
                "rhoCpS", "rhoCpL", "rhoL_Lh", "T_shift", "T_scale", "nu", "u_in", "Fbx", "Fby",
                "s_e", "s_eps", "s_q", "theta_c", "frozen_G", "frozen_y0", "frozen_V"):
         setattr(o, nm, float(d[nm]))
+    o.T_ymin = float(d.get("T_ymin", 0.0))
     return o
 
 

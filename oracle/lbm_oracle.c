@@ -34,6 +34,10 @@
  *            outflow column: f_i(L-1) = f_i(L-2).
  *   R-frozen prescribed theta(y, t) = theta_c + G (y - y0 - V t) with t the
  *            time at the start of the base step.
+ *   R-dirichlet  the cold bottom wall kept at T_b (Sec. 4.4): anti-bounce-back
+ *            at the half-way wall below row 0, f_i = -f*_opp(i) + 2 w_i T_b
+ *            for the links that enter row 0 from below; phi and U keep zero
+ *            flux there.
  */
 #include <math.h>
 #include <stdint.h>
@@ -117,12 +121,14 @@ typedef struct {
     int32_t accumulated;
     int32_t N_phi, N_U, N_T, N_F;
     int32_t tip_cx, tip_cy;
+    int32_t T_ymin_dirichlet;  /* 1: T = T_ymin on the wall below row 0 */
     double dt_base;
     double W0, tau0, eps, lam;
     double Mc, k, DL, DS;
     double kappaS, kappaL, rhoCpS, rhoCpL, rhoL_Lh, T_shift, T_scale;
     double nu, u_in, Fbx, Fby, s_e, s_eps, s_q;
     double theta_c, frozen_G, frozen_y0, frozen_V;
+    double T_ymin;
 } orc_params;
 
 typedef struct {
@@ -567,7 +573,11 @@ static void scalar_step(orc_sim* s, int fld) {
             double sum = 0.0;
             for (int i = 0; i < 9; ++i) {
                 int src = scalar_src(p, x, y, i);
-                double v = (src < 0) ? s->post[opposite(i) * nn + n] : s->post[i * nn + src]; /* Eq. 25 */
+                double v;
+                if (src >= 0) v = s->post[i * nn + src];                               /* Eq. 25 */
+                else if (fld == F_T && p->T_ymin_dirichlet && y - EY[i] < 0)
+                    v = -s->post[opposite(i) * nn + n] + 2.0 * WQ[i] * p->T_ymin;       /* R-dirichlet */
+                else v = s->post[opposite(i) * nn + n];                                 /* R-bb */
                 fn[i * nn + n] = v;
                 sum += v;
             }

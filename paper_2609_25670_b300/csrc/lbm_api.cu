@@ -240,6 +240,8 @@ lbm_status validate(const lbm_params* p, std::string& why) {
         return bad("flow boundary x must be PERIODIC, WALL or INLET_OUTFLOW; y PERIODIC or WALL");
     if (p->bc_flow_x == LBM_BC_INLET_OUTFLOW && (p->nx % TX) == 1)
         return bad("INLET_OUTFLOW needs nx % 32 != 1");
+    if (p->T_ymin_dirichlet && (!(p->fields & LBM_FIELD_T) || p->bc_scalar_y != LBM_BC_WALL))
+        return bad("T_ymin_dirichlet needs the T field and bc_scalar_y = WALL");
     if (p->precision > LBM_PREC_BF16_DEV) return bad("unknown precision");
     if (p->coupling > LBM_COUPLING_ACCUMULATED) return bad("unknown coupling");
     if (p->N_phi < 1 || p->N_U < 1 || p->N_T < 1 || p->N_F < 1) return bad("update factors must be >= 1");
@@ -290,6 +292,8 @@ template <typename R> KP<R> make_kp(const SimState& s) {
     k.u_in = (R)p.u_in;
     k.theta_c = (R)p.theta_c; k.fG = (R)p.frozen_G; k.fy0 = (R)p.frozen_y0; k.fV = (R)p.frozen_V;
     k.dt_base = (R)p.dt_base;
+    k.T_dir_ym = s.has_T && p.T_ymin_dirichlet;
+    k.T_ymin = (R)p.T_ymin;
     return k;
 }
 

@@ -44,6 +44,9 @@ template <typename R> struct KP {
     R dtF, cF, Fbx, Fby, se, seps, sq, snu, u_in;
     // prescribed undercooling
     R theta_c, fG, fy0, fV, dt_base;
+    // bottom wall held at T = T_ymin (anti-bounce-back) instead of zero flux
+    int T_dir_ym;
+    R T_ymin;
 };
 
 // Reciprocal.  FP32: the hardware approximation (PTX rcp.approx.ftz.f32,

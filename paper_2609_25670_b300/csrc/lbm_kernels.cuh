@@ -448,6 +448,8 @@ __device__ __forceinline__ void scalar_tile(ScalarSmem<R, TY>& sm, const KP<R>& 
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             fn[i] = w.hit(i) ? sm.post[opp_of(i)][ty + 1][tx + 1] : sm.post[i][ty + 1 - ey_of(i)][tx + 1 - ex_of(i)]; // Eq. 25
+            if (FIELD == 1 && !IN && ey_of(i) > 0 && w.ym && P.T_dir_ym)              // bottom wall at T_ymin
+                fn[i] = R(2) * wq<R>(i) * P.T_ymin - sm.post[opp_of(i)][ty + 1][tx + 1];
             sum += fn[i];
         }
         mac_out[node] = sum;                                                      // Eq. 18

@@ -246,6 +246,11 @@ __device__ __forceinline__ void scalar_strip(const KP<R>& P, const ST* __restric
                 if (wxp || wym) fn[6] = o[8];
                 if (wxp || wyp) fn[7] = o[5];
                 if (wxm || wyp) fn[8] = o[6];
+                if (FIELD == 1 && wym && P.T_dir_ym) {      // bottom wall at T_ymin: anti-bounce-back
+                    fn[2] = R(2) * Wt<R>::w1 * P.T_ymin - o[4];
+                    fn[5] = R(2) * Wt<R>::w2 * P.T_ymin - o[7];
+                    fn[6] = R(2) * Wt<R>::w2 * P.T_ymin - o[8];
+                }
             }
             R sum = R(0);
 #pragma unroll
@@ -958,12 +963,7 @@ __device__ __forceinline__ void transfer_vs_block(const KP<R>& P, const R* phio,
 // its own loaded populations and a_s^2, carried from its collision.
 // ---------------------------------------------------------------------------
 enum { PA_PHI = 8, PA_U = 9, PA_T = 10, PA_N = 11 };
-template <typename R> struct PRing {
-    static constexpr int EB = VW * (int)sizeof(R);
-    static constexpr int SLOT = PA_N * 32 * EB;
-    static constexpr int D = sizeof(R) == 8 ? 2 : 4;
-    static constexpr int BYTES = D * SLOT;
-};
+template <typename R> using PRing = VRingN<R, PA_N>;
 
 template <typename R, typename ST, bool DEV, int H, bool UP>
 __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restrict__ fin, ST* __restrict__ fout,

@@ -121,6 +121,9 @@ class Params:
     # diagnostics: node the tip crossings are measured from
     tip_cx: int = 0
     tip_cy: int = 0
+    # bottom wall held at T = T_ymin (Sec. 4.4) instead of zero flux for T
+    T_ymin_dirichlet: bool = False
+    T_ymin: float = 0.0
 
     def as_dict(self) -> Dict:
         return dict(self.__dict__)
@@ -265,6 +268,41 @@ def directional_saline(Le: int = 100, nx: int = 1024, ny: int = 2048, y0: float 
     phi = planar_front(nx, ny, y0, W0, noise, seed)
     return Workload("directional_Le%d_%dx%d" % (Le, nx, ny), p,
                     base_fields(p, phi, U0=0.0), n_base_steps)
+
+
+def directional_evolving_T(Le: int = 100, nx: int = 1000, ny: int = 1000, n_base_steps: int = 10_000_000) -> Workload:
+    """Directional thermosolutal solidification of saline water with an
+    evolving temperature field (Sec. 4.4, Table 1, Eqs. 41-42).
+
+    Table 1 lattice values: L_h = 133.6, C_pL = 1.676, C_pS = 0.836,
+    kappa_L = 0.0437, kappa_S = 0.178 (rho_S = rho_L = 1), k_c = 0.001,
+    C_inf = 0.03, m_L = -57, Gamma = 0.268, eps = 0.03; W0 = 2, tau0 = 150.
+    d0 = Gamma/(|m_L|(1-k)C_inf), lambda = a1 W0/d0, M_c per Eq. 5, and
+    theta = (T - T_m - m_L C_inf)/(L_h/C_pL) with T_m = 0 (Eq. 5).  D_L =
+    0.026/Le (Eq. 42 in lattice units), D_S = 1e-2 D_L, N_U = Le,
+    N_phi = N_T = 1.  Initial layer phi of Eq. 41 (mean height 10, amplitude
+    1, five wavelengths across), T = T_b = -20 everywhere and held at the
+    bottom wall, U = 0, no flow; zero flux for phi and U on every wall and
+    for T at the top; periodic in x (the Eq. 41 perturbation spans whole
+    wavelengths)."""
+    W0, k, Cinf, mL, Gamma = 2.0, 0.001, 0.03, -57.0, 0.268
+    Lh, CpL, CpS = 133.6, 1.676, 0.836
+    d0 = Gamma / (abs(mL) * (1.0 - k) * Cinf)
+    lam = A1 * W0 / d0
+    Mc = abs(mL) * (1.0 - k) * Cinf / (Lh / CpL)
+    DL = 0.026 / Le
+    Tb = -20.0
+    p = Params(nx=nx, ny=ny, has_U=True, has_T=True,
+               bc_scalar_x=BC_PERIODIC, bc_scalar_y=BC_WALL,
+               N_U=int(Le), W0=W0, tau0=150.0, eps=0.03, lam=lam,
+               Mc=Mc, k=k, DL=DL, DS=1e-2 * DL,
+               kappaS=0.178, kappaL=0.0437, rhoCpS=CpS, rhoCpL=CpL, rhoL_Lh=Lh,
+               T_shift=0.0 + mL * Cinf, T_scale=Lh / CpL,
+               T_ymin_dirichlet=True, T_ymin=Tb,
+               tip_cx=nx // 2, tip_cy=0)
+    phi = sinusoid_layer(nx, ny, W0, h=10.0, amp=1.0, waves=5.0)
+    return Workload("directional_evolving_T_Le%d_%dx%d" % (Le, nx, ny), p,
+                    base_fields(p, phi, U0=0.0, T0=Tb), n_base_steps)
 
 
 def ensemble_members(count: int = 64, seed: int = 4, sizes=(128, 256, 512, 1024),
