@@ -523,10 +523,87 @@ def run_ensemble(args):
     return 0
 
 
+def run_sweep(args):
+    """Update-factor sweeps (Secs. 4.1 and 4.4), measured on the GPU:
+
+    * the thermal free dendrite (128^2, phi + T) with N_T in {1, 2, 4, 8} at
+      fixed physics: tip velocity over the last 500 of 2000 base steps and
+      MLUPS of the 2000 steps;
+    * the Sec. 4.4 directional saline-water case with the evolving
+      temperature (Table 1, bottom wall at T_b = -20, 1000 x 1000) for
+      Le in {1, 10, 100, 1000} with N_U = Le: MLUPS over two schedule
+      periods (at least 2000 base steps), solute drift R_M and the front
+      height after them."""
+    import torch
+    import paper_2609_25670_b300 as lbm
+    prec = args.precision or "f32"
+
+    def timed(sim, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(sim.stream):
+            e0.record(sim.stream)
+        sim.advance(n)
+        with torch.cuda.stream(sim.stream):
+            e1.record(sim.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    thermal = []
+    for NT in (1, 2, 4, 8):
+        wl = W.thermal_free_dendrite(n=128, N_T=NT)
+        sim = lbm.Simulation(wl.params, precision=prec)
+        sim.init_fields(wl.fields)
+        hist = []
+        for _ in range(100):
+            sim.advance(20)
+            hist.append(sim.diagnostics()["tip"].copy())
+        sim.init_fields(wl.fields)
+        sim.advance(max(args.warmup, 3) * NT)
+        ms = timed(sim, 2000)
+        sim.close()
+        h = np.asarray(hist)
+        thermal.append({"N_T": NT, "tau_T": 3.0 * NT * wl.params.kappaL / wl.params.rhoCpL + 0.5,
+                        "v_tip": float(((h[-1] - h[-26]) / 500.0).mean()), "tip_2000": float(h[-1].mean()),
+                        "mlups": 128 * 128 * 2000 / (ms * 1e-3) / 1e6})
+    v1 = thermal[0]["v_tip"]
+    for r in thermal:
+        r["v_tip_rel_to_NT1"] = r["v_tip"] / v1
+
+    directional = []
+    for Le in (1, 10, 100, 1000):
+        wl = W.directional_evolving_T(Le=Le)
+        sim = lbm.Simulation(wl.params, precision=prec)
+        sim.init_fields(wl.fields)
+        m0 = sim.diagnostics()["M_C"]
+        period = max(1, Le)
+        sim.advance(period)
+        sim.autotune(reps=3)
+        n = 2 * max(1000, period)
+        ms = timed(sim, n)
+        d = sim.diagnostics()
+        sim.close()
+        directional.append({"Le": Le, "N_U": Le, "base_steps": n + period,
+                            "mlups": wl.params.nx * wl.params.ny * n / (ms * 1e-3) / 1e6,
+                            "R_M": (d["M_C"] - m0) / m0, "front_height": float(d["tip"][1]),
+                            "nonfinite": int(d["nonfinite"])})
+    line = {"metric": METRIC + " (update-factor sweeps)",
+            "value": next(r["mlups"] for r in directional if r["Le"] == 100), "unit": UNIT,
+            "n_gpus": 1, "steps": 1, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == "f64" else "f32", "data": "synthetic (seeded)",
+            "config": {"workload": "Sec. 4.4 directional saline water with evolving T, 1000x1000, Le = 100 "
+                                   "(value); thermal dendrite N_T sweep and Le sweep in the details",
+                       "storage": prec},
+            "thermal_dendrite_NT_sweep": thermal, "directional_Le_sweep": directional}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="convection512", choices=["convection512", "ensemble"],
-                    help="convection512: the reported workload; ensemble: batched-ensemble measurement")
+    ap.add_argument("--workload", default="convection512", choices=["convection512", "ensemble", "sweep"],
+                    help="convection512: the reported workload; ensemble: batched-ensemble measurement; "
+                         "sweep: update-factor sweeps (thermal dendrite N_T, directional Le)")
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--precision", default=None)
     ap.add_argument("--gpus", type=int, default=1)
@@ -548,6 +625,8 @@ def main():
         return run_reference(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_ours(args)
 
 
