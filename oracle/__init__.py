@@ -41,7 +41,7 @@ class _OrcParams(C.Structure):
         ("accumulated", C.c_int32),
         ("N_phi", C.c_int32), ("N_U", C.c_int32), ("N_T", C.c_int32), ("N_F", C.c_int32),
         ("tip_cx", C.c_int32), ("tip_cy", C.c_int32), ("T_ymin_dirichlet", C.c_int32),
-        ("dt_base", C.c_double),
+        ("q_scalar", C.c_int32), ("dt_base", C.c_double),
         ("W0", C.c_double), ("tau0", C.c_double), ("eps", C.c_double), ("lam", C.c_double),
         ("Mc", C.c_double), ("k", C.c_double), ("DL", C.c_double), ("DS", C.c_double),
         ("kappaS", C.c_double), ("kappaL", C.c_double), ("rhoCpS", C.c_double), ("rhoCpL", C.c_double),
@@ -75,6 +75,10 @@ def _load():
             getattr(lib, nm).argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, dp]
         lib.orc_matrices.argtypes = [dp, dp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
         lib.orc_collide_scalar.argtypes = [dp, dp, C.c_double, C.c_double, dp]
+        lib.orc_collide_scalar_q.argtypes = [C.c_int, dp, dp, C.c_double, C.c_double, dp]
+        lib.orc_matrices5.argtypes = [dp, dp, dp]
+        for nm in ("orc_feq_scalar_q", "orc_meq_scalar_q", "orc_feq_phase_q", "orc_meq_phase_q"):
+            getattr(lib, nm).argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, dp]
         lib.orc_relaxation_times.argtypes = [C.POINTER(_OrcParams), C.c_double, dp]
         lib.orc_num_threads.restype = C.c_int
         lib.orc_set_threads.argtypes = [C.c_int]
@@ -98,6 +102,7 @@ def to_orc_params(p) -> _OrcParams:
     o.N_phi, o.N_U, o.N_T, o.N_F = int(d["N_phi"]), int(d["N_U"]), int(d["N_T"]), int(d["N_F"])
     o.tip_cx, o.tip_cy = int(d["tip_cx"]), int(d["tip_cy"])
     o.T_ymin_dirichlet = int(bool(d.get("T_ymin_dirichlet", False)))
+    o.q_scalar = int(d.get("q_scalar", 9))
     for nm in ("dt_base", "W0", "tau0", "eps", "lam", "Mc", "k", "DL", "DS", "kappaS", "kappaL",
                "rhoCpS", "rhoCpL", "rhoL_Lh", "T_shift", "T_scale", "nu", "u_in", "Fbx", "Fby",
                "s_e", "s_eps", "s_q", "theta_c", "frozen_G", "frozen_y0", "frozen_V"):
@@ -175,6 +180,36 @@ def matrices():
     w = np.zeros(9)
     lib.orc_matrices(_dp(M), _dp(Mi), ex, ey, _dp(w))
     return M.reshape(9, 9), Mi.reshape(9, 9), np.array(ex[:]), np.array(ey[:]), w
+
+
+def matrices5():
+    """M, M^-1 and the weights of the five-velocity scalar lattice."""
+    lib = _load()
+    M = np.zeros(25)
+    Mi = np.zeros(25)
+    w = np.zeros(5)
+    lib.orc_matrices5(_dp(M), _dp(Mi), _dp(w))
+    return M.reshape(5, 5), Mi.reshape(5, 5), w
+
+
+def equilibrium_q(q: int, kind: str, a: float, ux: float, uy: float, c: float):
+    """f_eq and m_eq of the scalar ("scalar") or phase ("phase") equilibrium on
+    the q-velocity lattice (q = 9 or 5)."""
+    lib = _load()
+    f = np.zeros(q)
+    m = np.zeros(q)
+    getattr(lib, "orc_feq_%s_q" % kind)(q, a, ux, uy, c, _dp(f))
+    getattr(lib, "orc_meq_%s_q" % kind)(q, a, ux, uy, c, _dp(m))
+    return f, m
+
+
+def collide_scalar_q(q: int, f: np.ndarray, meq: np.ndarray, tau: float, dtQ: float) -> np.ndarray:
+    lib = _load()
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    meq = np.ascontiguousarray(meq, dtype=np.float64)
+    out = np.zeros(q)
+    lib.orc_collide_scalar_q(int(q), _dp(f), _dp(meq), float(tau), float(dtQ), _dp(out))
+    return out
 
 
 def equilibrium(kind: str, a: float, ux: float, uy: float, c: float):

@@ -34,6 +34,7 @@
  *            outflow column: f_i(L-1) = f_i(L-2).
  *   R-frozen prescribed theta(y, t) = theta_c + G (y - y0 - V t) with t the
  *            time at the start of the base step.
+ *   R-d2q5   the five-velocity option of the scalar lattices (see WQ5 / MM5).
  *   R-dirichlet  the cold bottom wall kept at T_b (Sec. 4.4): anti-bounce-back
  *            at the half-way wall below row 0, f_i = -f*_opp(i) + 2 w_i T_b
  *            for the links that enter row 0 from below; phi and U keep zero
@@ -54,6 +55,21 @@ static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 static const double WQ[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+/* Five-velocity option for the scalar lattices (phi, U, T); the paper fixes
+ * D2Q9 for all four fields, D2Q5 is read as the same scheme on the rest
+ * velocity and the four axis links of Eq. 15: weights 1/3 and 1/6 (c_s^2 =
+ * 1/3, so Eq. 24 ties tau to the diffusivity as on D2Q9), moments
+ * (1, e_x, e_y, -4 + 5|e|^2, e_x^2 - e_y^2) and every moment but the two
+ * fluxes relaxed at rate one, as Eq. 23 does on D2Q9. */
+static const double WQ5[5] = {1.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0};
+static const double MM5[5][5] = {
+    {1, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0},
+    {0, 0, 1, 0, -1},
+    {-4, 1, 1, 1, 1},
+    {0, 1, -1, 1, -1}};
+static double MI5[5][5];
 
 /* Transformation matrix of Eq. 16, as printed. */
 static const double MM[9][9] = {
@@ -76,31 +92,42 @@ static int opposite(int i) {
     return -1;
 }
 
-/* M^-1 by Gauss-Jordan elimination with partial pivoting. */
-static void build_minv(void) {
-    if (mi_ready) return;
+/* Inverse of an n x n matrix (n <= 9) by Gauss-Jordan elimination with
+ * partial pivoting; A and out are row-major. */
+static void gauss_jordan(int n, const double* A, double* out) {
     double a[9][18];
-    for (int r = 0; r < 9; ++r)
-        for (int c = 0; c < 18; ++c) a[r][c] = (c < 9) ? MM[r][c] : (c - 9 == r ? 1.0 : 0.0);
-    for (int c = 0; c < 9; ++c) {
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < 2 * n; ++c) a[r][c] = (c < n) ? A[r * n + c] : (c - n == r ? 1.0 : 0.0);
+    for (int c = 0; c < n; ++c) {
         int p = c;
-        for (int r = c + 1; r < 9; ++r)
+        for (int r = c + 1; r < n; ++r)
             if (fabs(a[r][c]) > fabs(a[p][c])) p = r;
         if (p != c)
-            for (int k = 0; k < 18; ++k) { double t = a[c][k]; a[c][k] = a[p][k]; a[p][k] = t; }
+            for (int k = 0; k < 2 * n; ++k) { double t = a[c][k]; a[c][k] = a[p][k]; a[p][k] = t; }
         double d = a[c][c];
-        for (int k = 0; k < 18; ++k) a[c][k] /= d;
-        for (int r = 0; r < 9; ++r) {
+        for (int k = 0; k < 2 * n; ++k) a[c][k] /= d;
+        for (int r = 0; r < n; ++r) {
             if (r == c) continue;
             double m = a[r][c];
             if (m != 0.0)
-                for (int k = 0; k < 18; ++k) a[r][k] -= m * a[c][k];
+                for (int k = 0; k < 2 * n; ++k) a[r][k] -= m * a[c][k];
         }
     }
-    for (int r = 0; r < 9; ++r)
-        for (int c = 0; c < 9; ++c) MI[r][c] = a[r][c + 9];
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) out[r * n + c] = a[r][c + n];
+}
+
+/* M^-1 of both lattices */
+static void build_minv(void) {
+    if (mi_ready) return;
+    gauss_jordan(9, &MM[0][0], &MI[0][0]);
+    gauss_jordan(5, &MM5[0][0], &MI5[0][0]);
     mi_ready = 1;
 }
+
+/* weight w_i of the q-velocity scalar lattice (q = 9 or 5, the first five
+ * velocities of Eq. 15) */
+static double wq_s(int q, int i) { return q == 5 ? WQ5[i] : WQ[i]; }
 
 static void mat_vec(const double A[9][9], const double* v, double* out) {
     for (int r = 0; r < 9; ++r) {
@@ -122,6 +149,7 @@ typedef struct {
     int32_t N_phi, N_U, N_T, N_F;
     int32_t tip_cx, tip_cy;
     int32_t T_ymin_dirichlet;  /* 1: T = T_ymin on the wall below row 0 */
+    int32_t q_scalar;          /* velocities of the phi, U, T lattices: 9 (0 reads as 9) or 5 */
     double dt_base;
     double W0, tau0, eps, lam;
     double Mc, k, DL, DS;
@@ -147,6 +175,8 @@ typedef struct {
 } orc_sim;
 
 enum { F_PHI = 0, F_U = 1, F_T = 2, F_F = 3 };
+
+static int qs(const orc_params* p) { return p->q_scalar == 5 ? 5 : 9; }
 
 /* ------------------------------------------------------------------ */
 /* Neighbour addressing                                                */
@@ -247,20 +277,37 @@ void orc_relaxation_times(const orc_params* p, double phi, double* out) {
 /* ------------------------------------------------------------------ */
 /* Equilibria (exported for the equilibrium-moment pins)                */
 /* ------------------------------------------------------------------ */
-void orc_feq_scalar(double chi, double ux, double uy, double c, double* feq) {   /* Eq. 19 */
-    for (int i = 0; i < 9; ++i) feq[i] = WQ[i] * chi * (1.0 + 3.0 * (EX[i] * ux + EY[i] * uy) / c);
+/* Eqs. 19-22 on the q-velocity scalar lattice; on D2Q5 the equilibrium
+ * moments are those of the same equilibrium, (chi, chi u_x/c, chi u_y/c,
+ * -2/3 chi, 0), resp. (phi, v_x/c, v_y/c, -2/3 phi, 0). */
+void orc_feq_scalar_q(int q, double chi, double ux, double uy, double c, double* feq) {   /* Eq. 19 */
+    for (int i = 0; i < q; ++i) feq[i] = wq_s(q, i) * chi * (1.0 + 3.0 * (EX[i] * ux + EY[i] * uy) / c);
 }
-void orc_meq_scalar(double chi, double ux, double uy, double c, double* m) {     /* Eq. 20 */
+void orc_meq_scalar_q(int q, double chi, double ux, double uy, double c, double* m) {     /* Eq. 20 */
+    if (q == 5) {
+        double v[5] = {chi, ux * chi / c, uy * chi / c, -2.0 / 3.0 * chi, 0.0};
+        memcpy(m, v, sizeof v);
+        return;
+    }
     double v[9] = {chi, -2.0 * chi, chi, ux * chi / c, -ux * chi / c, uy * chi / c, -uy * chi / c, 0.0, 0.0};
     memcpy(m, v, sizeof v);
 }
-void orc_feq_phase(double phi, double vx, double vy, double c, double* feq) {   /* Eq. 21 */
-    for (int i = 0; i < 9; ++i) feq[i] = WQ[i] * (phi + 3.0 * (EX[i] * vx + EY[i] * vy) / c);
+void orc_feq_phase_q(int q, double phi, double vx, double vy, double c, double* feq) {   /* Eq. 21 */
+    for (int i = 0; i < q; ++i) feq[i] = wq_s(q, i) * (phi + 3.0 * (EX[i] * vx + EY[i] * vy) / c);
 }
-void orc_meq_phase(double phi, double vx, double vy, double c, double* m) {      /* Eq. 22 */
+void orc_meq_phase_q(int q, double phi, double vx, double vy, double c, double* m) {      /* Eq. 22 */
+    if (q == 5) {
+        double v[5] = {phi, vx / c, vy / c, -2.0 / 3.0 * phi, 0.0};
+        memcpy(m, v, sizeof v);
+        return;
+    }
     double v[9] = {phi, -2.0 * phi, phi, vx / c, -vx / c, vy / c, -vy / c, 0.0, 0.0};
     memcpy(m, v, sizeof v);
 }
+void orc_feq_scalar(double chi, double ux, double uy, double c, double* feq) { orc_feq_scalar_q(9, chi, ux, uy, c, feq); }
+void orc_meq_scalar(double chi, double ux, double uy, double c, double* m) { orc_meq_scalar_q(9, chi, ux, uy, c, m); }
+void orc_feq_phase(double phi, double vx, double vy, double c, double* feq) { orc_feq_phase_q(9, phi, vx, vy, c, feq); }
+void orc_meq_phase(double phi, double vx, double vy, double c, double* m) { orc_meq_phase_q(9, phi, vx, vy, c, m); }
 void orc_feq_flow(double rho, double ux, double uy, double c, double* feq) {     /* Eq. 28 */
     double u2 = ux * ux + uy * uy;
     for (int i = 0; i < 9; ++i) {
@@ -293,17 +340,42 @@ void orc_matrices(double* M81, double* Minv81, int* ex, int* ey, double* w) {
         for (int c = 0; c < 9; ++c) { M81[r * 9 + c] = MM[r][c]; Minv81[r * 9 + c] = MI[r][c]; }
     for (int i = 0; i < 9; ++i) { ex[i] = EX[i]; ey[i] = EY[i]; w[i] = WQ[i]; }
 }
-
-/* Generic scalar collision of Eq. 14 with S of Eq. 23 (literal products):
- * f* = f - M^-1 S (M f - m_eq) + dt w_i Q. Exported for the closed-form pin. */
-void orc_collide_scalar(const double* f, const double* meq, double tau, double dtQ, double* fpost) {
+void orc_matrices5(double* M25, double* Minv25, double* w) {
     build_minv();
+    for (int r = 0; r < 5; ++r)
+        for (int c = 0; c < 5; ++c) { M25[r * 5 + c] = MM5[r][c]; Minv25[r * 5 + c] = MI5[r][c]; }
+    for (int i = 0; i < 5; ++i) w[i] = WQ5[i];
+}
+
+/* Scalar collision of Eq. 14 with S of Eq. 23 (literal products):
+ * f* = f - M^-1 S (M f - m_eq) + dt w_i Q, on the q-velocity lattice (on
+ * D2Q5 S = diag(1, 1/tau, 1/tau, 1, 1)). Exported for the closed-form pins. */
+void orc_collide_scalar_q(int q, const double* f, const double* meq, double tau, double dtQ, double* fpost) {
+    build_minv();
+    if (q == 5) {
+        double m[5], d[5];
+        const double S[5] = {1, 1.0 / tau, 1.0 / tau, 1, 1};
+        for (int r = 0; r < 5; ++r) {
+            m[r] = 0.0;
+            for (int c = 0; c < 5; ++c) m[r] += MM5[r][c] * f[c];
+            d[r] = S[r] * (m[r] - meq[r]);
+        }
+        for (int i = 0; i < 5; ++i) {
+            double corr = 0.0;
+            for (int c = 0; c < 5; ++c) corr += MI5[i][c] * d[c];
+            fpost[i] = f[i] - corr + dtQ * WQ5[i];
+        }
+        return;
+    }
     double m[9], d[9], corr[9];
     mat_vec(MM, f, m);
     double S[9] = {1, 1, 1, 1.0 / tau, 1, 1.0 / tau, 1, 1, 1};
     for (int k = 0; k < 9; ++k) d[k] = S[k] * (m[k] - meq[k]);
     mat_vec(MI, d, corr);
     for (int i = 0; i < 9; ++i) fpost[i] = f[i] - corr[i] + dtQ * WQ[i];
+}
+void orc_collide_scalar(const double* f, const double* meq, double tau, double dtQ, double* fpost) {
+    orc_collide_scalar_q(9, f, meq, tau, dtQ, fpost);
 }
 
 /* Flow collision of Eq. 14 with S of Eq. 31 and Guo forcing (Eq. 30). */
@@ -369,19 +441,21 @@ void orc_set_fields(orc_sim* s, const double* phi, const double* U, const double
     for (int b = 0; b < 4; ++b) s->cur[b] = 0;
     double cphi = 1.0 / (p->N_phi * p->dt_base), cU = 1.0 / (p->N_U * p->dt_base);
     double cT = 1.0 / (p->N_T * p->dt_base), cF = 1.0 / (p->N_F * p->dt_base);
+    const int q = qs(p);
+    for (int fld = 0; fld < 3; ++fld) memset(s->f[fld][0], 0, 9 * (size_t)nn * 8);
     for (int y = 0; y < p->ny; ++y)
         for (int x = 0; x < p->nx; ++x) {
             int n = y * p->nx + x;
             double feq[9], gx, gy, as, Nx, Ny;
             grad_iso(p, s->phi, x, y, &gx, &gy);
             orc_aniso(gx, gy, p->eps, &as, &Nx, &Ny);
-            orc_feq_phase(phi[n], -p->W0 * p->W0 * Nx / p->tau0, -p->W0 * p->W0 * Ny / p->tau0, cphi, feq);
-            for (int i = 0; i < 9; ++i) s->f[F_PHI][0][i * nn + n] = feq[i];
+            orc_feq_phase_q(q, phi[n], -p->W0 * p->W0 * Nx / p->tau0, -p->W0 * p->W0 * Ny / p->tau0, cphi, feq);
+            for (int i = 0; i < q; ++i) s->f[F_PHI][0][i * nn + n] = feq[i];
             double vx = p->has_flow ? ux[n] : 0.0, vy = p->has_flow ? uy[n] : 0.0;
-            orc_feq_scalar(U[n], vx, vy, cU, feq);
-            for (int i = 0; i < 9; ++i) s->f[F_U][0][i * nn + n] = feq[i];
-            orc_feq_scalar(T[n], vx, vy, cT, feq);
-            for (int i = 0; i < 9; ++i) s->f[F_T][0][i * nn + n] = feq[i];
+            orc_feq_scalar_q(q, U[n], vx, vy, cU, feq);
+            for (int i = 0; i < q; ++i) s->f[F_U][0][i * nn + n] = feq[i];
+            orc_feq_scalar_q(q, T[n], vx, vy, cT, feq);
+            for (int i = 0; i < q; ++i) s->f[F_T][0][i * nn + n] = feq[i];
             orc_feq_flow(rho[n], ux[n], uy[n], cF, feq);
             for (int i = 0; i < 9; ++i) s->f[F_F][0][i * nn + n] = feq[i];
         }
@@ -401,6 +475,7 @@ static void phase_step(orc_sim* s, double t) {
     double dt = p->N_phi * p->dt_base, c = 1.0 / dt;
     double* f = s->f[F_PHI][s->cur[F_PHI]];
     double* fn = s->f[F_PHI][1 - s->cur[F_PHI]];
+    const int q = qs(p);
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < p->ny; ++y)
         for (int x = 0; x < p->nx; ++x) {
@@ -416,10 +491,10 @@ static void phase_step(orc_sim* s, double t) {
             double one = 1.0 - ph * ph;
             double Q = ph * one - p->lam * (p->Mc * Ustar + th) * one * one;          /* Eq. 4 */
             double fl[9], meq[9], fp[9];
-            for (int i = 0; i < 9; ++i) fl[i] = f[i * nn + n];
-            orc_meq_phase(ph, vnx, vny, c, meq);
-            orc_collide_scalar(fl, meq, tau, dt * Q / p->tau0, fp);
-            for (int i = 0; i < 9; ++i) s->post[i * nn + n] = fp[i];
+            for (int i = 0; i < q; ++i) fl[i] = f[i * nn + n];
+            orc_meq_phase_q(q, ph, vnx, vny, c, meq);
+            orc_collide_scalar_q(q, fl, meq, tau, dt * Q / p->tau0, fp);
+            for (int i = 0; i < q; ++i) s->post[i * nn + n] = fp[i];
             s->as2[n] = as * as;
         }
 #pragma omp parallel for schedule(static)
@@ -427,7 +502,7 @@ static void phase_step(orc_sim* s, double t) {
         for (int x = 0; x < p->nx; ++x) {
             int n = y * p->nx + x;
             double a2 = s->as2[n], sum = 0.0;
-            for (int i = 0; i < 9; ++i) {
+            for (int i = 0; i < q; ++i) {
                 int src = scalar_src(p, x, y, i);
                 double inc = (src < 0) ? s->post[opposite(i) * nn + n] : s->post[i * nn + src];
                 double v = (inc - (1.0 - a2) * f[i * nn + n]) / a2;                /* Eq. 26 */
@@ -490,13 +565,14 @@ static void pc_transfer(orc_sim* s) {
         if (smax > s->J_U) s->J_U = smax;
         double* fu = s->f[F_U][s->cur[F_U]];
         double* ft = s->f[F_T][s->cur[F_T]];
+        const int q = qs(p);
         for (int n = 0; n < nn; ++n) {
             if (p->has_U) {
-                for (int i = 0; i < 9; ++i) fu[i * nn + n] += WQ[i] * s->dU[n];
+                for (int i = 0; i < q; ++i) fu[i * nn + n] += wq_s(q, i) * s->dU[n];
                 s->U[n] += s->dU[n];
             }
             if (p->has_T) {
-                for (int i = 0; i < 9; ++i) ft[i * nn + n] += WQ[i] * s->dT[n];
+                for (int i = 0; i < q; ++i) ft[i * nn + n] += wq_s(q, i) * s->dT[n];
                 s->T[n] += s->dT[n];
             }
         }
@@ -515,14 +591,14 @@ static void inject_accumulated(orc_sim* s, int fld) {
     double* acc = (fld == F_U) ? s->accU : s->accT;
     double* mac = (fld == F_U) ? s->U : s->T;
     double jmax = 0.0;
+    const int q = qs(p);
     for (int n = 0; n < nn; ++n) {
-        for (int i = 0; i < 9; ++i) f[i * nn + n] += WQ[i] * acc[n];
+        for (int i = 0; i < q; ++i) f[i * nn + n] += wq_s(q, i) * acc[n];
         mac[n] += acc[n];
         if (fld == F_U && fabs(acc[n]) > jmax) jmax = fabs(acc[n]);
         acc[n] = 0.0;
     }
     if (fld == F_U && jmax > s->J_U) s->J_U = jmax;
-    (void)p;
 }
 
 /* Concentration / temperature update: Eqs. 7-8 / 10-12 (tr parts), 14, 19-20,
@@ -536,13 +612,14 @@ static void scalar_step(orc_sim* s, int fld) {
     double* f = s->f[fld][s->cur[fld]];
     double* fn = s->f[fld][1 - s->cur[fld]];
     double* mac = (fld == F_U) ? s->U : s->T;
+    const int q = qs(p);
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < p->ny; ++y)
         for (int x = 0; x < p->nx; ++x) {
             int n = y * p->nx + x;
             double fl[9], feq[9], meq[9], fp[9];
             double chi = 0.0;
-            for (int i = 0; i < 9; ++i) { fl[i] = f[i * nn + n]; chi += fl[i]; }   /* Eq. 18 */
+            for (int i = 0; i < q; ++i) { fl[i] = f[i * nn + n]; chi += fl[i]; }   /* Eq. 18 */
             double ph = s->phi[n];
             double vx = p->has_flow ? s->ux[n] : 0.0, vy = p->has_flow ? s->uy[n] : 0.0;
             double D, coef;
@@ -555,23 +632,23 @@ static void scalar_step(orc_sim* s, int fld) {
                 coef = (p->rhoCpS - p->rhoCpL) / (2.0 * rc) * D;                     /* Eq. 12, tr */
             }
             double tau = 3.0 * dt * D + 0.5;                                          /* Eq. 24 */
-            orc_feq_scalar(chi, vx, vy, c, feq);
+            orc_feq_scalar_q(q, chi, vx, vy, c, feq);
             double sx = 0.0, sy = 0.0;
-            for (int i = 1; i < 9; ++i) { sx += (fl[i] - feq[i]) * EX[i]; sy += (fl[i] - feq[i]) * EY[i]; }
+            for (int i = 1; i < q; ++i) { sx += (fl[i] - feq[i]) * EX[i]; sy += (fl[i] - feq[i]) * EY[i]; }
             double gcx = -3.0 / tau * sx, gcy = -3.0 / tau * sy;                      /* Eq. 40 */
             double gpx, gpy;
             grad_iso(p, s->phi, x, y, &gpx, &gpy);
             double Q = coef * (gcx * gpx + gcy * gpy);
-            orc_meq_scalar(chi, vx, vy, c, meq);
-            orc_collide_scalar(fl, meq, tau, dt * Q, fp);
-            for (int i = 0; i < 9; ++i) s->post[i * nn + n] = fp[i];
+            orc_meq_scalar_q(q, chi, vx, vy, c, meq);
+            orc_collide_scalar_q(q, fl, meq, tau, dt * Q, fp);
+            for (int i = 0; i < q; ++i) s->post[i * nn + n] = fp[i];
         }
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < p->ny; ++y)
         for (int x = 0; x < p->nx; ++x) {
             int n = y * p->nx + x;
             double sum = 0.0;
-            for (int i = 0; i < 9; ++i) {
+            for (int i = 0; i < q; ++i) {
                 int src = scalar_src(p, x, y, i);
                 double v;
                 if (src >= 0) v = s->post[i * nn + src];                               /* Eq. 25 */

@@ -519,3 +519,115 @@ def test_dirichlet_wall_conduction_erf(N_T, alpha):
     y = np.arange(ny)
     exact = Tb + (T0 - Tb) * erf((y + 0.5) / (2.0 * math.sqrt(alpha * steps)))
     assert np.abs(T - exact[:, None])[: ny // 2].max() < 2e-3 * (T0 - Tb)
+
+
+# ---------------------------------------------------------------------------
+# Five-velocity option of the scalar lattices (D2Q5 for phi, U, T; flow D2Q9)
+# ---------------------------------------------------------------------------
+E5 = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1]])
+
+
+def test_d2q5_basis_equilibria_and_collision_closed_form():
+    """Moment basis (1, e_x, e_y, -4 + 5|e|^2, e_x^2 - e_y^2) is orthogonal
+    with M M^T = diag(5, 2, 2, 20, 4); the equilibria of Eqs. 19 and 21 on the
+    five velocities (weights 1/3, 1/6) have the moments the oracle relaxes to;
+    and the literal product f - M^-1 S (M f - m_eq) + dt w_i Q with
+    S = diag(1, 1/tau, 1/tau, 1, 1) equals the closed form
+    w_i A + 3 w_i e_i.b + (1 - 1/tau) e_i.(j - b)/2 (A = chi + dt Q, b the
+    first moment of f_eq, j that of f): the form the CUDA kernels use."""
+    M, Mi, w = oracle.matrices5()
+    assert np.array_equal(M @ M.T, np.diag([5.0, 2.0, 2.0, 20.0, 4.0]))
+    assert np.abs(M @ Mi - np.eye(5)).max() < 1e-15
+    assert np.allclose(w, [1 / 3, 1 / 6, 1 / 6, 1 / 6, 1 / 6], rtol=0, atol=1e-16)
+    rng = np.random.default_rng(7)
+    for kind in ("scalar", "phase"):
+        a, ux, uy, c = 0.7, 0.013, -0.021, 2.0
+        f, m = oracle.equilibrium_q(5, kind, a, ux, uy, c)
+        assert np.abs(M @ f - m).max() < 1e-15
+        assert abs(f.sum() - a) < 1e-15
+        b = f @ E5
+        exp_b = (a * np.array([ux, uy]) if kind == "scalar" else np.array([ux, uy])) / c
+        assert np.abs(b - exp_b).max() < 1e-16
+    for _ in range(5):
+        fin = 0.2 + 0.05 * rng.standard_normal(5)
+        chi, tau, dtQ = fin.sum(), 0.5 + rng.random() * 2, 0.01 * rng.standard_normal()
+        feq, meq = oracle.equilibrium_q(5, "scalar", chi, 0.01, -0.02, 1.0)
+        lit = oracle.collide_scalar_q(5, fin, meq, tau, dtQ)
+        A, b, j = chi + dtQ, feq @ E5, fin @ E5
+        closed = w * A + 3 * w * (E5 @ b) + (1 - 1 / tau) * (E5 @ (j - b)) / 2
+        assert np.abs(lit - closed).max() < 1e-15
+
+
+@pytest.mark.parametrize("field", ["U", "T"])
+@pytest.mark.parametrize("N,tol", [(1, 1e-3), (2, 5e-3)])
+def test_d2q5_gaussian_pulse_decay(field, N, tol):
+    """Pure diffusion on the five-velocity lattice: c_s^2 = 1/3 as on D2Q9, so
+    D = (tau - 1/2)/(3 dt) (Eq. 24) and the pulse decays as
+    A s0^2/(s0^2 + 2Dt) exp(-r^2/(2(s0^2 + 2Dt)))."""
+    n, s0, D, steps = 128, 5.0, 1.0 / 6.0, 400
+    if field == "U":
+        p = W.Params(nx=n, ny=n, has_U=True, bc_scalar_x=0, bc_scalar_y=0, N_U=N, DL=D, DS=D,
+                     k=0.15, W0=1, tau0=1, q_scalar=5)
+    else:
+        p = W.Params(nx=n, ny=n, has_T=True, bc_scalar_x=0, bc_scalar_y=0, N_T=N, kappaS=D,
+                     kappaL=D, W0=1, tau0=1, q_scalar=5)
+    f = W.base_fields(p, -np.ones((n, n)))
+    x, y = np.meshgrid(np.arange(n) - n / 2, np.arange(n) - n / 2)
+    r2 = x * x + y * y
+    f[field] = 0.1 * np.exp(-r2 / (2 * s0 * s0))
+    o = oracle.Oracle(p, f)
+    o.advance(steps)
+    s2 = s0 * s0 + 2 * D * steps
+    ana = 0.1 * s0 * s0 / s2 * np.exp(-r2 / (2 * s2))
+    got = o.get(field)
+    assert np.linalg.norm(got - ana) / np.linalg.norm(ana) < tol
+    assert abs(got.sum() - ana.sum()) / ana.sum() < 1e-3
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.05])
+def test_d2q5_planar_front_velocity(eps):
+    """The travelling front of Eq. 1 on the five-velocity phase lattice:
+    v = (4 sqrt 2 / 5) |lambda theta| W0 / (a_s tau0) to first order, as on
+    D2Q9 (the source, tau_phi and Eq. 26 do not depend on the velocity set)."""
+    W0, tau0, lt, n = 2.0, 12.0, -0.02, 256
+    p = W.Params(nx=n, ny=4, frozen_T=True, bc_scalar_x=1, bc_scalar_y=0, W0=W0, tau0=tau0,
+                 eps=eps, lam=1.0, theta_c=lt, q_scalar=5)
+    x = np.arange(n) + 0.0
+    phi = np.tile(-np.tanh((x - 60) / (math.sqrt(2) * W0 * (1 + eps))), (4, 1))
+    o = oracle.Oracle(p, W.base_fields(p, phi))
+    o.advance(1000)
+    a = _front_position(o.get("phi")[0])
+    o.advance(3000)
+    b = _front_position(o.get("phi")[0])
+    va = 4 * math.sqrt(2) / 5 * abs(lt) * W0 / (tau0 * (1 + eps))
+    assert abs((b - a) / 3000 / va - 1) < 0.03
+
+
+@pytest.mark.parametrize("bc", [W.BC_WALL, W.BC_PERIODIC])
+def test_d2q5_solute_balance_exact_over_phase_step(bc):
+    """The transfer (Eqs. 36-39) is lattice-independent apart from the
+    injection weights, which sum to one on D2Q5 too: sum C/C_inf is unchanged
+    by a phase update plus its transfer."""
+    wl = W.thermosolutal_convection(n=48, R=6.0)
+    p = wl.params
+    p.bc_scalar_x = p.bc_scalar_y = bc
+    p.eps, p.q_scalar = 0.05, 5
+    o = oracle.Oracle(p, wl.fields)
+    o.advance(60)
+    c0 = o.get("C").sum()
+    o.stage(0)
+    assert abs(o.get("dU")).max() > 1e-6
+    assert abs(o.get("C").sum() - c0) / c0 < 1e-13
+
+
+def test_d2q5_fourfold_symmetry_thermal_dendrite():
+    """The five velocities are invariant under the mirrors about the axes and
+    the diagonal, so a centred seed stays four-fold symmetric (FP64)."""
+    wl = W.thermal_free_dendrite(n=96)
+    wl.params.q_scalar = 5
+    o = oracle.Oracle(wl.params, wl.fields)
+    o.advance(400)
+    s = np.roll(np.roll(o.get("phi"), -48, 0), -48, 1)
+    assert np.abs(s[:, (-np.arange(96)) % 96] - s).max() < 1e-10
+    assert np.abs(s[(-np.arange(96)) % 96, :] - s).max() < 1e-10
+    assert np.abs(s.T - s).max() < 1e-10

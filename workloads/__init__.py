@@ -124,6 +124,8 @@ class Params:
     # bottom wall held at T = T_ymin (Sec. 4.4) instead of zero flux for T
     T_ymin_dirichlet: bool = False
     T_ymin: float = 0.0
+    # velocities of the phi, U, T lattices: 9 (the paper's D2Q9) or 5 (D2Q5)
+    q_scalar: int = 9
 
     def as_dict(self) -> Dict:
         return dict(self.__dict__)
