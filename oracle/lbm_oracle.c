@@ -653,7 +653,7 @@ static void scalar_step(orc_sim* s, int fld) {
                 double v;
                 if (src >= 0) v = s->post[i * nn + src];                               /* Eq. 25 */
                 else if (fld == F_T && p->T_ymin_dirichlet && y - EY[i] < 0)
-                    v = -s->post[opposite(i) * nn + n] + 2.0 * WQ[i] * p->T_ymin;       /* R-dirichlet */
+                    v = -s->post[opposite(i) * nn + n] + 2.0 * wq_s(q, i) * p->T_ymin;  /* R-dirichlet */
                 else v = s->post[opposite(i) * nn + n];                                 /* R-bb */
                 fn[i * nn + n] = v;
                 sum += v;

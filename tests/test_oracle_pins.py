@@ -499,20 +499,23 @@ def test_update_is_local_within_six_nodes_per_base_step(steps):
         o.close()
 
 
+@pytest.mark.parametrize("q", [9, 5])
 @pytest.mark.parametrize("N_T,alpha", [(1, 0.1), (2, 0.1), (1, 0.026)])
-def test_dirichlet_wall_conduction_erf(N_T, alpha):
+def test_dirichlet_wall_conduction_erf(N_T, alpha, q):
     """A bottom wall held at T_b (Sec. 4.4) conducting into a uniform liquid
     (phi = -1, no phase change, no flow): the semi-infinite solution
     T = T_b + (T0 - T_b) erf((y + 1/2) / (2 sqrt(alpha t))) with the wall half
     a link below row 0.  alpha = 0.026 is Table 1's liquid diffusivity
     (tau = 0.578); N_T = 2 takes the same alpha on the coarse clock.  A wall
     displaced by half a link misses by 2.6-5 %, plain bounce-back never
-    reaches T_b."""
+    reaches T_b.  q = 5: the same on the D2Q5 temperature lattice, whose
+    anti-bounce-back carries its own weight (2 w_2 T_b with w_2 = 1/6); the
+    D2Q9 weight there would hold the wall at 2/3 of T_b."""
     from scipy.special import erf
     nx, ny, steps, T0, Tb = 4, 300, 1200, 0.5, -1.0
     p = W.Params(nx=nx, ny=ny, has_T=True, bc_scalar_x=W.BC_PERIODIC, bc_scalar_y=W.BC_WALL,
                  N_T=N_T, W0=1.0, tau0=1.0, kappaS=alpha, kappaL=alpha, rhoCpS=1.0, rhoCpL=1.0,
-                 T_ymin_dirichlet=True, T_ymin=Tb, tip_cx=2, tip_cy=ny // 2)
+                 T_ymin_dirichlet=True, T_ymin=Tb, tip_cx=2, tip_cy=ny // 2, q_scalar=q)
     o = oracle.Oracle(p, W.base_fields(p, np.full((ny, nx), -1.0), U0=0.0, T0=T0))
     o.advance(steps)
     T = o.get("T")
