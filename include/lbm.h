@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define LBM_PARAMS_VERSION 2u
+#define LBM_PARAMS_VERSION 3u
 
 typedef enum {
     LBM_OK = 0,
@@ -89,7 +89,16 @@ enum { LBM_COUPLING_INSTANTANEOUS = 0, LBM_COUPLING_ACCUMULATED = 1 };
  *   T_ymin_dirichlet, T_ymin: with T on and bc_scalar_y = WALL, the bottom
  *             wall holds T = T_ymin (Sec. 4.4, the cold bottom boundary kept at
  *             T_b) instead of zero flux, by anti-bounce-back at the half-way
- *             wall; phi and U keep zero flux there. */
+ *             wall; phi and U keep zero flux there.
+ *   q_scalar: velocities of the phi, U and T lattices.  0 or 9: D2Q9, the
+ *             paper's lattice for all four fields (Sec. 3.1, Eq. 15).  5:
+ *             D2Q5, the rest velocity and the four axis links of Eq. 15 with
+ *             weights 1/3, 1/6 (c_s^2 = 1/3, so Eq. 24 is unchanged),
+ *             moments (1, e_x, e_y, 5|e|^2 - 4, e_x^2 - e_y^2) and every
+ *             moment but the two fluxes relaxed at rate one, as Eq. 23 does
+ *             on D2Q9; the phase field then stores 4 population planes
+ *             instead of 8.  The flow stays D2Q9.  All members of an
+ *             ensemble share it (version 3). */
 typedef struct {
     uint32_t struct_version; /* = LBM_PARAMS_VERSION */
     int32_t nx, ny;          /* lattice size, >= 4 each */
@@ -101,7 +110,7 @@ typedef struct {
     int32_t N_phi, N_U, N_T, N_F; /* update factors, >= 1 */
     int32_t tip_cx, tip_cy;
     int32_t T_ymin_dirichlet;    /* 1: T = T_ymin on the bottom wall (version 2) */
-    int32_t reserved;
+    int32_t q_scalar;            /* 0 / 9: D2Q9 scalar lattices; 5: D2Q5 (version 3) */
     double dt_base;
     double W0, tau0, eps, lam;
     double Mc, k, DL, DS;

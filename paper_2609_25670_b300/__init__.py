@@ -17,7 +17,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblbm.so")
 
-PARAMS_VERSION = 2
+PARAMS_VERSION = 3
 BC_PERIODIC, BC_WALL, BC_INLET_OUTFLOW = 0, 1, 2
 FIELD_U, FIELD_T, FIELD_FROZEN_T, FIELD_FLOW = 1, 2, 4, 8
 PRECISIONS = {"f64": 0, "f32": 1, "f16dev": 2, "bf16dev": 3}
@@ -48,7 +48,7 @@ class lbm_params(C.Structure):
         ("bc_flow_y", C.c_int32), ("precision", C.c_uint32), ("coupling", C.c_uint32),
         ("N_phi", C.c_int32), ("N_U", C.c_int32), ("N_T", C.c_int32), ("N_F", C.c_int32),
         ("tip_cx", C.c_int32), ("tip_cy", C.c_int32), ("T_ymin_dirichlet", C.c_int32),
-        ("reserved", C.c_int32), ("dt_base", C.c_double),
+        ("q_scalar", C.c_int32), ("dt_base", C.c_double),
         ("W0", C.c_double), ("tau0", C.c_double), ("eps", C.c_double), ("lam", C.c_double),
         ("Mc", C.c_double), ("k", C.c_double), ("DL", C.c_double), ("DS", C.c_double),
         ("kappaS", C.c_double), ("kappaL", C.c_double), ("rhoCpS", C.c_double), ("rhoCpL", C.c_double),
@@ -149,6 +149,7 @@ def make_params(p, precision: str = "f32") -> lbm_params:
         setattr(s, nm, int(_get(p, nm, 1)))
     s.tip_cx, s.tip_cy = int(_get(p, "tip_cx", 0)), int(_get(p, "tip_cy", 0))
     s.T_ymin_dirichlet = 1 if _get(p, "T_ymin_dirichlet", False) else 0
+    s.q_scalar = int(_get(p, "q_scalar", 9))
     defaults = dict(dt_base=1.0, W0=1.0, tau0=1.0, eps=0.0, lam=0.0, Mc=0.0, k=1.0, DL=0.0, DS=0.0,
                     kappaS=0.0, kappaL=0.0, rhoCpS=1.0, rhoCpL=1.0, rhoL_Lh=1.0, T_shift=0.0, T_scale=1.0,
                     nu=0.1, u_in=0.0, Fbx=0.0, Fby=0.0, s_e=1.2, s_eps=1.4, s_q=1.2, theta_c=0.0,

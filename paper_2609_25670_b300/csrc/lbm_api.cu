@@ -117,6 +117,7 @@ struct TimedEvent {
 struct lbm_sim {
     std::vector<SimState> sims;
     uint32_t precision = LBM_PREC_F32;
+    int q = 9;                           // velocities of the phase, U and T lattices (9 or 5)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     lbm_allocator alloc{};
@@ -243,6 +244,7 @@ lbm_status validate(const lbm_params* p, std::string& why) {
     if (p->T_ymin_dirichlet && (!(p->fields & LBM_FIELD_T) || p->bc_scalar_y != LBM_BC_WALL))
         return bad("T_ymin_dirichlet needs the T field and bc_scalar_y = WALL");
     if (p->precision > LBM_PREC_BF16_DEV) return bad("unknown precision");
+    if (p->q_scalar != 0 && p->q_scalar != 9 && p->q_scalar != 5) return bad("q_scalar must be 0, 9 or 5");
     if (p->coupling > LBM_COUPLING_ACCUMULATED) return bad("unknown coupling");
     if (p->N_phi < 1 || p->N_U < 1 || p->N_T < 1 || p->N_F < 1) return bad("update factors must be >= 1");
     if (!(p->dt_base > 0.0)) return bad("dt_base must be > 0");
@@ -500,17 +502,17 @@ void record_job(lbm_sim* h, SimState& s, int kind, const long long* clock, long 
     }
 }
 
-template <typename R, typename ST, bool DEV>
+template <typename R, typename ST, bool DEV, int Q>
 void launch_batch(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, int tiles) {
     LaunchScope ls(h, kind);
     const dim3 g(tiles);
     switch (kind) {
         case LBM_K_PHASE:
             if (tysel > VS)
-                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_phase_vs_batch<R, ST, DEV, HV>, g, dim3(32, PVW),
-                                                     (size_t)PVSmem<R>::BYTES, (const PhaseJob<R, ST>*)jobs, njobs)))
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_phase_vs_batch<R, ST, DEV, HV, Q>, g, dim3(32, PVW),
+                                                     (size_t)PVSmem<R, Q>::BYTES, (const PhaseJob<R, ST>*)jobs, njobs)))
             else
-                LBM_TY_SWITCH(tysel, (launch_ex(h, k_phase_batch<R, ST, DEV, TYV>, g, dim3(TX, TYV),
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_phase_batch<R, ST, DEV, TYV, Q>, g, dim3(TX, TYV),
                                                 (const PhaseJob<R, ST>*)jobs, njobs)))
             break;
         case LBM_K_TRANSFER:
@@ -523,26 +525,26 @@ void launch_batch(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, 
             break;
         case LBM_K_SCALAR_U:
             if (tysel > VS)
-                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs_batch<R, ST, DEV, HV, 0>, g, dim3(32 * VNW),
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs_batch<R, ST, DEV, HV, 0, Q>, g, dim3(32 * VNW),
                                                      (size_t)VNW * VSRing<R>::BYTES, (const ScalarJob<R, ST>*)jobs,
                                                      njobs)))
             else if (tysel < 0)
-                LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip_batch<R, ST, DEV, HV, 0>, g, dim3(32 * NWS),
+                LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip_batch<R, ST, DEV, HV, 0, Q>, g, dim3(32 * NWS),
                                                    (const ScalarJob<R, ST>*)jobs, njobs)))
             else
-                LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar_batch<R, ST, DEV, TYV, 0>, g, dim3(TX, TYV),
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar_batch<R, ST, DEV, TYV, 0, Q>, g, dim3(TX, TYV),
                                                 (const ScalarJob<R, ST>*)jobs, njobs)))
             break;
         case LBM_K_SCALAR_T:
             if (tysel > VS)
-                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs_batch<R, ST, DEV, HV, 1>, g, dim3(32 * VNW),
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs_batch<R, ST, DEV, HV, 1, Q>, g, dim3(32 * VNW),
                                                      (size_t)VNW * VSRing<R>::BYTES, (const ScalarJob<R, ST>*)jobs,
                                                      njobs)))
             else if (tysel < 0)
-                LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip_batch<R, ST, DEV, HV, 1>, g, dim3(32 * NWS),
+                LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip_batch<R, ST, DEV, HV, 1, Q>, g, dim3(32 * NWS),
                                                    (const ScalarJob<R, ST>*)jobs, njobs)))
             else
-                LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar_batch<R, ST, DEV, TYV, 1>, g, dim3(TX, TYV),
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar_batch<R, ST, DEV, TYV, 1, Q>, g, dim3(TX, TYV),
                                                 (const ScalarJob<R, ST>*)jobs, njobs)))
             break;
         case LBM_K_FLOW:
@@ -554,7 +556,7 @@ void launch_batch(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, 
                                                 (const FlowJob<R, ST>*)jobs, njobs)))
             break;
         case LBM_K_TRANSPORT:
-            LBM_TY_SWITCH(tysel, (launch_ex_smem(h, k_transport_batch<R, ST, DEV, TYV>, g, dim3(TX, TYV),
+            LBM_TY_SWITCH(tysel, (launch_ex_smem(h, k_transport_batch<R, ST, DEV, TYV, Q>, g, dim3(TX, TYV),
                                                  sizeof(TransportSmem<R, TYV>), (const TransportJob<R, ST>*)jobs,
                                                  njobs)));
             break;
@@ -562,16 +564,21 @@ void launch_batch(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, 
     }
 }
 
-void launch_batch_any(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, int tiles) {
+template <int Q>
+void launch_batch_q(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, int tiles) {
     switch (h->precision) {
-        case LBM_PREC_F64: launch_batch<double, double, false>(h, kind, tysel, jobs, njobs, tiles); break;
-        case LBM_PREC_F32: launch_batch<float, float, false>(h, kind, tysel, jobs, njobs, tiles); break;
-        case LBM_PREC_F16_DEV: launch_batch<float, __half, true>(h, kind, tysel, jobs, njobs, tiles); break;
-        default: launch_batch<float, __nv_bfloat16, true>(h, kind, tysel, jobs, njobs, tiles); break;
+        case LBM_PREC_F64: launch_batch<double, double, false, Q>(h, kind, tysel, jobs, njobs, tiles); break;
+        case LBM_PREC_F32: launch_batch<float, float, false, Q>(h, kind, tysel, jobs, njobs, tiles); break;
+        case LBM_PREC_F16_DEV: launch_batch<float, __half, true, Q>(h, kind, tysel, jobs, njobs, tiles); break;
+        default: launch_batch<float, __nv_bfloat16, true, Q>(h, kind, tysel, jobs, njobs, tiles); break;
     }
 }
+void launch_batch_any(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, int tiles) {
+    if (h->q == 5) launch_batch_q<5>(h, kind, tysel, jobs, njobs, tiles);
+    else launch_batch_q<9>(h, kind, tysel, jobs, njobs, tiles);
+}
 
-template <typename R, typename ST, bool DEV>
+template <typename R, typename ST, bool DEV, int Q>
 void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* clock, long long off) {
     if (h->recording) {
         record_job<R, ST, DEV>(h, s, kind, clock, off);
@@ -589,12 +596,12 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
     switch (kind) {
         case LBM_K_PHASE:
             if (tysel > VS)
-                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_phase_vs<R, ST, DEV, HV>, grid_v(s, kind, tysel),
-                    dim3(32, PVW), (size_t)PVSmem<R>::BYTES, P, (const ST*)s.pops[FP][s.cur_pop[FP]],
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_phase_vs<R, ST, DEV, HV, Q>, grid_v(s, kind, tysel),
+                    dim3(32, PVW), (size_t)PVSmem<R, Q>::BYTES, P, (const ST*)s.pops[FP][s.cur_pop[FP]],
                     (ST*)s.pops[FP][1 - s.cur_pop[FP]], phi_now, (R*)s.phi[1 - s.cur_phi],
                     s.has_U ? (const R*)s.U[s.cur_U] : null_r, s.has_T ? (const R*)s.T[s.cur_T] : null_r, clock, off)))
             else
-                LBM_TY_SWITCH(tysel, (launch_ex(h, k_phase<R, ST, DEV, TYV>, grid_of<TYV>(s), dim3(TX, TYV),
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_phase<R, ST, DEV, TYV, Q>, grid_of<TYV>(s), dim3(TX, TYV),
                     P, (const ST*)s.pops[FP][s.cur_pop[FP]], (ST*)s.pops[FP][1 - s.cur_pop[FP]], phi_now,
                     (R*)s.phi[1 - s.cur_phi], s.has_U ? (const R*)s.U[s.cur_U] : null_r,
                     s.has_T ? (const R*)s.T[s.cur_T] : null_r, clock, off)))
@@ -625,27 +632,27 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
             if (tysel > VS) {
                 const size_t sm = (size_t)VNW * VSRing<R>::BYTES;
                 if (isU)
-                    LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs<R, ST, DEV, HV, 0>, grid_v(s, kind, tysel),
+                    LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs<R, ST, DEV, HV, 0, Q>, grid_v(s, kind, tysel),
                         dim3(32 * VNW), sm, P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc,
                         s.smax)))
                 else
-                    LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs<R, ST, DEV, HV, 1>, grid_v(s, kind, tysel),
+                    LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs<R, ST, DEV, HV, 1, Q>, grid_v(s, kind, tysel),
                         dim3(32 * VNW), sm, P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc,
                         s.smax)))
             } else if (tysel < 0) {
                 if (isU)
-                    LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip<R, ST, DEV, HV, 0>, grid_v(s, kind, tysel),
+                    LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip<R, ST, DEV, HV, 0, Q>, grid_v(s, kind, tysel),
                         dim3(32 * NWS), P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc,
                         s.smax)))
                 else
-                    LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip<R, ST, DEV, HV, 1>, grid_v(s, kind, tysel),
+                    LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip<R, ST, DEV, HV, 1, Q>, grid_v(s, kind, tysel),
                         dim3(32 * NWS), P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc,
                         s.smax)))
             } else if (isU) {
-                LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar<R, ST, DEV, TYV, 0>, grid_of<TYV>(s), dim3(TX, TYV),
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar<R, ST, DEV, TYV, 0, Q>, grid_of<TYV>(s), dim3(TX, TYV),
                     P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc, s.smax)));
             } else {
-                LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar<R, ST, DEV, TYV, 1>, grid_of<TYV>(s), dim3(TX, TYV),
+                LBM_TY_SWITCH(tysel, (launch_ex(h, k_scalar<R, ST, DEV, TYV, 1, Q>, grid_of<TYV>(s), dim3(TX, TYV),
                     P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc, s.smax)));
             }
             break;
@@ -667,13 +674,18 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
     }
 }
 
-void launch_any(lbm_sim* h, SimState& s, int kind, int tysel, const long long* clock, long long off) {
+template <int Q>
+void launch_q(lbm_sim* h, SimState& s, int kind, int tysel, const long long* clock, long long off) {
     switch (h->precision) {
-        case LBM_PREC_F64: launch_kind<double, double, false>(h, s, kind, tysel, clock, off); break;
-        case LBM_PREC_F32: launch_kind<float, float, false>(h, s, kind, tysel, clock, off); break;
-        case LBM_PREC_F16_DEV: launch_kind<float, __half, true>(h, s, kind, tysel, clock, off); break;
-        default: launch_kind<float, __nv_bfloat16, true>(h, s, kind, tysel, clock, off); break;
+        case LBM_PREC_F64: launch_kind<double, double, false, Q>(h, s, kind, tysel, clock, off); break;
+        case LBM_PREC_F32: launch_kind<float, float, false, Q>(h, s, kind, tysel, clock, off); break;
+        case LBM_PREC_F16_DEV: launch_kind<float, __half, true, Q>(h, s, kind, tysel, clock, off); break;
+        default: launch_kind<float, __nv_bfloat16, true, Q>(h, s, kind, tysel, clock, off); break;
     }
+}
+void launch_any(lbm_sim* h, SimState& s, int kind, int tysel, const long long* clock, long long off) {
+    if (h->q == 5) launch_q<5>(h, s, kind, tysel, clock, off);
+    else launch_q<9>(h, s, kind, tysel, clock, off);
 }
 
 // The update sequence of one base step (Eq. 34 schedule, workflow of Fig. 1).
@@ -716,7 +728,13 @@ size_t transport_smem() { return sizeof(TransportSmem<R, TYV>); }
 template <typename R, typename ST, bool DEV>
 void launch_transport_jobs(lbm_sim* h, int tysel, const void* jobs, int njobs, int tiles) {
     LaunchScope ls(h, LBM_K_TRANSPORT);
-    LBM_TY_SWITCH(tysel, (launch_ex_smem(h, k_transport_batch<R, ST, DEV, TYV>, dim3(tiles), dim3(TX, TYV),
+    if (h->q == 5) {
+        LBM_TY_SWITCH(tysel, (launch_ex_smem(h, k_transport_batch<R, ST, DEV, TYV, 5>, dim3(tiles), dim3(TX, TYV),
+                                              transport_smem<R, ST, DEV, TYV>(),
+                                              (const TransportJob<R, ST>*)jobs, njobs)));
+        return;
+    }
+    LBM_TY_SWITCH(tysel, (launch_ex_smem(h, k_transport_batch<R, ST, DEV, TYV, 9>, dim3(tiles), dim3(TX, TYV),
                                           transport_smem<R, ST, DEV, TYV>(),
                                           (const TransportJob<R, ST>*)jobs, njobs)));
 }
@@ -1039,20 +1057,20 @@ lbm_status upload_and_init(lbm_sim* h, SimState& s, const double* src[6], int sr
         switch (h->precision) {
             case LBM_PREC_F64:
             case LBM_PREC_F32:
-                k_init<R, R, false><<<grd, blk, 0, h->stream>>>(P, (const R*)s.phi[0], (const R*)s.U[0], (const R*)s.T[0],
+                k_init<R, R, false><<<grd, blk, 0, h->stream>>>(P, h->q, (const R*)s.phi[0], (const R*)s.U[0], (const R*)s.T[0],
                                                                (const R*)s.ux[0], (const R*)s.uy[0], (const R*)s.rho[0],
                                                                (R*)s.pops[FP][0], (R*)s.pops[FU][0], (R*)s.pops[FT][0],
                                                                (R*)s.pops[FF][0]);
                 break;
             case LBM_PREC_F16_DEV:
                 k_init<float, __half, true><<<grd, blk, 0, h->stream>>>(
-                    make_kp<float>(s), (const float*)s.phi[0], (const float*)s.U[0], (const float*)s.T[0],
+                    make_kp<float>(s), h->q, (const float*)s.phi[0], (const float*)s.U[0], (const float*)s.T[0],
                     (const float*)s.ux[0], (const float*)s.uy[0], (const float*)s.rho[0], (__half*)s.pops[FP][0],
                     (__half*)s.pops[FU][0], (__half*)s.pops[FT][0], (__half*)s.pops[FF][0]);
                 break;
             default:
                 k_init<float, __nv_bfloat16, true><<<grd, blk, 0, h->stream>>>(
-                    make_kp<float>(s), (const float*)s.phi[0], (const float*)s.U[0], (const float*)s.T[0],
+                    make_kp<float>(s), h->q, (const float*)s.phi[0], (const float*)s.U[0], (const float*)s.T[0],
                     (const float*)s.ux[0], (const float*)s.uy[0], (const float*)s.rho[0], (__nv_bfloat16*)s.pops[FP][0],
                     (__nv_bfloat16*)s.pops[FU][0], (__nv_bfloat16*)s.pops[FT][0], (__nv_bfloat16*)s.pops[FF][0]);
         }
@@ -1181,9 +1199,12 @@ lbm_status lbm_create(const lbm_params* p, int32_t n_sims, const lbm_params* per
         lbm_status st = validate(&ps[i], why);
         if (st) return fail(nullptr, st, "sim %d: %s", i, why.c_str());
         if (ps[i].precision != p->precision) return fail(nullptr, LBM_E_INVALID_ARG, "sim %d: precision differs", i);
+        if ((ps[i].q_scalar == 5) != (p->q_scalar == 5))
+            return fail(nullptr, LBM_E_INVALID_ARG, "sim %d: q_scalar differs", i);
     }
     h = new lbm_sim();
     h->precision = p->precision;
+    h->q = p->q_scalar == 5 ? 5 : 9;
     if (a) { h->alloc = *a; h->has_alloc = true; }
     if (cuda_stream) h->stream = (cudaStream_t)cuda_stream;
     else {
@@ -1215,7 +1236,8 @@ lbm_status lbm_create(const lbm_params* p, int32_t n_sims, const lbm_params* per
         lbm_status st = LBM_OK;
         for (int f = 0; f < 4 && !st; ++f)
             for (int b = 0; b < 2 && !st; ++b)
-                if (present[f]) st = dev_alloc(h, (f == FU || f == FT ? 2 : 8) * s.nn * ss, &s.pops[f][b]);
+                if (present[f])
+                    st = dev_alloc(h, (f == FU || f == FT ? 2 : f == FP ? h->q - 1 : 8) * s.nn * ss, &s.pops[f][b]);
         for (int b = 0; b < 2 && !st; ++b) st = dev_alloc(h, s.nn * rs, &s.phi[b]);
         for (int b = 0; b < 2 && !st; ++b) if (s.has_U) st = dev_alloc(h, s.nn * rs, &s.U[b]);
         for (int b = 0; b < 2 && !st; ++b) if (s.has_T) st = dev_alloc(h, s.nn * rs, &s.T[b]);

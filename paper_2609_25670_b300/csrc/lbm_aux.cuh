@@ -7,12 +7,14 @@ namespace lbmk {
 
 // ---------------------------------------------------------------------------
 // Initial distributions f = f_eq of the macroscopic fields (Eqs. 19, 21, 28);
-// for U and T their first moments, the stored state of those fields
+// for U and T their first moments, the stored state of those fields.  q: the
+// velocities of the phase lattice (9, or 5 for D2Q5: populations 1..4 only).
 // ---------------------------------------------------------------------------
 template <typename R, typename ST, bool DEV>
-__global__ void k_init(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ Um, const R* __restrict__ Tm,
-                       const R* __restrict__ uxm, const R* __restrict__ uym, const R* __restrict__ rhom,
-                       ST* __restrict__ fphi, ST* __restrict__ fU, ST* __restrict__ fT, ST* __restrict__ fF) {
+__global__ void k_init(const KP<R> P, int q, const R* __restrict__ phi, const R* __restrict__ Um,
+                       const R* __restrict__ Tm, const R* __restrict__ uxm, const R* __restrict__ uym,
+                       const R* __restrict__ rhom, ST* __restrict__ fphi, ST* __restrict__ fU, ST* __restrict__ fT,
+                       ST* __restrict__ fF) {
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
     if (gx >= P.nx || gy >= P.ny) return;
     const size_t node = (size_t)gy * P.pitch + gx;
@@ -31,12 +33,13 @@ __global__ void k_init(const KP<R> P, const R* __restrict__ phi, const R* __rest
     if (P.has_flow) { vx = uxm[node]; vy = uym[node]; }
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
-        const R w = wq<R>(i), ex = (R)c_ex[i], ey = (R)c_ey[i];
+        if (i >= q) break;
+        const R w = q == 5 ? wqq<R, 5>(i) : wq<R>(i), ex = (R)c_ex[i], ey = (R)c_ey[i];
         const R dp = R(3) * w * (ex * bx + ey * by);                                   // Eq. 21 minus w_i phi
         fphi[(size_t)(i - 1) * P.plane + node] = Cvt<ST>::st(DEV ? dp : w * ph + dp);
     }
     // U, T: the first moment of f_eq of Eq. 19, sum_i e_i 3 w_i chi dt (e_i . u)
-    // = dt chi u (sum_i w_i e_i e_i = I / 3)
+    // = dt chi u (sum_i w_i e_i e_i = I / 3 on D2Q9 and on D2Q5)
     if (P.has_U) {
         const R U = Um[node];
         fU[node] = Cvt<ST>::st(P.dtU * U * vx);

@@ -26,6 +26,19 @@ template <typename R> __host__ __device__ constexpr R wq(int i) {
     return i == 0 ? Wt<R>::w0 : (i < 5 ? Wt<R>::w1 : Wt<R>::w2);
 }
 
+// Velocity set of the phase, U and T lattices: Q = 9 (D2Q9, the paper's
+// choice for all four fields, Sec. 3.1) or Q = 5 (D2Q5: the rest velocity
+// and the four axis links 1..4 of Eq. 15, weights 1/3 and 1/6, the same
+// c_s^2 = 1/3, so Eq. 24 ties tau to the diffusivity as on D2Q9).  On D2Q5
+// the populations 5..8 do not exist; the kernels treat them as zeros known
+// at compile time.
+template <typename R, int Q> __host__ __device__ constexpr R wqq(int i) {
+    return Q == 9 ? wq<R>(i) : (i == 0 ? R(1) / R(3) : (i < 5 ? R(1) / R(6) : R(0)));
+}
+// Factor of the first-moment columns of M^-1: e_i / 6 on D2Q9 (columns 3
+// and 5 of Eq. 16's inverse), e_i / 2 on D2Q5 (sum_i e_ix^2 = 2 there).
+template <typename R, int Q> __host__ __device__ constexpr R kneq() { return Q == 9 ? R(1) / R(6) : R(1) / R(2); }
+
 // Coefficients derived on the host in FP64, then rounded to R.
 template <typename R> struct KP {
     int nx, ny, pitch;
@@ -143,22 +156,25 @@ __device__ __forceinline__ void aniso(R gx, R gy, R eps, R& as, R& Nx, R& Ny) {
 }
 
 // f*_i = w_i A + 3 w_i (e_i . b) + (e_i . c): the scalar collision of Eq. 14
-// with S of Eq. 23 in closed form (columns 3 and 5 of M^-1 are e_x/6, e_y/6),
-// A = chi + dt Q, b = j_eq = first moment of f_eq, c = (1 - s) j_neq / 6.
-template <typename R, int HY, int HX>
+// with S of Eq. 23 in closed form (columns 3 and 5 of M^-1 are e_x/6, e_y/6;
+// on D2Q5 e_x/2, e_y/2), A = chi + dt Q, b = j_eq = first moment of f_eq,
+// c = (1 - s) j_neq kneq<Q>.  On D2Q5 only populations 0..4 are written.
+template <typename R, int HY, int HX, int Q = 9>
 __device__ __forceinline__ void put_scalar_post(R (*sp)[HY][HX], int ly, int lx, R A, R bx, R by, R cx, R cy) {
-    const R w1 = Wt<R>::w1, w2 = Wt<R>::w2;
+    const R w1 = wqq<R, Q>(1), w2 = Wt<R>::w2;
     const R a1 = w1 * A, a2 = w2 * A, b1x = R(3) * w1 * bx, b1y = R(3) * w1 * by;
     const R b2x = R(3) * w2 * bx, b2y = R(3) * w2 * by;
-    sp[0][ly][lx] = Wt<R>::w0 * A;
+    sp[0][ly][lx] = wqq<R, Q>(0) * A;
     sp[1][ly][lx] = a1 + b1x + cx;
     sp[2][ly][lx] = a1 + b1y + cy;
     sp[3][ly][lx] = a1 - b1x - cx;
     sp[4][ly][lx] = a1 - b1y - cy;
-    sp[5][ly][lx] = a2 + (b2x + b2y) + (cx + cy);
-    sp[6][ly][lx] = a2 + (b2y - b2x) + (cy - cx);
-    sp[7][ly][lx] = a2 - (b2x + b2y) - (cx + cy);
-    sp[8][ly][lx] = a2 + (b2x - b2y) + (cx - cy);
+    if constexpr (Q == 9) {
+        sp[5][ly][lx] = a2 + (b2x + b2y) + (cx + cy);
+        sp[6][ly][lx] = a2 + (b2y - b2x) + (cy - cx);
+        sp[7][ly][lx] = a2 - (b2x + b2y) - (cx + cy);
+        sp[8][ly][lx] = a2 + (b2x - b2y) + (cx - cy);
+    }
 }
 
 template <typename R> __device__ __forceinline__ R theta_frozen(const KP<R>& P, int y, R t) {

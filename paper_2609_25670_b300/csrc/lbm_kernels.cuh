@@ -9,9 +9,15 @@
 // its first barrier.  Tiles whose ghost ring lies inside the lattice take a
 // compile-time "interior" path without boundary maps or wall tests.
 //
+// Velocity sets: the flow is D2Q9; the phase, U and T lattices are D2Q9
+// (Q = 9, the paper's choice) or D2Q5 (Q = 5, rest velocity and axis links;
+// a template parameter of every phase, U, T and fused-transport kernel, with
+// the diagonal populations 5..8 compile-time zeros).
+//
 // Storage (per field, per ping-pong buffer), planes of `pitch * ny` elements
 // of type ST:
-//   phase, flow: populations 1..8; population 0 is never stored, it follows
+//   phase: populations 1..Q-1; flow: populations 1..8; population 0 is never
+//          stored, it follows
 //          from the node's zeroth moment, which the macroscopic arrays carry:
 //          phase f_0 = phi - sum_{i>0} f_i (Eq. 18), flow f_0 = rho -
 //          sum_{i>0} f_i (Eq. 27).
@@ -87,6 +93,12 @@ __device__ __forceinline__ void load8(const ST* __restrict__ f, int node, int pl
 #pragma unroll
     for (int i = 1; i < 9; ++i) v[i] = (R)Cvt<ST>::ld(f[node + (i - 1) * plane]);
 }
+// populations 1..Q-1 of a Q-velocity lattice; on D2Q5 populations 5..8 are zero
+template <typename R, typename ST, int Q>
+__device__ __forceinline__ void loadQ(const ST* __restrict__ f, int node, int plane, R* v) {
+#pragma unroll
+    for (int i = 1; i < 9; ++i) v[i] = i < Q ? (R)Cvt<ST>::ld(f[node + (i - 1) * plane]) : R(0);
+}
 template <typename R> __device__ __forceinline__ R mom_x(const R* v) { return v[1] - v[3] + v[5] - v[6] - v[7] + v[8]; }
 template <typename R> __device__ __forceinline__ R mom_y(const R* v) { return v[2] - v[4] + v[5] + v[6] - v[7] - v[8]; }
 
@@ -132,13 +144,13 @@ __device__ __forceinline__ Walls walls_of(int gx, int gy, int nx, int ny, int bc
 // ---------------------------------------------------------------------------
 // Phase-field update (Eqs. 2-4, 14, 21-24, 26, 18)
 // ---------------------------------------------------------------------------
-template <typename R, int TY> struct PhaseSmem {
+template <typename R, int TY, int Q = 9> struct PhaseSmem {
     R phi[TY + 4][36];
-    R post[9][TY + 2][34];
+    R post[Q][TY + 2][34];
 };
 
 // collision of the phase populations at halo position (lx, ly); returns a_s^2
-template <typename R, int TY>
+template <typename R, int TY, int Q>
 __device__ __forceinline__ R phase_collide(const KP<R>& P, const R (*sphi)[36], R (*sp)[TY + 2][34], int lx, int ly,
                                            int gy, R jx, R jy, R Us, R Tv, R tnow) {
     const R c = sphi[ly + 1][lx + 1];
@@ -152,15 +164,15 @@ __device__ __forceinline__ R phase_collide(const KP<R>& P, const R (*sphi)[36], 
     else if (P.frozen_T) th = theta_frozen(P, gy, tnow);
     else th = P.theta_c;
     const R one = R(1) - c * c;
-    const R Q = c * one - P.lam * (P.Mc * Us + th) * one * one;                   // Eq. 4
+    const R Qs = c * one - P.lam * (P.Mc * Us + th) * one * one;                  // Eq. 4
     const R bx = -P.dtp * P.W0sq_tau0 * Nx, by = -P.dtp * P.W0sq_tau0 * Ny;      // dt v_n (Eqs. 21-22)
-    const R k6 = (R(1) - s) * (R(1) / R(6));
-    put_scalar_post<R, TY + 2, 34>(sp, ly, lx, c + P.dtp * Q * P.inv_tau0, bx, by, k6 * (jx - bx), k6 * (jy - by));
+    const R k6 = (R(1) - s) * kneq<R, Q>();
+    put_scalar_post<R, TY + 2, 34, Q>(sp, ly, lx, c + P.dtp * Qs * P.inv_tau0, bx, by, k6 * (jx - bx), k6 * (jy - by));
     return a2;
 }
 
-template <typename R, typename ST, bool DEV, int TY, bool IN>
-__device__ __forceinline__ void phase_tile(PhaseSmem<R, TY>& sm, const KP<R>& P, const ST* __restrict__ fin,
+template <typename R, typename ST, bool DEV, int TY, bool IN, int Q>
+__device__ __forceinline__ void phase_tile(PhaseSmem<R, TY, Q>& sm, const KP<R>& P, const ST* __restrict__ fin,
                                            ST* __restrict__ fout, const R* __restrict__ phi, R* __restrict__ phin,
                                            const R* __restrict__ Um, const R* __restrict__ Tm, R tnow, int x0,
                                            int y0, Rect skip) {
@@ -183,20 +195,20 @@ __device__ __forceinline__ void phase_tile(PhaseSmem<R, TY>& sm, const KP<R>& P,
     R fa[9], fb[9];
     R Ua = R(0), Ta = R(0), Ub = R(0), Tb = R(0);
     if (va) {
-        load8<R, ST>(fin, na, pl, fa);
+        loadQ<R, ST, Q>(fin, na, pl, fa);
         if (P.has_U) Ua = Um[na];
         if (P.has_T) Ta = Tm[na];
     }
     if (vb) {
-        load8<R, ST>(fin, nb, pl, fb);
+        loadQ<R, ST, Q>(fin, nb, pl, fb);
         if (P.has_U) Ub = Um[nb];
         if (P.has_T) Tb = Tm[nb];
     }
     load_phi_ring2<R, TY, IN>(P, phi, sm.phi, x0, y0, tid);
     __syncthreads();
     R a2own = R(1);
-    if (va) a2own = phase_collide<R, TY>(P, sm.phi, sm.post, tx + 1, ty + 1, ay, mom_x(fa), mom_y(fa), Ua, Ta, tnow);
-    if (vb) phase_collide<R, TY>(P, sm.phi, sm.post, blx, bly, by, mom_x(fb), mom_y(fb), Ub, Tb, tnow);
+    if (va) a2own = phase_collide<R, TY, Q>(P, sm.phi, sm.post, tx + 1, ty + 1, ay, mom_x(fa), mom_y(fa), Ua, Ta, tnow);
+    if (vb) phase_collide<R, TY, Q>(P, sm.phi, sm.post, blx, bly, by, mom_x(fb), mom_y(fb), Ub, Tb, tnow);
     __syncthreads();
     if (!own) return;
     const int gx = x0 + tx, gy = y0 + ty;
@@ -205,15 +217,15 @@ __device__ __forceinline__ void phase_tile(PhaseSmem<R, TY>& sm, const KP<R>& P,
     const R inva2 = rcp(a2own);
     R s8 = R(0);
 #pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        if (DEV) fa[i] += wq<R>(i) * c;          // decode h_i = f_i - w_i phi
+    for (int i = 1; i < Q; ++i) {
+        if (DEV) fa[i] += wqq<R, Q>(i) * c;      // decode h_i = f_i - w_i phi
         s8 += fa[i];
     }
     fa[0] = c - s8;                              // population 0 from the zeroth moment
     const Walls w = walls_of<IN>(gx, gy, P.nx, P.ny, P.bsx, P.bsy);
     R fn[9], sum = R(0);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
+    for (int i = 0; i < Q; ++i) {
         const R inc = w.hit(i) ? sm.post[opp_of(i)][ty + 1][tx + 1] : sm.post[i][ty + 1 - ey_of(i)][tx + 1 - ex_of(i)];
         fn[i] = fa[i] + (inc - fa[i]) * inva2;                                   // Eq. 26
         sum += fn[i];
@@ -221,19 +233,19 @@ __device__ __forceinline__ void phase_tile(PhaseSmem<R, TY>& sm, const KP<R>& P,
     const int node = gy * P.pitch + gx;
     phin[node] = sum;                                                            // Eq. 18
 #pragma unroll
-    for (int i = 1; i < 9; ++i) fout[node + (i - 1) * pl] = Cvt<ST>::st(DEV ? fn[i] - wq<R>(i) * sum : fn[i]);
+    for (int i = 1; i < Q; ++i) fout[node + (i - 1) * pl] = Cvt<ST>::st(DEV ? fn[i] - wqq<R, Q>(i) * sum : fn[i]);
 }
 
-template <typename R, typename ST, bool DEV, int TY>
-__device__ __forceinline__ void phase_block(PhaseSmem<R, TY>& sm, const KP<R>& P, const ST* fin, ST* fout,
+template <typename R, typename ST, bool DEV, int TY, int Q>
+__device__ __forceinline__ void phase_block(PhaseSmem<R, TY, Q>& sm, const KP<R>& P, const ST* fin, ST* fout,
                                             const R* phi, R* phin, const R* Um, const R* Tm,
                                             const long long* clock, long long off, int x0, int y0,
                                             Rect skip = Rect{0, 0, 0, 0}) {
     R tnow = R(0);
     if (P.frozen_T) tnow = (R)((clock ? *clock : 0ll) + off) * P.dt_base;
     if (interior2<TY>(x0, y0, P.nx, P.ny))
-        phase_tile<R, ST, DEV, TY, true>(sm, P, fin, fout, phi, phin, Um, Tm, tnow, x0, y0, skip);
-    else phase_tile<R, ST, DEV, TY, false>(sm, P, fin, fout, phi, phin, Um, Tm, tnow, x0, y0, skip);
+        phase_tile<R, ST, DEV, TY, true, Q>(sm, P, fin, fout, phi, phin, Um, Tm, tnow, x0, y0, skip);
+    else phase_tile<R, ST, DEV, TY, false, Q>(sm, P, fin, fout, phi, phin, Um, Tm, tnow, x0, y0, skip);
 }
 
 // ---------------------------------------------------------------------------
@@ -366,15 +378,15 @@ __device__ __forceinline__ void transfer_block(TransferSmem<R, TY>& sm, const KP
 // Concentration / temperature update (Eqs. 7-8, 10-12 tr parts; 14, 19-20,
 // 23-25, 40, 18).  FIELD 0 = U, 1 = T.
 // ---------------------------------------------------------------------------
-template <typename R, int TY> struct ScalarSmem {
+template <typename R, int TY, int Q = 9> struct ScalarSmem {
     R phi[TY + 4][36];
-    R post[9][TY + 2][34];
+    R post[Q][TY + 2][34];
     R red[TY];
 };
 
 // sphi: the phase field on a tile of width GXW whose ring is OFF + 1 nodes
 // wide, so halo position (lx, ly) of the 1-ring sits at (lx + OFF, ly + OFF)
-template <typename R, int TY, int FIELD, int GXW = 36, int OFF = 1>
+template <typename R, int TY, int FIELD, int GXW = 36, int OFF = 1, int Q = 9>
 __device__ __forceinline__ void scalar_collide(const KP<R>& P, const R (*sphi)[GXW], R (*sp)[TY + 2][34], int lx,
                                                int ly, R chi, R jx, R jy, R vx, R vy) {
     const R dt = FIELD == 0 ? P.dtU : P.dtT;
@@ -394,13 +406,13 @@ __device__ __forceinline__ void scalar_collide(const KP<R>& P, const R (*sphi)[G
     const R jnx = jx - bx, jny = jy - by;
     R gpx, gpy;
     iso_grad<R, GXW>(sphi, lx + OFF, ly + OFF, gpx, gpy);
-    const R Q = coef * (R(-3) * s) * (jnx * gpx + jny * gpy);                       // Eq. 40 in Eq. 8 / 12
-    const R k6 = (R(1) - s) * (R(1) / R(6));
-    put_scalar_post<R, TY + 2, 34>(sp, ly, lx, chi + dt * Q, bx, by, k6 * jnx, k6 * jny);
+    const R Qs = coef * (R(-3) * s) * (jnx * gpx + jny * gpy);                      // Eq. 40 in Eq. 8 / 12
+    const R k6 = (R(1) - s) * kneq<R, Q>();
+    put_scalar_post<R, TY + 2, 34, Q>(sp, ly, lx, chi + dt * Qs, bx, by, k6 * jnx, k6 * jny);
 }
 
-template <typename R, typename ST, bool DEV, int TY, int FIELD, bool IN>
-__device__ __forceinline__ void scalar_tile(ScalarSmem<R, TY>& sm, const KP<R>& P, const ST* __restrict__ fin,
+template <typename R, typename ST, bool DEV, int TY, int FIELD, bool IN, int Q>
+__device__ __forceinline__ void scalar_tile(ScalarSmem<R, TY, Q>& sm, const KP<R>& P, const ST* __restrict__ fin,
                                             ST* __restrict__ fout, const R* __restrict__ mac_in,
                                             R* __restrict__ mac_out, const R* __restrict__ acc,
                                             const R* __restrict__ phi, const R* __restrict__ ux,
@@ -436,8 +448,8 @@ __device__ __forceinline__ void scalar_tile(ScalarSmem<R, TY>& sm, const KP<R>& 
     }
     load_phi_ring2<R, TY, IN>(P, phi, sm.phi, x0, y0, tid);
     __syncthreads();
-    if (va) scalar_collide<R, TY, FIELD>(P, sm.phi, sm.post, tx + 1, ty + 1, ca, jax, jay, uxa, uya);
-    if (vb) scalar_collide<R, TY, FIELD>(P, sm.phi, sm.post, blx, bly, cb, jbx, jby, uxb, uyb);
+    if (va) scalar_collide<R, TY, FIELD, 36, 1, Q>(P, sm.phi, sm.post, tx + 1, ty + 1, ca, jax, jay, uxa, uya);
+    if (vb) scalar_collide<R, TY, FIELD, 36, 1, Q>(P, sm.phi, sm.post, blx, bly, cb, jbx, jby, uxb, uyb);
     __syncthreads();
     const int gx = x0 + tx, gy = y0 + ty;
     R myj = R(0);
@@ -447,9 +459,10 @@ __device__ __forceinline__ void scalar_tile(ScalarSmem<R, TY>& sm, const KP<R>& 
         R fn[9], sum = R(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
+            if (i >= Q) { fn[i] = R(0); continue; }                                   // D2Q5: no diagonals
             fn[i] = w.hit(i) ? sm.post[opp_of(i)][ty + 1][tx + 1] : sm.post[i][ty + 1 - ey_of(i)][tx + 1 - ex_of(i)]; // Eq. 25
             if (FIELD == 1 && !IN && ey_of(i) > 0 && w.ym && P.T_dir_ym)              // bottom wall at T_ymin
-                fn[i] = R(2) * wq<R>(i) * P.T_ymin - sm.post[opp_of(i)][ty + 1][tx + 1];
+                fn[i] = R(2) * wqq<R, Q>(i) * P.T_ymin - sm.post[opp_of(i)][ty + 1][tx + 1];
             sum += fn[i];
         }
         mac_out[node] = sum;                                                      // Eq. 18
@@ -469,13 +482,13 @@ __device__ __forceinline__ void scalar_tile(ScalarSmem<R, TY>& sm, const KP<R>& 
     }
 }
 
-template <typename R, typename ST, bool DEV, int TY, int FIELD>
-__device__ __forceinline__ void scalar_block(ScalarSmem<R, TY>& sm, const KP<R>& P, const ST* fin, ST* fout,
+template <typename R, typename ST, bool DEV, int TY, int FIELD, int Q>
+__device__ __forceinline__ void scalar_block(ScalarSmem<R, TY, Q>& sm, const KP<R>& P, const ST* fin, ST* fout,
                                              const R* mac_in, R* mac_out, const R* acc, const R* phi, const R* ux,
                                              const R* uy, unsigned long long* smax, int x0, int y0) {
     if (interior2<TY>(x0, y0, P.nx, P.ny))
-        scalar_tile<R, ST, DEV, TY, FIELD, true>(sm, P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, x0, y0);
-    else scalar_tile<R, ST, DEV, TY, FIELD, false>(sm, P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, x0, y0);
+        scalar_tile<R, ST, DEV, TY, FIELD, true, Q>(sm, P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, x0, y0);
+    else scalar_tile<R, ST, DEV, TY, FIELD, false, Q>(sm, P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, x0, y0);
 }
 
 // ---------------------------------------------------------------------------
@@ -695,20 +708,20 @@ __device__ __forceinline__ const J& job_of_block(const J* __restrict__ jobs, int
     return j;
 }
 
-template <typename R, typename ST, bool DEV, int TY>
+template <typename R, typename ST, bool DEV, int TY, int Q>
 __global__ void __launch_bounds__(32 * TY)
 k_phase(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout, const R* __restrict__ phi,
         R* __restrict__ phin, const R* __restrict__ Um, const R* __restrict__ Tm,
         const long long* __restrict__ clock, long long step_off) {
-    __shared__ PhaseSmem<R, TY> sm;
-    phase_block<R, ST, DEV, TY>(sm, *P, fin, fout, phi, phin, Um, Tm, clock, step_off, blockIdx.x * 32, blockIdx.y * TY);
+    __shared__ PhaseSmem<R, TY, Q> sm;
+    phase_block<R, ST, DEV, TY, Q>(sm, *P, fin, fout, phi, phin, Um, Tm, clock, step_off, blockIdx.x * 32, blockIdx.y * TY);
 }
-template <typename R, typename ST, bool DEV, int TY>
+template <typename R, typename ST, bool DEV, int TY, int Q>
 __global__ void __launch_bounds__(32 * TY) k_phase_batch(const PhaseJob<R, ST>* __restrict__ jobs, int njobs) {
-    __shared__ PhaseSmem<R, TY> sm;
+    __shared__ PhaseSmem<R, TY, Q> sm;
     int x0, y0;
     const PhaseJob<R, ST>& j = job_of_block(jobs, njobs, blockIdx.x, x0, y0, TY);
-    phase_block<R, ST, DEV, TY>(sm, *j.P,j.fin, j.fout, j.phi, j.phin, j.Um, j.Tm, j.clock, j.off, x0, y0);
+    phase_block<R, ST, DEV, TY, Q>(sm, *j.P,j.fin, j.fout, j.phi, j.phin, j.Um, j.Tm, j.clock, j.off, x0, y0);
 }
 
 template <typename R, int TY>
@@ -730,21 +743,21 @@ __global__ void __launch_bounds__(32 * TY) k_transfer_batch(const TransferJob<R>
                           j.acc_reset_T, j.smax, x0, y0);
 }
 
-template <typename R, typename ST, bool DEV, int TY, int FIELD>
+template <typename R, typename ST, bool DEV, int TY, int FIELD, int Q>
 __global__ void __launch_bounds__(32 * TY)
 k_scalar(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout,
          const R* __restrict__ mac_in, R* __restrict__ mac_out, const R* __restrict__ acc, const R* __restrict__ phi,
          const R* __restrict__ ux, const R* __restrict__ uy, unsigned long long* __restrict__ smax) {
-    __shared__ ScalarSmem<R, TY> sm;
-    scalar_block<R, ST, DEV, TY, FIELD>(sm, *P,fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, blockIdx.x * 32,
+    __shared__ ScalarSmem<R, TY, Q> sm;
+    scalar_block<R, ST, DEV, TY, FIELD, Q>(sm, *P,fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, blockIdx.x * 32,
                                         blockIdx.y * TY);
 }
-template <typename R, typename ST, bool DEV, int TY, int FIELD>
+template <typename R, typename ST, bool DEV, int TY, int FIELD, int Q>
 __global__ void __launch_bounds__(32 * TY) k_scalar_batch(const ScalarJob<R, ST>* __restrict__ jobs, int njobs) {
-    __shared__ ScalarSmem<R, TY> sm;
+    __shared__ ScalarSmem<R, TY, Q> sm;
     int x0, y0;
     const ScalarJob<R, ST>& j = job_of_block(jobs, njobs, blockIdx.x, x0, y0, TY);
-    scalar_block<R, ST, DEV, TY, FIELD>(sm, *j.P,j.fin, j.fout, j.mac_in, j.mac_out, j.acc, j.phi, j.ux, j.uy,
+    scalar_block<R, ST, DEV, TY, FIELD, Q>(sm, *j.P,j.fin, j.fout, j.mac_in, j.mac_out, j.acc, j.phi, j.ux, j.uy,
                                         j.smax, x0, y0);
 }
 

@@ -54,28 +54,36 @@ __device__ __forceinline__ void strip_grad(int lane, R cm, R c0, R cp, R em, R e
 }
 
 // post-collision populations of the scalar collision (Eq. 14 with S of
-// Eq. 23 in closed form): p_i = w_i A + 3 w_i (e_i . b) + (e_i . c)
-template <typename R>
+// Eq. 23 in closed form): p_i = w_i A + 3 w_i (e_i . b) + (e_i . c), on the
+// Q-velocity lattice (on D2Q5, p_5..p_8 are compile-time zeros)
+template <typename R, int Q = 9>
 __device__ __forceinline__ void scalar_post9(R A, R bx, R by, R cx, R cy, R* p) {
-    const R w1 = Wt<R>::w1, w2 = Wt<R>::w2;
+    const R w1 = wqq<R, Q>(1), w2 = Wt<R>::w2;
     const R a1 = w1 * A, a2 = w2 * A, b1x = R(3) * w1 * bx, b1y = R(3) * w1 * by;
     const R b2x = R(3) * w2 * bx, b2y = R(3) * w2 * by;
-    p[0] = Wt<R>::w0 * A;
+    p[0] = wqq<R, Q>(0) * A;
     p[1] = a1 + b1x + cx;
     p[2] = a1 + b1y + cy;
     p[3] = a1 - b1x - cx;
     p[4] = a1 - b1y - cy;
-    p[5] = a2 + (b2x + b2y) + (cx + cy);
-    p[6] = a2 + (b2y - b2x) + (cy - cx);
-    p[7] = a2 - (b2x + b2y) - (cx + cy);
-    p[8] = a2 + (b2x - b2y) + (cx - cy);
+    if constexpr (Q == 9) {
+        p[5] = a2 + (b2x + b2y) + (cx + cy);
+        p[6] = a2 + (b2y - b2x) + (cy - cx);
+        p[7] = a2 - (b2x + b2y) - (cx + cy);
+        p[8] = a2 + (b2x - b2y) + (cx - cy);
+    } else {
+        p[5] = p[6] = p[7] = p[8] = R(0);
+    }
 }
+// a diagonal population moved one lane: on D2Q5 there is none to move
+template <int Q, typename R> __device__ __forceinline__ R diag_from_left(R v) { return Q == 9 ? from_left(v) : R(0); }
+template <int Q, typename R> __device__ __forceinline__ R diag_from_right(R v) { return Q == 9 ? from_right(v) : R(0); }
 
 // U (FIELD 0) or T (FIELD 1) collision at one node: chi the zeroth moment
 // (with every injection), (jx, jy) the first moment, (vx, vy) the advecting
 // velocity, ph and (gpx, gpy) phi and its gradient (Eqs. 7-8, 10-12, 19-20,
 // 24, 40)
-template <typename R, int FIELD>
+template <typename R, int FIELD, int Q = 9>
 __device__ __forceinline__ void scalar_collide9(const KP<R>& P, R ph, R gpx, R gpy, R chi, R jx, R jy, R vx, R vy,
                                                 R* p) {
     const R dt = FIELD == 0 ? P.dtU : P.dtT;
@@ -92,9 +100,9 @@ __device__ __forceinline__ void scalar_collide9(const KP<R>& P, R ph, R gpx, R g
     const R s = rcp(R(3) * dt * D + R(0.5));                                      // Eq. 24
     const R bx = dt * chi * vx, by = dt * chi * vy;                                // Eqs. 19-20
     const R jnx = jx - bx, jny = jy - by;
-    const R Q = coef * (R(-3) * s) * (jnx * gpx + jny * gpy);                       // Eq. 40 in Eq. 8 / 12
-    const R k6 = (R(1) - s) * (R(1) / R(6));
-    scalar_post9<R>(chi + dt * Q, bx, by, k6 * jnx, k6 * jny, p);
+    const R Qs = coef * (R(-3) * s) * (jnx * gpx + jny * gpy);                      // Eq. 40 in Eq. 8 / 12
+    const R k6 = (R(1) - s) * kneq<R, Q>();
+    scalar_post9<R, Q>(chi + dt * Qs, bx, by, k6 * jnx, k6 * jny, p);
 }
 
 // ---------------------------------------------------------------------------
@@ -164,7 +172,7 @@ __device__ __forceinline__ void scalar_row_fetch(const KP<R>& P, const ST* __res
     fetch_word<R>(slot + SA_PE * 32 + lane, phi, py * P.pitch + ex, true);
 }
 
-template <typename R, typename ST, bool DEV, int H, int FIELD, bool IN>
+template <typename R, typename ST, bool DEV, int H, int FIELD, bool IN, int Q>
 __device__ __forceinline__ void scalar_strip(const KP<R>& P, const ST* __restrict__ fin, ST* __restrict__ fout,
                                              const R* __restrict__ mac_in, R* __restrict__ mac_out,
                                              const R* __restrict__ acc, const R* __restrict__ phi,
@@ -225,9 +233,9 @@ __device__ __forceinline__ void scalar_strip(const KP<R>& P, const ST* __restric
         R gpx, gpy;
         strip_grad<R>(lane, cm, c0, pc, em, e0, pe, gpx, gpy);
         R p[9];
-        scalar_collide9<R, FIELD>(P, c0, gpx, gpy, chi, jx, jy, vx, vy, p);
-        const R s1 = from_left(p[1]), s3 = from_right(p[3]), s5 = from_left(p[5]);
-        const R s6 = from_right(p[6]), s7 = from_right(p[7]), s8 = from_left(p[8]);
+        scalar_collide9<R, FIELD, Q>(P, c0, gpx, gpy, chi, jx, jy, vx, vy, p);
+        const R s1 = from_left(p[1]), s3 = from_right(p[3]), s5 = diag_from_left<Q>(p[5]);
+        const R s6 = diag_from_right<Q>(p[6]), s7 = diag_from_right<Q>(p[7]), s8 = diag_from_left<Q>(p[8]);
         const int y = r - 1;                       // row completed in this iteration
         if (FIELD == 0 && P.accumulated && outl && r >= y0 && r < y0 + H && r < P.ny && !skip.in(gx, r))
             myj = fmax(myj, fabs(accv));
@@ -247,9 +255,11 @@ __device__ __forceinline__ void scalar_strip(const KP<R>& P, const ST* __restric
                 if (wxp || wyp) fn[7] = o[5];
                 if (wxm || wyp) fn[8] = o[6];
                 if (FIELD == 1 && wym && P.T_dir_ym) {      // bottom wall at T_ymin: anti-bounce-back
-                    fn[2] = R(2) * Wt<R>::w1 * P.T_ymin - o[4];
-                    fn[5] = R(2) * Wt<R>::w2 * P.T_ymin - o[7];
-                    fn[6] = R(2) * Wt<R>::w2 * P.T_ymin - o[8];
+                    fn[2] = R(2) * wqq<R, Q>(2) * P.T_ymin - o[4];
+                    if (Q == 9) {
+                        fn[5] = R(2) * Wt<R>::w2 * P.T_ymin - o[7];
+                        fn[6] = R(2) * Wt<R>::w2 * P.T_ymin - o[8];
+                    }
                 }
             }
             R sum = R(0);
@@ -274,7 +284,7 @@ __device__ __forceinline__ void scalar_strip(const KP<R>& P, const ST* __restric
     }
 }
 
-template <typename R, typename ST, bool DEV, int H, int FIELD>
+template <typename R, typename ST, bool DEV, int H, int FIELD, int Q>
 __device__ __forceinline__ void scalar_strip_block(const KP<R>& P, const ST* fin, ST* fout, const R* mac_in,
                                                    R* mac_out, const R* acc, const R* phi, const R* ux, const R* uy,
                                                    unsigned long long* smax, int bx, int by) {
@@ -285,11 +295,11 @@ __device__ __forceinline__ void scalar_strip_block(const KP<R>& P, const ST* fin
     if (sx * SW >= P.nx) return;                   // whole warp: past the last strip
     const Rect none{0, 0, 0, 0};
     if (strip_interior<H>(sx, y0, P.nx, P.ny))
-        scalar_strip<R, ST, DEV, H, FIELD, true>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, sx, y0,
-                                                  none, ring + w * RING);
+        scalar_strip<R, ST, DEV, H, FIELD, true, Q>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, sx, y0,
+                                                     none, ring + w * RING);
     else
-        scalar_strip<R, ST, DEV, H, FIELD, false>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, sx, y0,
-                                                   none, ring + w * RING);
+        scalar_strip<R, ST, DEV, H, FIELD, false, Q>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, sx, y0,
+                                                      none, ring + w * RING);
 }
 
 // ---------------------------------------------------------------------------
@@ -383,7 +393,7 @@ constexpr int VNW = 2;     // warps per block of the vector-strip launches
 // upwards and completes row r+1.  Neighbouring strip rows walk in opposite
 // directions, so the halo rows two strips share are read close in time (and
 // served by L2 the second time).
-template <typename R, typename ST, bool DEV, int H, int FIELD, bool UP>
+template <typename R, typename ST, bool DEV, int H, int FIELD, bool UP, int Q>
 __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restrict__ fin, ST* __restrict__ fout,
                                               const R* __restrict__ mac_in, R* __restrict__ mac_out,
                                               const R* __restrict__ acc, const R* __restrict__ phi,
@@ -466,12 +476,12 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
 #pragma unroll
         for (int k = 0; k < VW; ++k) {
             const R gpx = A[k + 2] - A[k], gpy = B[k + 1] * (R(1) / R(3)) + (B[k] + B[k + 2]) * (R(1) / R(12));
-            scalar_collide9<R, FIELD>(P, p0.v[k], gpx, gpy, chi.v[k], jx[k], jy[k], vx.v[k], vy.v[k], p[k]);
+            scalar_collide9<R, FIELD, Q>(P, p0.v[k], gpx, gpy, chi.v[k], jx[k], jy[k], vx.v[k], vy.v[k], p[k]);
         }
         // x-shifts: e_x = +1 (1, 5, 8) from the node on the left, e_x = -1 (3, 6, 7) from the right
         R s1[VW], s5[VW], s8[VW], s3[VW], s6[VW], s7[VW];
-        s1[0] = from_left(p[VW - 1][1]); s5[0] = from_left(p[VW - 1][5]); s8[0] = from_left(p[VW - 1][8]);
-        s3[VW - 1] = from_right(p[0][3]); s6[VW - 1] = from_right(p[0][6]); s7[VW - 1] = from_right(p[0][7]);
+        s1[0] = from_left(p[VW - 1][1]); s5[0] = diag_from_left<Q>(p[VW - 1][5]); s8[0] = diag_from_left<Q>(p[VW - 1][8]);
+        s3[VW - 1] = from_right(p[0][3]); s6[VW - 1] = diag_from_right<Q>(p[0][6]); s7[VW - 1] = diag_from_right<Q>(p[0][7]);
 #pragma unroll
         for (int k = 1; k < VW; ++k) { s1[k] = p[k - 1][1]; s5[k] = p[k - 1][5]; s8[k] = p[k - 1][8]; }
 #pragma unroll
@@ -538,7 +548,7 @@ __host__ __device__ inline int vs_blocks(int nx, int ny, int H) {
     return vs_vector_blocks(g) + (frame_of(g.in, nx, ny, SW, H).count() + VNW - 1) / VNW;
 }
 
-template <typename R, typename ST, bool DEV, int H, int FIELD>
+template <typename R, typename ST, bool DEV, int H, int FIELD, int Q>
 __device__ __forceinline__ void scalar_vs_block(const KP<R>& P, const ST* fin, ST* fout, const R* mac_in, R* mac_out,
                                                 const R* acc, const R* phi, const R* ux, const R* uy,
                                                 unsigned long long* smax, int b) {
@@ -552,11 +562,11 @@ __device__ __forceinline__ void scalar_vs_block(const KP<R>& P, const ST* fin, S
         if (vs >= g.nxv * g.nyv) return;           // whole warp
         const int sy = vs / g.nxv;
         if (sy & 1)
-            scalar_vstrip<R, ST, DEV, H, FIELD, true>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax,
-                                                      vs % g.nxv, VY0 + H * sy, mine);
+            scalar_vstrip<R, ST, DEV, H, FIELD, true, Q>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax,
+                                                         vs % g.nxv, VY0 + H * sy, mine);
         else
-            scalar_vstrip<R, ST, DEV, H, FIELD, false>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax,
-                                                       vs % g.nxv, VY0 + H * sy, mine);
+            scalar_vstrip<R, ST, DEV, H, FIELD, false, Q>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax,
+                                                          vs % g.nxv, VY0 + H * sy, mine);
         return;
     }
     b -= nvb;
@@ -569,9 +579,9 @@ __device__ __forceinline__ void scalar_vs_block(const KP<R>& P, const ST* fin, S
     const int y0 = t * H;
     Word<R>* r1 = reinterpret_cast<Word<R>*>(mine);
     if (strip_interior<H>(sx, y0, P.nx, P.ny))
-        scalar_strip<R, ST, DEV, H, FIELD, true>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, sx, y0, in, r1);
+        scalar_strip<R, ST, DEV, H, FIELD, true, Q>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, sx, y0, in, r1);
     else
-        scalar_strip<R, ST, DEV, H, FIELD, false>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, sx, y0, in, r1);
+        scalar_strip<R, ST, DEV, H, FIELD, false, Q>(P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, sx, y0, in, r1);
 }
 
 // ---------------------------------------------------------------------------
@@ -962,15 +972,19 @@ __device__ __forceinline__ void transfer_vs_block(const KP<R>& P, const R* phio,
 // f_i <- f_i + (p_i(x - e_i) - f_i) / a_s^2(x), so a completed row also needs
 // its own loaded populations and a_s^2, carried from its collision.
 // ---------------------------------------------------------------------------
-enum { PA_PHI = 8, PA_U = 9, PA_T = 10, PA_N = 11 };
-template <typename R> using PRing = VRingN<R, PA_N>;
+// ring arrays of a phase row: populations 1..Q-1, then phi, U, T
+template <int Q> struct PA {
+    static constexpr int PHI = Q - 1, U = Q, T = Q + 1, N = Q + 2;
+};
+template <typename R, int Q = 9> using PRing = VRingN<R, PA<Q>::N>;
 
-template <typename R, typename ST, bool DEV, int H, bool UP>
+template <typename R, typename ST, bool DEV, int H, bool UP, int Q>
 __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restrict__ fin, ST* __restrict__ fout,
                                              const R* __restrict__ phi, R* __restrict__ phin,
                                              const R* __restrict__ Um, const R* __restrict__ Tm, R tnow, int s,
                                              int y0, unsigned char* __restrict__ ring) {
-    using RG = PRing<R>;
+    using RG = PRing<R, Q>;
+    constexpr int PA_PHI = PA<Q>::PHI, PA_U = PA<Q>::U, PA_T = PA<Q>::T;
     constexpr int EB = RG::EB, NR = H + 2, D = RG::D, DIR = UP ? -1 : 1;
     constexpr int FAX = UP ? 4 : 2, FL = UP ? 8 : 5, FR = UP ? 7 : 6;     // far row: axis, from left, from right
     constexpr int NAX = UP ? 2 : 4, NL = UP ? 5 : 8, NRt = UP ? 6 : 7;    // near row (just collided)
@@ -982,7 +996,7 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
     auto fetch_row = [&](int r, unsigned char* slot) {      // populations, U, T of row r; phi of row r + DIR
         const int base = r * pitch + c0;
 #pragma unroll
-        for (int i = 1; i < 9; ++i) fetch_vec<ST>(slot + (i - 1) * 32 * EB, fin + (size_t)(i - 1) * pl + base);
+        for (int i = 1; i < Q; ++i) fetch_vec<ST>(slot + (i - 1) * 32 * EB, fin + (size_t)(i - 1) * pl + base);
         fetch_vec<R>(slot + PA_PHI * 32 * EB, phi + base + DIR * pitch);
         if (P.has_U) fetch_vec<R>(slot + PA_U * 32 * EB, Um + base);
         if (P.has_T) fetch_vec<R>(slot + PA_T * 32 * EB, Tm + base);
@@ -1014,6 +1028,11 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
         R f[9][VW];
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
+            if (i >= Q) {                          // D2Q5: no diagonal populations
+#pragma unroll
+                for (int k = 0; k < VW; ++k) f[i][k] = R(0);
+                continue;
+            }
             const Vec4<ST> v = sread<ST>(sl + (i - 1) * 32 * EB);
 #pragma unroll
             for (int k = 0; k < VW; ++k) f[i][k] = (R)Cvt<ST>::ld(v.v[k]);
@@ -1046,16 +1065,16 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
             else if (P.frozen_T) th = theta_frozen(P, r, tnow);
             else th = P.theta_c;
             const R one = R(1) - c * c;
-            const R Q = c * one - P.lam * (P.Mc * Us.v[k] + th) * one * one;              // Eq. 4
+            const R Qs = c * one - P.lam * (P.Mc * Us.v[k] + th) * one * one;             // Eq. 4
             const R bx = -P.dtp * P.W0sq_tau0 * Nx, by = -P.dtp * P.W0sq_tau0 * Ny;     // dt v_n (Eqs. 21-22)
-            const R k6 = (R(1) - sv) * (R(1) / R(6));
+            const R k6 = (R(1) - sv) * kneq<R, Q>();
             const R jx = f[1][k] - f[3][k] + f[5][k] - f[6][k] - f[7][k] + f[8][k];
             const R jy = f[2][k] - f[4][k] + f[5][k] + f[6][k] - f[7][k] - f[8][k];
-            scalar_post9<R>(c + P.dtp * Q * P.inv_tau0, bx, by, k6 * (jx - bx), k6 * (jy - by), p[k]);
+            scalar_post9<R, Q>(c + P.dtp * Qs * P.inv_tau0, bx, by, k6 * (jx - bx), k6 * (jy - by), p[k]);
         }
         R s1[VW], s5[VW], s8[VW], s3[VW], s6[VW], s7[VW];
-        s1[0] = from_left(p[VW - 1][1]); s5[0] = from_left(p[VW - 1][5]); s8[0] = from_left(p[VW - 1][8]);
-        s3[VW - 1] = from_right(p[0][3]); s6[VW - 1] = from_right(p[0][6]); s7[VW - 1] = from_right(p[0][7]);
+        s1[0] = from_left(p[VW - 1][1]); s5[0] = diag_from_left<Q>(p[VW - 1][5]); s8[0] = diag_from_left<Q>(p[VW - 1][8]);
+        s3[VW - 1] = from_right(p[0][3]); s6[VW - 1] = diag_from_right<Q>(p[0][6]); s7[VW - 1] = diag_from_right<Q>(p[0][7]);
 #pragma unroll
         for (int k = 1; k < VW; ++k) { s1[k] = p[k - 1][1]; s5[k] = p[k - 1][5]; s8[k] = p[k - 1][8]; }
 #pragma unroll
@@ -1073,7 +1092,7 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
                     fa[i] = fy[i][k];
-                    if (DEV) fa[i] += wq<R>(i) * c;                                  // decode h_i = f_i - w_i phi
+                    if (DEV && i < Q) fa[i] += wqq<R, Q>(i) * c;                     // decode h_i = f_i - w_i phi
                     s8v += fa[i];
                 }
                 fa[0] = c - s8v;                                                     // population 0 from phi
@@ -1084,18 +1103,18 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
                 const R inva2 = rcp(ay[k]);
                 R t = R(0);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    fn[i][k] = fa[i] + (inc[i] - fa[i]) * inva2;
+                for (int i = 0; i < Q; ++i) {
+                    fn[i][k] = fa[i] + (inc[i] - fa[i]) * inva2;                     // Eq. 26
                     t += fn[i][k];
                 }
                 sum.v[k] = t;
             }
             *reinterpret_cast<Vec4<R>*>(phin + node) = sum;
 #pragma unroll
-            for (int i = 1; i < 9; ++i) {
+            for (int i = 1; i < Q; ++i) {
                 Vec4<ST> o;
 #pragma unroll
-                for (int k = 0; k < VW; ++k) o.v[k] = Cvt<ST>::st(DEV ? fn[i][k] - wq<R>(i) * sum.v[k] : fn[i][k]);
+                for (int k = 0; k < VW; ++k) o.v[k] = Cvt<ST>::st(DEV ? fn[i][k] - wqq<R, Q>(i) * sum.v[k] : fn[i][k]);
                 *reinterpret_cast<Vec4<ST>*>(fout + (size_t)(i - 1) * pl + node) = o;
             }
         }
@@ -1115,9 +1134,9 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
 }
 
 constexpr int PVW = 4;     // warps per block of the phase vector launch (= tile height of its frame)
-template <typename R> struct PVSmem {
-    static constexpr int STRIPS = PVW * PRing<R>::BYTES;
-    static constexpr int TILE = (int)sizeof(PhaseSmem<R, PVW>);
+template <typename R, int Q = 9> struct PVSmem {
+    static constexpr int STRIPS = PVW * PRing<R, Q>::BYTES;
+    static constexpr int TILE = (int)sizeof(PhaseSmem<R, PVW, Q>);
     static constexpr int BYTES = STRIPS > TILE ? STRIPS : TILE;
 };
 __host__ __device__ inline int pvs_blocks(int nx, int ny, int H) {
@@ -1125,7 +1144,7 @@ __host__ __device__ inline int pvs_blocks(int nx, int ny, int H) {
     return (g.nxv * g.nyv + PVW - 1) / PVW + frame_of(g.in, nx, ny, 32, PVW).count();
 }
 
-template <typename R, typename ST, bool DEV, int H>
+template <typename R, typename ST, bool DEV, int H, int Q>
 __device__ __forceinline__ void phase_vs_block(const KP<R>& P, const ST* fin, ST* fout, const R* phi, R* phin,
                                                const R* Um, const R* Tm, const long long* clock, long long off,
                                                int b) {
@@ -1139,18 +1158,19 @@ __device__ __forceinline__ void phase_vs_block(const KP<R>& P, const ST* fin, ST
         R tnow = R(0);
         if (P.frozen_T) tnow = (R)((clock ? *clock : 0ll) + off) * P.dt_base;
         const int sy = vs / g.nxv;
-        unsigned char* mine = psm + w * PRing<R>::BYTES;
+        unsigned char* mine = psm + w * PRing<R, Q>::BYTES;
         if (sy & 1)
-            phase_vstrip<R, ST, DEV, H, true>(P, fin, fout, phi, phin, Um, Tm, tnow, vs % g.nxv, VY0 + H * sy, mine);
+            phase_vstrip<R, ST, DEV, H, true, Q>(P, fin, fout, phi, phin, Um, Tm, tnow, vs % g.nxv, VY0 + H * sy,
+                                                 mine);
         else
-            phase_vstrip<R, ST, DEV, H, false>(P, fin, fout, phi, phin, Um, Tm, tnow, vs % g.nxv, VY0 + H * sy,
-                                               mine);
+            phase_vstrip<R, ST, DEV, H, false, Q>(P, fin, fout, phi, phin, Um, Tm, tnow, vs % g.nxv, VY0 + H * sy,
+                                                  mine);
         return;
     }
     b -= nvb;
     int u, v;
     frame_of(g.in, P.nx, P.ny, 32, PVW).unit(b, u, v);
-    phase_block<R, ST, DEV, PVW>(*reinterpret_cast<PhaseSmem<R, PVW>*>(psm), P, fin, fout, phi, phin, Um, Tm, clock,
+    phase_block<R, ST, DEV, PVW, Q>(*reinterpret_cast<PhaseSmem<R, PVW, Q>*>(psm), P, fin, fout, phi, phin, Um, Tm, clock,
                                  off, u * 32, v * PVW, g.in);
 }
 
@@ -1179,42 +1199,42 @@ __device__ __forceinline__ const J& job_block(const J* __restrict__ jobs, int nj
     return j;
 }
 
-template <typename R, typename ST, bool DEV, int H, int FIELD>
+template <typename R, typename ST, bool DEV, int H, int FIELD, int Q>
 __global__ void __launch_bounds__(32 * NWS)
 k_scalar_strip(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout,
                const R* __restrict__ mac_in, R* __restrict__ mac_out, const R* __restrict__ acc,
                const R* __restrict__ phi, const R* __restrict__ ux, const R* __restrict__ uy,
                unsigned long long* __restrict__ smax) {
-    scalar_strip_block<R, ST, DEV, H, FIELD>(*P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, blockIdx.x,
+    scalar_strip_block<R, ST, DEV, H, FIELD, Q>(*P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, blockIdx.x,
                                              blockIdx.y);
 }
-template <typename R, typename ST, bool DEV, int H, int FIELD>
+template <typename R, typename ST, bool DEV, int H, int FIELD, int Q>
 __global__ void __launch_bounds__(32 * VNW)
 k_scalar_vs(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout,
             const R* __restrict__ mac_in, R* __restrict__ mac_out, const R* __restrict__ acc,
             const R* __restrict__ phi, const R* __restrict__ ux, const R* __restrict__ uy,
             unsigned long long* __restrict__ smax) {
-    scalar_vs_block<R, ST, DEV, H, FIELD>(*P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, blockIdx.x);
+    scalar_vs_block<R, ST, DEV, H, FIELD, Q>(*P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, blockIdx.x);
 }
-template <typename R, typename ST, bool DEV, int H, int FIELD>
+template <typename R, typename ST, bool DEV, int H, int FIELD, int Q>
 __global__ void __launch_bounds__(32 * VNW) k_scalar_vs_batch(const ScalarJob<R, ST>* __restrict__ jobs, int njobs) {
     int bx, by;
     const ScalarJob<R, ST>& j = job_block(jobs, njobs, blockIdx.x, bx, by);
-    scalar_vs_block<R, ST, DEV, H, FIELD>(*j.P, j.fin, j.fout, j.mac_in, j.mac_out, j.acc, j.phi, j.ux, j.uy, j.smax,
+    scalar_vs_block<R, ST, DEV, H, FIELD, Q>(*j.P, j.fin, j.fout, j.mac_in, j.mac_out, j.acc, j.phi, j.ux, j.uy, j.smax,
                                           by * j.tiles_x + bx);
 }
-template <typename R, typename ST, bool DEV, int H>
+template <typename R, typename ST, bool DEV, int H, int Q>
 __global__ void __launch_bounds__(32 * PVW)
 k_phase_vs(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout, const R* __restrict__ phi,
            R* __restrict__ phin, const R* __restrict__ Um, const R* __restrict__ Tm,
            const long long* __restrict__ clock, long long step_off) {
-    phase_vs_block<R, ST, DEV, H>(*P, fin, fout, phi, phin, Um, Tm, clock, step_off, blockIdx.x);
+    phase_vs_block<R, ST, DEV, H, Q>(*P, fin, fout, phi, phin, Um, Tm, clock, step_off, blockIdx.x);
 }
-template <typename R, typename ST, bool DEV, int H>
+template <typename R, typename ST, bool DEV, int H, int Q>
 __global__ void __launch_bounds__(32 * PVW) k_phase_vs_batch(const PhaseJob<R, ST>* __restrict__ jobs, int njobs) {
     int bx, by;
     const PhaseJob<R, ST>& j = job_block(jobs, njobs, blockIdx.x, bx, by);
-    phase_vs_block<R, ST, DEV, H>(*j.P, j.fin, j.fout, j.phi, j.phin, j.Um, j.Tm, j.clock, j.off,
+    phase_vs_block<R, ST, DEV, H, Q>(*j.P, j.fin, j.fout, j.phi, j.phin, j.Um, j.Tm, j.clock, j.off,
                                   by * j.tiles_x + bx);
 }
 template <typename R, int H>
@@ -1247,11 +1267,11 @@ __global__ void __launch_bounds__(32 * FVW) k_flow_vs_batch(const FlowJob<R, ST>
     flow_vs_block<R, ST, DEV, H>(*j.P, j.fin, j.fout, j.phi, j.ux_in, j.uy_in, j.rho_in, j.ux_out, j.uy_out,
                                  j.rho_out, by * j.tiles_x + bx);
 }
-template <typename R, typename ST, bool DEV, int H, int FIELD>
+template <typename R, typename ST, bool DEV, int H, int FIELD, int Q>
 __global__ void __launch_bounds__(32 * NWS) k_scalar_strip_batch(const ScalarJob<R, ST>* __restrict__ jobs, int njobs) {
     int bx, by;
     const ScalarJob<R, ST>& j = job_block(jobs, njobs, blockIdx.x, bx, by);
-    scalar_strip_block<R, ST, DEV, H, FIELD>(*j.P, j.fin, j.fout, j.mac_in, j.mac_out, j.acc, j.phi, j.ux, j.uy,
+    scalar_strip_block<R, ST, DEV, H, FIELD, Q>(*j.P, j.fin, j.fout, j.mac_in, j.mac_out, j.acc, j.phi, j.ux, j.uy,
                                              j.smax, bx, by);
 }
 

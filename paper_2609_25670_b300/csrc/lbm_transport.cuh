@@ -84,7 +84,7 @@ __device__ __forceinline__ void load_phi_ring3(const KP<R>& P, const R* __restri
     }
 }
 
-template <typename R, typename ST, bool DEV, int TY, bool IN>
+template <typename R, typename ST, bool DEV, int TY, bool IN, int Q>
 __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const KP<R>& P,
                                                const TransportJob<R, ST>& A, int x0, int y0) {
     constexpr int TX = 32, HX = 34, NT = 32 * TY, NR = 2 * HX + 2 * TY;
@@ -284,17 +284,18 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
         R fn[9], sum = R(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
+            if (i >= Q) { fn[i] = R(0); continue; }                                 // D2Q5: no diagonals
             fn[i] = ws.hit(i) ? sm.post[opp_of(i)][ty + 1][tx + 1] : sm.post[i][ty + 1 - ey_of(i)][tx + 1 - ex_of(i)];
             if (!IN && dir_ym && ey_of(i) > 0 && ws.ym)                            // bottom wall at T_ymin
-                fn[i] = R(2) * wq<R>(i) * P.T_ymin - sm.post[opp_of(i)][ty + 1][tx + 1];
+                fn[i] = R(2) * wqq<R, Q>(i) * P.T_ymin - sm.post[opp_of(i)][ty + 1][tx + 1];
             sum += fn[i];
         }
         mac_out[node] = sum;
         store_j<R, ST>(fout, node, pl, fn);
     };
     if (A.do_U) {
-        if (va) scalar_collide<R, TY, 0, 38, 2>(P, sm.phi, sm.post, tx + 1, ty + 1, Uia, jax, jay, uxa, uya);
-        if (vb) scalar_collide<R, TY, 0, 38, 2>(P, sm.phi, sm.post, blx, bly, Uib, jbx, jby, uxb, uyb);
+        if (va) scalar_collide<R, TY, 0, 38, 2, Q>(P, sm.phi, sm.post, tx + 1, ty + 1, Uia, jax, jay, uxa, uya);
+        if (vb) scalar_collide<R, TY, 0, 38, 2, Q>(P, sm.phi, sm.post, blx, bly, Uib, jbx, jby, uxb, uyb);
         __syncthreads();
         scalar_stream(A.fUout, A.Uout, false);
         __syncthreads();
@@ -309,8 +310,8 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
             jbx = word_value<R, ST>(sm.pb[PF_TJX][tid], (nb & 1) != 0);
             jby = word_value<R, ST>(sm.pb[PF_TJY][tid], (nb & 1) != 0);
         }
-        if (va) scalar_collide<R, TY, 1, 38, 2>(P, sm.phi, sm.post, tx + 1, ty + 1, Tia, jax, jay, uxa, uya);
-        if (vb) scalar_collide<R, TY, 1, 38, 2>(P, sm.phi, sm.post, blx, bly, Tib, jbx, jby, uxb, uyb);
+        if (va) scalar_collide<R, TY, 1, 38, 2, Q>(P, sm.phi, sm.post, tx + 1, ty + 1, Tia, jax, jay, uxa, uya);
+        if (vb) scalar_collide<R, TY, 1, 38, 2, Q>(P, sm.phi, sm.post, blx, bly, Tib, jbx, jby, uxb, uyb);
         __syncthreads();
         scalar_stream(A.fTout, A.Tout, P.T_dir_ym != 0);
         __syncthreads();
@@ -407,7 +408,7 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
 // occupancy the tile's latency hiding needs; FP64 (parity runs) unconstrained
 template <typename R, int TY> struct TransportOcc { static constexpr int MIN_BLOCKS = sizeof(R) == 4 ? 32 / TY : 1; };
 
-template <typename R, typename ST, bool DEV, int TY>
+template <typename R, typename ST, bool DEV, int TY, int Q>
 __global__ void __launch_bounds__(32 * TY, (TransportOcc<R, TY>::MIN_BLOCKS))
 k_transport_batch(const TransportJob<R, ST>* __restrict__ jobs, int njobs) {
     extern __shared__ __align__(16) unsigned char transport_smem[];
@@ -415,8 +416,8 @@ k_transport_batch(const TransportJob<R, ST>* __restrict__ jobs, int njobs) {
     int x0, y0;
     const TransportJob<R, ST>& j = job_of_block(jobs, njobs, blockIdx.x, x0, y0, TY);
     const KP<R>& P = *j.P;
-    if (interior3<TY>(x0, y0, P.nx, P.ny)) transport_tile<R, ST, DEV, TY, true>(sm, P, j, x0, y0);
-    else transport_tile<R, ST, DEV, TY, false>(sm, P, j, x0, y0);
+    if (interior3<TY>(x0, y0, P.nx, P.ny)) transport_tile<R, ST, DEV, TY, true, Q>(sm, P, j, x0, y0);
+    else transport_tile<R, ST, DEV, TY, false, Q>(sm, P, j, x0, y0);
 }
 
 }  // namespace lbmk

@@ -63,6 +63,7 @@ def _create(lib, p):
     (lambda p: setattr(p, "nx", 2), 1),
     (lambda p: setattr(p, "N_U", 0), 1),
     (lambda p: setattr(p, "precision", 7), 1),
+    (lambda p: setattr(p, "q_scalar", 7), 1),
     (lambda p: setattr(p, "bc_flow_y", 2), 1),
     (lambda p: setattr(p, "fields", lbm.FIELD_T | lbm.FIELD_FROZEN_T), 1),
     (lambda p: setattr(p, "tip_cx", 1000), 1),

@@ -39,13 +39,16 @@ def _bench_like(p, fields, steps, precision, warm=4):
     return out
 
 
+@pytest.mark.parametrize("q", [9, 5])
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 2e-4)])
-def test_convection_512_full_size(prec, tol):
+def test_convection_512_full_size(prec, tol, q):
     """FP32 bound: about 20 roundings per base step, each with relative error
     below 2^-22 (the FP32 reciprocals are the hardware approximation, the
     largest per-operation error of the path), over 40 steps on values of
-    order one: 40 * 20 * 2.4e-7 = 1.9e-4."""
+    order one: 40 * 20 * 2.4e-7 = 1.9e-4.  q: D2Q9 scalar lattices (the
+    paper's) or D2Q5 (the five-velocity option)."""
     wl = W.thermosolutal_convection(n=512, R=8.0)
+    wl.params.q_scalar = q
     steps = 40
     g = _bench_like(wl.params, wl.fields, steps, prec)
     o = run_oracle(wl.params, wl.fields, steps)
@@ -98,8 +101,8 @@ def _windows(n, pts, w, m):
     return out
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 4e-5)])
-def test_multi_dendrite_8192_sampled_windows(prec, tol):
+@pytest.mark.parametrize("prec,tol,q", [("f64", 1e-10, 9), ("f32", 4e-5, 9), ("f32", 4e-5, 5)])
+def test_multi_dendrite_8192_sampled_windows(prec, tol, q):
     """8192^2 multi-dendrite growth with convection (32 seeds, N = (1, 1, 4,
     2)), too large for the oracle as a whole: seeded through lbm_init_seed,
     autotuned and advanced through the period graphs as bench.py runs it,
@@ -109,11 +112,13 @@ def test_multi_dendrite_8192_sampled_windows(prec, tol):
     test_update_is_local_within_six_nodes_per_base_step), so the window's
     oracle result is the exact full-lattice result beyond that margin.
     FP32 bound: 8 steps x 20 roundings x 2^-22 (the hardware reciprocal) =
-    3.8e-5 on values of order one."""
+    3.8e-5 on values of order one.  q = 5: the same with D2Q5 phase, U and
+    T lattices."""
     from dataclasses import replace
     n, steps, w = 8192, 8, 160
     m = 6 * steps
     p, pts = W.multi_dendrite_params(n)
+    p.q_scalar = q
     seeds = [{"kind": "circle", "x": float(x), "y": float(y), "r": 8.0} for x, y in pts]
     sim = lbm.Simulation(p, precision=prec)
     sim.init_seed(seeds, U0=0.0, T0=-0.55)
