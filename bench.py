@@ -46,15 +46,16 @@ POP_BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
 MACRO_BYTES = {"f64": 8, "f32": 4, "f16dev": 4, "bf16dev": 4}
 
 
-def algo_bytes(prec="f32"):
+def algo_bytes(prec="f32", q=9):
     """Algorithmic bytes per node of one launch of each update kernel: the
-    stored state read and written once (phase and flow: 8 populations; U and
-    T: the 2 first-moment planes), each macro read / written once."""
+    stored state read and written once (phase: q - 1 populations, 8 on D2Q9
+    and 4 on D2Q5; flow: 8 populations; U and T: the 2 first-moment planes),
+    each macro read / written once."""
     pb, m = POP_BYTES[prec], MACRO_BYTES[prec]
     pops = 2 * 8 * pb
     moms = 2 * 2 * pb
     return {
-        "phase": pops + 4 * m,                  # pops R+W, phi^q R, U R, T R, phi^{q+1} W
+        "phase": 2 * (q - 1) * pb + 4 * m,      # pops R+W, phi^q R, U R, T R, phi^{q+1} W
         "transfer": 6 * m,                      # phi^q, phi^{q+1}, U, T R; U, T W
         "scalar_U": moms + 5 * m,               # j R+W, U R+W, phi R, u R (2)
         "scalar_T": moms + 5 * m,
@@ -116,22 +117,34 @@ def period_bytes(p, prec="f32"):
 # re-measured.
 TRAFFIC_SOURCE_SHA = "cbaed3b1e8860bde"
 TRAFFIC_PER_LAUNCH_512 = {"transport:8": 20006656.0, "phase:4": 11563008.0}
-TRAFFIC_PER_NODE_2048 = {"phase:1016": 72.68, "transfer:1016": 16.99, "scalar_T:1008": 29.08, "flow:1016": 83.53}
+TRAFFIC_PER_NODE_2048 = {"q9:phase:1016": 72.68, "q9:transfer:1016": 16.99, "q9:scalar_T:1008": 29.08, "q9:flow:1016": 83.53}
 
 
 def kernel_source_sha():
+    """Hash of the CUDA sources with comments and blank space removed: a
+    change of the code invalidates the stored traffic, a change of a comment
+    does not."""
     import hashlib
+    import re
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2609_25670_b300", "csrc")
     for nm in sorted(os.listdir(d)):
         if nm.endswith((".cu", ".cuh")):
-            with open(os.path.join(d, nm), "rb") as f:
-                h.update(f.read())
+            with open(os.path.join(d, nm)) as f:
+                src = f.read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            src = re.sub(r"//[^\n]*", "", src)
+            src = "\n".join(ln.rstrip() for ln in src.splitlines() if ln.strip())
+            h.update(nm.encode() + b"\0" + src.encode())
     return h.hexdigest()[:16]
 
 
+def lattice_label(p):
+    return "phi/U/T/flow on D2Q9" if getattr(p, "q_scalar", 9) != 5 else "phi/U/T on D2Q5, flow on D2Q9"
+
+
 def workload_label(p, prec="f32"):
-    return (f"thermosolutal free dendrite + forced convection, {p.nx}x{p.ny}, phi/U/T/flow on D2Q9, "
+    return (f"thermosolutal free dendrite + forced convection, {p.nx}x{p.ny}, {lattice_label(p)}, "
             f"N=({p.N_phi},{p.N_U},{p.N_T},{p.N_F}), {STORAGE_LABEL[prec]}")
 
 
@@ -139,8 +152,10 @@ STORAGE_LABEL = {"f64": "FP64", "f32": "FP32", "f16dev": "FP32 arithmetic, FP16 
                  "bf16dev": "FP32 arithmetic, BF16 deviation storage"}
 
 
-def workload(n=None):
-    return W.thermosolutal_convection(n=n or N_LATTICE, R=8.0)
+def workload(n=None, q=9):
+    wl = W.thermosolutal_convection(n=n or N_LATTICE, R=8.0)
+    wl.params.q_scalar = q
+    return wl
 
 
 def dist_env():
@@ -268,7 +283,7 @@ def run_ours(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
-    wl = workload(args.lattice)
+    wl = workload(args.lattice, args.q_scalar)
     p = wl.params
     nodes = p.nx * p.ny
     prec = args.precision or "f32"
@@ -296,7 +311,7 @@ def run_ours(args):
     sim.advance(STEP_BASE)
     kinds = ["phase", "transfer", "scalar_U", "scalar_T", "flow", "transport"]
     tb, tn = period_bytes(p, prec)
-    algo = algo_bytes(prec)
+    algo = algo_bytes(prec, args.q_scalar)
     algo["transport"] = tb / max(tn, 1)       # mean over the period's transport launches
     # untimed pre-pass with every kind timed, to find the dominant kernel; the
     # timed region then times only that kind (fewest event nodes in the graph)
@@ -343,7 +358,8 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = algo[dom] * nodes / avg_s / 1e9
     traffic = None
-    if args.lattice in (None, N_LATTICE) and prec == "f32" and TRAFFIC_SOURCE_SHA == kernel_source_sha():
+    if args.lattice in (None, N_LATTICE) and prec == "f32" and args.q_scalar == 9 and \
+            TRAFFIC_SOURCE_SHA == kernel_source_sha():
         traffic = TRAFFIC_PER_LAUNCH_512.get("%s:%d" % (dom, tiles[dom]))
 
     # end to end through the public API with pinned host buffers
@@ -388,7 +404,9 @@ def run_ours(args):
     del flush
     if rank == 0:
         if not args.no_large and world == 1:
-            line["large_lattice"] = large_lattice(args, torch, lbm, local, measured_peaks)
+            line["large_lattice"] = large_lattice(args, torch, lbm, local, measured_peaks, args.q_scalar)
+        if not args.no_d2q5 and world == 1 and args.q_scalar == 9:
+            line["d2q5"] = d2q5_variant(args, torch, lbm, local, dev, flush_bytes=512 * 1024 * 1024)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -397,13 +415,57 @@ def run_ours(args):
     return 0
 
 
-def large_lattice(args, torch, lbm, local, peaks_fn):
+def d2q5_variant(args, torch, lbm, local, dev, flush_bytes):
+    """The same workloads with D2Q5 phase, U and T lattices (the flow stays
+    D2Q9): the 512^2 headline configuration, timed as the main measurement
+    (CUDA events on the library stream, L2 flushed between steps), and the
+    8192^2 HBM-bound measurement with its dominant-kernel roofline."""
+    wl = workload(args.lattice, 5)
+    p = wl.params
+    prec = args.precision or "f32"
+    sim = lbm.Simulation(p, precision=prec)
+    if args.fusion != "auto":
+        sim.set_fusion(args.fusion == "on")
+    sim.init_fields(wl.fields)
+    stream = sim.stream
+    flush = torch.empty(flush_bytes // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        sim.advance(STEP_BASE)
+    tiles = sim.autotune(reps=10)
+    sim.advance(STEP_BASE)
+    steps = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+        sim.advance(STEP_BASE)
+        with torch.cuda.stream(stream):
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    fused = sim.fused
+    sim.close()
+    del flush
+    nodes = p.nx * p.ny
+    out = {"workload": workload_label(p, prec), "value": nodes * STEP_BASE * steps / (ms * 1e-3) / 1e6,
+           "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "fused_transport": fused,
+           "tiles": {k: tiles[k] for k in ("phase", "transfer", "scalar_U", "scalar_T", "flow", "transport")},
+           "l2": "flushed between steps (512 MiB write)"}
+    if not args.no_large:
+        out["large_lattice"] = large_lattice(args, torch, lbm, local, measured_peaks, 5)
+    return out
+
+
+def large_lattice(args, torch, lbm, local, peaks_fn, q=9):
     """The HBM-bound regime: the 8192^2 multi-dendrite workload (thermosolutal
     growth with convection, 32 Poisson-disc seeds, update factors (1, 1, 4,
     2), FP32; about 20 GB of state, so every step streams from HBM).  Seeded
     on the device's own data path (lbm_init_seed), autotuned, then timed over
     whole schedule periods of 4 base steps with CUDA events."""
     p, pts = W.multi_dendrite_params(8192)
+    p.q_scalar = q
     prec = args.precision or "f32"
     sim = lbm.Simulation(p, precision=prec)
     sim.init_seed([{"kind": "circle", "x": float(x), "y": float(y), "r": 8.0} for x, y in pts], U0=0.0, T0=-0.55)
@@ -441,7 +503,7 @@ def large_lattice(args, torch, lbm, local, peaks_fn):
     sim.close()
     nodes = p.nx * p.ny
     base = steps * period
-    ab = algo_bytes(prec)
+    ab = algo_bytes(prec, q)
     # algorithmic bytes per node per base step of the staged path (the fused
     # path moves fewer); U every step, T every 4th, flow every 2nd
     step_bytes = ab["phase"] + ab["transfer"] + ab["scalar_U"] + ab["scalar_T"] / p.N_T + ab["flow"] / p.N_F
@@ -456,11 +518,11 @@ def large_lattice(args, torch, lbm, local, peaks_fn):
     avg_s = kt[dom][0] * 1e-3 / max(kt[dom][1], 1)
     dom_gbs = dom_algo[dom] * nodes / avg_s / 1e9
     traffic = None
-    per_node = TRAFFIC_PER_NODE_2048.get("%s:%d" % (dom, tiles[dom]))
+    per_node = TRAFFIC_PER_NODE_2048.get("q%d:%s:%d" % (q, dom, tiles[dom]))
     if per_node is not None and prec == "f32" and TRAFFIC_SOURCE_SHA == kernel_source_sha():
         traffic = per_node * nodes
     return {"workload": "8192x8192 multi-dendrite thermosolutal growth with convection, 32 seeds, N=(1,1,4,2), "
-                        + STORAGE_LABEL[prec], "storage": prec,
+                        + lattice_label(p) + ", " + STORAGE_LABEL[prec], "storage": prec,
             "value": nodes * base / (ms * 1e-3) / 1e6, "unit": UNIT, "base_steps": base,
             "ms_per_period": ms / steps, "fused_transport": fused,
             "step": {"algo_bytes_per_node_per_base_step": step_bytes, "achieved_GBs": gbs, "peak": peak,
@@ -618,6 +680,9 @@ def main():
                          "or the autotuner's choice (auto)")
     ap.add_argument("--tile", action="append", metavar="KIND=V",
                     help="fix a kernel variant after autotuning (profiling runs): V > 0 tile height, V < 0 strip height")
+    ap.add_argument("--q-scalar", type=int, default=9, choices=[9, 5],
+                    help="velocities of the phase, U and T lattices: 9 (the paper's D2Q9) or 5 (D2Q5)")
+    ap.add_argument("--no-d2q5", action="store_true", help="skip the D2Q5 variant measurement")
     ap.add_argument("--lattice", type=int, default=None,
                     help="lattice size override for profiling runs (the reported workload is 512)")
     args = ap.parse_args()
