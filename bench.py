@@ -109,15 +109,25 @@ def period_bytes(p, prec="f32"):
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one ncu
-# capture per kernel variant ("kind:variant"), summarised in profiles/: per
-# launch on the 512^2 workload, and per node on 2048^2 (scaled by the nodes a
+# capture per kernel variant ("kind:variant"; on 2048^2 "q<velocities of the
+# phase, U, T lattices>:kind:variant"), summarised in profiles/: per launch on
+# the 512^2 workload, and per node on 2048^2 (scaled by the nodes a
 # launch processes for the 8192^2 measurement; traffic grows with the node
 # count once the state exceeds L2).  Reported only while the kernel sources
 # hash to TRAFFIC_SOURCE_SHA; after any change the traffic is null until
 # re-measured.
-TRAFFIC_SOURCE_SHA = "cbaed3b1e8860bde"
-TRAFFIC_PER_LAUNCH_512 = {"transport:8": 20006656.0, "phase:4": 11563008.0}
-TRAFFIC_PER_NODE_2048 = {"q9:phase:1016": 72.68, "q9:transfer:1016": 16.99, "q9:scalar_T:1008": 29.08, "q9:flow:1016": 83.53}
+TRAFFIC_SOURCE_SHA = "9d26614e1a4774c8"
+TRAFFIC_PER_LAUNCH_512 = {"transport:8": 20015104.0, "phase:4": 11563520.0}
+TRAFFIC_PER_NODE_2048 = {
+    "q5:flow:1008": 83.52, "q5:flow:1016": 82.92, "q5:flow:1032": 82.47, "q5:phase:1008": 39.14,
+    "q5:phase:1016": 38.25, "q5:phase:1032": 37.73, "q5:scalar_T:1008": 28.44, "q5:scalar_T:1016": 27.27,
+    "q5:scalar_T:1032": 27.89, "q5:scalar_U:1008": 28.29, "q5:scalar_U:1016": 27.29, "q5:scalar_U:1032": 27.85,
+    "q5:transfer:1008": 16.53, "q5:transfer:1016": 16.32, "q5:transfer:1032": 16.51, "q9:flow:1008": 83.72,
+    "q9:flow:1016": 82.93, "q9:flow:1032": 82.57, "q9:phase:1008": 72.16, "q9:phase:1016": 71.8,
+    "q9:phase:1032": 71.32, "q9:scalar_T:1008": 28.32, "q9:scalar_T:1016": 27.37, "q9:scalar_T:1032": 27.93,
+    "q9:scalar_U:1008": 28.56, "q9:scalar_U:1016": 27.34, "q9:scalar_U:1032": 27.97, "q9:transfer:1008": 16.4,
+    "q9:transfer:1016": 16.33, "q9:transfer:1032": 16.59
+}
 
 
 def kernel_source_sha():
