@@ -175,6 +175,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value, device=None):
+    """The maximum of a per-rank number over every rank of the process group
+    (the number itself with one rank or no group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(nodes, base_steps_per_step, steps, world, ms_max):
+    """Whole-job MLUPS: the node updates of every rank's replica over the
+    slowest rank's time (weak scaling: each rank advances its own lattice)."""
+    return nodes * base_steps_per_step * steps * world / (ms_max * 1e-3) / 1e6
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -356,11 +374,8 @@ def run_ours(args):
     launches1 = sim.launch_counts()
     gpu_launches = int(sum(launches1[k] - launches0[k] for k in launches1))
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t_local.item())
-    value = nodes * STEP_BASE * args.steps * world / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(ms, dev)
+    value = job_throughput(nodes, STEP_BASE, args.steps, world, ms_max)
 
     # roofline of the dominant kernel (largest share of the timed kernel time)
     dom_ms, dom_n = ktimes[dom]
