@@ -36,10 +36,14 @@ def _oracle_history(p, f):
     return hist
 
 
+@pytest.mark.parametrize("q", [9, 5])
 @pytest.mark.parametrize("N_T", [1, 2, 4])
 @pytest.mark.parametrize("prec", ["f32", "f16dev"])
-def test_tip_velocity_within_one_percent(prec, N_T):
+def test_tip_velocity_within_one_percent(prec, N_T, q):
+    """q: the phase and temperature lattices on D2Q9 (the paper's) or D2Q5
+    (the velocity sets the workload list names for this case)."""
     wl = W.thermal_free_dendrite(n=128, N_T=N_T)
+    wl.params.q_scalar = q
     sim = lbm.Simulation(wl.params, precision=prec)
     sim.init_fields(wl.fields)
     hist = []
