@@ -634,3 +634,32 @@ def test_d2q5_fourfold_symmetry_thermal_dendrite():
     assert np.abs(s[:, (-np.arange(96)) % 96] - s).max() < 1e-10
     assert np.abs(s[(-np.arange(96)) % 96, :] - s).max() < 1e-10
     assert np.abs(s.T - s).max() < 1e-10
+
+
+def test_isotropic_growth_without_anisotropy():
+    """With the four-fold anisotropy switched off (eps = 0) a circular seed in
+    an undercooled melt grows as a circle on the D2Q9 lattices: after 1500
+    base steps its radius along an axis and along a diagonal agree within 3 %
+    (the isotropy the nine-velocity set gives the phase-field streaming of
+    Eq. 26 and the thermal solver).  A dropped diagonal population or a wrong
+    diagonal weight breaks it."""
+    wl = W.thermal_free_dendrite(n=128, N_T=1)
+    p = wl.params
+    p.eps = 0.0
+    o = oracle.Oracle(p, wl.fields)
+    o.advance(1500)
+    phi = o.get("phi")
+    o.close()
+    c = 64
+
+    def radius(dx, dy):
+        r = 0.0
+        for t in np.arange(0.0, 63.0, 0.25):
+            i, j = int(round(c + dy * t)), int(round(c + dx * t))
+            if 0 <= i < 128 and 0 <= j < 128 and phi[i, j] > 0:
+                r = t * math.hypot(dx, dy)
+        return r
+
+    ra, rd = radius(1.0, 0.0), radius(1 / math.sqrt(2), 1 / math.sqrt(2))
+    assert ra > 20.0
+    assert abs(ra - rd) < 0.03 * ra, (ra, rd)
