@@ -193,6 +193,53 @@ def job_throughput(nodes, base_steps_per_step, steps, world, ms_max):
     return nodes * base_steps_per_step * steps * world / (ms_max * 1e-3) / 1e6
 
 
+def gated_steps(torch, stream, flush, advance, steps):
+    """`steps` bench steps on `stream`: an L2 flush (untimed), then one
+    advance() between two CUDA events.  A bounded sleep kernel queued first
+    holds the stream while the host enqueues every step, so the device runs
+    the steps back to back from its queue and a pause of the host thread
+    (scheduling, the clock sampler's queries) cannot fall inside a timed
+    step.  Returns the per-step times in ms."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    gate_s = min(2.0, 0.01 + 3e-4 * steps)
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(int(gate_s * 2.0e9))       # ~gate_s at the 2 GHz SM clock
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+        advance()
+        with torch.cuda.stream(stream):
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def refine_tiles(sim, torch, flush, tiles, steps=24):
+    """In-place refinement of the autotuner's choice on an L2-resident
+    lattice: lbm_autotune times each kind's variants back to back on the
+    live state, where every launch after the first finds the state in L2,
+    while a bench step starts from a flushed L2.  Time whole flushed steps
+    (graph replays) for the tile heights of the kinds that run every step
+    and keep the fastest; the live state is advanced by these steps, which
+    leaves the workload unchanged in kind (the timed region follows).
+    Returns the refined choices."""
+    stream = sim.stream
+    kinds = ["phase", "transport"] if sim.fused else ["phase", "transfer", "scalar_U"]
+    for kind in kinds:
+        best, best_v = None, tiles[kind]
+        for v in sorted({4, 8, 16, tiles[kind]}):
+            sim.set_tile(kind, v)
+            sim.advance(STEP_BASE)                    # capture with this variant
+            torch.cuda.synchronize()
+            ms = sorted(gated_steps(torch, stream, flush, lambda: sim.advance(STEP_BASE), steps))[steps // 2]
+            if best is None or ms < best:
+                best, best_v = ms, v
+        sim.set_tile(kind, best_v)
+        tiles[kind] = best_v
+    return tiles
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -332,6 +379,8 @@ def run_ours(args):
     for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
         sim.advance(STEP_BASE)
     tiles = sim.autotune(reps=10)
+    if nodes * 200 < 126 * 2 ** 20 and not args.tile:     # state in L2: refine on flushed steps
+        tiles = refine_tiles(sim, torch, flush, tiles)
     for spec in args.tile or []:            # fixed kernel variants (profiling runs)
         kind, v = spec.split("=")
         sim.set_tile(kind, int(v))
@@ -354,18 +403,11 @@ def run_ours(args):
     def timed_region():
         """args.steps steps, L2 flushed before each, CUDA events around each
         step on the library stream; returns (total ms, wall s)."""
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         barrier()
         w0 = time.perf_counter()
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(k))
-                ev[k][0].record(stream)
-            sim.advance(STEP_BASE)
-            with torch.cuda.stream(stream):
-                ev[k][1].record(stream)
+        t = gated_steps(torch, stream, flush, lambda: sim.advance(STEP_BASE), args.steps)
         barrier()
-        return sum(a.elapsed_time(b) for a, b in ev), time.perf_counter() - w0
+        return sum(t), time.perf_counter() - w0
 
     # the timed region: graphs without timing nodes (an event-record node
     # around a launch inside a graph adds several microseconds per launch)
@@ -437,6 +479,8 @@ def run_ours(args):
             "tiles": {k: tiles[k] for k in kinds},
             "gpu_launches": gpu_launches,
             "wall_s_timed_region": wall,
+            "timing": "CUDA events around each step's advance on the library stream; the steps are queued "
+                      "behind a bounded sleep kernel (included in wall_s_timed_region, not in value)",
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps, "calls": "init_fields(host f64 x6) + advance(2) + field(phi -> host)"},
@@ -473,19 +517,12 @@ def d2q5_variant(args, torch, lbm, local, dev, flush_bytes):
     for _ in range(max(args.warmup, 3)):
         sim.advance(STEP_BASE)
     tiles = sim.autotune(reps=10)
+    if p.nx * p.ny * 200 < 126 * 2 ** 20:
+        tiles = refine_tiles(sim, torch, flush, tiles)
     sim.advance(STEP_BASE)
     steps = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.synchronize()
-    for k in range(steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(float(k))
-            ev[k][0].record(stream)
-        sim.advance(STEP_BASE)
-        with torch.cuda.stream(stream):
-            ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms = sum(gated_steps(torch, stream, flush, lambda: sim.advance(STEP_BASE), steps))
     fused = sim.fused
     sim.close()
     del flush
