@@ -117,7 +117,11 @@ def period_bytes(p, prec="f32"):
 # hash to TRAFFIC_SOURCE_SHA; after any change the traffic is null until
 # re-measured.
 TRAFFIC_SOURCE_SHA = "9d26614e1a4774c8"
-TRAFFIC_PER_LAUNCH_512 = {"transport:8": 20015104.0, "phase:4": 11563520.0}
+# (transport: the mean of the period's two kinds of launch, transfer + U
+# alone and transfer + U + T + flow, like the algorithmic bytes it is set
+# against)
+TRAFFIC_PER_LAUNCH_512 = {"q5:transport:8": 14232736.0, "q5:transport:16": 14231744.0, "q5:phase:4": 7365120.0,
+                          "q5:phase:8": 7362560.0}
 TRAFFIC_PER_NODE_2048 = {
     "q5:flow:1008": 83.52, "q5:flow:1016": 82.92, "q5:flow:1032": 82.47, "q5:phase:1008": 39.14,
     "q5:phase:1016": 38.25, "q5:phase:1032": 37.73, "q5:scalar_T:1008": 28.44, "q5:scalar_T:1016": 27.27,
@@ -162,7 +166,7 @@ STORAGE_LABEL = {"f64": "FP64", "f32": "FP32", "f16dev": "FP32 arithmetic, FP16 
                  "bf16dev": "FP32 arithmetic, BF16 deviation storage"}
 
 
-def workload(n=None, q=9):
+def workload(n=None, q=5):
     wl = W.thermosolutal_convection(n=n or N_LATTICE, R=8.0)
     wl.params.q_scalar = q
     return wl
@@ -300,11 +304,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(target_s: float = 12.0, max_steps: int = 400):
+def cpu_baseline(target_s: float = 12.0, max_steps: int = 400, q: int = 5):
     """The FP64 oracle on the host cores, on a bounded sample of the workload:
     the full 512^2 lattice advanced for as many base steps as fit in ~target_s."""
     import oracle
-    wl = workload()
+    wl = workload(None, q)
     o = oracle.Oracle(wl.params, wl.fields)
     t0 = time.perf_counter()
     steps = 0
@@ -324,7 +328,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    wl = workload()
+    wl = workload(None, args.q_scalar)
     o = oracle.Oracle(wl.params, wl.fields)
     for _ in range(args.warmup):
         o.advance(STEP_BASE)
@@ -401,8 +405,11 @@ def run_ours(args):
     dom = max(kinds, key=lambda k: pre[k][0])
 
     def timed_region():
-        """args.steps steps, L2 flushed before each, CUDA events around each
+        """args.steps steps from the initial state (re-initialised, untimed,
+        so that every timed region covers the first 2 * steps base steps of
+        the workload), L2 flushed before each step, CUDA events around each
         step on the library stream; returns (total ms, wall s)."""
+        sim.init_fields(wl.fields)
         barrier()
         w0 = time.perf_counter()
         t = gated_steps(torch, stream, flush, lambda: sim.advance(STEP_BASE), args.steps)
@@ -431,6 +438,7 @@ def run_ours(args):
     ms_instr, _ = timed_region()
     ktimes = sim.timing_read(reset=True)
     sim.timing_enable([])
+    state_finite = not sim.diagnostics()["nonfinite"]
 
     # roofline of the dominant kernel (largest share of the timed kernel time)
     dom_ms, dom_n = ktimes[dom]
@@ -438,9 +446,8 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = algo[dom] * nodes / avg_s / 1e9
     traffic = None
-    if args.lattice in (None, N_LATTICE) and prec == "f32" and args.q_scalar == 9 and \
-            TRAFFIC_SOURCE_SHA == kernel_source_sha():
-        traffic = TRAFFIC_PER_LAUNCH_512.get("%s:%d" % (dom, tiles[dom]))
+    if args.lattice in (None, N_LATTICE) and prec == "f32" and TRAFFIC_SOURCE_SHA == kernel_source_sha():
+        traffic = TRAFFIC_PER_LAUNCH_512.get("q%d:%s:%d" % (args.q_scalar, dom, tiles[dom]))
 
     # end to end through the public API with pinned host buffers
     host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in wl.fields.items()}
@@ -479,6 +486,7 @@ def run_ours(args):
             "tiles": {k: tiles[k] for k in kinds},
             "gpu_launches": gpu_launches,
             "wall_s_timed_region": wall,
+            "state_finite_after_timed_regions": state_finite,
             "timing": "CUDA events around each step's advance on the library stream; the steps are queued "
                       "behind a bounded sleep kernel (included in wall_s_timed_region, not in value)",
             "clocks": clk,
@@ -490,22 +498,25 @@ def run_ours(args):
     if rank == 0:
         if not args.no_large and world == 1:
             line["large_lattice"] = large_lattice(args, torch, lbm, local, measured_peaks, args.q_scalar)
-        if not args.no_d2q5 and world == 1 and args.q_scalar == 9:
-            line["d2q5"] = d2q5_variant(args, torch, lbm, local, dev, flush_bytes=512 * 1024 * 1024)
+        if not args.no_alt_lattice and world == 1:
+            alt = 9 if args.q_scalar == 5 else 5
+            line["d2q%d" % alt] = lattice_variant(args, torch, lbm, local, dev, 512 * 1024 * 1024, alt)
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(q=args.q_scalar)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
-def d2q5_variant(args, torch, lbm, local, dev, flush_bytes):
-    """The same workloads with D2Q5 phase, U and T lattices (the flow stays
-    D2Q9): the 512^2 headline configuration, timed as the main measurement
-    (CUDA events on the library stream, L2 flushed between steps), and the
-    8192^2 HBM-bound measurement with its dominant-kernel roofline."""
-    wl = workload(args.lattice, 5)
+def lattice_variant(args, torch, lbm, local, dev, flush_bytes, q):
+    """The same workloads with the other velocity set of the phase, U and T
+    lattices (q = 9: the paper's D2Q9; q = 5: D2Q5; the flow is D2Q9 in
+    both): the 512^2 configuration, timed as the main measurement (CUDA
+    events on the library stream, L2 flushed between steps, from the
+    re-initialised state), and the 8192^2 HBM-bound measurement with its
+    dominant-kernel roofline."""
+    wl = workload(args.lattice, q)
     p = wl.params
     prec = args.precision or "f32"
     sim = lbm.Simulation(p, precision=prec)
@@ -521,18 +532,20 @@ def d2q5_variant(args, torch, lbm, local, dev, flush_bytes):
         tiles = refine_tiles(sim, torch, flush, tiles)
     sim.advance(STEP_BASE)
     steps = args.steps
+    sim.init_fields(wl.fields)
     torch.cuda.synchronize()
     ms = sum(gated_steps(torch, stream, flush, lambda: sim.advance(STEP_BASE), steps))
     fused = sim.fused
+    finite = not sim.diagnostics()["nonfinite"]
     sim.close()
     del flush
     nodes = p.nx * p.ny
     out = {"workload": workload_label(p, prec), "value": nodes * STEP_BASE * steps / (ms * 1e-3) / 1e6,
            "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "fused_transport": fused,
            "tiles": {k: tiles[k] for k in ("phase", "transfer", "scalar_U", "scalar_T", "flow", "transport")},
-           "l2": "flushed between steps (512 MiB write)"}
+           "l2": "flushed between steps (512 MiB write)", "state_finite_after_timed_region": finite}
     if not args.no_large:
-        out["large_lattice"] = large_lattice(args, torch, lbm, local, measured_peaks, 5)
+        out["large_lattice"] = large_lattice(args, torch, lbm, local, measured_peaks, q)
     return out
 
 
@@ -748,9 +761,165 @@ def run_sweep(args):
     return 0
 
 
+def run_configs(args):
+    """The workload list's cases at their stated lengths, with the outputs
+    each one names (physics results of the CUDA path; parity against the
+    oracle is the tests' job):
+
+    * thermal free dendrite, 128^2 periodic, FP64, N_T in {1, 2}, 2000 base
+      steps, on the D2Q9 and the D2Q5 phase / temperature lattices: tip
+      position history (every 20 steps), tip velocity over the last 500
+      steps, enthalpy drift;
+    * thermosolutal free dendrite with forced convection, 512^2, 20 000 base
+      steps, FP64 and FP32, on D2Q9 and D2Q5: upstream (-x, facing the inlet)
+      and downstream (+x) tip velocities over the last 2000 steps, solute
+      drift R_M, FP32 against FP64;
+    * directional solidification, 1024 x 2048, frozen pulled gradient, Le in
+      {1, 10, 100, 1000} (N_U = Le), 200 000 base steps, FP32 storage and
+      FP16 deviation storage: front height, R_M, finiteness;
+    * large multi-dendrite growth with convection, 8192^2, 50 000 base steps,
+      FP32, D2Q5 and D2Q9: R_M and the step-level algorithmic HBM throughput.
+    A run whose fields turn non-finite stops there and reports the base step
+    of the first diagnostics call that saw it."""
+    import torch
+    import paper_2609_25670_b300 as lbm
+
+    def timed(sim, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(sim.stream):
+            e0.record(sim.stream)
+        sim.advance(n)
+        with torch.cuda.stream(sim.stream):
+            e1.record(sim.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    def history(sim, total, every):
+        """Tip history sampled every `every` base steps; stops at the first
+        sample that sees a non-finite field (returns its base step, else None)."""
+        hist, ms, bad = [], 0.0, None
+        for k in range(total // every):
+            ms += timed(sim, every)
+            d = sim.diagnostics()
+            if d["nonfinite"]:
+                bad = (k + 1) * every
+                break
+            hist.append(d["tip"].copy())
+        return np.asarray(hist), ms, d, bad
+
+    def chunked(sim, total, chunk):
+        """advance in chunks with a finiteness check after each"""
+        ms, bad, done = 0.0, None, 0
+        while done < total:
+            n = min(chunk, total - done)
+            ms += timed(sim, n)
+            done += n
+            d = sim.diagnostics()
+            if d["nonfinite"]:
+                bad = done
+                break
+        return ms, d, bad, done
+
+    out = {}
+    # 1. thermal free dendrite
+    rows = []
+    for q in (9, 5):
+        for NT in (1, 2):
+            wl = W.thermal_free_dendrite(n=128, N_T=NT)
+            wl.params.q_scalar = q
+            sim = lbm.Simulation(wl.params, precision="f64")
+            sim.init_fields(wl.fields)
+            d0 = sim.diagnostics()
+            h, ms, d, bad = history(sim, 2000, 20)
+            sim.close()
+            rows.append({"lattice": "D2Q%d" % q, "N_T": NT, "storage": "f64",
+                         "v_tip": float(((h[-1] - h[-1 - min(25, len(h) - 1)]) / (20.0 * min(25, len(h) - 1))).mean()),
+                         "tip_last": h[-1].tolist(),
+                         "H_drift_rel": (d["H"] - d0["H"]) / abs(d0["H"]), "nonfinite_at_base_step": bad,
+                         "mlups": 128 * 128 * 20 * len(h) / (ms * 1e-3) / 1e6})
+    out["thermal_dendrite_128"] = rows
+    # 2. thermosolutal + convection
+    rows = []
+    for q, prec in ((9, "f64"), (9, "f32"), (5, "f64"), (5, "f32")):
+        wl = W.thermosolutal_convection(n=512, R=8.0)
+        wl.params.q_scalar = q
+        sim = lbm.Simulation(wl.params, precision=prec)
+        sim.init_fields(wl.fields)
+        m0 = sim.diagnostics()["M_C"]
+        sim.autotune(reps=3)                             # on the live state, which it leaves unchanged
+        h, ms, d, bad = history(sim, 20000, 200)         # 100 samples, the last at step 20 000
+        sim.close()
+        m = min(10, len(h) - 1)
+        v = (h[-1] - h[-1 - m]) / (m * 200)             # the last 2000 finite base steps (fewer if cut short)
+        rows.append({"lattice": "D2Q%d" % q, "storage": prec, "base_steps": 200 * len(h),
+                     "v_tip_downstream_+x": float(v[0]), "v_tip_upstream_-x": float(v[2]),
+                     "v_tip_+y": float(v[1]), "v_tip_-y": float(v[3]), "tips_last": h[-1].tolist(),
+                     "R_M": (d["M_C"] - m0) / m0 if bad is None else None, "nonfinite_at_base_step": bad,
+                     "mlups": 512 * 512 * 200 * len(h) / (ms * 1e-3) / 1e6})
+    for r in rows:
+        ref = next(x for x in rows if x["lattice"] == r["lattice"] and x["storage"] == "f64")
+        if r is not ref:
+            r["v_tip_rel_diff_vs_f64"] = {k: abs(r[k] - ref[k]) / abs(ref[k])
+                                          for k in ("v_tip_downstream_+x", "v_tip_upstream_-x")}
+    out["thermosolutal_convection_512"] = rows
+    # 3. directional Le sweep
+    rows = []
+    for Le in (1, 10, 100, 1000):
+        wl = W.directional_saline(Le=Le)
+        for prec in ("f32", "f16dev"):
+            sim = lbm.Simulation(wl.params, precision=prec)
+            sim.init_fields(wl.fields)
+            m0 = sim.diagnostics()["M_C"]
+            period = max(1, Le)
+            sim.advance(2 * period)
+            sim.autotune(reps=2)
+            n = 200000 - 2 * period
+            ms, d, bad, done = chunked(sim, n, 20000)
+            sim.close()
+            rows.append({"Le": Le, "N_U": Le, "storage": prec, "base_steps": 2 * period + done,
+                         "front_height": float(d["tip"][1]) if bad is None else None,
+                         "R_M": (d["M_C"] - m0) / m0 if bad is None else None, "nonfinite_at_base_step": bad,
+                         "mlups": wl.params.nx * wl.params.ny * done / (ms * 1e-3) / 1e6})
+    out["directional_1024x2048"] = rows
+    # 4. large multi-dendrite
+    rows = []
+    for q in (5, 9):
+        p, pts = W.multi_dendrite_params(8192)
+        p.q_scalar = q
+        sim = lbm.Simulation(p, precision="f32")
+        sim.init_seed([{"kind": "circle", "x": float(x), "y": float(y), "r": 8.0} for x, y in pts], U0=0.0,
+                      T0=-0.55)
+        m0 = sim.diagnostics()["M_C"]
+        sim.autotune(reps=3)
+        ms, d, bad, done = chunked(sim, 50000, 5000)
+        fused = sim.fused
+        sim.close()
+        ab = algo_bytes("f32", q)
+        step_bytes = ab["phase"] + ab["transfer"] + ab["scalar_U"] + ab["scalar_T"] / p.N_T + ab["flow"] / p.N_F
+        nodes = p.nx * p.ny
+        gbs = step_bytes * nodes * done / (ms * 1e-3) / 1e9
+        peak, peak_kind = measured_peaks()
+        rows.append({"lattice": "D2Q%d" % q, "storage": "f32", "base_steps": done,
+                     "R_M": (d["M_C"] - m0) / m0 if bad is None else None, "nonfinite_at_base_step": bad,
+                     "fused_transport": fused, "mlups": nodes * done / (ms * 1e-3) / 1e6,
+                     "step_algo_GBs": gbs if not fused else None, "peak": peak,
+                     "frac": gbs / peak if not fused else None, "peak_kind": peak_kind})
+    out["multi_dendrite_8192"] = rows
+    line = {"metric": METRIC + " (workload list, full lengths)",
+            "value": rows[0]["mlups"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded)",
+            "config": {"workload": "8192x8192 multi-dendrite, D2Q5 phase/U/T, 50 000 base steps (value); "
+                                   "the other cases in the details"},
+            "results": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="convection512", choices=["convection512", "ensemble", "sweep"],
+    ap.add_argument("--workload", default="convection512", choices=["convection512", "ensemble", "sweep", "configs"],
                     help="convection512: the reported workload; ensemble: batched-ensemble measurement; "
                          "sweep: update-factor sweeps (thermal dendrite N_T, directional Le)")
     ap.add_argument("--members", type=int, default=64)
@@ -767,9 +936,11 @@ def main():
                          "or the autotuner's choice (auto)")
     ap.add_argument("--tile", action="append", metavar="KIND=V",
                     help="fix a kernel variant after autotuning (profiling runs): V > 0 tile height, V < 0 strip height")
-    ap.add_argument("--q-scalar", type=int, default=9, choices=[9, 5],
-                    help="velocities of the phase, U and T lattices: 9 (the paper's D2Q9) or 5 (D2Q5)")
-    ap.add_argument("--no-d2q5", action="store_true", help="skip the D2Q5 variant measurement")
+    ap.add_argument("--q-scalar", type=int, default=5, choices=[9, 5],
+                    help="velocities of the phase, U and T lattices: 5 (D2Q5, as the workload list states "
+                         "them; default) or 9 (the paper's D2Q9)")
+    ap.add_argument("--no-alt-lattice", action="store_true",
+                    help="skip the measurement on the other velocity set")
     ap.add_argument("--lattice", type=int, default=None,
                     help="lattice size override for profiling runs (the reported workload is 512)")
     args = ap.parse_args()
@@ -779,6 +950,8 @@ def main():
         return run_ensemble(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "configs":
+        return run_configs(args)
     return run_ours(args)
 
 
