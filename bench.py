@@ -122,6 +122,10 @@ TRAFFIC_SOURCE_SHA = "9d26614e1a4774c8"
 # against)
 TRAFFIC_PER_LAUNCH_512 = {"q5:transport:8": 14232736.0, "q5:transport:16": 14231744.0, "q5:phase:4": 7365120.0,
                           "q5:phase:8": 7362560.0}
+# measured directly on an 8192^2 lattice (single-pass counters; the traffic
+# of a vector-strip launch does not depend on the data), FP32
+TRAFFIC_PER_NODE_8192 = {"q5:phase:1016": 48.17, "q5:transfer:1016": 23.79, "q5:scalar_U:1016": 36.04,
+                         "q5:scalar_T:1016": 36.03, "q5:flow:1016": 92.64}
 TRAFFIC_PER_NODE_2048 = {
     "q5:flow:1008": 83.52, "q5:flow:1016": 82.92, "q5:flow:1032": 82.47, "q5:phase:1008": 39.14,
     "q5:phase:1016": 38.25, "q5:phase:1032": 37.73, "q5:scalar_T:1008": 28.44, "q5:scalar_T:1016": 27.27,
@@ -618,10 +622,13 @@ def large_lattice(args, torch, lbm, local, peaks_fn, q=9):
     dom_algo["transport"] = tb / max(tn, 1)
     avg_s = kt[dom][0] * 1e-3 / max(kt[dom][1], 1)
     dom_gbs = dom_algo[dom] * nodes / avg_s / 1e9
-    traffic = None
-    per_node = TRAFFIC_PER_NODE_2048.get("q%d:%s:%d" % (q, dom, tiles[dom]))
-    if per_node is not None and prec == "f32" and TRAFFIC_SOURCE_SHA == kernel_source_sha():
-        traffic = per_node * nodes
+    traffic, traffic_note = None, None
+    key = "q%d:%s:%d" % (q, dom, tiles[dom])
+    if prec == "f32" and TRAFFIC_SOURCE_SHA == kernel_source_sha():
+        if key in TRAFFIC_PER_NODE_8192:
+            traffic, traffic_note = TRAFFIC_PER_NODE_8192[key] * nodes, "8192^2 capture of this variant"
+        elif key in TRAFFIC_PER_NODE_2048:
+            traffic, traffic_note = TRAFFIC_PER_NODE_2048[key] * nodes, "2048^2 capture scaled by nodes (a lower bound: part of a 2048^2 launch hits L2)"
     return {"workload": "8192x8192 multi-dendrite thermosolutal growth with convection, 32 seeds, N=(1,1,4,2), "
                         + lattice_label(p) + ", " + STORAGE_LABEL[prec], "storage": prec,
             "value": nodes * base / (ms * 1e-3) / 1e6, "unit": UNIT, "base_steps": base,
@@ -629,7 +636,7 @@ def large_lattice(args, torch, lbm, local, peaks_fn, q=9):
             "step": {"algo_bytes_per_node_per_base_step": step_bytes, "achieved_GBs": gbs, "peak": peak,
                      "frac": gbs / peak, "peak_kind": peak_kind},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
-                         "frac": dom_gbs / peak, "traffic": traffic, "traffic_note": "2048^2 capture scaled by nodes",
+                         "frac": dom_gbs / peak, "traffic": traffic, "traffic_note": traffic_note,
                          "algo_bytes_per_node": dom_algo[dom], "avg_launch_us": avg_s * 1e6,
                          "launches_timed": kt[dom][1]},
             "kernel_avg_us_prepass": {k: pre[k][0] / max(pre[k][1], 1) * 1e3 for k in kinds},
