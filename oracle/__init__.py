@@ -75,6 +75,8 @@ def _load():
             getattr(lib, nm).argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, dp]
         lib.orc_matrices.argtypes = [dp, dp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
         lib.orc_collide_scalar.argtypes = [dp, dp, C.c_double, C.c_double, dp]
+        lib.orc_aniso_frame.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, dp, dp, dp]
+        lib.orc_set_orientation.argtypes = [C.c_void_p, C.c_void_p]
         lib.orc_collide_scalar_q.argtypes = [C.c_int, dp, dp, C.c_double, C.c_double, dp]
         lib.orc_matrices5.argtypes = [dp, dp, dp]
         for nm in ("orc_feq_scalar_q", "orc_meq_scalar_q", "orc_feq_phase_q", "orc_meq_phase_q"):
@@ -127,6 +129,15 @@ class Oracle:
         self.set_fields(fields)
 
     def set_fields(self, fields: Dict[str, np.ndarray]):
+        """Initial macroscopic fields; an optional "theta" entry is the
+        per-node crystal angle of the grains (R-orientation)."""
+        th = fields.get("theta")
+        if th is not None:
+            th = np.ascontiguousarray(th, dtype=np.float64)
+            assert th.shape == (self.ny, self.nx)
+            self._lib.orc_set_orientation(self._h, th.ctypes.data)
+        else:
+            self._lib.orc_set_orientation(self._h, None)
         arrs = [np.ascontiguousarray(fields[k], dtype=np.float64) for k in ("phi", "U", "T", "ux", "uy", "rho")]
         for a in arrs:
             assert a.shape == (self.ny, self.nx)
@@ -252,3 +263,11 @@ def num_threads() -> int:
 
 def set_threads(n: int):
     _load().orc_set_threads(int(n))
+
+
+def aniso_frame(gx: float, gy: float, eps: float, vartheta: float):
+    """(a_s, N_x, N_y) of Eqs. 2-3 in the frame of a crystal turned by vartheta."""
+    lib = _load()
+    a, nx, ny = C.c_double(), C.c_double(), C.c_double()
+    lib.orc_aniso_frame(gx, gy, eps, vartheta, C.byref(a), C.byref(nx), C.byref(ny))
+    return a.value, nx.value, ny.value

@@ -35,6 +35,11 @@
  *   R-frozen prescribed theta(y, t) = theta_c + G (y - y0 - V t) with t the
  *            time at the start of the base step.
  *   R-d2q5   the five-velocity option of the scalar lattices (see WQ5 / MM5).
+ *   R-orientation  grains of different crystal orientation (the multi-
+ *            dendrite case): Eq. 2 is written for crystal axes along x and y;
+ *            a node of a grain turned by vartheta evaluates Eqs. 2-3 on its
+ *            gradient turned into the crystal frame and turns N back
+ *            (orc_aniso_frame).  Without an orientation field: Eq. 2 as printed.
  *   R-dirichlet  the cold bottom wall kept at T_b (Sec. 4.4): anti-bounce-back
  *            at the half-way wall below row 0, f_i = -f*_opp(i) + 2 w_i T_b
  *            for the links that enter row 0 from below; phi and U keep zero
@@ -171,6 +176,7 @@ typedef struct {
     double *as2;           /* nn */
     double *Jx, *Jy, *dU, *dT;
     double *accU, *accT;   /* accumulated-coupling stores */
+    double *ori;           /* crystal angle of each node's grain, or NULL (axis-aligned Eq. 2) */
     double S_phi, J_U;     /* maxima since the last diagnostics read */
 } orc_sim;
 
@@ -243,6 +249,25 @@ void orc_aniso(double gx, double gy, double eps, double* as, double* Nx, double*
     *as = a;
     *Nx = g2 * a * dax;
     *Ny = g2 * a * day;
+}
+
+/* Eqs. 2-3 in the frame of a crystal whose axes are turned by vartheta
+ * (R-orientation): the gradient is taken into the crystal frame,
+ * g' = R(-vartheta) g, Eq. 2 and Eq. 3 are evaluated there, and N is turned
+ * back, N = R(vartheta) N'.  With vartheta = 0 this is orc_aniso. */
+void orc_aniso_frame(double gx, double gy, double eps, double vartheta, double* as, double* Nx, double* Ny) {
+    const double c = cos(vartheta), sn = sin(vartheta);
+    const double Rm[2][2] = {{c, sn}, {-sn, c}};     /* R(-vartheta) */
+    const double gpx = Rm[0][0] * gx + Rm[0][1] * gy, gpy = Rm[1][0] * gx + Rm[1][1] * gy;
+    double Npx, Npy;
+    orc_aniso(gpx, gpy, eps, as, &Npx, &Npy);
+    *Nx = Rm[0][0] * Npx + Rm[1][0] * Npy;             /* R(vartheta) = R(-vartheta)^T */
+    *Ny = Rm[0][1] * Npx + Rm[1][1] * Npy;
+}
+
+static void aniso_at(const orc_sim* s, int n, double gx, double gy, double* as, double* Nx, double* Ny) {
+    if (s->ori) orc_aniso_frame(gx, gy, s->p.eps, s->ori[n], as, Nx, Ny);
+    else orc_aniso(gx, gy, s->p.eps, as, Nx, Ny);
 }
 
 static double theta_at(const orc_sim* s, int node, int y, double t) {
@@ -423,7 +448,16 @@ void orc_destroy(orc_sim* s) {
     free(s->phi); free(s->phi_new); free(s->U); free(s->T); free(s->ux); free(s->uy); free(s->rho);
     free(s->post); free(s->as2); free(s->Jx); free(s->Jy); free(s->dU); free(s->dT);
     free(s->accU); free(s->accT);
+    free(s->ori);
     free(s);
+}
+
+/* Per-node crystal angle (ny x nx, row-major), or NULL for the axis-aligned
+ * form; set it before orc_set_fields, whose phase equilibria use it. */
+void orc_set_orientation(orc_sim* s, const double* vartheta) {
+    if (!vartheta) { free(s->ori); s->ori = NULL; return; }
+    if (!s->ori) s->ori = (double*)malloc((size_t)s->nn * 8);
+    memcpy(s->ori, vartheta, (size_t)s->nn * 8);
 }
 
 /* Initial distributions f = f_eq of the initial macroscopic fields. For phi
@@ -448,7 +482,7 @@ void orc_set_fields(orc_sim* s, const double* phi, const double* U, const double
             int n = y * p->nx + x;
             double feq[9], gx, gy, as, Nx, Ny;
             grad_iso(p, s->phi, x, y, &gx, &gy);
-            orc_aniso(gx, gy, p->eps, &as, &Nx, &Ny);
+            aniso_at(s, n, gx, gy, &as, &Nx, &Ny);
             orc_feq_phase_q(q, phi[n], -p->W0 * p->W0 * Nx / p->tau0, -p->W0 * p->W0 * Ny / p->tau0, cphi, feq);
             for (int i = 0; i < q; ++i) s->f[F_PHI][0][i * nn + n] = feq[i];
             double vx = p->has_flow ? ux[n] : 0.0, vy = p->has_flow ? uy[n] : 0.0;
@@ -482,7 +516,7 @@ static void phase_step(orc_sim* s, double t) {
             int n = y * p->nx + x;
             double gx, gy, as, Nx, Ny;
             grad_iso(p, s->phi, x, y, &gx, &gy);
-            orc_aniso(gx, gy, p->eps, &as, &Nx, &Ny);
+            aniso_at(s, n, gx, gy, &as, &Nx, &Ny);
             double vnx = -p->W0 * p->W0 * Nx / p->tau0, vny = -p->W0 * p->W0 * Ny / p->tau0;
             double tau = 3.0 * dt * as * as * p->W0 * p->W0 / p->tau0 + 0.5;         /* Eq. 24 */
             double ph = s->phi[n];

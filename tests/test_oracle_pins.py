@@ -663,3 +663,87 @@ def test_isotropic_growth_without_anisotropy():
     ra, rd = radius(1.0, 0.0), radius(1 / math.sqrt(2), 1 / math.sqrt(2))
     assert ra > 20.0
     assert abs(ra - rd) < 0.03 * ra, (ra, rd)
+
+
+# ---------------------------------------------------------------------------
+# Grains of different crystal orientation (the multi-dendrite case)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("vartheta", [0.0, math.pi / 8, 0.3, math.pi / 4, 1.2])
+def test_anisotropy_in_a_turned_crystal_frame(vartheta):
+    """a_s of a crystal whose axes are turned by vartheta is
+    1 + eps cos 4(alpha - vartheta) (the trigonometric form of Eq. 2 about the
+    crystal axes), and N = |grad phi|^2 a_s d a_s / d(grad phi) (Eq. 3) holds
+    in the lattice frame: checked against central differences of a_s."""
+    eps = 0.05
+    for alpha in np.linspace(0.01, 2 * math.pi, 29):
+        r = 0.3
+        gx, gy = -r * math.cos(alpha), -r * math.sin(alpha)       # n = (cos alpha, sin alpha)
+        a, Nx, Ny = oracle.aniso_frame(gx, gy, eps, vartheta)
+        assert abs(a - (1 + eps * math.cos(4 * (alpha - vartheta)))) < 1e-14
+        h = 1e-6
+        dax = (oracle.aniso_frame(gx + h, gy, eps, vartheta)[0] - oracle.aniso_frame(gx - h, gy, eps, vartheta)[0]) / (2 * h)
+        day = (oracle.aniso_frame(gx, gy + h, eps, vartheta)[0] - oracle.aniso_frame(gx, gy - h, eps, vartheta)[0]) / (2 * h)
+        assert abs(Nx - r * r * a * dax) < 1e-8
+        assert abs(Ny - r * r * a * day) < 1e-8
+
+
+def test_quarter_turned_crystal_equals_the_unturned_one():
+    """Eq. 2 has four-fold symmetry, so a grain turned by pi/2 grows exactly
+    as an unturned one (up to the rounding of cos(pi/2)); a zero angle field
+    is the axis-aligned form bit for bit."""
+    wl = W.thermal_free_dendrite(n=64, R=5.0)
+    runs = []
+    for th in (None, 0.0, 0.5 * math.pi):
+        f = dict(wl.fields)
+        if th is not None:
+            f["theta"] = np.full_like(f["phi"], th)
+        o = oracle.Oracle(wl.params, f)
+        o.advance(200)
+        runs.append(o.get("phi"))
+        o.close()
+    assert np.array_equal(runs[0], runs[1])
+    assert np.abs(runs[0] - runs[2]).max() < 1e-12
+
+
+def test_turned_crystal_grows_along_its_own_axes():
+    """A seed in a grain turned by pi/4 grows its primary arms along the
+    diagonals: after 1500 base steps its diagonal and axial radii swap roles
+    against the unturned seed's (each within 10 % of the other's, the
+    difference being the lattice's own small anisotropy)."""
+    wl = W.thermal_free_dendrite(n=128, N_T=1)
+    c = 64
+
+    def radii(theta):
+        f = dict(wl.fields)
+        if theta is not None:
+            f["theta"] = np.full_like(f["phi"], theta)
+        o = oracle.Oracle(wl.params, f)
+        o.advance(1500)
+        phi = o.get("phi")
+        o.close()
+
+        def radius(dx, dy):
+            r = 0.0
+            for t in np.arange(0.0, 63.0, 0.25):
+                i, j = int(round(c + dy * t)), int(round(c + dx * t))
+                if 0 <= i < 128 and 0 <= j < 128 and phi[i, j] > 0:
+                    r = t * math.hypot(dx, dy)
+            return r
+        return radius(1.0, 0.0), radius(1 / math.sqrt(2), 1 / math.sqrt(2))
+
+    a0, d0 = radii(None)
+    a1, d1 = radii(math.pi / 4)
+    assert a0 > d0 * 1.1 and d1 > a1 * 1.1
+    assert abs(d1 - a0) < 0.1 * a0 and abs(a1 - d0) < 0.1 * d0
+
+
+def test_grain_orientation_is_the_nearest_seed_angle():
+    """The Voronoi orientation field of the input generator against brute
+    force on a small window."""
+    pts = np.array([[10.0, 10.0], [40.0, 12.0], [25.0, 40.0]])
+    ang = np.array([0.1, 0.7, 1.3])
+    th = W.grain_orientation(pts, ang, 5, 7, 30, 20, rows=3)
+    for yy in range(20):
+        for xx in range(30):
+            d = [(5 + xx - px) ** 2 + (7 + yy - py) ** 2 for px, py in pts]
+            assert th[yy, xx] == ang[int(np.argmin(d))]

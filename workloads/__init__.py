@@ -397,9 +397,30 @@ def multi_dendrite(n: int = 8192, n_seeds: int = 32, min_dist: float = 800.0, se
     phi = np.full((n, n), -1.0)
     for (cx, cy) in pts:
         phi = np.maximum(phi, circle_seed(n, n, cx, cy, 8.0, W0))
-    angles = 0.5 * math.pi * uniform01(seed + 1, len(pts))
+    angles = multi_dendrite_angles(len(pts), seed)
     return Workload("multi_dendrite_%d" % n, p, base_fields(p, phi, U0=0.0, T0=-0.55),
                     n_base_steps, extra={"seeds": pts, "angles": angles})
+
+
+def multi_dendrite_angles(n_seeds: int, seed: int = 5) -> np.ndarray:
+    """Crystal angles of the multi-dendrite grains, uniform in [0, pi/2)
+    (the draws multi_dendrite returns in extra['angles'])."""
+    return 0.5 * math.pi * uniform01(seed + 1, n_seeds)
+
+
+def grain_orientation(pts, angles, x0: int, y0: int, w: int, h: int, rows: int = 64) -> np.ndarray:
+    """Per-node crystal angle of the window [x0, x0 + w) x [y0, y0 + h): the
+    angle of the nearest seed centre (Voronoi grains at initialisation; the
+    first seed wins a tie).  Evaluated `rows` rows at a time."""
+    pts = np.asarray(pts, dtype=np.float64).reshape(-1, 2)
+    angles = np.asarray(angles, dtype=np.float64)
+    out = np.empty((h, w), dtype=np.float64)
+    x = np.arange(x0, x0 + w, dtype=np.float64)
+    for r0 in range(0, h, rows):
+        y = np.arange(y0 + r0, y0 + min(h, r0 + rows), dtype=np.float64)
+        d2 = (x[None, :, None] - pts[None, None, :, 0]) ** 2 + (y[:, None, None] - pts[None, None, :, 1]) ** 2
+        out[r0:r0 + len(y)] = angles[np.argmin(d2, axis=2)]
+    return out
 
 
 def circle_seeds_window(p: Params, pts, R: float, x0: int, y0: int, w: int, h: int,
