@@ -246,6 +246,19 @@ lbm_status lbm_set_fusion(lbm_handle h, int32_t enable);
 /* *enabled receives 1 when base steps run the fused transport launch. */
 lbm_status lbm_get_fusion(lbm_handle h, int32_t* enabled);
 
+/* Grain orientation of simulation `sim` (the multi-dendrite case draws a
+ * crystal angle per seed; Eq. 2 is written for crystal axes along x and y).
+ * theta: ny x nx FP64, the angle of the crystal axes of the grain each node
+ * belongs to; Eqs. 2-3 are then evaluated on the phase gradient turned into
+ * that frame, g' = R(-theta) g, and N is turned back, N = R(theta) N'.
+ * NULL restores the axis-aligned Eq. 2 of the paper (the default).
+ * src_is_device: 1 if theta is device memory.  The field is kept (in the
+ * arithmetic type, allocated on first use through the handle's allocator)
+ * until replaced; it applies from the next update, and to the initial phase
+ * equilibria of a later lbm_init_seed / lbm_init_fields, so set it before
+ * them.  Synchronises the stream.  Errors: INVALID_ARG, OOM, CUDA. */
+lbm_status lbm_set_orientation(lbm_handle h, int32_t sim, const double* theta, int32_t src_is_device);
+
 /* Kernel kinds for timing and launch counts. */
 enum { LBM_K_PHASE = 0, LBM_K_TRANSFER = 1, LBM_K_SCALAR_U = 2, LBM_K_SCALAR_T = 3,
        LBM_K_FLOW = 4, LBM_K_DIAG = 5, LBM_K_INIT = 6,

@@ -32,7 +32,7 @@ EXPORTED = ["lbm_create", "lbm_init_seed", "lbm_init_fields", "lbm_advance", "lb
             "lbm_diagnostics", "lbm_last_error", "lbm_destroy", "lbm_set_graphs", "lbm_timing_enable",
             "lbm_timing_read", "lbm_launch_counts", "lbm_device_bytes", "lbm_autotune",
             "lbm_diagnostics_noalloc", "lbm_set_batching", "lbm_set_tile", "lbm_set_fusion",
-            "lbm_get_fusion"]
+            "lbm_get_fusion", "lbm_set_orientation"]
 
 
 class LbmError(RuntimeError):
@@ -113,6 +113,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.lbm_set_fusion.argtypes = [vp, i32]
     lib.lbm_get_fusion.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.lbm_diagnostics_noalloc.argtypes = [C.POINTER(lbm_params)] + [vp] * 6 + [C.POINTER(lbm_diag)]
+    lib.lbm_set_orientation.argtypes = [vp, i32, vp, i32]
     for nm in EXPORTED:
         f = getattr(lib, nm)
         if nm not in ("lbm_last_error", "lbm_destroy"):
@@ -216,9 +217,28 @@ class Simulation:
             raise LbmError(st, self.lib.lbm_last_error(self.h).decode())
 
     # ---- initialisation
+    def set_orientation(self, theta, sim: int = 0):
+        """Per-node crystal angle of the grains ((ny, nx) float64 numpy array
+        or CUDA tensor), or None for the axis-aligned anisotropy."""
+        if theta is None:
+            self._ck(self.lib.lbm_set_orientation(self.h, sim, None, 0))
+            return
+        if isinstance(theta, np.ndarray):
+            theta = np.ascontiguousarray(theta, dtype=np.float64)
+            dev = 0
+        else:
+            assert theta.dtype == self._torch.float64 and theta.is_contiguous()
+            dev = 1 if theta.is_cuda else 0
+            if dev:
+                self.stream.wait_stream(self._torch.cuda.current_stream())
+        self._ck(self.lib.lbm_set_orientation(self.h, sim, C.c_void_p(_ptr(theta)), dev))
+
     def init_fields(self, fields: Dict, sim: int = 0):
         """fields: phi, U, T, ux, uy, rho as (ny, nx) float64 host numpy arrays,
-        or contiguous float64 CUDA tensors (all of one kind)."""
+        or contiguous float64 CUDA tensors (all of one kind); an optional
+        "theta" entry sets the grain orientation first (set_orientation)."""
+        if "theta" in fields:
+            self.set_orientation(fields["theta"], sim)
         keys = ("phi", "U", "T", "ux", "uy", "rho")
         arrs = []
         dev = 0

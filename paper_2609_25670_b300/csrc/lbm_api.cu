@@ -67,6 +67,8 @@ struct SimState {
     void* rho[2] = {};
     void* accU = nullptr;
     void* accT = nullptr;
+    void* ori_buf = nullptr;             // grain angles in the arithmetic type (allocated on first use)
+    void* ori = nullptr;                 // ori_buf when an orientation field is set, else null
     bool acc_reset_U = true, acc_reset_T = true;
     unsigned long long* smax = nullptr;  // [S_phi, J_U] as double bits
     long long* clock = nullptr;          // base step at the start of a graph replay
@@ -296,6 +298,7 @@ template <typename R> KP<R> make_kp(const SimState& s) {
     k.dt_base = (R)p.dt_base;
     k.T_dir_ym = s.has_T && p.T_ymin_dirichlet;
     k.T_ymin = (R)p.T_ymin;
+    k.ori = (const R*)s.ori;
     return k;
 }
 
@@ -1698,6 +1701,45 @@ lbm_status lbm_launch_counts(lbm_handle h, int64_t* counts) {
     if (!h || !counts) return fail(h, LBM_E_INVALID_ARG, "NULL argument");
     for (int k = 0; k < LBM_K_COUNT; ++k) counts[k] = h->launches[k];
     return LBM_OK;
+}
+
+lbm_status lbm_set_orientation(lbm_handle h, int32_t sim, const double* theta, int32_t src_is_device) {
+    if (!h) return fail(nullptr, LBM_E_INVALID_ARG, "handle is NULL");
+    if (sim < 0 || sim >= (int)h->sims.size()) return fail(h, LBM_E_INVALID_ARG, "sim index %d out of range", sim);
+    SimState& s = h->sims[sim];
+    const size_t rs = real_size(h->precision);
+    if (!theta) {
+        s.ori = nullptr;
+    } else {
+        if (!s.ori_buf) {
+            lbm_status st = dev_alloc(h, s.nn * rs, &s.ori_buf);
+            if (st) return st;
+        }
+        const size_t n = (size_t)s.nx * s.ny, need = n * sizeof(double);
+        if (h->staging_bytes < need) {
+            void* p = nullptr;
+            lbm_status st = dev_alloc(h, need, &p);
+            if (st) return st;
+            h->staging = (double*)p;
+            h->staging_bytes = need;
+        }
+        CK(cudaMemcpyAsync(h->staging, theta, need, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           h->stream));
+        const dim3 blk(32, 8), grd((s.nx + 31) / 32, (s.ny + 7) / 8);
+        if (h->precision == LBM_PREC_F64)
+            k_from_f64<double><<<grd, blk, 0, h->stream>>>(h->staging, (double*)s.ori_buf, s.nx, s.ny, s.pitch);
+        else
+            k_from_f64<float><<<grd, blk, 0, h->stream>>>(h->staging, (float*)s.ori_buf, s.nx, s.ny, s.pitch);
+        CK(cudaGetLastError());
+        s.ori = s.ori_buf;
+    }
+    // the coefficient block carries the pointer; kernels read it at every launch
+    if (h->precision == LBM_PREC_F64) {
+        const KP<double> k = make_kp<double>(s);
+        return upload_sync(h, s.dkp, &k, sizeof k);
+    }
+    const KP<float> k = make_kp<float>(s);
+    return upload_sync(h, s.dkp, &k, sizeof k);
 }
 
 lbm_status lbm_device_bytes(lbm_handle h, size_t* bytes) {

@@ -26,7 +26,8 @@ __global__ void k_init(const KP<R> P, int q, const R* __restrict__ phi, const R*
     const R gxv = (s[1][2] - s[1][0]) * (R(1) / R(3)) + (s[2][2] - s[2][0] + s[0][2] - s[0][0]) * (R(1) / R(12));
     const R gyv = (s[2][1] - s[0][1]) * (R(1) / R(3)) + (s[2][2] + s[2][0] - s[0][2] - s[0][0]) * (R(1) / R(12));
     R as, Nx, Ny;
-    aniso(gxv, gyv, P.eps, as, Nx, Ny);
+    if (P.ori) aniso_frame(gxv, gyv, P.eps, P.ori[node], as, Nx, Ny);     // grain frame
+    else aniso(gxv, gyv, P.eps, as, Nx, Ny);
     const R bx = -P.dtp * P.W0sq_tau0 * Nx, by = -P.dtp * P.W0sq_tau0 * Ny;
     const R ph = s[1][1];
     R vx = R(0), vy = R(0);

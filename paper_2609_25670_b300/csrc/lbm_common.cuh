@@ -60,6 +60,8 @@ template <typename R> struct KP {
     // bottom wall held at T = T_ymin (anti-bounce-back) instead of zero flux
     int T_dir_ym;
     R T_ymin;
+    // crystal angle of each node's grain (pitch layout), or null: Eq. 2 axis-aligned
+    const R* ori;
 };
 
 // Reciprocal.  FP32: the hardware approximation (PTX rcp.approx.ftz.f32,
@@ -153,6 +155,25 @@ __device__ __forceinline__ void aniso(R gx, R gy, R eps, R& as, R& Nx, R& Ny) {
     const R t = R(16) * eps * as * inv2;
     Nx = t * gx * gy2 * (gx2 - gy2);
     Ny = t * gy * gx2 * (gy2 - gx2);
+}
+
+// sin and cos of one angle: the CUDA fast single-precision intrinsic for
+// FP32 (an angle of order one, absolute error ~2^-21), the double-precision
+// library routine for FP64
+__device__ __forceinline__ void sincos_r(float x, float& s, float& c) { __sincosf(x, &s, &c); }
+__device__ __forceinline__ void sincos_r(double x, double& s, double& c) { sincos(x, &s, &c); }
+
+// Eqs. 2-3 for a grain whose crystal axes are turned by vt (grains of
+// different orientation): the gradient taken into the crystal frame,
+// g' = R(-vt) g, the anisotropy evaluated there, N turned back, N = R(vt) N'
+template <typename R>
+__device__ __forceinline__ void aniso_frame(R gx, R gy, R eps, R vt, R& as, R& Nx, R& Ny) {
+    R s, c;
+    sincos_r(vt, s, c);
+    R Npx, Npy;
+    aniso(c * gx + s * gy, c * gy - s * gx, eps, as, Npx, Npy);
+    Nx = c * Npx - s * Npy;
+    Ny = s * Npx + c * Npy;
 }
 
 // f*_i = w_i A + 3 w_i (e_i . b) + (e_i . c): the scalar collision of Eq. 14

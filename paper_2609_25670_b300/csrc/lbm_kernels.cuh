@@ -152,11 +152,12 @@ template <typename R, int TY, int Q = 9> struct PhaseSmem {
 // collision of the phase populations at halo position (lx, ly); returns a_s^2
 template <typename R, int TY, int Q>
 __device__ __forceinline__ R phase_collide(const KP<R>& P, const R (*sphi)[36], R (*sp)[TY + 2][34], int lx, int ly,
-                                           int gy, R jx, R jy, R Us, R Tv, R tnow) {
+                                           int gy, R jx, R jy, R Us, R Tv, R tnow, R ori) {
     const R c = sphi[ly + 1][lx + 1];
     R gxv, gyv, as, Nx, Ny;
     iso_grad<R, 36>(sphi, lx + 1, ly + 1, gxv, gyv);
-    aniso(gxv, gyv, P.eps, as, Nx, Ny);
+    if (P.ori) aniso_frame(gxv, gyv, P.eps, ori, as, Nx, Ny);     // grain frame
+    else aniso(gxv, gyv, P.eps, as, Nx, Ny);
     const R a2 = as * as;
     const R s = rcp(R(3) * P.dtp * a2 * P.W0sq_tau0 + R(0.5));                   // Eq. 24
     R th;
@@ -204,11 +205,16 @@ __device__ __forceinline__ void phase_tile(PhaseSmem<R, TY, Q>& sm, const KP<R>&
         if (P.has_U) Ub = Um[nb];
         if (P.has_T) Tb = Tm[nb];
     }
+    R Oa = R(0), Ob = R(0);                      // grain angles
+    if (P.ori) {
+        if (va) Oa = P.ori[na];
+        if (vb) Ob = P.ori[nb];
+    }
     load_phi_ring2<R, TY, IN>(P, phi, sm.phi, x0, y0, tid);
     __syncthreads();
     R a2own = R(1);
-    if (va) a2own = phase_collide<R, TY, Q>(P, sm.phi, sm.post, tx + 1, ty + 1, ay, mom_x(fa), mom_y(fa), Ua, Ta, tnow);
-    if (vb) phase_collide<R, TY, Q>(P, sm.phi, sm.post, blx, bly, by, mom_x(fb), mom_y(fb), Ub, Tb, tnow);
+    if (va) a2own = phase_collide<R, TY, Q>(P, sm.phi, sm.post, tx + 1, ty + 1, ay, mom_x(fa), mom_y(fa), Ua, Ta, tnow, Oa);
+    if (vb) phase_collide<R, TY, Q>(P, sm.phi, sm.post, blx, bly, by, mom_x(fb), mom_y(fb), Ub, Tb, tnow, Ob);
     __syncthreads();
     if (!own) return;
     const int gx = x0 + tx, gy = y0 + ty;

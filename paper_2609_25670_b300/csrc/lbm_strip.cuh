@@ -972,9 +972,10 @@ __device__ __forceinline__ void transfer_vs_block(const KP<R>& P, const R* phio,
 // f_i <- f_i + (p_i(x - e_i) - f_i) / a_s^2(x), so a completed row also needs
 // its own loaded populations and a_s^2, carried from its collision.
 // ---------------------------------------------------------------------------
-// ring arrays of a phase row: populations 1..Q-1, then phi, U, T
+// ring arrays of a phase row: populations 1..Q-1, then phi, U, T and the
+// grain angle
 template <int Q> struct PA {
-    static constexpr int PHI = Q - 1, U = Q, T = Q + 1, N = Q + 2;
+    static constexpr int PHI = Q - 1, U = Q, T = Q + 1, ORI = Q + 2, N = Q + 3;
 };
 template <typename R, int Q = 9> using PRing = VRingN<R, PA<Q>::N>;
 
@@ -984,7 +985,7 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
                                              const R* __restrict__ Um, const R* __restrict__ Tm, R tnow, int s,
                                              int y0, unsigned char* __restrict__ ring) {
     using RG = PRing<R, Q>;
-    constexpr int PA_PHI = PA<Q>::PHI, PA_U = PA<Q>::U, PA_T = PA<Q>::T;
+    constexpr int PA_PHI = PA<Q>::PHI, PA_U = PA<Q>::U, PA_T = PA<Q>::T, PA_ORI = PA<Q>::ORI;
     constexpr int EB = RG::EB, NR = H + 2, D = RG::D, DIR = UP ? -1 : 1;
     constexpr int FAX = UP ? 4 : 2, FL = UP ? 8 : 5, FR = UP ? 7 : 6;     // far row: axis, from left, from right
     constexpr int NAX = UP ? 2 : 4, NL = UP ? 5 : 8, NRt = UP ? 6 : 7;    // near row (just collided)
@@ -1000,6 +1001,7 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
         fetch_vec<R>(slot + PA_PHI * 32 * EB, phi + base + DIR * pitch);
         if (P.has_U) fetch_vec<R>(slot + PA_U * 32 * EB, Um + base);
         if (P.has_T) fetch_vec<R>(slot + PA_T * 32 * EB, Tm + base);
+        if (P.ori) fetch_vec<R>(slot + PA_ORI * 32 * EB, P.ori + base);
     };
 #pragma unroll
     for (int d = 0; d < D - 1; ++d) {
@@ -1038,9 +1040,10 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
             for (int k = 0; k < VW; ++k) f[i][k] = (R)Cvt<ST>::ld(v.v[k]);
         }
         const Vec4<R> pf = sread<R>(sl + PA_PHI * 32 * EB);
-        Vec4<R> Us{}, Tv{};
+        Vec4<R> Us{}, Tv{}, Ov{};
         if (P.has_U) Us = sread<R>(sl + PA_U * 32 * EB);
         if (P.has_T) Tv = sread<R>(sl + PA_T * 32 * EB);
+        if (P.ori) Ov = sread<R>(sl + PA_ORI * 32 * EB);
         const Vec4<R>& pm = UP ? pf : pb;
         const Vec4<R>& pp = UP ? pb : pf;
         R A[VW + 2], B[VW + 2];
@@ -1057,7 +1060,8 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
             const R gxv = A[k + 2] - A[k], gyv = B[k + 1] * (R(1) / R(3)) + (B[k] + B[k + 2]) * (R(1) / R(12));
             const R c = p0.v[k];
             R as, Nx, Ny;
-            aniso(gxv, gyv, P.eps, as, Nx, Ny);
+            if (P.ori) aniso_frame(gxv, gyv, P.eps, Ov.v[k], as, Nx, Ny);    // grain frame
+            else aniso(gxv, gyv, P.eps, as, Nx, Ny);
             a2[k] = as * as;
             const R sv = rcp(R(3) * P.dtp * a2[k] * P.W0sq_tau0 + R(0.5));                // Eq. 24
             R th;

@@ -101,6 +101,16 @@ def _windows(n, pts, w, m):
     return out
 
 
+_ORI = {}
+
+
+def _full_orientation(pts, ang, n):
+    """The Voronoi grain angles of the whole n x n lattice (built once)."""
+    if n not in _ORI:
+        _ORI[n] = W.grain_orientation(pts, ang, 0, 0, n, n, rows=32)
+    return _ORI[n]
+
+
 @pytest.mark.parametrize("prec,tol,q", [("f64", 1e-10, 9), ("f32", 4e-5, 9), ("f32", 4e-5, 5)])
 def test_multi_dendrite_8192_sampled_windows(prec, tol, q):
     """8192^2 multi-dendrite growth with convection (32 seeds, N = (1, 1, 4,
@@ -113,14 +123,18 @@ def test_multi_dendrite_8192_sampled_windows(prec, tol, q):
     oracle result is the exact full-lattice result beyond that margin.
     FP32 bound: 8 steps x 20 roundings x 2^-22 (the hardware reciprocal) =
     3.8e-5 on values of order one.  q = 5: the same with D2Q5 phase, U and
-    T lattices."""
+    T lattices.  Each seed's grain has its own crystal angle (Voronoi cells
+    of the seeds, angles drawn in [0, pi/2)); the windows carry the same
+    angles."""
     from dataclasses import replace
     n, steps, w = 8192, 8, 160
     m = 6 * steps
     p, pts = W.multi_dendrite_params(n)
     p.q_scalar = q
+    ang = W.multi_dendrite_angles(len(pts))
     seeds = [{"kind": "circle", "x": float(x), "y": float(y), "r": 8.0} for x, y in pts]
     sim = lbm.Simulation(p, precision=prec)
+    sim.set_orientation(_full_orientation(pts, ang, n))          # the grains' crystal frames
     sim.init_seed(seeds, U0=0.0, T0=-0.55)
     sim.autotune(reps=1)
     sim.advance(steps)
@@ -134,7 +148,9 @@ def test_multi_dendrite_8192_sampled_windows(prec, tol, q):
     sim.close()
     for (x0, y0, (xa, xb, ya, yb)) in _windows(n, pts, w, m):
         pw = replace(p, nx=w, ny=w, tip_cx=w // 2, tip_cy=w // 2)
-        o = run_oracle(pw, W.circle_seeds_window(p, pts, 8.0, x0, y0, w, w, 0.0, -0.55), steps)
+        fw = W.circle_seeds_window(p, pts, 8.0, x0, y0, w, w, 0.0, -0.55)
+        fw["theta"] = W.grain_orientation(pts, ang, x0, y0, w, w)
+        o = run_oracle(pw, fw, steps)
         for k in active(p):
             g = full[k][y0 + ya:y0 + yb, x0 + xa:x0 + xb].cpu().numpy()
             err = np.abs(g - o[k][ya:yb, xa:xb]).max()
