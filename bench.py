@@ -46,16 +46,17 @@ POP_BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
 MACRO_BYTES = {"f64": 8, "f32": 4, "f16dev": 4, "bf16dev": 4}
 
 
-def algo_bytes(prec="f32", q=9):
+def algo_bytes(prec="f32", q=9, ori=False):
     """Algorithmic bytes per node of one launch of each update kernel: the
     stored state read and written once (phase: q - 1 populations, 8 on D2Q9
     and 4 on D2Q5; flow: 8 populations; U and T: the 2 first-moment planes),
-    each macro read / written once."""
+    each macro read / written once; with grain orientations the phase update
+    also reads each node's crystal angle."""
     pb, m = POP_BYTES[prec], MACRO_BYTES[prec]
     pops = 2 * 8 * pb
     moms = 2 * 2 * pb
     return {
-        "phase": 2 * (q - 1) * pb + 4 * m,      # pops R+W, phi^q R, U R, T R, phi^{q+1} W
+        "phase": 2 * (q - 1) * pb + (5 if ori else 4) * m,   # pops R+W, phi^q, U, T (, angle) R, phi^{q+1} W
         "transfer": 6 * m,                      # phi^q, phi^{q+1}, U, T R; U, T W
         "scalar_U": moms + 5 * m,               # j R+W, U R+W, phi R, u R (2)
         "scalar_T": moms + 5 * m,
@@ -108,33 +109,27 @@ def period_bytes(p, prec="f32"):
     return tot, n
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one ncu
-# capture per kernel variant ("kind:variant"; on 2048^2 "q<velocities of the
-# phase, U, T lattices>:kind:variant"), summarised in profiles/: per launch on
-# the 512^2 workload, and per node on 2048^2 (scaled by the nodes a
-# launch processes for the 8192^2 measurement; traffic grows with the node
-# count once the state exceeds L2).  Reported only while the kernel sources
-# hash to TRAFFIC_SOURCE_SHA; after any change the traffic is null until
-# re-measured.
-TRAFFIC_SOURCE_SHA = "9d26614e1a4774c8"
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of ncu captures
+# per kernel variant ("q<velocities of the phase, U, T lattices>:kind:variant"),
+# summarised in profiles/: per launch on the 512^2 workload, and per node on
+# 8192^2 (times the nodes a launch processes for the 8192^2 measurement).
+# Reported only while the kernel sources hash to TRAFFIC_SOURCE_SHA; after any
+# change of the code the traffic is null until re-measured.
+TRAFFIC_SOURCE_SHA = "a38fd3df4bae6066"
 # (transport: the mean of the period's two kinds of launch, transfer + U
 # alone and transfer + U + T + flow, like the algorithmic bytes it is set
 # against)
-TRAFFIC_PER_LAUNCH_512 = {"q5:transport:8": 14232736.0, "q5:transport:16": 14231744.0, "q5:phase:4": 7365120.0,
-                          "q5:phase:8": 7362560.0}
+TRAFFIC_PER_LAUNCH_512 = {"q5:transport:8": 14234304.0, "q5:transport:16": 14233312.0, "q5:phase:4": 7369003.0,
+                          "q5:phase:8": 7366827.0}
 # measured directly on an 8192^2 lattice (single-pass counters; the traffic
-# of a vector-strip launch does not depend on the data), FP32
-TRAFFIC_PER_NODE_8192 = {"q5:phase:1016": 48.17, "q5:transfer:1016": 23.79, "q5:scalar_U:1016": 36.04,
-                         "q5:scalar_T:1016": 36.03, "q5:flow:1016": 92.64}
-TRAFFIC_PER_NODE_2048 = {
-    "q5:flow:1008": 83.52, "q5:flow:1016": 82.92, "q5:flow:1032": 82.47, "q5:phase:1008": 39.14,
-    "q5:phase:1016": 38.25, "q5:phase:1032": 37.73, "q5:scalar_T:1008": 28.44, "q5:scalar_T:1016": 27.27,
-    "q5:scalar_T:1032": 27.89, "q5:scalar_U:1008": 28.29, "q5:scalar_U:1016": 27.29, "q5:scalar_U:1032": 27.85,
-    "q5:transfer:1008": 16.53, "q5:transfer:1016": 16.32, "q5:transfer:1032": 16.51, "q9:flow:1008": 83.72,
-    "q9:flow:1016": 82.93, "q9:flow:1032": 82.57, "q9:phase:1008": 72.16, "q9:phase:1016": 71.8,
-    "q9:phase:1032": 71.32, "q9:scalar_T:1008": 28.32, "q9:scalar_T:1016": 27.37, "q9:scalar_T:1032": 27.93,
-    "q9:scalar_U:1008": 28.56, "q9:scalar_U:1016": 27.34, "q9:scalar_U:1032": 27.97, "q9:transfer:1008": 16.4,
-    "q9:transfer:1016": 16.33, "q9:transfer:1032": 16.59
+# of a vector-strip launch does not depend on the data), FP32; the phase
+# update with grain angles (":ori")
+TRAFFIC_PER_NODE_8192 = {
+    "q5:flow:1016": 92.65, "q5:flow:1032": 93.28, "q5:phase:1016:ori": 52.21, "q5:phase:1032:ori": 52.46,
+    "q5:scalar_T:1016": 36.01, "q5:scalar_T:1032": 36.39, "q5:scalar_U:1016": 36.04, "q5:scalar_U:1032": 36.42,
+    "q5:transfer:1016": 23.79, "q5:transfer:1032": 23.8, "q9:flow:1016": 92.66, "q9:flow:1032": 93.24,
+    "q9:phase:1016:ori": 84.7, "q9:phase:1032:ori": 84.99, "q9:scalar_T:1016": 35.94, "q9:scalar_T:1032": 36.28,
+    "q9:scalar_U:1016": 35.95, "q9:scalar_U:1032": 36.33, "q9:transfer:1016": 23.78, "q9:transfer:1032": 23.8,
 }
 
 
@@ -370,6 +365,8 @@ def run_ours(args):
     p = wl.params
     nodes = p.nx * p.ny
     prec = args.precision or "f32"
+    if args.orientation is not None:        # one grain turned by this angle (profiling of the angle reads)
+        wl.fields["theta"] = np.full((p.ny, p.nx), float(args.orientation))
     sim = lbm.Simulation(p, precision=prec)
     if args.fusion != "auto":
         sim.set_fusion(args.fusion == "on")
@@ -554,6 +551,18 @@ def lattice_variant(args, torch, lbm, local, dev, flush_bytes, q):
     return out
 
 
+_GRAINS = {}
+
+
+def grain_angles_8192():
+    """Voronoi grain angles of the 8192^2 multi-dendrite lattice (one crystal
+    angle per seed, drawn in [0, pi/2)); built once per process."""
+    if "theta" not in _GRAINS:
+        p, pts = W.multi_dendrite_params(8192)
+        _GRAINS["theta"] = W.grain_orientation(pts, W.multi_dendrite_angles(len(pts)), 0, 0, 8192, 8192, rows=32)
+    return _GRAINS["theta"]
+
+
 def large_lattice(args, torch, lbm, local, peaks_fn, q=9):
     """The HBM-bound regime: the 8192^2 multi-dendrite workload (thermosolutal
     growth with convection, 32 Poisson-disc seeds, update factors (1, 1, 4,
@@ -564,6 +573,7 @@ def large_lattice(args, torch, lbm, local, peaks_fn, q=9):
     p.q_scalar = q
     prec = args.precision or "f32"
     sim = lbm.Simulation(p, precision=prec)
+    sim.set_orientation(grain_angles_8192())          # each grain in its own crystal frame
     sim.init_seed([{"kind": "circle", "x": float(x), "y": float(y), "r": 8.0} for x, y in pts], U0=0.0, T0=-0.55)
     period = 4
     for _ in range(2):
@@ -608,7 +618,7 @@ def large_lattice(args, torch, lbm, local, peaks_fn, q=9):
     sim.close()
     nodes = p.nx * p.ny
     base = steps * period
-    ab = algo_bytes(prec, q)
+    ab = algo_bytes(prec, q, ori=True)
     # algorithmic bytes per node per base step of the staged path (the fused
     # path moves fewer); U every step, T every 4th, flow every 2nd
     step_bytes = ab["phase"] + ab["transfer"] + ab["scalar_U"] + ab["scalar_T"] / p.N_T + ab["flow"] / p.N_F
@@ -623,13 +633,11 @@ def large_lattice(args, torch, lbm, local, peaks_fn, q=9):
     avg_s = kt[dom][0] * 1e-3 / max(kt[dom][1], 1)
     dom_gbs = dom_algo[dom] * nodes / avg_s / 1e9
     traffic, traffic_note = None, None
-    key = "q%d:%s:%d" % (q, dom, tiles[dom])
-    if prec == "f32" and TRAFFIC_SOURCE_SHA == kernel_source_sha():
-        if key in TRAFFIC_PER_NODE_8192:
-            traffic, traffic_note = TRAFFIC_PER_NODE_8192[key] * nodes, "8192^2 capture of this variant"
-        elif key in TRAFFIC_PER_NODE_2048:
-            traffic, traffic_note = TRAFFIC_PER_NODE_2048[key] * nodes, "2048^2 capture scaled by nodes (a lower bound: part of a 2048^2 launch hits L2)"
-    return {"workload": "8192x8192 multi-dendrite thermosolutal growth with convection, 32 seeds, N=(1,1,4,2), "
+    key = "q%d:%s:%d%s" % (q, dom, tiles[dom], ":ori" if dom == "phase" else "")
+    if prec == "f32" and TRAFFIC_SOURCE_SHA == kernel_source_sha() and key in TRAFFIC_PER_NODE_8192:
+        traffic, traffic_note = TRAFFIC_PER_NODE_8192[key] * nodes, "8192^2 capture of this variant"
+    return {"workload": "8192x8192 multi-dendrite thermosolutal growth with convection, 32 seeds in grains of "
+                        "random crystal orientation, N=(1,1,4,2), "
                         + lattice_label(p) + ", " + STORAGE_LABEL[prec], "storage": prec,
             "value": nodes * base / (ms * 1e-3) / 1e6, "unit": UNIT, "base_steps": base,
             "ms_per_period": ms / steps, "fused_transport": fused,
@@ -896,6 +904,7 @@ def run_configs(args):
         p, pts = W.multi_dendrite_params(8192)
         p.q_scalar = q
         sim = lbm.Simulation(p, precision="f32")
+        sim.set_orientation(grain_angles_8192())
         sim.init_seed([{"kind": "circle", "x": float(x), "y": float(y), "r": 8.0} for x, y in pts], U0=0.0,
                       T0=-0.55)
         m0 = sim.diagnostics()["M_C"]
@@ -903,7 +912,7 @@ def run_configs(args):
         ms, d, bad, done = chunked(sim, 50000, 5000)
         fused = sim.fused
         sim.close()
-        ab = algo_bytes("f32", q)
+        ab = algo_bytes("f32", q, ori=True)
         step_bytes = ab["phase"] + ab["transfer"] + ab["scalar_U"] + ab["scalar_T"] / p.N_T + ab["flow"] / p.N_F
         nodes = p.nx * p.ny
         gbs = step_bytes * nodes * done / (ms * 1e-3) / 1e9
@@ -947,6 +956,8 @@ def main():
     ap.add_argument("--q-scalar", type=int, default=5, choices=[9, 5],
                     help="velocities of the phase, U and T lattices: 5 (D2Q5, as the workload list states "
                          "them; default) or 9 (the paper's D2Q9)")
+    ap.add_argument("--orientation", type=float, default=None,
+                    help="crystal angle of the (single) grain of the main workload (profiling runs)")
     ap.add_argument("--no-alt-lattice", action="store_true",
                     help="skip the measurement on the other velocity set")
     ap.add_argument("--lattice", type=int, default=None,
