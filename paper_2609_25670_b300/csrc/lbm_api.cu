@@ -1081,8 +1081,8 @@ lbm_status upload_and_init(lbm_sim* h, SimState& s, const double* src[6], int sr
     (void)P;
     CK(cudaGetLastError());
     const size_t rs = sizeof(R);
-    if (s.accU) CK(cudaMemsetAsync(s.accU, 0, s.nn * rs, h->stream));
-    if (s.accT) CK(cudaMemsetAsync(s.accT, 0, s.nn * rs, h->stream));
+    if (s.accU) CK(cudaMemsetAsync(s.accU, 0, 2 * s.nn * rs, h->stream));
+    if (s.accT) CK(cudaMemsetAsync(s.accT, 0, 2 * s.nn * rs, h->stream));
     CK(cudaMemsetAsync(s.smax, 0, 2 * sizeof(unsigned long long), h->stream));
     if (s.clock) CK(cudaMemsetAsync(s.clock, 0, sizeof(long long), h->stream));
     s.acc_reset_U = s.acc_reset_T = true;
@@ -1250,8 +1250,9 @@ lbm_status lbm_create(const lbm_params* p, int32_t n_sims, const lbm_params* per
                 if (!st) st = dev_alloc(h, s.nn * rs, &s.uy[b]);
                 if (!st) st = dev_alloc(h, s.nn * rs, &s.rho[b]);
             }
-        if (!st && s.accumulated && s.has_U) st = dev_alloc(h, s.nn * rs, &s.accU);
-        if (!st && s.accumulated && s.has_T) st = dev_alloc(h, s.nn * rs, &s.accT);
+        // accumulated coupling: the sums and their Kahan compensations, two planes each
+        if (!st && s.accumulated && s.has_U) st = dev_alloc(h, 2 * s.nn * rs, &s.accU);
+        if (!st && s.accumulated && s.has_T) st = dev_alloc(h, 2 * s.nn * rs, &s.accT);
         if (!st) st = dev_alloc(h, 2 * sizeof(unsigned long long), (void**)&s.smax);
         if (!st && s.frozen_T) st = dev_alloc(h, sizeof(long long), (void**)&s.clock);
         s.diag_blocks = (int)std::min<size_t>(1184, (s.nn + 255) / 256);

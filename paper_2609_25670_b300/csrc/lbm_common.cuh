@@ -157,6 +157,16 @@ __device__ __forceinline__ void aniso(R gx, R gy, R eps, R& as, R& Nx, R& Ny) {
     Ny = t * gy * gx2 * (gy2 - gx2);
 }
 
+// Kahan-compensated accumulation (the accumulated coupling's phase-change
+// sums over the fine steps between two coarse updates): sum s with the
+// compensation c of the low-order part lost so far, increment x
+template <typename R> __device__ __forceinline__ void kahan_add(R& s, R& c, R x) {
+    const R y = x - c;
+    const R t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
 // sin and cos of one angle: the CUDA fast single-precision intrinsic for
 // FP32 (an angle of order one, absolute error ~2^-21), the double-precision
 // library routine for FP64

@@ -303,13 +303,14 @@ __device__ __forceinline__ void transfer_tile(TransferSmem<R, TY>& sm, const KP<
     const bool own = (IN || (gx < P.nx && gy < P.ny)) && !skip.in(gx, gy);
     const int node = gy * P.pitch + gx;
     R poa = R(0), Usa = R(0), pob = R(0), Usb = R(0), Town = R(0), accUo = R(0), accTo = R(0);
+    R cUo = R(0), cTo = R(0);                     // Kahan compensations of the accumulators (second plane)
     if (va) { poa = phio[na]; if (P.has_U) Usa = Uin[na]; }
     if (vb) { pob = phio[nb]; if (P.has_U) Usb = Uin[nb]; }
     if (own) {
         if (P.has_T) Town = Tin[node];
         if (P.accumulated) {
-            if (P.has_U && !acc_reset_U) accUo = accU[node];
-            if (P.has_T && !acc_reset_T) accTo = accT[node];
+            if (P.has_U && !acc_reset_U) { accUo = accU[node]; cUo = accU[node + P.plane]; }
+            if (P.has_T && !acc_reset_T) { accTo = accT[node]; cTo = accT[node + P.plane]; }
         }
     }
     load_phi_ring2<R, TY, IN>(P, phin, sm.pn, x0, y0, tid);
@@ -346,13 +347,21 @@ __device__ __forceinline__ void transfer_tile(TransferSmem<R, TY>& sm, const KP<
             const R dU = ((R(1) + omk * Usa) * dphi - R(2) * div) * rcp((R(1) + P.k) - omk * pn);   // Eq. 38
             mydu = fabs(dU);
             if (!P.accumulated) Uout[node] = Usa + dU;                                // Eq. 39
-            else accU[node] = accUo + dU;
+            else {
+                kahan_add(accUo, cUo, dU);
+                accU[node] = accUo;
+                accU[node + P.plane] = cUo;
+            }
         }
         if (P.has_T) {
             const R rc = R(0.5) * (R(1) + pn) * P.cS + R(0.5) * (R(1) - pn) * P.cL;
             const R dT = P.rhoL_Lh * dphi * rcp(R(2) * rc);                           // Eq. 38
             if (!P.accumulated) Tout[node] = Town + dT;
-            else accT[node] = accTo + dT;
+            else {
+                kahan_add(accTo, cTo, dT);
+                accT[node] = accTo;
+                accT[node + P.plane] = cTo;
+            }
         }
     }
     // block maximum of |Delta U_pc| -> S_phi (and J_U when instantaneous)

@@ -885,7 +885,9 @@ __device__ __forceinline__ void transfer_vstrip(const KP<R>& P, const R* __restr
             Sx[VW + 1] = from_right(Sx[1]); Dy[VW + 1] = from_right(Dy[1]);
             if (outl) {
                 const int node = (r - DIR) * pitch + c0;
-                Vec4<R> oU, oT;
+                Vec4<R> oU, oT, cU{}, cT{};       // Kahan compensations (second plane of the accumulators)
+                if (ldAU) cU = *reinterpret_cast<const Vec4<R>*>(accU + P.plane + node);
+                if (ldAT) cT = *reinterpret_cast<const Vec4<R>*>(accT + P.plane + node);
 #pragma unroll
                 for (int k = 0; k < VW; ++k) {
                     const R div = Sx[k + 2] - Sx[k] + Dy[k + 1] * (R(1) / R(3)) + (Dy[k] + Dy[k + 2]) * (R(1) / R(12));
@@ -893,16 +895,28 @@ __device__ __forceinline__ void transfer_vstrip(const KP<R>& P, const R* __restr
                     if (ldU) {
                         const R dU = ((R(1) + omk * Uy[k]) * dphi - R(2) * div) * rcp((R(1) + P.k) - omk * pny[k]);  // Eq. 38
                         mydu = fmax(mydu, fabs(dU));
-                        oU.v[k] = P.accumulated ? aUy[k] + dU : Uy[k] + dU;                  // Eq. 39
+                        if (P.accumulated) {
+                            oU.v[k] = aUy[k];
+                            kahan_add(oU.v[k], cU.v[k], dU);
+                        } else {
+                            oU.v[k] = Uy[k] + dU;                                            // Eq. 39
+                        }
                     }
                     if (ldT) {
                         const R rc = R(0.5) * (R(1) + pny[k]) * P.cS + R(0.5) * (R(1) - pny[k]) * P.cL;
                         const R dT = P.rhoL_Lh * dphi * rcp(R(2) * rc);                       // Eq. 38
-                        oT.v[k] = P.accumulated ? aTy[k] + dT : Ty[k] + dT;
+                        if (P.accumulated) {
+                            oT.v[k] = aTy[k];
+                            kahan_add(oT.v[k], cT.v[k], dT);
+                        } else {
+                            oT.v[k] = Ty[k] + dT;
+                        }
                     }
                 }
                 if (ldU) *reinterpret_cast<Vec4<R>*>((P.accumulated ? accU : Uout) + node) = oU;
                 if (ldT) *reinterpret_cast<Vec4<R>*>((P.accumulated ? accT : Tout) + node) = oT;
+                if (ldU && P.accumulated) *reinterpret_cast<Vec4<R>*>(accU + P.plane + node) = cU;
+                if (ldT && P.accumulated) *reinterpret_cast<Vec4<R>*>(accT + P.plane + node) = cT;
             }
         }
 #pragma unroll
