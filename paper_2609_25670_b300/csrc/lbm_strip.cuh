@@ -793,7 +793,7 @@ template <typename R> struct TRing {
     static constexpr int BYTES = D * SLOT;
 };
 
-template <typename R, int H, bool UP>
+template <typename R, int H, bool UP, bool ACC>
 __device__ __forceinline__ void transfer_vstrip(const KP<R>& P, const R* __restrict__ phio,
                                                 const R* __restrict__ phin, const R* __restrict__ Uin,
                                                 R* __restrict__ Uout, const R* __restrict__ Tin, R* __restrict__ Tout,
@@ -806,8 +806,8 @@ __device__ __forceinline__ void transfer_vstrip(const KP<R>& P, const R* __restr
     const int c0 = VSW * s + VW * lane;
     const bool outl = lane >= 1 && lane <= 30;
     const int rfirst = UP ? y0 + H : y0 - 1;
-    const bool ldU = P.has_U, ldT = P.has_T;
-    const bool ldAU = P.accumulated && P.has_U && !acc_reset_U, ldAT = P.accumulated && P.has_T && !acc_reset_T;
+    const bool ldU = P.has_U, ldT = P.has_T;      // ACC: the accumulated coupling (P.accumulated)
+    const bool ldAU = ACC && P.has_U && !acc_reset_U, ldAT = ACC && P.has_T && !acc_reset_T;
     unsigned char* const mine = ring + lane * EB;
     auto fetch_row = [&](int r, unsigned char* slot) {      // phi^{q+1} of row r + DIR; the rest of row r
         const int base = r * pitch + c0;
@@ -886,8 +886,10 @@ __device__ __forceinline__ void transfer_vstrip(const KP<R>& P, const R* __restr
             if (outl) {
                 const int node = (r - DIR) * pitch + c0;
                 Vec4<R> oU, oT, cU{}, cT{};       // Kahan compensations (second plane of the accumulators)
-                if (ldAU) cU = *reinterpret_cast<const Vec4<R>*>(accU + P.plane + node);
-                if (ldAT) cT = *reinterpret_cast<const Vec4<R>*>(accT + P.plane + node);
+                if constexpr (ACC) {
+                    if (ldAU) cU = *reinterpret_cast<const Vec4<R>*>(accU + P.plane + node);
+                    if (ldAT) cT = *reinterpret_cast<const Vec4<R>*>(accT + P.plane + node);
+                }
 #pragma unroll
                 for (int k = 0; k < VW; ++k) {
                     const R div = Sx[k + 2] - Sx[k] + Dy[k + 1] * (R(1) / R(3)) + (Dy[k] + Dy[k + 2]) * (R(1) / R(12));
@@ -895,7 +897,7 @@ __device__ __forceinline__ void transfer_vstrip(const KP<R>& P, const R* __restr
                     if (ldU) {
                         const R dU = ((R(1) + omk * Uy[k]) * dphi - R(2) * div) * rcp((R(1) + P.k) - omk * pny[k]);  // Eq. 38
                         mydu = fmax(mydu, fabs(dU));
-                        if (P.accumulated) {
+                        if constexpr (ACC) {
                             oU.v[k] = aUy[k];
                             kahan_add(oU.v[k], cU.v[k], dU);
                         } else {
@@ -905,7 +907,7 @@ __device__ __forceinline__ void transfer_vstrip(const KP<R>& P, const R* __restr
                     if (ldT) {
                         const R rc = R(0.5) * (R(1) + pny[k]) * P.cS + R(0.5) * (R(1) - pny[k]) * P.cL;
                         const R dT = P.rhoL_Lh * dphi * rcp(R(2) * rc);                       // Eq. 38
-                        if (P.accumulated) {
+                        if constexpr (ACC) {
                             oT.v[k] = aTy[k];
                             kahan_add(oT.v[k], cT.v[k], dT);
                         } else {
@@ -913,10 +915,12 @@ __device__ __forceinline__ void transfer_vstrip(const KP<R>& P, const R* __restr
                         }
                     }
                 }
-                if (ldU) *reinterpret_cast<Vec4<R>*>((P.accumulated ? accU : Uout) + node) = oU;
-                if (ldT) *reinterpret_cast<Vec4<R>*>((P.accumulated ? accT : Tout) + node) = oT;
-                if (ldU && P.accumulated) *reinterpret_cast<Vec4<R>*>(accU + P.plane + node) = cU;
-                if (ldT && P.accumulated) *reinterpret_cast<Vec4<R>*>(accT + P.plane + node) = cT;
+                if (ldU) *reinterpret_cast<Vec4<R>*>((ACC ? accU : Uout) + node) = oU;
+                if (ldT) *reinterpret_cast<Vec4<R>*>((ACC ? accT : Tout) + node) = oT;
+                if constexpr (ACC) {
+                    if (ldU) *reinterpret_cast<Vec4<R>*>(accU + P.plane + node) = cU;
+                    if (ldT) *reinterpret_cast<Vec4<R>*>(accT + P.plane + node) = cT;
+                }
             }
         }
 #pragma unroll
@@ -932,7 +936,7 @@ __device__ __forceinline__ void transfer_vstrip(const KP<R>& P, const R* __restr
         for (int d = 16; d > 0; d >>= 1) mydu = fmax(mydu, __shfl_xor_sync(0xffffffffu, mydu, d));
         if (lane == 0) {
             atomic_max_pos(&smax[0], (double)mydu);
-            if (!P.accumulated) atomic_max_pos(&smax[1], (double)mydu);
+            if (!ACC) atomic_max_pos(&smax[1], (double)mydu);
         }
     }
 }
@@ -962,12 +966,21 @@ __device__ __forceinline__ void transfer_vs_block(const KP<R>& P, const R* phio,
         if (vs >= g.nxv * g.nyv) return;           // whole warp (no block barrier on this path)
         const int sy = vs / g.nxv;
         unsigned char* mine = tsm + w * TRing<R>::BYTES;
-        if (sy & 1)
-            transfer_vstrip<R, H, true>(P, phio, phin, Uin, Uout, Tin, Tout, accU, accT, ru, rt, smax, vs % g.nxv,
-                                        VY0 + H * sy, mine);
+        // the accumulated coupling (Kahan sums) and the instantaneous one as
+        // separate instantiations: the latter keeps none of the former's code
+        if (P.accumulated) {
+            if (sy & 1)
+                transfer_vstrip<R, H, true, true>(P, phio, phin, Uin, Uout, Tin, Tout, accU, accT, ru, rt, smax,
+                                                  vs % g.nxv, VY0 + H * sy, mine);
+            else
+                transfer_vstrip<R, H, false, true>(P, phio, phin, Uin, Uout, Tin, Tout, accU, accT, ru, rt, smax,
+                                                   vs % g.nxv, VY0 + H * sy, mine);
+        } else if (sy & 1)
+            transfer_vstrip<R, H, true, false>(P, phio, phin, Uin, Uout, Tin, Tout, accU, accT, ru, rt, smax,
+                                               vs % g.nxv, VY0 + H * sy, mine);
         else
-            transfer_vstrip<R, H, false>(P, phio, phin, Uin, Uout, Tin, Tout, accU, accT, ru, rt, smax, vs % g.nxv,
-                                         VY0 + H * sy, mine);
+            transfer_vstrip<R, H, false, false>(P, phio, phin, Uin, Uout, Tin, Tout, accU, accT, ru, rt, smax,
+                                                vs % g.nxv, VY0 + H * sy, mine);
         return;
     }
     b -= nvb;
