@@ -115,21 +115,21 @@ def period_bytes(p, prec="f32"):
 # 8192^2 (times the nodes a launch processes for the 8192^2 measurement).
 # Reported only while the kernel sources hash to TRAFFIC_SOURCE_SHA; after any
 # change of the code the traffic is null until re-measured.
-TRAFFIC_SOURCE_SHA = "a38fd3df4bae6066"
+TRAFFIC_SOURCE_SHA = "41b8cc7d99e6fd4d"
 # (transport: the mean of the period's two kinds of launch, transfer + U
 # alone and transfer + U + T + flow, like the algorithmic bytes it is set
 # against)
-TRAFFIC_PER_LAUNCH_512 = {"q5:transport:8": 14234304.0, "q5:transport:16": 14233312.0, "q5:phase:4": 7369003.0,
-                          "q5:phase:8": 7366827.0}
+TRAFFIC_PER_LAUNCH_512 = {"q5:transport:8": 14232256.0, "q5:transport:16": 14231744.0, "q5:phase:4": 7369088.0,
+                          "q5:phase:8": 7366272.0}
 # measured directly on an 8192^2 lattice (single-pass counters; the traffic
 # of a vector-strip launch does not depend on the data), FP32; the phase
 # update with grain angles (":ori")
 TRAFFIC_PER_NODE_8192 = {
-    "q5:flow:1016": 92.65, "q5:flow:1032": 93.28, "q5:phase:1016:ori": 52.21, "q5:phase:1032:ori": 52.46,
-    "q5:scalar_T:1016": 36.01, "q5:scalar_T:1032": 36.39, "q5:scalar_U:1016": 36.04, "q5:scalar_U:1032": 36.42,
-    "q5:transfer:1016": 23.79, "q5:transfer:1032": 23.8, "q9:flow:1016": 92.66, "q9:flow:1032": 93.24,
-    "q9:phase:1016:ori": 84.7, "q9:phase:1032:ori": 84.99, "q9:scalar_T:1016": 35.94, "q9:scalar_T:1032": 36.28,
-    "q9:scalar_U:1016": 35.95, "q9:scalar_U:1032": 36.33, "q9:transfer:1016": 23.78, "q9:transfer:1032": 23.8,
+    "q5:flow:1016": 92.63, "q5:flow:1032": 93.35, "q5:phase:1016:ori": 52.21, "q5:phase:1032:ori": 52.41,
+    "q5:scalar_T:1016": 36.04, "q5:scalar_T:1032": 36.54, "q5:scalar_U:1016": 36.03, "q5:scalar_U:1032": 36.58,
+    "q5:transfer:1016": 23.80, "q5:transfer:1032": 23.84, "q9:flow:1016": 92.63, "q9:flow:1032": 93.47,
+    "q9:phase:1016:ori": 84.72, "q9:phase:1032:ori": 85.0, "q9:scalar_T:1016": 35.95, "q9:scalar_T:1032": 36.32,
+    "q9:scalar_U:1016": 35.97, "q9:scalar_U:1032": 36.4, "q9:transfer:1016": 23.80, "q9:transfer:1032": 23.83,
 }
 
 
