@@ -196,26 +196,42 @@ def job_throughput(nodes, base_steps_per_step, steps, world, ms_max):
     return nodes * base_steps_per_step * steps * world / (ms_max * 1e-3) / 1e6
 
 
-def gated_steps(torch, stream, flush, advance, steps):
+def gated_steps(torch, stream, flush, advance, steps, reinit=None):
     """`steps` bench steps on `stream`: an L2 flush (untimed), then one
     advance() between two CUDA events.  A bounded sleep kernel queued first
     holds the stream while the host enqueues every step, so the device runs
     the steps back to back from its queue and a pause of the host thread
     (scheduling, the clock sampler's queries) cannot fall inside a timed
-    step.  Returns the per-step times in ms."""
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    gate_s = min(2.0, 0.01 + 3e-4 * steps)
-    with torch.cuda.stream(stream):
-        torch.cuda._sleep(int(gate_s * 2.0e9))       # ~gate_s at the 2 GHz SM clock
-    for k in range(steps):
+    step.  The gate is checked: an event recorded behind the sleep must still
+    be pending once the host has enqueued the last step.  If the device got
+    there first (a host slower than the gate), the times hold host gaps: the
+    state is re-initialised with `reinit` and the steps are timed again
+    behind a gate four times longer, at most three attempts in all.
+    Returns (the per-step times in ms, whether the gate held)."""
+    gate_s = 0.01 + 1e-3 * steps
+    for attempt in range(3):
+        if attempt and reinit is not None:
+            reinit()
+            torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        gate = torch.cuda.Event()
         with torch.cuda.stream(stream):
-            flush.fill_(float(k))
-            ev[k][0].record(stream)
-        advance()
-        with torch.cuda.stream(stream):
-            ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    return [a.elapsed_time(b) for a, b in ev]
+            torch.cuda._sleep(int(min(gate_s, 8.0) * 2.0e9))   # ~gate_s at the 2 GHz SM clock
+            gate.record(stream)
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+            advance()
+            with torch.cuda.stream(stream):
+                ev[k][1].record(stream)
+        held = not gate.query()
+        torch.cuda.synchronize()
+        times = [a.elapsed_time(b) for a, b in ev]
+        if held:
+            break
+        gate_s *= 4.0
+    return times, held
 
 
 def refine_tiles(sim, torch, flush, tiles, steps=24):
@@ -235,7 +251,7 @@ def refine_tiles(sim, torch, flush, tiles, steps=24):
             sim.set_tile(kind, v)
             sim.advance(STEP_BASE)                    # capture with this variant
             torch.cuda.synchronize()
-            ms = sorted(gated_steps(torch, stream, flush, lambda: sim.advance(STEP_BASE), steps))[steps // 2]
+            ms = sorted(gated_steps(torch, stream, flush, lambda: sim.advance(STEP_BASE), steps)[0])[steps // 2]
             if best is None or ms < best:
                 best, best_v = ms, v
         sim.set_tile(kind, best_v)
@@ -409,12 +425,13 @@ def run_ours(args):
         """args.steps steps (the caller re-initialises the state first, so
         that every timed region covers the first 2 * steps base steps of the
         workload), L2 flushed before each step, CUDA events around each step
-        on the library stream; returns (total ms, wall s)."""
+        on the library stream; returns (total ms, wall s, whether the gate held)."""
         barrier()
         w0 = time.perf_counter()
-        t = gated_steps(torch, stream, flush, lambda: sim.advance(STEP_BASE), args.steps)
+        t, held = gated_steps(torch, stream, flush, lambda: sim.advance(STEP_BASE), args.steps,
+                              reinit=lambda: sim.init_fields(wl.fields))
         barrier()
-        return sum(t), time.perf_counter() - w0
+        return sum(t), time.perf_counter() - w0, held
 
     # the timed region: graphs without timing nodes (an event-record node
     # around a launch inside a graph adds several microseconds per launch)
@@ -425,7 +442,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    ms, wall = timed_region()
+    ms, wall, gate_held = timed_region()
     clk = clocks.stop()
     launches1 = sim.launch_counts()
     gpu_launches = int(sum(launches1[k] - launches0[k] for k in launches1))
@@ -437,7 +454,7 @@ def run_ours(args):
     sim.advance(STEP_BASE)           # recapture with the dominant kind's timing nodes, untimed
     sim.timing_read(reset=True)
     sim.init_fields(wl.fields)
-    ms_instr, _ = timed_region()
+    ms_instr, _, _ = timed_region()
     ktimes = sim.timing_read(reset=True)
     sim.timing_enable([])
     state_finite = not sim.diagnostics()["nonfinite"]
@@ -488,9 +505,11 @@ def run_ours(args):
             "tiles": {k: tiles[k] for k in kinds},
             "gpu_launches": gpu_launches,
             "wall_s_timed_region": wall,
+            "gate_held": gate_held,
             "state_finite_after_timed_regions": state_finite,
             "timing": "CUDA events around each step's advance on the library stream; the steps are queued "
-                      "behind a bounded sleep kernel (included in wall_s_timed_region, not in value)",
+                      "behind a bounded sleep kernel (included in wall_s_timed_region, not in value) that is checked "
+                      "to outlast the host's enqueueing (re-timed behind a longer one otherwise)",
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps, "calls": "init_fields(host f64 x6) + advance(2) + field(phi -> host)"},
@@ -536,14 +555,16 @@ def lattice_variant(args, torch, lbm, local, dev, flush_bytes, q):
     steps = min(args.steps, 400)        # within the first 800 base steps (the D2Q9 reading of this
     sim.init_fields(wl.fields)          # workload turns non-finite after ~2 100)
     torch.cuda.synchronize()
-    ms = sum(gated_steps(torch, stream, flush, lambda: sim.advance(STEP_BASE), steps))
+    t, held = gated_steps(torch, stream, flush, lambda: sim.advance(STEP_BASE), steps,
+                          reinit=lambda: sim.init_fields(wl.fields))
+    ms = sum(t)
     fused = sim.fused
     finite = not sim.diagnostics()["nonfinite"]
     sim.close()
     del flush
     nodes = p.nx * p.ny
     out = {"workload": workload_label(p, prec), "value": nodes * STEP_BASE * steps / (ms * 1e-3) / 1e6,
-           "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "fused_transport": fused,
+           "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "gate_held": held, "fused_transport": fused,
            "tiles": {k: tiles[k] for k in ("phase", "transfer", "scalar_U", "scalar_T", "flow", "transport")},
            "l2": "flushed between steps (512 MiB write)", "state_finite_after_timed_region": finite}
     if not args.no_large:
