@@ -176,14 +176,18 @@ lbm_status lbm_create(const lbm_params* p, int32_t n_sims, const lbm_params* per
  * phi from the seeds, U = U0, T = T0, rho = 1, u = u_in (1 - phi)/2 along x
  * when the flow is on; then every distribution is set to the equilibrium of
  * these fields (for phi with v_n from the initial gradient, Eqs. 19, 21, 28).
- * Resets the base-step clock and the sticky error.  Synchronises the stream. */
+ * Resets the base-step clock and the sticky error.  Returns once the
+ * generated fields are on the device; the initialisation kernels run on,
+ * ordered on the stream before any later call's work. */
 lbm_status lbm_init_seed(lbm_handle h, int32_t sim, const lbm_seed* seeds, int32_t n_seeds,
                          double U0, double T0, uint64_t rng_seed);
 
 /* Initialise simulation `sim` from caller fields, each ny x nx FP64: phi, U,
  * T, ux, uy, rho (U / T / ux, uy, rho are ignored when that field is off, and
  * may then be NULL).  src_is_device: 1 if the pointers are device memory.
- * Then as lbm_init_seed.  Synchronises the stream. */
+ * Then as lbm_init_seed.  Returns once the source buffers have been read (the
+ * caller may then reuse or free them); the conversion and initialisation run
+ * on, ordered on the stream before any later call's work. */
 lbm_status lbm_init_fields(lbm_handle h, int32_t sim, const double* phi, const double* U,
                            const double* T, const double* ux, const double* uy,
                            const double* rho, int32_t src_is_device);

@@ -1038,20 +1038,35 @@ template <typename R>
 lbm_status upload_and_init(lbm_sim* h, SimState& s, const double* src[6], int src_dev) {
     const size_t n = (size_t)s.nx * s.ny;
     const size_t need = n * sizeof(double);
-    if (h->staging_bytes < need) {
+    void* dst[6] = {s.phi[0], s.U[0], s.T[0], s.ux[0], s.uy[0], s.rho[0]};
+    int nf = 0;
+    for (int f = 0; f < 6; ++f) nf += (dst[f] && src[f]) ? 1 : 0;
+    // one staging slot per field when they fit in 256 MiB: the copies then
+    // run back to back instead of each waiting for the previous conversion
+    const bool slots = (size_t)nf * need <= ((size_t)256 << 20);
+    const size_t want = slots ? (size_t)nf * need : need;
+    if (h->staging_bytes < want) {
         void* p = nullptr;
-        lbm_status st = dev_alloc(h, need, &p);
+        lbm_status st = dev_alloc(h, want, &p);
         if (st) return st;
         h->staging = (double*)p;
-        h->staging_bytes = need;
+        h->staging_bytes = want;
     }
     const dim3 blk(32, 8), grd((s.nx + 31) / 32, (s.ny + 7) / 8);
-    void* dst[6] = {s.phi[0], s.U[0], s.T[0], s.ux[0], s.uy[0], s.rho[0]};
-    for (int f = 0; f < 6; ++f) {
+    const cudaMemcpyKind kind = src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int f = 0, k = 0; f < 6; ++f) {
         if (!dst[f] || !src[f]) continue;
-        CK(cudaMemcpyAsync(h->staging, src[f], need, src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
-        k_from_f64<R><<<grd, blk, 0, h->stream>>>(h->staging, (R*)dst[f], s.nx, s.ny, s.pitch);
+        double* slot = h->staging + (slots ? (size_t)k++ * n : 0);
+        CK(cudaMemcpyAsync(slot, src[f], need, kind, h->stream));
+        if (!slots) k_from_f64<R><<<grd, blk, 0, h->stream>>>(slot, (R*)dst[f], s.nx, s.ny, s.pitch);
     }
+    // the caller may reuse its buffers once they have been read
+    cudaEvent_t copied = pool_get(h);
+    CK(cudaEventRecord(copied, h->stream));
+    if (slots)
+        for (int f = 0, k = 0; f < 6; ++f)
+            if (dst[f] && src[f])
+                k_from_f64<R><<<grd, blk, 0, h->stream>>>(h->staging + (size_t)k++ * n, (R*)dst[f], s.nx, s.ny, s.pitch);
     s.cur_phi = s.cur_U = s.cur_T = 0;
     for (int f = 0; f < 4; ++f) s.cur_pop[f] = 0;
     const KP<R> P = make_kp<R>(s);
@@ -1089,7 +1104,8 @@ lbm_status upload_and_init(lbm_sim* h, SimState& s, const double* src[6], int sr
     s.step = 0;
     s.initialized = true;
     s.sticky = false;
-    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaEventSynchronize(copied));
+    h->event_pool.push_back(copied);
     return LBM_OK;
 }
 
