@@ -553,7 +553,7 @@ void launch_batch(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, 
         case LBM_K_FLOW:
             if (tysel > VS)
                 LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_flow_vs_batch<R, ST, DEV, HV>, g, dim3(32, FVW),
-                                                     (size_t)FVSmem<R>::BYTES, (const FlowJob<R, ST>*)jobs, njobs)))
+                                                     (size_t)FVSmem<R, ST>::BYTES, (const FlowJob<R, ST>*)jobs, njobs)))
             else
                 LBM_TY_SWITCH(tysel, (launch_ex(h, k_flow_batch<R, ST, DEV, TYV>, g, dim3(TX, TYV),
                                                 (const FlowJob<R, ST>*)jobs, njobs)))
@@ -663,8 +663,8 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
         case LBM_K_FLOW: {
             const int c = s.cur_pop[FF];
             if (tysel > VS)
-                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_flow_vs<R, ST, DEV, HV>, grid_v(s, kind, tysel),
-                    dim3(32, FVW), (size_t)FVSmem<R>::BYTES, P, (const ST*)s.pops[FF][c], (ST*)s.pops[FF][1 - c],
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, flow_vs_kernel<R, ST, DEV, HV>(), grid_v(s, kind, tysel),
+                    dim3(32, FVW), (size_t)FVSmem<R, ST>::BYTES, P, (const ST*)s.pops[FF][c], (ST*)s.pops[FF][1 - c],
                     phi_now, (const R*)s.ux[c], (const R*)s.uy[c], (const R*)s.rho[c], (R*)s.ux[1 - c],
                     (R*)s.uy[1 - c], (R*)s.rho[1 - c])))
             else

@@ -379,10 +379,10 @@ template <typename T> __device__ __forceinline__ Vec4<T> sread(const unsigned ch
 enum { VA_JX = 0, VA_JY = 1, VA_CHI = 2, VA_ACC = 3, VA_VX = 4, VA_VY = 5, VA_PHI = 6, VA_N = 7 };
 // per-warp ring of row slots, each holding NA arrays of one 16-byte (FP32)
 // entry per lane
-template <typename R, int NA> struct VRingN {
+template <typename R, int NA, int DD = 0> struct VRingN {
     static constexpr int EB = VW * (int)sizeof(R);     // bytes of one lane's entry
     static constexpr int SLOT = NA * 32 * EB;          // one row
-    static constexpr int D = sizeof(R) == 8 ? 2 : 4;   // rows in the ring (D - 1 in flight)
+    static constexpr int D = DD ? DD : sizeof(R) == 8 ? 2 : 4;   // rows in the ring (D - 1 in flight)
     static constexpr int BYTES = D * SLOT;
 };
 template <typename R> using VRing = VRingN<R, VA_N>;     // scalar strips
@@ -593,7 +593,11 @@ __device__ __forceinline__ void scalar_vs_block(const KP<R>& P, const ST* fin, S
 // on either side; both are carried in registers as the warp walks.
 // ---------------------------------------------------------------------------
 enum { FA_RHO = 8, FA_UX = 9, FA_UY = 10, FA_PHI = 11, FA_N = 12 };
-template <typename R> using FRing = VRingN<R, FA_N>;    // flow strips: 8 populations, rho, u, phi
+// flow strips: 8 populations, rho, u, phi.  With 16-bit populations the
+// strip is bound by its instructions, not by DRAM: a ring of three rows lets
+// three blocks (12 warps) share an SM instead of two
+template <typename R, typename ST>
+using FRing = VRingN<R, FA_N, sizeof(ST) == 2 ? 3 : 0>;
 
 template <typename R, typename ST, bool DEV, int H, bool UP>
 __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict__ fin, ST* __restrict__ fout,
@@ -601,7 +605,7 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
                                             const R* __restrict__ uy_in, const R* __restrict__ rho_in,
                                             R* __restrict__ ux_out, R* __restrict__ uy_out, R* __restrict__ rho_out,
                                             int s, int y0, unsigned char* __restrict__ ring) {
-    using RG = FRing<R>;
+    using RG = FRing<R, ST>;
     constexpr int EB = RG::EB, NR = H + 2, D = RG::D, DIR = UP ? -1 : 1;
     // directions whose source lies in the row behind the walk (far) and in
     // the row just collided (near): axis, from the left (e_x = +1), from the right
@@ -737,8 +741,8 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
 // whole lattice (every boundary kind), skipping tiles wholly inside the
 // interior and leaving its nodes to the strips.
 constexpr int FVW = 4;     // warps per block of the flow vector launch (= tile height of its frame)
-template <typename R> struct FVSmem {
-    static constexpr int STRIPS = FVW * FRing<R>::BYTES;
+template <typename R, typename ST> struct FVSmem {
+    static constexpr int STRIPS = FVW * FRing<R, ST>::BYTES;
     static constexpr int TILE = (int)sizeof(FlowSmem<R, FVW>);
     static constexpr int BYTES = STRIPS > TILE ? STRIPS : TILE;
 };
@@ -752,7 +756,7 @@ template <typename R, typename ST, bool DEV, int H>
 __device__ __forceinline__ void flow_vs_block(const KP<R>& P, const ST* fin, ST* fout, const R* phi, const R* ux_in,
                                               const R* uy_in, const R* rho_in, R* ux_out, R* uy_out, R* rho_out,
                                               int b) {
-    extern __shared__ __align__(128) unsigned char fsm[];   // FVSmem<R>::BYTES, dynamic
+    extern __shared__ __align__(128) unsigned char fsm[];   // FVSmem<R, ST>::BYTES, dynamic
     const VGeo g = vgeo(P.nx, P.ny, H);
     const int nvb = fvs_vector_blocks(g);
     if (b < nvb) {
@@ -760,7 +764,7 @@ __device__ __forceinline__ void flow_vs_block(const KP<R>& P, const ST* fin, ST*
         const int vs = b * FVW + w;
         if (vs >= g.nxv * g.nyv) return;           // whole warp (no block barrier on this path)
         const int sy = vs / g.nxv;
-        unsigned char* mine = fsm + w * FRing<R>::BYTES;
+        unsigned char* mine = fsm + w * FRing<R, ST>::BYTES;
         if (sy & 1)
             flow_vstrip<R, ST, DEV, H, true>(P, fin, fout, phi, ux_in, uy_in, rho_in, ux_out, uy_out, rho_out,
                                              vs % g.nxv, VY0 + H * sy, mine);
@@ -1290,6 +1294,20 @@ k_flow_vs(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restric
           const R* __restrict__ ux_in, const R* __restrict__ uy_in, const R* __restrict__ rho_in,
           R* __restrict__ ux_out, R* __restrict__ uy_out, R* __restrict__ rho_out) {
     flow_vs_block<R, ST, DEV, H>(*P, fin, fout, phi, ux_in, uy_in, rho_in, ux_out, uy_out, rho_out, blockIdx.x);
+}
+// the same with 16-bit populations, three blocks (12 warps) per SM: 168
+// registers and the three-row ring fit three blocks where two fit before
+template <typename R, typename ST, bool DEV, int H>
+__global__ void __launch_bounds__(32 * FVW, 3)
+k_flow_vs16(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout, const R* __restrict__ phi,
+            const R* __restrict__ ux_in, const R* __restrict__ uy_in, const R* __restrict__ rho_in,
+            R* __restrict__ ux_out, R* __restrict__ uy_out, R* __restrict__ rho_out) {
+    flow_vs_block<R, ST, DEV, H>(*P, fin, fout, phi, ux_in, uy_in, rho_in, ux_out, uy_out, rho_out, blockIdx.x);
+}
+template <typename R, typename ST, bool DEV, int H>
+constexpr auto flow_vs_kernel() {
+    if constexpr (sizeof(ST) == 2) return &k_flow_vs16<R, ST, DEV, H>;
+    else return &k_flow_vs<R, ST, DEV, H>;
 }
 template <typename R, typename ST, bool DEV, int H>
 __global__ void __launch_bounds__(32 * FVW) k_flow_vs_batch(const FlowJob<R, ST>* __restrict__ jobs, int njobs) {
