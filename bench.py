@@ -115,7 +115,7 @@ def period_bytes(p, prec="f32"):
 # 8192^2 (times the nodes a launch processes for the 8192^2 measurement).
 # Reported only while the kernel sources hash to TRAFFIC_SOURCE_SHA; after any
 # change of the code the traffic is null until re-measured.
-TRAFFIC_SOURCE_SHA = "b312b40381c73c45"
+TRAFFIC_SOURCE_SHA = "ace4b0757b2c0eb7"
 # (transport: the mean of the period's two kinds of launch, transfer + U
 # alone and transfer + U + T + flow, like the algorithmic bytes it is set
 # against)

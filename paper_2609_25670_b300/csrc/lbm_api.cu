@@ -513,7 +513,7 @@ void launch_batch(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, 
         case LBM_K_PHASE:
             if (tysel > VS)
                 LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_phase_vs_batch<R, ST, DEV, HV, Q>, g, dim3(32, PVW),
-                                                     (size_t)PVSmem<R, Q>::BYTES, (const PhaseJob<R, ST>*)jobs, njobs)))
+                                                     (size_t)PVSmem<R, Q, ST>::BYTES, (const PhaseJob<R, ST>*)jobs, njobs)))
             else
                 LBM_TY_SWITCH(tysel, (launch_ex(h, k_phase_batch<R, ST, DEV, TYV, Q>, g, dim3(TX, TYV),
                                                 (const PhaseJob<R, ST>*)jobs, njobs)))
@@ -599,8 +599,8 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
     switch (kind) {
         case LBM_K_PHASE:
             if (tysel > VS)
-                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_phase_vs<R, ST, DEV, HV, Q>, grid_v(s, kind, tysel),
-                    dim3(32, PVW), (size_t)PVSmem<R, Q>::BYTES, P, (const ST*)s.pops[FP][s.cur_pop[FP]],
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, phase_vs_kernel<R, ST, DEV, HV, Q>(), grid_v(s, kind, tysel),
+                    dim3(32, PVW), (size_t)PVSmem<R, Q, ST>::BYTES, P, (const ST*)s.pops[FP][s.cur_pop[FP]],
                     (ST*)s.pops[FP][1 - s.cur_pop[FP]], phi_now, (R*)s.phi[1 - s.cur_phi],
                     s.has_U ? (const R*)s.U[s.cur_U] : null_r, s.has_T ? (const R*)s.T[s.cur_T] : null_r, clock, off)))
             else

@@ -1008,14 +1008,17 @@ __device__ __forceinline__ void transfer_vs_block(const KP<R>& P, const R* phio,
 template <int Q> struct PA {
     static constexpr int PHI = Q - 1, U = Q, T = Q + 1, ORI = Q + 2, N = Q + 3;
 };
-template <typename R, int Q = 9> using PRing = VRingN<R, PA<Q>::N>;
+// a ring of three rows for 16-bit D2Q5 populations (instruction-bound like
+// the 16-bit flow strip): four blocks (16 warps) per SM instead of three
+template <typename R, int Q = 9, typename ST = R>
+using PRing = VRingN<R, PA<Q>::N, (sizeof(ST) == 2 && Q == 5) ? 3 : 0>;
 
 template <typename R, typename ST, bool DEV, int H, bool UP, int Q>
 __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restrict__ fin, ST* __restrict__ fout,
                                              const R* __restrict__ phi, R* __restrict__ phin,
                                              const R* __restrict__ Um, const R* __restrict__ Tm, R tnow, int s,
                                              int y0, unsigned char* __restrict__ ring) {
-    using RG = PRing<R, Q>;
+    using RG = PRing<R, Q, ST>;
     constexpr int PA_PHI = PA<Q>::PHI, PA_U = PA<Q>::U, PA_T = PA<Q>::T, PA_ORI = PA<Q>::ORI;
     constexpr int EB = RG::EB, NR = H + 2, D = RG::D, DIR = UP ? -1 : 1;
     constexpr int FAX = UP ? 4 : 2, FL = UP ? 8 : 5, FR = UP ? 7 : 6;     // far row: axis, from left, from right
@@ -1169,8 +1172,8 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
 }
 
 constexpr int PVW = 4;     // warps per block of the phase vector launch (= tile height of its frame)
-template <typename R, int Q = 9> struct PVSmem {
-    static constexpr int STRIPS = PVW * PRing<R, Q>::BYTES;
+template <typename R, int Q = 9, typename ST = R> struct PVSmem {
+    static constexpr int STRIPS = PVW * PRing<R, Q, ST>::BYTES;
     static constexpr int TILE = (int)sizeof(PhaseSmem<R, PVW, Q>);
     static constexpr int BYTES = STRIPS > TILE ? STRIPS : TILE;
 };
@@ -1183,7 +1186,7 @@ template <typename R, typename ST, bool DEV, int H, int Q>
 __device__ __forceinline__ void phase_vs_block(const KP<R>& P, const ST* fin, ST* fout, const R* phi, R* phin,
                                                const R* Um, const R* Tm, const long long* clock, long long off,
                                                int b) {
-    extern __shared__ __align__(128) unsigned char psm[];   // PVSmem<R>::BYTES, dynamic
+    extern __shared__ __align__(128) unsigned char psm[];   // PVSmem<R, Q, ST>::BYTES, dynamic
     const VGeo g = vgeo(P.nx, P.ny, H);
     const int nvb = (g.nxv * g.nyv + PVW - 1) / PVW;
     if (b < nvb) {
@@ -1193,7 +1196,7 @@ __device__ __forceinline__ void phase_vs_block(const KP<R>& P, const ST* fin, ST
         R tnow = R(0);
         if (P.frozen_T) tnow = (R)((clock ? *clock : 0ll) + off) * P.dt_base;
         const int sy = vs / g.nxv;
-        unsigned char* mine = psm + w * PRing<R, Q>::BYTES;
+        unsigned char* mine = psm + w * PRing<R, Q, ST>::BYTES;
         if (sy & 1)
             phase_vstrip<R, ST, DEV, H, true, Q>(P, fin, fout, phi, phin, Um, Tm, tnow, vs % g.nxv, VY0 + H * sy,
                                                  mine);
@@ -1264,6 +1267,19 @@ k_phase_vs(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restri
            R* __restrict__ phin, const R* __restrict__ Um, const R* __restrict__ Tm,
            const long long* __restrict__ clock, long long step_off) {
     phase_vs_block<R, ST, DEV, H, Q>(*P, fin, fout, phi, phin, Um, Tm, clock, step_off, blockIdx.x);
+}
+// the same with 16-bit D2Q5 populations, four blocks (16 warps) per SM
+template <typename R, typename ST, bool DEV, int H, int Q>
+__global__ void __launch_bounds__(32 * PVW, 4)
+k_phase_vs16(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout, const R* __restrict__ phi,
+             R* __restrict__ phin, const R* __restrict__ Um, const R* __restrict__ Tm,
+             const long long* __restrict__ clock, long long step_off) {
+    phase_vs_block<R, ST, DEV, H, Q>(*P, fin, fout, phi, phin, Um, Tm, clock, step_off, blockIdx.x);
+}
+template <typename R, typename ST, bool DEV, int H, int Q>
+constexpr auto phase_vs_kernel() {
+    if constexpr (sizeof(ST) == 2 && Q == 5) return &k_phase_vs16<R, ST, DEV, H, Q>;
+    else return &k_phase_vs<R, ST, DEV, H, Q>;
 }
 template <typename R, typename ST, bool DEV, int H, int Q>
 __global__ void __launch_bounds__(32 * PVW) k_phase_vs_batch(const PhaseJob<R, ST>* __restrict__ jobs, int njobs) {
