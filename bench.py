@@ -1,26 +1,34 @@
 """Benchmark: coupled-field MLUPS of the multirate MRT-LBM on B300.
 
-Workload: the thermosolutal free dendrite with forced convection on a
-512 x 512 lattice (phi, U, T on D2Q9 plus D2Q9 flow; update factors
-phi 1, U 1, T 2, flow 2; k = 0.15, Le = 10, inlet velocity 0.01 from the left,
-outflow right, periodic top/bottom, seed radius 8), FP32 storage and
-arithmetic, synthetic seeded inputs.
+Reported workload: large multi-dendrite thermosolutal growth with convection
+on an 8192 x 8192 lattice -- phi, U, T on D2Q5 lattices and the D2Q9 flow,
+32 seeds of radius 8 placed by seeded dart throwing (Poisson disc), each in a
+grain of its own crystal orientation in [0, pi/2) (Voronoi cells), Le = 100,
+k = 0.3, inlet velocity 0.005 from the left, outflow right, periodic
+top/bottom, update factors (phi 1, U 1, T 4, flow 2) -- with FP32 storage
+and arithmetic; the same workload with FP16 deviation storage (FP32
+arithmetic) is measured beside it ("mixed_storage"), with its error against
+the FP64 path at the same configuration.  Synthetic seeded inputs.
 
-One step = one schedule period = 2 base steps, in which every field updates
-at least once (phase x2, transfer x2, U x2, T x1, flow x1).  Coupled-field
-MLUPS = lattice nodes x base steps / s / 1e6.  L2 is flushed (a 512 MiB
-buffer written) between timed steps, and each step is timed on the device
-with CUDA events on the library's stream.
+One step = one schedule period = 4 base steps (phase x4, transfer x4, U x4,
+T x1, flow x2).  Coupled-field MLUPS = lattice nodes x base steps / s / 1e6.
+The state (~20 GB in FP32) is far larger than L2, so every step streams from
+HBM; each step is timed on the device with CUDA events on the library's
+stream.  Also reported: the 512 x 512 thermosolutal free dendrite with forced
+convection (L2-resident, flushed between steps) and the paper's D2Q9 scalar
+lattices at 8192^2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle (the only other implementation of
-the method here) on the host cores, on a bounded sample of the same workload.
+the method here) on the host cores, on a bounded sample of the same workload
+(a window of the 8192^2 lattice around a seed, one schedule period per step).
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -35,10 +43,14 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
-N_LATTICE = 512
-STEP_BASE = 2          # base steps per bench step (one schedule period)
+N_LATTICE = 512        # the thermosolutal + convection lattice
+STEP_BASE = 2          # its base steps per bench step (one schedule period)
+MD_N = 8192            # the multi-dendrite lattice (the reported workload)
+MD_PERIOD = 4          # its schedule period: lcm(1, 1, 4, 2) base steps
+MD_RESEED_BASE_STEPS = 800   # timed steps restart from the initial state after this many base steps
 METRIC = "coupled-field MLUPS"
 UNIT = "MLUPS"
+KINDS = ["phase", "transfer", "scalar_U", "scalar_T", "flow", "transport"]
 
 # element sizes of the stored populations and of the macroscopic fields per
 # storage precision (16-bit storage keeps FP32 macros)
@@ -109,28 +121,35 @@ def period_bytes(p, prec="f32"):
     return tot, n
 
 
+def step_bytes_md(p, prec, fused, q):
+    """Algorithmic bytes per node per base step of the multi-dendrite
+    workload: phase and transfer every step, U every N_U-th, T every N_T-th,
+    flow every N_F-th (the fused path: the phase plus the period mean of the
+    fused launches)."""
+    ab = algo_bytes(prec, q, ori=True)
+    if fused:
+        tb, _ = period_bytes(p, prec)
+        return ab["phase"] + tb / (2 * MD_PERIOD)
+    return (ab["phase"] + ab["transfer"] + ab["scalar_U"] / p.N_U + ab["scalar_T"] / p.N_T
+            + ab["flow"] / p.N_F)
+
+
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of ncu captures
-# per kernel variant ("q<velocities of the phase, U, T lattices>:kind:variant"),
-# summarised in profiles/: per launch on the 512^2 workload, and per node on
-# 8192^2 (times the nodes a launch processes for the 8192^2 measurement).
-# Reported only while the kernel sources hash to TRAFFIC_SOURCE_SHA; after any
-# change of the code the traffic is null until re-measured.
+# per kernel variant, summarised in profiles/.  TRAFFIC_PER_LAUNCH_512: per
+# launch on the 512^2 workload ("q<velocities of the phase, U, T lattices>:
+# kind:variant").  TRAFFIC_PER_NODE: per node, from a 2048^2 capture of the
+# multi-dendrite workload ("<storage>:q<velocities>:kind:variant", ":ori" for
+# the phase update with grain angles); a vector-strip launch moves the same
+# bytes per node at any lattice size, so the reported traffic of an 8192^2
+# launch is this figure times its nodes.  Reported only while the kernel
+# sources hash to TRAFFIC_SOURCE_SHA; after any change of the code the
+# traffic is null until re-measured.
 TRAFFIC_SOURCE_SHA = "ace4b0757b2c0eb7"
 # (transport: the mean of the period's two kinds of launch, transfer + U
 # alone and transfer + U + T + flow, like the algorithmic bytes it is set
 # against)
-TRAFFIC_PER_LAUNCH_512 = {"q5:transport:8": 14232256.0, "q5:transport:16": 14231744.0, "q5:phase:4": 7369088.0,
-                          "q5:phase:8": 7366272.0}
-# measured directly on an 8192^2 lattice (single-pass counters; the traffic
-# of a vector-strip launch does not depend on the data), FP32; the phase
-# update with grain angles (":ori")
-TRAFFIC_PER_NODE_8192 = {
-    "q5:flow:1016": 92.63, "q5:flow:1032": 93.35, "q5:phase:1016:ori": 52.21, "q5:phase:1032:ori": 52.41,
-    "q5:scalar_T:1016": 36.04, "q5:scalar_T:1032": 36.54, "q5:scalar_U:1016": 36.03, "q5:scalar_U:1032": 36.58,
-    "q5:transfer:1016": 23.80, "q5:transfer:1032": 23.84, "q9:flow:1016": 92.63, "q9:flow:1032": 93.47,
-    "q9:phase:1016:ori": 84.72, "q9:phase:1032:ori": 85.0, "q9:scalar_T:1016": 35.95, "q9:scalar_T:1032": 36.32,
-    "q9:scalar_U:1016": 35.97, "q9:scalar_U:1032": 36.4, "q9:transfer:1016": 23.80, "q9:transfer:1032": 23.83,
-}
+TRAFFIC_PER_LAUNCH_512 = {}
+TRAFFIC_PER_NODE = {}
 
 
 def kernel_source_sha():
@@ -156,19 +175,69 @@ def lattice_label(p):
     return "phi/U/T/flow on D2Q9" if getattr(p, "q_scalar", 9) != 5 else "phi/U/T on D2Q5, flow on D2Q9"
 
 
+STORAGE_LABEL = {"f64": "FP64", "f32": "FP32", "f16dev": "FP32 arithmetic, FP16 deviation storage",
+                 "bf16dev": "FP32 arithmetic, BF16 deviation storage"}
+
+
 def workload_label(p, prec="f32"):
     return (f"thermosolutal free dendrite + forced convection, {p.nx}x{p.ny}, {lattice_label(p)}, "
             f"N=({p.N_phi},{p.N_U},{p.N_T},{p.N_F}), {STORAGE_LABEL[prec]}")
 
 
-STORAGE_LABEL = {"f64": "FP64", "f32": "FP32", "f16dev": "FP32 arithmetic, FP16 deviation storage",
-                 "bf16dev": "FP32 arithmetic, BF16 deviation storage"}
+def md_label(p, prec="f32"):
+    return (f"{p.nx}x{p.ny} multi-dendrite thermosolutal growth with convection, 32 Poisson-disc seeds in "
+            f"grains of random crystal orientation, Le=100, k=0.3, u_in=0.005, "
+            f"N=({p.N_phi},{p.N_U},{p.N_T},{p.N_F}), {lattice_label(p)}, {STORAGE_LABEL[prec]}")
 
 
 def workload(n=None, q=5):
     wl = W.thermosolutal_convection(n=n or N_LATTICE, R=8.0)
     wl.params.q_scalar = q
     return wl
+
+
+def md_workload(n=None, q=5):
+    """Parameters and seed centres of the multi-dendrite workload (n x n)."""
+    p, pts = W.multi_dendrite_params(n or MD_N)
+    p.q_scalar = q
+    return p, pts
+
+
+def md_seeds(pts):
+    return [{"kind": "circle", "x": float(x), "y": float(y), "r": 8.0} for x, y in pts]
+
+
+_GRAINS = {}
+
+
+def grain_angles(n=MD_N):
+    """Voronoi grain angles of the n x n multi-dendrite lattice (one crystal
+    angle per seed, drawn in [0, pi/2)); built once per process and size."""
+    if n not in _GRAINS:
+        p, pts = W.multi_dendrite_params(n)
+        _GRAINS[n] = W.grain_orientation(pts, W.multi_dendrite_angles(len(pts)), 0, 0, n, n, rows=32)
+    return _GRAINS[n]
+
+
+def grain_angles_8192():
+    return grain_angles(8192)
+
+
+def md_window(q, w, seed_index=0):
+    """A bounded sample of the multi-dendrite workload for the CPU oracle: the
+    w x w window of the 8192^2 lattice centred on one seed, with the
+    lattice's physics, boundary kinds, grain angles and initial fields read on
+    the window.  Returns (params, fields, description)."""
+    p, pts = md_workload(MD_N, q)
+    cx, cy = pts[seed_index]
+    x0 = int(min(max(0, round(cx) - w // 2), MD_N - w))
+    y0 = int(min(max(0, round(cy) - w // 2), MD_N - w))
+    theta = W.grain_orientation(pts, W.multi_dendrite_angles(len(pts)), x0, y0, w, w)
+    fields = W.circle_seeds_window(p, pts, 8.0, x0, y0, w, w, U0=0.0, T0=-0.55)
+    fields["theta"] = theta
+    p.nx = p.ny = w
+    p.tip_cx, p.tip_cy = int(round(cx)) - x0, int(round(cy)) - y0
+    return p, fields, "%dx%d window of the 8192^2 lattice at (%d, %d) around seed %d" % (w, w, x0, y0, seed_index)
 
 
 def dist_env():
@@ -197,17 +266,18 @@ def job_throughput(nodes, base_steps_per_step, steps, world, ms_max):
 
 
 def gated_steps(torch, stream, flush, advance, steps, reinit=None):
-    """`steps` bench steps on `stream`: an L2 flush (untimed), then one
-    advance() between two CUDA events.  A bounded sleep kernel queued first
-    holds the stream while the host enqueues every step, so the device runs
-    the steps back to back from its queue and a pause of the host thread
-    (scheduling, the clock sampler's queries) cannot fall inside a timed
-    step.  The gate is checked: an event recorded behind the sleep must still
-    be pending once the host has enqueued the last step.  If the device got
-    there first (a host slower than the gate), the times hold host gaps: the
-    state is re-initialised with `reinit` and the steps are timed again
-    behind a gate four times longer, at most three attempts in all.
-    Returns (the per-step times in ms, whether the gate held)."""
+    """`steps` bench steps on `stream`: an L2 flush (untimed, skipped when
+    `flush` is None), then one advance() between two CUDA events.  A bounded
+    sleep kernel queued first holds the stream while the host enqueues every
+    step, so the device runs the steps back to back from its queue and a
+    pause of the host thread (scheduling, the clock sampler's queries) cannot
+    fall inside a timed step.  The gate is checked: an event recorded behind
+    the sleep must still be pending once the host has enqueued the last
+    step.  If the device got there first (a host slower than the gate), the
+    times hold host gaps: the state is re-initialised with `reinit` and the
+    steps are timed again behind a gate four times longer, at most three
+    attempts in all.  Returns (the per-step times in ms, whether the gate
+    held)."""
     gate_s = 0.01 + 1e-3 * steps
     for attempt in range(3):
         if attempt and reinit is not None:
@@ -220,7 +290,8 @@ def gated_steps(torch, stream, flush, advance, steps, reinit=None):
             gate.record(stream)
         for k in range(steps):
             with torch.cuda.stream(stream):
-                flush.fill_(float(k))
+                if flush is not None:
+                    flush.fill_(float(k))
                 ev[k][0].record(stream)
             advance()
             with torch.cuda.stream(stream):
@@ -319,63 +390,270 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(target_s: float = 12.0, max_steps: int = 4000, q: int = 5):
-    """The FP64 oracle on the host cores, on a bounded sample of the workload:
-    the full 512^2 lattice advanced for as many base steps as fit in ~target_s."""
+def cpu_baseline(target_s: float = 12.0, q: int = 5, w: int = 512):
+    """The FP64 oracle on the host cores, on a bounded sample of the
+    multi-dendrite workload: a w x w window of the 8192^2 lattice around a
+    seed (the lattice's physics and grain angles), advanced for as many
+    schedule periods as fit in ~target_s; then the next periods on one
+    thread."""
     import oracle
-    wl = workload(None, q)
-    o = oracle.Oracle(wl.params, wl.fields)
+    p, fields, what = md_window(q, w)
+    o = oracle.Oracle(p, fields)
     t0 = time.perf_counter()
     steps = 0
-    while steps < max_steps and (time.perf_counter() - t0) < target_s:
-        o.advance(STEP_BASE)
-        steps += STEP_BASE
+    while (time.perf_counter() - t0) < target_s:
+        o.advance(MD_PERIOD)
+        steps += MD_PERIOD
     dt = time.perf_counter() - t0
     cores = oracle.num_threads()
-    # the same oracle on one thread, a shorter sample continuing the run
     oracle.set_threads(1)
     t1, steps1 = time.perf_counter(), 0
-    while steps1 < max_steps and (time.perf_counter() - t1) < target_s / 3:
-        o.advance(STEP_BASE)
-        steps1 += STEP_BASE
+    while (time.perf_counter() - t1) < target_s / 3:
+        o.advance(MD_PERIOD)
+        steps1 += MD_PERIOD
     dt1 = time.perf_counter() - t1
     oracle.set_threads(cores)
     o.close()
-    nodes = wl.params.nx * wl.params.ny
+    nodes = p.nx * p.ny
     return {"value": nodes * steps / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "value_1_thread": nodes * steps1 / dt1 / 1e6,
-            "sample": "%d^2 thermosolutal+flow lattice (%s), first %d base steps, FP64 oracle (%.1f s); "
-                      "1 thread: the next %d base steps (%.1f s)" % (
-                N_LATTICE, lattice_label(wl.params), steps, dt, steps1, dt1)}
+            "sample": "%s (%s, FP64 oracle), the first %d base steps (%.1f s); 1 thread: the next %d base "
+                      "steps (%.1f s)" % (what, lattice_label(p), steps, dt, steps1, dt1)}
 
 
 def run_reference(args):
+    """The FP64 oracle on the host cores on the reported workload's metric:
+    each step one schedule period (4 base steps) of a 256 x 256 window of the
+    8192^2 multi-dendrite lattice around a seed."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
-    wl = workload(None, args.q_scalar)
-    o = oracle.Oracle(wl.params, wl.fields)
+    p, fields, what = md_window(args.q_scalar, 256)
+    o = oracle.Oracle(p, fields)
     for _ in range(args.warmup):
-        o.advance(STEP_BASE)
+        o.advance(MD_PERIOD)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        o.advance(STEP_BASE)
+        o.advance(MD_PERIOD)
     dt = time.perf_counter() - t0
-    nodes = wl.params.nx * wl.params.ny
-    v = nodes * STEP_BASE * args.steps / dt / 1e6
+    nodes = p.nx * p.ny
+    v = nodes * MD_PERIOD * args.steps / dt / 1e6
+    full, _ = md_workload(MD_N, args.q_scalar)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)",
-            "config": {"workload": workload_label(wl.params, args.precision or "f32"),
-                       "base_steps_per_step": STEP_BASE},
+            "config": {"workload": md_label(full, args.precision or "f32"), "base_steps_per_step": MD_PERIOD},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": "%d steps of %d base steps on the full %d^2 lattice" % (
-                                 args.steps, STEP_BASE, N_LATTICE)},
+                             "sample": "each step: one schedule period (%d base steps) of the %s" % (
+                                 MD_PERIOD, what)},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def timed_md_steps(torch, sim, steps, reinit):
+    """`steps` schedule periods, each between two CUDA events on the library
+    stream; every MD_RESEED_BASE_STEPS base steps (untimed, between events)
+    the state restarts from the initial fields, so every timed step lies in
+    the workload's first base steps.  Returns per-step milliseconds."""
+    chunk = max(1, MD_RESEED_BASE_STEPS // MD_PERIOD)
+    times = []
+    done = 0
+    while done < steps:
+        n = min(chunk, steps - done)
+        if done:
+            reinit()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for k in range(n):
+            with torch.cuda.stream(sim.stream):
+                ev[k][0].record(sim.stream)
+            sim.advance(MD_PERIOD)
+            with torch.cuda.stream(sim.stream):
+                ev[k][1].record(sim.stream)
+        torch.cuda.synchronize()
+        times += [a.elapsed_time(b) for a, b in ev]
+        done += n
+    return times
+
+
+def measure_md(args, torch, lbm, local, dev, prec, q, world=1, with_e2e=False):
+    """One multi-dendrite measurement (n x n, storage `prec`, velocities q of
+    the phase, U, T lattices): seeded through lbm_init_seed, autotuned on the
+    live state, `args.steps` timed schedule periods from the initial state,
+    then the same steps again with the dominant kernel's CUDA events inside
+    the graphs for its launch duration; with_e2e adds the end-to-end pass
+    through the public API with pinned host buffers."""
+    p, pts = md_workload(args.lattice, q)
+    nodes = p.nx * p.ny
+    sim = lbm.Simulation(p, precision=prec)
+    if args.fusion != "auto":
+        sim.set_fusion(args.fusion == "on")
+    sim.set_orientation(grain_angles(p.nx))          # each grain in its own crystal frame
+    seeds = md_seeds(pts)
+
+    def reinit():
+        sim.init_seed(seeds, U0=0.0, T0=-0.55)
+
+    reinit()
+    for _ in range(max(args.warmup, 3)):
+        sim.advance(MD_PERIOD)
+    tiles = sim.autotune(reps=3)
+    for spec in args.tile or []:            # fixed kernel variants (profiling runs)
+        kind, v = spec.split("=")
+        sim.set_tile(kind, int(v))
+        tiles[kind] = int(v)
+    sim.advance(MD_PERIOD)
+    sim.timing_enable(KINDS)                # untimed pre-pass: which kind dominates
+    sim.advance(2 * MD_PERIOD)
+    pre = sim.timing_read(reset=True)
+    dom = max(KINDS, key=lambda k: pre[k][0])
+    sim.timing_enable([])
+    sim.advance(MD_PERIOD)                  # recapture without timing nodes, untimed
+    reinit()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches0 = sim.launch_counts()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
+    w0 = time.perf_counter()
+    times = timed_md_steps(torch, sim, args.steps, reinit)
+    wall = time.perf_counter() - w0
+    clk = clocks.stop()
+    launches1 = sim.launch_counts()
+    if world > 1:
+        torch.distributed.barrier()
+    # launches of the re-seeding between chunks are not inside timed steps
+    reseeds = (args.steps - 1) // max(1, MD_RESEED_BASE_STEPS // MD_PERIOD)
+    gpu_launches = int(sum(launches1[k] - launches0[k] for k in launches1 if k != "init"))
+    ms = sum(times)
+    ms_max = max_over_ranks(ms, dev)
+    fused = sim.fused
+    # the dominant kernel's own launches, timed inside the graphs
+    sim.timing_enable([dom])
+    sim.advance(MD_PERIOD)
+    sim.timing_read(reset=True)
+    reinit()
+    n_dom = min(args.steps, 50)
+    ms_instr = sum(timed_md_steps(torch, sim, n_dom, reinit))
+    kt = sim.timing_read(reset=True)
+    sim.timing_enable([])
+    finite = not sim.diagnostics()["nonfinite"]
+
+    peak, peak_kind = measured_peaks()
+    sb = step_bytes_md(p, prec, fused, q)
+    gbs = sb * nodes * MD_PERIOD * args.steps / (ms * 1e-3) / 1e9
+    dom_algo = algo_bytes(prec, q, ori=True)
+    tb, tn = period_bytes(p, prec)
+    dom_algo["transport"] = tb / max(tn, 1)
+    avg_s = kt[dom][0] * 1e-3 / max(kt[dom][1], 1)
+    dom_gbs = dom_algo[dom] * nodes / avg_s / 1e9
+    traffic, traffic_note = None, None
+    key = "%s:q%d:%s:%d%s" % (prec, q, dom, tiles[dom], ":ori" if dom == "phase" else "")
+    if TRAFFIC_SOURCE_SHA == kernel_source_sha() and key in TRAFFIC_PER_NODE:
+        traffic = TRAFFIC_PER_NODE[key] * nodes
+        traffic_note = "ncu capture of this variant on the 2048^2 lattice, per node x the nodes of one launch"
+    out = {
+        "workload": md_label(p, prec), "storage": prec, "nodes": nodes,
+        "value": job_throughput(nodes, MD_PERIOD, args.steps, world, ms_max), "unit": UNIT,
+        "ms_per_step": ms_max / args.steps, "ms_per_step_median": statistics.median(times),
+        "base_steps_per_step": MD_PERIOD, "fused_transport": fused, "gpu_launches": gpu_launches,
+        "reseeds_between_timed_steps": reseeds, "wall_s_timed_region": wall,
+        "step": {"algo_bytes_per_node_per_base_step": sb, "achieved": gbs, "peak": peak, "unit": "GB/s",
+                 "frac": gbs / peak, "peak_kind": peak_kind},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": dom_gbs / peak, "traffic": traffic, "traffic_note": traffic_note,
+                     "peak_kind": peak_kind, "algo_bytes_per_node": dom_algo[dom],
+                     "avg_launch_us": avg_s * 1e6, "launches_timed": kt[dom][1],
+                     "timed_in": "a second timed region of %d steps with the kernel's CUDA events inside the "
+                                 "graphs (%.3f ms per step there against %.3f without them)" % (
+                                     n_dom, ms_instr / n_dom, ms / args.steps)},
+        "kernel_avg_us_prepass": {k: pre[k][0] / max(pre[k][1], 1) * 1e3 for k in KINDS},
+        "tiles": {k: tiles[k] for k in KINDS}, "clocks": clk,
+        "state_finite_after_timed_regions": finite,
+        "l2": "inputs larger than L2 (%.1f GB of device state)" % (sim.device_bytes() / 1e9),
+    }
+    if with_e2e and not args.no_e2e:
+        out["e2e"] = md_e2e(args, torch, sim, p, pts, world)
+    sim.close()
+    return out
+
+
+def md_e2e(args, torch, sim, p, pts, world):
+    """End to end through the public API with pinned host buffers, each step:
+    lbm_init_fields from the six FP64 host fields of the initial state,
+    lbm_advance of one schedule period, lbm_fields of phi back into a host
+    FP64 buffer; host time over the steps with a synchronisation (and a
+    barrier under torchrun) on both sides."""
+    f = W.multi_dendrite_fields(p, pts)
+    host = {k: torch.from_numpy(f[k]).pin_memory().numpy() for k in ("phi", "U", "T", "ux", "uy", "rho")}
+    del f
+    out_phi = torch.empty((p.ny, p.nx), dtype=torch.float64).pin_memory().numpy()
+    steps = max(3, min(args.steps, 10))
+    sim.init_fields(host)                # one untimed pass (first-touch of the pinned pages)
+    sim.advance(MD_PERIOD)
+    sim.field("phi", out=out_phi)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.init_fields(host)
+        sim.advance(MD_PERIOD)
+        sim.field("phi", out=out_phi)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    dt = time.perf_counter() - t0
+    dt = max_over_ranks(dt)
+    nodes = p.nx * p.ny
+    return {"value": nodes * MD_PERIOD * steps * world / dt / 1e6, "unit": UNIT,
+            "h2d_bytes_per_step": 6 * 8 * nodes, "d2h_bytes_per_step": 8 * nodes, "steps": steps,
+            "ms_per_step": dt * 1e3 / steps,
+            "calls": "lbm_init_fields(6 pinned host FP64 fields) + lbm_advance(4) + lbm_fields(phi -> pinned "
+                     "host FP64) per step"}
+
+
+def md_accuracy(args, torch, lbm, dev, q, precs=("f32", "f16dev"), base_steps=200):
+    """Error of the FP32 and 16-bit storage forms against the FP64 path on the
+    same multi-dendrite configuration (the FP64 path itself matches the
+    oracle within 1e-10 in the parity tests): max-abs phi, U, T after
+    `base_steps` base steps, and the difference of the relative solute drift
+    R_M = (M_C - M_C(0)) / M_C(0)."""
+    p, pts = md_workload(args.lattice, q)
+    seeds = md_seeds(pts)
+    res = {}
+    ref = None
+    for prec in ("f64",) + tuple(precs):
+        sim = lbm.Simulation(p, precision=prec)
+        sim.set_orientation(grain_angles(p.nx))
+        sim.init_seed(seeds, U0=0.0, T0=-0.55)
+        m0 = sim.diagnostics()["M_C"]
+        sim.advance(base_steps)
+        d = sim.diagnostics()
+        fl = {}
+        for k in ("phi", "U", "T"):
+            t = torch.empty((p.ny, p.nx), dtype=torch.float64, device=dev)
+            sim.field(k, out=t)
+            fl[k] = t
+        torch.cuda.synchronize()
+        sim.close()
+        rm = (d["M_C"] - m0) / m0
+        if ref is None:
+            ref = (fl, rm)
+            res["f64"] = {"R_M": rm}
+            continue
+        res[prec] = {"max_abs_err_vs_f64": {k: float((fl[k] - ref[0][k]).abs().max()) for k in fl},
+                     "R_M": rm, "R_M_diff_vs_f64": abs(rm - ref[1])}
+        del fl
+    del ref
+    torch.cuda.empty_cache()
+    res["base_steps"] = base_steps
+    return res
 
 
 def run_ours(args):
@@ -388,299 +666,136 @@ def run_ours(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
-    wl = workload(args.lattice, args.q_scalar)
-    p = wl.params
-    nodes = p.nx * p.ny
     prec = args.precision or "f32"
-    if args.orientation is not None:        # one grain turned by this angle (profiling of the angle reads)
-        wl.fields["theta"] = np.full((p.ny, p.nx), float(args.orientation))
-    sim = lbm.Simulation(p, precision=prec)
-    if args.fusion != "auto":
-        sim.set_fusion(args.fusion == "on")
-    sim.init_fields(wl.fields)
-    stream = sim.stream
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-            torch.cuda.synchronize()
-
-    # warm-up, tile autotuning on the live state (leaves it unchanged), graph capture
-    for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
-        sim.advance(STEP_BASE)
-    tiles = sim.autotune(reps=10)
-    if nodes * 200 < 126 * 2 ** 20 and not args.tile:     # state in L2: refine on flushed steps
-        tiles = refine_tiles(sim, torch, flush, tiles)
-    for spec in args.tile or []:            # fixed kernel variants (profiling runs)
-        kind, v = spec.split("=")
-        sim.set_tile(kind, int(v))
-        tiles[kind] = int(v)
-    sim.advance(STEP_BASE)
-    kinds = ["phase", "transfer", "scalar_U", "scalar_T", "flow", "transport"]
-    tb, tn = period_bytes(p, prec)
-    algo = algo_bytes(prec, args.q_scalar)
-    algo["transport"] = tb / max(tn, 1)       # mean over the period's transport launches
-    # untimed pre-pass with every kind timed, to find the dominant kernel; the
-    # timed region then times only that kind (fewest event nodes in the graph)
-    sim.timing_enable(kinds)
-    for _ in range(10):
-        with torch.cuda.stream(stream):
-            flush.fill_(0.0)
-        sim.advance(STEP_BASE)
-    pre = sim.timing_read(reset=True)
-    dom = max(kinds, key=lambda k: pre[k][0])
-
-    def timed_region():
-        """args.steps steps (the caller re-initialises the state first, so
-        that every timed region covers the first 2 * steps base steps of the
-        workload), L2 flushed before each step, CUDA events around each step
-        on the library stream; returns (total ms, wall s, whether the gate held)."""
-        barrier()
-        w0 = time.perf_counter()
-        t, held = gated_steps(torch, stream, flush, lambda: sim.advance(STEP_BASE), args.steps,
-                              reinit=lambda: sim.init_fields(wl.fields))
-        barrier()
-        return sum(t), time.perf_counter() - w0, held
-
-    # the timed region: graphs without timing nodes (an event-record node
-    # around a launch inside a graph adds several microseconds per launch)
-    sim.timing_enable([])
-    sim.advance(STEP_BASE)           # recapture without timing nodes, untimed
-    sim.init_fields(wl.fields)       # untimed: the timed steps start from the initial state
-    launches0 = sim.launch_counts()
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    ms, wall, gate_held = timed_region()
-    clk = clocks.stop()
-    launches1 = sim.launch_counts()
-    gpu_launches = int(sum(launches1[k] - launches0[k] for k in launches1))
-    ms_max = max_over_ranks(ms, dev)
-    value = job_throughput(nodes, STEP_BASE, args.steps, world, ms_max)
-    # the dominant kernel's own launches: a second timed region of the same
-    # steps with its CUDA events recorded inside the graphs
-    sim.timing_enable([dom])
-    sim.advance(STEP_BASE)           # recapture with the dominant kind's timing nodes, untimed
-    sim.timing_read(reset=True)
-    sim.init_fields(wl.fields)
-    ms_instr, _, _ = timed_region()
-    ktimes = sim.timing_read(reset=True)
-    sim.timing_enable([])
-    state_finite = not sim.diagnostics()["nonfinite"]
-
-    # roofline of the dominant kernel (largest share of the timed kernel time)
-    dom_ms, dom_n = ktimes[dom]
-    avg_s = dom_ms * 1e-3 / max(dom_n, 1)
-    peak, peak_kind = measured_peaks()
-    achieved = algo[dom] * nodes / avg_s / 1e9
-    traffic = None
-    if args.lattice in (None, N_LATTICE) and prec == "f32" and TRAFFIC_SOURCE_SHA == kernel_source_sha():
-        traffic = TRAFFIC_PER_LAUNCH_512.get("q%d:%s:%d" % (args.q_scalar, dom, tiles[dom]))
-
-    # end to end through the public API with pinned host buffers
-    host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in wl.fields.items()}
-    host_np = {k: v.numpy() for k, v in host.items()}
-    out_phi = torch.empty((p.ny, p.nx), dtype=torch.float64).pin_memory().numpy()
-    e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 50))
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        sim.init_fields(host_np)
-        sim.advance(STEP_BASE)
-        sim.field("phi", out=out_phi)
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e_val = nodes * STEP_BASE * e2e_steps * world / e2e_s / 1e6 if e2e_steps else None
-    h2d = 6 * 8 * nodes
-    d2h = 8 * nodes
-
+    q = args.q_scalar
+    main = measure_md(args, torch, lbm, local, dev, prec, q, world=world, with_e2e=True)
+    line = None
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "f64" else "f32",
             "data": "synthetic (seeded)",
-            "config": {"workload": workload_label(p, prec), "storage": prec, "base_steps_per_step": STEP_BASE,
-                       "fused_transport": sim.fused, "fusion_choice": args.fusion,
-                       "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "algo_bytes_per_node": algo[dom], "avg_launch_us": avg_s * 1e6,
-                         "launches_timed": dom_n,
-                         "timed_in": "a second timed region of the same steps with the kernel's CUDA events "
-                                     "inside the graphs (%.1f us per step there against %.1f without them)" % (
-                                         ms_instr * 1e3 / args.steps, ms * 1e3 / args.steps)},
-            "kernel_avg_us_prepass": {k: pre[k][0] / max(pre[k][1], 1) * 1e3 for k in kinds},
-            "tiles": {k: tiles[k] for k in kinds},
-            "gpu_launches": gpu_launches,
-            "wall_s_timed_region": wall,
-            "gate_held": gate_held,
-            "state_finite_after_timed_regions": state_finite,
-            "timing": "CUDA events around each step's advance on the library stream; the steps are queued "
-                      "behind a bounded sleep kernel (included in wall_s_timed_region, not in value) that is checked "
-                      "to outlast the host's enqueueing (re-timed behind a longer one otherwise)",
-            "clocks": clk,
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": e2e_steps, "calls": "init_fields(host f64 x6) + advance(2) + field(phi -> host)"},
+            "config": {"workload": main["workload"], "storage": prec, "base_steps_per_step": MD_PERIOD,
+                       "fused_transport": main["fused_transport"], "l2": main["l2"],
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "roofline": main["roofline"], "step_roofline": main["step"],
+            "gpu_launches": main["gpu_launches"], "clocks": main["clocks"], "e2e": main.get("e2e"),
+            "timing": "CUDA events around each step's lbm_advance on the library stream; every %d timed steps "
+                      "the state restarts from the initial fields between steps (untimed)" % max(
+                          1, MD_RESEED_BASE_STEPS // MD_PERIOD),
+            "details": {k: main[k] for k in ("ms_per_step_median", "kernel_avg_us_prepass", "tiles",
+                                            "wall_s_timed_region", "state_finite_after_timed_regions",
+                                            "reseeds_between_timed_steps", "nodes")},
         }
-    sim.close()
-    del flush
+    if world == 1 and not args.no_extra:
+        torch.cuda.empty_cache()
+        mixed = measure_md(args, torch, lbm, local, dev, "f16dev", q)
+        torch.cuda.empty_cache()
+        mixed["speedup_vs_fp32"] = mixed["value"] / main["value"]
+        if not args.no_accuracy:
+            mixed["accuracy"] = md_accuracy(args, torch, lbm, dev, q)
+        line["mixed_storage"] = mixed
+        torch.cuda.empty_cache()
+        line["d2q%d" % (9 if q == 5 else 5)] = {
+            "multi_dendrite": measure_md(args, torch, lbm, local, dev, prec, 9 if q == 5 else 5)}
+        torch.cuda.empty_cache()
+        line["convection_512"] = measure_convection512(args, torch, lbm, local, dev, q)
     if rank == 0:
-        if not args.no_large and world == 1:
-            line["large_lattice"] = large_lattice(args, torch, lbm, local, measured_peaks, args.q_scalar)
-        if not args.no_alt_lattice and world == 1:
-            alt = 9 if args.q_scalar == 5 else 5
-            line["d2q%d" % alt] = lattice_variant(args, torch, lbm, local, dev, 512 * 1024 * 1024, alt)
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(q=args.q_scalar)
+            line["cpu_baseline"] = cpu_baseline(q=q)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
-def lattice_variant(args, torch, lbm, local, dev, flush_bytes, q):
-    """The same workloads with the other velocity set of the phase, U and T
-    lattices (q = 9: the paper's D2Q9; q = 5: D2Q5; the flow is D2Q9 in
-    both): the 512^2 configuration, timed as the main measurement (CUDA
-    events on the library stream, L2 flushed between steps, from the
-    re-initialised state), and the 8192^2 HBM-bound measurement with its
-    dominant-kernel roofline."""
-    wl = workload(args.lattice, q)
+def measure_convection512(args, torch, lbm, local, dev, q, print_line=False):
+    """The 512^2 thermosolutal free dendrite with forced convection (its
+    state fits L2): L2 flushed (512 MiB write) before every step, steps of
+    one schedule period (2 base steps) queued behind a checked sleep gate,
+    each timed with CUDA events; then the dominant kernel's launch time from
+    a second timed region with its events inside the graphs."""
+    wl = workload(N_LATTICE if args.workload != "convection512" else args.lattice, q)
     p = wl.params
+    nodes = p.nx * p.ny
     prec = args.precision or "f32"
     sim = lbm.Simulation(p, precision=prec)
     if args.fusion != "auto":
         sim.set_fusion(args.fusion == "on")
     sim.init_fields(wl.fields)
     stream = sim.stream
-    flush = torch.empty(flush_bytes // 4, dtype=torch.float32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(max(args.warmup, 3)):
         sim.advance(STEP_BASE)
     tiles = sim.autotune(reps=10)
-    if p.nx * p.ny * 200 < 126 * 2 ** 20:
+    if nodes * 200 < 126 * 2 ** 20 and not args.tile:     # state in L2: refine on flushed steps
         tiles = refine_tiles(sim, torch, flush, tiles)
+    for spec in args.tile or []:
+        kind, v = spec.split("=")
+        sim.set_tile(kind, int(v))
+        tiles[kind] = int(v)
     sim.advance(STEP_BASE)
-    steps = min(args.steps, 400)        # within the first 800 base steps (the D2Q9 reading of this
-    sim.init_fields(wl.fields)          # workload turns non-finite after ~2 100)
-    torch.cuda.synchronize()
-    t, held = gated_steps(torch, stream, flush, lambda: sim.advance(STEP_BASE), steps,
-                          reinit=lambda: sim.init_fields(wl.fields))
-    ms = sum(t)
-    fused = sim.fused
-    finite = not sim.diagnostics()["nonfinite"]
-    sim.close()
-    del flush
-    nodes = p.nx * p.ny
-    out = {"workload": workload_label(p, prec), "value": nodes * STEP_BASE * steps / (ms * 1e-3) / 1e6,
-           "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "gate_held": held, "fused_transport": fused,
-           "tiles": {k: tiles[k] for k in ("phase", "transfer", "scalar_U", "scalar_T", "flow", "transport")},
-           "l2": "flushed between steps (512 MiB write)", "state_finite_after_timed_region": finite}
-    if not args.no_large:
-        out["large_lattice"] = large_lattice(args, torch, lbm, local, measured_peaks, q)
-    return out
-
-
-_GRAINS = {}
-
-
-def grain_angles_8192():
-    """Voronoi grain angles of the 8192^2 multi-dendrite lattice (one crystal
-    angle per seed, drawn in [0, pi/2)); built once per process."""
-    if "theta" not in _GRAINS:
-        p, pts = W.multi_dendrite_params(8192)
-        _GRAINS["theta"] = W.grain_orientation(pts, W.multi_dendrite_angles(len(pts)), 0, 0, 8192, 8192, rows=32)
-    return _GRAINS["theta"]
-
-
-def large_lattice(args, torch, lbm, local, peaks_fn, q=9):
-    """The HBM-bound regime: the 8192^2 multi-dendrite workload (thermosolutal
-    growth with convection, 32 Poisson-disc seeds, update factors (1, 1, 4,
-    2), FP32; about 20 GB of state, so every step streams from HBM).  Seeded
-    on the device's own data path (lbm_init_seed), autotuned, then timed over
-    whole schedule periods of 4 base steps with CUDA events."""
-    p, pts = W.multi_dendrite_params(8192)
-    p.q_scalar = q
-    prec = args.precision or "f32"
-    sim = lbm.Simulation(p, precision=prec)
-    sim.set_orientation(grain_angles_8192())          # each grain in its own crystal frame
-    sim.init_seed([{"kind": "circle", "x": float(x), "y": float(y), "r": 8.0} for x, y in pts], U0=0.0, T0=-0.55)
-    period = 4
-    for _ in range(2):
-        sim.advance(period)
-    tiles = sim.autotune(reps=3)
-    sim.advance(period)
-    kinds = ["phase", "transfer", "scalar_U", "scalar_T", "flow", "transport"]
-    sim.timing_enable(kinds)
-    sim.advance(2 * period)
+    tb, tn = period_bytes(p, prec)
+    algo = algo_bytes(prec, q)
+    algo["transport"] = tb / max(tn, 1)
+    sim.timing_enable(KINDS)
+    for _ in range(10):
+        with torch.cuda.stream(stream):
+            flush.fill_(0.0)
+        sim.advance(STEP_BASE)
     pre = sim.timing_read(reset=True)
-    dom = max(kinds, key=lambda k: pre[k][0])
-    steps = 10
-    stream = sim.stream
+    dom = max(KINDS, key=lambda k: pre[k][0])
+    steps = min(args.steps, 400)        # within the workload's first 800 base steps
 
-    def timed_periods():
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    def timed_region():
         torch.cuda.synchronize()
-        with torch.cuda.stream(stream):
-            e0.record(stream)
-        for _ in range(steps):
-            sim.advance(period)
-        with torch.cuda.stream(stream):
-            e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1)
+        t, held = gated_steps(torch, stream, flush, lambda: sim.advance(STEP_BASE), steps,
+                              reinit=lambda: sim.init_fields(wl.fields))
+        return sum(t), held
 
-    # timed region without timing nodes in the graphs, then the same periods
-    # again with the dominant kind's CUDA events for its launch duration
     sim.timing_enable([])
-    sim.advance(period)
+    sim.advance(STEP_BASE)
+    sim.init_fields(wl.fields)
+    l0 = sim.launch_counts()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.2)
-    ms = timed_periods()
+    ms, held = timed_region()
     clk = clocks.stop()
+    l1 = sim.launch_counts()
     sim.timing_enable([dom])
-    sim.advance(period)
+    sim.advance(STEP_BASE)
     sim.timing_read(reset=True)
-    timed_periods()
+    sim.init_fields(wl.fields)
+    ms_instr, _ = timed_region()
     kt = sim.timing_read(reset=True)
+    sim.timing_enable([])
+    finite = not sim.diagnostics()["nonfinite"]
     fused = sim.fused
     sim.close()
-    nodes = p.nx * p.ny
-    base = steps * period
-    ab = algo_bytes(prec, q, ori=True)
-    # algorithmic bytes per node per base step of the staged path (the fused
-    # path moves fewer); U every step, T every 4th, flow every 2nd
-    step_bytes = ab["phase"] + ab["transfer"] + ab["scalar_U"] + ab["scalar_T"] / p.N_T + ab["flow"] / p.N_F
-    if fused:
-        tb, tn = period_bytes(p, prec)
-        step_bytes = ab["phase"] + tb / (2 * period)
-    peak, peak_kind = peaks_fn()
-    gbs = step_bytes * nodes * base / (ms * 1e-3) / 1e9
-    dom_algo = dict(ab)
-    tb, tn = period_bytes(p, prec)
-    dom_algo["transport"] = tb / max(tn, 1)
-    avg_s = kt[dom][0] * 1e-3 / max(kt[dom][1], 1)
-    dom_gbs = dom_algo[dom] * nodes / avg_s / 1e9
-    traffic, traffic_note = None, None
-    key = "q%d:%s:%d%s" % (q, dom, tiles[dom], ":ori" if dom == "phase" else "")
-    if prec == "f32" and TRAFFIC_SOURCE_SHA == kernel_source_sha() and key in TRAFFIC_PER_NODE_8192:
-        traffic, traffic_note = TRAFFIC_PER_NODE_8192[key] * nodes, "8192^2 capture of this variant"
-    return {"workload": "8192x8192 multi-dendrite thermosolutal growth with convection, 32 seeds in grains of "
-                        "random crystal orientation, N=(1,1,4,2), "
-                        + lattice_label(p) + ", " + STORAGE_LABEL[prec], "storage": prec,
-            "value": nodes * base / (ms * 1e-3) / 1e6, "unit": UNIT, "base_steps": base,
-            "ms_per_period": ms / steps, "fused_transport": fused,
-            "step": {"algo_bytes_per_node_per_base_step": step_bytes, "achieved_GBs": gbs, "peak": peak,
-                     "frac": gbs / peak, "peak_kind": peak_kind},
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
-                         "frac": dom_gbs / peak, "traffic": traffic, "traffic_note": traffic_note,
-                         "algo_bytes_per_node": dom_algo[dom], "avg_launch_us": avg_s * 1e6,
-                         "launches_timed": kt[dom][1]},
-            "kernel_avg_us_prepass": {k: pre[k][0] / max(pre[k][1], 1) * 1e3 for k in kinds},
-            "tiles": {k: tiles[k] for k in kinds}, "clocks": clk, "l2": "inputs larger than L2 (~20 GB state)"}
+    del flush
+    dom_ms, dom_n = kt[dom]
+    avg_s = dom_ms * 1e-3 / max(dom_n, 1)
+    peak, peak_kind = measured_peaks()
+    achieved = algo[dom] * nodes / avg_s / 1e9
+    traffic = None
+    if prec == "f32" and TRAFFIC_SOURCE_SHA == kernel_source_sha():
+        traffic = TRAFFIC_PER_LAUNCH_512.get("q%d:%s:%d" % (q, dom, tiles[dom]))
+    return {"workload": workload_label(p, prec), "value": nodes * STEP_BASE * steps / (ms * 1e-3) / 1e6,
+            "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "base_steps_per_step": STEP_BASE,
+            "gate_held": held, "fused_transport": fused, "gpu_launches": int(sum(l1[k] - l0[k] for k in l1)),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "algo_bytes_per_node": algo[dom], "avg_launch_us": avg_s * 1e6,
+                         "launches_timed": dom_n,
+                         "note": "the state (~51 MB) fits L2: the fraction is algorithmic bytes over time, "
+                                 "not DRAM throughput"},
+            "kernel_avg_us_prepass": {k: pre[k][0] / max(pre[k][1], 1) * 1e3 for k in KINDS},
+            "tiles": {k: tiles[k] for k in KINDS}, "clocks": clk,
+            "l2": "flushed between steps (512 MiB write)", "state_finite_after_timed_region": finite,
+            "timed_in": "%.1f us per step with the dominant kernel's events in the graphs against %.1f without" % (
+                ms_instr * 1e3 / steps, ms * 1e3 / steps)}
 
 
 def run_ensemble(args):
@@ -966,34 +1081,119 @@ def run_configs(args):
     return 0
 
 
+def run_ablation(args):
+    """Source-coupling ablation (Sec. 4.4): the directional saline-water case
+    with the evolving temperature (1000 x 1000, Table 1, N_U = Le) at
+    Le in {1, 10, 100}, instantaneous against accumulated coupling, each
+    advanced to `--ablation-steps` base steps (40 000 by default: the paper
+    reports the accumulated Le = 100 run non-finite at 0.0532 ms = 26 600
+    base steps).  Every `--ablation-every` base steps: S_phi and J_U (maxima
+    since the previous sample), R_M; a run stops at the first sample that
+    sees a non-finite field and reports that base step."""
+    import torch
+    import paper_2609_25670_b300 as lbm
+    prec = args.precision or "f32"
+    total, every = args.ablation_steps, args.ablation_every
+    runs = []
+    ms_total, nodes_steps = 0.0, 0
+    for Le in (1, 10, 100):
+        for coupling in ("instantaneous", "accumulated"):
+            wl = W.directional_evolving_T(Le=Le)
+            wl.params.accumulated = coupling == "accumulated"
+            sim = lbm.Simulation(wl.params, precision=prec)
+            sim.init_fields(wl.fields)
+            m0 = sim.diagnostics()["M_C"]
+            hist, bad, done, ms = [], None, 0, 0.0
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            while done < total:
+                n = min(every, total - done)
+                with torch.cuda.stream(sim.stream):
+                    e0.record(sim.stream)
+                sim.advance(n)
+                with torch.cuda.stream(sim.stream):
+                    e1.record(sim.stream)
+                d = sim.diagnostics()
+                ms += e0.elapsed_time(e1)
+                done += n
+                if d["nonfinite"]:
+                    bad = done
+                    break
+                hist.append((done, d["S_phi"], d["J_U"], (d["M_C"] - m0) / m0))
+            sim.close()
+            ms_total += ms
+            nodes_steps += wl.params.nx * wl.params.ny * done
+            h = np.asarray(hist) if hist else np.zeros((0, 4))
+            js = h[:, 2] if len(h) else np.zeros(1)
+            runs.append({"Le": Le, "N_U": Le, "coupling": coupling, "base_steps": done,
+                         "nonfinite_at_base_step": bad,
+                         "max_S_phi": float(h[:, 1].max()) if len(h) else None,
+                         "max_J_U": float(js.max()), "median_J_U": float(np.median(js)),
+                         "J_U_pulse_ratio": float(js.max() / max(np.median(js), 1e-300)),
+                         "R_M_last": float(h[-1, 3]) if len(h) else None,
+                         "mlups": wl.params.nx * wl.params.ny * done / (ms * 1e-3) / 1e6,
+                         "history_every_%d" % every: [[int(a), float(b), float(c), float(r)] for a, b, c, r in h]})
+    inst100 = next(r for r in runs if r["Le"] == 100 and r["coupling"] == "instantaneous")
+    line = {"metric": METRIC + " (source-coupling ablation)", "value": inst100["mlups"], "unit": UNIT,
+            "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == "f64" else "f32", "data": "synthetic (seeded)",
+            "config": {"workload": "Sec. 4.4 directional saline water with evolving T, 1000x1000, N_U = Le, "
+                                   "instantaneous vs accumulated coupling, %d base steps, samples every %d" % (
+                                       total, every), "storage": prec},
+            "summary": {"%s_Le%d" % (r["coupling"], r["Le"]): {k: r[k] for k in (
+                "nonfinite_at_base_step", "max_S_phi", "max_J_U", "J_U_pulse_ratio", "R_M_last")} for r in runs},
+            "runs": runs}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_convection512(args):
+    """The 512^2 thermosolutal + convection measurement alone (profiling runs:
+    --lattice sets its size)."""
+    import torch
+    import paper_2609_25670_b300 as lbm
+    dev = torch.device("cuda", torch.cuda.current_device())
+    r = measure_convection512(args, torch, lbm, 0, dev, args.q_scalar)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": r["steps"],
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if (args.precision or "f32") == "f64" else "f32",
+            "data": "synthetic (seeded)", "config": {"workload": r["workload"], "l2": r["l2"]},
+            "roofline": r["roofline"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "details": r}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="convection512", choices=["convection512", "ensemble", "sweep", "configs"],
-                    help="convection512: the reported workload; ensemble: batched-ensemble measurement; "
-                         "sweep: update-factor sweeps (thermal dendrite N_T, directional Le)")
+    ap.add_argument("--workload", default="multidendrite8192",
+                    choices=["multidendrite8192", "convection512", "ensemble", "sweep", "configs", "ablation"],
+                    help="multidendrite8192: the reported workload (with the FP16 arm, the D2Q9 lattices and "
+                         "the 512^2 case as extra keys); convection512: the 512^2 case alone; ensemble: "
+                         "batched-ensemble measurement; sweep: update-factor sweeps; configs: the workload list "
+                         "at its stated lengths; ablation: the source-coupling ablation")
     ap.add_argument("--members", type=int, default=64)
+    ap.add_argument("--ablation-steps", type=int, default=40000)
+    ap.add_argument("--ablation-every", type=int, default=200)
     ap.add_argument("--precision", default=None)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
-    ap.add_argument("--no-large", action="store_true", help="skip the 8192^2 HBM-bound measurement")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="only the reported measurement (no FP16 arm, other lattice or 512^2 case)")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the FP64 comparison of the FP16 arm")
     ap.add_argument("--fusion", default="auto", choices=["auto", "on", "off"],
                     help="one fused transport launch per base step (on), one launch per stage (off), "
                          "or the autotuner's choice (auto)")
     ap.add_argument("--tile", action="append", metavar="KIND=V",
-                    help="fix a kernel variant after autotuning (profiling runs): V > 0 tile height, V < 0 strip height")
+                    help="fix a kernel variant after autotuning (profiling runs): V > 0 tile height, V < 0 strip "
+                         "height, 1000 + H vector strip height")
     ap.add_argument("--q-scalar", type=int, default=5, choices=[9, 5],
                     help="velocities of the phase, U and T lattices: 5 (D2Q5, as the workload list states "
                          "them; default) or 9 (the paper's D2Q9)")
-    ap.add_argument("--orientation", type=float, default=None,
-                    help="crystal angle of the (single) grain of the main workload (profiling runs)")
-    ap.add_argument("--no-alt-lattice", action="store_true",
-                    help="skip the measurement on the other velocity set")
     ap.add_argument("--lattice", type=int, default=None,
-                    help="lattice size override for profiling runs (the reported workload is 512)")
+                    help="lattice size override for profiling runs (reported: 8192, or 512 for convection512)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -1003,6 +1203,10 @@ def main():
         return run_sweep(args)
     if args.workload == "configs":
         return run_configs(args)
+    if args.workload == "ablation":
+        return run_ablation(args)
+    if args.workload == "convection512":
+        return run_convection512(args)
     return run_ours(args)
 
 

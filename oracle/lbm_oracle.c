@@ -40,6 +40,8 @@
  *            a node of a grain turned by vartheta evaluates Eqs. 2-3 on its
  *            gradient turned into the crystal frame and turns N back
  *            (orc_aniso_frame).  Without an orientation field: Eq. 2 as printed.
+ *   R-force  the Guo forcing term of Eq. 14 carries the factor dt_F (see
+ *            collide_flow), so a flow update moves rho u by dt_F F_b.
  *   R-dirichlet  the cold bottom wall kept at T_b (Sec. 4.4): anti-bounce-back
  *            at the half-way wall below row 0, f_i = -f*_opp(i) + 2 w_i T_b
  *            for the links that enter row 0 from below; phi and U keep zero
@@ -403,7 +405,12 @@ void orc_collide_scalar(const double* f, const double* meq, double tau, double d
     orc_collide_scalar_q(9, f, meq, tau, dtQ, fpost);
 }
 
-/* Flow collision of Eq. 14 with S of Eq. 31 and Guo forcing (Eq. 30). */
+/* Flow collision of Eq. 14 with S of Eq. 31 and Guo forcing (Eq. 30).
+ * R-force: the forcing term enters as dt_F M^-1 (I - S/2) G_F, with the same
+ * factor dt_F that Eq. 14 gives the scalar sources and Eq. 27 the half-force
+ * shift, so that one flow update moves rho u by dt_F F_b (Guo's scheme); the
+ * printed G_F alone would move it by F_b per update whatever dt_F is.  At
+ * dt_F = 1 the two coincide. */
 static void collide_flow(const orc_params* p, const double* f, double c, double dt, double* fpost,
                          double* rho_o, double* ux_o, double* uy_o) {
     double rho = 0.0, jx = 0.0, jy = 0.0;
@@ -416,7 +423,7 @@ static void collide_flow(const orc_params* p, const double* f, double c, double 
     mat_vec(MM, f, m);
     orc_meq_flow(rho, ux, uy, c, meq);
     guo_moments(p->Fbx, p->Fby, ux, uy, c, G);
-    for (int k = 0; k < 9; ++k) mp[k] = m[k] - S[k] * (m[k] - meq[k]) + (1.0 - 0.5 * S[k]) * G[k];
+    for (int k = 0; k < 9; ++k) mp[k] = m[k] - S[k] * (m[k] - meq[k]) + dt * (1.0 - 0.5 * S[k]) * G[k];
     mat_vec(MI, mp, fpost);
     if (rho_o) { *rho_o = rho; *ux_o = ux; *uy_o = uy; }
 }

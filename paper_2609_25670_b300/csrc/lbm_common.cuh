@@ -190,12 +190,19 @@ __device__ __forceinline__ void aniso_frame(R gx, R gy, R eps, R vt, R& as, R& N
 // with S of Eq. 23 in closed form (columns 3 and 5 of M^-1 are e_x/6, e_y/6;
 // on D2Q5 e_x/2, e_y/2), A = chi + dt Q, b = j_eq = first moment of f_eq,
 // c = (1 - s) j_neq kneq<Q>.  On D2Q5 only populations 0..4 are written.
+// The rest population is A minus the moving ones' weight shares, so the nine
+// sum to A up to unbiased rounding: the weights rounded to FP32 sum to
+// 1 + 7.5e-9 (D2Q9) or 1 + 3.0e-8 (D2Q5), and w_0 A would scale the zeroth
+// moment by that every update -- a drift of the conserved solute sum.
+template <typename R, int Q> __device__ __forceinline__ R rest_share(R A, R a1, R a2) {
+    return Q == 9 ? A - R(4) * (a1 + a2) : A - R(4) * a1;
+}
 template <typename R, int HY, int HX, int Q = 9>
 __device__ __forceinline__ void put_scalar_post(R (*sp)[HY][HX], int ly, int lx, R A, R bx, R by, R cx, R cy) {
     const R w1 = wqq<R, Q>(1), w2 = Wt<R>::w2;
     const R a1 = w1 * A, a2 = w2 * A, b1x = R(3) * w1 * bx, b1y = R(3) * w1 * by;
     const R b2x = R(3) * w2 * bx, b2y = R(3) * w2 * by;
-    sp[0][ly][lx] = wqq<R, Q>(0) * A;
+    sp[0][ly][lx] = rest_share<R, Q>(A, a1, a2);
     sp[1][ly][lx] = a1 + b1x + cx;
     sp[2][ly][lx] = a1 + b1y + cy;
     sp[3][ly][lx] = a1 - b1x - cx;

@@ -516,17 +516,21 @@ template <typename R, int TY> struct FlowSmem {
 
 // MRT collision of Eq. 14 with S of Eq. 31 and Guo forcing (Eq. 30); f holds
 // populations 1..8 (decoded) on entry, rho the macro written with them; the
-// nine post-collision populations go to p
+// nine post-collision populations go to p.  The forcing term carries the
+// factor dt_F that Eq. 14 gives the scalar sources and Eq. 27 the half-force
+// shift: one update moves rho u by the impulse dt_F F_b (Guo's scheme; the
+// printed G_F alone would move it by F_b whatever dt_F is).
 template <typename R>
 __device__ __forceinline__ void flow_post9(const KP<R>& P, R* f, R rho, R* p) {
     const R c = P.cF, dt = P.dtF;
+    const R Ix = dt * P.Fbx, Iy = dt * P.Fby;                          // impulse per update
     R s8 = R(0);
 #pragma unroll
     for (int i = 1; i < 9; ++i) s8 += f[i];
     f[0] = rho - s8;
     const R jx = mom_x(f), jy = mom_y(f);
     const R irho = rcp(rho);
-    const R ux = (c * jx + R(0.5) * dt * P.Fbx) * irho, uy = (c * jy + R(0.5) * dt * P.Fby) * irho; // Eq. 27
+    const R ux = (c * jx + R(0.5) * Ix) * irho, uy = (c * jy + R(0.5) * Iy) * irho;     // Eq. 27
     const R ic = dt, ic2 = ic * ic, u2 = (ux * ux + uy * uy) * ic2;    // 1/c_F = dt_F
     // non-conserved moments of f (rows 1, 2, 4, 6, 7, 8 of M, Eq. 16)
     const R sa = f[1] + f[2] + f[3] + f[4], sd = f[5] + f[6] + f[7] + f[8];
@@ -538,9 +542,9 @@ __device__ __forceinline__ void flow_post9(const KP<R>& P, R* f, R rho, R* p) {
     const R m8 = f[5] - f[6] + f[7] - f[8];
     // Eq. 29 equilibria, Eq. 30 Guo moments, Eq. 31 rates; dm_k scaled by the
     // diagonal of M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
-    const R fu = (P.Fbx * ux + P.Fby * uy) * ic2;
-    const R G1 = R(6) * fu, G3 = P.Fbx * ic, G5 = P.Fby * ic;
-    const R G7 = R(2) * (P.Fbx * ux - P.Fby * uy) * ic2, G8 = (P.Fby * ux + P.Fbx * uy) * ic2;
+    const R fu = (Ix * ux + Iy * uy) * ic2;
+    const R G1 = R(6) * fu, G3 = Ix * ic, G5 = Iy * ic;
+    const R G7 = R(2) * (Ix * ux - Iy * uy) * ic2, G8 = (Iy * ux + Ix * uy) * ic2;
     const R d1 = (-P.se * (m1 - rho * (R(-2) + R(3) * u2)) + (R(1) - R(0.5) * P.se) * G1) * (R(1) / R(36));
     const R d2 = (-P.seps * (m2 - rho * (R(1) - R(3) * u2)) - (R(1) - R(0.5) * P.seps) * G1) * (R(1) / R(36));
     const R d3 = G3 * (R(1) / R(6));

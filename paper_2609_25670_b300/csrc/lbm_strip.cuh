@@ -55,13 +55,15 @@ __device__ __forceinline__ void strip_grad(int lane, R cm, R c0, R cp, R em, R e
 
 // post-collision populations of the scalar collision (Eq. 14 with S of
 // Eq. 23 in closed form): p_i = w_i A + 3 w_i (e_i . b) + (e_i . c), on the
-// Q-velocity lattice (on D2Q5, p_5..p_8 are compile-time zeros)
+// Q-velocity lattice (on D2Q5, p_5..p_8 are compile-time zeros); the rest
+// population takes the remainder of A (rest_share), so the zeroth moment
+// carries no bias from the rounded weights
 template <typename R, int Q = 9>
 __device__ __forceinline__ void scalar_post9(R A, R bx, R by, R cx, R cy, R* p) {
     const R w1 = wqq<R, Q>(1), w2 = Wt<R>::w2;
     const R a1 = w1 * A, a2 = w2 * A, b1x = R(3) * w1 * bx, b1y = R(3) * w1 * by;
     const R b2x = R(3) * w2 * bx, b2y = R(3) * w2 * by;
-    p[0] = wqq<R, Q>(0) * A;
+    p[0] = rest_share<R, Q>(A, a1, a2);
     p[1] = a1 + b1x + cx;
     p[2] = a1 + b1y + cy;
     p[3] = a1 - b1x - cx;

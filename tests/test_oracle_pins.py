@@ -248,6 +248,144 @@ def test_partial_bounce_back_mass_and_solid_reversal():
 
 
 # ---------------------------------------------------------------------------
+# Body force (Eqs. 13, 14, 27, 30): Newton's law, Guo's second moments,
+# body-force Poiseuille flow.  Reading R-force: the forcing term of Eq. 14
+# carries dt_F, so one flow update moves rho u by dt_F F_b.
+# ---------------------------------------------------------------------------
+E9 = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]])
+
+
+def _liquid_flow_params(nx, ny, NF, nu, Fbx, Fby, bc_y=W.BC_PERIODIC, **kw):
+    return W.Params(nx=nx, ny=ny, has_flow=True, bc_flow_x=W.BC_PERIODIC, bc_flow_y=bc_y,
+                    bc_scalar_x=W.BC_PERIODIC, bc_scalar_y=bc_y, N_F=NF, nu=nu, Fbx=Fbx, Fby=Fby,
+                    W0=1, tau0=1, **kw)
+
+
+@pytest.mark.parametrize("NF", [1, 2, 3])
+def test_uniform_body_force_newton_and_guo_moments(NF):
+    """A uniform liquid on a periodic lattice under a constant body force is
+    homogeneous, so streaming is the identity and only the collision acts.
+    (1) Newton: after K updates (time t = K dt_F) the Eq. 27 velocity is
+    u0 + F (t + dt_F/2), exactly, and rho stays 1 (G_0 = 0).
+    (2) Guo's forcing (Eq. 30 with (I - S/2), Eq. 14) makes every relaxed
+    moment m_k with equilibrium E_k(u) and forcing G_k(u, F) settle at
+    E_k(u) - (the part of G_k linear in F)/2 in lattice units, whatever its
+    rate s_k: the raw moments then describe the raw momentum exactly.  Derived
+    here for the D2Q9 basis polynomials: energy e = -2 + 3u^2 - 3u.F,
+    epsilon = 1 - 3u^2 + 3u.F, q_x = -u_x + F_x/2, p_xx - p_yy =
+    u_x^2 - u_y^2 - (F_x u_x - F_y u_y), p_xy = u_x u_y - (F_x u_y + F_y u_x)/2,
+    with u' = u dt_F and F' = F dt_F^2 (the per-update impulse over c_F).  A
+    wrong sign, factor or dt_F scaling in any G_k fails one of them."""
+    n, nu = 6, 0.04
+    dt = float(NF)
+    Fx, Fy = 3.0e-6, -2.0e-6
+    p = _liquid_flow_params(n, n, NF, nu, Fx, Fy)
+    f = W.base_fields(p, -np.ones((n, n)))
+    u0x, u0y = 4.0e-3, -1.5e-3
+    f["ux"] = np.full((n, n), u0x)
+    f["uy"] = np.full((n, n), u0y)
+    o = oracle.Oracle(p, f)
+    K = 80                                     # updates; transients decay as |1 - s_k|^K
+    o.advance(K * NF)
+    t = K * dt
+    assert np.abs(o.get("ux") - (u0x + Fx * (t + 0.5 * dt))).max() < 1e-13
+    assert np.abs(o.get("uy") - (u0y + Fy * (t + 0.5 * dt))).max() < 1e-13
+    assert np.abs(o.get("rho") - 1.0).max() < 1e-14
+    fp = o.pops("F")[:, 0, 0]
+    o.close()
+    ux = (u0x + Fx * (t + 0.5 * dt)) * dt      # lattice units
+    uy = (u0y + Fy * (t + 0.5 * dt)) * dt
+    fx, fy = Fx * dt * dt, Fy * dt * dt
+    ex, ey = E9[:, 0], E9[:, 1]
+    e2 = ex * ex + ey * ey
+    u2, uF = ux * ux + uy * uy, ux * fx + uy * fy
+    got = {
+        "e": np.dot(-4 + 3 * e2, fp),
+        "eps": np.dot(4 - 10.5 * e2 + 4.5 * e2 * e2, fp),
+        "qx": np.dot((-5 + 3 * e2) * ex, fp),
+        "qy": np.dot((-5 + 3 * e2) * ey, fp),
+        "pxx": np.dot(ex * ex - ey * ey, fp),
+        "pxy": np.dot(ex * ey, fp),
+    }
+    want = {
+        "e": -2 + 3 * u2 - 3 * uF,
+        "eps": 1 - 3 * u2 + 3 * uF,
+        "qx": -ux + fx / 2,
+        "qy": -uy + fy / 2,
+        "pxx": ux * ux - uy * uy - (fx * ux - fy * uy),
+        "pxy": ux * uy - (fx * uy + fy * ux) / 2,
+    }
+    for k in got:
+        assert abs(got[k] - want[k]) < 1e-13, (k, got[k], want[k])   # |u.F| terms ~1e-7
+
+
+@pytest.mark.parametrize("NF", [1, 2])
+def test_body_force_poiseuille(NF):
+    """Body-force Poiseuille flow between half-way bounce-back walls (periodic
+    in x, liquid phi = -1 so Eq. 33 is plain streaming).  Steady Eq. 13:
+    nu u'' + F = 0, so (a) in the bulk the discrete second difference of u is
+    -F/nu (the LBM reproduces the parabola exactly there) in base time units
+    at every update factor -- the force acts per unit time, not per update;
+    (b) u is symmetric about the channel centre, u_y = 0; (c) with the energy
+    flux rate s_q set so that (1/s_nu - 1/2)(1/s_q - 1/2) = 3/16 the bounce-back
+    wall sits exactly half a link outside the last node, and u equals the
+    parabola F/(2 nu) (y + 1/2)(ny - 1/2 - y); (d) with the paper's s_q = 1.2
+    the parabola holds up to a uniform wall slip below 1 % of u_max."""
+    nx, ny, nu, F = 4, 12, 1.0 / 6.0, 1.0e-6
+    dt = float(NF)
+    tauF = 3 * dt * nu + 0.5
+    y = np.arange(ny)
+    ana = F / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    for sq, tol in ((1.0 / (0.5 + (3.0 / 16.0) / (tauF - 0.5)), 1e-8), (1.2, 1e-2)):
+        p = _liquid_flow_params(nx, ny, NF, nu, F, 0.0, bc_y=W.BC_WALL, s_q=sq)
+        o = oracle.Oracle(p, W.base_fields(p, -np.ones((ny, nx))))
+        o.advance(5000)
+        u = o.get("ux")
+        uy = o.get("uy")
+        o.close()
+        assert np.abs(u - u[:, :1]).max() < 1e-18             # uniform along x
+        u = u[:, 0]
+        d2 = u[2:] - 2 * u[1:-1] + u[:-2]
+        assert np.abs(d2 / (-F / nu) - 1).max() < 1e-8, (sq, d2)
+        assert np.abs(u - u[::-1]).max() < 1e-9 * ana.max()
+        assert np.abs(uy).max() < 1e-15
+        assert np.abs(u - ana).max() < tol * ana.max(), (sq, np.abs(u - ana).max() / ana.max())
+
+
+def test_inlet_outflow_columns_with_nonuniform_density():
+    """Reading Q9 on a state whose density varies along x, so that the inlet
+    column's new density is not its old one: after every flow update the
+    inlet column x = 0 carries exactly the inlet velocity (u_x = u_in, u_y = 0)
+    at the density of its downstream neighbour x = 1 (zero-gradient density,
+    the populations being f_eq(rho(x=1), u_in)); the outflow column copies
+    x = L-2 (equal rho, u).  Taking the density from any other column, or
+    before streaming, breaks rho(0) == rho(1)."""
+    nx, ny = 24, 10
+    p = W.Params(nx=nx, ny=ny, has_flow=True, bc_flow_x=W.BC_INLET_OUTFLOW, bc_flow_y=W.BC_PERIODIC,
+                 bc_scalar_x=W.BC_WALL, bc_scalar_y=W.BC_PERIODIC, N_F=1, nu=0.05, u_in=0.01,
+                 W0=1, tau0=1)
+    x, yy = np.meshgrid(np.arange(nx) + 0.0, np.arange(ny) + 0.0)
+    f = W.base_fields(p, -np.ones((ny, nx)))
+    f["rho"] = 1.0 + 0.02 * np.sin(2 * np.pi * x / nx) + 0.005 * np.cos(2 * np.pi * yy / ny)
+    f["ux"] = 0.01 + 0.003 * np.cos(2 * np.pi * yy / ny)
+    f["uy"] = 0.002 * np.sin(2 * np.pi * x / nx)
+    o = oracle.Oracle(p, f)
+    prev0 = f["rho"][:, 0]
+    for _ in range(6):
+        o.advance(1)
+        rho, ux, uy = o.get("rho"), o.get("ux"), o.get("uy")
+        assert np.abs(rho[:, 0] - rho[:, 1]).max() < 1e-15
+        assert np.abs(rho[:, 0] - prev0).max() > 1e-5          # the inlet density did move
+        assert np.abs(ux[:, 0] - 0.01).max() < 1e-16
+        assert np.abs(uy[:, 0]).max() < 1e-17
+        for a in (rho, ux, uy):
+            assert np.array_equal(a[:, -1], a[:, -2])
+        assert np.ptp(rho[:, 1]) > 1e-4                        # still non-uniform
+        prev0 = rho[:, 0].copy()
+    o.close()
+
+
+# ---------------------------------------------------------------------------
 # Phase field: closed forms
 # ---------------------------------------------------------------------------
 def _front_position(row):

@@ -402,6 +402,25 @@ def multi_dendrite(n: int = 8192, n_seeds: int = 32, min_dist: float = 800.0, se
                     n_base_steps, extra={"seeds": pts, "angles": angles})
 
 
+def multi_dendrite_fields(p: Params, pts, R: float = 8.0, U0: float = 0.0, T0: float = -0.55) -> Dict[str, np.ndarray]:
+    """Initial fields of the whole multi-dendrite lattice (circles of radius R
+    at the centres `pts`, Sec. 4.1 profile), built seed by seed on windows:
+    beyond r = R + 20 sqrt(2) W0 + 2 the profile tanh[(R - r)/(sqrt 2 W0)]
+    rounds to -1 exactly, so the result equals the full-lattice evaluation of
+    multi_dendrite() without its cost on large lattices."""
+    nx, ny = p.nx, p.ny
+    sw = math.sqrt(2.0) * p.W0
+    phi = np.full((ny, nx), -1.0)
+    reach = abs(R) + 20.0 * sw + 2.0
+    for (cx, cy) in np.asarray(pts, dtype=np.float64).reshape(-1, 2):
+        xa, xb = int(max(0, math.floor(cx - reach))), int(min(nx, math.ceil(cx + reach) + 1))
+        ya, yb = int(max(0, math.floor(cy - reach))), int(min(ny, math.ceil(cy + reach) + 1))
+        y, x = np.mgrid[ya:yb, xa:xb]
+        r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2)
+        np.maximum(phi[ya:yb, xa:xb], np.tanh((R - r) / sw), out=phi[ya:yb, xa:xb])
+    return base_fields(p, phi, U0=U0, T0=T0)
+
+
 def multi_dendrite_angles(n_seeds: int, seed: int = 5) -> np.ndarray:
     """Crystal angles of the multi-dendrite grains, uniform in [0, pi/2)
     (the draws multi_dendrite returns in extra['angles'])."""
