@@ -197,6 +197,28 @@ __device__ __forceinline__ void aniso_frame(R gx, R gy, R eps, R vt, R& as, R& N
 template <typename R, int Q> __device__ __forceinline__ R rest_share(R A, R a1, R a2) {
     return Q == 9 ? A - R(4) * (a1 + a2) : A - R(4) * a1;
 }
+// Zeroth moment of a node's streamed populations fn[0..Q-1] (Eq. 18) when its
+// own collision took the zeroth moment chi: chi + sum_i (fn_i - r_i), with r_i
+// the populations of chi at rest (w_i chi; the rest population as the
+// remainder, as rest_share builds it).  Equal to sum_i fn_i in exact
+// arithmetic, since sum_i r_i = chi.  In FP32 the roundings of w_i A in the
+// neighbours' post-collision values and of w_i chi here cancel wherever the
+// field is smooth, and a node of a uniform region keeps its value exactly,
+// so the stored macro does not drift the way a plain Q-term sum of values of
+// order chi does (the roundings of neighbouring nodes are then correlated).
+template <typename R, int Q> __device__ __forceinline__ R streamed_zeroth(R chi, const R* fn) {
+    const R r1 = wqq<R, Q>(1) * chi, r2 = Wt<R>::w2 * chi;
+    R d = (fn[0] - rest_share<R, Q>(chi, r1, r2)) + ((fn[1] - r1) + (fn[3] - r1)) + ((fn[2] - r1) + (fn[4] - r1));
+    if constexpr (Q == 9) d += ((fn[5] - r2) + (fn[7] - r2)) + ((fn[6] - r2) + (fn[8] - r2));
+    return chi + d;
+}
+// a / b correctly rounded: the phase-change increment of Eq. 38, whose
+// product with the denominator must return the numerator for the exact
+// solute balance of the transfer (a reciprocal approximation leaves a
+// relative error of up to 2^-22 in every injection)
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return a / b; }
+
 template <typename R, int HY, int HX, int Q = 9>
 __device__ __forceinline__ void put_scalar_post(R (*sp)[HY][HX], int ly, int lx, R A, R bx, R by, R cx, R cy) {
     const R w1 = wqq<R, Q>(1), w2 = Wt<R>::w2;

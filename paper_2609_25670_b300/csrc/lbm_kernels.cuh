@@ -344,7 +344,7 @@ __device__ __forceinline__ void transfer_tile(TransferSmem<R, TY>& sm, const KP<
         const R pn = sm.pn[ty + 2][tx + 2];
         const R dphi = pn - poa;                      // item A of an own node is the node itself
         if (P.has_U) {
-            const R dU = ((R(1) + omk * Usa) * dphi - R(2) * div) * rcp((R(1) + P.k) - omk * pn);   // Eq. 38
+            const R dU = div_rn((R(1) + omk * Usa) * dphi - R(2) * div, (R(1) + P.k) - omk * pn);   // Eq. 38
             mydu = fabs(dU);
             if (!P.accumulated) Uout[node] = Usa + dU;                                // Eq. 39
             else {
@@ -471,16 +471,15 @@ __device__ __forceinline__ void scalar_tile(ScalarSmem<R, TY, Q>& sm, const KP<R
     if (IN || (gx < P.nx && gy < P.ny)) {
         const int node = gy * P.pitch + gx;
         const Walls w = walls_of<IN>(gx, gy, P.nx, P.ny, P.bsx, P.bsy);
-        R fn[9], sum = R(0);
+        R fn[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             if (i >= Q) { fn[i] = R(0); continue; }                                   // D2Q5: no diagonals
             fn[i] = w.hit(i) ? sm.post[opp_of(i)][ty + 1][tx + 1] : sm.post[i][ty + 1 - ey_of(i)][tx + 1 - ex_of(i)]; // Eq. 25
             if (FIELD == 1 && !IN && ey_of(i) > 0 && w.ym && P.T_dir_ym)              // bottom wall at T_ymin
                 fn[i] = R(2) * wqq<R, Q>(i) * P.T_ymin - sm.post[opp_of(i)][ty + 1][tx + 1];
-            sum += fn[i];
         }
-        mac_out[node] = sum;                                                      // Eq. 18
+        mac_out[node] = streamed_zeroth<R, Q>(ca, fn);                            // Eq. 18
         store_j<R, ST>(fout, node, pl, fn);
         if (FIELD == 0 && P.accumulated) myj = fabs(acca);
     }

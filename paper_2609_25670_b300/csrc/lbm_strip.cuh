@@ -214,6 +214,7 @@ __device__ __forceinline__ void scalar_strip(const KP<R>& P, const ST* __restric
     // carried post-collision values: row r-1 (q0, q1s, q3s; q2, q5s, q6s) and
     // row r-2 (z2, z5s, z6s); own unshifted row r-1 for walls (o[])
     R q0 = R(0), q1 = R(0), q3 = R(0), q2 = R(0), q5 = R(0), q6 = R(0), z2 = R(0), z5 = R(0), z6 = R(0);
+    R cq = R(0);                                   // zeroth moment that entered row r-1's collision
     R o[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) o[i] = R(0);
@@ -264,15 +265,13 @@ __device__ __forceinline__ void scalar_strip(const KP<R>& P, const ST* __restric
                     }
                 }
             }
-            R sum = R(0);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) sum += fn[i];
             const int node = y * P.pitch + gx;
-            mac_out[node] = sum;                                                  // Eq. 18
+            mac_out[node] = streamed_zeroth<R, Q>(cq, fn);                        // Eq. 18
             store_j<R, ST>(fout, node, pl, fn);
         }
         z2 = q2; z5 = q5; z6 = q6;
         q0 = p[0]; q1 = s1; q3 = s3; q2 = p[2]; q5 = s5; q6 = s6;
+        cq = chi;
         if (!IN) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) o[i] = p[i];
@@ -434,8 +433,9 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
     // (za*).  Walking down the latter are e_y = +1 (2, 5, 6); walking up,
     // e_y = -1 (4, 7, 8).
     R q0[VW], q1[VW], q3[VW], qa[VW], qb[VW], qc[VW], za[VW], zb[VW], zc[VW];
+    R cqv[VW];                                  // zeroth moments that entered row r - DIR's collision
 #pragma unroll
-    for (int k = 0; k < VW; ++k) q0[k] = q1[k] = q3[k] = qa[k] = qb[k] = qc[k] = za[k] = zb[k] = zc[k] = R(0);
+    for (int k = 0; k < VW; ++k) q0[k] = q1[k] = q3[k] = qa[k] = qb[k] = qc[k] = za[k] = zb[k] = zc[k] = cqv[k] = R(0);
     R myj = R(0);
 #pragma unroll 1
     for (int it = 0; it < NR; ++it) {
@@ -505,10 +505,10 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
                     fn[4][k] = za[k]; fn[7][k] = zb[k]; fn[8][k] = zc[k];
                     fn[2][k] = p[k][2]; fn[5][k] = s5[k]; fn[6][k] = s6[k];
                 }
-                R t = R(0);
+                R f9[9];
 #pragma unroll
-                for (int i = 0; i < 9; ++i) t += fn[i][k];
-                sum.v[k] = t;
+                for (int i = 0; i < 9; ++i) f9[i] = fn[i][k];
+                sum.v[k] = streamed_zeroth<R, Q>(cqv[k], f9);
             }
             *reinterpret_cast<Vec4<R>*>(mac_out + node) = sum;                    // Eq. 18
             Vec4<ST> ox, oy;
@@ -526,6 +526,7 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
             q0[k] = p[k][0]; q1[k] = s1[k]; q3[k] = s3[k];
             if (!UP) { qa[k] = p[k][2]; qb[k] = s5[k]; qc[k] = s6[k]; }
             else { qa[k] = p[k][4]; qb[k] = s7[k]; qc[k] = s8[k]; }
+            cqv[k] = chi.v[k];
         }
         pb = p0;
         p0 = pf;
@@ -901,7 +902,7 @@ __device__ __forceinline__ void transfer_vstrip(const KP<R>& P, const R* __restr
                     const R div = Sx[k + 2] - Sx[k] + Dy[k + 1] * (R(1) / R(3)) + (Dy[k] + Dy[k + 2]) * (R(1) / R(12));
                     const R dphi = pny[k] - poy[k];
                     if (ldU) {
-                        const R dU = ((R(1) + omk * Uy[k]) * dphi - R(2) * div) * rcp((R(1) + P.k) - omk * pny[k]);  // Eq. 38
+                        const R dU = div_rn((R(1) + omk * Uy[k]) * dphi - R(2) * div, (R(1) + P.k) - omk * pny[k]);  // Eq. 38
                         mydu = fmax(mydu, fabs(dU));
                         if constexpr (ACC) {
                             oU.v[k] = aUy[k];

@@ -234,7 +234,7 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
             const R dph = sm.dphi[hy][hx];
             if (P.has_U) {
                 const R Us = sm.Us[hy][hx];
-                const R dU = ((R(1) + omk * Us) * dph - R(2) * div) * rcp((R(1) + P.k) - omk * pn);   // Eq. 38
+                const R dU = div_rn((R(1) + omk * Us) * dph - R(2) * div, (R(1) + P.k) - omk * pn);   // Eq. 38
                 Ui = Us + dU;                                                                      // Eq. 39
                 adu = fabs(dU);
             }
@@ -278,26 +278,25 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
     const Walls ws = walls_of<IN>(gx, gy, P.nx, P.ny, P.bsx, P.bsy);
 
     // ---- scalar updates (Eqs. 7-8, 10-12 tr parts; 14, 19-20, 23-25, 40)
-    auto scalar_stream = [&](ST* __restrict__ fout, R* __restrict__ mac_out, bool dir_ym) {
+    auto scalar_stream = [&](ST* __restrict__ fout, R* __restrict__ mac_out, bool dir_ym, R chi) {
         if (!own) return;
         const int node = gy * P.pitch + gx;
-        R fn[9], sum = R(0);
+        R fn[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             if (i >= Q) { fn[i] = R(0); continue; }                                 // D2Q5: no diagonals
             fn[i] = ws.hit(i) ? sm.post[opp_of(i)][ty + 1][tx + 1] : sm.post[i][ty + 1 - ey_of(i)][tx + 1 - ex_of(i)];
             if (!IN && dir_ym && ey_of(i) > 0 && ws.ym)                            // bottom wall at T_ymin
                 fn[i] = R(2) * wqq<R, Q>(i) * P.T_ymin - sm.post[opp_of(i)][ty + 1][tx + 1];
-            sum += fn[i];
         }
-        mac_out[node] = sum;
+        mac_out[node] = streamed_zeroth<R, Q>(chi, fn);                          // Eq. 18
         store_j<R, ST>(fout, node, pl, fn);
     };
     if (A.do_U) {
         if (va) scalar_collide<R, TY, 0, 38, 2, Q>(P, sm.phi, sm.post, tx + 1, ty + 1, Uia, jax, jay, uxa, uya);
         if (vb) scalar_collide<R, TY, 0, 38, 2, Q>(P, sm.phi, sm.post, blx, bly, Uib, jbx, jby, uxb, uyb);
         __syncthreads();
-        scalar_stream(A.fUout, A.Uout, false);
+        scalar_stream(A.fUout, A.Uout, false, Uia);
         __syncthreads();
     }
     if (A.do_T) {
@@ -313,7 +312,7 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
         if (va) scalar_collide<R, TY, 1, 38, 2, Q>(P, sm.phi, sm.post, tx + 1, ty + 1, Tia, jax, jay, uxa, uya);
         if (vb) scalar_collide<R, TY, 1, 38, 2, Q>(P, sm.phi, sm.post, blx, bly, Tib, jbx, jby, uxb, uyb);
         __syncthreads();
-        scalar_stream(A.fTout, A.Tout, P.T_dir_ym != 0);
+        scalar_stream(A.fTout, A.Tout, P.T_dir_ym != 0, Tia);
         __syncthreads();
     }
 
