@@ -142,13 +142,17 @@ typedef struct {
  *             previous call (equals S_phi under instantaneous coupling)
  *   tip[d]  = distance from (tip_cx, tip_cy) of the outermost phi = 0 crossing
  *             along +x, +y, -x, -y (linear interpolation)
- *   nonfinite = 1 if any phi, U, T, ux, uy is NaN or Inf */
+ *   nonfinite = 1 if any phi, U, T, ux, uy is NaN or Inf
+ *   R_M     = relative solute drift (M_C - M_C(0)) / M_C(0) since the last
+ *             lbm_init_seed / lbm_init_fields (Sec. 4.4); 0 from
+ *             lbm_diagnostics_noalloc, which keeps no history */
 typedef struct {
     int64_t base_step;
     double M_C, H_total, S_phi, J_U;
     double tip[4];
     int32_t nonfinite;
     int32_t reserved;
+    double R_M;       /* (M_C - M_C(0)) / M_C(0), M_C(0) of the last initialisation (Sec. 4.4) */
 } lbm_diag;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc
@@ -329,10 +333,16 @@ lbm_status lbm_device_bytes(lbm_handle h, size_t* bytes);
  * Scratch: a fixed file-scope device array of about 28 KB (partial sums of at
  * most 1184 blocks plus result slots), held by every GPU that loads the
  * library until the process exits.  Lattices of more than 2^31 - 1 nodes are
- * rejected with LBM_E_INVALID_ARG.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Calls share the array and
- * it keeps the last call's contents: calls that overlap on the GPU race.
+ * rejected with LBM_E_INVALID_ARG.  Every call looks up the array's device
+ * address (cudaGetSymbolAddress) with the current device.  The call
+ * synchronises its stream and copies the results to the host, so it may
+ * never run while a capture into a CUDA graph is active: on a capturing
+ * stream it returns LBM_E_INVALID_ARG; in the global capture mode it would
+ * also invalidate captures on other streams, so do not call it then.  Calls
+ * share the array and it keeps the last call's contents: calls that overlap
+ * on the GPU race.  With FP32 arithmetic lbm_diagnostics adds the residual of
+ * the compensated U macro to the solute sum, which the caller's FP32 U field
+ * does not hold: the two M_C agree to the rounding of U to FP32.
  * Errors: INVALID_ARG, UNSTABLE_PARAMS (as lbm_create), CUDA, NONFINITE
  * (out is filled).  Errors are reported by lbm_last_error(NULL). */
 lbm_status lbm_diagnostics_noalloc(const lbm_params* p, const void* phi, const void* U, const void* T,

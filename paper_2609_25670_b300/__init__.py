@@ -68,7 +68,7 @@ class lbm_seed(C.Structure):
 class lbm_diag(C.Structure):
     _fields_ = [("base_step", C.c_int64), ("M_C", C.c_double), ("H_total", C.c_double),
                 ("S_phi", C.c_double), ("J_U", C.c_double), ("tip", C.c_double * 4),
-                ("nonfinite", C.c_int32), ("reserved", C.c_int32)]
+                ("nonfinite", C.c_int32), ("reserved", C.c_int32), ("R_M", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -315,8 +315,8 @@ class Simulation:
         st = self.lib.lbm_diagnostics(self.h, sim, C.byref(d))
         if st != 0 and (st != 5 or raise_nonfinite):
             self._ck(st)
-        return {"base_step": d.base_step, "M_C": d.M_C, "H": d.H_total, "S_phi": d.S_phi, "J_U": d.J_U,
-                "tip": np.array(list(d.tip)), "nonfinite": d.nonfinite, "status": st}
+        return {"base_step": d.base_step, "M_C": d.M_C, "R_M": d.R_M, "H": d.H_total, "S_phi": d.S_phi,
+                "J_U": d.J_U, "tip": np.array(list(d.tip)), "nonfinite": d.nonfinite, "status": st}
 
     # ---- measurement hooks
     def timing_enable(self, kinds: Iterable[str]):

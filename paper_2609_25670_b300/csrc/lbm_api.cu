@@ -9,7 +9,6 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
-#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -54,7 +53,8 @@ struct SimState {
     lbm_params p{};
     int nx = 0, ny = 0, pitch = 0;
     size_t nn = 0;        // pitch * ny
-    void* pops[4][2] = {};   // phase, flow: 8 population planes; U, T: 2 first-moment planes
+    void* pops[4][2] = {};   // phase, flow: 8 population planes; U, T: 2 first-moment planes (U with FP32
+                             // arithmetic: a third, the residual of its compensated macro)
     int cur_pop[4] = {0, 0, 0, 0};
     void* phi[2] = {};
     int cur_phi = 0;
@@ -174,6 +174,10 @@ lbm_status fail(lbm_sim* h, lbm_status s, const char* fmt, ...) {
         cudaError_t e_ = (call);                                                          \
         if (e_ != cudaSuccess) return fail(h, LBM_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
+
+// planes of the stored U state: (j_x, j_y), plus the residual of the
+// compensated macro with FP32 arithmetic (Compensated in lbm_common.cuh)
+int u_planes(uint32_t precision) { return precision == LBM_PREC_F64 ? 2 : 3; }
 
 lbm_status dev_alloc(lbm_sim* h, size_t bytes, void** out) {
     *out = nullptr;
@@ -1034,6 +1038,8 @@ lbm_status graph_replay(lbm_sim* h, SimState& s, int which) {
     return LBM_OK;
 }
 
+template <typename R> void enqueue_diag(lbm_sim* h, SimState& s);
+
 template <typename R>
 lbm_status upload_and_init(lbm_sim* h, SimState& s, const double* src[6], int src_dev) {
     const size_t n = (size_t)s.nx * s.ny;
@@ -1100,6 +1106,12 @@ lbm_status upload_and_init(lbm_sim* h, SimState& s, const double* src[6], int sr
     if (s.accT) CK(cudaMemsetAsync(s.accT, 0, 2 * s.nn * rs, h->stream));
     CK(cudaMemsetAsync(s.smax, 0, 2 * sizeof(unsigned long long), h->stream));
     if (s.clock) CK(cudaMemsetAsync(s.clock, 0, sizeof(long long), h->stream));
+    {   // solute inventory of the initial state: the reference M_C(0) of R_M (Sec. 4.4)
+        LaunchScope ls(h, LBM_K_INIT);
+        enqueue_diag<R>(h, s);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(s.dout + 9, s.dout, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     s.acc_reset_U = s.acc_reset_T = true;
     s.step = 0;
     s.initialized = true;
@@ -1145,18 +1157,21 @@ lbm_status read_field(lbm_sim* h, SimState& s, uint32_t which, void* dst, int ds
     // clock holds the base step of the last graph replay start; keep it exact here
     if (s.clock) k_set_clock<<<1, 1, 0, h->stream>>>(s.clock, (long long)s.step);
     const int fc = s.cur_pop[FF];
+    // U carries the residual of its compensated macro (FP32 arithmetic)
+    const int lo_kind = !s.has_U || h->precision == LBM_PREC_F64 ? 0 : h->precision == LBM_PREC_F32 ? 1 : 2;
+    const void* ulo = lo_kind ? (const char*)s.pops[FU][s.cur_pop[FU]] + 2 * s.nn * (lo_kind == 1 ? 4 : 2) : nullptr;
     if (as_f64)
         k_out<R, double><<<grd, blk, 0, h->stream>>>(P, (int)which, (const R*)s.phi[s.cur_phi],
                                                      s.has_U ? (const R*)s.U[s.cur_U] : nullptr,
                                                      s.has_T ? (const R*)s.T[s.cur_T] : nullptr, (const R*)s.ux[fc],
-                                                     (const R*)s.uy[fc], (const R*)s.rho[fc], (const R*)s.accU,
-                                                     (const R*)s.accT, (double*)out, s.clock);
+                                                     (const R*)s.uy[fc], (const R*)s.rho[fc], ulo, lo_kind,
+                                                     (double*)out, s.clock);
     else
         k_out<R, R><<<grd, blk, 0, h->stream>>>(P, (int)which, (const R*)s.phi[s.cur_phi],
                                                 s.has_U ? (const R*)s.U[s.cur_U] : nullptr,
                                                 s.has_T ? (const R*)s.T[s.cur_T] : nullptr, (const R*)s.ux[fc],
-                                                (const R*)s.uy[fc], (const R*)s.rho[fc], (const R*)s.accU,
-                                                (const R*)s.accT, (R*)out, s.clock);
+                                                (const R*)s.uy[fc], (const R*)s.rho[fc], ulo, lo_kind, (R*)out,
+                                                s.clock);
     CK(cudaGetLastError());
     if (!dst_dev) {
         CK(cudaMemcpyAsync(dst, out, n * esz, cudaMemcpyDeviceToHost, h->stream));
@@ -1165,24 +1180,49 @@ lbm_status read_field(lbm_sim* h, SimState& s, uint32_t which, void* dst, int ds
     return LBM_OK;
 }
 
+// The diagnostics reductions of simulation s into s.dout[0..8] (asynchronous).
 template <typename R>
-lbm_status run_diag(lbm_sim* h, SimState& s, lbm_diag* out) {
+void enqueue_diag(lbm_sim* h, SimState& s) {
     const KP<R> P = make_kp<R>(s);
     {
-        LaunchScope ls(h, LBM_K_DIAG);
         const int fc = s.cur_pop[FF];
-        k_diag_partial<R><<<s.diag_blocks, 256, 0, h->stream>>>(
-            P, (const R*)s.phi[s.cur_phi], s.has_U ? (const R*)s.U[s.cur_U] : nullptr,
-            s.has_T ? (const R*)s.T[s.cur_T] : nullptr, (const R*)s.ux[fc], (const R*)s.uy[fc], s.part);
+        const R* Um = s.has_U ? (const R*)s.U[s.cur_U] : nullptr;
+        const R* Tm = s.has_T ? (const R*)s.T[s.cur_T] : nullptr;
+        // the solute sum includes the residual plane of the compensated U macro
+        if constexpr (sizeof(R) == 4) {
+            if (s.has_U && h->precision == LBM_PREC_F32)
+                k_diag_partial<R, float><<<s.diag_blocks, 256, 0, h->stream>>>(
+                    P, (const R*)s.phi[s.cur_phi], Um, Tm, (const R*)s.ux[fc], (const R*)s.uy[fc], s.part,
+                    (const float*)s.pops[FU][s.cur_pop[FU]] + 2 * s.nn);
+            else if (s.has_U)
+                k_diag_partial<R, __nv_bfloat16><<<s.diag_blocks, 256, 0, h->stream>>>(
+                    P, (const R*)s.phi[s.cur_phi], Um, Tm, (const R*)s.ux[fc], (const R*)s.uy[fc], s.part,
+                    (const __nv_bfloat16*)s.pops[FU][s.cur_pop[FU]] + 2 * s.nn);
+            else
+                k_diag_partial<R><<<s.diag_blocks, 256, 0, h->stream>>>(
+                    P, (const R*)s.phi[s.cur_phi], Um, Tm, (const R*)s.ux[fc], (const R*)s.uy[fc], s.part);
+        } else {
+            k_diag_partial<R><<<s.diag_blocks, 256, 0, h->stream>>>(
+                P, (const R*)s.phi[s.cur_phi], Um, Tm, (const R*)s.ux[fc], (const R*)s.uy[fc], s.part);
+        }
         k_diag_final<R><<<1, 128, 0, h->stream>>>(P, s.part, s.diag_blocks, (const R*)s.phi[s.cur_phi], s.p.tip_cx,
                                                  s.p.tip_cy, s.smax, s.dout);
     }
+}
+
+template <typename R>
+lbm_status run_diag(lbm_sim* h, SimState& s, lbm_diag* out) {
+    {
+        LaunchScope ls(h, LBM_K_DIAG);
+        enqueue_diag<R>(h, s);
+    }
     CK(cudaGetLastError());
-    double r[9];
+    double r[10];       // [9]: the solute inventory of the last initialisation
     CK(cudaMemcpyAsync(r, s.dout, sizeof r, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     out->base_step = s.step;
     out->M_C = r[0];
+    out->R_M = r[9] != 0.0 ? (r[0] - r[9]) / r[9] : 0.0;
     out->H_total = r[1];
     out->nonfinite = r[2] > 0.0 ? 1 : 0;
     for (int d = 0; d < 4; ++d) out->tip[d] = r[3 + d];
@@ -1256,7 +1296,8 @@ lbm_status lbm_create(const lbm_params* p, int32_t n_sims, const lbm_params* per
         for (int f = 0; f < 4 && !st; ++f)
             for (int b = 0; b < 2 && !st; ++b)
                 if (present[f])
-                    st = dev_alloc(h, (f == FU || f == FT ? 2 : f == FP ? h->q - 1 : 8) * s.nn * ss, &s.pops[f][b]);
+                    st = dev_alloc(h, (f == FU ? u_planes(h->precision) : f == FT ? 2 : f == FP ? h->q - 1 : 8) * s.nn * ss,
+                                   &s.pops[f][b]);
         for (int b = 0; b < 2 && !st; ++b) st = dev_alloc(h, s.nn * rs, &s.phi[b]);
         for (int b = 0; b < 2 && !st; ++b) if (s.has_U) st = dev_alloc(h, s.nn * rs, &s.U[b]);
         for (int b = 0; b < 2 && !st; ++b) if (s.has_T) st = dev_alloc(h, s.nn * rs, &s.T[b]);
@@ -1791,26 +1832,16 @@ constexpr int kNoAllocBlocks = 1184;                 // 8 blocks per SM on 148 S
 constexpr int kNoAllocSlots = 3 * kNoAllocBlocks + 16;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocSlots];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kMaxDevices] = {};
-
-// Device address of the scratch array for the current device.  In host code
+// Device address of the scratch array on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address is looked up
-// once per device, with that device current, and then reused.
+// with the device current -- on every call: a lookup costs far less than the
+// reduction, and no address survives a device reset (which unloads the
+// module and places the array anew when it is loaded again).
 cudaError_t noalloc_scratch(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_addr[dev] = p;
-    }
-    *out = (double*)g_noalloc_addr[dev];
+    *out = (double*)p;
     return cudaSuccess;
 }
 
@@ -1839,6 +1870,7 @@ lbm_status noalloc_diag(const SimState& s, const void* phi, const void* U, const
     out->S_phi = 0.0;
     out->J_U = 0.0;
     out->reserved = 0;
+    out->R_M = 0.0;
     return out->nonfinite ? fail(nullptr, LBM_E_NONFINITE, "non-finite value in the fields") : LBM_OK;
 }
 
@@ -1866,9 +1898,15 @@ extern "C" lbm_status lbm_diagnostics_noalloc(const lbm_params* p, const void* p
     s.has_flow = (p->fields & LBM_FIELD_FLOW) != 0;
     if ((s.has_U && !U) || (s.has_T && !T) || (s.has_flow && (!ux || !uy)))
         return fail(nullptr, LBM_E_INVALID_ARG, "a field that is switched on was passed as NULL");
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    // the call synchronises its stream and copies to the host: never inside a capture
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(nullptr, LBM_E_INVALID_ARG, "the stream is being captured into a CUDA graph; this call "
+                                                "synchronises its stream and may not run during a capture");
     double* scratch = nullptr;
     CK(noalloc_scratch(&scratch));
-    cudaStream_t stream = (cudaStream_t)cuda_stream;
     return p->precision == LBM_PREC_F64 ? noalloc_diag<double>(s, phi, U, T, ux, uy, stream, scratch, out)
                                         : noalloc_diag<float>(s, phi, U, T, ux, uy, stream, scratch, out);
 }

@@ -45,6 +45,10 @@ __global__ void k_init(const KP<R> P, int q, const R* __restrict__ phi, const R*
         const R U = Um[node];
         fU[node] = Cvt<ST>::st(P.dtU * U * vx);
         fU[(size_t)P.plane + node] = Cvt<ST>::st(P.dtU * U * vy);
+        if constexpr (Compensated<R>::value) {          // residual of the compensated macro
+            using Lo = typename LoOf<ST>::T;
+            reinterpret_cast<Lo*>(fU + 2 * (size_t)P.plane)[node] = Cvt<Lo>::st(R(0));
+        }
     }
     if (P.has_T) {
         const R T = Tm[node];
@@ -68,32 +72,39 @@ __global__ void k_from_f64(const double* __restrict__ src, R* __restrict__ dst, 
 }
 
 // derived output fields into a dense ny x nx buffer of type O
-// which: 0 phi 1 U 2 T 3 ux 4 uy 5 rho 6 C/C_inf 7 theta
+// which: 0 phi 1 U 2 T 3 ux 4 uy 5 rho 6 C/C_inf 7 theta.  ulo: the residual
+// plane of the compensated U macro (lo_kind 1: float, 2: BF16; 0: none),
+// added to U in U and C/C_inf.
 template <typename R, typename O>
 __global__ void k_out(const KP<R> P, int which, const R* __restrict__ phi, const R* __restrict__ Um,
                       const R* __restrict__ Tm, const R* __restrict__ uxm, const R* __restrict__ uym,
-                      const R* __restrict__ rhom, const R* __restrict__ accU, const R* __restrict__ accT,
+                      const R* __restrict__ rhom, const void* __restrict__ ulo, int lo_kind,
                       O* __restrict__ dst, const long long* __restrict__ clock) {
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
     if (gx >= P.nx || gy >= P.ny) return;
     const size_t node = (size_t)gy * P.pitch + gx;
     R v = R(0);
     const R U = P.has_U ? Um[node] : R(0);
+    O Uo = (O)U;
+    if (P.has_U && lo_kind == 1) Uo += (O)static_cast<const float*>(ulo)[node];
+    if (P.has_U && lo_kind == 2) Uo += (O)__bfloat162float(static_cast<const __nv_bfloat16*>(ulo)[node]);
     switch (which) {
         case 0: v = phi[node]; break;
-        case 1: v = U; break;
+        case 1: dst[(size_t)gy * P.nx + gx] = Uo; return;
         case 2: v = P.has_T ? Tm[node] : R(0); break;
         case 3: v = P.has_flow ? uxm[node] : R(0); break;
         case 4: v = P.has_flow ? uym[node] : R(0); break;
         case 5: v = P.has_flow ? rhom[node] : R(1); break;
-        case 6: v = R(0.5) * (R(1) + (R(1) - P.k) * U) * ((R(1) + P.k) - (R(1) - P.k) * phi[node]); break;
+        case 6:
+            dst[(size_t)gy * P.nx + gx] =
+                O(0.5) * (O(1) + (O(1) - (O)P.k) * Uo) * ((O(1) + (O)P.k) - (O(1) - (O)P.k) * (O)phi[node]);
+            return;
         case 7:
             if (P.has_T) v = (Tm[node] - P.T_shift) * P.inv_T_scale;
             else if (P.frozen_T) v = theta_frozen(P, gy, (R)(*clock) * P.dt_base);
             else v = P.theta_c;
             break;
     }
-    (void)accU; (void)accT;
     dst[(size_t)gy * P.nx + gx] = (O)v;
 }
 
@@ -101,10 +112,13 @@ __global__ void k_out(const KP<R> P, int which, const R* __restrict__ phi, const
 // Diagnostics: deterministic FP64 reductions (warp shuffle -> block -> grid)
 // ---------------------------------------------------------------------------
 // part[b*3 + 0] = sum C/C_inf, [1] = sum H, [2] = non-finite count, for block b
-template <typename R>
+// Ulo: the residual plane of the compensated U macro (type Lo, pitch layout),
+// added to U in the solute sum, or null.
+template <typename R, typename Lo = R>
 __global__ void __launch_bounds__(256)
 k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ Um, const R* __restrict__ Tm,
-               const R* __restrict__ uxm, const R* __restrict__ uym, double* __restrict__ part) {
+               const R* __restrict__ uxm, const R* __restrict__ uym, double* __restrict__ part,
+               const Lo* __restrict__ Ulo = nullptr) {
     __shared__ double s[3][8];
     double mc = 0.0, h = 0.0, bad = 0.0;
     const long long nn = (long long)P.nx * P.ny;
@@ -112,7 +126,7 @@ k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ U
         const int y = (int)(n / P.nx), x = (int)(n - (long long)y * P.nx);
         const size_t node = (size_t)y * P.pitch + x;
         const double ph = (double)phi[node];
-        const double U = P.has_U ? (double)Um[node] : 0.0;
+        const double U = P.has_U ? (double)Um[node] + (Ulo ? (double)Cvt<Lo>::ld(Ulo[node]) : 0.0) : 0.0;
         const double T = P.has_T ? (double)Tm[node] : 0.0;
         const double vx = P.has_flow ? (double)uxm[node] : 0.0, vy = P.has_flow ? (double)uym[node] : 0.0;
         const double k = (double)P.k;

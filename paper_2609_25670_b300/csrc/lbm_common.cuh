@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
+#include <type_traits>
 
 namespace lbmk {
 
@@ -186,6 +187,21 @@ __device__ __forceinline__ void aniso_frame(R gx, R gy, R eps, R vt, R& as, R& N
     Ny = s * Npx + c * Npy;
 }
 
+// Additions and products in round-to-nearest that the compiler may not
+// contract into fused multiply-adds, and the error-free sum of two numbers
+// (Knuth's TwoSum: s = fl(a + b) and e with a + b = s + e exactly).
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+template <typename R> __device__ __forceinline__ void two_sum(R a, R b, R& s, R& e) {
+    s = add_rn(a, b);
+    const R bv = sub_rn(s, a);
+    e = add_rn(sub_rn(a, sub_rn(s, bv)), sub_rn(b, bv));
+}
+
 // f*_i = w_i A + 3 w_i (e_i . b) + (e_i . c): the scalar collision of Eq. 14
 // with S of Eq. 23 in closed form (columns 3 and 5 of M^-1 are e_x/6, e_y/6;
 // on D2Q5 e_x/2, e_y/2), A = chi + dt Q, b = j_eq = first moment of f_eq,
@@ -195,22 +211,44 @@ __device__ __forceinline__ void aniso_frame(R gx, R gy, R eps, R vt, R& as, R& N
 // 1 + 7.5e-9 (D2Q9) or 1 + 3.0e-8 (D2Q5), and w_0 A would scale the zeroth
 // moment by that every update -- a drift of the conserved solute sum.
 template <typename R, int Q> __device__ __forceinline__ R rest_share(R A, R a1, R a2) {
-    return Q == 9 ? A - R(4) * (a1 + a2) : A - R(4) * a1;
+    return Q == 9 ? sub_rn(A, mul_rn(R(4), add_rn(a1, a2))) : sub_rn(A, mul_rn(R(4), a1));
 }
-// Zeroth moment of a node's streamed populations fn[0..Q-1] (Eq. 18) when its
-// own collision took the zeroth moment chi: chi + sum_i (fn_i - r_i), with r_i
-// the populations of chi at rest (w_i chi; the rest population as the
-// remainder, as rest_share builds it).  Equal to sum_i fn_i in exact
-// arithmetic, since sum_i r_i = chi.  In FP32 the roundings of w_i A in the
-// neighbours' post-collision values and of w_i chi here cancel wherever the
-// field is smooth, and a node of a uniform region keeps its value exactly,
-// so the stored macro does not drift the way a plain Q-term sum of values of
-// order chi does (the roundings of neighbouring nodes are then correlated).
-template <typename R, int Q> __device__ __forceinline__ R streamed_zeroth(R chi, const R* fn) {
-    const R r1 = wqq<R, Q>(1) * chi, r2 = Wt<R>::w2 * chi;
+// Change of a node's zeroth moment by its streamed populations fn[0..Q-1]
+// (Eq. 18) when its own collision took the zeroth moment chi:
+// sum_i (fn_i - r_i), with r_i the populations of chi at rest (w_i chi; the
+// rest population as the remainder, as rest_share builds it), so that
+// chi + streamed_increment = sum_i fn_i in exact arithmetic (sum_i r_i = chi).
+// In FP32 the roundings of w_i A in the neighbours' post-collision values and
+// of w_i chi here cancel wherever the field is smooth, and a node of a
+// uniform region keeps its value exactly; a plain Q-term sum of values of
+// order chi carries the correlated roundings of neighbouring nodes into the
+// stored macro as a drift.
+template <typename R, int Q> __device__ __forceinline__ R streamed_increment(R chi, const R* fn) {
+    // rounded products (mul_rn): a contraction of w_i chi into the
+    // subtractions below would leave the rounding errors of w_i chi -- the
+    // same at every node of a uniform region -- in the increment
+    const R r1 = mul_rn(wqq<R, Q>(1), chi), r2 = mul_rn(Wt<R>::w2, chi);
     R d = (fn[0] - rest_share<R, Q>(chi, r1, r2)) + ((fn[1] - r1) + (fn[3] - r1)) + ((fn[2] - r1) + (fn[4] - r1));
     if constexpr (Q == 9) d += ((fn[5] - r2) + (fn[7] - r2)) + ((fn[6] - r2) + (fn[8] - r2));
-    return chi + d;
+    return d;
+}
+
+// Compensated solute macro.  With FP32 arithmetic the U macro is stored as
+// hi (the macro plane, what every other kernel reads) plus a residual lo in
+// a third plane of the U state, so that increments far below the last bit of
+// hi -- the transport-related source of Eq. 8 and the slow exchange of a
+// smooth field are mostly such -- accumulate instead of being rounded away
+// update after update (which drifts the solute inventory).  lo has the
+// arithmetic type with FP32 storage and BF16 with 16-bit storage (BF16 keeps
+// FP32's exponent range: the residuals lie far below FP16's smallest
+// normal); FP64 stores no residual.
+template <typename ST> struct LoOf { using T = ST; };
+template <> struct LoOf<__half> { using T = __nv_bfloat16; };
+template <typename R> struct Compensated { static constexpr bool value = sizeof(R) == 4; };
+// hi + lo + d as a new (hi, lo): hi takes the rounded sum, lo its exact error
+// (the error of lo + d itself lies far below lo's last bit)
+template <typename R> __device__ __forceinline__ void comp_add(R hi, R lo, R d, R& hi_out, R& lo_out) {
+    two_sum(hi, add_rn(lo, d), hi_out, lo_out);
 }
 // a / b correctly rounded: the phase-change increment of Eq. 38, whose
 // product with the denominator must return the numerator for the exact
@@ -222,7 +260,7 @@ __device__ __forceinline__ double div_rn(double a, double b) { return a / b; }
 template <typename R, int HY, int HX, int Q = 9>
 __device__ __forceinline__ void put_scalar_post(R (*sp)[HY][HX], int ly, int lx, R A, R bx, R by, R cx, R cy) {
     const R w1 = wqq<R, Q>(1), w2 = Wt<R>::w2;
-    const R a1 = w1 * A, a2 = w2 * A, b1x = R(3) * w1 * bx, b1y = R(3) * w1 * by;
+    const R a1 = mul_rn(w1, A), a2 = mul_rn(w2, A), b1x = R(3) * w1 * bx, b1y = R(3) * w1 * by;
     const R b2x = R(3) * w2 * bx, b2y = R(3) * w2 * by;
     sp[0][ly][lx] = rest_share<R, Q>(A, a1, a2);
     sp[1][ly][lx] = a1 + b1x + cx;

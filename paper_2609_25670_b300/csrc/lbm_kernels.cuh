@@ -401,9 +401,12 @@ template <typename R, int TY, int Q = 9> struct ScalarSmem {
 
 // sphi: the phase field on a tile of width GXW whose ring is OFF + 1 nodes
 // wide, so halo position (lx, ly) of the 1-ring sits at (lx + OFF, ly + OFF)
+// Returns the rounding error of A = chi + dt Q (error-free sum): the part of
+// the source the post-collision populations could not carry, which the node
+// adds to its own zeroth moment when it completes its update.
 template <typename R, int TY, int FIELD, int GXW = 36, int OFF = 1, int Q = 9>
-__device__ __forceinline__ void scalar_collide(const KP<R>& P, const R (*sphi)[GXW], R (*sp)[TY + 2][34], int lx,
-                                               int ly, R chi, R jx, R jy, R vx, R vy) {
+__device__ __forceinline__ R scalar_collide(const KP<R>& P, const R (*sphi)[GXW], R (*sp)[TY + 2][34], int lx,
+                                            int ly, R chi, R jx, R jy, R vx, R vy) {
     const R dt = FIELD == 0 ? P.dtU : P.dtT;
     const R ph = sphi[ly + OFF][lx + OFF];
     R D, coef;
@@ -423,7 +426,30 @@ __device__ __forceinline__ void scalar_collide(const KP<R>& P, const R (*sphi)[G
     iso_grad<R, GXW>(sphi, lx + OFF, ly + OFF, gpx, gpy);
     const R Qs = coef * (R(-3) * s) * (jnx * gpx + jny * gpy);                      // Eq. 40 in Eq. 8 / 12
     const R k6 = (R(1) - s) * kneq<R, Q>();
-    put_scalar_post<R, TY + 2, 34, Q>(sp, ly, lx, chi + dt * Qs, bx, by, k6 * jnx, k6 * jny);
+    R A, Ae;
+    two_sum(chi, dt * Qs, A, Ae);
+    put_scalar_post<R, TY + 2, 34, Q>(sp, ly, lx, A, bx, by, k6 * jnx, k6 * jny);
+    return Ae;
+}
+
+// The node's new zeroth moment chi + d (d: streamed_increment plus the
+// source's rounding error) into mac_out; for U with FP32 arithmetic as the
+// compensated pair (hi in mac_out, lo in the third plane of the U state,
+// read from fin's and written to fout's).
+template <typename R, typename ST, int FIELD>
+__device__ __forceinline__ void store_zeroth(const ST* __restrict__ fin, ST* __restrict__ fout, size_t plane,
+                                             size_t node, R chi, R d, R* __restrict__ mac_out) {
+    if constexpr (FIELD == 0 && Compensated<R>::value) {
+        using Lo = typename LoOf<ST>::T;
+        const Lo* lin = reinterpret_cast<const Lo*>(fin + 2 * plane);
+        Lo* lout = reinterpret_cast<Lo*>(fout + 2 * plane);
+        R hi, lo;
+        comp_add(chi, (R)Cvt<Lo>::ld(lin[node]), d, hi, lo);
+        mac_out[node] = hi;
+        lout[node] = Cvt<Lo>::st(lo);
+    } else {
+        mac_out[node] = chi + d;
+    }
 }
 
 template <typename R, typename ST, bool DEV, int TY, int FIELD, bool IN, int Q>
@@ -463,7 +489,8 @@ __device__ __forceinline__ void scalar_tile(ScalarSmem<R, TY, Q>& sm, const KP<R
     }
     load_phi_ring2<R, TY, IN>(P, phi, sm.phi, x0, y0, tid);
     __syncthreads();
-    if (va) scalar_collide<R, TY, FIELD, 36, 1, Q>(P, sm.phi, sm.post, tx + 1, ty + 1, ca, jax, jay, uxa, uya);
+    R aea = R(0);
+    if (va) aea = scalar_collide<R, TY, FIELD, 36, 1, Q>(P, sm.phi, sm.post, tx + 1, ty + 1, ca, jax, jay, uxa, uya);
     if (vb) scalar_collide<R, TY, FIELD, 36, 1, Q>(P, sm.phi, sm.post, blx, bly, cb, jbx, jby, uxb, uyb);
     __syncthreads();
     const int gx = x0 + tx, gy = y0 + ty;
@@ -479,7 +506,8 @@ __device__ __forceinline__ void scalar_tile(ScalarSmem<R, TY, Q>& sm, const KP<R
             if (FIELD == 1 && !IN && ey_of(i) > 0 && w.ym && P.T_dir_ym)              // bottom wall at T_ymin
                 fn[i] = R(2) * wqq<R, Q>(i) * P.T_ymin - sm.post[opp_of(i)][ty + 1][tx + 1];
         }
-        mac_out[node] = streamed_zeroth<R, Q>(ca, fn);                            // Eq. 18
+        store_zeroth<R, ST, FIELD>(fin, fout, (size_t)pl, (size_t)node, ca,
+                                   streamed_increment<R, Q>(ca, fn) + aea, mac_out);     // Eq. 18
         store_j<R, ST>(fout, node, pl, fn);
         if (FIELD == 0 && P.accumulated) myj = fabs(acca);
     }

@@ -61,7 +61,7 @@ __device__ __forceinline__ void strip_grad(int lane, R cm, R c0, R cp, R em, R e
 template <typename R, int Q = 9>
 __device__ __forceinline__ void scalar_post9(R A, R bx, R by, R cx, R cy, R* p) {
     const R w1 = wqq<R, Q>(1), w2 = Wt<R>::w2;
-    const R a1 = w1 * A, a2 = w2 * A, b1x = R(3) * w1 * bx, b1y = R(3) * w1 * by;
+    const R a1 = mul_rn(w1, A), a2 = mul_rn(w2, A), b1x = R(3) * w1 * bx, b1y = R(3) * w1 * by;
     const R b2x = R(3) * w2 * bx, b2y = R(3) * w2 * by;
     p[0] = rest_share<R, Q>(A, a1, a2);
     p[1] = a1 + b1x + cx;
@@ -85,9 +85,10 @@ template <int Q, typename R> __device__ __forceinline__ R diag_from_right(R v) {
 // (with every injection), (jx, jy) the first moment, (vx, vy) the advecting
 // velocity, ph and (gpx, gpy) phi and its gradient (Eqs. 7-8, 10-12, 19-20,
 // 24, 40)
+// (returns the rounding error of chi + dt Q, as scalar_collide does)
 template <typename R, int FIELD, int Q = 9>
-__device__ __forceinline__ void scalar_collide9(const KP<R>& P, R ph, R gpx, R gpy, R chi, R jx, R jy, R vx, R vy,
-                                                R* p) {
+__device__ __forceinline__ R scalar_collide9(const KP<R>& P, R ph, R gpx, R gpy, R chi, R jx, R jy, R vx, R vy,
+                                             R* p) {
     const R dt = FIELD == 0 ? P.dtU : P.dtT;
     R D, coef;
     if (FIELD == 0) {
@@ -104,7 +105,10 @@ __device__ __forceinline__ void scalar_collide9(const KP<R>& P, R ph, R gpx, R g
     const R jnx = jx - bx, jny = jy - by;
     const R Qs = coef * (R(-3) * s) * (jnx * gpx + jny * gpy);                      // Eq. 40 in Eq. 8 / 12
     const R k6 = (R(1) - s) * kneq<R, Q>();
-    scalar_post9<R, Q>(chi + dt * Qs, bx, by, k6 * jnx, k6 * jny, p);
+    R A, Ae;
+    two_sum(chi, dt * Qs, A, Ae);
+    scalar_post9<R, Q>(A, bx, by, k6 * jnx, k6 * jny, p);
+    return Ae;
 }
 
 // ---------------------------------------------------------------------------
@@ -214,7 +218,7 @@ __device__ __forceinline__ void scalar_strip(const KP<R>& P, const ST* __restric
     // carried post-collision values: row r-1 (q0, q1s, q3s; q2, q5s, q6s) and
     // row r-2 (z2, z5s, z6s); own unshifted row r-1 for walls (o[])
     R q0 = R(0), q1 = R(0), q3 = R(0), q2 = R(0), q5 = R(0), q6 = R(0), z2 = R(0), z5 = R(0), z6 = R(0);
-    R cq = R(0);                                   // zeroth moment that entered row r-1's collision
+    R cq = R(0), aq = R(0);                        // row r-1: zeroth moment that entered its collision, source rounding
     R o[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) o[i] = R(0);
@@ -236,7 +240,7 @@ __device__ __forceinline__ void scalar_strip(const KP<R>& P, const ST* __restric
         R gpx, gpy;
         strip_grad<R>(lane, cm, c0, pc, em, e0, pe, gpx, gpy);
         R p[9];
-        scalar_collide9<R, FIELD, Q>(P, c0, gpx, gpy, chi, jx, jy, vx, vy, p);
+        const R ae = scalar_collide9<R, FIELD, Q>(P, c0, gpx, gpy, chi, jx, jy, vx, vy, p);
         const R s1 = from_left(p[1]), s3 = from_right(p[3]), s5 = diag_from_left<Q>(p[5]);
         const R s6 = diag_from_right<Q>(p[6]), s7 = diag_from_right<Q>(p[7]), s8 = diag_from_left<Q>(p[8]);
         const int y = r - 1;                       // row completed in this iteration
@@ -266,12 +270,14 @@ __device__ __forceinline__ void scalar_strip(const KP<R>& P, const ST* __restric
                 }
             }
             const int node = y * P.pitch + gx;
-            mac_out[node] = streamed_zeroth<R, Q>(cq, fn);                        // Eq. 18
+            store_zeroth<R, ST, FIELD>(fin, fout, (size_t)pl, (size_t)node, cq,
+                                       streamed_increment<R, Q>(cq, fn) + aq, mac_out);  // Eq. 18
             store_j<R, ST>(fout, node, pl, fn);
         }
         z2 = q2; z5 = q5; z6 = q6;
         q0 = p[0]; q1 = s1; q3 = s3; q2 = p[2]; q5 = s5; q6 = s6;
         cq = chi;
+        aq = ae;
         if (!IN) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) o[i] = p[i];
@@ -433,9 +439,15 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
     // (za*).  Walking down the latter are e_y = +1 (2, 5, 6); walking up,
     // e_y = -1 (4, 7, 8).
     R q0[VW], q1[VW], q3[VW], qa[VW], qb[VW], qc[VW], za[VW], zb[VW], zc[VW];
-    R cqv[VW];                                  // zeroth moments that entered row r - DIR's collision
+    // row r - DIR: the zeroth moments that entered its collision, their source
+    // rounding errors and (U, FP32 arithmetic) the residuals of the
+    // compensated macro
+    R cqv[VW], aqv[VW], lqv[VW];
 #pragma unroll
-    for (int k = 0; k < VW; ++k) q0[k] = q1[k] = q3[k] = qa[k] = qb[k] = qc[k] = za[k] = zb[k] = zc[k] = cqv[k] = R(0);
+    for (int k = 0; k < VW; ++k)
+        q0[k] = q1[k] = q3[k] = qa[k] = qb[k] = qc[k] = za[k] = zb[k] = zc[k] = cqv[k] = aqv[k] = lqv[k] = R(0);
+    constexpr bool COMP = FIELD == 0 && Compensated<R>::value;
+    using Lo = typename LoOf<ST>::T;
     R myj = R(0);
 #pragma unroll 1
     for (int it = 0; it < NR; ++it) {
@@ -474,11 +486,17 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
         }
         A[0] = from_left(A[VW]); B[0] = from_left(B[VW]);
         A[VW + 1] = from_right(A[1]); B[VW + 1] = from_right(B[1]);
-        R p[VW][9];
+        R p[VW][9], ae[VW], lo_r[VW];
+        if constexpr (COMP) {                      // residuals of row r, used when it completes
+            const Vec4<Lo> lv = *reinterpret_cast<const Vec4<Lo>*>(reinterpret_cast<const Lo*>(fin + 2 * (size_t)pl) +
+                                                                   (size_t)r * pitch + c0);
+#pragma unroll
+            for (int k = 0; k < VW; ++k) lo_r[k] = (R)Cvt<Lo>::ld(lv.v[k]);
+        }
 #pragma unroll
         for (int k = 0; k < VW; ++k) {
             const R gpx = A[k + 2] - A[k], gpy = B[k + 1] * (R(1) / R(3)) + (B[k] + B[k + 2]) * (R(1) / R(12));
-            scalar_collide9<R, FIELD, Q>(P, p0.v[k], gpx, gpy, chi.v[k], jx[k], jy[k], vx.v[k], vy.v[k], p[k]);
+            ae[k] = scalar_collide9<R, FIELD, Q>(P, p0.v[k], gpx, gpy, chi.v[k], jx[k], jy[k], vx.v[k], vy.v[k], p[k]);
         }
         // x-shifts: e_x = +1 (1, 5, 8) from the node on the left, e_x = -1 (3, 6, 7) from the right
         R s1[VW], s5[VW], s8[VW], s3[VW], s6[VW], s7[VW];
@@ -493,7 +511,7 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
             for (int k = 0; k < VW; ++k) myj = fmax(myj, fabs(accv.v[k]));
         if (it >= 2 && outl) {                     // complete row r - DIR
             const int node = (r - DIR) * pitch + c0;
-            Vec4<R> sum;
+            Vec4<R> sum, lnew;
             R fn[9][VW];
 #pragma unroll
             for (int k = 0; k < VW; ++k) {
@@ -508,9 +526,17 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
                 R f9[9];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) f9[i] = fn[i][k];
-                sum.v[k] = streamed_zeroth<R, Q>(cqv[k], f9);
+                const R d = streamed_increment<R, Q>(cqv[k], f9) + aqv[k];
+                if constexpr (COMP) comp_add(cqv[k], lqv[k], d, sum.v[k], lnew.v[k]);
+                else sum.v[k] = cqv[k] + d;
             }
             *reinterpret_cast<Vec4<R>*>(mac_out + node) = sum;                    // Eq. 18
+            if constexpr (COMP) {
+                Vec4<Lo> lo_o;
+#pragma unroll
+                for (int k = 0; k < VW; ++k) lo_o.v[k] = Cvt<Lo>::st(lnew.v[k]);
+                *reinterpret_cast<Vec4<Lo>*>(reinterpret_cast<Lo*>(fout + 2 * (size_t)pl) + node) = lo_o;
+            }
             Vec4<ST> ox, oy;
 #pragma unroll
             for (int k = 0; k < VW; ++k) {
@@ -527,6 +553,8 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
             if (!UP) { qa[k] = p[k][2]; qb[k] = s5[k]; qc[k] = s6[k]; }
             else { qa[k] = p[k][4]; qb[k] = s7[k]; qc[k] = s8[k]; }
             cqv[k] = chi.v[k];
+            aqv[k] = ae[k];
+            if constexpr (COMP) lqv[k] = lo_r[k];
         }
         pb = p0;
         p0 = pf;

@@ -278,7 +278,8 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
     const Walls ws = walls_of<IN>(gx, gy, P.nx, P.ny, P.bsx, P.bsy);
 
     // ---- scalar updates (Eqs. 7-8, 10-12 tr parts; 14, 19-20, 23-25, 40)
-    auto scalar_stream = [&](ST* __restrict__ fout, R* __restrict__ mac_out, bool dir_ym, R chi) {
+    auto scalar_stream = [&](const ST* __restrict__ fin, ST* __restrict__ fout, R* __restrict__ mac_out, bool dir_ym,
+                             R chi, R ae, auto field) {
         if (!own) return;
         const int node = gy * P.pitch + gx;
         R fn[9];
@@ -289,14 +290,16 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
             if (!IN && dir_ym && ey_of(i) > 0 && ws.ym)                            // bottom wall at T_ymin
                 fn[i] = R(2) * wqq<R, Q>(i) * P.T_ymin - sm.post[opp_of(i)][ty + 1][tx + 1];
         }
-        mac_out[node] = streamed_zeroth<R, Q>(chi, fn);                          // Eq. 18
+        store_zeroth<R, ST, decltype(field)::value>(fin, fout, (size_t)pl, (size_t)node, chi,
+                                                     streamed_increment<R, Q>(chi, fn) + ae, mac_out);   // Eq. 18
         store_j<R, ST>(fout, node, pl, fn);
     };
     if (A.do_U) {
-        if (va) scalar_collide<R, TY, 0, 38, 2, Q>(P, sm.phi, sm.post, tx + 1, ty + 1, Uia, jax, jay, uxa, uya);
+        R aea = R(0);
+        if (va) aea = scalar_collide<R, TY, 0, 38, 2, Q>(P, sm.phi, sm.post, tx + 1, ty + 1, Uia, jax, jay, uxa, uya);
         if (vb) scalar_collide<R, TY, 0, 38, 2, Q>(P, sm.phi, sm.post, blx, bly, Uib, jbx, jby, uxb, uyb);
         __syncthreads();
-        scalar_stream(A.fUout, A.Uout, false, Uia);
+        scalar_stream(A.fUin, A.fUout, A.Uout, false, Uia, aea, std::integral_constant<int, 0>{});
         __syncthreads();
     }
     if (A.do_T) {
@@ -309,10 +312,11 @@ __device__ __forceinline__ void transport_tile(TransportSmem<R, TY>& sm, const K
             jbx = word_value<R, ST>(sm.pb[PF_TJX][tid], (nb & 1) != 0);
             jby = word_value<R, ST>(sm.pb[PF_TJY][tid], (nb & 1) != 0);
         }
-        if (va) scalar_collide<R, TY, 1, 38, 2, Q>(P, sm.phi, sm.post, tx + 1, ty + 1, Tia, jax, jay, uxa, uya);
+        R aea = R(0);
+        if (va) aea = scalar_collide<R, TY, 1, 38, 2, Q>(P, sm.phi, sm.post, tx + 1, ty + 1, Tia, jax, jay, uxa, uya);
         if (vb) scalar_collide<R, TY, 1, 38, 2, Q>(P, sm.phi, sm.post, blx, bly, Tib, jbx, jby, uxb, uyb);
         __syncthreads();
-        scalar_stream(A.fTout, A.Tout, P.T_dir_ym != 0, Tia);
+        scalar_stream(A.fTin, A.fTout, A.Tout, P.T_dir_ym != 0, Tia, aea, std::integral_constant<int, 1>{});
         __syncthreads();
     }
 

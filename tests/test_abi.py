@@ -40,15 +40,15 @@ def test_header_declarations_are_exported(lib):
 def test_struct_layout_matches_c(tmp_path):
     prog = tmp_path / "layout.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbm.h"\nint main(void){'
-                    'printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lbm_params), sizeof(lbm_seed), '
+                    'printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lbm_params), sizeof(lbm_seed), '
                     'sizeof(lbm_diag), offsetof(lbm_params, dt_base), offsetof(lbm_params, frozen_V), '
-                    'offsetof(lbm_diag, tip), sizeof(lbm_allocator)); return 0;}\n')
+                    'offsetof(lbm_diag, tip), sizeof(lbm_allocator), offsetof(lbm_diag, R_M)); return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [C.sizeof(lbm.lbm_params), C.sizeof(lbm.lbm_seed), C.sizeof(lbm.lbm_diag),
             lbm.lbm_params.dt_base.offset, lbm.lbm_params.frozen_V.offset, lbm.lbm_diag.tip.offset,
-            C.sizeof(lbm.lbm_allocator)]
+            C.sizeof(lbm.lbm_allocator), lbm.lbm_diag.R_M.offset]
     assert got == want
 
 

@@ -1,0 +1,71 @@
+"""Solute inventory of the reduced-precision forms against the FP64 oracle
+(the accuracy statement of the mixed-precision design: the relative solute
+drift R_M = (M_C - M_C(0)) / M_C(0) of a run, Sec. 4.4, within 1e-8 of the
+oracle's at the same base step).
+
+The FP32 path keeps the solute macro compensated (hi plus a residual plane)
+and adds the rounding error of each node's chi + dt Q to its own update, so
+increments below the last bit of the stored macro are not rounded away
+update after update; the transfer of Eqs. 36-39 conserves the inventory
+exactly up to rounding.  Workloads: the 128^2 thermosolutal free dendrite
+with forced convection, on D2Q9 and D2Q5 scalar lattices, with the solid
+diffusivity of the workload list (D_S = 1e-2 D_L, tau_U in the solid 0.508)
+and a tenfold one (tau_U = 0.58)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_helpers import run_oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2609_25670_b300 as lbm  # noqa: E402
+
+STEPS = 1000
+
+
+def _drift_pair(q, ds_ratio, precision, steps=STEPS):
+    wl = W.thermosolutal_convection(n=128, R=8.0)
+    p = wl.params
+    p.q_scalar = q
+    p.DS = ds_ratio * p.DL
+    o = oracle.Oracle(p, wl.fields)
+    m0 = o.diagnostics()["M_C"]
+    o.advance(steps)
+    r_or = (o.diagnostics()["M_C"] - m0) / m0
+    o.close()
+    sim = lbm.Simulation(p, precision=precision)
+    sim.init_fields(wl.fields)
+    sim.advance(steps)
+    d = sim.diagnostics()
+    sim.close()
+    return d["R_M"], r_or
+
+
+@pytest.mark.parametrize("q", [9, 5])
+@pytest.mark.parametrize("ds_ratio", [1e-2, 1e-1])
+def test_fp32_solute_drift_within_1e8_of_the_oracle(q, ds_ratio):
+    r, r_or = _drift_pair(q, ds_ratio, "f32")
+    assert abs(r - r_or) < 1e-8, (r, r_or, abs(r - r_or))
+
+
+@pytest.mark.parametrize("q", [9, 5])
+def test_fp64_solute_drift_matches_the_oracle(q):
+    r, r_or = _drift_pair(q, 1e-1, "f64")
+    assert abs(r - r_or) < 1e-12, (r, r_or)
+
+
+def test_r_m_is_zero_right_after_initialisation():
+    wl = W.thermosolutal_convection(n=64, R=6.0)
+    sim = lbm.Simulation(wl.params, precision="f32")
+    sim.init_fields(wl.fields)
+    assert sim.diagnostics()["R_M"] == 0.0
+    sim.advance(10)
+    sim.init_fields(wl.fields)                    # a new initialisation is a new reference
+    assert sim.diagnostics()["R_M"] == 0.0
+    sim.close()
