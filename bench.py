@@ -56,6 +56,9 @@ KINDS = ["phase", "transfer", "scalar_U", "scalar_T", "flow", "transport"]
 # storage precision (16-bit storage keeps FP32 macros)
 POP_BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
 MACRO_BYTES = {"f64": 8, "f32": 4, "f16dev": 4, "bf16dev": 4}
+# the residual plane of the compensated U macro (BF16, read and written by
+# each U update) with FP32 arithmetic
+U_RESIDUAL_BYTES = {"f64": 0, "f32": 4, "f16dev": 4, "bf16dev": 4}
 
 
 def algo_bytes(prec="f32", q=9, ori=False):
@@ -70,7 +73,7 @@ def algo_bytes(prec="f32", q=9, ori=False):
     return {
         "phase": 2 * (q - 1) * pb + (5 if ori else 4) * m,   # pops R+W, phi^q, U, T (, angle) R, phi^{q+1} W
         "transfer": 6 * m,                      # phi^q, phi^{q+1}, U, T R; U, T W
-        "scalar_U": moms + 5 * m,               # j R+W, U R+W, phi R, u R (2)
+        "scalar_U": moms + 5 * m + U_RESIDUAL_BYTES[prec],   # j R+W, U R+W, phi R, u R (2), residual R+W
         "scalar_T": moms + 5 * m,
         "flow": pops + 7 * m,                   # pops, phi R, (rho, ux, uy) R + W
     }
@@ -95,7 +98,7 @@ def transport_bytes(tr, u, t, f, has_T=True, has_flow=True, prec="f32"):
     if (u or t) and has_flow:
         b += 2 * m                              # u for the scalar equilibria
     if u:
-        b += moms + m
+        b += moms + m + U_RESIDUAL_BYTES[prec]
     if t:
         b += moms + m
     if f:

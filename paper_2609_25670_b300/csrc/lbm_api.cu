@@ -178,6 +178,12 @@ lbm_status fail(lbm_sim* h, lbm_status s, const char* fmt, ...) {
 // planes of the stored U state: (j_x, j_y), plus the residual of the
 // compensated macro with FP32 arithmetic (Compensated in lbm_common.cuh)
 int u_planes(uint32_t precision) { return precision == LBM_PREC_F64 ? 2 : 3; }
+// the residual plane (BF16) of the current U state, or null
+const __nv_bfloat16* u_residual(const lbm_sim* h, const SimState& s) {
+    if (!s.has_U || h->precision == LBM_PREC_F64) return nullptr;
+    const size_t esz = h->precision == LBM_PREC_F32 ? sizeof(float) : 2;    // element size of the U state
+    return (const __nv_bfloat16*)((const char*)s.pops[FU][s.cur_pop[FU]] + 2 * s.nn * esz);
+}
 
 lbm_status dev_alloc(lbm_sim* h, size_t bytes, void** out) {
     *out = nullptr;
@@ -1158,8 +1164,8 @@ lbm_status read_field(lbm_sim* h, SimState& s, uint32_t which, void* dst, int ds
     if (s.clock) k_set_clock<<<1, 1, 0, h->stream>>>(s.clock, (long long)s.step);
     const int fc = s.cur_pop[FF];
     // U carries the residual of its compensated macro (FP32 arithmetic)
-    const int lo_kind = !s.has_U || h->precision == LBM_PREC_F64 ? 0 : h->precision == LBM_PREC_F32 ? 1 : 2;
-    const void* ulo = lo_kind ? (const char*)s.pops[FU][s.cur_pop[FU]] + 2 * s.nn * (lo_kind == 1 ? 4 : 2) : nullptr;
+    const void* ulo = u_residual(h, s);
+    const int lo_kind = ulo ? 2 : 0;
     if (as_f64)
         k_out<R, double><<<grd, blk, 0, h->stream>>>(P, (int)which, (const R*)s.phi[s.cur_phi],
                                                      s.has_U ? (const R*)s.U[s.cur_U] : nullptr,
@@ -1190,14 +1196,10 @@ void enqueue_diag(lbm_sim* h, SimState& s) {
         const R* Tm = s.has_T ? (const R*)s.T[s.cur_T] : nullptr;
         // the solute sum includes the residual plane of the compensated U macro
         if constexpr (sizeof(R) == 4) {
-            if (s.has_U && h->precision == LBM_PREC_F32)
-                k_diag_partial<R, float><<<s.diag_blocks, 256, 0, h->stream>>>(
-                    P, (const R*)s.phi[s.cur_phi], Um, Tm, (const R*)s.ux[fc], (const R*)s.uy[fc], s.part,
-                    (const float*)s.pops[FU][s.cur_pop[FU]] + 2 * s.nn);
-            else if (s.has_U)
+            if (s.has_U)
                 k_diag_partial<R, __nv_bfloat16><<<s.diag_blocks, 256, 0, h->stream>>>(
                     P, (const R*)s.phi[s.cur_phi], Um, Tm, (const R*)s.ux[fc], (const R*)s.uy[fc], s.part,
-                    (const __nv_bfloat16*)s.pops[FU][s.cur_pop[FU]] + 2 * s.nn);
+                    u_residual(h, s));
             else
                 k_diag_partial<R><<<s.diag_blocks, 256, 0, h->stream>>>(
                     P, (const R*)s.phi[s.cur_phi], Um, Tm, (const R*)s.ux[fc], (const R*)s.uy[fc], s.part);

@@ -238,23 +238,29 @@ template <typename R, int Q> __device__ __forceinline__ R streamed_increment(R c
 // a third plane of the U state, so that increments far below the last bit of
 // hi -- the transport-related source of Eq. 8 and the slow exchange of a
 // smooth field are mostly such -- accumulate instead of being rounded away
-// update after update (which drifts the solute inventory).  lo has the
-// arithmetic type with FP32 storage and BF16 with 16-bit storage (BF16 keeps
-// FP32's exponent range: the residuals lie far below FP16's smallest
-// normal); FP64 stores no residual.
-template <typename ST> struct LoOf { using T = ST; };
-template <> struct LoOf<__half> { using T = __nv_bfloat16; };
+// update after update (which drifts the solute inventory).  lo is stored in
+// BF16 (the plane's first half with FP32 storage): it keeps FP32's exponent
+// range -- the residuals lie far below FP16's smallest normal -- and its 8
+// bits leave a loss below 2^-9 of hi's last bit per update.  FP64 stores no
+// residual.
+template <typename ST> struct LoOf { using T = __nv_bfloat16; };
 template <typename R> struct Compensated { static constexpr bool value = sizeof(R) == 4; };
 // hi + lo + d as a new (hi, lo): hi takes the rounded sum, lo its exact error
 // (the error of lo + d itself lies far below lo's last bit)
 template <typename R> __device__ __forceinline__ void comp_add(R hi, R lo, R d, R& hi_out, R& lo_out) {
     two_sum(hi, add_rn(lo, d), hi_out, lo_out);
 }
-// a / b correctly rounded: the phase-change increment of Eq. 38, whose
-// product with the denominator must return the numerator for the exact
-// solute balance of the transfer (a reciprocal approximation leaves a
-// relative error of up to 2^-22 in every injection)
-__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+// a / b for the phase-change increment of Eq. 38, whose product with the
+// denominator must return the numerator for the exact solute balance of the
+// transfer.  FP32: the quotient from the hardware reciprocal, q = a rcp(b),
+// then one correction by its residual, q + (a - q b) rcp(b) (Newton's step on
+// the quotient, Markstein's residual form): the residual is exact in a fused
+// multiply-add, so the result is within one unit in the last place and
+// carries no systematic part of the reciprocal's error.  FP64: IEEE division.
+__device__ __forceinline__ float div_rn(float a, float b) {
+    const float r = rcp(b), q = a * r;
+    return fmaf(fmaf(-q, b, a), r, q);
+}
 __device__ __forceinline__ double div_rn(double a, double b) { return a / b; }
 
 template <typename R, int HY, int HX, int Q = 9>

@@ -383,7 +383,7 @@ template <typename T> __device__ __forceinline__ Vec4<T> sread(const unsigned ch
     return *reinterpret_cast<const Vec4<T>*>(p);
 }
 
-enum { VA_JX = 0, VA_JY = 1, VA_CHI = 2, VA_ACC = 3, VA_VX = 4, VA_VY = 5, VA_PHI = 6, VA_N = 7 };
+enum { VA_JX = 0, VA_JY = 1, VA_CHI = 2, VA_ACC = 3, VA_VX = 4, VA_VY = 5, VA_PHI = 6, VA_LO = 7, VA_N = 8 };
 // per-warp ring of row slots, each holding NA arrays of one 16-byte (FP32)
 // entry per lane
 template <typename R, int NA, int DD = 0> struct VRingN {
@@ -414,11 +414,14 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
     const bool outl = lane >= 1 && lane <= 30;
     const int rfirst = UP ? y0 + H : y0 - 1;    // first collision row
     unsigned char* const mine = ring + lane * EB;
+    constexpr bool COMP = FIELD == 0 && Compensated<R>::value;
+    using Lo = typename LoOf<ST>::T;
     auto fetch_row = [&](int r, unsigned char* slot) {      // collision row r, phi row r + DIR
         const int base = r * pitch + c0;
         fetch_vec<ST>(slot + VA_JX * 32 * EB, fin + base);
         fetch_vec<ST>(slot + VA_JY * 32 * EB, fin + (size_t)pl + base);
         fetch_vec<R>(slot + VA_CHI * 32 * EB, mac_in + base);
+        if constexpr (COMP) fetch_vec<Lo>(slot + VA_LO * 32 * EB, reinterpret_cast<const Lo*>(fin + 2 * (size_t)pl) + base);
         if (P.accumulated) fetch_vec<R>(slot + VA_ACC * 32 * EB, acc + base);
         if (P.has_flow) {
             fetch_vec<R>(slot + VA_VX * 32 * EB, ux + base);
@@ -446,8 +449,6 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
 #pragma unroll
     for (int k = 0; k < VW; ++k)
         q0[k] = q1[k] = q3[k] = qa[k] = qb[k] = qc[k] = za[k] = zb[k] = zc[k] = cqv[k] = aqv[k] = lqv[k] = R(0);
-    constexpr bool COMP = FIELD == 0 && Compensated<R>::value;
-    using Lo = typename LoOf<ST>::T;
     R myj = R(0);
 #pragma unroll 1
     for (int it = 0; it < NR; ++it) {
@@ -488,8 +489,7 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
         A[VW + 1] = from_right(A[1]); B[VW + 1] = from_right(B[1]);
         R p[VW][9], ae[VW], lo_r[VW];
         if constexpr (COMP) {                      // residuals of row r, used when it completes
-            const Vec4<Lo> lv = *reinterpret_cast<const Vec4<Lo>*>(reinterpret_cast<const Lo*>(fin + 2 * (size_t)pl) +
-                                                                   (size_t)r * pitch + c0);
+            const Vec4<Lo> lv = sread<Lo>(sl + VA_LO * 32 * EB);
 #pragma unroll
             for (int k = 0; k < VW; ++k) lo_r[k] = (R)Cvt<Lo>::ld(lv.v[k]);
         }
