@@ -210,6 +210,25 @@ def stable_solid(p: Params, tau_min: float = TAU_U_SOLID_MIN) -> Params:
     return p
 
 
+def stable_variant(p: Params, tau_min: float = TAU_U_SOLID_MIN) -> Params:
+    """The labelled variant of a listed workload whose relaxation times all
+    lie at or above tau_min, in the way the paper keeps them in range -- by
+    the update factors (Sec. 3.3; Secs. 4.3-4.4 choose N_U so that tau_U stays
+    in 0.524 - 0.860): N_phi raised to the smallest factor with
+    tau_phi = 3 N_phi dt_base W0^2 / tau0 + 1/2 >= tau_min (Eq. 24 at
+    a_s = 1), N_U to the smallest with tau_U,L >= tau_min, and then D_S by
+    stable_solid.  A workload already in range is returned unchanged.
+    Returns p."""
+    w = p.W0 * p.W0 / p.tau0
+    while 3.0 * p.N_phi * p.dt_base * w + 0.5 < tau_min:
+        p.N_phi += 1
+    if p.has_U:
+        while tau_U(p, -1.0) < tau_min:
+            p.N_U += 1
+        stable_solid(p, tau_min)
+    return p
+
+
 def tau_U(p: Params, phi: float) -> float:
     """Solute relaxation time of Eq. 24 with D_eff of Eq. 7."""
     D = ((1 + phi) * p.DS + (1 - phi) * p.DL) / ((1 + p.k) - (1 - p.k) * phi)
