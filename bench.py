@@ -132,8 +132,8 @@ def step_bytes_md(p, prec, fused, q):
     ab = algo_bytes(prec, q, ori=True)
     if fused:
         tb, _ = period_bytes(p, prec)
-        return ab["phase"] + tb / (2 * MD_PERIOD)
-    return (ab["phase"] + ab["transfer"] + ab["scalar_U"] / p.N_U + ab["scalar_T"] / p.N_T
+        return ab["phase"] / p.N_phi + tb / (2 * MD_PERIOD)
+    return ((ab["phase"] + ab["transfer"]) / p.N_phi + ab["scalar_U"] / p.N_U + ab["scalar_T"] / p.N_T
             + ab["flow"] / p.N_F)
 
 
@@ -456,11 +456,13 @@ def run_reference(args):
     return 0
 
 
-def timed_md_steps(torch, sim, steps, reinit):
+def timed_md_steps(torch, sim, steps, reinit, nvtx=False):
     """`steps` schedule periods, each between two CUDA events on the library
     stream; every MD_RESEED_BASE_STEPS base steps (untimed, between events)
     the state restarts from the initial fields, so every timed step lies in
-    the workload's first base steps.  Returns per-step milliseconds."""
+    the workload's first base steps.  nvtx: the first step's launches inside
+    an NVTX range "lbm_period" (profiling runs select them by it).  Returns
+    per-step milliseconds."""
     chunk = max(1, MD_RESEED_BASE_STEPS // MD_PERIOD)
     times = []
     done = 0
@@ -473,7 +475,12 @@ def timed_md_steps(torch, sim, steps, reinit):
         for k in range(n):
             with torch.cuda.stream(sim.stream):
                 ev[k][0].record(sim.stream)
+            mark = nvtx and done == 0 and k == 0
+            if mark:
+                torch.cuda.nvtx.range_push("lbm_period")
             sim.advance(MD_PERIOD)
+            if mark:
+                torch.cuda.nvtx.range_pop()
             with torch.cuda.stream(sim.stream):
                 ev[k][1].record(sim.stream)
         torch.cuda.synchronize()
@@ -494,6 +501,8 @@ def measure_md(args, torch, lbm, local, dev, prec, q, world=1, with_e2e=False):
     sim = lbm.Simulation(p, precision=prec)
     if args.fusion != "auto":
         sim.set_fusion(args.fusion == "on")
+    if args.no_graphs:
+        sim.set_graphs(False)
     sim.set_orientation(grain_angles(p.nx))          # each grain in its own crystal frame
     seeds = md_seeds(pts)
 
@@ -524,7 +533,7 @@ def measure_md(args, torch, lbm, local, dev, prec, q, world=1, with_e2e=False):
     clocks.start()
     time.sleep(0.2)
     w0 = time.perf_counter()
-    times = timed_md_steps(torch, sim, args.steps, reinit)
+    times = timed_md_steps(torch, sim, args.steps, reinit, nvtx=args.nvtx)
     wall = time.perf_counter() - w0
     clk = clocks.stop()
     launches1 = sim.launch_counts()
@@ -1219,6 +1228,9 @@ def main():
     ap.add_argument("--q-scalar", type=int, default=5, choices=[9, 5],
                     help="velocities of the phase, U and T lattices: 5 (D2Q5, as the workload list states "
                          "them; default) or 9 (the paper's D2Q9)")
+    ap.add_argument("--nvtx", action="store_true",
+                    help="profiling runs: the first timed step's launches inside an NVTX range 'lbm_period'")
+    ap.add_argument("--no-graphs", action="store_true", help="profiling runs: plain stream launches, no CUDA graphs")
     ap.add_argument("--lattice", type=int, default=None,
                     help="lattice size override for profiling runs (reported: 8192, or 512 for convection512)")
     args = ap.parse_args()
