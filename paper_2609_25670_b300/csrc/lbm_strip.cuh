@@ -372,6 +372,39 @@ __host__ __device__ inline Frame frame_of(const Rect& in, int nx, int ny, int uw
 
 template <typename T> struct alignas(sizeof(T) * VW) Vec4 { T v[VW]; };
 
+// a lane's four stored values to and from the arithmetic type; 16-bit
+// types convert two at a time (one paired conversion instruction each)
+template <typename ST, typename R> __device__ __forceinline__ Vec4<ST> pack4(const R* v) {
+    Vec4<ST> o;
+    if constexpr (std::is_same<ST, __half>::value) {
+        __half2* h = reinterpret_cast<__half2*>(o.v);
+        h[0] = __floats2half2_rn((float)v[0], (float)v[1]);
+        h[1] = __floats2half2_rn((float)v[2], (float)v[3]);
+    } else if constexpr (std::is_same<ST, __nv_bfloat16>::value) {
+        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(o.v);
+        h[0] = __floats2bfloat162_rn((float)v[0], (float)v[1]);
+        h[1] = __floats2bfloat162_rn((float)v[2], (float)v[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < VW; ++k) o.v[k] = Cvt<ST>::st(v[k]);
+    }
+    return o;
+}
+template <typename ST, typename R> __device__ __forceinline__ void unpack4(const Vec4<ST>& in, R* v) {
+    if constexpr (std::is_same<ST, __half>::value) {
+        const __half2* h = reinterpret_cast<const __half2*>(in.v);
+        const float2 a = __half22float2(h[0]), b = __half22float2(h[1]);
+        v[0] = (R)a.x; v[1] = (R)a.y; v[2] = (R)b.x; v[3] = (R)b.y;
+    } else if constexpr (std::is_same<ST, __nv_bfloat16>::value) {
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(in.v);
+        const float2 a = __bfloat1622float2(h[0]), b = __bfloat1622float2(h[1]);
+        v[0] = (R)a.x; v[1] = (R)a.y; v[2] = (R)b.x; v[3] = (R)b.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < VW; ++k) v[k] = (R)Cvt<ST>::ld(in.v[k]);
+    }
+}
+
 // asynchronous copy of one lane's vector (VW elements of T) into shared memory
 template <typename T>
 __device__ __forceinline__ void fetch_vec(unsigned char* dst, const T* src) {
@@ -459,14 +492,8 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
         const unsigned char* sl = mine + (it % D) * RG::SLOT;
         // first moments of the streamed populations
         R jx[VW], jy[VW];
-        {
-            const Vec4<ST> vjx = sread<ST>(sl + VA_JX * 32 * EB), vjy = sread<ST>(sl + VA_JY * 32 * EB);
-#pragma unroll
-            for (int k = 0; k < VW; ++k) {
-                jx[k] = (R)Cvt<ST>::ld(vjx.v[k]);
-                jy[k] = (R)Cvt<ST>::ld(vjy.v[k]);
-            }
-        }
+        unpack4<ST, R>(sread<ST>(sl + VA_JX * 32 * EB), jx);
+        unpack4<ST, R>(sread<ST>(sl + VA_JY * 32 * EB), jy);
         Vec4<R> chi = sread<R>(sl + VA_CHI * 32 * EB), accv{}, vx{}, vy{};
         if (P.accumulated) {
             accv = sread<R>(sl + VA_ACC * 32 * EB);
@@ -488,11 +515,7 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
         A[0] = from_left(A[VW]); B[0] = from_left(B[VW]);
         A[VW + 1] = from_right(A[1]); B[VW + 1] = from_right(B[1]);
         R p[VW][9], ae[VW], lo_r[VW];
-        if constexpr (COMP) {                      // residuals of row r, used when it completes
-            const Vec4<Lo> lv = sread<Lo>(sl + VA_LO * 32 * EB);
-#pragma unroll
-            for (int k = 0; k < VW; ++k) lo_r[k] = (R)Cvt<Lo>::ld(lv.v[k]);
-        }
+        if constexpr (COMP) unpack4<Lo, R>(sread<Lo>(sl + VA_LO * 32 * EB), lo_r);   // residuals of row r
 #pragma unroll
         for (int k = 0; k < VW; ++k) {
             const R gpx = A[k + 2] - A[k], gpy = B[k + 1] * (R(1) / R(3)) + (B[k] + B[k + 2]) * (R(1) / R(12));
@@ -532,19 +555,17 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
             }
             *reinterpret_cast<Vec4<R>*>(mac_out + node) = sum;                    // Eq. 18
             if constexpr (COMP) {
-                Vec4<Lo> lo_o;
-#pragma unroll
-                for (int k = 0; k < VW; ++k) lo_o.v[k] = Cvt<Lo>::st(lnew.v[k]);
-                *reinterpret_cast<Vec4<Lo>*>(reinterpret_cast<Lo*>(fout + 2 * (size_t)pl) + node) = lo_o;
+                *reinterpret_cast<Vec4<Lo>*>(reinterpret_cast<Lo*>(fout + 2 * (size_t)pl) + node) =
+                    pack4<Lo, R>(lnew.v);
             }
-            Vec4<ST> ox, oy;
+            R ox[VW], oy[VW];
 #pragma unroll
             for (int k = 0; k < VW; ++k) {
-                ox.v[k] = Cvt<ST>::st(fn[1][k] - fn[3][k] + fn[5][k] - fn[6][k] - fn[7][k] + fn[8][k]);
-                oy.v[k] = Cvt<ST>::st(fn[2][k] - fn[4][k] + fn[5][k] + fn[6][k] - fn[7][k] - fn[8][k]);
+                ox[k] = fn[1][k] - fn[3][k] + fn[5][k] - fn[6][k] - fn[7][k] + fn[8][k];
+                oy[k] = fn[2][k] - fn[4][k] + fn[5][k] + fn[6][k] - fn[7][k] - fn[8][k];
             }
-            *reinterpret_cast<Vec4<ST>*>(fout + node) = ox;
-            *reinterpret_cast<Vec4<ST>*>(fout + (size_t)pl + node) = oy;
+            *reinterpret_cast<Vec4<ST>*>(fout + node) = pack4<ST, R>(ox);
+            *reinterpret_cast<Vec4<ST>*>(fout + (size_t)pl + node) = pack4<ST, R>(oy);
         }
 #pragma unroll
         for (int k = 0; k < VW; ++k) {
@@ -683,15 +704,14 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
         const unsigned char* sl = mine + (it % D) * RG::SLOT;
         const Vec4<R> rho = sread<R>(sl + FA_RHO * 32 * EB), vx = sread<R>(sl + FA_UX * 32 * EB);
         const Vec4<R> vy = sread<R>(sl + FA_UY * 32 * EB), ph = sread<R>(sl + FA_PHI * 32 * EB);
-        R p[VW][9], fl[VW];
+        R p[VW][9], fl[VW], fr[9][VW];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) unpack4<ST, R>(sread<ST>(sl + (i - 1) * 32 * EB), fr[i]);
 #pragma unroll
         for (int k = 0; k < VW; ++k) {
             R f[9];
 #pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                const Vec4<ST> v = sread<ST>(sl + (i - 1) * 32 * EB);
-                f[i] = (R)Cvt<ST>::ld(v.v[k]);
-            }
+            for (int i = 1; i < 9; ++i) f[i] = fr[i][k];
             if (DEV)       // h_i = f_i - w_i rho of the writer's density
 #pragma unroll
                 for (int i = 1; i < 9; ++i) f[i] += wq<R>(i) * rho.v[k];
@@ -747,10 +767,10 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
             *reinterpret_cast<Vec4<R>*>(uy_out + node) = vuy;
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
-                Vec4<ST> ov;
+                R ev[VW];
 #pragma unroll
-                for (int k = 0; k < VW; ++k) ov.v[k] = Cvt<ST>::st(DEV ? fn[i][k] - wq<R>(i) * vrho.v[k] : fn[i][k]);
-                *reinterpret_cast<Vec4<ST>*>(fout + (size_t)(i - 1) * pl + node) = ov;
+                for (int k = 0; k < VW; ++k) ev[k] = DEV ? fn[i][k] - wq<R>(i) * vrho.v[k] : fn[i][k];
+                *reinterpret_cast<Vec4<ST>*>(fout + (size_t)(i - 1) * pl + node) = pack4<ST, R>(ev);
             }
         }
         // roll: row y becomes the far row, row r becomes row y
@@ -1100,9 +1120,7 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
                 for (int k = 0; k < VW; ++k) f[i][k] = R(0);
                 continue;
             }
-            const Vec4<ST> v = sread<ST>(sl + (i - 1) * 32 * EB);
-#pragma unroll
-            for (int k = 0; k < VW; ++k) f[i][k] = (R)Cvt<ST>::ld(v.v[k]);
+            unpack4<ST, R>(sread<ST>(sl + (i - 1) * 32 * EB), f[i]);
         }
         const Vec4<R> pf = sread<R>(sl + PA_PHI * 32 * EB);
         Vec4<R> Us{}, Tv{}, Ov{};
@@ -1181,9 +1199,10 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
             *reinterpret_cast<Vec4<R>*>(phin + node) = sum;
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
-                Vec4<ST> o;
+                R ev[VW];
 #pragma unroll
-                for (int k = 0; k < VW; ++k) o.v[k] = Cvt<ST>::st(DEV ? fn[i][k] - wqq<R, Q>(i) * sum.v[k] : fn[i][k]);
+                for (int k = 0; k < VW; ++k) ev[k] = DEV ? fn[i][k] - wqq<R, Q>(i) * sum.v[k] : fn[i][k];
+                const Vec4<ST> o = pack4<ST, R>(ev);
                 *reinterpret_cast<Vec4<ST>*>(fout + (size_t)(i - 1) * pl + node) = o;
             }
         }
