@@ -512,7 +512,10 @@ def measure_md(args, torch, lbm, local, dev, prec, q, world=1, with_e2e=False):
     reinit()
     for _ in range(max(args.warmup, 3)):
         sim.advance(MD_PERIOD)
-    tiles = sim.autotune(reps=3)
+    if args.no_autotune:                    # profiling runs: the variants --tile fixes, the defaults otherwise
+        tiles = {k: 0 for k in KINDS}
+    else:
+        tiles = sim.autotune(reps=3)
     for spec in args.tile or []:            # fixed kernel variants (profiling runs)
         kind, v = spec.split("=")
         sim.set_tile(kind, int(v))
@@ -1231,6 +1234,7 @@ def main():
     ap.add_argument("--nvtx", action="store_true",
                     help="profiling runs: the first timed step's launches inside an NVTX range 'lbm_period'")
     ap.add_argument("--no-graphs", action="store_true", help="profiling runs: plain stream launches, no CUDA graphs")
+    ap.add_argument("--no-autotune", action="store_true", help="profiling runs: no autotuning (use --tile)")
     ap.add_argument("--lattice", type=int, default=None,
                     help="lattice size override for profiling runs (reported: 8192, or 512 for convection512)")
     args = ap.parse_args()
