@@ -140,19 +140,24 @@ def step_bytes_md(p, prec, fused, q):
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of ncu captures
 # per kernel variant, summarised in profiles/.  TRAFFIC_PER_LAUNCH_512: per
 # launch on the 512^2 workload ("q<velocities of the phase, U, T lattices>:
-# kind:variant").  TRAFFIC_PER_NODE: per node, from a 2048^2 capture of the
-# multi-dendrite workload ("<storage>:q<velocities>:kind:variant", ":ori" for
-# the phase update with grain angles); a vector-strip launch moves the same
-# bytes per node at any lattice size, so the reported traffic of an 8192^2
-# launch is this figure times its nodes.  Reported only while the kernel
-# sources hash to TRAFFIC_SOURCE_SHA; after any change of the code the
-# traffic is null until re-measured.
-TRAFFIC_SOURCE_SHA = "ace4b0757b2c0eb7"
-# (transport: the mean of the period's two kinds of launch, transfer + U
-# alone and transfer + U + T + flow, like the algorithmic bytes it is set
-# against)
+# kind:variant"; none recorded).  TRAFFIC_PER_NODE: per node
+# ("<storage>:q<velocities>:kind:variant", ":ori" for the phase update with
+# grain angles), times the nodes of a launch.  Reported only while the
+# kernel sources hash to TRAFFIC_SOURCE_SHA; after any change of the code
+# the traffic is null until re-measured.
+TRAFFIC_SOURCE_SHA = "b2f20251040b44a0"
 TRAFFIC_PER_LAUNCH_512 = {}
-TRAFFIC_PER_NODE = {}
+# one launch per kernel of the 8192^2 multi-dendrite workload (D2Q5 phase,
+# U, T; grain angles), single-pass counters (profiles/
+# dram_traffic_multidendrite8192_d2q5_f32_f16.md); equal to the algorithmic
+# bytes within 1 %.  A 2048^2 capture keeps most of a launch's writes in the
+# 126 MB L2 until after the kernel, so it undercounts them.
+TRAFFIC_PER_NODE = {
+    "f32:q5:phase:1016:ori": 52.26, "f32:q5:phase:1032:ori": 52.48, "f32:q5:transfer:1016": 23.84,
+    "f32:q5:scalar_U:1016": 40.06, "f32:q5:scalar_T:1016": 35.99, "f32:q5:flow:1016": 92.71,
+    "f16dev:q5:phase:1016:ori": 36.11, "f16dev:q5:phase:1032:ori": 36.15, "f16dev:q5:transfer:1016": 23.84,
+    "f16dev:q5:scalar_U:1016": 32.02, "f16dev:q5:scalar_T:1016": 28.19, "f16dev:q5:flow:1016": 60.14,
+}
 
 
 def kernel_source_sha():
@@ -571,7 +576,7 @@ def measure_md(args, torch, lbm, local, dev, prec, q, world=1, with_e2e=False):
     key = "%s:q%d:%s:%d%s" % (prec, q, dom, tiles[dom], ":ori" if dom == "phase" else "")
     if TRAFFIC_SOURCE_SHA == kernel_source_sha() and key in TRAFFIC_PER_NODE:
         traffic = TRAFFIC_PER_NODE[key] * nodes
-        traffic_note = "ncu capture of this variant on the 2048^2 lattice, per node x the nodes of one launch"
+        traffic_note = "ncu capture of one launch of this variant on the 8192^2 lattice (single-pass counters)"
     out = {
         "workload": md_label(p, prec), "storage": prec, "nodes": nodes,
         "value": job_throughput(nodes, MD_PERIOD, args.steps, world, ms_max), "unit": UNIT,
