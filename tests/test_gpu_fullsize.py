@@ -9,7 +9,8 @@ chooses):
 * the 64-member ensemble, batched: every member element by element (FP64);
 * 8192^2 multi-dendrite (too large for the oracle as a whole): sampled
   outputs, element by element against the oracle run on windows of the same
-  initial state (exact beyond the method's dependence radius), FP64 and FP32.
+  initial state (exact beyond the method's dependence radius), FP64, FP32
+  and FP16 deviation storage.
 """
 import numpy as np
 import pytest
@@ -111,7 +112,7 @@ def _full_orientation(pts, ang, n):
     return _ORI[n]
 
 
-@pytest.mark.parametrize("prec,tol,q", [("f64", 1e-10, 9), ("f32", 4e-5, 9), ("f32", 4e-5, 5)])
+@pytest.mark.parametrize("prec,tol,q", [("f64", 1e-10, 9), ("f32", 4e-5, 9), ("f32", 4e-5, 5), ("f16dev", 2e-4, 5)])
 def test_multi_dendrite_8192_sampled_windows(prec, tol, q):
     """8192^2 multi-dendrite growth with convection (32 seeds, N = (1, 1, 4,
     2)), too large for the oracle as a whole: seeded through lbm_init_seed,
@@ -123,7 +124,9 @@ def test_multi_dendrite_8192_sampled_windows(prec, tol, q):
     oracle result is the exact full-lattice result beyond that margin.
     FP32 bound: 8 steps x 20 roundings x 2^-22 (the hardware reciprocal) =
     3.8e-5 on values of order one.  q = 5: the same with D2Q5 phase, U and
-    T lattices.  Each seed's grain has its own crystal angle (Voronoi cells
+    T lattices.  FP16 deviation storage (the mixed form the bench measures
+    beside FP32): each store rounds deviations of order 1e-2 by up to
+    2^-11, ~5e-6 a store, two stores a base step over 8 steps, x2.  Each seed's grain has its own crystal angle (Voronoi cells
     of the seeds, angles drawn in [0, pi/2)); the windows carry the same
     angles."""
     from dataclasses import replace
