@@ -386,11 +386,13 @@ inline dim3 grid_of(const SimState& s) { return dim3((s.nx + TX - 1) / TX, (s.ny
 // of height h over the interior with 1-wide strips on the frame (one 1-D
 // launch).  Blocks of one launch over an nx x ny lattice:
 constexpr int VS = 1000;
-inline void blocks_of(int kind, int v, int nx, int ny, int& bx, int& by) {
+// fv: nodes per lane of the flow or phase vector strips (nodes_per_lane_of:
+// 2 for the 16-bit flow and the 16-bit D2Q5 phase, else VW)
+inline void blocks_of(int kind, int v, int nx, int ny, int& bx, int& by, int fv = VW) {
     if (v > VS) {
-        bx = kind == LBM_K_FLOW       ? fvs_blocks(nx, ny, v - VS)
+        bx = kind == LBM_K_FLOW       ? fvs_blocks(nx, ny, v - VS, fv)
              : kind == LBM_K_TRANSFER ? tvs_blocks(nx, ny, v - VS)
-             : kind == LBM_K_PHASE    ? pvs_blocks(nx, ny, v - VS)
+             : kind == LBM_K_PHASE    ? pvs_blocks(nx, ny, v - VS, fv)
                                       : vs_blocks(nx, ny, v - VS);
         by = 1;
     } else if (v > 0) {
@@ -402,10 +404,18 @@ inline void blocks_of(int kind, int v, int nx, int ny, int& bx, int& by) {
         by = (ny - v - 1) / (-v);
     }
 }
-inline dim3 grid_v(const SimState& s, int kind, int v) {
+inline dim3 grid_v(const SimState& s, int kind, int v, int fv = VW) {
     int bx, by;
-    blocks_of(kind, v, s.nx, s.ny, bx, by);
+    blocks_of(kind, v, s.nx, s.ny, bx, by, fv);
     return dim3(bx, by);
+}
+inline int nodes_per_lane_of(int kind, uint32_t precision, int q) {
+    const bool st16 = precision == LBM_PREC_F16_DEV || precision == LBM_PREC_BF16_DEV;
+    if (kind == LBM_K_FLOW) return st16 ? flow_nodes_per_lane<__half>() : flow_nodes_per_lane<float>();
+    if (kind == LBM_K_PHASE)
+        return q == 5 ? (st16 ? phase_nodes_per_lane<5, __half>() : phase_nodes_per_lane<5, float>())
+                      : (st16 ? phase_nodes_per_lane<9, __half>() : phase_nodes_per_lane<9, float>());
+    return VW;
 }
 inline bool has_strips(int kind) { return kind == LBM_K_SCALAR_U || kind == LBM_K_SCALAR_T; }
 inline bool has_vstrips(int kind) {
@@ -462,7 +472,7 @@ inline void launch_ex(lbm_sim* h, void (*kern)(KArgs...), dim3 g, dim3 b, Args..
 template <typename J>
 void push_job(lbm_sim* h, int kind, J& j, const SimState& s) {
     int bx, by;
-    blocks_of(kind, h->batch_tile[kind], s.nx, s.ny, bx, by);
+    blocks_of(kind, h->batch_tile[kind], s.nx, s.ny, bx, by, nodes_per_lane_of(kind, h->precision, h->q));
     j.tiles_x = bx;
     j.tile0 = h->rec_tiles[kind];
     h->rec_tiles[kind] += bx * by;
@@ -538,7 +548,7 @@ void launch_batch(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, 
             break;
         case LBM_K_SCALAR_U:
             if (tysel > VS)
-                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs_batch<R, ST, DEV, HV, 0, Q>, g, dim3(32 * VNW),
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, scalar_vs_batch_kernel<R, ST, DEV, HV, 0, Q>(), g, dim3(32 * VNW),
                                                      (size_t)VNW * VSRing<R>::BYTES, (const ScalarJob<R, ST>*)jobs,
                                                      njobs)))
             else if (tysel < 0)
@@ -550,7 +560,7 @@ void launch_batch(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, 
             break;
         case LBM_K_SCALAR_T:
             if (tysel > VS)
-                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs_batch<R, ST, DEV, HV, 1, Q>, g, dim3(32 * VNW),
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, scalar_vs_batch_kernel<R, ST, DEV, HV, 1, Q>(), g, dim3(32 * VNW),
                                                      (size_t)VNW * VSRing<R>::BYTES, (const ScalarJob<R, ST>*)jobs,
                                                      njobs)))
             else if (tysel < 0)
@@ -609,7 +619,8 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
     switch (kind) {
         case LBM_K_PHASE:
             if (tysel > VS)
-                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, phase_vs_kernel<R, ST, DEV, HV, Q>(), grid_v(s, kind, tysel),
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, phase_vs_kernel<R, ST, DEV, HV, Q>(),
+                    grid_v(s, kind, tysel, phase_nodes_per_lane<Q, ST>()),
                     dim3(32, PVW), (size_t)PVSmem<R, Q, ST>::BYTES, P, (const ST*)s.pops[FP][s.cur_pop[FP]],
                     (ST*)s.pops[FP][1 - s.cur_pop[FP]], phi_now, (R*)s.phi[1 - s.cur_phi],
                     s.has_U ? (const R*)s.U[s.cur_U] : null_r, s.has_T ? (const R*)s.T[s.cur_T] : null_r, clock, off)))
@@ -645,11 +656,11 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
             if (tysel > VS) {
                 const size_t sm = (size_t)VNW * VSRing<R>::BYTES;
                 if (isU)
-                    LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs<R, ST, DEV, HV, 0, Q>, grid_v(s, kind, tysel),
+                    LBM_VS_SWITCH(tysel, (launch_ex_smem(h, scalar_vs_kernel<R, ST, DEV, HV, 0, Q>(), grid_v(s, kind, tysel),
                         dim3(32 * VNW), sm, P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc,
                         s.smax)))
                 else
-                    LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_scalar_vs<R, ST, DEV, HV, 1, Q>, grid_v(s, kind, tysel),
+                    LBM_VS_SWITCH(tysel, (launch_ex_smem(h, scalar_vs_kernel<R, ST, DEV, HV, 1, Q>(), grid_v(s, kind, tysel),
                         dim3(32 * VNW), sm, P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc,
                         s.smax)))
             } else if (tysel < 0) {
@@ -673,7 +684,8 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
         case LBM_K_FLOW: {
             const int c = s.cur_pop[FF];
             if (tysel > VS)
-                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, flow_vs_kernel<R, ST, DEV, HV>(), grid_v(s, kind, tysel),
+                LBM_VS_SWITCH(tysel, (launch_ex_smem(h, flow_vs_kernel<R, ST, DEV, HV>(),
+                    grid_v(s, kind, tysel, flow_nodes_per_lane<ST>()),
                     dim3(32, FVW), (size_t)FVSmem<R, ST>::BYTES, P, (const ST*)s.pops[FF][c], (ST*)s.pops[FF][1 - c],
                     phi_now, (const R*)s.ux[c], (const R*)s.uy[c], (const R*)s.rho[c], (R*)s.ux[1 - c],
                     (R*)s.uy[1 - c], (R*)s.rho[1 - c])))

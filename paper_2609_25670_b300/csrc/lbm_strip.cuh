@@ -329,12 +329,15 @@ struct VGeo {
     int nxv, nyv;                  // vector strips across / down
     Rect in;                       // the interior they cover
 };
-__host__ __device__ inline VGeo vgeo(int nx, int ny, int H) {
+// V: nodes per lane (VW for every strip but the 16-bit flow strip, which
+// takes two): strip s covers columns 30 V s .. 30 V s + 32 V - 1 and writes
+// the middle 30 V of them
+__host__ __device__ inline VGeo vgeo(int nx, int ny, int H, int V = VW) {
     VGeo g;
-    g.nxv = nx >= 32 * VW ? (nx - 32 * VW) / VSW + 1 : 0;          // columns 120 s .. 120 s + 127 inside
+    g.nxv = nx >= 32 * V ? (nx - 32 * V) / (30 * V) + 1 : 0;        // columns 120 s .. 120 s + 127 inside (V = 4)
     g.nyv = ny - 4 - H >= 0 ? (ny - 4 - H) / H + 1 : 0;            // rows y0 - 2 .. y0 + H + 1 inside
     if (!g.nxv || !g.nyv) g.nxv = g.nyv = 0;
-    g.in = Rect{VX0, VX0 + VSW * g.nxv, VY0, VY0 + H * g.nyv};
+    g.in = Rect{V, V + 30 * V * g.nxv, VY0, VY0 + H * g.nyv};
     return g;
 }
 
@@ -370,50 +373,57 @@ __host__ __device__ inline Frame frame_of(const Rect& in, int nx, int ny, int uw
     return f;
 }
 
-template <typename T> struct alignas(sizeof(T) * VW) Vec4 { T v[VW]; };
+template <typename T, int N> struct alignas(sizeof(T) * N) VecN { T v[N]; };
+template <typename T> using Vec4 = VecN<T, VW>;
 
-// a lane's four stored values to and from the arithmetic type; 16-bit
-// types convert two at a time (one paired conversion instruction each)
-template <typename ST, typename R> __device__ __forceinline__ Vec4<ST> pack4(const R* v) {
-    Vec4<ST> o;
+// a lane's N stored values to and from the arithmetic type; 16-bit types
+// convert two at a time (one paired conversion instruction each)
+template <typename ST, typename R, int N = VW> __device__ __forceinline__ VecN<ST, N> pack4(const R* v) {
+    VecN<ST, N> o;
     if constexpr (std::is_same<ST, __half>::value) {
         __half2* h = reinterpret_cast<__half2*>(o.v);
-        h[0] = __floats2half2_rn((float)v[0], (float)v[1]);
-        h[1] = __floats2half2_rn((float)v[2], (float)v[3]);
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) h[k] = __floats2half2_rn((float)v[2 * k], (float)v[2 * k + 1]);
     } else if constexpr (std::is_same<ST, __nv_bfloat16>::value) {
         __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(o.v);
-        h[0] = __floats2bfloat162_rn((float)v[0], (float)v[1]);
-        h[1] = __floats2bfloat162_rn((float)v[2], (float)v[3]);
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) h[k] = __floats2bfloat162_rn((float)v[2 * k], (float)v[2 * k + 1]);
     } else {
 #pragma unroll
-        for (int k = 0; k < VW; ++k) o.v[k] = Cvt<ST>::st(v[k]);
+        for (int k = 0; k < N; ++k) o.v[k] = Cvt<ST>::st(v[k]);
     }
     return o;
 }
-template <typename ST, typename R> __device__ __forceinline__ void unpack4(const Vec4<ST>& in, R* v) {
+template <typename ST, typename R, int N = VW> __device__ __forceinline__ void unpack4(const VecN<ST, N>& in, R* v) {
     if constexpr (std::is_same<ST, __half>::value) {
         const __half2* h = reinterpret_cast<const __half2*>(in.v);
-        const float2 a = __half22float2(h[0]), b = __half22float2(h[1]);
-        v[0] = (R)a.x; v[1] = (R)a.y; v[2] = (R)b.x; v[3] = (R)b.y;
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) {
+            const float2 a = __half22float2(h[k]);
+            v[2 * k] = (R)a.x; v[2 * k + 1] = (R)a.y;
+        }
     } else if constexpr (std::is_same<ST, __nv_bfloat16>::value) {
         const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(in.v);
-        const float2 a = __bfloat1622float2(h[0]), b = __bfloat1622float2(h[1]);
-        v[0] = (R)a.x; v[1] = (R)a.y; v[2] = (R)b.x; v[3] = (R)b.y;
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) {
+            const float2 a = __bfloat1622float2(h[k]);
+            v[2 * k] = (R)a.x; v[2 * k + 1] = (R)a.y;
+        }
     } else {
 #pragma unroll
-        for (int k = 0; k < VW; ++k) v[k] = (R)Cvt<ST>::ld(in.v[k]);
+        for (int k = 0; k < N; ++k) v[k] = (R)Cvt<ST>::ld(in.v[k]);
     }
 }
 
-// asynchronous copy of one lane's vector (VW elements of T) into shared memory
-template <typename T>
+// asynchronous copy of one lane's vector (N elements of T) into shared memory
+template <typename T, int N = VW>
 __device__ __forceinline__ void fetch_vec(unsigned char* dst, const T* src) {
-    constexpr int B = (int)sizeof(T) * VW, C = B < 16 ? B : 16;
+    constexpr int B = (int)sizeof(T) * N, C = B < 16 ? B : 16;
 #pragma unroll
     for (int o = 0; o < B; o += C) __pipeline_memcpy_async(dst + o, (const unsigned char*)src + o, C);
 }
-template <typename T> __device__ __forceinline__ Vec4<T> sread(const unsigned char* p) {
-    return *reinterpret_cast<const Vec4<T>*>(p);
+template <typename T, int N = VW> __device__ __forceinline__ VecN<T, N> sread(const unsigned char* p) {
+    return *reinterpret_cast<const VecN<T, N>*>(p);
 }
 
 enum { VA_JX = 0, VA_JY = 1, VA_CHI = 2, VA_ACC = 3, VA_VX = 4, VA_VY = 5, VA_PHI = 6, VA_LO = 7, VA_N = 8 };
@@ -646,10 +656,19 @@ __device__ __forceinline__ void scalar_vs_block(const KP<R>& P, const ST* fin, S
 // ---------------------------------------------------------------------------
 enum { FA_RHO = 8, FA_UX = 9, FA_UY = 10, FA_PHI = 11, FA_N = 12 };
 // flow strips: 8 populations, rho, u, phi.  With 16-bit populations the
-// strip is bound by its instructions, not by DRAM: a ring of three rows lets
-// three blocks (12 warps) share an SM instead of two
-template <typename R, typename ST>
-using FRing = VRingN<R, FA_N, sizeof(ST) == 2 ? 3 : 0>;
+// strip is bound by its instructions and its live state (the nine
+// post-collision values of a row and the source values of two rows, per
+// node), not by DRAM: it takes two nodes per lane instead of four, which
+// halves that state per thread and lets more warps share an SM, and a ring
+// of three rows
+template <typename ST> constexpr int flow_nodes_per_lane() { return sizeof(ST) == 2 ? 2 : VW; }
+template <typename R, typename ST> struct FRing {
+    static constexpr int V = flow_nodes_per_lane<ST>();
+    static constexpr int EB = V * (int)sizeof(R);            // bytes of one lane's entry
+    static constexpr int SLOT = FA_N * 32 * EB;              // one row
+    static constexpr int D = sizeof(ST) == 2 ? 3 : sizeof(R) == 8 ? 2 : 4;
+    static constexpr int BYTES = D * SLOT;
+};
 
 template <typename R, typename ST, bool DEV, int H, bool UP>
 __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict__ fin, ST* __restrict__ fout,
@@ -658,6 +677,7 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
                                             R* __restrict__ ux_out, R* __restrict__ uy_out, R* __restrict__ rho_out,
                                             int s, int y0, unsigned char* __restrict__ ring) {
     using RG = FRing<R, ST>;
+    constexpr int V = RG::V;                   // nodes per lane
     constexpr int EB = RG::EB, NR = H + 2, D = RG::D, DIR = UP ? -1 : 1;
     // directions whose source lies in the row behind the walk (far) and in
     // the row just collided (near): axis, from the left (e_x = +1), from the right
@@ -665,18 +685,18 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
     constexpr int NAX = UP ? 2 : 4, NL = UP ? 5 : 8, NRt = UP ? 6 : 7;
     const int lane = threadIdx.x & 31, pl = (int)P.plane, pitch = P.pitch;
     const R c = P.cF, dt = P.dtF;
-    const int c0 = VSW * s + VW * lane;
+    const int c0 = 30 * V * s + V * lane;
     const bool outl = lane >= 1 && lane <= 30;
     const int rfirst = UP ? y0 + H : y0 - 1;
     unsigned char* const mine = ring + lane * EB;
     auto fetch_row = [&](int r, unsigned char* slot) {
         const int base = r * pitch + c0;
 #pragma unroll
-        for (int i = 1; i < 9; ++i) fetch_vec<ST>(slot + (i - 1) * 32 * EB, fin + (size_t)(i - 1) * pl + base);
-        fetch_vec<R>(slot + FA_RHO * 32 * EB, rho_in + base);
-        fetch_vec<R>(slot + FA_UX * 32 * EB, ux_in + base);
-        fetch_vec<R>(slot + FA_UY * 32 * EB, uy_in + base);
-        fetch_vec<R>(slot + FA_PHI * 32 * EB, phi + base);
+        for (int i = 1; i < 9; ++i) fetch_vec<ST, V>(slot + (i - 1) * 32 * EB, fin + (size_t)(i - 1) * pl + base);
+        fetch_vec<R, V>(slot + FA_RHO * 32 * EB, rho_in + base);
+        fetch_vec<R, V>(slot + FA_UX * 32 * EB, ux_in + base);
+        fetch_vec<R, V>(slot + FA_UY * 32 * EB, uy_in + base);
+        fetch_vec<R, V>(slot + FA_PHI * 32 * EB, phi + base);
     };
 #pragma unroll
     for (int d = 0; d < D - 1; ++d) {
@@ -685,11 +705,11 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
     }
     // row y (the next to complete): own post o, f_L own / left / right, the
     // shifted post values of directions 1, 3 and of the far pair
-    R o[9][VW], fy[VW], fyl[VW], fyr[VW], q1[VW], q3[VW], qa[VW], qb[VW];
+    R o[9][V], fy[V], fyl[V], fyr[V], q1[V], q3[V], qa[V], qb[V];
     // far row: axis post, shifted pair, f_L own / left / right
-    R zx[VW], zl[VW], zr[VW], zf[VW], zfl[VW], zfr[VW];
+    R zx[V], zl[V], zr[V], zf[V], zfl[V], zfr[V];
 #pragma unroll
-    for (int k = 0; k < VW; ++k) {
+    for (int k = 0; k < V; ++k) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) o[i][k] = R(0);
         fy[k] = fyl[k] = fyr[k] = q1[k] = q3[k] = qa[k] = qb[k] = R(0);
@@ -702,13 +722,13 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
         __pipeline_commit();
         __pipeline_wait_prior(D - 1);
         const unsigned char* sl = mine + (it % D) * RG::SLOT;
-        const Vec4<R> rho = sread<R>(sl + FA_RHO * 32 * EB), vx = sread<R>(sl + FA_UX * 32 * EB);
-        const Vec4<R> vy = sread<R>(sl + FA_UY * 32 * EB), ph = sread<R>(sl + FA_PHI * 32 * EB);
-        R p[VW][9], fl[VW], fr[9][VW];
+        const VecN<R, V> rho = sread<R, V>(sl + FA_RHO * 32 * EB), vx = sread<R, V>(sl + FA_UX * 32 * EB);
+        const VecN<R, V> vy = sread<R, V>(sl + FA_UY * 32 * EB), ph = sread<R, V>(sl + FA_PHI * 32 * EB);
+        R p[V][9], fl[V], fr[9][V];
 #pragma unroll
-        for (int i = 1; i < 9; ++i) unpack4<ST, R>(sread<ST>(sl + (i - 1) * 32 * EB), fr[i]);
+        for (int i = 1; i < 9; ++i) unpack4<ST, R, V>(sread<ST, V>(sl + (i - 1) * 32 * EB), fr[i]);
 #pragma unroll
-        for (int k = 0; k < VW; ++k) {
+        for (int k = 0; k < V; ++k) {
             R f[9];
 #pragma unroll
             for (int i = 1; i < 9; ++i) f[i] = fr[i][k];
@@ -719,23 +739,23 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
             fl[k] = R(0.5) * (R(1) - ph.v[k]);                                       // f_L = (1 - phi)/2
         }
         // x-shifts of the post values and of f_L
-        R s1[VW], s5[VW], s8[VW], s3[VW], s6[VW], s7[VW], fll[VW], flr[VW];
-        s1[0] = from_left(p[VW - 1][1]); s5[0] = from_left(p[VW - 1][5]); s8[0] = from_left(p[VW - 1][8]);
-        fll[0] = from_left(fl[VW - 1]);
-        s3[VW - 1] = from_right(p[0][3]); s6[VW - 1] = from_right(p[0][6]); s7[VW - 1] = from_right(p[0][7]);
-        flr[VW - 1] = from_right(fl[0]);
+        R s1[V], s5[V], s8[V], s3[V], s6[V], s7[V], fll[V], flr[V];
+        s1[0] = from_left(p[V - 1][1]); s5[0] = from_left(p[V - 1][5]); s8[0] = from_left(p[V - 1][8]);
+        fll[0] = from_left(fl[V - 1]);
+        s3[V - 1] = from_right(p[0][3]); s6[V - 1] = from_right(p[0][6]); s7[V - 1] = from_right(p[0][7]);
+        flr[V - 1] = from_right(fl[0]);
 #pragma unroll
-        for (int k = 1; k < VW; ++k) { s1[k] = p[k - 1][1]; s5[k] = p[k - 1][5]; s8[k] = p[k - 1][8]; fll[k] = fl[k - 1]; }
+        for (int k = 1; k < V; ++k) { s1[k] = p[k - 1][1]; s5[k] = p[k - 1][5]; s8[k] = p[k - 1][8]; fll[k] = fl[k - 1]; }
 #pragma unroll
-        for (int k = 0; k < VW - 1; ++k) { s3[k] = p[k + 1][3]; s6[k] = p[k + 1][6]; s7[k] = p[k + 1][7]; flr[k] = fl[k + 1]; }
-        R(&sNL)[VW] = UP ? s5 : s8;            // near pair, shifted
-        R(&sNR)[VW] = UP ? s6 : s7;
+        for (int k = 0; k < V - 1; ++k) { s3[k] = p[k + 1][3]; s6[k] = p[k + 1][6]; s7[k] = p[k + 1][7]; flr[k] = fl[k + 1]; }
+        R(&sNL)[V] = UP ? s5 : s8;            // near pair, shifted
+        R(&sNR)[V] = UP ? s6 : s7;
         if (it >= 2 && outl) {                 // complete row r - DIR
             const int node = (r - DIR) * pitch + c0;
-            Vec4<R> vrho, vux, vuy;
-            R fn[9][VW];
+            VecN<R, V> vrho, vux, vuy;
+            R fn[9][V];
 #pragma unroll
-            for (int k = 0; k < VW; ++k) {
+            for (int k = 0; k < V; ++k) {
                 const R f0 = fy[k];
                 auto pull = [&](int i, R src, R fls) -> R {
                     const R fLm = R(0.5) * (fls + f0);
@@ -762,20 +782,20 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
                 vux.v[k] = (c * jx + R(0.5) * dt * P.Fbx) * irho;                   // Eq. 27
                 vuy.v[k] = (c * jy + R(0.5) * dt * P.Fby) * irho;
             }
-            *reinterpret_cast<Vec4<R>*>(rho_out + node) = vrho;
-            *reinterpret_cast<Vec4<R>*>(ux_out + node) = vux;
-            *reinterpret_cast<Vec4<R>*>(uy_out + node) = vuy;
+            *reinterpret_cast<VecN<R, V>*>(rho_out + node) = vrho;
+            *reinterpret_cast<VecN<R, V>*>(ux_out + node) = vux;
+            *reinterpret_cast<VecN<R, V>*>(uy_out + node) = vuy;
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
-                R ev[VW];
+                R ev[V];
 #pragma unroll
-                for (int k = 0; k < VW; ++k) ev[k] = DEV ? fn[i][k] - wq<R>(i) * vrho.v[k] : fn[i][k];
-                *reinterpret_cast<Vec4<ST>*>(fout + (size_t)(i - 1) * pl + node) = pack4<ST, R>(ev);
+                for (int k = 0; k < V; ++k) ev[k] = DEV ? fn[i][k] - wq<R>(i) * vrho.v[k] : fn[i][k];
+                *reinterpret_cast<VecN<ST, V>*>(fout + (size_t)(i - 1) * pl + node) = pack4<ST, R, V>(ev);
             }
         }
         // roll: row y becomes the far row, row r becomes row y
 #pragma unroll
-        for (int k = 0; k < VW; ++k) {
+        for (int k = 0; k < V; ++k) {
             zx[k] = o[FAX][k]; zl[k] = qa[k]; zr[k] = qb[k]; zf[k] = fy[k]; zfl[k] = fyl[k]; zfr[k] = fyr[k];
 #pragma unroll
             for (int i = 0; i < 9; ++i) o[i][k] = p[k][i];
@@ -798,8 +818,9 @@ template <typename R, typename ST> struct FVSmem {
     static constexpr int BYTES = STRIPS > TILE ? STRIPS : TILE;
 };
 __host__ __device__ inline int fvs_vector_blocks(const VGeo& g) { return (g.nxv * g.nyv + FVW - 1) / FVW; }
-__host__ __device__ inline int fvs_blocks(int nx, int ny, int H) {
-    const VGeo g = vgeo(nx, ny, H);
+// blocks of one flow vector launch; V: nodes per lane of its strips
+__host__ __device__ inline int fvs_blocks(int nx, int ny, int H, int V = VW) {
+    const VGeo g = vgeo(nx, ny, H, V);
     return fvs_vector_blocks(g) + frame_of(g.in, nx, ny, 32, FVW).count();
 }
 
@@ -808,7 +829,7 @@ __device__ __forceinline__ void flow_vs_block(const KP<R>& P, const ST* fin, ST*
                                               const R* uy_in, const R* rho_in, R* ux_out, R* uy_out, R* rho_out,
                                               int b) {
     extern __shared__ __align__(128) unsigned char fsm[];   // FVSmem<R, ST>::BYTES, dynamic
-    const VGeo g = vgeo(P.nx, P.ny, H);
+    const VGeo g = vgeo(P.nx, P.ny, H, flow_nodes_per_lane<ST>());
     const int nvb = fvs_vector_blocks(g);
     if (b < nvb) {
         const int w = threadIdx.y;
@@ -1059,10 +1080,18 @@ __device__ __forceinline__ void transfer_vs_block(const KP<R>& P, const R* phio,
 template <int Q> struct PA {
     static constexpr int PHI = Q - 1, U = Q, T = Q + 1, ORI = Q + 2, N = Q + 3;
 };
-// a ring of three rows for 16-bit D2Q5 populations (instruction-bound like
-// the 16-bit flow strip): four blocks (16 warps) per SM instead of three
-template <typename R, int Q = 9, typename ST = R>
-using PRing = VRingN<R, PA<Q>::N, (sizeof(ST) == 2 && Q == 5) ? 3 : 0>;
+// 16-bit D2Q5 populations: the strip is bound by its instructions and its
+// live state (the row's own pre-collision populations, a_s^2 and the source
+// values of two rows, per node), like the 16-bit flow strip; it takes two
+// nodes per lane instead of four and a ring of three rows
+template <int Q, typename ST> constexpr int phase_nodes_per_lane() { return (sizeof(ST) == 2 && Q == 5) ? 2 : VW; }
+template <typename R, int Q = 9, typename ST = R> struct PRing {
+    static constexpr int V = phase_nodes_per_lane<Q, ST>();
+    static constexpr int EB = V * (int)sizeof(R);            // bytes of one lane's entry
+    static constexpr int SLOT = PA<Q>::N * 32 * EB;          // one row
+    static constexpr int D = (sizeof(ST) == 2 && Q == 5) ? 3 : sizeof(R) == 8 ? 2 : 4;
+    static constexpr int BYTES = D * SLOT;
+};
 
 template <typename R, typename ST, bool DEV, int H, bool UP, int Q>
 __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restrict__ fin, ST* __restrict__ fout,
@@ -1070,36 +1099,37 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
                                              const R* __restrict__ Um, const R* __restrict__ Tm, R tnow, int s,
                                              int y0, unsigned char* __restrict__ ring) {
     using RG = PRing<R, Q, ST>;
+    constexpr int V = RG::V;                   // nodes per lane
     constexpr int PA_PHI = PA<Q>::PHI, PA_U = PA<Q>::U, PA_T = PA<Q>::T, PA_ORI = PA<Q>::ORI;
     constexpr int EB = RG::EB, NR = H + 2, D = RG::D, DIR = UP ? -1 : 1;
     constexpr int FAX = UP ? 4 : 2, FL = UP ? 8 : 5, FR = UP ? 7 : 6;     // far row: axis, from left, from right
     constexpr int NAX = UP ? 2 : 4, NL = UP ? 5 : 8, NRt = UP ? 6 : 7;    // near row (just collided)
     const int lane = threadIdx.x & 31, pl = (int)P.plane, pitch = P.pitch;
-    const int c0 = VSW * s + VW * lane;
+    const int c0 = 30 * V * s + V * lane;
     const bool outl = lane >= 1 && lane <= 30;
     const int rfirst = UP ? y0 + H : y0 - 1;
     unsigned char* const mine = ring + lane * EB;
     auto fetch_row = [&](int r, unsigned char* slot) {      // populations, U, T of row r; phi of row r + DIR
         const int base = r * pitch + c0;
 #pragma unroll
-        for (int i = 1; i < Q; ++i) fetch_vec<ST>(slot + (i - 1) * 32 * EB, fin + (size_t)(i - 1) * pl + base);
-        fetch_vec<R>(slot + PA_PHI * 32 * EB, phi + base + DIR * pitch);
-        if (P.has_U) fetch_vec<R>(slot + PA_U * 32 * EB, Um + base);
-        if (P.has_T) fetch_vec<R>(slot + PA_T * 32 * EB, Tm + base);
-        if (P.ori) fetch_vec<R>(slot + PA_ORI * 32 * EB, P.ori + base);
+        for (int i = 1; i < Q; ++i) fetch_vec<ST, V>(slot + (i - 1) * 32 * EB, fin + (size_t)(i - 1) * pl + base);
+        fetch_vec<R, V>(slot + PA_PHI * 32 * EB, phi + base + DIR * pitch);
+        if (P.has_U) fetch_vec<R, V>(slot + PA_U * 32 * EB, Um + base);
+        if (P.has_T) fetch_vec<R, V>(slot + PA_T * 32 * EB, Tm + base);
+        if (P.ori) fetch_vec<R, V>(slot + PA_ORI * 32 * EB, P.ori + base);
     };
 #pragma unroll
     for (int d = 0; d < D - 1; ++d) {
         fetch_row(rfirst + DIR * d, mine + d * RG::SLOT);
         __pipeline_commit();
     }
-    Vec4<R> pb = *reinterpret_cast<const Vec4<R>*>(phi + (rfirst - DIR) * pitch + c0);
-    Vec4<R> p0 = *reinterpret_cast<const Vec4<R>*>(phi + rfirst * pitch + c0);
+    VecN<R, V> pb = *reinterpret_cast<const VecN<R, V>*>(phi + (rfirst - DIR) * pitch + c0);
+    VecN<R, V> p0 = *reinterpret_cast<const VecN<R, V>*>(phi + rfirst * pitch + c0);
     // row y: own loaded populations (raw), phi, a_s^2, post values q0, q1s,
     // q3s and its far triple; far row: za, zb, zc
-    R fy[9][VW], cy[VW], ay[VW], q0[VW], q1[VW], q3[VW], qa[VW], qb[VW], qc[VW], za[VW], zb[VW], zc[VW];
+    R fy[9][V], cy[V], ay[V], q0[V], q1[V], q3[V], qa[V], qb[V], qc[V], za[V], zb[V], zc[V];
 #pragma unroll
-    for (int k = 0; k < VW; ++k) {
+    for (int k = 0; k < V; ++k) {
 #pragma unroll
         for (int i = 1; i < 9; ++i) fy[i][k] = R(0);
         cy[k] = R(0); ay[k] = R(1);
@@ -1112,34 +1142,34 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
         __pipeline_commit();
         __pipeline_wait_prior(D - 1);
         const unsigned char* sl = mine + (it % D) * RG::SLOT;
-        R f[9][VW];
+        R f[9][V];
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             if (i >= Q) {                          // D2Q5: no diagonal populations
 #pragma unroll
-                for (int k = 0; k < VW; ++k) f[i][k] = R(0);
+                for (int k = 0; k < V; ++k) f[i][k] = R(0);
                 continue;
             }
-            unpack4<ST, R>(sread<ST>(sl + (i - 1) * 32 * EB), f[i]);
+            unpack4<ST, R, V>(sread<ST, V>(sl + (i - 1) * 32 * EB), f[i]);
         }
-        const Vec4<R> pf = sread<R>(sl + PA_PHI * 32 * EB);
-        Vec4<R> Us{}, Tv{}, Ov{};
-        if (P.has_U) Us = sread<R>(sl + PA_U * 32 * EB);
-        if (P.has_T) Tv = sread<R>(sl + PA_T * 32 * EB);
-        if (P.ori) Ov = sread<R>(sl + PA_ORI * 32 * EB);
-        const Vec4<R>& pm = UP ? pf : pb;
-        const Vec4<R>& pp = UP ? pb : pf;
-        R A[VW + 2], B[VW + 2];
+        const VecN<R, V> pf = sread<R, V>(sl + PA_PHI * 32 * EB);
+        VecN<R, V> Us{}, Tv{}, Ov{};
+        if (P.has_U) Us = sread<R, V>(sl + PA_U * 32 * EB);
+        if (P.has_T) Tv = sread<R, V>(sl + PA_T * 32 * EB);
+        if (P.ori) Ov = sread<R, V>(sl + PA_ORI * 32 * EB);
+        const VecN<R, V>& pm = UP ? pf : pb;
+        const VecN<R, V>& pp = UP ? pb : pf;
+        R A[V + 2], B[V + 2];
 #pragma unroll
-        for (int k = 0; k < VW; ++k) {
+        for (int k = 0; k < V; ++k) {
             A[k + 1] = p0.v[k] * (R(1) / R(3)) + (pm.v[k] + pp.v[k]) * (R(1) / R(12));
             B[k + 1] = pp.v[k] - pm.v[k];
         }
-        A[0] = from_left(A[VW]); B[0] = from_left(B[VW]);
-        A[VW + 1] = from_right(A[1]); B[VW + 1] = from_right(B[1]);
-        R p[VW][9], a2[VW];
+        A[0] = from_left(A[V]); B[0] = from_left(B[V]);
+        A[V + 1] = from_right(A[1]); B[V + 1] = from_right(B[1]);
+        R p[V][9], a2[V];
 #pragma unroll
-        for (int k = 0; k < VW; ++k) {
+        for (int k = 0; k < V; ++k) {
             const R gxv = A[k + 2] - A[k], gyv = B[k + 1] * (R(1) / R(3)) + (B[k] + B[k + 2]) * (R(1) / R(12));
             const R c = p0.v[k];
             R as, Nx, Ny;
@@ -1159,21 +1189,21 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
             const R jy = f[2][k] - f[4][k] + f[5][k] + f[6][k] - f[7][k] - f[8][k];
             scalar_post9<R, Q>(c + P.dtp * Qs * P.inv_tau0, bx, by, k6 * (jx - bx), k6 * (jy - by), p[k]);
         }
-        R s1[VW], s5[VW], s8[VW], s3[VW], s6[VW], s7[VW];
-        s1[0] = from_left(p[VW - 1][1]); s5[0] = diag_from_left<Q>(p[VW - 1][5]); s8[0] = diag_from_left<Q>(p[VW - 1][8]);
-        s3[VW - 1] = from_right(p[0][3]); s6[VW - 1] = diag_from_right<Q>(p[0][6]); s7[VW - 1] = diag_from_right<Q>(p[0][7]);
+        R s1[V], s5[V], s8[V], s3[V], s6[V], s7[V];
+        s1[0] = from_left(p[V - 1][1]); s5[0] = diag_from_left<Q>(p[V - 1][5]); s8[0] = diag_from_left<Q>(p[V - 1][8]);
+        s3[V - 1] = from_right(p[0][3]); s6[V - 1] = diag_from_right<Q>(p[0][6]); s7[V - 1] = diag_from_right<Q>(p[0][7]);
 #pragma unroll
-        for (int k = 1; k < VW; ++k) { s1[k] = p[k - 1][1]; s5[k] = p[k - 1][5]; s8[k] = p[k - 1][8]; }
+        for (int k = 1; k < V; ++k) { s1[k] = p[k - 1][1]; s5[k] = p[k - 1][5]; s8[k] = p[k - 1][8]; }
 #pragma unroll
-        for (int k = 0; k < VW - 1; ++k) { s3[k] = p[k + 1][3]; s6[k] = p[k + 1][6]; s7[k] = p[k + 1][7]; }
-        R(&sNL)[VW] = UP ? s5 : s8;
-        R(&sNR)[VW] = UP ? s6 : s7;
+        for (int k = 0; k < V - 1; ++k) { s3[k] = p[k + 1][3]; s6[k] = p[k + 1][6]; s7[k] = p[k + 1][7]; }
+        R(&sNL)[V] = UP ? s5 : s8;
+        R(&sNR)[V] = UP ? s6 : s7;
         if (it >= 2 && outl) {                     // complete row y = r - DIR (Eq. 26, Eq. 18)
             const int node = (r - DIR) * pitch + c0;
-            Vec4<R> sum;
-            R fn[9][VW];
+            VecN<R, V> sum;
+            R fn[9][V];
 #pragma unroll
-            for (int k = 0; k < VW; ++k) {
+            for (int k = 0; k < V; ++k) {
                 const R c = cy[k];
                 R fa[9], s8v = R(0);
 #pragma unroll
@@ -1196,18 +1226,18 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
                 }
                 sum.v[k] = t;
             }
-            *reinterpret_cast<Vec4<R>*>(phin + node) = sum;
+            *reinterpret_cast<VecN<R, V>*>(phin + node) = sum;
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
-                R ev[VW];
+                R ev[V];
 #pragma unroll
-                for (int k = 0; k < VW; ++k) ev[k] = DEV ? fn[i][k] - wqq<R, Q>(i) * sum.v[k] : fn[i][k];
-                const Vec4<ST> o = pack4<ST, R>(ev);
-                *reinterpret_cast<Vec4<ST>*>(fout + (size_t)(i - 1) * pl + node) = o;
+                for (int k = 0; k < V; ++k) ev[k] = DEV ? fn[i][k] - wqq<R, Q>(i) * sum.v[k] : fn[i][k];
+                const VecN<ST, V> o = pack4<ST, R, V>(ev);
+                *reinterpret_cast<VecN<ST, V>*>(fout + (size_t)(i - 1) * pl + node) = o;
             }
         }
 #pragma unroll
-        for (int k = 0; k < VW; ++k) {
+        for (int k = 0; k < V; ++k) {
             za[k] = qa[k]; zb[k] = qb[k]; zc[k] = qc[k];
             q0[k] = p[k][0]; q1[k] = s1[k]; q3[k] = s3[k];
             qa[k] = p[k][FAX]; qb[k] = UP ? s8[k] : s5[k]; qc[k] = UP ? s7[k] : s6[k];
@@ -1227,8 +1257,8 @@ template <typename R, int Q = 9, typename ST = R> struct PVSmem {
     static constexpr int TILE = (int)sizeof(PhaseSmem<R, PVW, Q>);
     static constexpr int BYTES = STRIPS > TILE ? STRIPS : TILE;
 };
-__host__ __device__ inline int pvs_blocks(int nx, int ny, int H) {
-    const VGeo g = vgeo(nx, ny, H);
+__host__ __device__ inline int pvs_blocks(int nx, int ny, int H, int V = VW) {
+    const VGeo g = vgeo(nx, ny, H, V);
     return (g.nxv * g.nyv + PVW - 1) / PVW + frame_of(g.in, nx, ny, 32, PVW).count();
 }
 
@@ -1237,7 +1267,7 @@ __device__ __forceinline__ void phase_vs_block(const KP<R>& P, const ST* fin, ST
                                                const R* Um, const R* Tm, const long long* clock, long long off,
                                                int b) {
     extern __shared__ __align__(128) unsigned char psm[];   // PVSmem<R, Q, ST>::BYTES, dynamic
-    const VGeo g = vgeo(P.nx, P.ny, H);
+    const VGeo g = vgeo(P.nx, P.ny, H, phase_nodes_per_lane<Q, ST>());
     const int nvb = (g.nxv * g.nyv + PVW - 1) / PVW;
     if (b < nvb) {
         const int w = threadIdx.y;
@@ -1304,12 +1334,41 @@ k_scalar_vs(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restr
             unsigned long long* __restrict__ smax) {
     scalar_vs_block<R, ST, DEV, H, FIELD, Q>(*P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, blockIdx.x);
 }
+// The same with 16-bit storage, compiled for six blocks per SM (the
+// shared-memory limit of the ring).  Without a stated minimum the register
+// allocator kept the 16-bit D2Q5 T strip at 96 registers with spills inside
+// its row loop; with it, the strip takes the registers it needs.
+template <typename R, typename ST, bool DEV, int H, int FIELD, int Q>
+__global__ void __launch_bounds__(32 * VNW, 6)
+k_scalar_vs16(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout,
+              const R* __restrict__ mac_in, R* __restrict__ mac_out, const R* __restrict__ acc,
+              const R* __restrict__ phi, const R* __restrict__ ux, const R* __restrict__ uy,
+              unsigned long long* __restrict__ smax) {
+    scalar_vs_block<R, ST, DEV, H, FIELD, Q>(*P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, blockIdx.x);
+}
+template <typename R, typename ST, bool DEV, int H, int FIELD, int Q>
+constexpr auto scalar_vs_kernel() {
+    if constexpr (sizeof(ST) == 2) return &k_scalar_vs16<R, ST, DEV, H, FIELD, Q>;
+    else return &k_scalar_vs<R, ST, DEV, H, FIELD, Q>;
+}
 template <typename R, typename ST, bool DEV, int H, int FIELD, int Q>
 __global__ void __launch_bounds__(32 * VNW) k_scalar_vs_batch(const ScalarJob<R, ST>* __restrict__ jobs, int njobs) {
     int bx, by;
     const ScalarJob<R, ST>& j = job_block(jobs, njobs, blockIdx.x, bx, by);
     scalar_vs_block<R, ST, DEV, H, FIELD, Q>(*j.P, j.fin, j.fout, j.mac_in, j.mac_out, j.acc, j.phi, j.ux, j.uy, j.smax,
                                           by * j.tiles_x + bx);
+}
+template <typename R, typename ST, bool DEV, int H, int FIELD, int Q>
+__global__ void __launch_bounds__(32 * VNW, 6) k_scalar_vs16_batch(const ScalarJob<R, ST>* __restrict__ jobs, int njobs) {
+    int bx, by;
+    const ScalarJob<R, ST>& j = job_block(jobs, njobs, blockIdx.x, bx, by);
+    scalar_vs_block<R, ST, DEV, H, FIELD, Q>(*j.P, j.fin, j.fout, j.mac_in, j.mac_out, j.acc, j.phi, j.ux, j.uy, j.smax,
+                                          by * j.tiles_x + bx);
+}
+template <typename R, typename ST, bool DEV, int H, int FIELD, int Q>
+constexpr auto scalar_vs_batch_kernel() {
+    if constexpr (sizeof(ST) == 2) return &k_scalar_vs16_batch<R, ST, DEV, H, FIELD, Q>;
+    else return &k_scalar_vs_batch<R, ST, DEV, H, FIELD, Q>;
 }
 template <typename R, typename ST, bool DEV, int H, int Q>
 __global__ void __launch_bounds__(32 * PVW)
@@ -1318,9 +1377,9 @@ k_phase_vs(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restri
            const long long* __restrict__ clock, long long step_off) {
     phase_vs_block<R, ST, DEV, H, Q>(*P, fin, fout, phi, phin, Um, Tm, clock, step_off, blockIdx.x);
 }
-// the same with 16-bit D2Q5 populations, four blocks (16 warps) per SM
+// the same with 16-bit D2Q5 populations (two nodes per lane), five blocks (20 warps) per SM
 template <typename R, typename ST, bool DEV, int H, int Q>
-__global__ void __launch_bounds__(32 * PVW, 4)
+__global__ void __launch_bounds__(32 * PVW, 5)
 k_phase_vs16(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout, const R* __restrict__ phi,
              R* __restrict__ phin, const R* __restrict__ Um, const R* __restrict__ Tm,
              const long long* __restrict__ clock, long long step_off) {
@@ -1364,7 +1423,7 @@ k_flow_vs(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restric
 // the same with 16-bit populations, three blocks (12 warps) per SM: 168
 // registers and the three-row ring fit three blocks where two fit before
 template <typename R, typename ST, bool DEV, int H>
-__global__ void __launch_bounds__(32 * FVW, 3)
+__global__ void __launch_bounds__(32 * FVW, 5)
 k_flow_vs16(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout, const R* __restrict__ phi,
             const R* __restrict__ ux_in, const R* __restrict__ uy_in, const R* __restrict__ rho_in,
             R* __restrict__ ux_out, R* __restrict__ uy_out, R* __restrict__ rho_out) {
