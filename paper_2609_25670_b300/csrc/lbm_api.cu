@@ -549,7 +549,7 @@ void launch_batch(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, 
         case LBM_K_SCALAR_U:
             if (tysel > VS)
                 LBM_VS_SWITCH(tysel, (launch_ex_smem(h, scalar_vs_batch_kernel<R, ST, DEV, HV, 0, Q>(), g, dim3(32 * VNW),
-                                                     (size_t)VNW * VSRing<R>::BYTES, (const ScalarJob<R, ST>*)jobs,
+                                                     (size_t)VNW * VSRing<R, ST>::BYTES, (const ScalarJob<R, ST>*)jobs,
                                                      njobs)))
             else if (tysel < 0)
                 LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip_batch<R, ST, DEV, HV, 0, Q>, g, dim3(32 * NWS),
@@ -561,7 +561,7 @@ void launch_batch(lbm_sim* h, int kind, int tysel, const void* jobs, int njobs, 
         case LBM_K_SCALAR_T:
             if (tysel > VS)
                 LBM_VS_SWITCH(tysel, (launch_ex_smem(h, scalar_vs_batch_kernel<R, ST, DEV, HV, 1, Q>(), g, dim3(32 * VNW),
-                                                     (size_t)VNW * VSRing<R>::BYTES, (const ScalarJob<R, ST>*)jobs,
+                                                     (size_t)VNW * VSRing<R, ST>::BYTES, (const ScalarJob<R, ST>*)jobs,
                                                      njobs)))
             else if (tysel < 0)
                 LBM_STRIP_SWITCH(tysel, (launch_ex(h, k_scalar_strip_batch<R, ST, DEV, HV, 1, Q>, g, dim3(32 * NWS),
@@ -654,7 +654,7 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
             const int cm = isU ? s.cur_U : s.cur_T;
             const R* acc = (const R*)(isU ? s.accU : s.accT);
             if (tysel > VS) {
-                const size_t sm = (size_t)VNW * VSRing<R>::BYTES;
+                const size_t sm = (size_t)VNW * VSRing<R, ST>::BYTES;
                 if (isU)
                     LBM_VS_SWITCH(tysel, (launch_ex_smem(h, scalar_vs_kernel<R, ST, DEV, HV, 0, Q>(), grid_v(s, kind, tysel),
                         dim3(32 * VNW), sm, P, fin, fout, (const R*)mac[cm], (R*)mac[1 - cm], acc, phi_now, uxc, uyc,

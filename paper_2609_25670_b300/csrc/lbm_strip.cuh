@@ -435,7 +435,9 @@ template <typename R, int NA, int DD = 0> struct VRingN {
     static constexpr int D = DD ? DD : sizeof(R) == 8 ? 2 : 4;   // rows in the ring (D - 1 in flight)
     static constexpr int BYTES = D * SLOT;
 };
-template <typename R> using VRing = VRingN<R, VA_N>;     // scalar strips
+// scalar strips; with 16-bit storage a ring of three rows (two in flight), so
+// that eight blocks (16 warps) fit on an SM
+template <typename R, typename ST = R> using VRing = VRingN<R, VA_N, sizeof(ST) == 2 ? 3 : 0>;
 constexpr int VNW = 2;     // warps per block of the vector-strip launches
 
 // One vector strip.  UP = false walks rows y0-1 .. y0+H downwards and
@@ -450,7 +452,7 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
                                               const R* __restrict__ ux, const R* __restrict__ uy,
                                               unsigned long long* __restrict__ smax, int s, int y0,
                                               unsigned char* __restrict__ ring) {
-    using RG = VRing<R>;
+    using RG = VRing<R, ST>;
     constexpr int EB = RG::EB, NR = H + 2, D = RG::D, DIR = UP ? -1 : 1;
     const int lane = threadIdx.x & 31, pl = (int)P.plane, pitch = P.pitch;
     const int c0 = VSW * s + VW * lane;
@@ -600,9 +602,9 @@ __device__ __forceinline__ void scalar_vstrip(const KP<R>& P, const ST* __restri
 // One launch: blocks [0, nvb) run vector strips over the interior, the rest
 // run the 1-wide strips of the whole lattice, skipping those whose outputs
 // all lie in the interior.
-template <typename R> struct VSRing {
+template <typename R, typename ST = R> struct VSRing {
     static constexpr int V1 = Pipe<R>::D * SA_N * 32 * (int)sizeof(Word<R>);
-    static constexpr int BYTES = VRing<R>::BYTES > V1 ? VRing<R>::BYTES : V1;   // per warp
+    static constexpr int BYTES = VRing<R, ST>::BYTES > V1 ? VRing<R, ST>::BYTES : V1;   // per warp
 };
 __host__ __device__ inline int vs_vector_blocks(const VGeo& g) { return (g.nxv * g.nyv + VNW - 1) / VNW; }
 __host__ __device__ inline int vs_blocks(int nx, int ny, int H) {
@@ -614,9 +616,9 @@ template <typename R, typename ST, bool DEV, int H, int FIELD, int Q>
 __device__ __forceinline__ void scalar_vs_block(const KP<R>& P, const ST* fin, ST* fout, const R* mac_in, R* mac_out,
                                                 const R* acc, const R* phi, const R* ux, const R* uy,
                                                 unsigned long long* smax, int b) {
-    extern __shared__ __align__(128) unsigned char ring[];    // VNW * VSRing<R>::BYTES, dynamic
+    extern __shared__ __align__(128) unsigned char ring[];    // VNW * VSRing<R, ST>::BYTES, dynamic
     const int w = threadIdx.x >> 5;
-    unsigned char* mine = ring + w * VSRing<R>::BYTES;
+    unsigned char* mine = ring + w * VSRing<R, ST>::BYTES;
     const VGeo g = vgeo(P.nx, P.ny, H);
     const int nvb = vs_vector_blocks(g);
     if (b < nvb) {
@@ -1334,12 +1336,14 @@ k_scalar_vs(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restr
             unsigned long long* __restrict__ smax) {
     scalar_vs_block<R, ST, DEV, H, FIELD, Q>(*P, fin, fout, mac_in, mac_out, acc, phi, ux, uy, smax, blockIdx.x);
 }
-// The same with 16-bit storage, compiled for six blocks per SM (the
-// shared-memory limit of the ring).  Without a stated minimum the register
-// allocator kept the 16-bit D2Q5 T strip at 96 registers with spills inside
-// its row loop; with it, the strip takes the registers it needs.
+// The same with 16-bit storage, compiled for the blocks per SM its three-row
+// ring allows (eight) where the registers fit, D2Q5; six on D2Q9, whose U
+// strip needs more than 128 registers.  Without a stated minimum the register
+// allocator had kept the 16-bit D2Q5 T strip at 96 registers with spills
+// inside its row loop.
+template <int Q, bool BATCH> constexpr int scalar16_min_blocks() { return Q == 5 ? (BATCH ? 7 : 8) : 6; }
 template <typename R, typename ST, bool DEV, int H, int FIELD, int Q>
-__global__ void __launch_bounds__(32 * VNW, 6)
+__global__ void __launch_bounds__(32 * VNW, scalar16_min_blocks<Q, false>())
 k_scalar_vs16(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout,
               const R* __restrict__ mac_in, R* __restrict__ mac_out, const R* __restrict__ acc,
               const R* __restrict__ phi, const R* __restrict__ ux, const R* __restrict__ uy,
@@ -1359,7 +1363,7 @@ __global__ void __launch_bounds__(32 * VNW) k_scalar_vs_batch(const ScalarJob<R,
                                           by * j.tiles_x + bx);
 }
 template <typename R, typename ST, bool DEV, int H, int FIELD, int Q>
-__global__ void __launch_bounds__(32 * VNW, 6) k_scalar_vs16_batch(const ScalarJob<R, ST>* __restrict__ jobs, int njobs) {
+__global__ void __launch_bounds__(32 * VNW, scalar16_min_blocks<Q, true>()) k_scalar_vs16_batch(const ScalarJob<R, ST>* __restrict__ jobs, int njobs) {
     int bx, by;
     const ScalarJob<R, ST>& j = job_block(jobs, njobs, blockIdx.x, bx, by);
     scalar_vs_block<R, ST, DEV, H, FIELD, Q>(*j.P, j.fin, j.fout, j.mac_in, j.mac_out, j.acc, j.phi, j.ux, j.uy, j.smax,
