@@ -12,10 +12,12 @@ DEPS = SRC + [os.path.join(HERE, "csrc", n) for n in ("lbm_kernels.cuh", "lbm_co
     [os.path.join(ROOT, "include", "lbm.h")]
 LIB = os.path.join(HERE, "liblbm.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-# -split-compile=0: the device optimiser runs on every host core (the one
-# translation unit instantiates every kernel variant; about half the wall time)
+# No -split-compile: with the module split across threads the code of one
+# kernel depended on how unrelated kernels were partitioned (the FP32 flow
+# strip ran 4 % slower in one split than in another; a 16-bit strip spilled
+# in one).  One optimiser pass over the whole module takes about five minutes.
 FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
-         "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr", "-split-compile=0"]
+         "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]
 
 
 def build(force: bool = False, verbose_ptxas: bool = False) -> str:

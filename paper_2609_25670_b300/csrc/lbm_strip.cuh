@@ -1137,7 +1137,11 @@ __device__ __forceinline__ void phase_vstrip(const KP<R>& P, const ST* __restric
         cy[k] = R(0); ay[k] = R(1);
         q0[k] = q1[k] = q3[k] = qa[k] = qb[k] = qc[k] = za[k] = zb[k] = zc[k] = R(0);
     }
-#pragma unroll 1
+    // rows two at a time with 16-bit D2Q5 populations (an instruction-bound
+    // strip: the unrolled loop renames the rolled row state instead of
+    // copying it); one at a time otherwise, where the larger body cost more
+    // than the copies
+#pragma unroll (sizeof(ST) == 2 && Q == 5 ? 2 : 1)
     for (int it = 0; it < NR; ++it) {
         const int r = rfirst + DIR * it;
         if (it + D - 1 < NR) fetch_row(r + DIR * (D - 1), mine + ((it + D - 1) % D) * RG::SLOT);
@@ -1338,10 +1342,11 @@ k_scalar_vs(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restr
 }
 // The same with 16-bit storage, compiled for the blocks per SM its three-row
 // ring allows (eight) where the registers fit, D2Q5; six on D2Q9, whose U
-// strip needs more than 128 registers.  Without a stated minimum the register
+// strip needs more than 128 registers, and for the batched form (its job
+// lookup adds registers).  Without a stated minimum the register
 // allocator had kept the 16-bit D2Q5 T strip at 96 registers with spills
 // inside its row loop.
-template <int Q, bool BATCH> constexpr int scalar16_min_blocks() { return Q == 5 ? (BATCH ? 7 : 8) : 6; }
+template <int Q, bool BATCH> constexpr int scalar16_min_blocks() { return Q == 5 && !BATCH ? 8 : 6; }
 template <typename R, typename ST, bool DEV, int H, int FIELD, int Q>
 __global__ void __launch_bounds__(32 * VNW, scalar16_min_blocks<Q, false>())
 k_scalar_vs16(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout,
