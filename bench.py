@@ -81,32 +81,6 @@ def algo_bytes(prec="f32", q=9, ori=False):
 
 ALGO_BYTES = algo_bytes("f32")
 
-FUSED_PHASE = 2000           # phase variants 2000 + h: the phase update fused with the transfer
-
-
-def fused_interior(nx, ny, h, v=2):
-    """Nodes of the interior the fused phase-transfer strips cover (strips of
-    height h, v nodes per lane, spaced 28 v columns apart, rows 4 ..; the
-    same rectangle as the library's strip geometry); the rest of the lattice
-    is the frame, where the phase runs as tiles and the transfer as a
-    second launch."""
-    nxv = (nx - 32 * v) // (28 * v) + 1 if nx >= 32 * v else 0
-    nyv = (ny - 8 - h) // h + 1 if ny - 8 - h >= 0 else 0
-    return 0 if not nxv or not nyv else 28 * v * nxv * h * nyv
-
-
-def fused_phase_bytes(prec, q, nx, ny, h, ori=True, has_T=True):
-    """Algorithmic bytes per node of one fused phase-transfer launch plus the
-    frame's transfer launch: an interior node moves the phase update's bytes
-    and writes U*, T* (the transfer's other inputs are the phase update's);
-    a frame node moves the phase update's and the staged transfer's."""
-    ab = algo_bytes(prec, q, ori)
-    m = MACRO_BYTES[prec]
-    nin = fused_interior(nx, ny, h)
-    n = nx * ny
-    inner = ab["phase"] + m + (m if has_T else 0)
-    return (inner * nin + (ab["phase"] + ab["transfer"]) * (n - nin)) / n
-
 
 def transport_bytes(tr, u, t, f, has_T=True, has_flow=True, prec="f32"):
     """Algorithmic bytes per node of one fused transport launch: the transfer
@@ -150,20 +124,17 @@ def period_bytes(p, prec="f32"):
     return tot, n
 
 
-def step_bytes_md(p, prec, fused, q, phase_variant=0):
+def step_bytes_md(p, prec, fused, q):
     """Algorithmic bytes per node per base step of the multi-dendrite
     workload: phase and transfer every step, U every N_U-th, T every N_T-th,
-    flow every N_F-th (the fused transport: the phase plus the period mean of
-    the fused launches; a fused phase variant: the phase-transfer launches'
-    bytes in place of the two staged updates')."""
+    flow every N_F-th (the fused path: the phase plus the period mean of the
+    fused launches)."""
     ab = algo_bytes(prec, q, ori=True)
     if fused:
         tb, _ = period_bytes(p, prec)
         return ab["phase"] / p.N_phi + tb / (2 * MD_PERIOD)
-    pt = ab["phase"] + ab["transfer"]
-    if phase_variant > FUSED_PHASE:
-        pt = fused_phase_bytes(prec, q, p.nx, p.ny, phase_variant - FUSED_PHASE, True, p.has_T)
-    return pt / p.N_phi + ab["scalar_U"] / p.N_U + ab["scalar_T"] / p.N_T + ab["flow"] / p.N_F
+    return ((ab["phase"] + ab["transfer"]) / p.N_phi + ab["scalar_U"] / p.N_U + ab["scalar_T"] / p.N_T
+            + ab["flow"] / p.N_F)
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of ncu captures
@@ -370,7 +341,7 @@ def refine_tiles(sim, torch, flush, tiles, steps=24):
 VECTOR_STRIP_HEIGHTS = (8, 16, 32)
 
 
-def refine_vector_tiles(sim, torch, tiles, period, steps=8, fused_phase=False):
+def refine_vector_tiles(sim, torch, tiles, period, steps=8):
     """Refinement of the autotuner's choice among the vector-strip heights
     (variants 1000 + H) on a lattice larger than L2: lbm_autotune times a
     kind's launches back to back, each as the only kernel in flight, which
@@ -378,17 +349,13 @@ def refine_vector_tiles(sim, torch, tiles, period, steps=8, fused_phase=False):
     follows another.  For each kind that runs a vector strip, time whole
     schedule periods (graph replays, the median of `steps`) for each strip
     height and keep the fastest.  The live state is advanced by these
-    periods; the caller re-initialises before its timed region.  With
-    fused_phase the phase candidates include the phase update fused with the
-    transfer (2000 + h).  Returns the refined choices."""
+    periods; the caller re-initialises before its timed region.  Returns the
+    refined choices."""
     stream = sim.stream
     kinds = [k for k in KINDS if k != "transport" and tiles.get(k, 0) > 1000]
     for kind in kinds:
         best, best_v = None, tiles[kind]
-        cand = {1000 + h for h in VECTOR_STRIP_HEIGHTS} | {tiles[kind]}
-        if kind == "phase" and fused_phase:
-            cand |= {FUSED_PHASE + h for h in (16, 32)}
-        for v in sorted(cand):
+        for v in sorted({1000 + h for h in VECTOR_STRIP_HEIGHTS} | {tiles[kind]}):
             sim.set_tile(kind, v)
             sim.advance(period)                       # capture with this variant
             torch.cuda.synchronize()
@@ -583,7 +550,7 @@ def measure_md(args, torch, lbm, local, dev, prec, q, world=1, with_e2e=False):
         tiles = {k: 0 for k in KINDS}
     else:
         tiles = sim.autotune(reps=3)
-        tiles = refine_vector_tiles(sim, torch, tiles, MD_PERIOD, fused_phase=not sim.fused)
+        tiles = refine_vector_tiles(sim, torch, tiles, MD_PERIOD)
     for spec in args.tile or []:            # fixed kernel variants (profiling runs)
         kind, v = spec.split("=")
         sim.set_tile(kind, int(v))
@@ -628,14 +595,9 @@ def measure_md(args, torch, lbm, local, dev, prec, q, world=1, with_e2e=False):
     finite = not sim.diagnostics()["nonfinite"]
 
     peak, peak_kind = measured_peaks()
-    sb = step_bytes_md(p, prec, fused, q, tiles["phase"])
+    sb = step_bytes_md(p, prec, fused, q)
     gbs = sb * nodes * MD_PERIOD * args.steps / (ms * 1e-3) / 1e9
     dom_algo = algo_bytes(prec, q, ori=True)
-    if not fused and tiles["phase"] > FUSED_PHASE:     # the phase launch also does the interior's transfer
-        h = tiles["phase"] - FUSED_PHASE
-        nin = fused_interior(p.nx, p.ny, h)
-        dom_algo["phase"] = (dom_algo["phase"] * nodes + 2 * MACRO_BYTES[prec] * nin) / nodes
-        dom_algo["transfer"] = dom_algo["transfer"] * (nodes - nin) / nodes
     tb, tn = period_bytes(p, prec)
     dom_algo["transport"] = tb / max(tn, 1)
     avg_s = kt[dom][0] * 1e-3 / max(kt[dom][1], 1)

@@ -267,10 +267,7 @@ lbm_status lbm_get_fusion(lbm_handle h, int32_t* enabled);
  * them.  Synchronises the stream.  Errors: INVALID_ARG, OOM, CUDA. */
 lbm_status lbm_set_orientation(lbm_handle h, int32_t sim, const double* theta, int32_t src_is_device);
 
-/* Kernel kinds for timing and launch counts.  With a fused phase variant
- * (2000 + h, lbm_set_tile) the PHASE launch also performs the transfer
- * (Eqs. 36-39) of the interior it covers, and the TRANSFER launch covers only
- * the frame around it. */
+/* Kernel kinds for timing and launch counts. */
 enum { LBM_K_PHASE = 0, LBM_K_TRANSFER = 1, LBM_K_SCALAR_U = 2, LBM_K_SCALAR_T = 3,
        LBM_K_FLOW = 4, LBM_K_DIAG = 5, LBM_K_INIT = 6,
        LBM_K_TRANSPORT = 7,   /* fused transfer + U + T + flow of one base step */
@@ -296,11 +293,8 @@ lbm_status lbm_timing_read(lbm_handle h, double* ms, int64_t* count, int32_t res
  * lbm_set_fusion was called, it also times one half schedule period both as
  * fused transport launches and as one launch per stage (from the per-launch
  * times, each transport stage combination the schedule uses timed once) and
- * keeps the faster.  For a single simulation under the instantaneous
- * coupling it also times the phase update fused with the transfer (phase
- * variants 2000 + 16, 2000 + 32, plus the transfer of the frame) against the
- * best phase and transfer launches and keeps the faster.  chosen (nullable)
- * receives LBM_K_COUNT tile heights of simulation 0.  Recaptures graphs.
+ * keeps the faster.  chosen (nullable) receives LBM_K_COUNT tile heights of
+ * simulation 0.  Recaptures graphs.
  * Errors: STATE (not initialised), CUDA. */
 lbm_status lbm_autotune(lbm_handle h, int32_t reps, int32_t* chosen);
 
@@ -308,11 +302,7 @@ lbm_status lbm_autotune(lbm_handle h, int32_t reps, int32_t* chosen);
  * (LBM_K_PHASE .. LBM_K_FLOW) for every simulation and for the batched
  * launches.  Different tile shapes are different compilations of the same
  * arithmetic and agree to floating-point contraction rounding; a fixed
- * choice makes runs bitwise reproducible.  Phase variants 2000 + 16 and
- * 2000 + 32 fuse the transfer into the phase launch (vector strips of that
- * height); they apply to single simulations under the instantaneous
- * coupling (others run the phase variant 1000 + h and the staged transfer)
- * and leave the batched launches' choice unchanged.  Recaptures graphs.
+ * choice makes runs bitwise reproducible.  Recaptures graphs.
  * Errors: INVALID_ARG. */
 lbm_status lbm_set_tile(lbm_handle h, int32_t kind, int32_t ty);
 

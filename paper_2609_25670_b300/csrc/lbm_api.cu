@@ -421,18 +421,11 @@ inline bool has_strips(int kind) { return kind == LBM_K_SCALAR_U || kind == LBM_
 inline bool has_vstrips(int kind) {
     return has_strips(kind) || kind == LBM_K_FLOW || kind == LBM_K_TRANSFER || kind == LBM_K_PHASE;
 }
-// v = VS2 + h: the phase update fused with the transfer (vector strips of
-// height h, single simulations under the instantaneous coupling); the
-// transfer kind then runs only on the frame around the fused strips
-constexpr int VS2 = 2000;
 inline bool valid_variant(int kind, int v) {
     return v == 4 || v == 8 || v == 16 ||
            (has_strips(kind) && (v == -4 || v == -8 || v == -16 || v == -32)) ||
-           (has_vstrips(kind) && (v == VS + 8 || v == VS + 16 || v == VS + 32)) ||
-           (kind == LBM_K_PHASE && (v == VS2 + 16 || v == VS2 + 32));
+           (has_vstrips(kind) && (v == VS + 8 || v == VS + 16 || v == VS + 32));
 }
-// the phase variant without the fusion
-inline int plain_phase(int v) { return v > VS2 ? v - VS2 + VS : v; }
 
 // Update-kernel launch on the handle's stream, with dynamic shared memory
 // (opted in above the 48 KB default when a kernel needs more).
@@ -464,11 +457,6 @@ inline void launch_ex(lbm_sim* h, void (*kern)(KArgs...), dim3 g, dim3 b, Args..
     switch (sel) {                                          \
         case VS + 8: { constexpr int HV = 8; BODY; } break;    \
         case VS + 32: { constexpr int HV = 32; BODY; } break;  \
-        default: { constexpr int HV = 16; BODY; } break;       \
-    }
-#define LBM_VS2_SWITCH(sel, BODY)                           \
-    switch (sel) {                                          \
-        case VS2 + 32: { constexpr int HV = 32; BODY; } break; \
         default: { constexpr int HV = 16; BODY; } break;       \
     }
 #define LBM_STRIP_SWITCH(sel, BODY)                      \
@@ -630,15 +618,7 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
     R* null_w = nullptr;
     switch (kind) {
         case LBM_K_PHASE:
-            if (tysel > VS2)       // fused with the transfer of the interior (U*, T* into the other buffers)
-                LBM_VS2_SWITCH(tysel, (launch_ex_smem(h, k_phase_transfer_vs<R, ST, DEV, HV, Q>,
-                    dim3(pts_blocks(s.nx, s.ny, HV, fused_nodes_per_lane<Q, ST>())), dim3(32, PVW),
-                    (size_t)PTSmem<R, Q, ST>::BYTES, P, (const ST*)s.pops[FP][s.cur_pop[FP]],
-                    (ST*)s.pops[FP][1 - s.cur_pop[FP]], phi_now, (R*)s.phi[1 - s.cur_phi],
-                    s.has_U ? (const R*)s.U[s.cur_U] : null_r, s.has_T ? (const R*)s.T[s.cur_T] : null_r,
-                    s.has_U ? (R*)s.U[1 - s.cur_U] : null_w, s.has_T ? (R*)s.T[1 - s.cur_T] : null_w, s.smax, clock,
-                    off)))
-            else if (tysel > VS)
+            if (tysel > VS)
                 LBM_VS_SWITCH(tysel, (launch_ex_smem(h, phase_vs_kernel<R, ST, DEV, HV, Q>(),
                     grid_v(s, kind, tysel, phase_nodes_per_lane<Q, ST>()),
                     dim3(32, PVW), (size_t)PVSmem<R, Q, ST>::BYTES, P, (const ST*)s.pops[FP][s.cur_pop[FP]],
@@ -651,13 +631,7 @@ void launch_kind(lbm_sim* h, SimState& s, int kind, int tysel, const long long* 
                     s.has_T ? (const R*)s.T[s.cur_T] : null_r, clock, off)))
             break;
         case LBM_K_TRANSFER:   // phi^q = phi[1 - cur], phi^{q+1} = phi[cur] (after the phase flip)
-            if (tysel > VS2)       // the frame around fused phase strips of height tysel - VS2
-                LBM_VS2_SWITCH(tysel, (launch_ex(h, k_transfer_frame<R, HV, fused_nodes_per_lane<Q, ST>()>,
-                    dim3(transfer_frame_blocks(s.nx, s.ny, HV, fused_nodes_per_lane<Q, ST>())), dim3(TX, TVW), P,
-                    (const R*)s.phi[1 - s.cur_phi], phi_now, s.has_U ? (const R*)s.U[s.cur_U] : null_r,
-                    s.has_U ? (R*)s.U[1 - s.cur_U] : null_w, s.has_T ? (const R*)s.T[s.cur_T] : null_r,
-                    s.has_T ? (R*)s.T[1 - s.cur_T] : null_w, s.smax)))
-            else if (tysel > VS)
+            if (tysel > VS)
                 LBM_VS_SWITCH(tysel, (launch_ex_smem(h, k_transfer_vs<R, HV>, grid_v(s, kind, tysel), dim3(32, TVW),
                     (size_t)TVSmem<R>::BYTES, P, (const R*)s.phi[1 - s.cur_phi], phi_now,
                     s.has_U ? (const R*)s.U[s.cur_U] : null_r, s.has_U ? (R*)s.U[1 - s.cur_U] : null_w,
@@ -828,11 +802,6 @@ void transport_any(lbm_sim* h, SimState& s, bool tr, bool u, bool t, bool f) {
     }
 }
 
-// the phase variant fuses the transfer (single simulation, instantaneous coupling)
-bool phase_fused(const lbm_sim* h, const SimState& s) {
-    return s.tile[LBM_K_PHASE] > VS2 && !s.accumulated && !h->batching;
-}
-
 void enqueue_base_step(lbm_sim* h, SimState& s, int64_t n, const long long* clock, long long off) {
     const lbm_params& p = s.p;
     if (h->fuse && !s.accumulated) {
@@ -841,7 +810,7 @@ void enqueue_base_step(lbm_sim* h, SimState& s, int64_t n, const long long* cloc
         const bool t = s.has_T && (n + 1) % p.N_T == 0;
         const bool f = s.has_flow && (n + 1) % p.N_F == 0;
         if (ph) {
-            launch_any(h, s, LBM_K_PHASE, plain_phase(s.tile[LBM_K_PHASE]), clock, off);
+            launch_any(h, s, LBM_K_PHASE, s.tile[LBM_K_PHASE], clock, off);
             s.cur_pop[FP] ^= 1;
             s.cur_phi ^= 1;                  // phi[cur] = phi^{q+1}
         }
@@ -856,11 +825,10 @@ void enqueue_base_step(lbm_sim* h, SimState& s, int64_t n, const long long* cloc
         return;
     }
     if ((n + 1) % p.N_phi == 0) {
-        const bool pf = phase_fused(h, s);   // the phase launch does the interior's transfer
-        launch_any(h, s, LBM_K_PHASE, pf ? s.tile[LBM_K_PHASE] : plain_phase(s.tile[LBM_K_PHASE]), clock, off);
+        launch_any(h, s, LBM_K_PHASE, s.tile[LBM_K_PHASE], clock, off);
         s.cur_pop[FP] ^= 1;
         s.cur_phi ^= 1;                      // phi[cur] = phi^{q+1}
-        launch_any(h, s, LBM_K_TRANSFER, pf ? s.tile[LBM_K_PHASE] : s.tile[LBM_K_TRANSFER], clock, off);
+        launch_any(h, s, LBM_K_TRANSFER, s.tile[LBM_K_TRANSFER], clock, off);
         if (!s.accumulated) {
             if (s.has_U) s.cur_U ^= 1;
             if (s.has_T) s.cur_T ^= 1;
@@ -1608,16 +1576,15 @@ lbm_status lbm_set_tile(lbm_handle h, int32_t kind, int32_t ty) {
     if (kind < 0 || (kind > LBM_K_FLOW && kind != LBM_K_TRANSPORT))
         return fail(h, LBM_E_INVALID_ARG, "kind %d is not an update kernel", kind);
     if (!valid_variant(kind, ty))
-        return fail(h, LBM_E_INVALID_ARG, "variant %d is not a tile height in {4, 8, 16}%s%s", ty,
+        return fail(h, LBM_E_INVALID_ARG, "variant %d is not a tile height in {4, 8, 16}%s", ty,
                     has_strips(kind) ? ", a strip height in {-4, -8, -16, -32} or 1000 + a vector strip height in "
                                        "{8, 16, 32}" : has_vstrips(kind) ? " or 1000 + a vector strip height in {8, 16, 32}"
-                                                                         : "",
-                    kind == LBM_K_PHASE ? " or 2000 + a fused phase-transfer strip height in {16, 32}" : "");
+                                                                         : "");
     for (auto& s : h->sims) {
         s.tile[kind] = ty;
         drop_graph(s);
     }
-    if (ty < VS2) h->batch_tile[kind] = ty;      // batched launches have no fused phase variant
+    h->batch_tile[kind] = ty;
     drop_batch_graph(h);
     return LBM_OK;
 }
@@ -1718,27 +1685,6 @@ lbm_status lbm_autotune(lbm_handle h, int32_t reps, int32_t* chosen) {
             s.tile[kind] = bestv;
             best_ms[kind] = best;
         }
-        // the phase update fused with the transfer (one launch over the
-        // interior and the transfer of the frame) against the two staged
-        // launches; the fused-transport path keeps the plain phase variant
-        const double plain_phase_ms = best_ms[LBM_K_PHASE];
-        if (present[LBM_K_PHASE] && present[LBM_K_TRANSFER] && !h->batching) {
-            double best_f = 1e30, f_phase = 0.0, f_frame = 0.0;
-            int bestv = 0;
-            for (int hv : {16, 32}) {
-                float mp = 0.f, mt = 0.f;
-                lbm_status st = time_launch(LBM_K_PHASE, VS2 + hv, all_stages, &mp);
-                if (st) return st;
-                st = time_launch(LBM_K_TRANSFER, VS2 + hv, all_stages, &mt);
-                if (st) return st;
-                if (mp + mt < best_f) { best_f = mp + mt; bestv = VS2 + hv; f_phase = mp; f_frame = mt; }
-            }
-            if (best_f < best_ms[LBM_K_PHASE] + best_ms[LBM_K_TRANSFER]) {
-                s.tile[LBM_K_PHASE] = bestv;
-                best_ms[LBM_K_PHASE] = f_phase;
-                best_ms[LBM_K_TRANSFER] = f_frame;
-            }
-        }
         if (pick) {
             // cost of one half period (lcm of the update factors) both ways
             choose = true;
@@ -1751,10 +1697,9 @@ lbm_status lbm_autotune(lbm_handle h, int32_t reps, int32_t* chosen) {
                 const bool u = s.has_U && (k + 1) % q.N_U == 0;
                 const bool t = s.has_T && (k + 1) % q.N_T == 0;
                 const bool f = s.has_flow && (k + 1) % q.N_F == 0;
-                cost_staged += (ph ? best_ms[LBM_K_PHASE] + best_ms[LBM_K_TRANSFER] : 0.0) +
-                               (u ? best_ms[LBM_K_SCALAR_U] : 0.0) + (t ? best_ms[LBM_K_SCALAR_T] : 0.0) +
-                               (f ? best_ms[LBM_K_FLOW] : 0.0);
-                const double base = ph ? plain_phase_ms : 0.0;
+                const double base = ph ? best_ms[LBM_K_PHASE] : 0.0;
+                cost_staged += base + (ph ? best_ms[LBM_K_TRANSFER] : 0.0) + (u ? best_ms[LBM_K_SCALAR_U] : 0.0) +
+                               (t ? best_ms[LBM_K_SCALAR_T] : 0.0) + (f ? best_ms[LBM_K_FLOW] : 0.0);
                 const int combo = (ph ? 1 : 0) | (u ? 2 : 0) | (t ? 4 : 0) | (f ? 8 : 0);
                 if (combo && combo_ms[combo] < 0.0) {
                     float ms = 0.f;

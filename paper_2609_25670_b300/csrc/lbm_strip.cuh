@@ -1298,345 +1298,6 @@ __device__ __forceinline__ void phase_vs_block(const KP<R>& P, const ST* fin, ST
                                  off, u * 32, v * PVW, g.in);
 }
 
-
-// ---------------------------------------------------------------------------
-// The phase update fused with the phase-change transfer (Eqs. 2-4, 14, 18,
-// 21-26, then Eqs. 36-39 on the new phi) in one pass over the interior, for
-// the instantaneous coupling.  Staged, the transfer reads phi^q, phi^{q+1},
-// U and T back from memory right after the phase update has read or written
-// them; fused, it takes them from the phase strip's registers and only its
-// outputs U*, T* go to memory (a D2Q5 phase update with grain angles: 52 + 24
-// B/node staged, 60 fused, FP32).
-//
-// The transfer at a node needs phi^{q+1} two nodes away (J from grad phi^{q+1}
-// on a 3 x 3 stencil, then div J on a 3 x 3 stencil), and a strip completes
-// phi^{q+1} only on lanes 1..30 (its halo lanes lack their outer
-// neighbours' populations).  So the fused strips are spaced 28 V columns
-// apart and write lanes 2..29 only; vertically a strip collides rows
-// y0 - 3 .. y0 + H + 2, so that phi^{q+1} is complete on rows y0 - 2 ..
-// y0 + H + 1, and writes rows y0 .. y0 + H - 1 of both updates.  Its extra
-// rows and columns repeat work of the neighbouring strips (their inputs come
-// from L2).  The phase frame around the interior runs in the same launch as
-// 32 x 4 tiles; the transfer of the frame is a second launch
-// (k_transfer_frame) over the same complement.
-// ---------------------------------------------------------------------------
-constexpr int VY0F = 4;            // first interior row of the fused strips
-template <int Q, typename ST> constexpr int fused_nodes_per_lane() { return 2; }
-__host__ __device__ inline VGeo vgeo_fused(int nx, int ny, int H, int V) {
-    VGeo g;
-    g.nxv = nx >= 32 * V ? (nx - 32 * V) / (28 * V) + 1 : 0;   // strip s: columns 28 V s .. 28 V s + 32 V - 1
-    g.nyv = ny - 8 - H >= 0 ? (ny - 8 - H) / H + 1 : 0;       // rows y0 - 4 .. y0 + H + 3 inside
-    if (!g.nxv || !g.nyv) g.nxv = g.nyv = 0;
-    g.in = Rect{2 * V, 2 * V + 28 * V * g.nxv, VY0F, VY0F + H * g.nyv};
-    return g;
-}
-template <typename R, int Q, typename ST> struct FusedRing {
-    static constexpr int V = fused_nodes_per_lane<Q, ST>();
-    static constexpr int EB = V * (int)sizeof(R);
-    static constexpr int SLOT = PA<Q>::N * 32 * EB;
-    static constexpr int D = sizeof(R) == 8 ? 2 : 4;
-    static constexpr int BYTES = D * SLOT;
-};
-
-template <typename R, typename ST, bool DEV, int H, bool UP, int Q>
-__device__ __forceinline__ void phase_transfer_vstrip(const KP<R>& P, const ST* __restrict__ fin,
-                                                      ST* __restrict__ fout, const R* __restrict__ phi,
-                                                      R* __restrict__ phin, const R* __restrict__ Um,
-                                                      const R* __restrict__ Tm, R* __restrict__ Uout,
-                                                      R* __restrict__ Tout, R tnow, int s, int y0,
-                                                      unsigned char* __restrict__ ring, R& mydu) {
-    using RG = FusedRing<R, Q, ST>;
-    constexpr int V = RG::V;
-    constexpr int PA_PHI = PA<Q>::PHI, PA_U = PA<Q>::U, PA_T = PA<Q>::T, PA_ORI = PA<Q>::ORI;
-    constexpr int EB = RG::EB, NR = H + 6, D = RG::D, DIR = UP ? -1 : 1;
-    constexpr int FAX = UP ? 4 : 2, FL = UP ? 8 : 5, FR = UP ? 7 : 6;     // far row: axis, from left, from right
-    constexpr int NAX = UP ? 2 : 4, NL = UP ? 5 : 8, NRt = UP ? 6 : 7;    // near row (just collided)
-    const int lane = threadIdx.x & 31, pl = (int)P.plane, pitch = P.pitch;
-    const int c0 = 28 * V * s + V * lane;
-    const bool outw = lane >= 2 && lane <= 29;
-    const int rfirst = UP ? y0 + H + 2 : y0 - 3;
-    unsigned char* const mine = ring + lane * EB;
-    auto fetch_row = [&](int r, unsigned char* slot) {      // populations, U, T of row r; phi of row r + DIR
-        const int base = r * pitch + c0;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) fetch_vec<ST, V>(slot + (i - 1) * 32 * EB, fin + (size_t)(i - 1) * pl + base);
-        fetch_vec<R, V>(slot + PA_PHI * 32 * EB, phi + base + DIR * pitch);
-        if (P.has_U) fetch_vec<R, V>(slot + PA_U * 32 * EB, Um + base);
-        if (P.has_T) fetch_vec<R, V>(slot + PA_T * 32 * EB, Tm + base);
-        if (P.ori) fetch_vec<R, V>(slot + PA_ORI * 32 * EB, P.ori + base);
-    };
-#pragma unroll
-    for (int d = 0; d < D - 1; ++d) {
-        fetch_row(rfirst + DIR * d, mine + d * RG::SLOT);
-        __pipeline_commit();
-    }
-    VecN<R, V> pb = *reinterpret_cast<const VecN<R, V>*>(phi + (rfirst - DIR) * pitch + c0);
-    VecN<R, V> p0 = *reinterpret_cast<const VecN<R, V>*>(phi + rfirst * pitch + c0);
-    // phase: row y = r - DIR's own loaded populations, phi, a_s^2, post
-    // values q0, q1s, q3s and its far triple; far row: za, zb, zc
-    R fy[9][V], cy[V], ay[V], q0[V], q1[V], q3[V], qa[V], qb[V], qc[V], za[V], zb[V], zc[V];
-    // transfer, at the start of the row of collision r: phi^{q+1} of rows
-    // r - 2 DIR (nA) and r - 3 DIR (nB); J of rows r - 3 DIR (A) and r - 4 DIR
-    // (B); phi^q of rows r - 2 DIR, r - 3 DIR; U and T of rows r - DIR, r - 2 DIR,
-    // r - 3 DIR
-    R nA[V], nB[V], jxA[V], jyA[V], jxB[V], jyB[V], oA[V], oB[V], uA[V], uB[V], uC[V], tA[V], tB[V], tC[V];
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-#pragma unroll
-        for (int i = 1; i < 9; ++i) fy[i][k] = R(0);
-        cy[k] = R(0); ay[k] = R(1);
-        q0[k] = q1[k] = q3[k] = qa[k] = qb[k] = qc[k] = za[k] = zb[k] = zc[k] = R(0);
-        nA[k] = nB[k] = jxA[k] = jyA[k] = jxB[k] = jyB[k] = oA[k] = oB[k] = R(0);
-        uA[k] = uB[k] = uC[k] = tA[k] = tB[k] = tC[k] = R(0);
-    }
-    const R pre = P.at_pre, omk = R(1) - P.k;
-#pragma unroll 1
-    for (int it = 0; it < NR; ++it) {
-        const int r = rfirst + DIR * it;
-        if (it + D - 1 < NR) fetch_row(r + DIR * (D - 1), mine + ((it + D - 1) % D) * RG::SLOT);
-        __pipeline_commit();
-        __pipeline_wait_prior(D - 1);
-        const unsigned char* sl = mine + (it % D) * RG::SLOT;
-        R f[9][V];
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            if (i >= Q) {                          // D2Q5: no diagonal populations
-#pragma unroll
-                for (int k = 0; k < V; ++k) f[i][k] = R(0);
-                continue;
-            }
-            unpack4<ST, R, V>(sread<ST, V>(sl + (i - 1) * 32 * EB), f[i]);
-        }
-        const VecN<R, V> pf = sread<R, V>(sl + PA_PHI * 32 * EB);
-        VecN<R, V> Us{}, Tv{}, Ov{};
-        if (P.has_U) Us = sread<R, V>(sl + PA_U * 32 * EB);
-        if (P.has_T) Tv = sread<R, V>(sl + PA_T * 32 * EB);
-        if (P.ori) Ov = sread<R, V>(sl + PA_ORI * 32 * EB);
-        const VecN<R, V>& pm = UP ? pf : pb;
-        const VecN<R, V>& pp = UP ? pb : pf;
-        // ---- phase collision of row r (as in the phase strip)
-        R A[V + 2], B[V + 2];
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            A[k + 1] = p0.v[k] * (R(1) / R(3)) + (pm.v[k] + pp.v[k]) * (R(1) / R(12));
-            B[k + 1] = pp.v[k] - pm.v[k];
-        }
-        A[0] = from_left(A[V]); B[0] = from_left(B[V]);
-        A[V + 1] = from_right(A[1]); B[V + 1] = from_right(B[1]);
-        R p[V][9], a2[V];
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            const R gxv = A[k + 2] - A[k], gyv = B[k + 1] * (R(1) / R(3)) + (B[k] + B[k + 2]) * (R(1) / R(12));
-            const R c = p0.v[k];
-            R as, Nx, Ny;
-            if (P.ori) aniso_frame(gxv, gyv, P.eps, Ov.v[k], as, Nx, Ny);    // grain frame
-            else aniso(gxv, gyv, P.eps, as, Nx, Ny);
-            a2[k] = as * as;
-            const R sv = rcp(R(3) * P.dtp * a2[k] * P.W0sq_tau0 + R(0.5));                // Eq. 24
-            R th;
-            if (P.has_T) th = (Tv.v[k] - P.T_shift) * P.inv_T_scale;                    // Eq. 5
-            else if (P.frozen_T) th = theta_frozen(P, r, tnow);
-            else th = P.theta_c;
-            const R one = R(1) - c * c;
-            const R Qs = c * one - P.lam * (P.Mc * Us.v[k] + th) * one * one;             // Eq. 4
-            const R bx = -P.dtp * P.W0sq_tau0 * Nx, by = -P.dtp * P.W0sq_tau0 * Ny;     // dt v_n (Eqs. 21-22)
-            const R k6 = (R(1) - sv) * kneq<R, Q>();
-            const R jx = f[1][k] - f[3][k] + f[5][k] - f[6][k] - f[7][k] + f[8][k];
-            const R jy = f[2][k] - f[4][k] + f[5][k] + f[6][k] - f[7][k] - f[8][k];
-            scalar_post9<R, Q>(c + P.dtp * Qs * P.inv_tau0, bx, by, k6 * (jx - bx), k6 * (jy - by), p[k]);
-        }
-        R s1[V], s5[V], s8[V], s3[V], s6[V], s7[V];
-        s1[0] = from_left(p[V - 1][1]); s5[0] = diag_from_left<Q>(p[V - 1][5]); s8[0] = diag_from_left<Q>(p[V - 1][8]);
-        s3[V - 1] = from_right(p[0][3]); s6[V - 1] = diag_from_right<Q>(p[0][6]); s7[V - 1] = diag_from_right<Q>(p[0][7]);
-#pragma unroll
-        for (int k = 1; k < V; ++k) { s1[k] = p[k - 1][1]; s5[k] = p[k - 1][5]; s8[k] = p[k - 1][8]; }
-#pragma unroll
-        for (int k = 0; k < V - 1; ++k) { s3[k] = p[k + 1][3]; s6[k] = p[k + 1][6]; s7[k] = p[k + 1][7]; }
-        R(&sNL)[V] = UP ? s5 : s8;
-        R(&sNR)[V] = UP ? s6 : s7;
-        // ---- row yc = r - DIR completes: phi^{q+1} (Eq. 26, Eq. 18) on every
-        // lane (the halo lanes' values are not used for written nodes)
-        R nc[V];
-#pragma unroll
-        for (int k = 0; k < V; ++k) nc[k] = R(0);
-        if (it >= 2) {
-            R fn[9][V];
-#pragma unroll
-            for (int k = 0; k < V; ++k) {
-                const R c = cy[k];
-                R fa[9], s8v = R(0);
-#pragma unroll
-                for (int i = 1; i < 9; ++i) {
-                    fa[i] = fy[i][k];
-                    if (DEV && i < Q) fa[i] += wqq<R, Q>(i) * c;                     // decode h_i = f_i - w_i phi
-                    s8v += fa[i];
-                }
-                fa[0] = c - s8v;                                                     // population 0 from phi
-                R inc[9];
-                inc[0] = q0[k]; inc[1] = q1[k]; inc[3] = q3[k];
-                inc[FAX] = za[k]; inc[FL] = zb[k]; inc[FR] = zc[k];
-                inc[NAX] = p[k][NAX]; inc[NL] = sNL[k]; inc[NRt] = sNR[k];
-                const R inva2 = rcp(ay[k]);
-                R t = R(0);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    fn[i][k] = fa[i] + (inc[i] - fa[i]) * inva2;                     // Eq. 26
-                    t += fn[i][k];
-                }
-                nc[k] = t;
-            }
-            const int yc = r - DIR;
-            if (outw && yc >= y0 && yc < y0 + H) {
-                const int node = yc * pitch + c0;
-                VecN<R, V> sum;
-#pragma unroll
-                for (int k = 0; k < V; ++k) sum.v[k] = nc[k];
-                *reinterpret_cast<VecN<R, V>*>(phin + node) = sum;
-#pragma unroll
-                for (int i = 1; i < Q; ++i) {
-                    R ev[V];
-#pragma unroll
-                    for (int k = 0; k < V; ++k) ev[k] = DEV ? fn[i][k] - wqq<R, Q>(i) * nc[k] : fn[i][k];
-                    *reinterpret_cast<VecN<ST, V>*>(fout + (size_t)(i - 1) * pl + node) = pack4<ST, R, V>(ev);
-                }
-            }
-        }
-        // ---- J of row r - 2 DIR (Eqs. 36-37) from phi^{q+1} of rows r - 3 DIR,
-        // r - 2 DIR, r - DIR
-        R jxn[V], jyn[V];
-#pragma unroll
-        for (int k = 0; k < V; ++k) jxn[k] = jyn[k] = R(0);
-        if (it >= 4) {
-            const R(&qm)[V] = UP ? nc : nB;        // phi^{q+1} of the rows below and above row r - 2 DIR
-            const R(&qp)[V] = UP ? nB : nc;
-            R E[V + 2], F[V + 2];
-#pragma unroll
-            for (int k = 0; k < V; ++k) {
-                E[k + 1] = nA[k] * (R(1) / R(3)) + (qm[k] + qp[k]) * (R(1) / R(12));
-                F[k + 1] = qp[k] - qm[k];
-            }
-            E[0] = from_left(E[V]); F[0] = from_left(F[V]);
-            E[V + 1] = from_right(E[1]); F[V + 1] = from_right(F[1]);
-#pragma unroll
-            for (int k = 0; k < V; ++k) {
-                const R gxv = E[k + 2] - E[k], gyv = F[k + 1] * (R(1) / R(3)) + (F[k] + F[k + 2]) * (R(1) / R(12));
-                const R g2 = gxv * gxv + gyv * gyv;
-                if (g2 > R(1e-12)) {
-                    const R a = pre * (R(1) + omk * uB[k]) * (nA[k] - oA[k]) * rsq(g2);
-                    jxn[k] = -a * gxv;             // n = -grad phi / |grad phi|
-                    jyn[k] = -a * gyv;
-                }
-            }
-        }
-        // ---- div J and the transfer of row r - 3 DIR (Eqs. 38-39)
-        if (it >= 6) {
-            const R(&jxm)[V] = UP ? jxn : jxB;
-            const R(&jxp)[V] = UP ? jxB : jxn;
-            const R(&jym)[V] = UP ? jyn : jyB;
-            const R(&jyp)[V] = UP ? jyB : jyn;
-            R Sx[V + 2], Dy[V + 2];
-#pragma unroll
-            for (int k = 0; k < V; ++k) {
-                Sx[k + 1] = jxA[k] * (R(1) / R(3)) + (jxm[k] + jxp[k]) * (R(1) / R(12));
-                Dy[k + 1] = jyp[k] - jym[k];
-            }
-            Sx[0] = from_left(Sx[V]); Dy[0] = from_left(Dy[V]);
-            Sx[V + 1] = from_right(Sx[1]); Dy[V + 1] = from_right(Dy[1]);
-            if (outw) {
-                const int node = (r - 3 * DIR) * pitch + c0;
-                VecN<R, V> oU, oT;
-#pragma unroll
-                for (int k = 0; k < V; ++k) {
-                    const R div = Sx[k + 2] - Sx[k] + Dy[k + 1] * (R(1) / R(3)) + (Dy[k] + Dy[k + 2]) * (R(1) / R(12));
-                    const R dphi = nB[k] - oB[k];
-                    if (P.has_U) {
-                        const R dU = div_rn((R(1) + omk * uC[k]) * dphi - R(2) * div, (R(1) + P.k) - omk * nB[k]);  // Eq. 38
-                        mydu = fmax(mydu, fabs(dU));
-                        oU.v[k] = uC[k] + dU;                                                 // Eq. 39
-                    }
-                    if (P.has_T) {
-                        const R rc = R(0.5) * (R(1) + nB[k]) * P.cS + R(0.5) * (R(1) - nB[k]) * P.cL;
-                        oT.v[k] = tC[k] + P.rhoL_Lh * dphi * rcp(R(2) * rc);               // Eq. 38
-                    }
-                }
-                if (P.has_U) *reinterpret_cast<VecN<R, V>*>(Uout + node) = oU;
-                if (P.has_T) *reinterpret_cast<VecN<R, V>*>(Tout + node) = oT;
-            }
-        }
-        // ---- roll
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            za[k] = qa[k]; zb[k] = qb[k]; zc[k] = qc[k];
-            q0[k] = p[k][0]; q1[k] = s1[k]; q3[k] = s3[k];
-            qa[k] = p[k][FAX]; qb[k] = UP ? s8[k] : s5[k]; qc[k] = UP ? s7[k] : s6[k];
-#pragma unroll
-            for (int i = 1; i < 9; ++i) fy[i][k] = f[i][k];
-            cy[k] = p0.v[k];
-            ay[k] = a2[k];
-            nB[k] = nA[k]; nA[k] = nc[k];
-            jxB[k] = jxA[k]; jyB[k] = jyA[k]; jxA[k] = jxn[k]; jyA[k] = jyn[k];
-            oB[k] = oA[k]; oA[k] = pb.v[k];
-            uC[k] = uB[k]; uB[k] = uA[k]; uA[k] = Us.v[k];
-            tC[k] = tB[k]; tB[k] = tA[k]; tA[k] = Tv.v[k];
-        }
-        pb = p0;
-        p0 = pf;
-    }
-}
-
-template <typename R, int Q = 9, typename ST = R> struct PTSmem {
-    static constexpr int STRIPS = PVW * FusedRing<R, Q, ST>::BYTES;
-    static constexpr int TILE = (int)sizeof(PhaseSmem<R, PVW, Q>);
-    static constexpr int BYTES = STRIPS > TILE ? STRIPS : TILE;
-};
-__host__ __device__ inline int pts_blocks(int nx, int ny, int H, int V) {
-    const VGeo g = vgeo_fused(nx, ny, H, V);
-    return (g.nxv * g.nyv + PVW - 1) / PVW + frame_of(g.in, nx, ny, 32, PVW).count();
-}
-__host__ __device__ inline int transfer_frame_blocks(int nx, int ny, int H, int V) {
-    return frame_of(vgeo_fused(nx, ny, H, V).in, nx, ny, 32, TVW).count();
-}
-
-template <typename R, typename ST, bool DEV, int H, int Q>
-__device__ __forceinline__ void phase_transfer_vs_block(const KP<R>& P, const ST* fin, ST* fout, const R* phi,
-                                                        R* phin, const R* Um, const R* Tm, R* Uout, R* Tout,
-                                                        unsigned long long* smax, const long long* clock,
-                                                        long long off, int b) {
-    extern __shared__ __align__(128) unsigned char psm[];   // PTSmem<R, Q, ST>::BYTES, dynamic
-    const VGeo g = vgeo_fused(P.nx, P.ny, H, fused_nodes_per_lane<Q, ST>());
-    const int nvb = (g.nxv * g.nyv + PVW - 1) / PVW;
-    if (b < nvb) {
-        const int w = threadIdx.y;
-        const int vs = b * PVW + w;
-        if (vs >= g.nxv * g.nyv) return;           // whole warp (no block barrier on this path)
-        R tnow = R(0);
-        if (P.frozen_T) tnow = (R)((clock ? *clock : 0ll) + off) * P.dt_base;
-        const int sy = vs / g.nxv;
-        unsigned char* mine = psm + w * FusedRing<R, Q, ST>::BYTES;
-        R mydu = R(0);
-        if (sy & 1)
-            phase_transfer_vstrip<R, ST, DEV, H, true, Q>(P, fin, fout, phi, phin, Um, Tm, Uout, Tout, tnow,
-                                                          vs % g.nxv, VY0F + H * sy, mine, mydu);
-        else
-            phase_transfer_vstrip<R, ST, DEV, H, false, Q>(P, fin, fout, phi, phin, Um, Tm, Uout, Tout, tnow,
-                                                           vs % g.nxv, VY0F + H * sy, mine, mydu);
-        if (P.has_U) {       // warp maximum of |Delta U_pc| -> S_phi and J_U
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) mydu = fmax(mydu, __shfl_xor_sync(0xffffffffu, mydu, d));
-            if ((threadIdx.x & 31) == 0) {
-                atomic_max_pos(&smax[0], (double)mydu);
-                atomic_max_pos(&smax[1], (double)mydu);
-            }
-        }
-        return;
-    }
-    b -= nvb;
-    int u, v;
-    frame_of(g.in, P.nx, P.ny, 32, PVW).unit(b, u, v);
-    phase_block<R, ST, DEV, PVW, Q>(*reinterpret_cast<PhaseSmem<R, PVW, Q>*>(psm), P, fin, fout, phi, phin, Um, Tm, clock,
-                                 off, u * 32, v * PVW, g.in);
-}
-
 }  // namespace lbmk
 
 // ---------------------------------------------------------------------------
@@ -1737,28 +1398,6 @@ template <typename R, typename ST, bool DEV, int H, int Q>
 constexpr auto phase_vs_kernel() {
     if constexpr (sizeof(ST) == 2 && Q == 5) return &k_phase_vs16<R, ST, DEV, H, Q>;
     else return &k_phase_vs<R, ST, DEV, H, Q>;
-}
-// the phase update fused with the transfer (interior strips and frame phase
-// tiles), then the transfer of the frame
-template <typename R, typename ST, bool DEV, int H, int Q>
-__global__ void __launch_bounds__(32 * PVW)
-k_phase_transfer_vs(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout,
-                    const R* __restrict__ phi, R* __restrict__ phin, const R* __restrict__ Um,
-                    const R* __restrict__ Tm, R* __restrict__ Uout, R* __restrict__ Tout,
-                    unsigned long long* __restrict__ smax, const long long* __restrict__ clock, long long step_off) {
-    phase_transfer_vs_block<R, ST, DEV, H, Q>(*P, fin, fout, phi, phin, Um, Tm, Uout, Tout, smax, clock, step_off,
-                                              blockIdx.x);
-}
-template <typename R, int H, int V>
-__global__ void __launch_bounds__(32 * TVW)
-k_transfer_frame(const KP<R>* __restrict__ P, const R* __restrict__ phio, const R* __restrict__ phin,
-                 const R* __restrict__ Uin, R* __restrict__ Uout, const R* __restrict__ Tin, R* __restrict__ Tout,
-                 unsigned long long* __restrict__ smax) {
-    __shared__ TransferSmem<R, TVW> sm;
-    const Rect in = vgeo_fused(P->nx, P->ny, H, V).in;
-    int u, v;
-    frame_of(in, P->nx, P->ny, 32, TVW).unit(blockIdx.x, u, v);
-    transfer_block<R, TVW>(sm, *P, phio, phin, Uin, Uout, Tin, Tout, nullptr, nullptr, 0, 0, smax, u * 32, v * TVW, in);
 }
 template <typename R, typename ST, bool DEV, int H, int Q>
 __global__ void __launch_bounds__(32 * PVW) k_phase_vs_batch(const PhaseJob<R, ST>* __restrict__ jobs, int njobs) {
