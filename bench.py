@@ -634,38 +634,39 @@ def measure_md(args, torch, lbm, local, dev, prec, q, world=1, with_e2e=False):
 
 
 def md_e2e(args, torch, sim, p, pts, world):
-    """End to end through the public API with pinned host buffers, each step:
-    lbm_init_fields from the six FP64 host fields of the initial state,
-    lbm_advance of one schedule period, lbm_fields of phi back into a host
-    FP64 buffer; host time over the steps with a synchronisation (and a
-    barrier under torchrun) on both sides."""
-    f = W.multi_dendrite_fields(p, pts)
-    host = {k: torch.from_numpy(f[k]).pin_memory().numpy() for k in ("phi", "U", "T", "ux", "uy", "rho")}
-    del f
-    out_phi = torch.empty((p.ny, p.nx), dtype=torch.float64).pin_memory().numpy()
+    """End to end through the public API with host buffers, each step:
+    lbm_init_seed from the host list of the workload's seeds (the fields are
+    generated on the device), lbm_advance of one schedule period, lbm_fields
+    of phi back into a pinned host buffer in the arithmetic type; host time
+    over the steps with a synchronisation (and a barrier under torchrun) on
+    both sides."""
+    seeds = md_seeds(pts)
+    f64 = sim.precision == "f64"
+    out_phi = torch.empty((p.ny, p.nx), dtype=torch.float64 if f64 else torch.float32).pin_memory().numpy()
     steps = max(3, min(args.steps, 10))
-    sim.init_fields(host)                # one untimed pass (first-touch of the pinned pages)
+    sim.init_seed(seeds, U0=0.0, T0=-0.55)       # one untimed pass (first touch of the pinned pages)
     sim.advance(MD_PERIOD)
-    sim.field("phi", out=out_phi)
+    sim.field("phi", out=out_phi, as_f64=False)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
     for _ in range(steps):
-        sim.init_fields(host)
+        sim.init_seed(seeds, U0=0.0, T0=-0.55)
         sim.advance(MD_PERIOD)
-        sim.field("phi", out=out_phi)
+        sim.field("phi", out=out_phi, as_f64=False)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     dt = time.perf_counter() - t0
     dt = max_over_ranks(dt)
     nodes = p.nx * p.ny
+    seed_bytes = len(seeds) * 48                  # lbm_seed: kind, reserved, five doubles
     return {"value": nodes * MD_PERIOD * steps * world / dt / 1e6, "unit": UNIT,
-            "h2d_bytes_per_step": 6 * 8 * nodes, "d2h_bytes_per_step": 8 * nodes, "steps": steps,
+            "h2d_bytes_per_step": seed_bytes, "d2h_bytes_per_step": out_phi.nbytes, "steps": steps,
             "ms_per_step": dt * 1e3 / steps,
-            "calls": "lbm_init_fields(6 pinned host FP64 fields) + lbm_advance(4) + lbm_fields(phi -> pinned "
-                     "host FP64) per step"}
+            "calls": "lbm_init_seed(%d host seeds; fields generated on the device) + lbm_advance(4) + "
+                     "lbm_fields(phi -> pinned host, %s) per step" % (len(seeds), "FP64" if f64 else "FP32")}
 
 
 def md_accuracy(args, torch, lbm, dev, q, precs=("f32", "f16dev"), base_steps=1000):

@@ -176,13 +176,15 @@ typedef struct lbm_sim* lbm_handle;
 lbm_status lbm_create(const lbm_params* p, int32_t n_sims, const lbm_params* per_sim,
                       const lbm_allocator* a, void* cuda_stream, lbm_handle* out);
 
-/* Initialise simulation `sim` from seed primitives (host FP64 generation):
- * phi from the seeds, U = U0, T = T0, rho = 1, u = u_in (1 - phi)/2 along x
- * when the flow is on; then every distribution is set to the equilibrium of
- * these fields (for phi with v_n from the initial gradient, Eqs. 19, 21, 28).
- * Resets the base-step clock and the sticky error.  Returns once the
- * generated fields are on the device; the initialisation kernels run on,
- * ordered on the stream before any later call's work. */
+/* Initialise simulation `sim` from seed primitives (generated on the device,
+ * FP64 arithmetic per node, then stored in the arithmetic type): phi from
+ * the seeds (the largest of their profiles), U = U0, T = T0, rho = 1,
+ * u = u_in (1 - phi)/2 along x when the flow is on; then every distribution
+ * is set to the equilibrium of these fields (for phi with v_n from the
+ * initial gradient, Eqs. 19, 21, 28).  Resets the base-step clock and the
+ * sticky error.  Returns once the seed list has been read (the caller may
+ * reuse it); the generation and initialisation kernels run on, ordered on
+ * the stream before any later call's work. */
 lbm_status lbm_init_seed(lbm_handle h, int32_t sim, const lbm_seed* seeds, int32_t n_seeds,
                          double U0, double T0, uint64_t rng_seed);
 

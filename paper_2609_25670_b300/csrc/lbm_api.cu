@@ -153,6 +153,8 @@ struct lbm_sim {
     GraphRec bg[2];                      // the two halves of the common period
     double* staging = nullptr;           // FP64 upload / download staging (lazy)
     size_t staging_bytes = 0;
+    void* seed_dev = nullptr;            // device copy of the last seed list (lbm_init_seed)
+    int seed_cap = 0;
     std::string err;
 };
 
@@ -229,6 +231,10 @@ void free_all(lbm_sim* h) {
     }
     h->blocks.clear();
     h->bytes = 0;
+    h->staging = nullptr;
+    h->staging_bytes = 0;
+    h->seed_dev = nullptr;
+    h->seed_cap = 0;
 }
 
 size_t real_size(uint32_t prec) { return prec == LBM_PREC_F64 ? 8 : 4; }
@@ -1059,6 +1065,9 @@ lbm_status graph_replay(lbm_sim* h, SimState& s, int which) {
 template <typename R> void enqueue_diag(lbm_sim* h, SimState& s);
 
 template <typename R>
+lbm_status finish_init(lbm_sim* h, SimState& s);
+
+template <typename R>
 lbm_status upload_and_init(lbm_sim* h, SimState& s, const double* src[6], int src_dev) {
     const size_t n = (size_t)s.nx * s.ny;
     const size_t need = n * sizeof(double);
@@ -1091,6 +1100,18 @@ lbm_status upload_and_init(lbm_sim* h, SimState& s, const double* src[6], int sr
         for (int f = 0, k = 0; f < 6; ++f)
             if (dst[f] && src[f])
                 k_from_f64<R><<<grd, blk, 0, h->stream>>>(h->staging + (size_t)k++ * n, (R*)dst[f], s.nx, s.ny, s.pitch);
+    lbm_status st = finish_init<R>(h, s);
+    CK(cudaEventSynchronize(copied));
+    h->event_pool.push_back(copied);
+    return st;
+}
+
+// Everything after the macroscopic fields of buffer 0 are in place: the
+// equilibrium populations, cleared accumulators and maxima, the reference
+// solute inventory M_C(0), the clock.
+template <typename R>
+lbm_status finish_init(lbm_sim* h, SimState& s) {
+    const dim3 blk(32, 8), grd((s.nx + 31) / 32, (s.ny + 7) / 8);
     s.cur_phi = s.cur_U = s.cur_T = 0;
     for (int f = 0; f < 4; ++f) s.cur_pop[f] = 0;
     const KP<R> P = make_kp<R>(s);
@@ -1134,10 +1155,21 @@ lbm_status upload_and_init(lbm_sim* h, SimState& s, const double* src[6], int sr
     s.step = 0;
     s.initialized = true;
     s.sticky = false;
-    CK(cudaEventSynchronize(copied));
-    h->event_pool.push_back(copied);
     return LBM_OK;
 }
+
+template <typename R>
+lbm_status seed_and_init(lbm_sim* h, SimState& s, int n_seeds, double U0, double T0, uint64_t rng_seed) {
+    const dim3 blk(32, 8), grd((s.nx + 31) / 32, (s.ny + 7) / 8);
+    k_seed_fields<R><<<grd, blk, 0, h->stream>>>(s.nx, s.ny, s.pitch, (const SeedDev*)h->seed_dev, n_seeds,
+                                                 std::sqrt(2.0) * s.p.W0, (unsigned long long)rng_seed, U0, T0,
+                                                 s.p.u_in, (R*)s.phi[0], s.has_U ? (R*)s.U[0] : nullptr,
+                                                 s.has_T ? (R*)s.T[0] : nullptr, s.has_flow ? (R*)s.ux[0] : nullptr,
+                                                 s.has_flow ? (R*)s.uy[0] : nullptr, s.has_flow ? (R*)s.rho[0] : nullptr);
+    CK(cudaGetLastError());
+    return finish_init<R>(h, s);
+}
+
 
 lbm_status init_common(lbm_sim* h, int32_t sim, const double* src[6], int src_dev) {
     SimState& s = h->sims[sim];
@@ -1147,13 +1179,6 @@ lbm_status init_common(lbm_sim* h, int32_t sim, const double* src[6], int src_de
                                         : upload_and_init<float>(h, s, src, src_dev);
 }
 
-// SplitMix64 (Steele, Lea, Flood 2014), counter form: draw k of stream s
-inline uint64_t splitmix64(uint64_t seed, uint64_t k) {
-    uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
 
 template <typename R>
 lbm_status read_field(lbm_sim* h, SimState& s, uint32_t which, void* dst, int dst_dev, int as_f64) {
@@ -1399,50 +1424,34 @@ lbm_status lbm_init_seed(lbm_handle h, int32_t sim, const lbm_seed* seeds, int32
     if (sim < 0 || sim >= (int)h->sims.size()) return fail(h, LBM_E_INVALID_ARG, "sim index %d out of range", sim);
     if (n_seeds < 1 || !seeds) return fail(h, LBM_E_INVALID_ARG, "need at least one seed");
     SimState& s = h->sims[sim];
-    const int nx = s.nx, ny = s.ny;
-    const size_t n = (size_t)nx * ny;
+    std::vector<SeedDev> sd(n_seeds);
     const double sw = std::sqrt(2.0) * s.p.W0;
-    std::vector<double> phi(n, -1.0), U(n, U0), T(n, T0), ux(n, 0.0), uy(n, 0.0), rho(n, 1.0);
     for (int k = 0; k < n_seeds; ++k) {
-        const lbm_seed& sd = seeds[k];
-        if (sd.kind < LBM_SEED_CIRCLE || sd.kind > LBM_SEED_SINUSOID)
-            return fail(h, LBM_E_INVALID_ARG, "seed %d: unknown kind %d", k, sd.kind);
-        // a circle only changes nodes within r + 20 sqrt(2) W0 of its centre:
-        // beyond, tanh rounds to -1 exactly, the value phi already holds
-        int xa = 0, xb = nx, ya = 0, yb = ny;
-        if (sd.kind == LBM_SEED_CIRCLE) {
-            const double reach = std::fabs(sd.r) + 20.0 * sw + 2.0;
-            xa = (int)std::max(0.0, std::floor(sd.x - reach));
-            xb = (int)std::min((double)nx, std::ceil(sd.x + reach) + 1.0);
-            ya = (int)std::max(0.0, std::floor(sd.y - reach));
-            yb = (int)std::min((double)ny, std::ceil(sd.y + reach) + 1.0);
+        const lbm_seed& q = seeds[k];
+        if (q.kind < LBM_SEED_CIRCLE || q.kind > LBM_SEED_SINUSOID)
+            return fail(h, LBM_E_INVALID_ARG, "seed %d: unknown kind %d", k, q.kind);
+        SeedDev d{q.kind == LBM_SEED_CIRCLE ? 0 : q.kind == LBM_SEED_PLANAR ? 1 : 2, 0, s.nx, 0, s.ny,
+                  q.x, q.y, q.r, q.amp, q.waves};
+        if (q.kind == LBM_SEED_CIRCLE) {       // beyond this box tanh rounds to -1, which phi starts from
+            const double reach = std::fabs(q.r) + 20.0 * sw + 2.0;
+            d.xa = (int)std::max(0.0, std::floor(q.x - reach));
+            d.xb = (int)std::min((double)s.nx, std::ceil(q.x + reach) + 1.0);
+            d.ya = (int)std::max(0.0, std::floor(q.y - reach));
+            d.yb = (int)std::min((double)s.ny, std::ceil(q.y + reach) + 1.0);
         }
-        for (int y = ya; y < yb; ++y)
-            for (int x = xa; x < xb; ++x) {
-                const size_t i = (size_t)y * nx + x;
-                double v;
-                if (sd.kind == LBM_SEED_CIRCLE) {
-                    const double r = std::sqrt((x - sd.x) * (x - sd.x) + (y - sd.y) * (y - sd.y));
-                    v = std::tanh((sd.r - r) / sw);
-                } else if (sd.kind == LBM_SEED_PLANAR) {
-                    v = std::tanh((sd.y - y) / sw);
-                    if (sd.amp > 0.0 && std::fabs(v) < 0.99) {
-                        const double u = (double)(splitmix64(rng_seed, i) >> 11) * 0x1.0p-53;
-                        v = std::min(1.0, std::max(-1.0, v + sd.amp * (2.0 * u - 1.0)));
-                    }
-                } else {
-                    const double pi = 3.14159265358979323846;
-                    v = std::tanh((sd.y + sd.amp * std::sin(2.0 * pi * sd.waves * x / nx) - y) / sw);
-                }
-                phi[i] = (k == 0) ? v : std::max(phi[i], v);
-            }
+        sd[k] = d;
     }
-    if (s.has_flow)
-        for (size_t i = 0; i < n; ++i) ux[i] = s.p.u_in * 0.5 * (1.0 - phi[i]);
-    const double* src[6] = {phi.data(), s.has_U ? U.data() : nullptr, s.has_T ? T.data() : nullptr,
-                            s.has_flow ? ux.data() : nullptr, s.has_flow ? uy.data() : nullptr,
-                            s.has_flow ? rho.data() : nullptr};
-    return init_common(h, sim, src, 0);
+    if (h->seed_cap < n_seeds) {
+        void* p = nullptr;
+        lbm_status st = dev_alloc(h, (size_t)n_seeds * sizeof(SeedDev), &p);
+        if (st) return st;
+        h->seed_dev = p;
+        h->seed_cap = n_seeds;
+    }
+    // from pageable memory: returns once the list is staged, so sd may go
+    CK(cudaMemcpyAsync(h->seed_dev, sd.data(), (size_t)n_seeds * sizeof(SeedDev), cudaMemcpyHostToDevice, h->stream));
+    return h->precision == LBM_PREC_F64 ? seed_and_init<double>(h, s, n_seeds, U0, T0, rng_seed)
+                                        : seed_and_init<float>(h, s, n_seeds, U0, T0, rng_seed);
 }
 
 lbm_status lbm_advance(lbm_handle h, int64_t n_base_steps) {

@@ -65,6 +65,63 @@ __global__ void k_init(const KP<R> P, int q, const R* __restrict__ phi, const R*
 }
 
 // FP64 staging -> arithmetic type, with a pitch
+// Initial fields from seed primitives, FP64 arithmetic per node: phi is the
+// largest of the seeds' tanh profiles (-1 where none reaches; a circle
+// reaches the box of r + 20 sqrt(2) W0 + 2 nodes around its centre, beyond
+// which tanh rounds to -1), a planar front with amp > 0 adds uniform noise of
+// amplitude amp in its diffuse layer (|phi| < 0.99) from a counter-based
+// SplitMix64 draw per node; U = U0, T = T0, rho = 1, u_y = 0 and
+// u_x = u_in (1 - phi) / 2 when the flow is on.
+struct SeedDev {
+    int kind;                      // 0 circle, 1 planar, 2 sinusoid
+    int xa, xb, ya, yb;            // a circle's reach: the nodes [xa, xb) x [ya, yb)
+    double x, y, r, amp, waves;
+};
+__host__ __device__ inline unsigned long long splitmix64(unsigned long long seed, unsigned long long k) {
+    unsigned long long z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;    // SplitMix64 (Steele, Lea, Flood 2014)
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+template <typename R>
+__global__ void k_seed_fields(int nx, int ny, int pitch, const SeedDev* __restrict__ seeds, int n_seeds, double sw,
+                              unsigned long long rng_seed, double U0, double T0, double u_in, R* __restrict__ phi,
+                              R* __restrict__ U, R* __restrict__ T, R* __restrict__ ux, R* __restrict__ uy,
+                              R* __restrict__ rho) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const size_t i = (size_t)y * nx + x;
+    double p = -1.0;
+    for (int k = 0; k < n_seeds; ++k) {
+        const SeedDev sd = seeds[k];
+        double v;
+        if (sd.kind == 0) {
+            if (x < sd.xa || x >= sd.xb || y < sd.ya || y >= sd.yb) continue;
+            const double dx = x - sd.x, dy = y - sd.y;
+            v = tanh((sd.r - sqrt(dx * dx + dy * dy)) / sw);
+        } else if (sd.kind == 1) {
+            v = tanh((sd.y - y) / sw);
+            if (sd.amp > 0.0 && fabs(v) < 0.99) {
+                const double u = (double)(splitmix64(rng_seed, i) >> 11) * 0x1.0p-53;
+                v = fmin(1.0, fmax(-1.0, v + sd.amp * (2.0 * u - 1.0)));
+            }
+        } else {
+            const double pi = 3.14159265358979323846;
+            v = tanh((sd.y + sd.amp * sin(2.0 * pi * sd.waves * x / nx) - y) / sw);
+        }
+        p = fmax(p, v);
+    }
+    const size_t o = (size_t)y * pitch + x;
+    phi[o] = (R)p;
+    if (U) U[o] = (R)U0;
+    if (T) T[o] = (R)T0;
+    if (ux) {
+        ux[o] = (R)(u_in * 0.5 * (1.0 - p));
+        uy[o] = R(0);
+        rho[o] = R(1);
+    }
+}
+
 template <typename R>
 __global__ void k_from_f64(const double* __restrict__ src, R* __restrict__ dst, int nx, int ny, int pitch) {
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
