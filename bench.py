@@ -12,7 +12,7 @@ the FP64 path at the same configuration.  Synthetic seeded inputs.
 
 One step = one schedule period = 4 base steps (phase x4, transfer x4, U x4,
 T x1, flow x2).  Coupled-field MLUPS = lattice nodes x base steps / s / 1e6.
-The state (~20 GB in FP32) is far larger than L2, so every step streams from
+The state (13.2 GB in FP32, 8.6 GB with FP16 storage) is far larger than L2, so every step streams from
 HBM; each step is timed on the device with CUDA events on the library's
 stream.  Also reported: the 512 x 512 thermosolutal free dendrite with forced
 convection (L2-resident, flushed between steps) and the paper's D2Q9 scalar
