@@ -374,6 +374,9 @@ __host__ __device__ inline Frame frame_of(const Rect& in, int nx, int ny, int uw
 }
 
 template <typename T, int N> struct alignas(sizeof(T) * N) VecN { T v[N]; };
+// fused multiply-add in the arithmetic type
+__device__ __forceinline__ float fmaf_r(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaf_r(double a, double b, double c) { return fma(a, b, c); }
 template <typename T> using Vec4 = VecN<T, VW>;
 
 // a lane's N stored values to and from the arithmetic type; 16-bit types
@@ -652,7 +655,9 @@ __device__ __forceinline__ void scalar_vs_block(const KP<R>& P, const ST* fin, S
 // Flow vector strips (Eqs. 27-33 in the interior).  Streaming with the
 // partial bounce-back of Eq. 33: the population of direction i entering x
 // from s = x - e_i is  fLm p_i(s) + (1 - fLm) p_opp(i)(x),  fLm = (f_L(s) +
-// f_L(x)) / 2, f_L = (1 - phi)/2.  A completed row needs its own nine
+// f_L(x)) / 2, f_L = (1 - phi)/2, evaluated as p_opp + fLm (p_i - p_opp)
+// with the halves f_L / 2 carried, so that each link costs an add, a
+// subtraction and a fused multiply-add.  A completed row needs its own nine
 // post-collision values and f_L, and (p_i, f_L) of its sources in the rows
 // on either side; both are carried in registers as the warp walks.
 // ---------------------------------------------------------------------------
@@ -738,7 +743,7 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
 #pragma unroll
                 for (int i = 1; i < 9; ++i) f[i] += wq<R>(i) * rho.v[k];
             flow_post9<R>(P, f, rho.v[k], p[k]);
-            fl[k] = R(0.5) * (R(1) - ph.v[k]);                                       // f_L = (1 - phi)/2
+            fl[k] = R(0.25) * (R(1) - ph.v[k]);                                      // f_L / 2 = (1 - phi)/4
         }
         // x-shifts of the post values and of f_L
         R s1[V], s5[V], s8[V], s3[V], s6[V], s7[V], fll[V], flr[V];
@@ -760,8 +765,9 @@ __device__ __forceinline__ void flow_vstrip(const KP<R>& P, const ST* __restrict
             for (int k = 0; k < V; ++k) {
                 const R f0 = fy[k];
                 auto pull = [&](int i, R src, R fls) -> R {
-                    const R fLm = R(0.5) * (fls + f0);
-                    return fLm * src + (R(1) - fLm) * o[opp_of(i)][k];
+                    const R fLm = fls + f0;                  // the mean f_L of the link (halves carried)
+                    const R ob = o[opp_of(i)][k];
+                    return fmaf_r(fLm, src - ob, ob);
                 };
                 fn[0][k] = pull(0, o[0][k], f0);
                 fn[1][k] = pull(1, q1[k], fyl[k]);
