@@ -1160,7 +1160,7 @@ lbm_status finish_init(lbm_sim* h, SimState& s) {
 
 template <typename R>
 lbm_status seed_and_init(lbm_sim* h, SimState& s, int n_seeds, double U0, double T0, uint64_t rng_seed) {
-    const dim3 blk(32, 8), grd((s.nx + 31) / 32, (s.ny + 7) / 8);
+    const dim3 blk(32, 8), grd((s.nx + 31) / 32, (s.ny + 8 * SEED_ROWS - 1) / (8 * SEED_ROWS));
     k_seed_fields<R><<<grd, blk, 0, h->stream>>>(s.nx, s.ny, s.pitch, (const SeedDev*)h->seed_dev, n_seeds,
                                                  std::sqrt(2.0) * s.p.W0, (unsigned long long)rng_seed, U0, T0,
                                                  s.p.u_in, (R*)s.phi[0], s.has_U ? (R*)s.U[0] : nullptr,

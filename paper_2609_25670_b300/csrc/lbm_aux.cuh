@@ -83,42 +83,72 @@ __host__ __device__ inline unsigned long long splitmix64(unsigned long long seed
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
 }
+constexpr int SEED_ROWS = 8;      // row groups of blockDim.y rows per seed-field block
 template <typename R>
-__global__ void k_seed_fields(int nx, int ny, int pitch, const SeedDev* __restrict__ seeds, int n_seeds, double sw,
-                              unsigned long long rng_seed, double U0, double T0, double u_in, R* __restrict__ phi,
-                              R* __restrict__ U, R* __restrict__ T, R* __restrict__ ux, R* __restrict__ uy,
-                              R* __restrict__ rho) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= nx || y >= ny) return;
-    const size_t i = (size_t)y * nx + x;
-    double p = -1.0;
-    for (int k = 0; k < n_seeds; ++k) {
-        const SeedDev sd = seeds[k];
-        double v;
-        if (sd.kind == 0) {
-            if (x < sd.xa || x >= sd.xb || y < sd.ya || y >= sd.yb) continue;
-            const double dx = x - sd.x, dy = y - sd.y;
-            v = tanh((sd.r - sqrt(dx * dx + dy * dy)) / sw);
-        } else if (sd.kind == 1) {
-            v = tanh((sd.y - y) / sw);
-            if (sd.amp > 0.0 && fabs(v) < 0.99) {
-                const double u = (double)(splitmix64(rng_seed, i) >> 11) * 0x1.0p-53;
-                v = fmin(1.0, fmax(-1.0, v + sd.amp * (2.0 * u - 1.0)));
-            }
-        } else {
-            const double pi = 3.14159265358979323846;
-            v = tanh((sd.y + sd.amp * sin(2.0 * pi * sd.waves * x / nx) - y) / sw);
+__global__ void __launch_bounds__(256)
+k_seed_fields(int nx, int ny, int pitch, const SeedDev* __restrict__ seeds, int n_seeds, double sw,
+              unsigned long long rng_seed, double U0, double T0, double u_in, R* __restrict__ phi,
+              R* __restrict__ U, R* __restrict__ T, R* __restrict__ ux, R* __restrict__ uy, R* __restrict__ rho) {
+    // a block covers blockDim.x x (SEED_ROWS blockDim.y) nodes; it first lists
+    // the seeds that can reach its region (64 at a time)
+    __shared__ int list[64];
+    __shared__ int cnt;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    const int bx0 = blockIdx.x * blockDim.x, by0 = blockIdx.y * blockDim.y * SEED_ROWS;
+    const int bx1 = bx0 + blockDim.x, by1 = by0 + blockDim.y * SEED_ROWS;
+    double p[SEED_ROWS];
+#pragma unroll
+    for (int g = 0; g < SEED_ROWS; ++g) p[g] = -1.0;
+    for (int base = 0; base < n_seeds; base += 64) {
+        if (t == 0) cnt = 0;
+        __syncthreads();
+        if (t < 64 && base + t < n_seeds) {
+            const SeedDev& q = seeds[base + t];
+            if (q.kind != 0 || (q.xa < bx1 && q.xb > bx0 && q.ya < by1 && q.yb > by0)) list[atomicAdd(&cnt, 1)] = base + t;
         }
-        p = fmax(p, v);
+        __syncthreads();
+        const int c = cnt;
+        for (int j = 0; x < nx && j < c; ++j) {   // the largest profile: the order of the list does not matter
+            const SeedDev sd = seeds[list[j]];
+#pragma unroll
+            for (int g = 0; g < SEED_ROWS; ++g) {
+                const int y = by0 + g * blockDim.y + threadIdx.y;
+                if (y >= ny) break;
+                double v;
+                if (sd.kind == 0) {
+                    if (x < sd.xa || x >= sd.xb || y < sd.ya || y >= sd.yb) continue;
+                    const double dx = x - sd.x, dy = y - sd.y;
+                    v = tanh((sd.r - sqrt(dx * dx + dy * dy)) / sw);
+                } else if (sd.kind == 1) {
+                    v = tanh((sd.y - y) / sw);
+                    if (sd.amp > 0.0 && fabs(v) < 0.99) {
+                        const double u = (double)(splitmix64(rng_seed, (size_t)y * nx + x) >> 11) * 0x1.0p-53;
+                        v = fmin(1.0, fmax(-1.0, v + sd.amp * (2.0 * u - 1.0)));
+                    }
+                } else {
+                    const double pi = 3.14159265358979323846;
+                    v = tanh((sd.y + sd.amp * sin(2.0 * pi * sd.waves * x / nx) - y) / sw);
+                }
+                p[g] = fmax(p[g], v);
+            }
+        }
+        __syncthreads();                          // before the list is refilled
     }
-    const size_t o = (size_t)y * pitch + x;
-    phi[o] = (R)p;
-    if (U) U[o] = (R)U0;
-    if (T) T[o] = (R)T0;
-    if (ux) {
-        ux[o] = (R)(u_in * 0.5 * (1.0 - p));
-        uy[o] = R(0);
-        rho[o] = R(1);
+    if (x >= nx) return;
+#pragma unroll
+    for (int g = 0; g < SEED_ROWS; ++g) {
+        const int y = by0 + g * blockDim.y + threadIdx.y;
+        if (y >= ny) break;
+        const size_t o = (size_t)y * pitch + x;
+        phi[o] = (R)p[g];
+        if (U) U[o] = (R)U0;
+        if (T) T[o] = (R)T0;
+        if (ux) {
+            ux[o] = (R)(u_in * 0.5 * (1.0 - p[g]));
+            uy[o] = R(0);
+            rho[o] = R(1);
+        }
     }
 }
 
@@ -170,7 +200,12 @@ __global__ void k_out(const KP<R> P, int which, const R* __restrict__ phi, const
 // ---------------------------------------------------------------------------
 // part[b*3 + 0] = sum C/C_inf, [1] = sum H, [2] = non-finite count, for block b
 // Ulo: the residual plane of the compensated U macro (type Lo, pitch layout),
-// added to U in the solute sum, or null.
+// added to U in the solute sum, or null.  Block b sums rows b, b + gridDim.x,
+// ... (threads across each row), so the order is fixed for a given lattice.
+// FP64 arithmetic is a small fraction of the FP32 rate on this GPU: with an
+// FP32 state the solute term (the conservation diagnostic, Eq. 39) is formed
+// in FP64 from the stored values, the enthalpy term in FP32, and the
+// non-finite test runs on the stored values; both sums accumulate in FP64.
 template <typename R, typename Lo = R>
 __global__ void __launch_bounds__(256)
 k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ Um, const R* __restrict__ Tm,
@@ -178,19 +213,25 @@ k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ U
                const Lo* __restrict__ Ulo = nullptr) {
     __shared__ double s[3][8];
     double mc = 0.0, h = 0.0, bad = 0.0;
-    const long long nn = (long long)P.nx * P.ny;
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(n / P.nx), x = (int)(n - (long long)y * P.nx);
-        const size_t node = (size_t)y * P.pitch + x;
-        const double ph = (double)phi[node];
-        const double U = P.has_U ? (double)Um[node] + (Ulo ? (double)Cvt<Lo>::ld(Ulo[node]) : 0.0) : 0.0;
-        const double T = P.has_T ? (double)Tm[node] : 0.0;
-        const double vx = P.has_flow ? (double)uxm[node] : 0.0, vy = P.has_flow ? (double)uym[node] : 0.0;
-        const double k = (double)P.k;
-        if (P.has_U) mc += 0.5 * (1.0 + (1.0 - k) * U) * ((1.0 + k) - (1.0 - k) * ph);
-        if (P.has_T)
-            h += (0.5 * (1.0 + ph) * (double)P.cS + 0.5 * (1.0 - ph) * (double)P.cL) * T - 0.5 * (double)P.rhoL_Lh * ph;
-        if (!isfinite(ph) || !isfinite(U) || !isfinite(T) || !isfinite(vx) || !isfinite(vy)) bad += 1.0;
+    const double omk = 1.0 - (double)P.k, opk = 1.0 + (double)P.k;
+    for (int y = blockIdx.x; y < P.ny; y += gridDim.x) {
+        const size_t row = (size_t)y * P.pitch;
+        for (int x = threadIdx.x; x < P.nx; x += blockDim.x) {
+            const size_t node = row + x;
+            const R ph = phi[node];
+            const R U = P.has_U ? Um[node] : R(0);
+            const R T = P.has_T ? Tm[node] : R(0);
+            const R vx = P.has_flow ? uxm[node] : R(0), vy = P.has_flow ? uym[node] : R(0);
+            if (P.has_U) {
+                const double Ud = (double)U + (Ulo ? (double)Cvt<Lo>::ld(Ulo[node]) : 0.0);
+                mc += 0.5 * fma(omk, Ud, 1.0) * fma(-omk, (double)ph, opk);
+            }
+            if (P.has_T) {
+                const R ht = (R(0.5) * (R(1) + ph) * P.cS + R(0.5) * (R(1) - ph) * P.cL) * T - R(0.5) * P.rhoL_Lh * ph;
+                h += (double)ht;
+            }
+            if (!isfinite(ph) || !isfinite(U) || !isfinite(T) || !isfinite(vx) || !isfinite(vy)) bad += 1.0;
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
