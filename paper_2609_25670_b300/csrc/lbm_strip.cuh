@@ -315,7 +315,9 @@ __device__ __forceinline__ void scalar_strip_block(const KP<R>& P, const ST* fin
 // row -- 512 contiguous bytes per warp -- and the x-shifts of the streaming
 // and of the phi stencil need one shuffle per direction for four nodes.
 // Lane l holds columns 120 s + 4 l .. +3; lanes 1..30 are the strip's 120
-// output columns, lanes 0 and 31 its neighbours.  Vector strips cover only
+// output columns, lanes 0 and 31 its neighbours.  The 16-bit flow strip and
+// the 16-bit D2Q5 phase strip, bound by instruction issue and live state,
+// take two nodes per lane instead (60 output columns).  Vector strips cover only
 // the interior rectangle [VX0, x1) x [VY0, y1) of a lattice (no index maps,
 // no walls, rows padded to 32 elements so every vector is aligned); the 1-wide
 // strips of the same launch complete the frame around it.
@@ -329,9 +331,9 @@ struct VGeo {
     int nxv, nyv;                  // vector strips across / down
     Rect in;                       // the interior they cover
 };
-// V: nodes per lane (VW for every strip but the 16-bit flow strip, which
-// takes two): strip s covers columns 30 V s .. 30 V s + 32 V - 1 and writes
-// the middle 30 V of them
+// V: nodes per lane (VW, or two for the 16-bit flow and 16-bit D2Q5 phase
+// strips): strip s covers columns 30 V s .. 30 V s + 32 V - 1 and writes the
+// middle 30 V of them
 __host__ __device__ inline VGeo vgeo(int nx, int ny, int H, int V = VW) {
     VGeo g;
     g.nxv = nx >= 32 * V ? (nx - 32 * V) / (30 * V) + 1 : 0;        // columns 120 s .. 120 s + 127 inside (V = 4)
@@ -1435,8 +1437,8 @@ k_flow_vs(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restric
           R* __restrict__ ux_out, R* __restrict__ uy_out, R* __restrict__ rho_out) {
     flow_vs_block<R, ST, DEV, H>(*P, fin, fout, phi, ux_in, uy_in, rho_in, ux_out, uy_out, rho_out, blockIdx.x);
 }
-// the same with 16-bit populations, three blocks (12 warps) per SM: 168
-// registers and the three-row ring fit three blocks where two fit before
+// the same with 16-bit populations, two nodes per lane and five blocks
+// (20 warps) per SM: 96 registers and the three-row ring
 template <typename R, typename ST, bool DEV, int H>
 __global__ void __launch_bounds__(32 * FVW, 5)
 k_flow_vs16(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout, const R* __restrict__ phi,
