@@ -79,8 +79,6 @@ def algo_bytes(prec="f32", q=9, ori=False):
     }
 
 
-ALGO_BYTES = algo_bytes("f32")
-
 
 def transport_bytes(tr, u, t, f, has_T=True, has_flow=True, prec="f32"):
     """Algorithmic bytes per node of one fused transport launch: the transfer
