@@ -204,16 +204,23 @@ __global__ void k_out(const KP<R> P, int which, const R* __restrict__ phi, const
 // ... (threads across each row), so the order is fixed for a given lattice.
 // FP64 arithmetic is a small fraction of the FP32 rate on this GPU: with an
 // FP32 state the solute term (the conservation diagnostic, Eq. 39) is formed
-// in FP64 from the stored values, the enthalpy term in FP32, and the
-// non-finite test runs on the stored values; both sums accumulate in FP64.
+// in FP64 from the stored macro values (the compensated macro's residual
+// plane, ~1e-8 of them, in FP32), the enthalpy term in FP32, and the
+// non-finite test runs on the stored values; the sums accumulate in FP64.
 template <typename R, typename Lo = R>
 __global__ void __launch_bounds__(256)
 k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ Um, const R* __restrict__ Tm,
                const R* __restrict__ uxm, const R* __restrict__ uym, double* __restrict__ part,
                const Lo* __restrict__ Ulo = nullptr) {
     __shared__ double s[3][8];
+    // mc: twice the solute sum of the stored macros (the factor 1/2 of C is
+    // applied once at the end: exact); mlo: the residual plane's part,
+    // (1 - k) lo ((1 + k) - (1 - k) phi), a term ~1e-8 of the rest, in the
+    // arithmetic type
     double mc = 0.0, h = 0.0, bad = 0.0;
+    R mlo = R(0);
     const double omk = 1.0 - (double)P.k, opk = 1.0 + (double)P.k;
+    const R omkR = R(1) - P.k, opkR = R(1) + P.k;
     for (int y = blockIdx.x; y < P.ny; y += gridDim.x) {
         const size_t row = (size_t)y * P.pitch;
         for (int x = threadIdx.x; x < P.nx; x += blockDim.x) {
@@ -223,8 +230,8 @@ k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ U
             const R T = P.has_T ? Tm[node] : R(0);
             const R vx = P.has_flow ? uxm[node] : R(0), vy = P.has_flow ? uym[node] : R(0);
             if (P.has_U) {
-                const double Ud = (double)U + (Ulo ? (double)Cvt<Lo>::ld(Ulo[node]) : 0.0);
-                mc += 0.5 * fma(omk, Ud, 1.0) * fma(-omk, (double)ph, opk);
+                mc += fma(omk, (double)U, 1.0) * fma(-omk, (double)ph, opk);
+                if (Ulo) mlo += omkR * (R)Cvt<Lo>::ld(Ulo[node]) * (opkR - omkR * ph);
             }
             if (P.has_T) {
                 const R ht = (R(0.5) * (R(1) + ph) * P.cS + R(0.5) * (R(1) - ph) * P.cL) * T - R(0.5) * P.rhoL_Lh * ph;
@@ -233,6 +240,7 @@ k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ U
             if (!isfinite(ph) || !isfinite(U) || !isfinite(T) || !isfinite(vx) || !isfinite(vy)) bad += 1.0;
         }
     }
+    mc = 0.5 * (mc + (double)mlo);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mc += __shfl_xor_sync(0xffffffffu, mc, o);
