@@ -143,7 +143,7 @@ def step_bytes_md(p, prec, fused, q):
 # grain angles), times the nodes of a launch.  Reported only while the
 # kernel sources hash to TRAFFIC_SOURCE_SHA; after any change of the code
 # the traffic is null until re-measured.
-TRAFFIC_SOURCE_SHA = "2ca17f737faf45e9"
+TRAFFIC_SOURCE_SHA = "1b288512306de817"
 TRAFFIC_PER_LAUNCH_512 = {}
 # one launch per kernel of the 8192^2 multi-dendrite workload (D2Q5 phase,
 # U, T; grain angles), single-pass counters (profiles/
@@ -151,9 +151,9 @@ TRAFFIC_PER_LAUNCH_512 = {}
 # bytes within 1 %.  A 2048^2 capture keeps most of a launch's writes in the
 # 126 MB L2 until after the kernel, so it undercounts them.
 TRAFFIC_PER_NODE = {
-    "f32:q5:flow:1016": 92.77, "f32:q5:phase:1016:ori": 52.25, "f32:q5:phase:1032:ori": 52.45,
-    "f32:q5:scalar_T:1016": 36.00, "f32:q5:scalar_U:1016": 40.06, "f32:q5:transfer:1016": 23.83,
-    "f16dev:q5:flow:1032": 60.73, "f16dev:q5:phase:1016:ori": 36.13, "f16dev:q5:phase:1032:ori": 36.17,
+    "f32:q5:flow:1016": 92.75, "f32:q5:phase:1016:ori": 52.43, "f32:q5:phase:1032:ori": 52.97,
+    "f32:q5:scalar_T:1016": 36.01, "f32:q5:scalar_U:1016": 40.07, "f32:q5:transfer:1016": 23.84,
+    "f16dev:q5:flow:1032": 60.75, "f16dev:q5:phase:1016:ori": 36.13, "f16dev:q5:phase:1032:ori": 36.17,
     "f16dev:q5:scalar_T:1032": 28.11, "f16dev:q5:scalar_U:1032": 32.16, "f16dev:q5:transfer:1016": 23.84,
 }
 

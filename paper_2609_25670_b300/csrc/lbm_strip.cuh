@@ -1099,7 +1099,9 @@ template <typename R, int Q = 9, typename ST = R> struct PRing {
     static constexpr int V = phase_nodes_per_lane<Q, ST>();
     static constexpr int EB = V * (int)sizeof(R);            // bytes of one lane's entry
     static constexpr int SLOT = PA<Q>::N * 32 * EB;          // one row
-    static constexpr int D = (sizeof(ST) == 2 && Q == 5) ? 3 : sizeof(R) == 8 ? 2 : 4;
+    // three rows on D2Q5 with 16-bit or FP32 storage (four blocks per SM fit
+    // the ring), two in FP64, four on D2Q9
+    static constexpr int D = (sizeof(ST) <= 4 && Q == 5) ? 3 : sizeof(R) == 8 ? 2 : 4;
     static constexpr int BYTES = D * SLOT;
 };
 
@@ -1402,9 +1404,19 @@ k_phase_vs16(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __rest
              const long long* __restrict__ clock, long long step_off) {
     phase_vs_block<R, ST, DEV, H, Q>(*P, fin, fout, phi, phin, Um, Tm, clock, step_off, blockIdx.x);
 }
+// the same with FP32 D2Q5 populations, four blocks (16 warps) per SM: the
+// three-row ring and 128 registers (146 unbounded, three blocks)
+template <typename R, typename ST, bool DEV, int H, int Q>
+__global__ void __launch_bounds__(32 * PVW, 4)
+k_phase_vs32(const KP<R>* __restrict__ P, const ST* __restrict__ fin, ST* __restrict__ fout, const R* __restrict__ phi,
+             R* __restrict__ phin, const R* __restrict__ Um, const R* __restrict__ Tm,
+             const long long* __restrict__ clock, long long step_off) {
+    phase_vs_block<R, ST, DEV, H, Q>(*P, fin, fout, phi, phin, Um, Tm, clock, step_off, blockIdx.x);
+}
 template <typename R, typename ST, bool DEV, int H, int Q>
 constexpr auto phase_vs_kernel() {
     if constexpr (sizeof(ST) == 2 && Q == 5) return &k_phase_vs16<R, ST, DEV, H, Q>;
+    else if constexpr (sizeof(ST) == 4 && Q == 5) return &k_phase_vs32<R, ST, DEV, H, Q>;
     else return &k_phase_vs<R, ST, DEV, H, Q>;
 }
 template <typename R, typename ST, bool DEV, int H, int Q>
