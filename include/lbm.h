@@ -136,7 +136,10 @@ typedef struct {
 
 /* Diagnostics of one simulation (Sec. 4.1 tip histories, Sec. 4.4 ablation).
  *   M_C     = sum over nodes of C/C_inf = (1 + (1-k) U)((1+k) - (1-k) phi)/2 (Eq. 5), FP64 sum
- *   H_total = sum of (rho Cp)_eff(phi) T - rho_L L_h phi / 2, FP64 sum
+ *             (FP32 states: each node's term and each thread's partial sum as a
+ *             pair of FP32 numbers, ~2^-46 relative; the totals FP64)
+ *   H_total = sum of (rho Cp)_eff(phi) T - rho_L L_h phi / 2, FP64 sum (FP32
+ *             states: the per-thread partial sums as pairs of FP32 numbers)
  *   S_phi   = max |Delta U_pc| over nodes and phase steps since the previous call
  *   J_U     = max |U_post - U_pre| over the phase-change applications since the
  *             previous call (equals S_phi under instantaneous coupling)
@@ -214,7 +217,7 @@ lbm_status lbm_advance(lbm_handle h, int64_t n_base_steps);
 lbm_status lbm_fields(lbm_handle h, int32_t sim, uint32_t which, void* dst, int32_t dst_is_device,
                       int32_t as_f64);
 
-/* Reduce the diagnostics of simulation `sim` on the device (FP64 sums,
+/* Reduce the diagnostics of simulation `sim` on the device (FP64 totals,
  * deterministic order) and return them; resets the S_phi / J_U maxima.
  * Synchronises the stream.  Returns NONFINITE (and sets the sticky state)
  * when a non-finite value is present; *out is filled in either case. */

@@ -153,8 +153,8 @@ struct lbm_sim {
     GraphRec bg[2];                      // the two halves of the common period
     double* staging = nullptr;           // FP64 upload / download staging (lazy)
     size_t staging_bytes = 0;
-    void* seed_dev = nullptr;            // device copy of the last seed list (lbm_init_seed)
-    int seed_cap = 0;
+    void* seed_dev = nullptr;            // device copy of the last seed list and its block list (lbm_init_seed)
+    size_t seed_bytes = 0;
     std::string err;
 };
 
@@ -234,7 +234,7 @@ void free_all(lbm_sim* h) {
     h->staging = nullptr;
     h->staging_bytes = 0;
     h->seed_dev = nullptr;
-    h->seed_cap = 0;
+    h->seed_bytes = 0;
 }
 
 size_t real_size(uint32_t prec) { return prec == LBM_PREC_F64 ? 8 : 4; }
@@ -1064,8 +1064,10 @@ lbm_status graph_replay(lbm_sim* h, SimState& s, int which) {
 
 template <typename R> void enqueue_diag(lbm_sim* h, SimState& s);
 
+// seeded: the macroscopic fields come from lbm_init_seed (U = U0, T = T0,
+// u_y = 0, rho = 1 everywhere)
 template <typename R>
-lbm_status finish_init(lbm_sim* h, SimState& s);
+lbm_status finish_init(lbm_sim* h, SimState& s, bool seeded = false, double U0 = 0.0, double T0 = 0.0);
 
 template <typename R>
 lbm_status upload_and_init(lbm_sim* h, SimState& s, const double* src[6], int src_dev) {
@@ -1110,7 +1112,7 @@ lbm_status upload_and_init(lbm_sim* h, SimState& s, const double* src[6], int sr
 // equilibrium populations, cleared accumulators and maxima, the reference
 // solute inventory M_C(0), the clock.
 template <typename R>
-lbm_status finish_init(lbm_sim* h, SimState& s) {
+lbm_status finish_init(lbm_sim* h, SimState& s, bool seeded, double U0, double T0) {
     const dim3 blk(32, 8), grd((s.nx + 31) / 32, (s.ny + 7) / 8);
     s.cur_phi = s.cur_U = s.cur_T = 0;
     for (int f = 0; f < 4; ++f) s.cur_pop[f] = 0;
@@ -1123,19 +1125,21 @@ lbm_status finish_init(lbm_sim* h, SimState& s) {
                 k_init<R, R, false><<<grd, blk, 0, h->stream>>>(P, h->q, (const R*)s.phi[0], (const R*)s.U[0], (const R*)s.T[0],
                                                                (const R*)s.ux[0], (const R*)s.uy[0], (const R*)s.rho[0],
                                                                (R*)s.pops[FP][0], (R*)s.pops[FU][0], (R*)s.pops[FT][0],
-                                                               (R*)s.pops[FF][0]);
+                                                               (R*)s.pops[FF][0], (int)seeded, (R)U0, (R)T0);
                 break;
             case LBM_PREC_F16_DEV:
                 k_init<float, __half, true><<<grd, blk, 0, h->stream>>>(
                     make_kp<float>(s), h->q, (const float*)s.phi[0], (const float*)s.U[0], (const float*)s.T[0],
                     (const float*)s.ux[0], (const float*)s.uy[0], (const float*)s.rho[0], (__half*)s.pops[FP][0],
-                    (__half*)s.pops[FU][0], (__half*)s.pops[FT][0], (__half*)s.pops[FF][0]);
+                    (__half*)s.pops[FU][0], (__half*)s.pops[FT][0], (__half*)s.pops[FF][0], (int)seeded, (float)U0,
+                    (float)T0);
                 break;
             default:
                 k_init<float, __nv_bfloat16, true><<<grd, blk, 0, h->stream>>>(
                     make_kp<float>(s), h->q, (const float*)s.phi[0], (const float*)s.U[0], (const float*)s.T[0],
                     (const float*)s.ux[0], (const float*)s.uy[0], (const float*)s.rho[0], (__nv_bfloat16*)s.pops[FP][0],
-                    (__nv_bfloat16*)s.pops[FU][0], (__nv_bfloat16*)s.pops[FT][0], (__nv_bfloat16*)s.pops[FF][0]);
+                    (__nv_bfloat16*)s.pops[FU][0], (__nv_bfloat16*)s.pops[FT][0], (__nv_bfloat16*)s.pops[FF][0],
+                    (int)seeded, (float)U0, (float)T0);
         }
     }
     (void)P;
@@ -1158,16 +1162,37 @@ lbm_status finish_init(lbm_sim* h, SimState& s) {
     return LBM_OK;
 }
 
+// n_listed: the number of seed-field blocks in the block list that follows
+// the seeds in h->seed_dev (the lattice is first filled with the values no
+// seed reaches), or -1 to run every block.
 template <typename R>
-lbm_status seed_and_init(lbm_sim* h, SimState& s, int n_seeds, double U0, double T0, uint64_t rng_seed) {
-    const dim3 blk(32, 8), grd((s.nx + 31) / 32, (s.ny + 8 * SEED_ROWS - 1) / (8 * SEED_ROWS));
-    k_seed_fields<R><<<grd, blk, 0, h->stream>>>(s.nx, s.ny, s.pitch, (const SeedDev*)h->seed_dev, n_seeds,
-                                                 std::sqrt(2.0) * s.p.W0, (unsigned long long)rng_seed, U0, T0,
-                                                 s.p.u_in, (R*)s.phi[0], s.has_U ? (R*)s.U[0] : nullptr,
-                                                 s.has_T ? (R*)s.T[0] : nullptr, s.has_flow ? (R*)s.ux[0] : nullptr,
-                                                 s.has_flow ? (R*)s.uy[0] : nullptr, s.has_flow ? (R*)s.rho[0] : nullptr);
+lbm_status seed_and_init(lbm_sim* h, SimState& s, int n_seeds, int n_listed, double U0, double T0,
+                         uint64_t rng_seed) {
+    const dim3 blk(SEED_BX, SEED_BY), grd((s.nx + SEED_BX - 1) / SEED_BX, (s.ny + SEED_BH - 1) / SEED_BH);
+    R* const phi = (R*)s.phi[0];
+    R* const U = s.has_U ? (R*)s.U[0] : nullptr;
+    R* const T = s.has_T ? (R*)s.T[0] : nullptr;
+    R* const ux = s.has_flow ? (R*)s.ux[0] : nullptr;
+    R* const uy = s.has_flow ? (R*)s.uy[0] : nullptr;
+    R* const rho = s.has_flow ? (R*)s.rho[0] : nullptr;
+    const SeedDev* sd = (const SeedDev*)h->seed_dev;
+    const double sw = std::sqrt(2.0) * s.p.W0;
+    if (n_listed < 0) {
+        k_seed_fields<R><<<grd, blk, 0, h->stream>>>(s.nx, s.ny, s.pitch, sd, n_seeds, nullptr, (int)grd.x, sw,
+                                                     (unsigned long long)rng_seed, U0, T0, s.p.u_in, phi, U, T,
+                                                     ux, uy, rho);
+    } else {
+        const R ux_liquid = (R)(s.p.u_in * 0.5 * (1.0 - (-1.0)));      // the profile's u_x at phi = -1
+        k_seed_fill<R><<<grd, blk, 0, h->stream>>>(s.nx, s.ny, s.pitch, (R)U0, (R)T0, ux_liquid, phi, U, T, ux,
+                                                   uy, rho);
+        if (n_listed > 0)
+            k_seed_fields<R><<<n_listed, blk, 0, h->stream>>>(s.nx, s.ny, s.pitch, sd, n_seeds,
+                                                              (const int*)(sd + n_seeds), (int)grd.x, sw,
+                                                              (unsigned long long)rng_seed, U0, T0, s.p.u_in, phi,
+                                                              U, T, ux, uy, rho);
+    }
     CK(cudaGetLastError());
-    return finish_init<R>(h, s);
+    return finish_init<R>(h, s, true, U0, T0);
 }
 
 
@@ -1244,7 +1269,7 @@ void enqueue_diag(lbm_sim* h, SimState& s) {
             k_diag_partial<R><<<s.diag_blocks, 256, 0, h->stream>>>(
                 P, (const R*)s.phi[s.cur_phi], Um, Tm, (const R*)s.ux[fc], (const R*)s.uy[fc], s.part);
         }
-        k_diag_final<R><<<1, 128, 0, h->stream>>>(P, s.part, s.diag_blocks, (const R*)s.phi[s.cur_phi], s.p.tip_cx,
+        k_diag_final<R><<<1, DIAG_FINAL_THREADS, 0, h->stream>>>(P, s.part, s.diag_blocks, (const R*)s.phi[s.cur_phi], s.p.tip_cx,
                                                  s.p.tip_cy, s.smax, s.dout);
     }
 }
@@ -1441,17 +1466,37 @@ lbm_status lbm_init_seed(lbm_handle h, int32_t sim, const lbm_seed* seeds, int32
         }
         sd[k] = d;
     }
-    if (h->seed_cap < n_seeds) {
+    // the seed-field blocks that a circle's box reaches (every block when a
+    // planar or sinusoidal seed is present: n_listed = -1)
+    const int nbx = (s.nx + SEED_BX - 1) / SEED_BX, nby = (s.ny + SEED_BH - 1) / SEED_BH;
+    bool everywhere = false;
+    std::vector<unsigned char> mark((size_t)nbx * nby, 0);
+    for (const SeedDev& d : sd) {
+        if (d.kind != 0) { everywhere = true; break; }
+        if (d.xb <= d.xa || d.yb <= d.ya) continue;
+        for (int by = d.ya / SEED_BH; by <= (d.yb - 1) / SEED_BH; ++by)
+            for (int bx = d.xa / SEED_BX; bx <= (d.xb - 1) / SEED_BX; ++bx) mark[(size_t)by * nbx + bx] = 1;
+    }
+    std::vector<int> listed;
+    if (!everywhere)
+        for (size_t b = 0; b < mark.size(); ++b)
+            if (mark[b]) listed.push_back((int)b);
+    const size_t sbytes = (size_t)n_seeds * sizeof(SeedDev), lbytes = listed.size() * sizeof(int);
+    if (h->seed_bytes < sbytes + lbytes) {
         void* p = nullptr;
-        lbm_status st = dev_alloc(h, (size_t)n_seeds * sizeof(SeedDev), &p);
+        lbm_status st = dev_alloc(h, sbytes + lbytes, &p);
         if (st) return st;
         h->seed_dev = p;
-        h->seed_cap = n_seeds;
+        h->seed_bytes = sbytes + lbytes;
     }
-    // from pageable memory: returns once the list is staged, so sd may go
-    CK(cudaMemcpyAsync(h->seed_dev, sd.data(), (size_t)n_seeds * sizeof(SeedDev), cudaMemcpyHostToDevice, h->stream));
-    return h->precision == LBM_PREC_F64 ? seed_and_init<double>(h, s, n_seeds, U0, T0, rng_seed)
-                                        : seed_and_init<float>(h, s, n_seeds, U0, T0, rng_seed);
+    std::vector<unsigned char> up(sbytes + lbytes);
+    std::memcpy(up.data(), sd.data(), sbytes);
+    if (lbytes) std::memcpy(up.data() + sbytes, listed.data(), lbytes);
+    // from pageable memory: returns once the bytes are staged, so up may go
+    CK(cudaMemcpyAsync(h->seed_dev, up.data(), sbytes + lbytes, cudaMemcpyHostToDevice, h->stream));
+    const int n_listed = everywhere ? -1 : (int)listed.size();
+    return h->precision == LBM_PREC_F64 ? seed_and_init<double>(h, s, n_seeds, n_listed, U0, T0, rng_seed)
+                                        : seed_and_init<float>(h, s, n_seeds, n_listed, U0, T0, rng_seed);
 }
 
 lbm_status lbm_advance(lbm_handle h, int64_t n_base_steps) {
@@ -1880,7 +1925,7 @@ lbm_status noalloc_diag(const SimState& s, const void* phi, const void* U, const
     CK(cudaMemsetAsync(smax, 0, 2 * sizeof(unsigned long long), st));   // the maxima must start at zero
     k_diag_partial<R><<<blocks, 256, 0, st>>>(P, (const R*)phi, (const R*)U, (const R*)T, (const R*)ux,
                                               (const R*)uy, part);
-    k_diag_final<R><<<1, 128, 0, st>>>(P, part, blocks, (const R*)phi, s.p.tip_cx, s.p.tip_cy, smax, res);
+    k_diag_final<R><<<1, DIAG_FINAL_THREADS, 0, st>>>(P, part, blocks, (const R*)phi, s.p.tip_cx, s.p.tip_cy, smax, res);
     CK(cudaGetLastError());
     double r[9];
     CK(cudaMemcpyAsync(r, res, sizeof r, cudaMemcpyDeviceToHost, st));

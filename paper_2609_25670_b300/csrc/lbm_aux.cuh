@@ -9,12 +9,14 @@ namespace lbmk {
 // Initial distributions f = f_eq of the macroscopic fields (Eqs. 19, 21, 28);
 // for U and T their first moments, the stored state of those fields.  q: the
 // velocities of the phase lattice (9, or 5 for D2Q5: populations 1..4 only).
+// seeded: the fields come from seed primitives, so U = U0, T = T0, u_y = 0
+// and rho = 1 on every node and only phi and u_x are read.
 // ---------------------------------------------------------------------------
 template <typename R, typename ST, bool DEV>
 __global__ void k_init(const KP<R> P, int q, const R* __restrict__ phi, const R* __restrict__ Um,
                        const R* __restrict__ Tm, const R* __restrict__ uxm, const R* __restrict__ uym,
                        const R* __restrict__ rhom, ST* __restrict__ fphi, ST* __restrict__ fU, ST* __restrict__ fT,
-                       ST* __restrict__ fF) {
+                       ST* __restrict__ fF, int seeded, R U0, R T0) {
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
     if (gx >= P.nx || gy >= P.ny) return;
     const size_t node = (size_t)gy * P.pitch + gx;
@@ -30,8 +32,11 @@ __global__ void k_init(const KP<R> P, int q, const R* __restrict__ phi, const R*
     else aniso(gxv, gyv, P.eps, as, Nx, Ny);
     const R bx = -P.dtp * P.W0sq_tau0 * Nx, by = -P.dtp * P.W0sq_tau0 * Ny;
     const R ph = s[1][1];
-    R vx = R(0), vy = R(0);
-    if (P.has_flow) { vx = uxm[node]; vy = uym[node]; }
+    R vx = R(0), vy = R(0), rho = R(1);
+    if (P.has_flow) {
+        vx = uxm[node];
+        if (!seeded) { vy = uym[node]; rho = rhom[node]; }
+    }
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         if (i >= q) break;
@@ -42,7 +47,7 @@ __global__ void k_init(const KP<R> P, int q, const R* __restrict__ phi, const R*
     // U, T: the first moment of f_eq of Eq. 19, sum_i e_i 3 w_i chi dt (e_i . u)
     // = dt chi u (sum_i w_i e_i e_i = I / 3 on D2Q9 and on D2Q5)
     if (P.has_U) {
-        const R U = Um[node];
+        const R U = seeded ? U0 : Um[node];
         fU[node] = Cvt<ST>::st(P.dtU * U * vx);
         fU[(size_t)P.plane + node] = Cvt<ST>::st(P.dtU * U * vy);
         if constexpr (Compensated<R>::value) {          // residual of the compensated macro
@@ -51,20 +56,19 @@ __global__ void k_init(const KP<R> P, int q, const R* __restrict__ phi, const R*
         }
     }
     if (P.has_T) {
-        const R T = Tm[node];
+        const R T = seeded ? T0 : Tm[node];
         fT[node] = Cvt<ST>::st(P.dtT * T * vx);
         fT[(size_t)P.plane + node] = Cvt<ST>::st(P.dtT * T * vy);
     }
     if (P.has_flow) {
         R fe[9];
-        feq_flow<R>(rhom[node], uxm[node], uym[node], P.cF, fe);                          // Eq. 28
+        feq_flow<R>(rho, vx, vy, P.cF, fe);                                                // Eq. 28
 #pragma unroll
         for (int i = 1; i < 9; ++i)
-            fF[(size_t)(i - 1) * P.plane + node] = Cvt<ST>::st(DEV ? fe[i] - wq<R>(i) * rhom[node] : fe[i]);
+            fF[(size_t)(i - 1) * P.plane + node] = Cvt<ST>::st(DEV ? fe[i] - wq<R>(i) * rho : fe[i]);
     }
 }
 
-// FP64 staging -> arithmetic type, with a pitch
 // Initial fields from seed primitives, FP64 arithmetic per node: phi is the
 // largest of the seeds' tanh profiles (-1 where none reaches; a circle
 // reaches the box of r + 20 sqrt(2) W0 + 2 nodes around its centre, beyond
@@ -83,20 +87,51 @@ __host__ __device__ inline unsigned long long splitmix64(unsigned long long seed
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
 }
-constexpr int SEED_ROWS = 8;      // row groups of blockDim.y rows per seed-field block
+// a seed-field block: SEED_BX x SEED_BY threads over SEED_BX columns and
+// SEED_BY * SEED_ROWS rows
+constexpr int SEED_BX = 32, SEED_BY = 8, SEED_ROWS = 8;
+constexpr int SEED_BH = SEED_BY * SEED_ROWS;
+
+// The values of a node that no seed reaches, on every node: phi = -1, U = U0,
+// T = T0, u_x = u_in (the FP64 profile at phi = -1, rounded on the host),
+// u_y = 0, rho = 1.  k_seed_fields then rewrites the blocks that seeds
+// reach.  (The FP64 profile code sizes that kernel's registers, three blocks
+// per SM, which would leave this store stream at half the bandwidth.)
 template <typename R>
-__global__ void __launch_bounds__(256)
-k_seed_fields(int nx, int ny, int pitch, const SeedDev* __restrict__ seeds, int n_seeds, double sw,
-              unsigned long long rng_seed, double U0, double T0, double u_in, R* __restrict__ phi,
-              R* __restrict__ U, R* __restrict__ T, R* __restrict__ ux, R* __restrict__ uy, R* __restrict__ rho) {
-    // a block covers blockDim.x x (SEED_ROWS blockDim.y) nodes; it first lists
-    // the seeds that can reach its region (64 at a time)
+__global__ void __launch_bounds__(SEED_BX * SEED_BY)
+k_seed_fill(int nx, int ny, int pitch, R U0, R T0, R ux_liquid, R* __restrict__ phi, R* __restrict__ U,
+            R* __restrict__ T, R* __restrict__ ux, R* __restrict__ uy, R* __restrict__ rho) {
+    const int x = blockIdx.x * SEED_BX + threadIdx.x;
+    if (x >= nx) return;
+#pragma unroll
+    for (int g = 0; g < SEED_ROWS; ++g) {
+        const int y = blockIdx.y * SEED_BH + g * SEED_BY + threadIdx.y;
+        if (y >= ny) break;
+        const size_t o = (size_t)y * pitch + x;
+        phi[o] = R(-1);
+        if (U) U[o] = U0;
+        if (T) T[o] = T0;
+        if (ux) { ux[o] = ux_liquid; uy[o] = R(0); rho[o] = R(1); }
+    }
+}
+
+// blocks: the block indices (by * nbx + bx) to run, one per CUDA block, or
+// null for the whole grid (blockIdx.x, blockIdx.y).  A block first lists the
+// seeds that can reach its region (64 at a time).
+template <typename R>
+__global__ void __launch_bounds__(SEED_BX * SEED_BY)
+k_seed_fields(int nx, int ny, int pitch, const SeedDev* __restrict__ seeds, int n_seeds,
+              const int* __restrict__ blocks, int nbx, double sw, unsigned long long rng_seed, double U0, double T0,
+              double u_in, R* __restrict__ phi, R* __restrict__ U, R* __restrict__ T, R* __restrict__ ux,
+              R* __restrict__ uy, R* __restrict__ rho) {
     __shared__ int list[64];
     __shared__ int cnt;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int t = threadIdx.y * blockDim.x + threadIdx.x;
-    const int bx0 = blockIdx.x * blockDim.x, by0 = blockIdx.y * blockDim.y * SEED_ROWS;
-    const int bx1 = bx0 + blockDim.x, by1 = by0 + blockDim.y * SEED_ROWS;
+    int bxi = blockIdx.x, byi = blockIdx.y;
+    if (blocks) { const int b = blocks[blockIdx.x]; bxi = b % nbx; byi = b / nbx; }
+    const int x = bxi * SEED_BX + threadIdx.x;
+    const int t = threadIdx.y * SEED_BX + threadIdx.x;
+    const int bx0 = bxi * SEED_BX, by0 = byi * SEED_BH;
+    const int bx1 = bx0 + SEED_BX, by1 = by0 + SEED_BH;
     double p[SEED_ROWS];
 #pragma unroll
     for (int g = 0; g < SEED_ROWS; ++g) p[g] = -1.0;
@@ -113,7 +148,7 @@ k_seed_fields(int nx, int ny, int pitch, const SeedDev* __restrict__ seeds, int 
             const SeedDev sd = seeds[list[j]];
 #pragma unroll
             for (int g = 0; g < SEED_ROWS; ++g) {
-                const int y = by0 + g * blockDim.y + threadIdx.y;
+                const int y = by0 + g * SEED_BY + threadIdx.y;
                 if (y >= ny) break;
                 double v;
                 if (sd.kind == 0) {
@@ -138,7 +173,7 @@ k_seed_fields(int nx, int ny, int pitch, const SeedDev* __restrict__ seeds, int 
     if (x >= nx) return;
 #pragma unroll
     for (int g = 0; g < SEED_ROWS; ++g) {
-        const int y = by0 + g * blockDim.y + threadIdx.y;
+        const int y = by0 + g * SEED_BY + threadIdx.y;
         if (y >= ny) break;
         const size_t o = (size_t)y * pitch + x;
         phi[o] = (R)p[g];
@@ -152,6 +187,7 @@ k_seed_fields(int nx, int ny, int pitch, const SeedDev* __restrict__ seeds, int 
     }
 }
 
+// FP64 staging -> arithmetic type, with a pitch
 template <typename R>
 __global__ void k_from_f64(const double* __restrict__ src, R* __restrict__ dst, int nx, int ny, int pitch) {
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
@@ -171,21 +207,25 @@ __global__ void k_out(const KP<R> P, int which, const R* __restrict__ phi, const
     if (gx >= P.nx || gy >= P.ny) return;
     const size_t node = (size_t)gy * P.pitch + gx;
     R v = R(0);
-    const R U = P.has_U ? Um[node] : R(0);
-    O Uo = (O)U;
-    if (P.has_U && lo_kind == 1) Uo += (O)static_cast<const float*>(ulo)[node];
-    if (P.has_U && lo_kind == 2) Uo += (O)__bfloat162float(static_cast<const __nv_bfloat16*>(ulo)[node]);
+    auto u_total = [&]() -> O {         // U and the residual of its compensated macro (read only when asked for)
+        O Uo = (O)(P.has_U ? Um[node] : R(0));
+        if (P.has_U && lo_kind == 1) Uo += (O)static_cast<const float*>(ulo)[node];
+        if (P.has_U && lo_kind == 2) Uo += (O)__bfloat162float(static_cast<const __nv_bfloat16*>(ulo)[node]);
+        return Uo;
+    };
     switch (which) {
         case 0: v = phi[node]; break;
-        case 1: dst[(size_t)gy * P.nx + gx] = Uo; return;
+        case 1: dst[(size_t)gy * P.nx + gx] = u_total(); return;
         case 2: v = P.has_T ? Tm[node] : R(0); break;
         case 3: v = P.has_flow ? uxm[node] : R(0); break;
         case 4: v = P.has_flow ? uym[node] : R(0); break;
         case 5: v = P.has_flow ? rhom[node] : R(1); break;
-        case 6:
+        case 6: {
+            const O Uo = u_total();
             dst[(size_t)gy * P.nx + gx] =
                 O(0.5) * (O(1) + (O(1) - (O)P.k) * Uo) * ((O(1) + (O)P.k) - (O(1) - (O)P.k) * (O)phi[node]);
             return;
+        }
         case 7:
             if (P.has_T) v = (Tm[node] - P.T_shift) * P.inv_T_scale;
             else if (P.frozen_T) v = theta_frozen(P, gy, (R)(*clock) * P.dt_base);
@@ -204,9 +244,26 @@ __global__ void k_out(const KP<R> P, int which, const R* __restrict__ phi, const
 // ... (threads across each row), so the order is fixed for a given lattice.
 // FP64 arithmetic is a small fraction of the FP32 rate on this GPU: with an
 // FP32 state the solute term (the conservation diagnostic, Eq. 39) is formed
-// in FP64 from the stored macro values (the compensated macro's residual
-// plane, ~1e-8 of them, in FP32), the enthalpy term in FP32, and the
-// non-finite test runs on the stored values; the sums accumulate in FP64.
+// from the stored macro values in double-float arithmetic (a value held as
+// the unevaluated sum of two FP32 numbers: Dekker's product via a fused
+// multiply-add, Knuth's TwoSum; about 2^-46 relative per term) and summed
+// per thread the same way, the residual plane's part (~1e-8 of the rest) in
+// FP32; the enthalpy term is formed in FP32 and summed in double-float; the
+// non-finite test runs on the stored values.  Each thread's sums become FP64
+// once, and the warp, block and grid sums are FP64.  An FP64 state takes FP64
+// throughout.
+struct DFloat { float h, l; };                 // h + l, |l| <= ulp(h) / 2 after renormalising
+__device__ __forceinline__ void df_add(DFloat& s, float h, float l) {
+    float t, e;
+    two_sum(s.h, h, t, e);
+    s.h = t;
+    s.l = add_rn(s.l, add_rn(e, l));
+}
+// a b + c as (hi, lo): hi = fl(a b), lo = c + (a b - hi) rounded once
+__device__ __forceinline__ void df_mul(float a, float b, float& hi, float& lo) {
+    hi = __fmul_rn(a, b);
+    lo = __fmaf_rn(a, b, -hi);
+}
 template <typename R, typename Lo = R>
 __global__ void __launch_bounds__(256)
 k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ Um, const R* __restrict__ Tm,
@@ -221,6 +278,10 @@ k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ U
     R mlo = R(0);
     const double omk = 1.0 - (double)P.k, opk = 1.0 + (double)P.k;
     const R omkR = R(1) - P.k, opkR = R(1) + P.k;
+    // FP32 state: 1 - k and 1 + k as double-float pairs, the sums as pairs
+    const float omk_h = (float)omk, omk_l = (float)(omk - (double)omk_h);
+    const float opk_h = (float)opk, opk_l = (float)(opk - (double)opk_h);
+    DFloat smc{0.f, 0.f}, sh{0.f, 0.f};
     for (int y = blockIdx.x; y < P.ny; y += gridDim.x) {
         const size_t row = (size_t)y * P.pitch;
         for (int x = threadIdx.x; x < P.nx; x += blockDim.x) {
@@ -230,15 +291,36 @@ k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ U
             const R T = P.has_T ? Tm[node] : R(0);
             const R vx = P.has_flow ? uxm[node] : R(0), vy = P.has_flow ? uym[node] : R(0);
             if (P.has_U) {
-                mc += fma(omk, (double)U, 1.0) * fma(-omk, (double)ph, opk);
+                if constexpr (sizeof(R) == 8) {
+                    mc += fma(omk, (double)U, 1.0) * fma(-omk, (double)ph, opk);
+                } else {
+                    // A = 1 + (1 - k) U and B = (1 + k) - (1 - k) phi as pairs, then A B
+                    float pa, ea, pb, eb, ah, at, bh, bt, mh, ml;
+                    df_mul(omk_h, (float)U, pa, ea);
+                    ea = __fmaf_rn(omk_l, (float)U, ea);
+                    two_sum(1.0f, pa, ah, at);
+                    const float al = add_rn(at, ea);
+                    df_mul(omk_h, (float)ph, pb, eb);
+                    eb = __fmaf_rn(omk_l, (float)ph, eb);
+                    two_sum(opk_h, -pb, bh, bt);
+                    const float bl = sub_rn(add_rn(bt, opk_l), eb);
+                    df_mul(ah, bh, mh, ml);
+                    ml = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, ml));
+                    df_add(smc, mh, ml);
+                }
                 if (Ulo) mlo += omkR * (R)Cvt<Lo>::ld(Ulo[node]) * (opkR - omkR * ph);
             }
             if (P.has_T) {
                 const R ht = (R(0.5) * (R(1) + ph) * P.cS + R(0.5) * (R(1) - ph) * P.cL) * T - R(0.5) * P.rhoL_Lh * ph;
-                h += (double)ht;
+                if constexpr (sizeof(R) == 8) h += ht;
+                else df_add(sh, (float)ht, 0.f);
             }
             if (!isfinite(ph) || !isfinite(U) || !isfinite(T) || !isfinite(vx) || !isfinite(vy)) bad += 1.0;
         }
+    }
+    if constexpr (sizeof(R) == 4) {
+        mc = (double)smc.h + (double)smc.l;
+        h = (double)sh.h + (double)sh.l;
     }
     mc = 0.5 * (mc + (double)mlo);
 #pragma unroll
@@ -258,11 +340,15 @@ k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ U
 }
 
 // out[0..2] = totals of the partials (fixed order), out[3..6] tips,
-// out[7] = S_phi, out[8] = J_U; the maxima slots are then cleared.
+// out[7] = S_phi, out[8] = J_U; the maxima slots are then cleared.  One block
+// of DIAG_FINAL_THREADS: warp 0 sums the partials, and four warps scan each
+// tip direction.
+constexpr int DIAG_FINAL_THREADS = 512;
 template <typename R>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(DIAG_FINAL_THREADS)
 k_diag_final(const KP<R> P, const double* __restrict__ part, int nblocks, const R* __restrict__ phi, int cx, int cy,
              unsigned long long* __restrict__ smax, double* __restrict__ out) {
+    __shared__ int sbest[DIAG_FINAL_THREADS / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) {
         double a[3] = {0.0, 0.0, 0.0};
@@ -279,8 +365,9 @@ k_diag_final(const KP<R> P, const double* __restrict__ part, int nblocks, const 
             out[8] = __longlong_as_double((long long)smax[1]);
         }
     }
-    // tips: warp d scans direction d (+x, +y, -x, -y) for the outermost crossing
-    const int d = warp;
+    // tips: warps 4d .. 4d + 3 scan direction d (+x, +y, -x, -y) for the
+    // outermost crossing
+    const int d = warp >> 2, sub = warp & 3;
     const int len = (d == 0) ? P.nx - cx : (d == 1) ? P.ny - cy : (d == 2) ? cx + 1 : cy + 1;
     auto at = [&](int k) -> double {
         const int x = (d == 0) ? cx + k : (d == 2) ? cx - k : cx;
@@ -288,11 +375,15 @@ k_diag_final(const KP<R> P, const double* __restrict__ part, int nblocks, const 
         return (double)phi[(size_t)y * P.pitch + x];
     };
     int best = -1;
-    for (int k = lane; k < len - 1; k += 32)
+#pragma unroll 4
+    for (int k = 32 * sub + lane; k < len - 1; k += 128)
         if (at(k) >= 0.0 && at(k + 1) < 0.0) best = max(best, k);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if (lane == 0) {
+    if (lane == 0) sbest[warp] = best;
+    __syncthreads();
+    if (sub == 0 && lane == 0) {
+        best = max(max(sbest[warp], sbest[warp + 1]), max(sbest[warp + 2], sbest[warp + 3]));
         double r = 0.0;
         if (len > 0 && at(len - 1) >= 0.0) r = (double)(len - 1);
         else if (best >= 0) { const double a = at(best), b = at(best + 1); r = (double)best + a / (a - b); }
