@@ -1062,7 +1062,7 @@ lbm_status graph_replay(lbm_sim* h, SimState& s, int which) {
     return LBM_OK;
 }
 
-template <typename R> void enqueue_diag(lbm_sim* h, SimState& s);
+template <typename R> void enqueue_diag(lbm_sim* h, SimState& s, bool solute_only = false);
 
 // seeded: the macroscopic fields come from lbm_init_seed (U = U0, T = T0,
 // u_y = 0, rho = 1 everywhere)
@@ -1151,7 +1151,7 @@ lbm_status finish_init(lbm_sim* h, SimState& s, bool seeded, double U0, double T
     if (s.clock) CK(cudaMemsetAsync(s.clock, 0, sizeof(long long), h->stream));
     {   // solute inventory of the initial state: the reference M_C(0) of R_M (Sec. 4.4)
         LaunchScope ls(h, LBM_K_INIT);
-        enqueue_diag<R>(h, s);
+        enqueue_diag<R>(h, s, true);
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(s.dout + 9, s.dout, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -1249,28 +1249,32 @@ lbm_status read_field(lbm_sim* h, SimState& s, uint32_t which, void* dst, int ds
 }
 
 // The diagnostics reductions of simulation s into s.dout[0..8] (asynchronous).
+// solute_only: dout[0] (M_C, bit for bit the value of the full reduction) and
+// the cleared maxima only; the other slots are left as they were.
 template <typename R>
-void enqueue_diag(lbm_sim* h, SimState& s) {
+void enqueue_diag(lbm_sim* h, SimState& s, bool solute_only) {
     const KP<R> P = make_kp<R>(s);
     {
         const int fc = s.cur_pop[FF];
         const R* Um = s.has_U ? (const R*)s.U[s.cur_U] : nullptr;
         const R* Tm = s.has_T ? (const R*)s.T[s.cur_T] : nullptr;
+        const int so = solute_only ? 1 : 0;
         // the solute sum includes the residual plane of the compensated U macro
         if constexpr (sizeof(R) == 4) {
             if (s.has_U)
                 k_diag_partial<R, __nv_bfloat16><<<s.diag_blocks, 256, 0, h->stream>>>(
                     P, (const R*)s.phi[s.cur_phi], Um, Tm, (const R*)s.ux[fc], (const R*)s.uy[fc], s.part,
-                    u_residual(h, s));
+                    u_residual(h, s), so);
             else
-                k_diag_partial<R><<<s.diag_blocks, 256, 0, h->stream>>>(
-                    P, (const R*)s.phi[s.cur_phi], Um, Tm, (const R*)s.ux[fc], (const R*)s.uy[fc], s.part);
+                k_diag_partial<R, R><<<s.diag_blocks, 256, 0, h->stream>>>(
+                    P, (const R*)s.phi[s.cur_phi], Um, Tm, (const R*)s.ux[fc], (const R*)s.uy[fc], s.part, nullptr,
+                    so);
         } else {
-            k_diag_partial<R><<<s.diag_blocks, 256, 0, h->stream>>>(
-                P, (const R*)s.phi[s.cur_phi], Um, Tm, (const R*)s.ux[fc], (const R*)s.uy[fc], s.part);
+            k_diag_partial<R, R><<<s.diag_blocks, 256, 0, h->stream>>>(
+                P, (const R*)s.phi[s.cur_phi], Um, Tm, (const R*)s.ux[fc], (const R*)s.uy[fc], s.part, nullptr, so);
         }
-        k_diag_final<R><<<1, DIAG_FINAL_THREADS, 0, h->stream>>>(P, s.part, s.diag_blocks, (const R*)s.phi[s.cur_phi], s.p.tip_cx,
-                                                 s.p.tip_cy, s.smax, s.dout);
+        k_diag_final<R><<<1, DIAG_FINAL_THREADS, 0, h->stream>>>(P, s.part, s.diag_blocks, (const R*)s.phi[s.cur_phi],
+                                                                 s.p.tip_cx, s.p.tip_cy, s.smax, s.dout, so);
     }
 }
 

@@ -264,11 +264,14 @@ __device__ __forceinline__ void df_mul(float a, float b, float& hi, float& lo) {
     hi = __fmul_rn(a, b);
     lo = __fmaf_rn(a, b, -hi);
 }
+// solute_only: the solute sum alone (T, u_x, u_y are not read; the enthalpy
+// and non-finite slots are zero), each thread's order unchanged, so M_C is
+// the same to the last bit.
 template <typename R, typename Lo = R>
 __global__ void __launch_bounds__(256)
 k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ Um, const R* __restrict__ Tm,
                const R* __restrict__ uxm, const R* __restrict__ uym, double* __restrict__ part,
-               const Lo* __restrict__ Ulo = nullptr) {
+               const Lo* __restrict__ Ulo = nullptr, int solute_only = 0) {
     __shared__ double s[3][8];
     // mc: twice the solute sum of the stored macros (the factor 1/2 of C is
     // applied once at the end: exact); mlo: the residual plane's part,
@@ -288,8 +291,9 @@ k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ U
             const size_t node = row + x;
             const R ph = phi[node];
             const R U = P.has_U ? Um[node] : R(0);
-            const R T = P.has_T ? Tm[node] : R(0);
-            const R vx = P.has_flow ? uxm[node] : R(0), vy = P.has_flow ? uym[node] : R(0);
+            const bool full = !solute_only;
+            const R T = P.has_T && full ? Tm[node] : R(0);
+            const R vx = P.has_flow && full ? uxm[node] : R(0), vy = P.has_flow && full ? uym[node] : R(0);
             if (P.has_U) {
                 if constexpr (sizeof(R) == 8) {
                     mc += fma(omk, (double)U, 1.0) * fma(-omk, (double)ph, opk);
@@ -310,12 +314,12 @@ k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ U
                 }
                 if (Ulo) mlo += omkR * (R)Cvt<Lo>::ld(Ulo[node]) * (opkR - omkR * ph);
             }
-            if (P.has_T) {
+            if (P.has_T && full) {
                 const R ht = (R(0.5) * (R(1) + ph) * P.cS + R(0.5) * (R(1) - ph) * P.cL) * T - R(0.5) * P.rhoL_Lh * ph;
                 if constexpr (sizeof(R) == 8) h += ht;
                 else df_add(sh, (float)ht, 0.f);
             }
-            if (!isfinite(ph) || !isfinite(U) || !isfinite(T) || !isfinite(vx) || !isfinite(vy)) bad += 1.0;
+            if (full && (!isfinite(ph) || !isfinite(U) || !isfinite(T) || !isfinite(vx) || !isfinite(vy))) bad += 1.0;
         }
     }
     if constexpr (sizeof(R) == 4) {
@@ -342,12 +346,12 @@ k_diag_partial(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ U
 // out[0..2] = totals of the partials (fixed order), out[3..6] tips,
 // out[7] = S_phi, out[8] = J_U; the maxima slots are then cleared.  One block
 // of DIAG_FINAL_THREADS: warp 0 sums the partials, and four warps scan each
-// tip direction.
+// tip direction.  sums_only: out[0..2] and the maxima only (tips not scanned).
 constexpr int DIAG_FINAL_THREADS = 512;
 template <typename R>
 __global__ void __launch_bounds__(DIAG_FINAL_THREADS)
 k_diag_final(const KP<R> P, const double* __restrict__ part, int nblocks, const R* __restrict__ phi, int cx, int cy,
-             unsigned long long* __restrict__ smax, double* __restrict__ out) {
+             unsigned long long* __restrict__ smax, double* __restrict__ out, int sums_only = 0) {
     __shared__ int sbest[DIAG_FINAL_THREADS / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) {
@@ -365,29 +369,31 @@ k_diag_final(const KP<R> P, const double* __restrict__ part, int nblocks, const 
             out[8] = __longlong_as_double((long long)smax[1]);
         }
     }
-    // tips: warps 4d .. 4d + 3 scan direction d (+x, +y, -x, -y) for the
-    // outermost crossing
-    const int d = warp >> 2, sub = warp & 3;
-    const int len = (d == 0) ? P.nx - cx : (d == 1) ? P.ny - cy : (d == 2) ? cx + 1 : cy + 1;
-    auto at = [&](int k) -> double {
-        const int x = (d == 0) ? cx + k : (d == 2) ? cx - k : cx;
-        const int y = (d == 1) ? cy + k : (d == 3) ? cy - k : cy;
-        return (double)phi[(size_t)y * P.pitch + x];
-    };
-    int best = -1;
+    if (!sums_only) {          // uniform over the block: its barriers are reached by every thread
+        // tips: warps 4d .. 4d + 3 scan direction d (+x, +y, -x, -y) for the
+        // outermost crossing
+        const int d = warp >> 2, sub = warp & 3;
+        const int len = (d == 0) ? P.nx - cx : (d == 1) ? P.ny - cy : (d == 2) ? cx + 1 : cy + 1;
+        auto at = [&](int k) -> double {
+            const int x = (d == 0) ? cx + k : (d == 2) ? cx - k : cx;
+            const int y = (d == 1) ? cy + k : (d == 3) ? cy - k : cy;
+            return (double)phi[(size_t)y * P.pitch + x];
+        };
+        int best = -1;
 #pragma unroll 4
-    for (int k = 32 * sub + lane; k < len - 1; k += 128)
-        if (at(k) >= 0.0 && at(k + 1) < 0.0) best = max(best, k);
+        for (int k = 32 * sub + lane; k < len - 1; k += 128)
+            if (at(k) >= 0.0 && at(k + 1) < 0.0) best = max(best, k);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if (lane == 0) sbest[warp] = best;
-    __syncthreads();
-    if (sub == 0 && lane == 0) {
-        best = max(max(sbest[warp], sbest[warp + 1]), max(sbest[warp + 2], sbest[warp + 3]));
-        double r = 0.0;
-        if (len > 0 && at(len - 1) >= 0.0) r = (double)(len - 1);
-        else if (best >= 0) { const double a = at(best), b = at(best + 1); r = (double)best + a / (a - b); }
-        out[3 + d] = r;
+        for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (lane == 0) sbest[warp] = best;
+        __syncthreads();
+        if (sub == 0 && lane == 0) {
+            best = max(max(sbest[warp], sbest[warp + 1]), max(sbest[warp + 2], sbest[warp + 3]));
+            double r = 0.0;
+            if (len > 0 && at(len - 1) >= 0.0) r = (double)(len - 1);
+            else if (best >= 0) { const double a = at(best), b = at(best + 1); r = (double)best + a / (a - b); }
+            out[3 + d] = r;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) { smax[0] = 0ull; smax[1] = 0ull; }

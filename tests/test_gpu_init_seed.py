@@ -1,8 +1,9 @@
 """lbm_init_seed generates the initial fields on the device (FP64 arithmetic
 per node) from the seed list: compared with the seeded generators of
 workloads (numpy, FP64) on lattices with many circles, circles clipped by
-the lattice edges, a sinusoidal layer (Eq. 41) and a noisy planar front,
-for FP64 and FP32 storage, with and without the flow."""
+the lattice edges, circles wholly off the lattice, a sinusoidal layer
+(Eq. 41) and a noisy planar front, for FP64 and FP32 storage, with and
+without the flow."""
 import math
 
 import numpy as np
@@ -39,6 +40,23 @@ def test_many_circles_match_the_generator(precision, tol):
     sim.init_seed([{"kind": "circle", "x": float(x), "y": float(y), "r": R} for x, y in pts], U0=0.02, T0=-0.4)
     for k in ("phi", "U", "T", "ux", "uy", "rho"):
         assert np.abs(sim.field(k) - want[k]).max() < tol, k
+    sim.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-14), ("f32", 1e-7)])
+def test_seeds_off_the_lattice(precision, tol):
+    """A circle whose reach misses the lattice reaches no block; with every
+    seed off the lattice no block is seeded and the fields are the liquid
+    values alone (phi = -1, u_x = u_in)."""
+    p, pts = _circles_case(n=300, m=200, count=4)
+    far = np.array([[-500.0, 50.0], [150.0, 900.0], [1e4, -1e4]])
+    sim = lbm.Simulation(p, precision=precision)
+    for cen in (np.vstack([pts, far]), far):
+        sim.init_seed([{"kind": "circle", "x": float(x), "y": float(y), "r": 7.5} for x, y in cen], U0=0.01, T0=-0.3)
+        want = W.circle_seeds_window(p, cen, 7.5, 0, 0, p.nx, p.ny, U0=0.01, T0=-0.3)
+        for k in ("phi", "U", "T", "ux", "uy", "rho"):
+            assert np.abs(sim.field(k) - want[k]).max() < tol, k
+    assert np.all(sim.field("phi") == -1.0)
     sim.close()
 
 
