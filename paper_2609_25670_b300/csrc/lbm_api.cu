@@ -1208,7 +1208,7 @@ lbm_status init_common(lbm_sim* h, int32_t sim, const double* src[6], int src_de
 template <typename R>
 lbm_status read_field(lbm_sim* h, SimState& s, uint32_t which, void* dst, int dst_dev, int as_f64) {
     const KP<R> P = make_kp<R>(s);
-    const dim3 blk(32, 8), grd((s.nx + 31) / 32, (s.ny + 7) / 8);
+    const dim3 blk(32, 8), grd((s.nx + 31) / 32, (s.ny + 8 * OUT_ROWS - 1) / (8 * OUT_ROWS));
     const size_t n = (size_t)s.nx * s.ny;
     const size_t esz = as_f64 ? sizeof(double) : sizeof(R);
     void* out = dst;

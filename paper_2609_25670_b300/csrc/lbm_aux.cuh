@@ -197,42 +197,59 @@ __global__ void k_from_f64(const double* __restrict__ src, R* __restrict__ dst, 
 // derived output fields into a dense ny x nx buffer of type O
 // which: 0 phi 1 U 2 T 3 ux 4 uy 5 rho 6 C/C_inf 7 theta.  ulo: the residual
 // plane of the compensated U macro (lo_kind 1: float, 2: BF16; 0: none),
-// added to U in U and C/C_inf.
+// added to U in U and C/C_inf.  A block of blockDim.x x blockDim.y threads
+// covers OUT_ROWS groups of blockDim.y rows: with one node per thread the
+// launch of a one-load, one-store copy ran at the rate blocks are started.
+constexpr int OUT_ROWS = 8;
 template <typename R, typename O>
 __global__ void k_out(const KP<R> P, int which, const R* __restrict__ phi, const R* __restrict__ Um,
                       const R* __restrict__ Tm, const R* __restrict__ uxm, const R* __restrict__ uym,
                       const R* __restrict__ rhom, const void* __restrict__ ulo, int lo_kind,
                       O* __restrict__ dst, const long long* __restrict__ clock) {
-    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
-    if (gx >= P.nx || gy >= P.ny) return;
-    const size_t node = (size_t)gy * P.pitch + gx;
-    R v = R(0);
-    auto u_total = [&]() -> O {         // U and the residual of its compensated macro (read only when asked for)
-        O Uo = (O)(P.has_U ? Um[node] : R(0));
-        if (P.has_U && lo_kind == 1) Uo += (O)static_cast<const float*>(ulo)[node];
-        if (P.has_U && lo_kind == 2) Uo += (O)__bfloat162float(static_cast<const __nv_bfloat16*>(ulo)[node]);
-        return Uo;
-    };
-    switch (which) {
-        case 0: v = phi[node]; break;
-        case 1: dst[(size_t)gy * P.nx + gx] = u_total(); return;
-        case 2: v = P.has_T ? Tm[node] : R(0); break;
-        case 3: v = P.has_flow ? uxm[node] : R(0); break;
-        case 4: v = P.has_flow ? uym[node] : R(0); break;
-        case 5: v = P.has_flow ? rhom[node] : R(1); break;
-        case 6: {
-            const O Uo = u_total();
-            dst[(size_t)gy * P.nx + gx] =
-                O(0.5) * (O(1) + (O(1) - (O)P.k) * Uo) * ((O(1) + (O)P.k) - (O(1) - (O)P.k) * (O)phi[node]);
-            return;
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gx >= P.nx) return;
+    // every row's value first, then the stores: the loads of the OUT_ROWS rows
+    // are in flight together
+    O vals[OUT_ROWS];
+#pragma unroll
+    for (int g = 0; g < OUT_ROWS; ++g) {
+        const int gy = (blockIdx.y * OUT_ROWS + g) * blockDim.y + threadIdx.y;
+        vals[g] = O(0);
+        if (gy >= P.ny) continue;
+        const size_t node = (size_t)gy * P.pitch + gx;
+        auto u_total = [&]() -> O {     // U and the residual of its compensated macro (read only when asked for)
+            O Uo = (O)(P.has_U ? Um[node] : R(0));
+            if (P.has_U && lo_kind == 1) Uo += (O)static_cast<const float*>(ulo)[node];
+            if (P.has_U && lo_kind == 2) Uo += (O)__bfloat162float(static_cast<const __nv_bfloat16*>(ulo)[node]);
+            return Uo;
+        };
+        switch (which) {
+            case 0: vals[g] = (O)phi[node]; break;
+            case 1: vals[g] = u_total(); break;
+            case 2: vals[g] = (O)(P.has_T ? Tm[node] : R(0)); break;
+            case 3: vals[g] = (O)(P.has_flow ? uxm[node] : R(0)); break;
+            case 4: vals[g] = (O)(P.has_flow ? uym[node] : R(0)); break;
+            case 5: vals[g] = (O)(P.has_flow ? rhom[node] : R(1)); break;
+            case 6: {
+                const O Uo = u_total();
+                vals[g] = O(0.5) * (O(1) + (O(1) - (O)P.k) * Uo) * ((O(1) + (O)P.k) - (O(1) - (O)P.k) * (O)phi[node]);
+                break;
+            }
+            case 7: {
+                R v;
+                if (P.has_T) v = (Tm[node] - P.T_shift) * P.inv_T_scale;
+                else if (P.frozen_T) v = theta_frozen(P, gy, (R)(*clock) * P.dt_base);
+                else v = P.theta_c;
+                vals[g] = (O)v;
+                break;
+            }
         }
-        case 7:
-            if (P.has_T) v = (Tm[node] - P.T_shift) * P.inv_T_scale;
-            else if (P.frozen_T) v = theta_frozen(P, gy, (R)(*clock) * P.dt_base);
-            else v = P.theta_c;
-            break;
     }
-    dst[(size_t)gy * P.nx + gx] = (O)v;
+#pragma unroll
+    for (int g = 0; g < OUT_ROWS; ++g) {
+        const int gy = (blockIdx.y * OUT_ROWS + g) * blockDim.y + threadIdx.y;
+        if (gy < P.ny) dst[(size_t)gy * P.nx + gx] = vals[g];
+    }
 }
 
 // ---------------------------------------------------------------------------
