@@ -1111,38 +1111,31 @@ lbm_status upload_and_init(lbm_sim* h, SimState& s, const double* src[6], int sr
 // Everything after the macroscopic fields of buffer 0 are in place: the
 // equilibrium populations, cleared accumulators and maxima, the reference
 // solute inventory M_C(0), the clock.
+// the initial distributions of buffer 0 (k_init), for the phase lattice's
+// velocity count
+template <typename R, typename ST, bool DEV>
+void launch_init(lbm_sim* h, SimState& s, bool seeded, double U0, double T0) {
+    const dim3 blk(32, 8), grd((s.nx + 31) / 32, (s.ny + 7) / 8);
+    const auto kern = h->q == 5 ? &k_init<R, ST, DEV, 5> : &k_init<R, ST, DEV, 9>;
+    kern<<<grd, blk, 0, h->stream>>>(make_kp<R>(s), (const R*)s.phi[0], (const R*)s.U[0], (const R*)s.T[0],
+                                     (const R*)s.ux[0], (const R*)s.uy[0], (const R*)s.rho[0], (ST*)s.pops[FP][0],
+                                     (ST*)s.pops[FU][0], (ST*)s.pops[FT][0], (ST*)s.pops[FF][0], (int)seeded, (R)U0,
+                                     (R)T0);
+}
+
 template <typename R>
 lbm_status finish_init(lbm_sim* h, SimState& s, bool seeded, double U0, double T0) {
-    const dim3 blk(32, 8), grd((s.nx + 31) / 32, (s.ny + 7) / 8);
     s.cur_phi = s.cur_U = s.cur_T = 0;
     for (int f = 0; f < 4; ++f) s.cur_pop[f] = 0;
-    const KP<R> P = make_kp<R>(s);
     {
         LaunchScope ls(h, LBM_K_INIT);
         switch (h->precision) {
             case LBM_PREC_F64:
-            case LBM_PREC_F32:
-                k_init<R, R, false><<<grd, blk, 0, h->stream>>>(P, h->q, (const R*)s.phi[0], (const R*)s.U[0], (const R*)s.T[0],
-                                                               (const R*)s.ux[0], (const R*)s.uy[0], (const R*)s.rho[0],
-                                                               (R*)s.pops[FP][0], (R*)s.pops[FU][0], (R*)s.pops[FT][0],
-                                                               (R*)s.pops[FF][0], (int)seeded, (R)U0, (R)T0);
-                break;
-            case LBM_PREC_F16_DEV:
-                k_init<float, __half, true><<<grd, blk, 0, h->stream>>>(
-                    make_kp<float>(s), h->q, (const float*)s.phi[0], (const float*)s.U[0], (const float*)s.T[0],
-                    (const float*)s.ux[0], (const float*)s.uy[0], (const float*)s.rho[0], (__half*)s.pops[FP][0],
-                    (__half*)s.pops[FU][0], (__half*)s.pops[FT][0], (__half*)s.pops[FF][0], (int)seeded, (float)U0,
-                    (float)T0);
-                break;
-            default:
-                k_init<float, __nv_bfloat16, true><<<grd, blk, 0, h->stream>>>(
-                    make_kp<float>(s), h->q, (const float*)s.phi[0], (const float*)s.U[0], (const float*)s.T[0],
-                    (const float*)s.ux[0], (const float*)s.uy[0], (const float*)s.rho[0], (__nv_bfloat16*)s.pops[FP][0],
-                    (__nv_bfloat16*)s.pops[FU][0], (__nv_bfloat16*)s.pops[FT][0], (__nv_bfloat16*)s.pops[FF][0],
-                    (int)seeded, (float)U0, (float)T0);
+            case LBM_PREC_F32: launch_init<R, R, false>(h, s, seeded, U0, T0); break;
+            case LBM_PREC_F16_DEV: launch_init<float, __half, true>(h, s, seeded, U0, T0); break;
+            default: launch_init<float, __nv_bfloat16, true>(h, s, seeded, U0, T0);
         }
     }
-    (void)P;
     CK(cudaGetLastError());
     const size_t rs = sizeof(R);
     if (s.accU) CK(cudaMemsetAsync(s.accU, 0, 2 * s.nn * rs, h->stream));

@@ -7,13 +7,16 @@ namespace lbmk {
 
 // ---------------------------------------------------------------------------
 // Initial distributions f = f_eq of the macroscopic fields (Eqs. 19, 21, 28);
-// for U and T their first moments, the stored state of those fields.  q: the
+// for U and T their first moments, the stored state of those fields.  Q: the
 // velocities of the phase lattice (9, or 5 for D2Q5: populations 1..4 only).
 // seeded: the fields come from seed primitives, so U = U0, T = T0, u_y = 0
-// and rho = 1 on every node and only phi and u_x are read.
+// and rho = 1 on every node and only phi and u_x are read.  (The kernel is
+// bound by instruction issue: interior nodes read their 3 x 3 neighbourhood
+// at fixed offsets, and only the lattice's edge nodes map ghosts; eight
+// blocks of 256 threads stay resident, as with one ghost map per neighbour.)
 // ---------------------------------------------------------------------------
-template <typename R, typename ST, bool DEV>
-__global__ void k_init(const KP<R> P, int q, const R* __restrict__ phi, const R* __restrict__ Um,
+template <typename R, typename ST, bool DEV, int Q>
+__global__ void __launch_bounds__(256, 8) k_init(const KP<R> P, const R* __restrict__ phi, const R* __restrict__ Um,
                        const R* __restrict__ Tm, const R* __restrict__ uxm, const R* __restrict__ uym,
                        const R* __restrict__ rhom, ST* __restrict__ fphi, ST* __restrict__ fU, ST* __restrict__ fT,
                        ST* __restrict__ fF, int seeded, R U0, R T0) {
@@ -22,9 +25,18 @@ __global__ void k_init(const KP<R> P, int q, const R* __restrict__ phi, const R*
     const size_t node = (size_t)gy * P.pitch + gx;
     // gradient with the same ghost rule as the update kernels
     R s[3][3];
-    for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx)
-            s[dy + 1][dx + 1] = phi[(size_t)scalar_map(gy + dy, P.ny, P.bsy) * P.pitch + scalar_map(gx + dx, P.nx, P.bsx)];
+    if (gx > 0 && gx < P.nx - 1 && gy > 0 && gy < P.ny - 1) {
+        const R* c = phi + node;
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) s[dy + 1][dx + 1] = c[(ptrdiff_t)dy * P.pitch + dx];
+    } else {
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx)
+                s[dy + 1][dx + 1] =
+                    phi[(size_t)scalar_map(gy + dy, P.ny, P.bsy) * P.pitch + scalar_map(gx + dx, P.nx, P.bsx)];
+    }
     const R gxv = (s[1][2] - s[1][0]) * (R(1) / R(3)) + (s[2][2] - s[2][0] + s[0][2] - s[0][0]) * (R(1) / R(12));
     const R gyv = (s[2][1] - s[0][1]) * (R(1) / R(3)) + (s[2][2] + s[2][0] - s[0][2] - s[0][0]) * (R(1) / R(12));
     R as, Nx, Ny;
@@ -38,9 +50,8 @@ __global__ void k_init(const KP<R> P, int q, const R* __restrict__ phi, const R*
         if (!seeded) { vy = uym[node]; rho = rhom[node]; }
     }
 #pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        if (i >= q) break;
-        const R w = q == 5 ? wqq<R, 5>(i) : wq<R>(i), ex = (R)c_ex[i], ey = (R)c_ey[i];
+    for (int i = 1; i < Q; ++i) {
+        const R w = Q == 5 ? wqq<R, 5>(i) : wq<R>(i), ex = (R)c_ex[i], ey = (R)c_ey[i];
         const R dp = R(3) * w * (ex * bx + ey * by);                                   // Eq. 21 minus w_i phi
         fphi[(size_t)(i - 1) * P.plane + node] = Cvt<ST>::st(DEV ? dp : w * ph + dp);
     }
